@@ -1,0 +1,316 @@
+"""Benchmark of the WFP time march on GB300: scatterer-steps per second (M * steps / s).
+
+Workload: free space, M = 1e4 springs uniform in Omega, stiffnesses log-uniform in [0.1, 100],
+three Gaussian pulses (widths 0.02, 0.05, 0.1), dt = 1e-3, tol = 1e-12, p = 8 (seeded synthetic
+input, `workloads.config1`).  One step = one pass of the whole hot path (local sum, type-1 NUFFT,
+mode update, radiation projection on projection steps, type-2 NUFFT, implicit solve, receivers).
+
+Timing: W untimed warm-up steps, then K steps; before every timed step the L2 cache is flushed by
+writing a 512 MiB buffer, and each step is timed with CUDA events on the caller's stream (the plan's
+work is stream-ordered on it).  The march state stays on the device between steps.
+
+`--impl reference` times the plain CPU oracle of the same scheme (oracle/wfp.py) on the host
+cores, on the same workload, one oracle time step per bench step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "scatterer-steps/s (M*N_t/s) at stated error vs FP64 oracle; % of HBM roofline"
+UNIT = "scatterer-steps/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons while the timed region runs."""
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"wave1d_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        except Exception:
+            return out
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [c.strip() for c in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except Exception:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if sm:
+            out.update(sm_mhz=float(np.median(sm)), sm_max_mhz=float(max(mx)), samples=len(sm))
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2507_07823_gb300 import build, wave1d, workloads
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    w = workloads.config1()
+    K, Wm = args.steps, args.warmup
+    assert Wm >= 3
+    stream = torch.cuda.current_stream()
+    t_plan = time.perf_counter()
+    plan = wave1d.Plan.from_workload(w.with_(Nt=Wm + 3 * K + 16), stream=stream.cuda_stream)
+    t_plan = time.perf_counter() - t_plan
+    info = plan.info
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    for _ in range(Wm):
+        plan.step()
+    torch.cuda.synchronize()
+
+    # --- device-timed march: K steps, L2 flushed before each -------------------------------
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        for i in range(K):
+            flush.zero_()
+            evs[i][0].record(stream)
+            wave1d._check(wave1d.wave1d_step(plan.h), "wave1d_step")
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    ms_steps = [a.elapsed_time(b) for a, b in evs]
+    ms_total = float(sum(ms_steps))
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms_total], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+        dist.barrier()
+    value = w.M * K * world / (ms_total * 1e-3)
+
+    # --- per-stage device times (CUDA events between the stages, same plan, K steps) --------
+    wave1d.wave1d_profile(plan.h, 1)
+    for i in range(K):
+        flush.zero_()
+        wave1d._check(wave1d.wave1d_step(plan.h), "wave1d_step")
+    stage_ms, nprof = wave1d.wave1d_profile_read(plan.h)
+    wave1d.wave1d_profile(plan.h, 0)
+    per_step = {s: float(stage_ms[i] / nprof) for i, s in enumerate(wave1d.STAGES)}
+    top = max(per_step, key=per_step.get)
+
+    # --- end to end through the public API with host buffers ------------------------------------
+    # forcing g_j(t_{n+1}) = beta_j f(x_j - t_{n+1}) supplied from pinned host memory every step,
+    # densities read back to pinned host memory every step
+    n0 = plan.info.n if hasattr(plan.info, "n") else 0
+    cur = wave1d.wave1d_get_info(plan.h).n
+    g_host = torch.empty((K, w.M), dtype=torch.float64, pin_memory=True)
+    tt = (cur + 1 + np.arange(K)) * w.dt
+    f = np.zeros((K, w.M))
+    for a, c, wd in zip(w.amp, w.center, w.width):
+        f += a * np.exp(-0.5 * ((w.x[None, :] - tt[:, None] - c) / wd) ** 2)
+    g_host.numpy()[:] = w.beta[None, :] * f
+    out_host = torch.empty((K, w.M), dtype=torch.float64, pin_memory=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(K):
+        wave1d._check(wave1d.wave1d_step(plan.h, g_host[i].numpy(), 0), "wave1d_step")
+        wave1d._check(wave1d.wave1d_get_sigma(plan.h, out_host[i].numpy(), 0), "wave1d_get_sigma")
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_value = w.M * K * world / e2e_s
+    del n0
+
+    # --- roofline of the dominant kernel -------------------------------------------------------
+    hbm, peak_kind = _peaks()
+    bytes_per_step = stage_bytes(info, w, top)
+    achieved = bytes_per_step / (per_step[top] * 1e-3) / 1e9 if bytes_per_step else None
+    roof = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": (achieved / hbm) if achieved else None, "traffic": None,
+            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s",
+            "algorithmic_bytes_per_launch": bytes_per_step}
+    launches = 13 * K + (K // info.rbc_period + 1) * 2
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": Wm, "ms_per_step": ms_total / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{w.name}: {w.description}", "M": w.M, "dt": w.dt,
+                   "tol": w.tol, "p": w.p, "K": info.K, "W": info.W, "nufft_w": info.nufft_w,
+                   "nf": info.nf, "local_pairs": info.local_pairs,
+                   "local_weights": info.local_weights, "parallelism": f"replicas x{world}",
+                   "l2": "flushed (512 MiB write) before every timed step",
+                   "plan_seconds": t_plan},
+        "stage_ms_per_step": per_step,
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * w.M,
+                "d2h_bytes_per_step": 8 * w.M},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+        "wall_s_timed_region": wall,
+    }
+    plan.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, args.cpu_steps)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def stage_bytes(info, w, stage):
+    """Algorithmic HBM bytes per launch of a stage (what the method must move once per step)."""
+    M = info.M
+    if stage == "local":
+        # stored weights Q_m (8 B each) + per pair source index, m range, weight offset (16 B)
+        # + one read of the target's output (8 B per target); the density ring is L2-resident
+        return 8 * info.local_weights + 16 * info.local_pairs + 8 * M
+    if stage == "spread":
+        return M * (8 + 8 * info.nufft_w) + 8 * info.nf
+    if stage == "interp":
+        return M * (8 + 8 * info.nufft_w) + 8 * info.nf
+    if stage in ("fft_fwd", "fft_inv"):
+        return 4 * 16 * (info.nf // 2)
+    if stage == "modes":
+        return (info.K + 1) * (16 * info.W + 16 * info.W + 64)
+    return None
+
+
+def cpu_baseline(w, nsteps):
+    """The oracle of the same scheme (oracle/wfp.py) timed on the host cores, plan excluded."""
+    from oracle import wfp
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count()
+    o = wfp.from_workload(w)
+    for _ in range(3):
+        o.step()
+    t0 = time.perf_counter()
+    for _ in range(nsteps):
+        o.step()
+    dt = time.perf_counter() - t0
+    return {"value": w.M * nsteps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{nsteps} time steps (after 3 warm-up steps) of the same M=1e4 free-space "
+                      f"march with oracle/wfp.py (numpy/scipy FP64, direct Fourier sums); plan "
+                      f"precompute excluded"}
+
+
+def run_reference(args):
+    rank, world, local = _dist()
+    if rank != 0:
+        return
+    from paper_2507_07823_gb300 import workloads
+    w = workloads.config1()
+    cb = None
+    from oracle import wfp
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
+    except Exception:
+        cores = os.cpu_count()
+    o = wfp.from_workload(w)
+    for _ in range(args.warmup):
+        o.step()
+    K = min(args.steps, args.ref_max_steps)
+    t0 = time.perf_counter()
+    for _ in range(K):
+        o.step()
+    dt = time.perf_counter() - t0
+    value = w.M * K / dt
+    cb = {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+          "sample": f"{K} oracle time steps of the M=1e4 free-space march after {args.warmup} "
+                    f"warm-up steps (oracle/wfp.py, plan excluded)"}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": 1e3 * dt / K,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"{w.name}: {w.description}", "M": w.M},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=540)
+    ap.add_argument("--warmup", type=int, default=60)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-steps", type=int, default=20)
+    ap.add_argument("--ref-max-steps", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * wave1d — windowed Fourier projection (WFP) time marching for 1D waves scattered by point
+ * springs, on one NVIDIA GB300 GPU (sm_103a).
+ *
+ * The method (arXiv 2507.07823): M springs of stiffness beta_j at x_j on a string, driven by an
+ * incident wave u_inc(x, t) = f(x - t) (Sec. 1, eqs. uinc-gj).  The scattered field is the single
+ * layer potential u = 1/2 sum_j int_0^{t - |x - x_j|} sigma_j (eq. singleLayerSol) whose
+ * densities solve a Volterra system (eq. IEfree; eq. periodicIE in the periodic box [-pi, pi]).
+ * Each time step splits the potential with a Kaiser-Bessel blending window of width
+ * delta = W dt (eq. phi) into
+ *   - a local part over the last delta of history, summed directly with Gauss-Legendre
+ *     quadrature of p-point interpolants (Sec. 4.1), and
+ *   - a history part carried by N_F = 2K + 1 Fourier modes alpha_k (eq. historySol1), advanced by
+ *     an exact rotation plus a W-tap driving term (eqs. alphakEvolutionFormulas, hkcompdisc).
+ * One step is a type-1 NUFFT (springs -> modes, eq. densco), the mode update, a type-2 NUFFT
+ * (modes -> springs and receivers), the local sum and a sparse implicit density solve
+ * (eq. linearSystem).  Free space adds the radiation projection of Sec. 4.4 every few steps.
+ *
+ * Conventions for every call:
+ *   - Arrays are FP64, in the caller's spring order, contiguous.  A pointer documented as
+ *     "device" must be a CUDA device (or managed) pointer usable from the current device; "host"
+ *     pointers are ordinary (preferably pinned) host memory.
+ *   - The plan copies every input it is given; the caller keeps ownership of its buffers and of
+ *     every output buffer.  The plan owns its device memory and frees it in wave1d_destroy.
+ *   - Work is queued on the plan's stream (wave1d_opts.stream; NULL is the legacy default
+ *     stream).  Calls that return data to the host synchronise that stream.
+ *   - Every call returns a wave1d_status.  Device-side faults of the numerics (non-finite
+ *     densities) are latched in a device status word and reported by the next synchronising call
+ *     (wave1d_sync, wave1d_read_receivers, wave1d_get_sigma, wave1d_solve).
+ *   - Plans are not thread-safe; use one plan per host thread.
+ */
+#ifndef WAVE1D_H
+#define WAVE1D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct wave1d_plan_s* wave1d_plan_t;
+
+/* boundary conditions: the periodic box [-pi, pi] (Sec. 2) or free space (Sec. 4.4) */
+enum wave1d_bc { WAVE1D_PERIODIC = 0, WAVE1D_FREE = 1 };
+
+enum wave1d_status {
+    WAVE1D_OK = 0,
+    WAVE1D_EINVAL = -1,        /* bad argument (NULL pointer, M < 1, dt <= 0, odd p, ...)       */
+    WAVE1D_EDOMAIN = -2,       /* delta >= pi, or a free-space spring/receiver outside Omega   */
+    WAVE1D_ENOMEM = -3,        /* device or host allocation failed / over the memory budget    */
+    WAVE1D_ECUDA = -4,         /* a CUDA runtime call failed                                   */
+    WAVE1D_ENONFINITE = -6,    /* a density became NaN or Inf (latched on the device)          */
+    WAVE1D_EDONE = -7,         /* stepping past the Nt given to wave1d_plan                    */
+    WAVE1D_EUNSUPPORTED = -9   /* a size this build does not handle (see wave1d_strerror)      */
+};
+
+/* Optional parameters.  wave1d_opts_default fills the paper's defaults. */
+typedef struct {
+    int p;              /* local interpolation order, even, 2..16; default 8 (Sec. 6.3)            */
+    double gamma;       /* fraction of K lost to windowing (Remark r:gamma); default 0.5           */
+    int W;              /* window width in steps; 0 = ceil(2 ln(1/tol) / (pi gamma)) (eq. W)      */
+    int NL;             /* Gauss-Legendre nodes of the local rule; 0 = W (Sec. 4.3)               */
+    int Ng;             /* Gauss-Legendre nodes for p_k, q_k (eq. pkqkcomp); default 32           */
+    int nufft_w;        /* spreading kernel width in fine-grid points; 0 = ceil(log10(1/tol)) + 1 */
+    int rbc_period;     /* steps between radiation projections (Sec. 4.4); 0 = ceil(1.5 W)        */
+    int max_block;      /* largest block of springs closer than dt solved directly; default 4096  */
+    int64_t max_local_bytes; /* budget for stored local weights; default 16 GiB                  */
+    void* stream;       /* cudaStream_t for all work of the plan; NULL = legacy default stream   */
+} wave1d_opts;
+
+/* Derived sizes of a plan (read-only report). */
+typedef struct {
+    int64_t M, R, Nt, n;      /* springs, receivers, steps planned, steps taken                     */
+    int K, NF, W, m_max, p, NL, Ng, nufft_w, nf, rbc_period;
+    double dt, tol, b, delta;
+    int64_t local_pairs;      /* (target, source) pairs within delta, springs only                   */
+    int64_t local_weights;    /* stored local weights Q_m                                            */
+    int64_t nearby_pairs;     /* pairs closer than dt (entries of S, eq. linearSystem)               */
+    int64_t blocks, max_block;/* connected blocks of the nearby graph and the largest block size     */
+    int64_t device_bytes;     /* device memory owned by the plan                                     */
+} wave1d_info;
+
+/* Fill *o with defaults.  Returns WAVE1D_EINVAL if o is NULL. */
+int wave1d_opts_default(wave1d_opts* o);
+
+/*
+ * Build a plan (Sec. 3-4): parameters b = ln(1/tol) (eq. b), K = floor(pi/dt) (eq. Kdt),
+ * N_F = 2K + 1, W, delta = W dt (eq. W), the window tables, p_k and q_k (eq. pkqkcomp), the local
+ * weights Q_m of every pair closer than delta (Sec. 4.1), the blocks of the implicit matrix
+ * I + S (eq. linearSystem) and the NUFFT tables.  The densities start at zero (sigma(t <= 0) = 0).
+ *   x, beta : host, M values each; positions (wrapped into [-pi, pi) for WAVE1D_PERIODIC) and
+ *             stiffnesses (>= 0).  Free space needs |x_j| <= pi - 3 max(delta, W pi/K).
+ *   bc      : WAVE1D_PERIODIC or WAVE1D_FREE.
+ *   dt      : time step (> 0);  Nt: number of steps the plan may take (>= 1).
+ *   tol     : window tolerance epsilon in (0, 0.1) (eq. b).
+ *   opts    : NULL for defaults.
+ *   out     : receives the plan handle (NULL on failure).
+ */
+int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double dt, int64_t Nt,
+                double tol, const wave1d_opts* opts, wave1d_plan_t* out);
+
+/*
+ * Incident wave f(s) = sum_i amp_i exp(-(s - center_i)^2 / (2 width_i^2)), periodised over 2 pi
+ * in the periodic box; it drives g_j(t) = beta_j f(x_j - t) (eq. gj, smooth f).  Host arrays of
+ * n >= 0 values; n = 0 removes the incident wave.  Call before stepping.
+ */
+int wave1d_set_incident_gaussians(wave1d_plan_t plan, int n, const double* amp,
+                                  const double* center, const double* width);
+
+/*
+ * Extra evaluation points for u = u_L + u_H (Sec. 3.1, last paragraph; eq. localSol2).
+ * xr: host, R values (free space: inside Omega like the springs).  Call before stepping.
+ */
+int wave1d_set_receivers(wave1d_plan_t plan, const double* xr, int64_t R);
+
+/*
+ * Advance one step n -> n+1 (eq. linearSystem).  g_next: M values of g_j(t_{n+1}) in caller
+ * order (host if g_on_device == 0, device otherwise), or NULL to use the incident wave.
+ * Returns WAVE1D_EDONE once Nt steps have been taken.  Asynchronous.
+ */
+int wave1d_step(wave1d_plan_t plan, const double* g_next, int g_on_device);
+
+/*
+ * Advance nsteps steps driven by the incident wave, recording u at the receivers after each
+ * step into u_rec[s * R + r] and, if sigma is not NULL, the densities into sigma[s * M + j]
+ * (caller order).  Outputs are device pointers if out_on_device, host pointers otherwise.
+ * Steps are replayed from captured CUDA graphs.  Synchronises the stream before returning.
+ */
+int wave1d_solve(wave1d_plan_t plan, int64_t nsteps, double* u_rec, double* sigma,
+                 int out_on_device);
+
+/* u at the receivers at the current time t_n (R values; device or host pointer).  Synchronises. */
+int wave1d_read_receivers(wave1d_plan_t plan, double* u, int on_device);
+
+/* sigma^n in caller order (M values; device or host pointer).  Synchronises. */
+int wave1d_get_sigma(wave1d_plan_t plan, double* out, int on_device);
+
+/* Wait for the plan's queued work and report a latched device status. */
+int wave1d_sync(wave1d_plan_t plan);
+
+/* Fill *info with the plan's derived sizes. */
+int wave1d_get_info(wave1d_plan_t plan, wave1d_info* info);
+
+/*
+ * Copy an internal array to host memory for verification (synchronises).  Arrays in the plan's
+ * internal (position-sorted) spring order unless stated; `count` is the number of doubles the
+ * caller's buffer holds and must equal the size given here:
+ *   WAVE1D_ARR_ALPHA      alpha_k^n, k = 0..K, interleaved (re, im)          2 (K+1)
+ *   WAVE1D_ARR_ALPHA_P    alpha'_k^n                                          2 (K+1)
+ *   WAVE1D_ARR_S_LAST     S_k^{n-1} of the last step, k = 0..K, (re, im)     2 (K+1)
+ *   WAVE1D_ARR_UH         u_H(x_j, t_n) at springs, caller order              M
+ *   WAVE1D_ARR_LOCAL      local explicit sum c_j of the last step, caller order M
+ *   WAVE1D_ARR_SIGMA_RING sigma^{n-m}, m = 0..m_max, caller order, row m       (m_max+1) M
+ *   WAVE1D_ARR_PERM       caller index of each sorted spring (as doubles)      M
+ */
+enum wave1d_array {
+    WAVE1D_ARR_ALPHA = 0, WAVE1D_ARR_ALPHA_P = 1, WAVE1D_ARR_S_LAST = 2, WAVE1D_ARR_UH = 3,
+    WAVE1D_ARR_LOCAL = 4, WAVE1D_ARR_SIGMA_RING = 5, WAVE1D_ARR_PERM = 6
+};
+int wave1d_inspect(wave1d_plan_t plan, int array, double* host_out, int64_t count);
+
+/*
+ * Per-stage device timing.  While enabled, steps run without graphs and CUDA events recorded on
+ * the plan's stream between the stages of every step accumulate each stage's device time
+ * (wave1d_stage order below).  wave1d_profile(plan, 1) resets the totals; (plan, 0) stops.
+ * wave1d_profile_read copies the per-stage total milliseconds into ms[0..nstage-1] and the number
+ * of profiled steps into *steps (synchronises).  nstage must be WAVE1D_NSTAGE.
+ */
+enum wave1d_stage {
+    WAVE1D_STAGE_LOCAL = 0,      /* local explicit sum (Sec. 4.1)                     */
+    WAVE1D_STAGE_SPREAD = 1,     /* type-1 spreading                                  */
+    WAVE1D_STAGE_FFT_FWD = 2,    /* forward FFT                                       */
+    WAVE1D_STAGE_MODES = 3,      /* S_k, driving terms, rotation (Sec. 3)             */
+    WAVE1D_STAGE_RBC = 4,        /* radiation projection (Sec. 4.4), projection steps */
+    WAVE1D_STAGE_FFT_INV = 5,    /* inverse FFT                                       */
+    WAVE1D_STAGE_INTERP = 6,     /* type-2 interpolation                              */
+    WAVE1D_STAGE_SOLVE = 7,      /* forcing, right-hand side, block solve             */
+    WAVE1D_STAGE_RECEIVERS = 8,  /* receiver readout                                  */
+    WAVE1D_NSTAGE = 9
+};
+int wave1d_profile(wave1d_plan_t plan, int enable);
+int wave1d_profile_read(wave1d_plan_t plan, double* ms, int nstage, int64_t* steps);
+
+/* Free the plan and its device memory (synchronises).  NULL is accepted. */
+int wave1d_destroy(wave1d_plan_t plan);
+
+/* Static description of a status code, or of the last error detail of the calling thread. */
+const char* wave1d_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WAVE1D_H */

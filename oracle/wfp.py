@@ -226,38 +226,53 @@ def distance(xa, xb, periodic):
     return d
 
 
-def local_weights(d, P: Params, win: Window):
+def local_weights(d, P: Params, win: Window, chunk=100_000):
     """Q_m(d), m = 0..m_max, for an array of distances d (shape (npairs,)).
 
     Nodes s_i = t_{n+1} - xi_i run over [d, delta] (time before t_{n+1}); the interpolant at xi
     uses the p nearest grid times t_{n+1-m} with m_min <= m <= m_max, where m_min = 0 for nearby
     pairs (d < dt) and 1 otherwise; weights by the Lagrange formula.  Q_m = 0 for d >= delta.
+    For each stencil offset r the node contributions w_i (1 - phi(s_i)) v_{lo+r}(s_i) are summed
+    over the nodes with one bincount.
     """
     d = np.asarray(d, dtype=np.float64)
     npairs = d.shape[0]
-    Q = np.zeros((npairs, P.m_max + 1))
+    ncol = P.m_max + 1
+    Q = np.zeros((npairs, ncol))
     gx, gw = legendre.leggauss(P.NL)
-    live = d < P.delta
-    dd = d[live]
-    if dd.size == 0:
-        return Q
-    idx = np.nonzero(live)[0]
-    s = dd[:, None] + 0.5 * (P.delta - dd)[:, None] * (1.0 + gx[None, :])   # (n, NL)
-    w = 0.5 * (P.delta - dd)[:, None] * gw[None, :]
-    one_minus_phi = 1.0 - win.phi(s)
-    y = s / P.dt                                                          # time in steps
-    m_min = np.where(dd < P.dt, 0, 1)[:, None]
-    lo = np.floor(y).astype(np.int64) - P.p // 2 + 1
-    lo = np.maximum(lo, m_min)
-    lo = np.minimum(lo, P.m_max - P.p + 1)
-    for r in range(P.p):
-        L = np.ones_like(y)
-        for q in range(P.p):
-            if q != r:
-                L *= (y - (lo + q)) / (r - q)
-        val = w * one_minus_phi * L
-        for i in range(P.NL):
-            Q[idx, lo[:, i] + r] += val[:, i]      # each pair appears once per (r, i)
+    for c0 in range(0, npairs, chunk):
+        dc = d[c0:c0 + chunk]
+        live = dc < P.delta
+        dd = dc[live]
+        if dd.size == 0:
+            continue
+        idx = np.nonzero(live)[0]
+        s = dd[:, None] + 0.5 * (P.delta - dd)[:, None] * (1.0 + gx[None, :])   # (n, NL)
+        w = 0.5 * (P.delta - dd)[:, None] * gw[None, :]
+        one_minus_phi = 1.0 - win.phi(s)
+        y = s / P.dt                                                          # time in steps
+        m_min = np.where(dd < P.dt, 0, 1)[:, None]
+        lo = np.floor(y).astype(np.int64) - P.p // 2 + 1
+        lo = np.maximum(lo, m_min)
+        lo = np.minimum(lo, P.m_max - P.p + 1)
+        rowbase = (idx * ncol)[:, None]
+        block = np.zeros(len(dc) * ncol)
+        # Lagrange basis L_r(y) = prod_{q != r} (y - lo - q) / (r - q), via prefix/suffix products
+        diff = [y - (lo + q) for q in range(P.p)]
+        prefix = [np.ones_like(y)]
+        for q in range(P.p - 1):
+            prefix.append(prefix[-1] * diff[q])
+        suffix = [np.ones_like(y)] * (P.p + 1)
+        for q in range(P.p - 1, 0, -1):
+            suffix[q] = suffix[q + 1] * diff[q]
+        wphi = w * one_minus_phi
+        for r in range(P.p):
+            denom = float(np.prod([r - q for q in range(P.p) if q != r]))
+            L = prefix[r] * suffix[r + 1] / denom
+            val = wphi * L
+            block += np.bincount((rowbase + lo + r).ravel(), weights=val.ravel(),
+                                 minlength=len(dc) * ncol)
+        Q[c0:c0 + chunk] = block.reshape(len(dc), ncol)
     return Q
 
 

@@ -1,0 +1,685 @@
+// C-ABI of the wave1d library (declared in include/wave1d.h).
+//
+// Each plan owns a private non-blocking stream.  Every call orders itself after the work already
+// queued on the caller's stream (opts.stream, which may be the legacy default stream) and makes
+// the caller's stream wait for the plan's work, so from the caller's point of view all work is
+// stream-ordered on its own stream.  The private stream allows CUDA-graph capture of whole chunks
+// of time steps (the legacy stream cannot be captured).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "../../include/wave1d.h"
+
+namespace wave1d {
+__global__ void k_spread(DevPlan P);
+__global__ void k_fft_cols(const double2*, double2*, const double2*, int, int, int, int, int);
+__global__ void k_fft_rows(const double2*, double2*, const double2*, int, int, int, int, int);
+__global__ void k_modes(DevPlan P);
+__global__ void k_rbc_grid(DevPlan P);
+__global__ void k_rbc_update(DevPlan P, int npts);
+__global__ void k_interp(DevPlan P);
+__global__ void k_local(DevPlan P);
+__global__ void k_rhs(DevPlan P);
+__global__ void k_solve(DevPlan P);
+__global__ void k_receivers(DevPlan P);
+__global__ void k_sigma_to_caller(DevPlan P, int64_t q, double* out);
+__global__ void k_internal_to_caller(const int32_t* perm, int64_t M, const double* in, double* out);
+__global__ void k_caller_to_internal(const int32_t* perm, int64_t M, const double* in, double* out);
+}  // namespace wave1d
+
+using namespace wave1d;
+
+namespace {
+thread_local std::string g_last_error;
+
+struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    bool with_sigma = false;
+};
+}  // namespace
+
+struct wave1d_plan_s {
+    HostPlan hp;
+    DevPlan dp{};
+    cudaStream_t user = nullptr;      // caller's stream (may be the legacy default stream)
+    cudaStream_t s = nullptr;         // private stream
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    int device = 0;
+    int64_t n = 0;                    // host mirror of the device step counter
+    std::vector<void*> allocs;
+    int64_t bytes = 0;
+    bool started = false;
+    double* d_g = nullptr;            // internal-order forcing
+    double* d_gstage = nullptr;       // caller-order staging for a host forcing vector
+    double* d_pulse = nullptr;
+    int chunk = 32;
+    double* d_sig_hist = nullptr;
+    Graph graphs[2];                  // chunk graphs without / with the sigma history
+    Graph step_graphs[2];             // single-step graphs: ordinary step / projection step
+    bool profiling = false;
+    cudaEvent_t prof_ev[WAVE1D_NSTAGE + 1] = {};
+    double prof_ms[WAVE1D_NSTAGE] = {};
+    int64_t prof_steps = 0;
+};
+
+namespace {
+
+int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+#define CK(call)                                                                               \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail(WAVE1D_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));    \
+    } while (0)
+
+template <typename T>
+int dalloc(wave1d_plan_t p, T** out, size_t count) {
+    *out = nullptr;
+    if (count == 0) count = 1;
+    void* ptr = nullptr;
+    cudaError_t e = cudaMalloc(&ptr, count * sizeof(T));
+    if (e != cudaSuccess) return fail(WAVE1D_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    p->allocs.push_back(ptr);
+    p->bytes += (int64_t)(count * sizeof(T));
+    *out = (T*)ptr;
+    return WAVE1D_OK;
+}
+
+template <typename T>
+int upload(wave1d_plan_t p, const std::vector<T>& v, T** out) {
+    int rc = dalloc(p, out, v.size());
+    if (rc) return rc;
+    if (!v.empty()) CK(cudaMemcpyAsync(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, p->s));
+    return WAVE1D_OK;
+}
+
+template <typename T>
+int zeros(wave1d_plan_t p, T** out, size_t count) {
+    int rc = dalloc(p, out, count);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(*out, 0, std::max<size_t>(count, 1) * sizeof(T), p->s));
+    return WAVE1D_OK;
+}
+
+int ilog2(int v) {
+    int l = 0;
+    while ((1 << l) < v) l++;
+    return l;
+}
+
+// order the private stream after the caller's stream
+int enter(wave1d_plan_t p) {
+    CK(cudaSetDevice(p->device));
+    CK(cudaEventRecord(p->ev_in, p->user));
+    CK(cudaStreamWaitEvent(p->s, p->ev_in, 0));
+    return WAVE1D_OK;
+}
+
+// order the caller's stream after the private stream
+int leave(wave1d_plan_t p) {
+    CK(cudaEventRecord(p->ev_out, p->s));
+    CK(cudaStreamWaitEvent(p->user, p->ev_out, 0));
+    return WAVE1D_OK;
+}
+
+int upload_receivers(wave1d_plan_t p) {
+    HostPlan& hp = p->hp;
+    DevPlan& d = p->dp;
+    d.R = hp.P.R;
+    int rc = 0;
+    int32_t* i32;
+    int64_t* i64;
+    double* f64;
+    if ((rc = upload(p, hp.rc_i0, &i32))) return rc;
+    d.rc_i0 = i32;
+    if ((rc = upload(p, hp.rc_ker, &f64))) return rc;
+    d.rc_ker = f64;
+    if ((rc = upload(p, hp.rloc.row_ptr, &i64))) return rc;
+    d.rrow_ptr = i64;
+    if ((rc = upload(p, hp.rloc.src, &i32))) return rc;
+    d.rsrc = i32;
+    if ((rc = upload(p, hp.rloc.mrange, &i32))) return rc;
+    d.rmrange = i32;
+    if ((rc = upload(p, hp.rloc.woff, &i64))) return rc;
+    d.rwoff = i64;
+    if ((rc = upload(p, hp.rloc.w, &f64))) return rc;
+    d.rwq = f64;
+    if ((rc = zeros(p, &d.uHr, (size_t)std::max<int64_t>(1, d.R)))) return rc;
+    if ((rc = zeros(p, &d.rec_hist, (size_t)p->chunk * std::max<int64_t>(1, d.R)))) return rc;
+    return WAVE1D_OK;
+}
+
+bool is_rbc_step(const wave1d_plan_t p, int64_t n) {
+    return p->hp.P.bc == WAVE1D_FREE && ((n + 1) % p->hp.P.rbc_period) == 0;
+}
+
+// queue one step n -> n+1 on the private stream; ev (optional) gets WAVE1D_NSTAGE + 1 events
+// recorded between the stages
+int enqueue_step(wave1d_plan_t p, int64_t n, const double* g_ext, double* sig_hist,
+                 cudaEvent_t* ev = nullptr) {
+    const Params& P = p->hp.P;
+    DevPlan d = p->dp;
+    d.g_ext = g_ext;
+    d.sig_hist = sig_hist;
+    cudaStream_t s = p->s;
+    const int T = 256;
+    auto blocks = [](int64_t work, int per) { return (unsigned)std::max<int64_t>(1, (work + per - 1) / per); };
+    auto mark = [&](int i) {
+        if (ev) cudaEventRecord(ev[i], s);
+    };
+    mark(WAVE1D_STAGE_LOCAL);
+    k_local<<<blocks(P.M * 32, T), T, 0, s>>>(d);
+    mark(WAVE1D_STAGE_SPREAD);
+    k_spread<<<blocks(P.nf, T), T, 0, s>>>(d);
+    mark(WAVE1D_STAGE_FFT_FWD);
+    int l1 = ilog2(P.L1), l2 = ilog2(P.L2);
+    int t1 = std::max(32, std::min(P.L1 / 2, 512)), t2 = std::max(32, std::min(P.L2 / 2, 512));
+    const double2* tw = (const double2*)d.twiddle;
+    k_fft_cols<<<P.L2, t1, P.L1 * sizeof(double2), s>>>((const double2*)d.grid, (double2*)d.work, tw, P.L,
+                                                         P.L1, P.L2, l1, +1);
+    k_fft_rows<<<P.L1, t2, P.L2 * sizeof(double2), s>>>((const double2*)d.work, (double2*)d.spec, tw, P.L,
+                                                         P.L1, P.L2, l2, +1);
+    mark(WAVE1D_STAGE_MODES);
+    k_modes<<<blocks(4 * (int64_t)(P.K + 1), T), T, 0, s>>>(d);
+    mark(WAVE1D_STAGE_RBC);
+    if (is_rbc_step(p, n)) {
+        int npts = (int)p->hp.rbc_idx.size();
+        k_rbc_grid<<<npts, T, 0, s>>>(d);
+        k_rbc_update<<<blocks(P.K + 1, 128), 128, 0, s>>>(d, npts);
+    }
+    mark(WAVE1D_STAGE_FFT_INV);
+    k_fft_cols<<<P.L2, t1, P.L1 * sizeof(double2), s>>>((const double2*)d.spec2, (double2*)d.work, tw, P.L,
+                                                         P.L1, P.L2, l1, -1);
+    k_fft_rows<<<P.L1, t2, P.L2 * sizeof(double2), s>>>((const double2*)d.work, (double2*)d.grid, tw, P.L,
+                                                         P.L1, P.L2, l2, -1);
+    mark(WAVE1D_STAGE_INTERP);
+    k_interp<<<blocks(P.M + P.R, T), T, 0, s>>>(d);
+    mark(WAVE1D_STAGE_SOLVE);
+    k_rhs<<<blocks(P.M, T), T, 0, s>>>(d);
+    k_solve<<<blocks(d.nblocks * 32, T), T, 0, s>>>(d);
+    mark(WAVE1D_STAGE_RECEIVERS);
+    k_receivers<<<blocks(std::max<int64_t>(P.R, 1) * 32, T), T, 0, s>>>(d);
+    mark(WAVE1D_NSTAGE);
+    CK(cudaGetLastError());
+    return WAVE1D_OK;
+}
+
+int check_status(wave1d_plan_t p) {
+    int st = 0;
+    CK(cudaMemcpyAsync(&st, p->dp.status, sizeof(int), cudaMemcpyDeviceToHost, p->s));
+    CK(cudaStreamSynchronize(p->s));
+    if (st != 0) return fail(st, "a density became non-finite during the march");
+    return WAVE1D_OK;
+}
+
+int build_graph(wave1d_plan_t p, Graph& g, bool with_sigma) {
+    if (g.exec) return WAVE1D_OK;
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(p->s, cudaStreamCaptureModeThreadLocal));
+    // the chunk starts at a multiple of `chunk`, so step offsets inside it fix the projections
+    int rc = WAVE1D_OK;
+    for (int i = 0; i < p->chunk && rc == WAVE1D_OK; i++)
+        rc = enqueue_step(p, i, nullptr, with_sigma ? p->d_sig_hist : nullptr);
+    cudaError_t e = cudaStreamEndCapture(p->s, &graph);
+    if (rc) return rc;
+    if (e != cudaSuccess) return fail(WAVE1D_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    CK(cudaGraphInstantiate(&g.exec, graph, 0));
+    CK(cudaGraphDestroy(graph));
+    g.with_sigma = with_sigma;
+    return WAVE1D_OK;
+}
+
+// one step through the fastest path available: profiled eager, eager with external forcing or
+// sigma history, else a replayed single-step graph
+int run_step(wave1d_plan_t p, const double* g_ext, double* sig_hist) {
+    int64_t n = p->n;
+    if (p->profiling) {
+        int rc = enqueue_step(p, n, g_ext, sig_hist, p->prof_ev);
+        if (rc) return rc;
+        CK(cudaEventSynchronize(p->prof_ev[WAVE1D_NSTAGE]));
+        for (int i = 0; i < WAVE1D_NSTAGE; i++) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, p->prof_ev[i], p->prof_ev[i + 1]));
+            p->prof_ms[i] += ms;
+        }
+        p->prof_steps++;
+        return WAVE1D_OK;
+    }
+    if (g_ext || sig_hist) return enqueue_step(p, n, g_ext, sig_hist);
+    Graph& g = p->step_graphs[is_rbc_step(p, n) ? 1 : 0];
+    if (!g.exec) {
+        cudaGraph_t graph;
+        CK(cudaStreamBeginCapture(p->s, cudaStreamCaptureModeThreadLocal));
+        int rc = enqueue_step(p, n, nullptr, nullptr);
+        cudaError_t e = cudaStreamEndCapture(p->s, &graph);
+        if (rc) return rc;
+        if (e != cudaSuccess) return fail(WAVE1D_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+        CK(cudaGraphInstantiate(&g.exec, graph, 0));
+        CK(cudaGraphDestroy(graph));
+    }
+    CK(cudaGraphLaunch(g.exec, p->s));
+    return WAVE1D_OK;
+}
+
+void drop_graphs(wave1d_plan_t p) {
+    for (auto& g : p->graphs)
+        if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
+    for (auto& g : p->step_graphs)
+        if (g.exec) { cudaGraphExecDestroy(g.exec); g.exec = nullptr; }
+}
+
+}  // namespace
+
+extern "C" {
+
+int wave1d_opts_default(wave1d_opts* o) {
+    if (!o) return fail(WAVE1D_EINVAL, "opts is NULL");
+    std::memset(o, 0, sizeof(*o));
+    o->p = 8;
+    o->gamma = 0.5;
+    o->Ng = 32;
+    o->max_block = 4096;
+    o->max_local_bytes = (int64_t)16 << 30;
+    return WAVE1D_OK;
+}
+
+const char* wave1d_strerror(int status) {
+    if (!g_last_error.empty() && status != WAVE1D_OK) return g_last_error.c_str();
+    switch (status) {
+        case WAVE1D_OK: return "ok";
+        case WAVE1D_EINVAL: return "invalid argument";
+        case WAVE1D_EDOMAIN: return "input outside the method's domain";
+        case WAVE1D_ENOMEM: return "out of memory";
+        case WAVE1D_ECUDA: return "CUDA runtime error";
+        case WAVE1D_ENONFINITE: return "non-finite density";
+        case WAVE1D_EDONE: return "all planned steps taken";
+        case WAVE1D_EUNSUPPORTED: return "size not supported by this build";
+        default: return "unknown status";
+    }
+}
+
+int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double dt, int64_t Nt,
+                double tol, const wave1d_opts* opts, wave1d_plan_t* out) {
+    if (!out) return fail(WAVE1D_EINVAL, "out is NULL");
+    *out = nullptr;
+    g_last_error.clear();
+    if (!x || !beta || M < 1 || M > INT32_MAX / 2) return fail(WAVE1D_EINVAL, "need x, beta and 1 <= M < 2^30");
+    if (bc != WAVE1D_PERIODIC && bc != WAVE1D_FREE) return fail(WAVE1D_EINVAL, "bc must be WAVE1D_PERIODIC or WAVE1D_FREE");
+    if (!(dt > 0.0) || Nt < 1 || !(tol > 0.0 && tol < 0.1)) return fail(WAVE1D_EINVAL, "need dt > 0, Nt >= 1, 0 < tol < 0.1");
+    wave1d_opts o;
+    if (opts) o = *opts;
+    else wave1d_opts_default(&o);
+    if (o.p < 2 || o.p > 16 || (o.p % 2) != 0) return fail(WAVE1D_EINVAL, "p must be even, 2..16");
+    if (!(o.gamma > 0.0 && o.gamma < 1.0)) return fail(WAVE1D_EINVAL, "gamma must lie in (0, 1)");
+    if (o.max_block <= 0) o.max_block = 4096;
+    if (o.max_local_bytes <= 0) o.max_local_bytes = (int64_t)16 << 30;
+
+    wave1d_plan_t p = new (std::nothrow) wave1d_plan_s();
+    if (!p) return fail(WAVE1D_ENOMEM, "host allocation");
+    std::string err;
+    int rc = build_host_plan(x, beta, M, bc, dt, Nt, tol, o.p, o.gamma, o.W, o.NL, o.Ng, o.nufft_w,
+                             o.rbc_period, o.max_block, o.max_local_bytes, p->hp, err);
+    if (rc == WAVE1D_OK) {
+        double none = 0.0;
+        rc = build_receivers(p->hp, &none, 0, err);
+    }
+    if (rc != WAVE1D_OK) {
+        delete p;
+        return fail(rc, err);
+    }
+    const Params& P = p->hp.P;
+    p->chunk = P.bc == WAVE1D_FREE ? P.rbc_period : 32;
+    p->user = (cudaStream_t)o.stream;
+    auto cleanup = [&](int code) {
+        wave1d_destroy(p);
+        return code;
+    };
+    if (cudaGetDevice(&p->device) != cudaSuccess) return cleanup(fail(WAVE1D_ECUDA, "no CUDA device"));
+    if (cudaStreamCreateWithFlags(&p->s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming) != cudaSuccess)
+        return cleanup(fail(WAVE1D_ECUDA, "stream/event creation failed"));
+    if ((rc = enter(p))) return cleanup(rc);
+
+    HostPlan& hp = p->hp;
+    DevPlan& d = p->dp;
+    d.M = P.M;
+    d.R = 0;
+    d.K = P.K;
+    d.W = P.W;
+    d.m_max = P.m_max;
+    d.ring = P.ring;
+    d.nf = P.nf;
+    d.L = P.L;
+    d.L1 = P.L1;
+    d.L2 = P.L2;
+    d.w = P.nufft_w;
+    d.bc = P.bc;
+    d.npulse = 0;
+    d.dt = P.dt;
+    d.chunk = p->chunk;
+    d.rbc_h = P.h_rbc;
+    int32_t* i32;
+    int64_t* i64;
+    double* f64;
+#define UP(vec, field, tmp)                      \
+    if ((rc = upload(p, vec, &tmp))) return cleanup(rc); \
+    d.field = tmp;
+    if ((rc = zeros(p, &d.step, 2))) return cleanup(rc);
+    if ((rc = zeros(p, &d.status, 1))) return cleanup(rc);
+    UP(hp.x, x, f64);
+    UP(hp.beta, beta, f64);
+    UP(hp.perm, perm, i32);
+    UP(hp.pq, pq, f64);
+    UP(hp.rot, rot, f64);
+    UP(hp.deconv1, deconv1, f64);
+    UP(hp.deconv2, deconv2, f64);
+    UP(hp.twiddle, twiddle, f64);
+    if ((rc = zeros(p, &d.Sring, (size_t)P.W * (P.K + 1) * 2))) return cleanup(rc);
+    if ((rc = zeros(p, &d.alpha, (size_t)(P.K + 1) * 2))) return cleanup(rc);
+    if ((rc = zeros(p, &d.alpha_p, (size_t)(P.K + 1) * 2))) return cleanup(rc);
+    if ((rc = zeros(p, &d.grid, (size_t)P.nf))) return cleanup(rc);
+    if ((rc = zeros(p, &d.spec, (size_t)P.L * 2))) return cleanup(rc);
+    if ((rc = zeros(p, &d.spec2, (size_t)P.L * 2))) return cleanup(rc);
+    if ((rc = zeros(p, &d.work, (size_t)P.L * 2))) return cleanup(rc);
+    if ((rc = zeros(p, &d.rhs, (size_t)P.M))) return cleanup(rc);
+    UP(hp.sp_i0, sp_i0, i32);
+    UP(hp.sp_ker, sp_ker, f64);
+    UP(hp.bin_ptr, bin_ptr, i32);
+    UP(hp.bin_list, bin_list, i32);
+    if ((rc = zeros(p, &d.uH, (size_t)P.M))) return cleanup(rc);
+    UP(hp.loc.row_ptr, row_ptr, i64);
+    UP(hp.loc.src, src, i32);
+    UP(hp.loc.mrange, mrange, i32);
+    UP(hp.loc.woff, woff, i64);
+    UP(hp.loc.w, wq, f64);
+    if ((rc = zeros(p, &d.clocal, (size_t)P.M))) return cleanup(rc);
+    if ((rc = zeros(p, &d.sig, (size_t)P.M * P.ring))) return cleanup(rc);
+    UP(hp.blk_ptr, blk_ptr, i64);
+    UP(hp.blk_members, blk_members, i32);
+    UP(hp.blk_inv_off, blk_inv_off, i64);
+    UP(hp.inv, inv, f64);
+    d.nblocks = (int64_t)hp.blk_ptr.size() - 1;
+    UP(hp.rbc_idx, rbc_idx, i32);
+    UP(hp.rbc_x, rbc_x, f64);
+    UP(hp.rbc_phi, rbc_phi, f64);
+    UP(hp.rbc_dphi, rbc_dphi, f64);
+    if ((rc = zeros(p, &d.rbc_uv, std::max<size_t>(4, hp.rbc_idx.size() * 4)))) return cleanup(rc);
+    if ((rc = dalloc(p, &p->d_g, (size_t)P.M))) return cleanup(rc);
+    if ((rc = dalloc(p, &p->d_gstage, (size_t)P.M))) return cleanup(rc);
+    if ((rc = upload_receivers(p))) return cleanup(rc);
+    d.pulse = nullptr;
+#undef UP
+    if ((rc = leave(p))) return cleanup(rc);
+    if (cudaStreamSynchronize(p->s) != cudaSuccess) return cleanup(fail(WAVE1D_ECUDA, "plan upload failed"));
+    *out = p;
+    return WAVE1D_OK;
+}
+
+int wave1d_set_incident_gaussians(wave1d_plan_t p, int n, const double* amp, const double* center,
+                                  const double* width) {
+    if (!p || n < 0 || (n > 0 && (!amp || !center || !width))) return fail(WAVE1D_EINVAL, "bad incident-wave arguments");
+    if (p->started) return fail(WAVE1D_EINVAL, "set the incident wave before stepping");
+    std::vector<double> h(3 * (size_t)std::max(n, 1), 0.0);
+    for (int i = 0; i < n; i++) {
+        if (!(width[i] > 0.0) || !std::isfinite(amp[i]) || !std::isfinite(center[i]))
+            return fail(WAVE1D_EINVAL, "pulse widths must be positive and parameters finite");
+        h[3 * i] = amp[i];
+        h[3 * i + 1] = center[i];
+        h[3 * i + 2] = width[i];
+    }
+    int rc = enter(p);
+    if (rc) return rc;
+    double* dptr;
+    if ((rc = upload(p, h, &dptr))) return rc;
+    p->dp.pulse = dptr;
+    p->dp.npulse = n;
+    drop_graphs(p);
+    return leave(p);
+}
+
+int wave1d_set_receivers(wave1d_plan_t p, const double* xr, int64_t R) {
+    if (!p || R < 0 || (R > 0 && !xr)) return fail(WAVE1D_EINVAL, "bad receiver arguments");
+    if (p->started) return fail(WAVE1D_EINVAL, "set receivers before stepping");
+    std::string err;
+    int rc = build_receivers(p->hp, xr, R, err);
+    if (rc) return fail(rc, err);
+    if ((rc = enter(p))) return rc;
+    if ((rc = upload_receivers(p))) return rc;
+    drop_graphs(p);
+    return leave(p);
+}
+
+int wave1d_step(wave1d_plan_t p, const double* g_next, int g_on_device) {
+    if (!p) return fail(WAVE1D_EINVAL, "plan is NULL");
+    if (p->n >= p->hp.P.Nt) return fail(WAVE1D_EDONE, "all planned steps taken");
+    int rc = enter(p);
+    if (rc) return rc;
+    const double* gext = nullptr;
+    if (g_next) {
+        const double* src = g_next;
+        if (!g_on_device) {
+            CK(cudaMemcpyAsync(p->d_gstage, g_next, p->hp.P.M * sizeof(double), cudaMemcpyHostToDevice, p->s));
+            src = p->d_gstage;
+        }
+        k_caller_to_internal<<<(unsigned)((p->hp.P.M + 255) / 256), 256, 0, p->s>>>(p->dp.perm, p->hp.P.M, src, p->d_g);
+        gext = p->d_g;
+    }
+    p->started = true;
+    if ((rc = run_step(p, gext, nullptr))) return rc;
+    p->n++;
+    return leave(p);
+}
+
+int wave1d_solve(wave1d_plan_t p, int64_t nsteps, double* u_rec, double* sigma, int out_on_device) {
+    if (!p || nsteps < 0) return fail(WAVE1D_EINVAL, "bad solve arguments");
+    if (p->n + nsteps > p->hp.P.Nt) return fail(WAVE1D_EDONE, "nsteps beyond the Nt of the plan");
+    const Params& P = p->hp.P;
+    int rc = enter(p);
+    if (rc) return rc;
+    p->started = true;
+    if (sigma && !p->d_sig_hist) {
+        if ((rc = dalloc(p, &p->d_sig_hist, (size_t)p->chunk * P.M))) return rc;
+    }
+    cudaMemcpyKind kind = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    int64_t done = 0;
+    while (done < nsteps) {
+        int64_t rem = nsteps - done;
+        int64_t slot0 = p->n % p->chunk;
+        int64_t cnt;
+        if (slot0 == 0 && rem >= p->chunk && !p->profiling) {
+            Graph& g = p->graphs[sigma ? 1 : 0];
+            if ((rc = build_graph(p, g, sigma != nullptr))) return rc;
+            CK(cudaGraphLaunch(g.exec, p->s));
+            cnt = p->chunk;
+        } else {
+            if ((rc = run_step(p, nullptr, sigma ? p->d_sig_hist : nullptr))) return rc;
+            cnt = 1;
+        }
+        if (u_rec && P.R > 0)
+            CK(cudaMemcpyAsync(u_rec + done * P.R, p->dp.rec_hist + slot0 * P.R, cnt * P.R * sizeof(double),
+                               kind, p->s));
+        if (sigma)
+            CK(cudaMemcpyAsync(sigma + done * P.M, p->d_sig_hist + slot0 * P.M, cnt * P.M * sizeof(double),
+                               kind, p->s));
+        p->n += cnt;
+        done += cnt;
+    }
+    if ((rc = leave(p))) return rc;
+    return check_status(p);
+}
+
+int wave1d_read_receivers(wave1d_plan_t p, double* u, int on_device) {
+    if (!p || (!u && p->hp.P.R > 0)) return fail(WAVE1D_EINVAL, "bad arguments");
+    if (p->hp.P.R == 0) return WAVE1D_OK;
+    int rc = enter(p);
+    if (rc) return rc;
+    if (p->n == 0) {
+        std::vector<double> z(p->hp.P.R, 0.0);
+        if (on_device)
+            CK(cudaMemcpyAsync(u, z.data(), z.size() * sizeof(double), cudaMemcpyHostToDevice, p->s));
+        else
+            std::memcpy(u, z.data(), z.size() * sizeof(double));
+    } else {
+        int64_t slot = (p->n - 1) % p->chunk;
+        CK(cudaMemcpyAsync(u, p->dp.rec_hist + slot * p->hp.P.R, p->hp.P.R * sizeof(double),
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p->s));
+    }
+    if ((rc = leave(p))) return rc;
+    return check_status(p);
+}
+
+int wave1d_get_sigma(wave1d_plan_t p, double* out, int on_device) {
+    if (!p || !out) return fail(WAVE1D_EINVAL, "bad arguments");
+    int rc = enter(p);
+    if (rc) return rc;
+    const Params& P = p->hp.P;
+    double* dst = on_device ? out : p->d_gstage;
+    k_sigma_to_caller<<<(unsigned)((P.M + 255) / 256), 256, 0, p->s>>>(p->dp, p->n, dst);
+    CK(cudaGetLastError());
+    if (!on_device) CK(cudaMemcpyAsync(out, p->d_gstage, P.M * sizeof(double), cudaMemcpyDeviceToHost, p->s));
+    if ((rc = leave(p))) return rc;
+    return check_status(p);
+}
+
+int wave1d_sync(wave1d_plan_t p) {
+    if (!p) return fail(WAVE1D_EINVAL, "plan is NULL");
+    int rc = enter(p);
+    if (rc) return rc;
+    if ((rc = leave(p))) return rc;
+    return check_status(p);
+}
+
+int wave1d_get_info(wave1d_plan_t p, wave1d_info* info) {
+    if (!p || !info) return fail(WAVE1D_EINVAL, "bad arguments");
+    const Params& P = p->hp.P;
+    std::memset(info, 0, sizeof(*info));
+    info->M = P.M;
+    info->R = P.R;
+    info->Nt = P.Nt;
+    info->n = p->n;
+    info->K = P.K;
+    info->NF = 2 * P.K + 1;
+    info->W = P.W;
+    info->m_max = P.m_max;
+    info->p = P.p;
+    info->NL = P.NL;
+    info->Ng = P.Ng;
+    info->nufft_w = P.nufft_w;
+    info->nf = P.nf;
+    info->rbc_period = P.rbc_period;
+    info->dt = P.dt;
+    info->tol = P.tol;
+    info->b = P.b;
+    info->delta = P.delta;
+    info->local_pairs = (int64_t)p->hp.loc.src.size();
+    info->local_weights = (int64_t)p->hp.loc.w.size();
+    info->nearby_pairs = p->hp.loc.nearby;
+    info->blocks = (int64_t)p->hp.blk_ptr.size() - 1;
+    info->max_block = p->hp.max_block;
+    info->device_bytes = p->bytes;
+    return WAVE1D_OK;
+}
+
+int wave1d_inspect(wave1d_plan_t p, int array, double* host_out, int64_t count) {
+    if (!p || !host_out) return fail(WAVE1D_EINVAL, "bad arguments");
+    const Params& P = p->hp.P;
+    int64_t need = 0;
+    switch (array) {
+        case WAVE1D_ARR_ALPHA:
+        case WAVE1D_ARR_ALPHA_P:
+        case WAVE1D_ARR_S_LAST: need = 2 * (int64_t)(P.K + 1); break;
+        case WAVE1D_ARR_UH:
+        case WAVE1D_ARR_LOCAL:
+        case WAVE1D_ARR_PERM: need = P.M; break;
+        case WAVE1D_ARR_SIGMA_RING: need = (int64_t)(P.m_max + 1) * P.M; break;
+        default: return fail(WAVE1D_EINVAL, "unknown array");
+    }
+    if (count != need) return fail(WAVE1D_EINVAL, "count does not match the array size");
+    int rc = enter(p);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(p->s));
+    switch (array) {
+        case WAVE1D_ARR_ALPHA:
+            CK(cudaMemcpy(host_out, p->dp.alpha, need * sizeof(double), cudaMemcpyDeviceToHost));
+            break;
+        case WAVE1D_ARR_ALPHA_P:
+            CK(cudaMemcpy(host_out, p->dp.alpha_p, need * sizeof(double), cudaMemcpyDeviceToHost));
+            break;
+        case WAVE1D_ARR_S_LAST: {
+            if (p->n == 0) { std::fill(host_out, host_out + need, 0.0); break; }
+            int slot = (int)((p->n - 1) % P.W);
+            CK(cudaMemcpy(host_out, p->dp.Sring + (size_t)slot * need, need * sizeof(double), cudaMemcpyDeviceToHost));
+            break;
+        }
+        case WAVE1D_ARR_UH:
+        case WAVE1D_ARR_LOCAL: {
+            k_internal_to_caller<<<(unsigned)((P.M + 255) / 256), 256, 0, p->s>>>(
+                p->dp.perm, P.M, array == WAVE1D_ARR_UH ? p->dp.uH : p->dp.clocal, p->d_gstage);
+            CK(cudaGetLastError());
+            CK(cudaMemcpyAsync(host_out, p->d_gstage, P.M * sizeof(double), cudaMemcpyDeviceToHost, p->s));
+            CK(cudaStreamSynchronize(p->s));
+            break;
+        }
+        case WAVE1D_ARR_SIGMA_RING:
+            for (int m = 0; m <= P.m_max; m++) {
+                k_sigma_to_caller<<<(unsigned)((P.M + 255) / 256), 256, 0, p->s>>>(p->dp, p->n - m, p->d_gstage);
+                CK(cudaGetLastError());
+                CK(cudaMemcpyAsync(host_out + (size_t)m * P.M, p->d_gstage, P.M * sizeof(double),
+                                   cudaMemcpyDeviceToHost, p->s));
+            }
+            CK(cudaStreamSynchronize(p->s));
+            break;
+        case WAVE1D_ARR_PERM:
+            for (int64_t j = 0; j < P.M; j++) host_out[j] = (double)p->hp.perm[j];
+            break;
+    }
+    return leave(p);
+}
+
+int wave1d_profile(wave1d_plan_t p, int enable) {
+    if (!p) return fail(WAVE1D_EINVAL, "plan is NULL");
+    if (enable) {
+        for (int i = 0; i <= WAVE1D_NSTAGE; i++)
+            if (!p->prof_ev[i]) CK(cudaEventCreate(&p->prof_ev[i]));
+        for (int i = 0; i < WAVE1D_NSTAGE; i++) p->prof_ms[i] = 0.0;
+        p->prof_steps = 0;
+    }
+    p->profiling = enable != 0;
+    return WAVE1D_OK;
+}
+
+int wave1d_profile_read(wave1d_plan_t p, double* ms, int nstage, int64_t* steps) {
+    if (!p || !ms || nstage != WAVE1D_NSTAGE) return fail(WAVE1D_EINVAL, "bad arguments");
+    CK(cudaStreamSynchronize(p->s));
+    for (int i = 0; i < WAVE1D_NSTAGE; i++) ms[i] = p->prof_ms[i];
+    if (steps) *steps = p->prof_steps;
+    return WAVE1D_OK;
+}
+
+int wave1d_destroy(wave1d_plan_t p) {
+    if (!p) return WAVE1D_OK;
+    if (p->s) cudaStreamSynchronize(p->s);
+    drop_graphs(p);
+    for (int i = 0; i <= WAVE1D_NSTAGE; i++)
+        if (p->prof_ev[i]) cudaEventDestroy(p->prof_ev[i]);
+    for (void* a : p->allocs) cudaFree(a);
+    if (p->ev_in) cudaEventDestroy(p->ev_in);
+    if (p->ev_out) cudaEventDestroy(p->ev_out);
+    if (p->s) cudaStreamDestroy(p->s);
+    delete p;
+    return WAVE1D_OK;
+}
+
+}  // extern "C"

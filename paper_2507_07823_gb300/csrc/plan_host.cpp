@@ -1,0 +1,638 @@
+// Host-side plan construction: everything that depends only on the geometry and the
+// parameters, computed once before the time march (the paper's "precomputation", Sec. 4.3).
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <numeric>
+#include <thread>
+
+#include "internal.h"
+#include "../../include/wave1d.h"
+
+namespace wave1d {
+namespace {
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+// ---------------------------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------------------------
+void parallel_for(int64_t n, const std::function<void(int64_t, int64_t)>& body) {
+    unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    int64_t nt = std::min<int64_t>(hw, std::max<int64_t>(1, n / 256));
+    if (nt <= 1) {
+        body(0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    int64_t chunk = (n + nt - 1) / nt;
+    for (int64_t t = 0; t < nt; t++) {
+        int64_t a = t * chunk, b = std::min(n, a + chunk);
+        if (a >= b) break;
+        th.emplace_back([=, &body] { body(a, b); });
+    }
+    for (auto& t : th) t.join();
+}
+
+// Gauss-Legendre nodes and weights on [-1, 1] by Newton iteration on P_n.
+void gauss_legendre(int n, std::vector<double>& xs, std::vector<double>& ws) {
+    xs.assign(n, 0.0);
+    ws.assign(n, 0.0);
+    for (int i = 0; i < (n + 1) / 2; i++) {
+        double z = std::cos(kPi * (i + 0.75) / (n + 0.5));
+        double dp = 0.0;
+        for (int it = 0; it < 100; it++) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; k++) {
+                double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (n == 1) { p1 = z; p0 = 1.0; }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) {
+                // one more update of dp at the converged node
+                p0 = 1.0; p1 = z;
+                for (int k = 2; k <= n; k++) {
+                    double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                    p0 = p1;
+                    p1 = p2;
+                }
+                dp = n * (z * p1 - p0) / (z * z - 1.0);
+                break;
+            }
+        }
+        xs[i] = -z;
+        xs[n - 1 - i] = z;
+        ws[i] = ws[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+    if (n % 2 == 1) xs[n / 2] = 0.0;
+}
+
+double bessel_i0(double z) { return std::cyl_bessel_i(0.0, z); }
+double bessel_i1(double z) { return std::cyl_bessel_i(1.0, z); }
+
+// ---------------------------------------------------------------------------------------------
+// Blending window of eq. phi: phi' is the Kaiser-Bessel bump scaled to [0, delta]; phi is its
+// integral.  phi is tabulated on [0, delta/2] by Chebyshev panels built from Gauss-Legendre
+// integrals of phi', and reflected with phi(t) = 1 - phi(delta - t) (phi' is symmetric).
+// ---------------------------------------------------------------------------------------------
+class Window {
+  public:
+    Window(double delta, double b) : delta_(delta), b_(b) {
+        scale_ = b_ / (delta_ * std::sinh(b_));
+        gauss_legendre(40, gx_, gw_);
+        double half = 0.5 * delta_;
+        pw_ = half / kPanels;
+        coef_.assign(kPanels * (kDeg + 1), 0.0);
+        double base = 0.0;
+        for (int pnl = 0; pnl < kPanels; pnl++) {
+            double a = pnl * pw_;
+            double vals[kDeg + 1];
+            for (int i = 0; i <= kDeg; i++) {
+                double c = std::cos(kPi * (i + 0.5) / (kDeg + 1));   // Chebyshev points, 1st kind
+                double t = a + 0.5 * pw_ * (c + 1.0);
+                vals[i] = base + integral(a, t);
+            }
+            for (int m = 0; m <= kDeg; m++) {
+                double s = 0.0;
+                for (int i = 0; i <= kDeg; i++)
+                    s += vals[i] * std::cos(kPi * m * (i + 0.5) / (kDeg + 1));
+                coef_[pnl * (kDeg + 1) + m] = s * (m == 0 ? 1.0 : 2.0) / (kDeg + 1);
+            }
+            base += integral(a, a + pw_);
+        }
+    }
+    double delta() const { return delta_; }
+    double dphi(double t) const {
+        if (t < 0.0 || t > delta_) return 0.0;
+        double u = 2.0 * t / delta_ - 1.0;
+        double r = 1.0 - u * u;
+        return scale_ * bessel_i0(b_ * std::sqrt(r > 0.0 ? r : 0.0));
+    }
+    // phi''(t) = -(2 b^3 u / (delta^2 sinh b)) I1(z)/z, z = b sqrt(1 - u^2)
+    double ddphi(double t) const {
+        if (t < 0.0 || t > delta_) return 0.0;
+        double u = 2.0 * t / delta_ - 1.0;
+        double r = 1.0 - u * u;
+        double z = b_ * std::sqrt(r > 0.0 ? r : 0.0);
+        double i1z = z > 1e-8 ? bessel_i1(z) / z : 0.5;
+        return -(2.0 * b_ * b_ * b_ * u / (delta_ * delta_ * std::sinh(b_))) * i1z;
+    }
+    double phi(double t) const {
+        if (t <= 0.0) return 0.0;
+        if (t >= delta_) return 1.0;
+        if (t <= 0.5 * delta_) return low(t);
+        return 1.0 - low(delta_ - t);
+    }
+
+  private:
+    static constexpr int kPanels = 48;
+    static constexpr int kDeg = 18;
+    double integral(double a, double c) const {
+        double s = 0.0, hw = 0.5 * (c - a);
+        for (size_t i = 0; i < gx_.size(); i++) s += gw_[i] * dphi(a + hw * (gx_[i] + 1.0));
+        return s * hw;
+    }
+    double low(double t) const {
+        int pnl = std::min(kPanels - 1, (int)(t / pw_));
+        double z = 2.0 * (t - pnl * pw_) / pw_ - 1.0;
+        const double* c = &coef_[pnl * (kDeg + 1)];
+        double b0 = 0.0, b1 = 0.0;      // Clenshaw
+        for (int m = kDeg; m >= 1; m--) {
+            double b2 = b1;
+            b1 = b0;
+            b0 = 2.0 * z * b1 - b2 + c[m];
+        }
+        return z * b0 - b1 + c[0];
+    }
+    double delta_, b_, scale_, pw_;
+    std::vector<double> gx_, gw_, coef_;
+};
+
+// sin(k a)/k with the k = 0 limit a (Remark r:kzero)
+inline double sinc_k(double k, double a) { return k == 0.0 ? a : std::sin(k * a) / k; }
+
+// ---------------------------------------------------------------------------------------------
+// Local weights Q_m(d), m = 0..m_max (Sec. 4.1): an NL-point Gauss-Legendre rule over the
+// look-back interval s in [d, delta] (s = t_{n+1} - tau) of (1 - phi(s)) times the p-point
+// interpolant through the nearest available grid times m dt, m_min <= m <= m_max, with
+// m_min = 0 for d < dt (nearby, implicit) and 1 otherwise.  Barycentric Lagrange weights.
+// ---------------------------------------------------------------------------------------------
+struct LocalRule {
+    const Params* P;
+    const Window* win;
+    std::vector<double> gx, gw, lam;       // GL rule; barycentric weights of p equispaced points
+    void init(const Params& Pp, const Window& w) {
+        P = &Pp;
+        win = &w;
+        gauss_legendre(Pp.NL, gx, gw);
+        lam.assign(Pp.p, 0.0);
+        // lambda_r = (-1)^r binom(p-1, r) for equispaced nodes (common factor dropped)
+        double c = 1.0;
+        for (int r = 0; r < Pp.p; r++) {
+            lam[r] = (r % 2 == 0 ? 1.0 : -1.0) * c;
+            c = c * (Pp.p - 1 - r) / (r + 1);
+        }
+    }
+    // fills Q[0..m_max]; returns false if every weight is zero (d >= delta)
+    bool weights(double d, double* Q) const {
+        const Params& p = *P;
+        for (int m = 0; m <= p.m_max; m++) Q[m] = 0.0;
+        if (!(d < p.delta)) return false;
+        int m_min = d < p.dt ? 0 : 1;
+        double half = 0.5 * (p.delta - d);
+        for (size_t i = 0; i < gx.size(); i++) {
+            double s = d + half * (gx[i] + 1.0);
+            double wi = half * gw[i] * (1.0 - win->phi(s));
+            double y = s / p.dt;
+            int lo = (int)std::floor(y) - p.p / 2 + 1;
+            lo = std::max(lo, m_min);
+            lo = std::min(lo, p.m_max - p.p + 1);
+            // barycentric weights at y for nodes lo .. lo+p-1
+            int hit = -1;
+            double den = 0.0, tmp[32];
+            for (int r = 0; r < p.p; r++) {
+                double dy = y - (double)(lo + r);
+                if (dy == 0.0) { hit = r; break; }
+                tmp[r] = lam[r] / dy;
+                den += tmp[r];
+            }
+            if (hit >= 0) {
+                Q[lo + hit] += wi;
+            } else {
+                for (int r = 0; r < p.p; r++) Q[lo + r] += wi * tmp[r] / den;
+            }
+        }
+        return true;
+    }
+};
+
+// all (target, source) pairs with distance < delta, sources sorted; periodic images folded
+void find_pairs(const std::vector<double>& xt, const std::vector<double>& xs, double radius,
+                bool periodic, std::vector<std::vector<std::pair<int32_t, double>>>& out) {
+    int64_t T = (int64_t)xt.size();
+    int64_t S = (int64_t)xs.size();
+    out.assign(T, {});
+    parallel_for(T, [&](int64_t a, int64_t b) {
+        for (int64_t j = a; j < b; j++) {
+            auto& lst = out[j];
+            for (int img = -1; img <= 1; img++) {
+                if (!periodic && img != 0) continue;
+                double shift = 2.0 * kPi * img;
+                double lo = xt[j] - radius - shift, hi = xt[j] + radius - shift;
+                auto it = std::lower_bound(xs.begin(), xs.end(), lo);
+                for (; it != xs.end() && *it <= hi; ++it) {
+                    int64_t l = it - xs.begin();
+                    double d = std::fabs(xt[j] - (xs[l] + shift));
+                    if (d < radius) lst.emplace_back((int32_t)l, d);
+                }
+            }
+            std::sort(lst.begin(), lst.end(),
+                      [](const std::pair<int32_t, double>& u, const std::pair<int32_t, double>& v) {
+                          return u.first < v.first || (u.first == v.first && u.second < v.second);
+                      });
+            (void)S;
+        }
+    });
+}
+
+int build_local(const Params& P, const Window& win, const std::vector<double>& xt,
+                const std::vector<double>& xs, bool include_m0, LocalCSR& csr,
+                std::vector<std::vector<std::pair<int32_t, double>>>* nearby_out,
+                int64_t max_bytes, std::string& err) {
+    LocalRule rule;
+    rule.init(P, win);
+    std::vector<std::vector<std::pair<int32_t, double>>> pairs;
+    find_pairs(xt, xs, P.delta, P.bc == WAVE1D_PERIODIC, pairs);
+    int64_t T = (int64_t)xt.size();
+    csr.row_ptr.assign(T + 1, 0);
+    for (int64_t j = 0; j < T; j++) csr.row_ptr[j + 1] = csr.row_ptr[j] + (int64_t)pairs[j].size();
+    int64_t np = csr.row_ptr[T];
+    csr.src.assign(np, 0);
+    csr.mrange.assign(np, 0);
+    csr.woff.assign(np + 1, 0);
+    // first pass: ranges
+    std::vector<int32_t> lo(np), cnt(np);
+    std::atomic<int64_t> nearby{0};
+    parallel_for(T, [&](int64_t a, int64_t b) {
+        std::vector<double> Q(P.m_max + 1);
+        int64_t nb = 0;
+        for (int64_t j = a; j < b; j++) {
+            for (size_t e = 0; e < pairs[j].size(); e++) {
+                int64_t q = csr.row_ptr[j] + (int64_t)e;
+                double d = pairs[j][e].second;
+                csr.src[q] = pairs[j][e].first;
+                rule.weights(d, Q.data());
+                int m0 = include_m0 ? 0 : 1;
+                int first = -1, last = -1;
+                for (int m = m0; m <= P.m_max; m++)
+                    if (Q[m] != 0.0) { if (first < 0) first = m; last = m; }
+                if (first < 0) { first = m0; last = m0 - 1; }
+                lo[q] = first;
+                cnt[q] = last - first + 1;
+                if (d < P.dt) nb++;
+            }
+        }
+        nearby += nb;
+    });
+    csr.nearby = nearby.load();
+    for (int64_t q = 0; q < np; q++) {
+        csr.woff[q + 1] = csr.woff[q] + cnt[q];
+        csr.mrange[q] = lo[q] | (cnt[q] << 16);
+    }
+    int64_t nw = csr.woff[np];
+    if ((double)nw * 8.0 > (double)max_bytes) {
+        err = "local weights need " + std::to_string(nw * 8) + " bytes, over the budget max_local_bytes";
+        return WAVE1D_ENOMEM;
+    }
+    csr.w.assign(nw, 0.0);
+    parallel_for(T, [&](int64_t a, int64_t b) {
+        std::vector<double> Q(P.m_max + 1);
+        for (int64_t j = a; j < b; j++) {
+            for (size_t e = 0; e < pairs[j].size(); e++) {
+                int64_t q = csr.row_ptr[j] + (int64_t)e;
+                rule.weights(pairs[j][e].second, Q.data());
+                for (int c = 0; c < cnt[q]; c++) csr.w[csr.woff[q] + c] = Q[lo[q] + c];
+            }
+        }
+    });
+    if (nearby_out) {
+        nearby_out->assign(T, {});
+        for (int64_t j = 0; j < T; j++)
+            for (auto& pr : pairs[j])
+                if (pr.second < P.dt) (*nearby_out)[j].push_back(pr);
+    }
+    return WAVE1D_OK;
+}
+
+// Gauss-Jordan inverse with partial pivoting of an n x n row-major matrix (in place into inv)
+bool invert(int n, std::vector<double>& A, double* inv) {
+    for (int i = 0; i < n; i++)
+        for (int j = 0; j < n; j++) inv[i * n + j] = (i == j) ? 1.0 : 0.0;
+    for (int c = 0; c < n; c++) {
+        int piv = c;
+        for (int r = c + 1; r < n; r++)
+            if (std::fabs(A[r * n + c]) > std::fabs(A[piv * n + c])) piv = r;
+        if (A[piv * n + c] == 0.0) return false;
+        if (piv != c) {
+            for (int j = 0; j < n; j++) {
+                std::swap(A[c * n + j], A[piv * n + j]);
+                std::swap(inv[c * n + j], inv[piv * n + j]);
+            }
+        }
+        double d = 1.0 / A[c * n + c];
+        for (int j = 0; j < n; j++) { A[c * n + j] *= d; inv[c * n + j] *= d; }
+        for (int r = 0; r < n; r++) {
+            if (r == c) continue;
+            double f = A[r * n + c];
+            if (f == 0.0) continue;
+            for (int j = 0; j < n; j++) { A[r * n + j] -= f * A[c * n + j]; inv[r * n + j] -= f * inv[c * n + j]; }
+        }
+    }
+    return true;
+}
+
+int64_t next_pow2(int64_t v) {
+    int64_t p = 1;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+void spread_weights(const Params& P, const std::vector<double>& x, std::vector<int32_t>& i0,
+                    std::vector<double>& ker) {
+    int64_t n = (int64_t)x.size();
+    int w = P.nufft_w;
+    i0.assign(n, 0);
+    ker.assign(n * w, 0.0);
+    double inv_i0b = 1.0 / bessel_i0(P.kb_beta);
+    parallel_for(n, [&](int64_t a, int64_t b) {
+        for (int64_t j = a; j < b; j++) {
+            double u = (x[j] + kPi) / P.h_f;
+            int64_t first = (int64_t)std::ceil(u - 0.5 * w);
+            for (int t = 0; t < w; t++) {
+                double z = (double)(first + t - u) * 2.0 / w;
+                double r = 1.0 - z * z;
+                ker[j * w + t] = r > 0.0 ? bessel_i0(P.kb_beta * std::sqrt(r)) * inv_i0b : 0.0;
+            }
+            int64_t c = first % P.nf;
+            if (c < 0) c += P.nf;
+            i0[j] = (int32_t)c;
+        }
+    });
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+int build_host_plan(const double* x_in, const double* beta_in, int64_t M, int bc, double dt,
+                    int64_t Nt, double tol, int p, double gamma, int W, int NL, int Ng, int nufft_w,
+                    int rbc_period, int max_block, int64_t max_local_bytes, HostPlan& hp,
+                    std::string& err) {
+    Params& P = hp.P;
+    P.M = M;
+    P.Nt = Nt;
+    P.bc = bc;
+    P.dt = dt;
+    P.tol = tol;
+    P.p = p;
+    P.gamma = gamma;
+    P.b = std::log(1.0 / tol);                                        // eq. b
+    P.K = (int)std::floor(kPi / dt);                                  // eq. Kdt (floor)
+    P.W = W > 0 ? W : (int)std::ceil(2.0 * P.b / (kPi * gamma));      // W = 2b/(pi gamma)
+    P.delta = P.W * dt;                                               // eq. W
+    P.m_max = P.W + (p + 1) / 2;                                      // Sec. 4.1
+    P.NL = NL > 0 ? NL : P.W;                                         // Sec. 4.3
+    P.Ng = Ng > 0 ? Ng : 32;
+    P.ring = P.m_max + 1;
+    if (P.K < 2) { err = "dt too large: K = floor(pi/dt) < 2"; return WAVE1D_EINVAL; }
+    if (!(P.delta < kPi)) { err = "window delta = W dt must be below pi (Sec. 3)"; return WAVE1D_EDOMAIN; }
+    if (P.m_max - p + 1 < 1) { err = "window too short for the interpolation order"; return WAVE1D_EINVAL; }
+    // radiation projection grid (Sec. 4.4)
+    P.h_rbc = kPi / P.K;
+    P.delta_s = P.W * P.h_rbc;
+    P.rbc_period = rbc_period > 0 ? rbc_period : (int)std::ceil(1.5 * P.W);
+    if (bc == WAVE1D_FREE && 4 * P.W >= 2 * P.K) { err = "K too small for the radiation projection (4W >= 2K)"; return WAVE1D_EDOMAIN; }
+    // NUFFT fine grid: power of two, at least twice N_F
+    P.nf = (int)next_pow2(2 * (2 * (int64_t)P.K + 1));
+    if (P.nf < 64) P.nf = 64;
+    P.L = P.nf / 2;
+    int lg = 0;
+    while ((1 << lg) < P.L) lg++;
+    P.L1 = 1 << (lg / 2);
+    P.L2 = P.L / P.L1;
+    if (P.L2 > 1024) { err = "fine grid too large for this build (nf > 2^21)"; return WAVE1D_EUNSUPPORTED; }
+    P.h_f = 2.0 * kPi / P.nf;
+    P.nufft_w = nufft_w > 0 ? nufft_w : (int)std::ceil(std::log10(1.0 / tol)) + 1;
+    P.nufft_w = std::max(4, std::min(16, P.nufft_w));
+    double upsamp = (double)P.nf / (2.0 * P.K + 1.0);
+    P.kb_beta = kPi * P.nufft_w * (1.0 - 1.0 / (2.0 * upsamp));
+
+    // positions: wrap (periodic) or check Omega (free space), then sort
+    std::vector<double> xw(M);
+    double omega_lim = kPi - 3.0 * std::max(P.delta, P.delta_s);
+    for (int64_t j = 0; j < M; j++) {
+        double v = x_in[j];
+        if (!std::isfinite(v) || !std::isfinite(beta_in[j]) || beta_in[j] < 0.0) {
+            err = "non-finite position or negative/non-finite stiffness";
+            return WAVE1D_EINVAL;
+        }
+        if (bc == WAVE1D_PERIODIC) {
+            v = std::fmod(v + kPi, 2.0 * kPi);
+            if (v < 0) v += 2.0 * kPi;
+            v -= kPi;
+            if (v >= kPi) v -= 2.0 * kPi;
+        } else if (std::fabs(v) > omega_lim) {
+            err = "free-space spring outside Omega = [-pi + 3 delta, pi - 3 delta] (Sec. 4.4)";
+            return WAVE1D_EDOMAIN;
+        }
+        xw[j] = v;
+    }
+    hp.perm.resize(M);
+    std::iota(hp.perm.begin(), hp.perm.end(), 0);
+    std::stable_sort(hp.perm.begin(), hp.perm.end(), [&](int32_t a, int32_t b) { return xw[a] < xw[b]; });
+    hp.x.resize(M);
+    hp.beta.resize(M);
+    for (int64_t j = 0; j < M; j++) {
+        hp.x[j] = xw[hp.perm[j]];
+        hp.beta[j] = beta_in[hp.perm[j]];
+    }
+
+    Window win(P.delta, P.b);
+
+    // history kernels p_k, q_k (eq. pkqkcomp) with Ng-point Gauss-Legendre, dt folded in
+    {
+        std::vector<double> gx, gw;
+        gauss_legendre(P.Ng, gx, gw);
+        int K1 = P.K + 1;
+        std::vector<double> mu(P.Ng), wt(P.Ng), d1(P.W * P.Ng), d2(P.W * P.Ng);
+        for (int g = 0; g < P.Ng; g++) {
+            mu[g] = 0.5 * dt * (gx[g] + 1.0);
+            wt[g] = 0.5 * dt * gw[g];
+        }
+        for (int m = 0; m < P.W; m++)
+            for (int g = 0; g < P.Ng; g++) {
+                double tau = m * dt + mu[g];
+                d1[m * P.Ng + g] = win.dphi(tau);
+                d2[m * P.Ng + g] = win.ddphi(tau);
+            }
+        hp.pq.assign((size_t)P.W * K1 * 2, 0.0);
+        parallel_for(K1, [&](int64_t a, int64_t b) {
+            for (int64_t k = a; k < b; k++) {
+                double kd = (double)k;
+                for (int m = 0; m < P.W; m++) {
+                    double sp = 0.0, sq = 0.0;
+                    for (int g = 0; g < P.Ng; g++) {
+                        double tau = m * dt + mu[g];
+                        double psi = 2.0 * std::cos(kd * tau) * d1[m * P.Ng + g] +
+                                     sinc_k(kd, tau) * d2[m * P.Ng + g];       // eq. psidef
+                        sp += wt[g] * sinc_k(kd, dt - mu[g]) * psi;
+                        sq += wt[g] * std::cos(kd * (dt - mu[g])) * psi;
+                    }
+                    hp.pq[((size_t)m * K1 + k) * 2 + 0] = dt * sp;               // eq. hkcompdisc
+                    hp.pq[((size_t)m * K1 + k) * 2 + 1] = dt * sq;
+                }
+            }
+        });
+        hp.rot.assign((size_t)K1 * 3, 0.0);
+        for (int k = 0; k < K1; k++) {
+            hp.rot[k * 3 + 0] = std::cos(k * dt);
+            hp.rot[k * 3 + 1] = sinc_k(k, dt);
+            hp.rot[k * 3 + 2] = k * std::sin(k * dt);
+        }
+        // NUFFT deconvolution: psihat(k) = w h sinh(r)/r / I0(beta), r = sqrt(beta^2 - (k w h/2)^2)
+        hp.deconv1.assign(K1, 0.0);
+        hp.deconv2.assign(K1, 0.0);
+        double i0b = bessel_i0(P.kb_beta);
+        for (int k = 0; k < K1; k++) {
+            double om = 0.5 * k * P.nufft_w * P.h_f;
+            double r = std::sqrt(P.kb_beta * P.kb_beta - om * om);
+            double ph = P.nufft_w * P.h_f * (r > 0 ? std::sinh(r) / r : 1.0) / i0b;
+            double sgn = (k % 2 == 0) ? 1.0 : -1.0;
+            hp.deconv1[k] = sgn * P.h_f / (2.0 * kPi * ph);
+            hp.deconv2[k] = sgn * P.h_f / ph;
+        }
+        hp.twiddle.assign((size_t)P.L * 2, 0.0);
+        for (int j = 0; j < P.L; j++) {
+            double a = 2.0 * kPi * (double)j / (double)P.L;
+            hp.twiddle[2 * j] = std::cos(a);
+            hp.twiddle[2 * j + 1] = std::sin(a);
+        }
+    }
+
+    // spreading weights and bins by first grid index
+    spread_weights(P, hp.x, hp.sp_i0, hp.sp_ker);
+    hp.bin_ptr.assign(P.nf + 1, 0);
+    for (int64_t j = 0; j < M; j++) hp.bin_ptr[hp.sp_i0[j] + 1]++;
+    for (int c = 0; c < P.nf; c++) hp.bin_ptr[c + 1] += hp.bin_ptr[c];
+    hp.bin_list.assign(M, 0);
+    {
+        std::vector<int32_t> fill(hp.bin_ptr.begin(), hp.bin_ptr.end() - 1);
+        for (int64_t j = 0; j < M; j++) hp.bin_list[fill[hp.sp_i0[j]]++] = (int32_t)j;
+    }
+
+    // local part (Sec. 4.1) and nearby blocks (eq. linearSystem)
+    std::vector<std::vector<std::pair<int32_t, double>>> nearby;
+    int rc = build_local(P, win, hp.x, hp.x, false, hp.loc, &nearby, max_local_bytes, err);
+    if (rc) return rc;
+    {
+        std::vector<int32_t> parent(M);
+        std::iota(parent.begin(), parent.end(), 0);
+        std::function<int32_t(int32_t)> find = [&](int32_t i) {
+            while (parent[i] != i) { parent[i] = parent[parent[i]]; i = parent[i]; }
+            return i;
+        };
+        for (int64_t j = 0; j < M; j++)
+            for (auto& pr : nearby[j]) {
+                int32_t a = find((int32_t)j), b = find(pr.first);
+                if (a != b) parent[a] = b;
+            }
+        std::vector<int64_t> cnt(M + 1, 0);
+        for (int64_t j = 0; j < M; j++) cnt[find((int32_t)j) + 1]++;
+        std::vector<int32_t> roots;
+        for (int64_t r = 0; r < M; r++) if (cnt[r + 1] > 0) roots.push_back((int32_t)r);
+        std::vector<int64_t> rid(M, -1);
+        for (size_t i = 0; i < roots.size(); i++) rid[roots[i]] = (int64_t)i;
+        int64_t nb = (int64_t)roots.size();
+        hp.blk_ptr.assign(nb + 1, 0);
+        for (int64_t j = 0; j < M; j++) hp.blk_ptr[rid[find((int32_t)j)] + 1]++;
+        for (int64_t b = 0; b < nb; b++) hp.blk_ptr[b + 1] += hp.blk_ptr[b];
+        hp.blk_members.assign(M, 0);
+        std::vector<int64_t> fill(hp.blk_ptr.begin(), hp.blk_ptr.end() - 1);
+        std::vector<int32_t> local_of(M);
+        for (int64_t j = 0; j < M; j++) {
+            int64_t b = rid[find((int32_t)j)];
+            local_of[j] = (int32_t)(fill[b] - hp.blk_ptr[b]);
+            hp.blk_members[fill[b]++] = (int32_t)j;
+        }
+        hp.blk_inv_off.assign(nb + 1, 0);
+        hp.max_block = 0;
+        for (int64_t b = 0; b < nb; b++) {
+            int64_t s = hp.blk_ptr[b + 1] - hp.blk_ptr[b];
+            hp.max_block = std::max(hp.max_block, s);
+            hp.blk_inv_off[b + 1] = hp.blk_inv_off[b] + s * s;
+        }
+        if (hp.max_block > max_block) {
+            err = "a block of springs closer than dt has " + std::to_string(hp.max_block) +
+                  " members, above max_block; the direct block solve of this build does not cover it";
+            return WAVE1D_EUNSUPPORTED;
+        }
+        hp.inv.assign(hp.blk_inv_off[nb], 0.0);
+        LocalRule rule;
+        rule.init(P, win);
+        std::atomic<int> bad{0};
+        parallel_for(nb, [&](int64_t a, int64_t bb) {
+            std::vector<double> A, Q(P.m_max + 1);
+            for (int64_t b = a; b < bb; b++) {
+                int64_t s = hp.blk_ptr[b + 1] - hp.blk_ptr[b];
+                A.assign(s * s, 0.0);
+                for (int64_t i = 0; i < s; i++) {
+                    int32_t j = hp.blk_members[hp.blk_ptr[b] + i];
+                    A[i * s + i] += 1.0;
+                    for (auto& pr : nearby[j]) {
+                        rule.weights(pr.second, Q.data());
+                        A[i * s + local_of[pr.first]] += 0.5 * hp.beta[j] * Q[0];
+                    }
+                }
+                if (!invert((int)s, A, &hp.inv[hp.blk_inv_off[b]])) bad = 1;
+            }
+        });
+        if (bad) { err = "singular block of I + S"; return WAVE1D_EINVAL; }
+    }
+
+    // radiation projection tables (Sec. 4.4): grid x_i = i h (i < K), (i - 2K) h (i >= K)
+    if (bc == WAVE1D_FREE) {
+        Window swin(P.delta_s, P.b);
+        hp.rbc_idx.clear();
+        hp.rbc_x.clear();
+        hp.rbc_phi.clear();
+        hp.rbc_dphi.clear();
+        for (int i = P.K - 2 * P.W; i < P.K; i++) {
+            double xg = i * P.h_rbc, arg = kPi - P.delta_s - xg;
+            hp.rbc_idx.push_back(i);
+            hp.rbc_x.push_back(xg);
+            hp.rbc_phi.push_back(swin.phi(arg));
+            hp.rbc_dphi.push_back(swin.dphi(arg));
+        }
+        for (int i = P.K; i < P.K + 2 * P.W; i++) {
+            double xg = (i - 2 * P.K) * P.h_rbc, arg = kPi - P.delta_s + xg;
+            hp.rbc_idx.push_back(i);
+            hp.rbc_x.push_back(xg);
+            hp.rbc_phi.push_back(swin.phi(arg));
+            hp.rbc_dphi.push_back(swin.dphi(arg));
+        }
+    }
+    return WAVE1D_OK;
+}
+
+int build_receivers(HostPlan& hp, const double* xr, int64_t R, std::string& err) {
+    const Params& P = hp.P;
+    hp.P.R = R;
+    hp.xr.assign(xr, xr + R);
+    double omega_lim = kPi - 3.0 * std::max(P.delta, P.delta_s);
+    for (int64_t r = 0; r < R; r++) {
+        double v = hp.xr[r];
+        if (!std::isfinite(v)) { err = "non-finite receiver position"; return WAVE1D_EINVAL; }
+        if (P.bc == WAVE1D_PERIODIC) {
+            v = std::fmod(v + kPi, 2.0 * kPi);
+            if (v < 0) v += 2.0 * kPi;
+            v -= kPi;
+            if (v >= kPi) v -= 2.0 * kPi;
+        } else if (std::fabs(v) > omega_lim) {
+            err = "free-space receiver outside Omega (Sec. 4.4)";
+            return WAVE1D_EDOMAIN;
+        }
+        hp.xr[r] = v;
+    }
+    Window win(P.delta, P.b);
+    int rc = build_local(P, win, hp.xr, hp.x, true, hp.rloc, nullptr, INT64_MAX, err);
+    if (rc) return rc;
+    spread_weights(P, hp.xr, hp.rc_i0, hp.rc_ker);
+    return WAVE1D_OK;
+}
+
+}  // namespace wave1d

@@ -1,0 +1,277 @@
+"""ctypes binding of the wave1d C-ABI (include/wave1d.h).  Argument marshalling only.
+
+Every function below has the name and argument order of the C entry point.  Arrays are
+numpy float64 arrays (host) or torch tensors (device, via `data_ptr()`); the CUDA library
+does all the work.  There is no CPU fallback: `lib()` raises if the library is missing.
+`Plan` is a small convenience wrapper used by the tests and the benchmark.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libwave1d.so")
+
+WAVE1D_PERIODIC = 0
+WAVE1D_FREE = 1
+
+WAVE1D_OK = 0
+WAVE1D_EINVAL = -1
+WAVE1D_EDOMAIN = -2
+WAVE1D_ENOMEM = -3
+WAVE1D_ECUDA = -4
+WAVE1D_ENONFINITE = -6
+WAVE1D_EDONE = -7
+WAVE1D_EUNSUPPORTED = -9
+
+WAVE1D_ARR_ALPHA = 0
+WAVE1D_ARR_ALPHA_P = 1
+WAVE1D_ARR_S_LAST = 2
+WAVE1D_ARR_UH = 3
+WAVE1D_ARR_LOCAL = 4
+WAVE1D_ARR_SIGMA_RING = 5
+WAVE1D_ARR_PERM = 6
+
+EXPORTED = ["wave1d_opts_default", "wave1d_plan", "wave1d_set_incident_gaussians",
+            "wave1d_set_receivers", "wave1d_step", "wave1d_solve", "wave1d_read_receivers",
+            "wave1d_get_sigma", "wave1d_sync", "wave1d_get_info", "wave1d_inspect",
+            "wave1d_destroy", "wave1d_strerror", "wave1d_profile", "wave1d_profile_read"]
+
+WAVE1D_NSTAGE = 9
+STAGES = ["local", "spread", "fft_fwd", "modes", "rbc", "fft_inv", "interp", "solve", "receivers"]
+
+
+class wave1d_opts(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("gamma", ctypes.c_double), ("W", ctypes.c_int),
+                ("NL", ctypes.c_int), ("Ng", ctypes.c_int), ("nufft_w", ctypes.c_int),
+                ("rbc_period", ctypes.c_int), ("max_block", ctypes.c_int),
+                ("max_local_bytes", ctypes.c_int64), ("stream", ctypes.c_void_p)]
+
+
+class wave1d_info(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int64), ("R", ctypes.c_int64), ("Nt", ctypes.c_int64),
+                ("n", ctypes.c_int64),
+                ("K", ctypes.c_int), ("NF", ctypes.c_int), ("W", ctypes.c_int),
+                ("m_max", ctypes.c_int), ("p", ctypes.c_int), ("NL", ctypes.c_int),
+                ("Ng", ctypes.c_int), ("nufft_w", ctypes.c_int), ("nf", ctypes.c_int),
+                ("rbc_period", ctypes.c_int),
+                ("dt", ctypes.c_double), ("tol", ctypes.c_double), ("b", ctypes.c_double),
+                ("delta", ctypes.c_double),
+                ("local_pairs", ctypes.c_int64), ("local_weights", ctypes.c_int64),
+                ("nearby_pairs", ctypes.c_int64), ("blocks", ctypes.c_int64),
+                ("max_block", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+
+
+_lib = None
+_D = ctypes.POINTER(ctypes.c_double)
+
+
+def lib(path: str = LIB_PATH):
+    """Load the CUDA library (built by `paper_2507_07823_gb300.build.build()`)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"wave1d CUDA library not built: {path} (run __graft_entry__.build())")
+        L = ctypes.CDLL(path)
+        P = ctypes.c_void_p
+        L.wave1d_opts_default.argtypes = [ctypes.POINTER(wave1d_opts)]
+        L.wave1d_plan.argtypes = [_D, _D, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
+                                  ctypes.c_int64, ctypes.c_double, ctypes.POINTER(wave1d_opts),
+                                  ctypes.POINTER(P)]
+        L.wave1d_set_incident_gaussians.argtypes = [P, ctypes.c_int, _D, _D, _D]
+        L.wave1d_set_receivers.argtypes = [P, _D, ctypes.c_int64]
+        L.wave1d_step.argtypes = [P, _D, ctypes.c_int]
+        L.wave1d_solve.argtypes = [P, ctypes.c_int64, _D, _D, ctypes.c_int]
+        L.wave1d_read_receivers.argtypes = [P, _D, ctypes.c_int]
+        L.wave1d_get_sigma.argtypes = [P, _D, ctypes.c_int]
+        L.wave1d_sync.argtypes = [P]
+        L.wave1d_get_info.argtypes = [P, ctypes.POINTER(wave1d_info)]
+        L.wave1d_inspect.argtypes = [P, ctypes.c_int, _D, ctypes.c_int64]
+        L.wave1d_destroy.argtypes = [P]
+        L.wave1d_profile.argtypes = [P, ctypes.c_int]
+        L.wave1d_profile_read.argtypes = [P, _D, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]
+        L.wave1d_strerror.argtypes = [ctypes.c_int]
+        L.wave1d_strerror.restype = ctypes.c_char_p
+        for name in EXPORTED:
+            if name != "wave1d_strerror":
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+class Wave1DError(RuntimeError):
+    def __init__(self, status, where):
+        msg = lib().wave1d_strerror(status).decode()
+        super().__init__(f"{where}: status {status}: {msg}")
+        self.status = status
+
+
+def _check(status, where):
+    if status != WAVE1D_OK:
+        raise Wave1DError(status, where)
+
+
+def _hptr(a):
+    return a.ctypes.data_as(_D)
+
+
+def _dptr(t):
+    return ctypes.cast(ctypes.c_void_p(t.data_ptr()), _D)
+
+
+# --- the C entry points, same names -------------------------------------------------------
+def wave1d_opts_default():
+    o = wave1d_opts()
+    _check(lib().wave1d_opts_default(ctypes.byref(o)), "wave1d_opts_default")
+    return o
+
+
+def wave1d_plan(x, beta, M, bc, dt, Nt, tol, opts=None):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    beta = np.ascontiguousarray(beta, dtype=np.float64)
+    h = ctypes.c_void_p()
+    st = lib().wave1d_plan(_hptr(x), _hptr(beta), int(M), int(bc), float(dt), int(Nt), float(tol),
+                           ctypes.byref(opts) if opts is not None else None, ctypes.byref(h))
+    return st, h
+
+
+def wave1d_set_incident_gaussians(plan, n, amp, center, width):
+    a, c, w = (np.ascontiguousarray(v, dtype=np.float64) for v in (amp, center, width))
+    return lib().wave1d_set_incident_gaussians(plan, int(n), _hptr(a), _hptr(c), _hptr(w))
+
+
+def wave1d_set_receivers(plan, xr, R):
+    xr = np.ascontiguousarray(xr, dtype=np.float64)
+    return lib().wave1d_set_receivers(plan, _hptr(xr) if R else None, int(R))
+
+
+def wave1d_step(plan, g_next=None, g_on_device=0):
+    if g_next is None:
+        return lib().wave1d_step(plan, None, 0)
+    ptr = _dptr(g_next) if g_on_device else _hptr(g_next)
+    return lib().wave1d_step(plan, ptr, int(g_on_device))
+
+
+def wave1d_solve(plan, nsteps, u_rec, sigma, out_on_device):
+    f = _dptr if out_on_device else _hptr
+    return lib().wave1d_solve(plan, int(nsteps), f(u_rec) if u_rec is not None else None,
+                              f(sigma) if sigma is not None else None, int(out_on_device))
+
+
+def wave1d_read_receivers(plan, u, on_device):
+    return lib().wave1d_read_receivers(plan, _dptr(u) if on_device else _hptr(u), int(on_device))
+
+
+def wave1d_get_sigma(plan, out, on_device):
+    return lib().wave1d_get_sigma(plan, _dptr(out) if on_device else _hptr(out), int(on_device))
+
+
+def wave1d_sync(plan):
+    return lib().wave1d_sync(plan)
+
+
+def wave1d_get_info(plan):
+    info = wave1d_info()
+    _check(lib().wave1d_get_info(plan, ctypes.byref(info)), "wave1d_get_info")
+    return info
+
+
+def wave1d_inspect(plan, array, host_out):
+    return lib().wave1d_inspect(plan, int(array), _hptr(host_out), int(host_out.size))
+
+
+def wave1d_destroy(plan):
+    return lib().wave1d_destroy(plan)
+
+
+def wave1d_profile(plan, enable):
+    return lib().wave1d_profile(plan, int(enable))
+
+
+def wave1d_profile_read(plan):
+    ms = np.zeros(WAVE1D_NSTAGE)
+    steps = ctypes.c_int64()
+    _check(lib().wave1d_profile_read(plan, _hptr(ms), WAVE1D_NSTAGE, ctypes.byref(steps)),
+           "wave1d_profile_read")
+    return ms, steps.value
+
+
+def wave1d_strerror(status):
+    return lib().wave1d_strerror(int(status)).decode()
+
+
+# --- convenience wrapper ------------------------------------------------------------------
+class Plan:
+    """One wave1d plan built from a `workloads.Workload` (or explicit arrays)."""
+
+    def __init__(self, x, beta, bc, dt, Nt, tol, amp=(), center=(), width=(), xr=(), stream=None,
+                 **opt):
+        o = wave1d_opts_default()
+        for k, v in opt.items():
+            setattr(o, k, v)
+        if stream is not None:
+            o.stream = ctypes.c_void_p(stream)
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        st, h = wave1d_plan(x, beta, x.shape[0], bc, dt, Nt, tol, o)
+        _check(st, "wave1d_plan")
+        self.h = h
+        self.M = x.shape[0]
+        if len(amp):
+            _check(wave1d_set_incident_gaussians(h, len(amp), amp, center, width), "set_incident")
+        xr = np.ascontiguousarray(xr, dtype=np.float64).reshape(-1)
+        self.R = xr.shape[0]
+        if self.R:
+            _check(wave1d_set_receivers(h, xr, self.R), "set_receivers")
+        self.info = wave1d_get_info(h)
+
+    @classmethod
+    def from_workload(cls, w, **kw):
+        return cls(w.x, w.beta, w.bc, w.dt, w.Nt, w.tol, w.amp, w.center, w.width, w.xr,
+                   p=w.p, **kw)
+
+    def solve(self, nsteps, with_sigma=True):
+        u = np.zeros((nsteps, max(self.R, 1)))
+        s = np.zeros((nsteps, self.M)) if with_sigma else None
+        _check(wave1d_solve(self.h, nsteps, u if self.R else None, s, 0), "wave1d_solve")
+        return (s, u[:, :self.R])
+
+    def step(self, g=None):
+        _check(wave1d_step(self.h, g, 0), "wave1d_step")
+
+    def sigma(self):
+        out = np.zeros(self.M)
+        _check(wave1d_get_sigma(self.h, out, 0), "wave1d_get_sigma")
+        return out
+
+    def receivers(self):
+        out = np.zeros(max(self.R, 1))
+        _check(wave1d_read_receivers(self.h, out, 0), "wave1d_read_receivers")
+        return out[:self.R]
+
+    def inspect(self, array):
+        inf = wave1d_get_info(self.h)
+        sizes = {WAVE1D_ARR_ALPHA: 2 * (inf.K + 1), WAVE1D_ARR_ALPHA_P: 2 * (inf.K + 1),
+                 WAVE1D_ARR_S_LAST: 2 * (inf.K + 1), WAVE1D_ARR_UH: self.M,
+                 WAVE1D_ARR_LOCAL: self.M, WAVE1D_ARR_SIGMA_RING: (inf.m_max + 1) * self.M,
+                 WAVE1D_ARR_PERM: self.M}
+        out = np.zeros(sizes[array])
+        _check(wave1d_inspect(self.h, array, out), "wave1d_inspect")
+        if array in (WAVE1D_ARR_ALPHA, WAVE1D_ARR_ALPHA_P, WAVE1D_ARR_S_LAST):
+            return out[0::2] + 1j * out[1::2]
+        if array == WAVE1D_ARR_SIGMA_RING:
+            return out.reshape(inf.m_max + 1, self.M)
+        return out
+
+    def close(self):
+        if self.h:
+            wave1d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

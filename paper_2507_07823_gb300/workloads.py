@@ -111,8 +111,12 @@ def make(name: str = "custom", *, M: int, bc: int, dt: float, Nt: int, tol: floa
          p: int = 8, seed: int = 7823, layout: str = "uniform",
          beta_range=(1.0, 10.0), beta_dist: str = "uniform",
          amp=(1.0,), center=(-2.0,), width=(0.1,), R: int = 4,
-         xr: Optional[np.ndarray] = None, description: str = "") -> Workload:
-    """Draw one seeded workload.  Springs avoid the pulse support at t = 0."""
+         xr: Optional[np.ndarray] = None, description: str = "",
+         margin: float = FREE_MARGIN) -> Workload:
+    """Draw one seeded workload.  Springs avoid the pulse support at t = 0.
+
+    margin: free space only, springs and receivers lie in [-pi + margin, pi - margin]; it must
+    cover 3 delta = 3 W dt of the plan (Sec. 4.4)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     amp = np.asarray(amp, dtype=np.float64)
     center = np.asarray(center, dtype=np.float64)
@@ -121,7 +125,7 @@ def make(name: str = "custom", *, M: int, bc: int, dt: float, Nt: int, tol: floa
     if periodic:
         lo, hi = -PI, PI
     else:
-        lo, hi = -PI + FREE_MARGIN, PI - FREE_MARGIN
+        lo, hi = -PI + margin, PI - margin
     x = _draw_positions(rng, M, layout, periodic, center, width, lo, hi)
     if beta_dist == "uniform":
         beta = rng.uniform(beta_range[0], beta_range[1], size=M)

@@ -1,0 +1,58 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point include/wave1d.h
+declares.  No GPU work is done here (argument checks return before any CUDA call)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2507_07823_gb300 import build, wave1d
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return wave1d.lib()
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "wave1d.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(wave1d_\w+)\s*\(", txt, re.M)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 13
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(wave1d.EXPORTED)
+
+
+def test_defaults_and_strerror(lib):
+    o = wave1d.wave1d_opts_default()
+    assert o.p == 8 and o.gamma == 0.5 and o.Ng == 32 and o.W == 0
+    for st in (0, -1, -2, -3, -4, -6, -7, -9):
+        assert isinstance(wave1d.wave1d_strerror(st), str)
+
+
+def test_argument_validation_without_gpu(lib):
+    x = np.array([0.1, 0.2])
+    b = np.array([1.0, 2.0])
+    assert wave1d.wave1d_plan(x, b, 0, 0, 0.01, 10, 1e-10)[0] == wave1d.WAVE1D_EINVAL
+    assert wave1d.wave1d_plan(x, b, 2, 7, 0.01, 10, 1e-10)[0] == wave1d.WAVE1D_EINVAL
+    assert wave1d.wave1d_plan(x, b, 2, 0, -0.01, 10, 1e-10)[0] == wave1d.WAVE1D_EINVAL
+    assert wave1d.wave1d_plan(x, b, 2, 0, 0.01, 10, 0.5)[0] == wave1d.WAVE1D_EINVAL
+    o = wave1d.wave1d_opts_default()
+    o.p = 7
+    assert wave1d.wave1d_plan(x, b, 2, 0, 0.01, 10, 1e-10, o)[0] == wave1d.WAVE1D_EINVAL
+    # window wider than pi (Sec. 3 assumes delta < pi)
+    assert wave1d.wave1d_plan(x, b, 2, 0, 0.2, 10, 1e-10)[0] == wave1d.WAVE1D_EDOMAIN
+    # free-space spring outside Omega (Sec. 4.4)
+    assert wave1d.wave1d_plan(np.array([3.1, 0.0]), b, 2, 1, 0.01, 10, 1e-10)[0] == wave1d.WAVE1D_EDOMAIN
+    bad = np.array([np.nan, 0.0])
+    assert wave1d.wave1d_plan(bad, b, 2, 0, 0.01, 10, 1e-10)[0] == wave1d.WAVE1D_EINVAL
+    assert wave1d.wave1d_plan(x, np.array([1.0, -1.0]), 2, 0, 0.01, 10, 1e-10)[0] == wave1d.WAVE1D_EINVAL
+    assert wave1d.wave1d_destroy(None) == 0
