@@ -182,6 +182,25 @@ enum wave1d_stage {
 int wave1d_profile(wave1d_plan_t plan, int enable);
 int wave1d_profile_read(wave1d_plan_t plan, double* ms, int nstage, int64_t* steps);
 
+/*
+ * Type-1 NUFFT of device arrays without any memory allocation (the paper has no counterpart; it
+ * is a service for callers that cannot allocate device memory — code running under a memory
+ * budget reserved up front, or in a loop that must not take the implicit device synchronisation
+ * cudaMalloc/cudaFree can cause).
+ *   S[2k], S[2k+1] = Re, Im of (1/2 pi) sum_j c[j] e^{i k x[j]},  k = 0..K
+ * computed with the spreading kernel, fine grid and FFT a plan of the same K and tol uses.
+ *   x, c : device, M values (x read periodically on [-pi, pi)); S: device, 2 (K+1) values.
+ *   stream: cudaStream_t (NULL = legacy default stream).  Asynchronous.
+ * All intermediates live in one file-scope device array of 2 MiB that every GPU loading the
+ * library keeps until exit; fine grids above 65536 points (K > 16383) return
+ * WAVE1D_EUNSUPPORTED.  The first call on a device looks up that array's address (with that
+ * device current); make it before any stream capture.  The array is shared by all calls and keeps
+ * the last call's contents, so calls that overlap on the GPU race; serialise them on one stream.
+ * No cudaMalloc, cudaFree or other allocating routine is called.
+ */
+int wave1d_nufft1_noalloc(const double* x, const double* c, int64_t M, int K, double tol,
+                          double* S, void* stream);
+
 /* Free the plan and its device memory (synchronises).  NULL is accepted. */
 int wave1d_destroy(wave1d_plan_t plan);
 

@@ -38,7 +38,8 @@ WAVE1D_ARR_PERM = 6
 EXPORTED = ["wave1d_opts_default", "wave1d_plan", "wave1d_set_incident_gaussians",
             "wave1d_set_receivers", "wave1d_step", "wave1d_solve", "wave1d_read_receivers",
             "wave1d_get_sigma", "wave1d_sync", "wave1d_get_info", "wave1d_inspect",
-            "wave1d_destroy", "wave1d_strerror", "wave1d_profile", "wave1d_profile_read"]
+            "wave1d_destroy", "wave1d_strerror", "wave1d_profile", "wave1d_profile_read",
+            "wave1d_nufft1_noalloc"]
 
 WAVE1D_NSTAGE = 9
 STAGES = ["local", "spread", "fft_fwd", "modes", "rbc", "fft_inv", "interp", "solve", "receivers"]
@@ -93,6 +94,8 @@ def lib(path: str = LIB_PATH):
         L.wave1d_destroy.argtypes = [P]
         L.wave1d_profile.argtypes = [P, ctypes.c_int]
         L.wave1d_profile_read.argtypes = [P, _D, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]
+        L.wave1d_nufft1_noalloc.argtypes = [_D, _D, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
+                                            _D, ctypes.c_void_p]
         L.wave1d_strerror.argtypes = [ctypes.c_int]
         L.wave1d_strerror.restype = ctypes.c_char_p
         for name in EXPORTED:
@@ -197,6 +200,12 @@ def wave1d_profile_read(plan):
     _check(lib().wave1d_profile_read(plan, _hptr(ms), WAVE1D_NSTAGE, ctypes.byref(steps)),
            "wave1d_profile_read")
     return ms, steps.value
+
+
+def wave1d_nufft1_noalloc(x, c, M, K, tol, S, stream=None):
+    """x, c, S: device tensors (float64); S holds 2 (K+1) values."""
+    return lib().wave1d_nufft1_noalloc(_dptr(x), _dptr(c), int(M), int(K), float(tol), _dptr(S),
+                                       ctypes.c_void_p(stream) if stream else None)
 
 
 def wave1d_strerror(status):
