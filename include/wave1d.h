@@ -79,6 +79,8 @@ typedef struct {
     int64_t nearby_pairs;     /* pairs closer than dt (entries of S, eq. linearSystem)               */
     int64_t blocks, max_block;/* connected blocks of the nearby graph and the largest block size     */
     int64_t device_bytes;     /* device memory owned by the plan                                     */
+    int64_t local_bytes;      /* bytes the local-sum kernel streams per step: weights, source lists,
+                                 per-m counts, row offsets and its output                         */
 } wave1d_info;
 
 /* Fill *o with defaults.  Returns WAVE1D_EINVAL if o is NULL. */

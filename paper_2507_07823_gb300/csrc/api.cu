@@ -25,8 +25,7 @@ __global__ void k_modes(DevPlan P);
 __global__ void k_rbc_grid(DevPlan P);
 __global__ void k_rbc_update(DevPlan P, int npts);
 __global__ void k_interp(DevPlan P);
-__global__ void k_local(DevPlan P);
-__global__ void k_rhs(DevPlan P);
+__global__ void k_local_items(DevPlan P);
 __global__ void k_solve(DevPlan P);
 __global__ void k_receivers(DevPlan P);
 __global__ void k_sigma_to_caller(DevPlan P, int64_t q, double* out);
@@ -50,8 +49,10 @@ struct wave1d_plan_s {
     DevPlan dp{};
     cudaStream_t user = nullptr;      // caller's stream (may be the legacy default stream)
     cudaStream_t s = nullptr;         // private stream
-    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaStream_t s2 = nullptr;        // side stream for the local sum (joined within each step)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_fork = nullptr, ev_join = nullptr;
     int device = 0;
+    int sms = 1;                      // multiprocessors of the device
     int64_t n = 0;                    // host mirror of the device step counter
     std::vector<void*> allocs;
     int64_t bytes = 0;
@@ -133,31 +134,81 @@ int leave(wave1d_plan_t p) {
     return WAVE1D_OK;
 }
 
+struct ItemsDev {
+    const int64_t* item_ptr;
+    const int32_t* row;
+    const int32_t* s0;
+    const int32_t* len;
+    const int64_t* wbase;
+    const int32_t* src;
+    const float* w;
+};
+
+int upload_items(wave1d_plan_t p, const LocalItems& L, ItemsDev& o) {
+    int rc;
+    int64_t* i64;
+    int32_t* i32;
+    float* f32;
+    if ((rc = upload(p, L.item_ptr, &i64))) return rc;
+    o.item_ptr = i64;
+    if ((rc = upload(p, L.row, &i32))) return rc;
+    o.row = i32;
+    if ((rc = upload(p, L.s0, &i32))) return rc;
+    o.s0 = i32;
+    if ((rc = upload(p, L.len, &i32))) return rc;
+    o.len = i32;
+    if ((rc = upload(p, L.wbase, &i64))) return rc;
+    o.wbase = i64;
+    if ((rc = upload(p, L.src, &i32))) return rc;
+    o.src = i32;
+    if ((rc = upload(p, L.w, &f32))) return rc;
+    o.w = f32;
+    return WAVE1D_OK;
+}
+
 int upload_receivers(wave1d_plan_t p) {
     HostPlan& hp = p->hp;
     DevPlan& d = p->dp;
     d.R = hp.P.R;
     int rc = 0;
     int32_t* i32;
-    int64_t* i64;
     double* f64;
     if ((rc = upload(p, hp.rc_i0, &i32))) return rc;
     d.rc_i0 = i32;
     if ((rc = upload(p, hp.rc_ker, &f64))) return rc;
     d.rc_ker = f64;
-    if ((rc = upload(p, hp.rloc.row_ptr, &i64))) return rc;
-    d.rrow_ptr = i64;
-    if ((rc = upload(p, hp.rloc.src, &i32))) return rc;
-    d.rsrc = i32;
-    if ((rc = upload(p, hp.rloc.mrange, &i32))) return rc;
-    d.rmrange = i32;
-    if ((rc = upload(p, hp.rloc.woff, &i64))) return rc;
-    d.rwoff = i64;
-    if ((rc = upload(p, hp.rloc.w, &f64))) return rc;
-    d.rwq = f64;
+    ItemsDev it;
+    if ((rc = upload_items(p, hp.ritems, it))) return rc;
+    d.r_mfirst = hp.ritems.m_first;
+    d.r_nitems = (int64_t)hp.ritems.row.size();
+    d.r_item_ptr = it.item_ptr;
+    d.r_s0 = it.s0;
+    d.r_len = it.len;
+    d.r_wbase = it.wbase;
+    d.r_src = it.src;
+    d.r_w = it.w;
+    if ((rc = zeros(p, &d.r_part, (size_t)std::max<int64_t>(1, d.r_nitems)))) return rc;
+    int64_t* i64b;
+    if ((rc = upload(p, hp.r0_ptr, &i64b))) return rc;
+    d.r0_ptr = i64b;
+    int32_t* i32b;
+    if ((rc = upload(p, hp.r0_src, &i32b))) return rc;
+    d.r0_src = i32b;
+    double* f64b;
+    if ((rc = upload(p, hp.r0_w, &f64b))) return rc;
+    d.r0_w = f64b;
     if ((rc = zeros(p, &d.uHr, (size_t)std::max<int64_t>(1, d.R)))) return rc;
     if ((rc = zeros(p, &d.rec_hist, (size_t)p->chunk * std::max<int64_t>(1, d.R)))) return rc;
     return WAVE1D_OK;
+}
+
+// items kernel: as many 8-warp blocks as are resident at once; warps fetch items dynamically
+unsigned local_grid(const wave1d_plan_t p) {
+    const DevPlan& d = p->dp;
+    int64_t items = d.l_nitems + d.r_nitems;
+    int64_t want = (items + 7) / 8;
+    int64_t cap = (int64_t)p->sms * 4;           // blocks resident at once (launch bounds 256, 4)
+    return (unsigned)std::max<int64_t>(1, std::min(want, cap));
 }
 
 bool is_rbc_step(const wave1d_plan_t p, int64_t n) {
@@ -178,18 +229,27 @@ int enqueue_step(wave1d_plan_t p, int64_t n, const double* g_ext, double* sig_hi
     auto mark = [&](int i) {
         if (ev) cudaEventRecord(ev[i], s);
     };
+    // the local sum needs only sigma^{<= n}: without profiling it runs on the side stream,
+    // concurrently with the history pipeline, and is joined before the solve
+    bool fork = (ev == nullptr);
     mark(WAVE1D_STAGE_LOCAL);
-    k_local<<<blocks(P.M * 32, T), T, 0, s>>>(d);
+    if (fork) {
+        cudaEventRecord(p->ev_fork, s);
+        cudaStreamWaitEvent(p->s2, p->ev_fork, 0);
+        k_local_items<<<local_grid(p), T, 0, p->s2>>>(d);
+        cudaEventRecord(p->ev_join, p->s2);
+    } else {
+        k_local_items<<<local_grid(p), T, 0, s>>>(d);
+    }
     mark(WAVE1D_STAGE_SPREAD);
     k_spread<<<blocks(P.nf, T), T, 0, s>>>(d);
     mark(WAVE1D_STAGE_FFT_FWD);
     int l1 = ilog2(P.L1), l2 = ilog2(P.L2);
     int t1 = std::max(32, std::min(P.L1 / 2, 512)), t2 = std::max(32, std::min(P.L2 / 2, 512));
+    size_t sm1 = fft_smem_bytes(P.L1), sm2 = fft_smem_bytes(P.L2);
     const double2* tw = (const double2*)d.twiddle;
-    k_fft_cols<<<P.L2, t1, P.L1 * sizeof(double2), s>>>((const double2*)d.grid, (double2*)d.work, tw, P.L,
-                                                         P.L1, P.L2, l1, +1);
-    k_fft_rows<<<P.L1, t2, P.L2 * sizeof(double2), s>>>((const double2*)d.work, (double2*)d.spec, tw, P.L,
-                                                         P.L1, P.L2, l2, +1);
+    k_fft_cols<<<P.L2, t1, sm1, s>>>((const double2*)d.grid, (double2*)d.work, tw, P.L, P.L1, P.L2, l1, +1);
+    k_fft_rows<<<P.L1, t2, sm2, s>>>((const double2*)d.work, (double2*)d.spec, tw, P.L, P.L1, P.L2, l2, +1);
     mark(WAVE1D_STAGE_MODES);
     k_modes<<<blocks(4 * (int64_t)(P.K + 1), T), T, 0, s>>>(d);
     mark(WAVE1D_STAGE_RBC);
@@ -199,14 +259,12 @@ int enqueue_step(wave1d_plan_t p, int64_t n, const double* g_ext, double* sig_hi
         k_rbc_update<<<blocks(P.K + 1, 128), 128, 0, s>>>(d, npts);
     }
     mark(WAVE1D_STAGE_FFT_INV);
-    k_fft_cols<<<P.L2, t1, P.L1 * sizeof(double2), s>>>((const double2*)d.spec2, (double2*)d.work, tw, P.L,
-                                                         P.L1, P.L2, l1, -1);
-    k_fft_rows<<<P.L1, t2, P.L2 * sizeof(double2), s>>>((const double2*)d.work, (double2*)d.grid, tw, P.L,
-                                                         P.L1, P.L2, l2, -1);
+    k_fft_cols<<<P.L2, t1, sm1, s>>>((const double2*)d.spec2, (double2*)d.work, tw, P.L, P.L1, P.L2, l1, -1);
+    k_fft_rows<<<P.L1, t2, sm2, s>>>((const double2*)d.work, (double2*)d.grid, tw, P.L, P.L1, P.L2, l2, -1);
     mark(WAVE1D_STAGE_INTERP);
     k_interp<<<blocks(P.M + P.R, T), T, 0, s>>>(d);
     mark(WAVE1D_STAGE_SOLVE);
-    k_rhs<<<blocks(P.M, T), T, 0, s>>>(d);
+    if (fork) cudaStreamWaitEvent(s, p->ev_join, 0);
     k_solve<<<blocks(d.nblocks * 32, T), T, 0, s>>>(d);
     mark(WAVE1D_STAGE_RECEIVERS);
     k_receivers<<<blocks(std::max<int64_t>(P.R, 1) * 32, T), T, 0, s>>>(d);
@@ -346,9 +404,14 @@ int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double d
         return code;
     };
     if (cudaGetDevice(&p->device) != cudaSuccess) return cleanup(fail(WAVE1D_ECUDA, "no CUDA device"));
+    if (cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess)
+        return cleanup(fail(WAVE1D_ECUDA, "cannot read the multiprocessor count"));
     if (cudaStreamCreateWithFlags(&p->s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&p->s2, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess)
         return cleanup(fail(WAVE1D_ECUDA, "stream/event creation failed"));
     if ((rc = enter(p))) return cleanup(rc);
 
@@ -377,6 +440,7 @@ int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double d
     if ((rc = upload(p, vec, &tmp))) return cleanup(rc); \
     d.field = tmp;
     if ((rc = zeros(p, &d.step, 2))) return cleanup(rc);
+    if ((rc = zeros(p, &d.item_ctr, 1))) return cleanup(rc);
     if ((rc = zeros(p, &d.status, 1))) return cleanup(rc);
     UP(hp.x, x, f64);
     UP(hp.beta, beta, f64);
@@ -386,6 +450,11 @@ int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double d
     UP(hp.deconv1, deconv1, f64);
     UP(hp.deconv2, deconv2, f64);
     UP(hp.twiddle, twiddle, f64);
+    UP(hp.modefac, modefac, f64);
+    UP(hp.tw2K, tw2K, f64);
+    UP(hp.g_ptr, g_ptr, i32);
+    UP(hp.g_src, g_src, i32);
+    UP(hp.g_w, g_w, f64);
     if ((rc = zeros(p, &d.Sring, (size_t)P.W * (P.K + 1) * 2))) return cleanup(rc);
     if ((rc = zeros(p, &d.alpha, (size_t)(P.K + 1) * 2))) return cleanup(rc);
     if ((rc = zeros(p, &d.alpha_p, (size_t)(P.K + 1) * 2))) return cleanup(rc);
@@ -396,16 +465,24 @@ int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double d
     if ((rc = zeros(p, &d.rhs, (size_t)P.M))) return cleanup(rc);
     UP(hp.sp_i0, sp_i0, i32);
     UP(hp.sp_ker, sp_ker, f64);
-    UP(hp.bin_ptr, bin_ptr, i32);
-    UP(hp.bin_list, bin_list, i32);
     if ((rc = zeros(p, &d.uH, (size_t)P.M))) return cleanup(rc);
-    UP(hp.loc.row_ptr, row_ptr, i64);
-    UP(hp.loc.src, src, i32);
-    UP(hp.loc.mrange, mrange, i32);
-    UP(hp.loc.woff, woff, i64);
-    UP(hp.loc.w, wq, f64);
+    {
+        ItemsDev it;
+        if ((rc = upload_items(p, hp.litems, it))) return cleanup(rc);
+        d.l_mfirst = hp.litems.m_first;
+        d.l_nitems = (int64_t)hp.litems.row.size();
+        d.l_item_ptr = it.item_ptr;
+        d.l_row = it.row;
+        d.l_s0 = it.s0;
+        d.l_len = it.len;
+        d.l_wbase = it.wbase;
+        d.l_src = it.src;
+        d.l_w = it.w;
+        if ((rc = zeros(p, &d.l_part, (size_t)std::max<int64_t>(1, d.l_nitems)))) return cleanup(rc);
+    }
     if ((rc = zeros(p, &d.clocal, (size_t)P.M))) return cleanup(rc);
     if ((rc = zeros(p, &d.sig, (size_t)P.M * P.ring))) return cleanup(rc);
+    if ((rc = zeros(p, &d.sig2, (size_t)P.M * P.ring * 4))) return cleanup(rc);
     UP(hp.blk_ptr, blk_ptr, i64);
     UP(hp.blk_members, blk_members, i32);
     UP(hp.blk_inv_off, blk_inv_off, i64);
@@ -437,7 +514,7 @@ int wave1d_set_incident_gaussians(wave1d_plan_t p, int n, const double* amp, con
             return fail(WAVE1D_EINVAL, "pulse widths must be positive and parameters finite");
         h[3 * i] = amp[i];
         h[3 * i + 1] = center[i];
-        h[3 * i + 2] = width[i];
+        h[3 * i + 2] = 1.0 / width[i];
     }
     int rc = enter(p);
     if (rc) return rc;
@@ -584,11 +661,16 @@ int wave1d_get_info(wave1d_plan_t p, wave1d_info* info) {
     info->b = P.b;
     info->delta = P.delta;
     info->local_pairs = (int64_t)p->hp.loc.src.size();
-    info->local_weights = (int64_t)p->hp.loc.w.size();
+    info->local_weights = (int64_t)p->hp.lrows.w.size() / 2;
     info->nearby_pairs = p->hp.loc.nearby;
     info->blocks = (int64_t)p->hp.blk_ptr.size() - 1;
     info->max_block = p->hp.max_block;
     info->device_bytes = p->bytes;
+    const LocalItems& L = p->hp.litems;
+    info->local_bytes = (int64_t)(L.w.size() * sizeof(float) + L.src.size() * sizeof(int32_t) +
+                                  (L.s0.size() + L.len.size()) * sizeof(int32_t) +
+                                  L.wbase.size() * sizeof(int64_t)) +
+                        8 * (int64_t)L.row.size();
     return WAVE1D_OK;
 }
 
@@ -677,6 +759,10 @@ int wave1d_destroy(wave1d_plan_t p) {
     for (void* a : p->allocs) cudaFree(a);
     if (p->ev_in) cudaEventDestroy(p->ev_in);
     if (p->ev_out) cudaEventDestroy(p->ev_out);
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_join) cudaEventDestroy(p->ev_join);
+    if (p->s2) cudaStreamSynchronize(p->s2);
+    if (p->s2) cudaStreamDestroy(p->s2);
     if (p->s) cudaStreamDestroy(p->s);
     delete p;
     return WAVE1D_OK;

@@ -35,6 +35,36 @@ struct LocalCSR {
     int64_t nearby = 0;                // pairs with d < dt
 };
 
+// The same weights regrouped for the step kernel (Sec. 4.1 local sum), one row per target:
+// sources sorted by the first m they need (m_lo, which grows with the distance), and for each
+// m = m_first .. m_top the weights of the cnt[m] sources active at that m (a prefix of the sorted
+// list), stored m-major so a warp reads each m's weights contiguously.  Weights are split into a
+// pair of floats (hi = fl(Q), lo = fl(Q - hi)) for compensated FP32 arithmetic.
+struct LocalRows {
+    int m_first = 1, nm = 0;            // m = m_first .. m_first + nm - 1
+    std::vector<int64_t> src_off;       // rows + 1
+    std::vector<int32_t> src;           // per row, sorted sources
+    std::vector<int64_t> w_off;         // rows + 1 (in weights)
+    std::vector<uint16_t> cnt;          // rows * nm
+    std::vector<float> w;               // 2 floats per weight (hi, lo)
+};
+
+// The local weights as independent work items of 32 sources (a "chunk" of one target row): lane l
+// of item c handles source rank 32 c + l of its row and walks the m-slices s0 .. s0 + len - 1; the
+// weights of elements 2u, 2u+1 are at w[wbase + 64 u + 2 l + {0, 1}] (zero before the source's
+// first slice, past the row's last source, and in the padding that makes len even), so a warp reads
+// one contiguous 512-byte line per element pair.
+struct LocalItems {
+    int m_first = 1;
+    std::vector<int64_t> item_ptr;      // rows + 1
+    std::vector<int32_t> row;           // per item
+    std::vector<int32_t> s0, len;       // first slice, number of slices
+    std::vector<int64_t> wbase;         // offset (in weights) of element 0, lane 0
+    std::vector<int32_t> src;           // 32 per item (source index, 0 for padded lanes)
+    std::vector<float> w;               // 2 floats per weight (hi, lo)
+};
+int build_items(const LocalRows& rows, LocalItems& items);
+
 struct HostPlan {
     Params P;
     std::vector<int32_t> perm;         // internal index -> caller index
@@ -46,6 +76,13 @@ struct HostPlan {
     std::vector<double> deconv1;       // [k] type-1 deconvolution (-1)^k h / (2 pi psihat(k))
     std::vector<double> deconv2;       // [k] type-2 deconvolution (-1)^k h / psihat(k)
     std::vector<double> twiddle;       // [j][2] e^{+2 pi i j / L}, j < L
+    std::vector<double> modefac;       // [k][8]: deconv1, Re/Im deconv1 e^{2 pi i k/nf},
+                                       //         Re/Im deconv2 (1 + i e^{-2 pi i k/nf}),
+                                       //         Re/Im deconv2 (1 - i e^{-2 pi i (L-k)/nf}), 0
+    std::vector<double> tw2K;          // [a][2] e^{i pi a / K}, a < 2K (radiation projection)
+    std::vector<int32_t> g_ptr;        // nf + 1: spreading as a sparse matrix, grid-row major
+    std::vector<int32_t> g_src;        //   spring of each entry (internal order)
+    std::vector<double> g_w;           //   kernel weight of each entry
     // spreading / interpolation
     std::vector<int32_t> sp_i0;        // springs: first fine-grid index (wrapped)
     std::vector<double> sp_ker;        // springs: [j][w] kernel weights
@@ -56,11 +93,18 @@ struct HostPlan {
     // local part
     LocalCSR loc;                      // springs (m >= 1 only; m = 0 lives in the blocks)
     LocalCSR rloc;                     // receivers (m >= 0)
+    LocalRows lrows;                   // springs, m-major rows
+    LocalRows rrows;                   // receivers, m-major rows
+    LocalItems litems;                 // springs, step-kernel layout
+    LocalItems ritems;                 // receivers, m >= 1, step-kernel layout
+    std::vector<int64_t> r0_ptr;       // receivers: sources closer than dt with their m = 0 weight
+    std::vector<int32_t> r0_src;
+    std::vector<double> r0_w;
     // implicit blocks of I + S (eq. linearSystem), inverted
     std::vector<int64_t> blk_ptr;      // blocks + 1 into blk_members
     std::vector<int32_t> blk_members;  // internal spring indices
     std::vector<int64_t> blk_inv_off;  // offset of each block's inverse in inv
-    std::vector<double> inv;           // row-major inverses
+    std::vector<double> inv;           // column-major inverses: inv[l * s + i] = inverse[i][l]
     int64_t max_block = 0;
     // radiation projection: grid points i of the 2K-point grid that are rolled off
     std::vector<int32_t> rbc_idx;      // 4W grid indices
@@ -69,12 +113,17 @@ struct HostPlan {
     std::vector<double> rbc_dphi;      // phi_s'(arg)
 };
 
+// Dynamic shared memory of k_fft_cols / k_fft_rows for a line of N points: the line itself and
+// its N/2 twiddles (every launch site must use this).
+inline size_t fft_smem_bytes(int N) { return (size_t)(N + N / 2) * 16; }
+
 // Returns 0 or a negative wave1d_status; fills err with a message on failure.
 int build_host_plan(const double* x, const double* beta, int64_t M, int bc, double dt, int64_t Nt,
                     double tol, int p, double gamma, int W, int NL, int Ng, int nufft_w,
                     int rbc_period, int max_block, int64_t max_local_bytes, HostPlan& hp,
                     std::string& err);
 int build_receivers(HostPlan& hp, const double* xr, int64_t R, std::string& err);
+int build_rows(const LocalCSR& csr, int m_first, LocalRows& rows, std::string& err);
 
 // ---------------------------------------------------------------------------------------------
 // Device view (passed by value to kernels)
@@ -113,24 +162,42 @@ struct DevPlan {
     const double* sp_ker;
     const int32_t* rc_i0;
     const double* rc_ker;
-    const int32_t* bin_ptr;
-    const int32_t* bin_list;
     double* uH;               // M (internal order)
     double* uHr;              // R
-    // local part
-    const int64_t* row_ptr;
-    const int32_t* src;
-    const int32_t* mrange;
-    const int64_t* woff;
-    const double* wq;
-    const int64_t* rrow_ptr;
-    const int32_t* rsrc;
-    const int32_t* rmrange;
-    const int64_t* rwoff;
-    const double* rwq;
-    double* clocal;           // M
-    // density ring, time-contiguous per spring: sig[j * ring + (q mod ring)] = sigma_j^q
+    double* clocal;           // M, local explicit sum of the step
+    // density rings, time-major: sig[(q mod ring) * M + j] = sigma_j^q, and the same values as
+    // float pairs (hi, lo) in sig2 for the compensated local sum
     double* sig;
+    float* sig2;              // interleaved (hi, lo)
+    // local part, step-kernel layout (see LocalItems); sig2 holds 2 * ring slots (slot s and s + ring
+    // carry the same values) so a walk over m never wraps
+    int l_mfirst, r_mfirst;
+    int64_t l_nitems, r_nitems;
+    const int64_t* l_item_ptr;
+    const int32_t* l_row;
+    const int32_t* l_s0;
+    const int32_t* l_len;
+    const int64_t* l_wbase;
+    const int32_t* l_src;
+    const float* l_w;             // interleaved (hi, lo)
+    const int64_t* r_item_ptr;
+    const int32_t* r_s0;
+    const int32_t* r_len;
+    const int64_t* r_wbase;
+    const int32_t* r_src;
+    const float* r_w;
+    double* l_part;               // per spring item: partial local sum
+    double* r_part;               // per receiver item: partial local sum (m >= 1)
+    unsigned long long* item_ctr; // items handed out in this step (reset by the solve)
+    const int64_t* r0_ptr;        // receivers: m = 0 terms (sources closer than dt)
+    const int32_t* r0_src;
+    const double* r0_w;
+    // spreading matrix and per-mode factors
+    const int32_t* g_ptr;
+    const int32_t* g_src;
+    const double* g_w;
+    const double* modefac;
+    const double* tw2K;
     // blocks
     const int64_t* blk_ptr;
     const int32_t* blk_members;

@@ -1,14 +1,19 @@
-// Per-step kernels of the WFP march.  One time step n -> n+1 is, in launch order:
-//   k_local      local explicit sum over the last delta of history (Sec. 4.1, m >= 1)
-//   k_spread     type-1 spreading of sigma^n onto the fine grid (eq. densco via NUFFT)
+// Per-step kernels of the WFP march.  One time step n -> n+1:
+//   k_local_items local explicit sum over the last delta of history (Sec. 4.1, m >= 1), on a side
+//                 stream, concurrent with the history pipeline below
+//   k_spread      type-1 spreading of sigma^n onto the fine grid (eq. densco via NUFFT)
 //   k_fft_cols / k_fft_rows   forward complex FFT of the grid viewed as L = nf/2 complex points
-//   k_modes      S_k^n, FIR driving terms, exact rotation, type-2 spectrum (Sec. 3)
+//   k_modes       S_k^n, FIR driving terms, exact rotation, type-2 spectrum (Sec. 3)
 //   [k_rbc_grid, k_rbc_update]  radiation projection on projection steps (Sec. 4.4)
 //   k_fft_cols / k_fft_rows   inverse FFT of the type-2 spectrum
-//   k_interp     u_H at springs and receivers (eq. historySol1 via NUFFT)
-//   k_solve      right-hand side and block solve of -(I + S) sigma^{n+1} = ... (eq. linearSystem)
-//   k_receivers  u = u_L + u_H at receivers; the last block advances the step counter
+//   k_interp      u_H at springs and receivers (eq. historySol1 via NUFFT)
+//   k_solve       forcing, right-hand side and block solve of eq. linearSystem
+//   k_receivers   u = u_L + u_H at receivers; the last block advances the step counter
 // Kernels read the step index n from device memory so that captured graphs can be replayed.
+//
+// GB300 runs FP64 at about 2 FMA per clock per SM and FP32 at 128, so the one kernel with a
+// per-pair inner loop (the local sum) does its products and sums in compensated FP32 pairs
+// (hi + lo, about 48 significant bits), which keeps it bound by HBM rather than by the FP64 pipe.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -40,24 +45,154 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// type-1 spreading, gather form: G[i] = sum over springs whose support starts at c = i - t of
-// sigma_j^n psi_{j,t}.  Deterministic (no atomics).
+// compensated FP32 pairs: a value is hi + lo with |lo| <= ulp(hi)/2 (error-free transformations,
+// written with rounding intrinsics so the compiler neither contracts nor reassociates them)
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (sh, sl) += (wh + wl) (vh + vl), dropping wl vl (relative 2^-48)
+__device__ __forceinline__ void pair_mac(float& sh, float& sl, float2 w, float2 v) {
+    float p = __fmul_rn(w.x, v.x);
+    float e = __fmaf_rn(w.x, v.x, -p);
+    e = __fmaf_rn(w.x, v.y, e);
+    e = __fmaf_rn(w.y, v.x, e);
+    float s, t;
+    two_sum(sh, p, s, t);
+    sh = s;
+    sl = __fadd_rn(sl, __fadd_rn(t, e));
+}
+
+__device__ __forceinline__ void pair_add(float& sh, float& sl, float oh, float ol) {
+    float s, t;
+    two_sum(sh, oh, s, t);
+    sh = s;
+    sl = __fadd_rn(sl, __fadd_rn(ol, t));
+}
+
+__device__ __forceinline__ void pair_warp_sum(float& sh, float& sl) {
+    for (int o = 16; o > 0; o >>= 1) {
+        float oh = __shfl_xor_sync(0xffffffffu, sh, o);
+        float ol = __shfl_xor_sync(0xffffffffu, sl, o);
+        pair_add(sh, sl, oh, ol);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// local explicit sum (Sec. 4.1), one work item = 32 sources of one target row (see LocalItems):
+//   partial = sum_t sum_lanes Q[slice s0 + t][rank] sigma_src^{n+1-m},  m = m_first + s0 + t
+// The density ring sig2 has 2 ring slots (slot s and s + ring hold the same values), so the slot
+// of slice s0 + t is b0 - t with b0 in [ring, 2 ring): the walk never wraps.  Each element is one
+// contiguous 256-byte weight line per warp, one density load and one compensated multiply-add.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ void local_item(const float2* __restrict__ sig2, int64_t M, int ring, int q,
+                                           int mfirst, int s0, int len, const float4* __restrict__ wp,
+                                           int sj, float& sh, float& sl) {
+    int b0 = (q - mfirst - s0) % ring;
+    if (b0 < 0) b0 += ring;
+    b0 += ring;
+    const float2* sp = sig2 + (int64_t)b0 * M + sj;
+    int t = 0;
+    for (; t + 8 <= len; t += 8) {
+        float4 w01 = __ldg(wp + 32 * (t >> 1)), w23 = __ldg(wp + 32 * ((t >> 1) + 1));
+        float4 w45 = __ldg(wp + 32 * ((t >> 1) + 2)), w67 = __ldg(wp + 32 * ((t >> 1) + 3));
+        float2 v0 = __ldg(sp), v1 = __ldg(sp - M), v2 = __ldg(sp - 2 * M), v3 = __ldg(sp - 3 * M);
+        float2 v4 = __ldg(sp - 4 * M), v5 = __ldg(sp - 5 * M), v6 = __ldg(sp - 6 * M), v7 = __ldg(sp - 7 * M);
+        pair_mac(sh, sl, make_float2(w01.x, w01.y), v0);
+        pair_mac(sh, sl, make_float2(w01.z, w01.w), v1);
+        pair_mac(sh, sl, make_float2(w23.x, w23.y), v2);
+        pair_mac(sh, sl, make_float2(w23.z, w23.w), v3);
+        pair_mac(sh, sl, make_float2(w45.x, w45.y), v4);
+        pair_mac(sh, sl, make_float2(w45.z, w45.w), v5);
+        pair_mac(sh, sl, make_float2(w67.x, w67.y), v6);
+        pair_mac(sh, sl, make_float2(w67.z, w67.w), v7);
+        sp -= 8 * M;
+    }
+    for (; t < len; t += 2) {
+        float4 w = __ldg(wp + 32 * (t >> 1));
+        pair_mac(sh, sl, make_float2(w.x, w.y), __ldg(sp));
+        pair_mac(sh, sl, make_float2(w.z, w.w), __ldg(sp - M));
+        sp -= 2 * M;
+    }
+}
+
+// one warp per item, items handed out by an atomic counter (spring items, then receiver items
+// with m >= 1); the solve resets the counter after the step's local sums are done
+__global__ void __launch_bounds__(256, 4) k_local_items(DevPlan P) {
+    int64_t n = load_step(P);
+    int lane = threadIdx.x & 31;
+    int q = ring_slot(n + 1, P.ring);
+    unsigned long long total = (unsigned long long)(P.l_nitems + P.r_nitems);
+    for (;;) {
+        unsigned long long g = 0;
+        if (lane == 0) g = atomicAdd(P.item_ctr, 1ull);
+        g = __shfl_sync(0xffffffffu, g, 0);
+        if (g >= total) break;
+        float sh = 0.f, sl = 0.f;
+        if (g < (unsigned long long)P.l_nitems) {
+            int sj = __ldg(P.l_src + g * 32 + lane);
+            local_item((const float2*)P.sig2, P.M, P.ring, q, P.l_mfirst, P.l_s0[g], P.l_len[g],
+                       (const float4*)(P.l_w + 2 * P.l_wbase[g]) + lane, sj, sh, sl);
+            pair_warp_sum(sh, sl);
+            if (lane == 0) P.l_part[g] = (double)sh + (double)sl;
+        } else {
+            int64_t it = (int64_t)g - P.l_nitems;
+            int sj = __ldg(P.r_src + it * 32 + lane);
+            local_item((const float2*)P.sig2, P.M, P.ring, q, P.r_mfirst, P.r_s0[it], P.r_len[it],
+                       (const float4*)(P.r_w + 2 * P.r_wbase[it]) + lane, sj, sh, sl);
+            pair_warp_sum(sh, sl);
+            if (lane == 0) P.r_part[it] = (double)sh + (double)sl;
+        }
+    }
+}
+
+// receivers, after the solve: u = 1/2 (sum of the m >= 1 item partials + sum over sources closer
+// than dt of Q_0 sigma^{n+1}) + u_H; one warp per receiver.  The block that finishes last advances
+// the step counter (every other block has read n before it counts itself done).
+__global__ void __launch_bounds__(256) k_receivers(DevPlan P) {
+    int64_t n = load_step(P);
+    int lane = threadIdx.x & 31;
+    int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (r < P.R) {
+        double acc = 0.0;
+        for (int64_t it = P.r_item_ptr[r] + lane; it < P.r_item_ptr[r + 1]; it += 32) acc += P.r_part[it];
+        const double* s1 = P.sig + (int64_t)ring_slot(n + 1, P.ring) * P.M;
+        for (int64_t e = P.r0_ptr[r] + lane; e < P.r0_ptr[r + 1]; e += 32) acc = fma(P.r0_w[e], s1[P.r0_src[e]], acc);
+        acc = warp_sum(acc);
+        if (lane == 0) P.rec_hist[(n % P.chunk) * P.R + r] = 0.5 * acc + P.uHr[r];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        unsigned long long done = atomicAdd((unsigned long long*)&P.step[1], 1ull);
+        if (done == gridDim.x - 1) {
+            P.step[1] = 0;
+            __threadfence();
+            P.step[0] = n + 1;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// type-1 spreading as a sparse matrix, one thread per fine-grid point:
+//   G[i] = sum_e g_w[e] sigma^n_{g_src[e]}    (deterministic, no atomics)
 // ---------------------------------------------------------------------------------------------
 __global__ void k_spread(DevPlan P) {
     int64_t n = load_step(P);
-    int slot = ring_slot(n, P.ring);
+    const double* sg = P.sig + (int64_t)ring_slot(n, P.ring) * P.M;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.nf; i += gridDim.x * blockDim.x) {
-        double acc = 0.0;
-        for (int t = 0; t < P.w; t++) {
-            int c = i - t;
-            if (c < 0) c += P.nf;
-            int e1 = P.bin_ptr[c + 1];
-            for (int e = P.bin_ptr[c]; e < e1; e++) {
-                int j = P.bin_list[e];
-                acc = fma(P.sig[(int64_t)j * P.ring + slot], P.sp_ker[(int64_t)j * P.w + t], acc);
-            }
+        int e0 = P.g_ptr[i], e1 = P.g_ptr[i + 1];
+        double a0 = 0.0, a1 = 0.0;
+        int e = e0;
+        for (; e + 1 < e1; e += 2) {
+            a0 = fma(__ldg(P.g_w + e), sg[__ldg(P.g_src + e)], a0);
+            a1 = fma(__ldg(P.g_w + e + 1), sg[__ldg(P.g_src + e + 1)], a1);
         }
-        P.grid[i] = acc;
+        if (e < e1) a0 = fma(__ldg(P.g_w + e), sg[__ldg(P.g_src + e)], a0);
+        P.grid[i] = a0 + a1;
     }
 }
 
@@ -65,20 +200,18 @@ __global__ void k_spread(DevPlan P) {
 // Complex FFT of length L = L1 * L2 (powers of two), X[k] = sum_i z[i] e^{sign 2 pi i ik/L}:
 //   columns: for each i2, FFT over i1 of z[i2 + L2 i1], times e^{sign 2 pi i i2 k1/L} -> Y[k1 L2 + i2]
 //   rows:    for each k1, FFT over i2 of Y[k1 L2 + i2] -> X[k1 + L1 k2]
-// Each block transforms one line in shared memory: bit-reversed load, radix-2 DIT stages.
-// tw[j] = e^{+2 pi i j / L}.
+// Each block transforms one line in shared memory: bit-reversed load, radix-2 DIT stages with the
+// line's N/2 twiddles staged in shared memory.  tw[j] = e^{+2 pi i j / L}.
 // ---------------------------------------------------------------------------------------------
-__device__ void fft_line(double2* a, int N, int logN, const double2* tw, int L, int sign) {
+__device__ void fft_line(double2* a, const double2* twN, int N, int logN) {
     for (int s = 1; s <= logN; s++) {
         int half = 1 << (s - 1);
-        int step = L / (2 * half);
+        int step = N / (2 * half);
         for (int j = threadIdx.x; j < N / 2; j += blockDim.x) {
             int pos = j & (half - 1);
             int i0 = ((j >> (s - 1)) << s) + pos;
             int i1 = i0 + half;
-            double2 w = tw[pos * step];
-            if (sign < 0) w.y = -w.y;
-            double2 t = cmul(w, a[i1]);
+            double2 t = cmul(twN[pos * step], a[i1]);
             double2 u = a[i0];
             a[i0] = cadd(u, t);
             a[i1] = csub(u, t);
@@ -87,14 +220,25 @@ __device__ void fft_line(double2* a, int N, int logN, const double2* tw, int L, 
     }
 }
 
+__device__ __forceinline__ void stage_twiddles(double2* twN, const double2* tw, int L, int N, int sign) {
+    int stride = L / N;
+    for (int j = threadIdx.x; j < N / 2; j += blockDim.x) {
+        double2 w = tw[j * stride];
+        if (sign < 0) w.y = -w.y;
+        twN[j] = w;
+    }
+}
+
 __global__ void k_fft_cols(const double2* __restrict__ in, double2* __restrict__ out,
                            const double2* __restrict__ tw, int L, int L1, int L2, int logL1, int sign) {
     extern __shared__ double2 sm[];
+    double2* twN = sm + L1;
     int i2 = blockIdx.x;
+    stage_twiddles(twN, tw, L, L1, sign);
     for (int i1 = threadIdx.x; i1 < L1; i1 += blockDim.x)
         sm[__brev(i1) >> (32 - logL1)] = in[i2 + (int64_t)L2 * i1];
     __syncthreads();
-    fft_line(sm, L1, logL1, tw, L, sign);
+    fft_line(sm, twN, L1, logL1);
     for (int k1 = threadIdx.x; k1 < L1; k1 += blockDim.x) {
         int idx = (int)(((int64_t)i2 * k1) % L);
         double2 w = tw[idx];
@@ -106,38 +250,30 @@ __global__ void k_fft_cols(const double2* __restrict__ in, double2* __restrict__
 __global__ void k_fft_rows(const double2* __restrict__ in, double2* __restrict__ out,
                            const double2* __restrict__ tw, int L, int L1, int L2, int logL2, int sign) {
     extern __shared__ double2 sm[];
+    double2* twN = sm + L2;
     int k1 = blockIdx.x;
+    stage_twiddles(twN, tw, L, L2, sign);
     for (int i2 = threadIdx.x; i2 < L2; i2 += blockDim.x)
         sm[__brev(i2) >> (32 - logL2)] = in[(int64_t)k1 * L2 + i2];
     __syncthreads();
-    fft_line(sm, L2, logL2, tw, L, sign);
+    fft_line(sm, twN, L2, logL2);
     for (int k2 = threadIdx.x; k2 < L2; k2 += blockDim.x) out[k1 + (int64_t)L1 * k2] = sm[k2];
 }
 
 // ---------------------------------------------------------------------------------------------
-// Type-2 spectrum of mode k for the inverse real FFT: F'_k = deconv2_k alpha_k;
-// Zs[k] = F'_k (1 + i w^k), Zs[L-k] = conj(F'_k) (1 - i w^{L-k}), w = e^{-2 pi i / nf}.
-// (Entries with K < idx < L - K stay zero.)
+// Type-2 spectrum of mode k for the inverse real FFT (factors precomputed in modefac):
+//   Zs[k] = alpha_k deconv2_k (1 + i w^k),  Zs[L-k] = conj(alpha_k) deconv2_k (1 - i w^{L-k}),
+//   w = e^{-2 pi i / nf}; entries with K < idx < L - K stay zero.
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ void write_type2(const DevPlan& P, int k, double2 a, double2* Zs) {
-    double d2 = P.deconv2[k];
-    double2 F = make_double2(d2 * a.x, d2 * a.y);
-    double s, c;
-    sincospi(-2.0 * (double)k / (double)P.nf, &s, &c);          // w^k
-    double2 iw = make_double2(-s, c);                            // i w^k
-    Zs[k] = cadd(F, cmul(F, iw));
-    if (k > 0) {
-        int kk = P.L - k;
-        sincospi(-2.0 * (double)kk / (double)P.nf, &s, &c);
-        double2 iw2 = make_double2(-s, c);
-        double2 Fc = cconj(F);
-        Zs[kk] = csub(Fc, cmul(Fc, iw2));
-    }
+    const double* f = P.modefac + 8 * (int64_t)k;
+    Zs[k] = cmul(a, make_double2(f[3], f[4]));
+    if (k > 0) Zs[P.L - k] = cmul(cconj(a), make_double2(f[5], f[6]));
 }
 
 // ---------------------------------------------------------------------------------------------
 // Modes: four threads per mode k.
-//   S_k^n = deconv1_k F_k, F_k = E_k + e^{2 pi i k/nf} O_k from the half-length FFT Z
+//   S_k^n = deconv1_k E_k + deconv1_k e^{2 pi i k/nf} O_k from the half-length FFT Z
 //   (E = (Z_k + conj Z_{L-k})/2, O = (Z_k - conj Z_{L-k})/(2i)), stored in ring slot n mod W;
 //   h_k = sum_m dt p_k(m dt) S_k^{n-m}, g_k likewise (eq. hkcompdisc);
 //   alpha, alpha' rotated and driven (eq. alphakEvolutionFormulas); type-2 spectrum written.
@@ -151,26 +287,17 @@ __global__ void k_modes(DevPlan P) {
     const double2* Z = (const double2*)P.spec;
     double2 zk = Z[kk];
     double2 zm = Z[kk == 0 ? 0 : P.L - kk];
+    const double* f = P.modefac + 8 * (int64_t)kk;
     double2 E = make_double2(0.5 * (zk.x + zm.x), 0.5 * (zk.y - zm.y));
     double2 D = make_double2(0.5 * (zk.x - zm.x), 0.5 * (zk.y + zm.y));
     double2 O = make_double2(D.y, -D.x);
-    double s, c;
-    sincospi(2.0 * (double)kk / (double)P.nf, &s, &c);
-    double2 F = cadd(E, cmul(make_double2(c, s), O));
-    double d1 = P.deconv1[kk];
-    double2 Sn = make_double2(d1 * F.x, d1 * F.y);
+    double2 Sn = cadd(make_double2(f[0] * E.x, f[0] * E.y), cmul(make_double2(f[1], f[2]), O));
     int K1 = P.K + 1;
     double2* Sring = (double2*)P.Sring;
     const double2* pq = (const double2*)P.pq;
     double2 h = make_double2(0.0, 0.0), g = make_double2(0.0, 0.0);
     for (int m = q; m < P.W; m += 4) {
-        double2 Sm;
-        if (m == 0) {
-            Sm = Sn;
-        } else {
-            int slot = ring_slot(n - m, P.W);
-            Sm = Sring[(int64_t)slot * K1 + kk];
-        }
+        double2 Sm = (m == 0) ? Sn : Sring[(int64_t)ring_slot(n - m, P.W) * K1 + kk];
         double2 w = pq[(int64_t)m * K1 + kk];
         h.x = fma(w.x, Sm.x, h.x);
         h.y = fma(w.x, Sm.y, h.y);
@@ -196,29 +323,31 @@ __global__ void k_modes(DevPlan P) {
     write_type2(P, k, an, (double2*)P.spec2);
 }
 
-
 // ---------------------------------------------------------------------------------------------
 // Radiation projection (Sec. 4.4), applied to alpha^{n+1}, alpha'^{n+1} on projection steps.
 // The 2K-point grid values of the real field with modes |k| <= K-1 change only at the 4W points
 // next to x = +-pi, so the projected coefficients are
 //   alpha_k + (1/2K) sum_{i in I} du_i e^{+i k x_i},  alpha'_k + (1/2K) sum_{i in I} dv_i e^{+i k x_i}
 // with du = (phi_s - 1) u, dv = phi_s' u + (phi_s - 1) v (eq. vtilde), and alpha_K = 0.
-// x_i = i pi/K, so e^{i k x_i} = e^{i pi (k i mod 2K)/K} (exact argument reduction).
+// x_i = i pi/K, so e^{i k x_i} = tw2K[k i mod 2K] (exact argument reduction).
 // ---------------------------------------------------------------------------------------------
 __global__ void k_rbc_grid(DevPlan P) {
     int pt = blockIdx.x;                     // one block per rolled-off grid point
     int ig = P.rbc_idx[pt];
     const double2* al = (const double2*)P.alpha;
     const double2* alp = (const double2*)P.alpha_p;
-    double su = 0.0, sv = 0.0;
+    const double2* t2 = (const double2*)P.tw2K;
     int64_t twoK = 2 * (int64_t)P.K;
-    for (int k = 1 + threadIdx.x; k < P.K; k += blockDim.x) {
-        int64_t a = ((int64_t)k * ig) % twoK;
-        double s, c;
-        sincospi((double)a / (double)P.K, &s, &c);            // e^{+i k x}; use conj for e^{-ikx}
-        double2 e = make_double2(c, -s);
+    double su = 0.0, sv = 0.0;
+    int k = 1 + threadIdx.x;
+    int64_t a = ((int64_t)k * ig) % twoK;
+    int64_t inc = ((int64_t)blockDim.x * ig) % twoK;
+    for (; k < P.K; k += blockDim.x) {
+        double2 e = cconj(t2[a]);                     // e^{-i k x}
         su += cmul(al[k], e).x;
         sv += cmul(alp[k], e).x;
+        a += inc;
+        if (a >= twoK) a -= twoK;
     }
     __shared__ double red[2][32];
     su = warp_sum(su);
@@ -244,6 +373,7 @@ __global__ void k_rbc_update(DevPlan P, int npts) {
     if (k > P.K) return;
     double2* al = (double2*)P.alpha;
     double2* alp = (double2*)P.alpha_p;
+    const double2* t2 = (const double2*)P.tw2K;
     double2 a, ap;
     if (k == P.K) {
         a = make_double2(0.0, 0.0);
@@ -252,14 +382,12 @@ __global__ void k_rbc_update(DevPlan P, int npts) {
         double2 du = make_double2(0.0, 0.0), dv = make_double2(0.0, 0.0);
         int64_t twoK = 2 * (int64_t)P.K;
         for (int pt = 0; pt < npts; pt++) {
-            int64_t ang = ((int64_t)k * P.rbc_idx[pt]) % twoK;
-            double s, c;
-            sincospi((double)ang / (double)P.K, &s, &c);
+            double2 e = t2[((int64_t)k * P.rbc_idx[pt]) % twoK];
             double xu = P.rbc_uv[4 * pt + 2], xv = P.rbc_uv[4 * pt + 3];
-            du.x = fma(xu, c, du.x);
-            du.y = fma(xu, s, du.y);
-            dv.x = fma(xv, c, dv.x);
-            dv.y = fma(xv, s, dv.y);
+            du.x = fma(xu, e.x, du.x);
+            du.y = fma(xu, e.y, du.y);
+            dv.x = fma(xv, e.x, dv.x);
+            dv.y = fma(xv, e.y, dv.y);
         }
         double inv = 1.0 / (double)twoK;
         a = al[k];
@@ -272,9 +400,11 @@ __global__ void k_rbc_update(DevPlan P, int npts) {
     write_type2(P, k, a, (double2*)P.spec2);
 }
 
+__device__ double incident(const DevPlan& P, double s);
+
 // ---------------------------------------------------------------------------------------------
 // type-2 interpolation: u_H(x_t) = sum_{t'} G'[(i0 + t') mod nf] psi_{t,t'} for springs, then
-// receivers.
+// receivers; for springs also the forcing and u_H part of the right-hand side of eq. linearSystem.
 // ---------------------------------------------------------------------------------------------
 __global__ void k_interp(DevPlan P) {
     int64_t total = P.M + P.R;
@@ -290,133 +420,114 @@ __global__ void k_interp(DevPlan P) {
             acc = fma(P.grid[i], ker[tt], acc);
             i = (i + 1 == P.nf) ? 0 : i + 1;
         }
-        if (spring) P.uH[j] = acc;
-        else P.uHr[j] = acc;
-    }
-}
-
-// ---------------------------------------------------------------------------------------------
-// local explicit sum (Sec. 4.1, eq. periodicIE_disc, m >= 1): one warp per target spring
-//   c_j = sum_{l in N_delta(x_j)} sum_{m} Q_m(d_jl) sigma_l^{n+1-m}
-// ---------------------------------------------------------------------------------------------
-__global__ void k_local(DevPlan P) {
-    int64_t n = load_step(P);
-    int lane = threadIdx.x & 31;
-    int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (j >= P.M) return;
-    double acc = 0.0;
-    int64_t e1 = P.row_ptr[j + 1];
-    for (int64_t e = P.row_ptr[j] + lane; e < e1; e += 32) {
-        int l = P.src[e];
-        int mr = P.mrange[e];
-        int mlo = mr & 0xffff, cnt = mr >> 16;
-        const double* wq = P.wq + P.woff[e];
-        const double* sl = P.sig + (int64_t)l * P.ring;
-        int slot = ring_slot(n + 1 - mlo, P.ring);
-        for (int c = 0; c < cnt; c++) {
-            acc = fma(wq[c], sl[slot], acc);
-            slot = (slot == 0) ? P.ring - 1 : slot - 1;
+        if (spring) {
+            P.uH[j] = acc;
+            double bj = P.beta[j];
+            double g = P.g_ext ? P.g_ext[j] : bj * incident(P, P.x[j] - (double)(load_step(P) + 1) * P.dt);
+            P.rhs[j] = -g - bj * acc;
+        } else {
+            P.uHr[j] = acc;
         }
     }
-    acc = warp_sum(acc);
-    if (lane == 0) P.clocal[j] = acc;
 }
 
-// incident forcing g_j(t) = beta_j f(x_j - t), f periodised over 2 pi in the periodic box (eq. gj)
+// incident forcing g_j(t) = beta_j f(x_j - t), f periodised over 2 pi in the periodic box (eq. gj).
+// pulse[3i..3i+2] = amp, centre, 1/width.  Gaussian terms beyond 12 widths (below e^-72 of the
+// amplitude) are skipped.
 __device__ double incident(const DevPlan& P, double s) {
     double f = 0.0;
     const double kTwoPi = 6.283185307179586476925286766559;
+    const double kInvTwoPi = 0.15915494309189533576888376337251;
     for (int i = 0; i < P.npulse; i++) {
-        double amp = P.pulse[3 * i], cen = P.pulse[3 * i + 1], wid = P.pulse[3 * i + 2];
+        double amp = P.pulse[3 * i], cen = P.pulse[3 * i + 1], iw = P.pulse[3 * i + 2];
         if (P.bc == WAVE1D_FREE) {
-            double z = (s - cen) / wid;
-            if (fabs(z) <= 40.0) f += amp * exp(-0.5 * z * z);
+            double z = (s - cen) * iw;
+            if (fabs(z) <= 12.0) f += amp * exp(-0.5 * z * z);
         } else {
-            double span = 40.0 * wid;
-            int64_t m0 = (int64_t)floor((cen - s - span) / kTwoPi);
-            int64_t m1 = (int64_t)ceil((cen - s + span) / kTwoPi);
+            double span = 12.0 / iw;
+            int64_t m0 = (int64_t)floor((cen - s - span) * kInvTwoPi);
+            int64_t m1 = (int64_t)ceil((cen - s + span) * kInvTwoPi);
             for (int64_t m = m0; m <= m1; m++) {
-                double z = (s + kTwoPi * (double)m - cen) / wid;
-                if (fabs(z) <= 40.0) f += amp * exp(-0.5 * z * z);
+                double z = (s + kTwoPi * (double)m - cen) * iw;
+                if (fabs(z) <= 12.0) f += amp * exp(-0.5 * z * z);
             }
         }
     }
     return f;
 }
 
-// right-hand side of eq. linearSystem: rhs_j = -g_j - (beta_j/2) c_j - beta_j u_H(x_j)
-__global__ void k_rhs(DevPlan P) {
-    int64_t n = load_step(P);
-    double t1 = (double)(n + 1) * P.dt;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < P.M;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        double bj = P.beta[j];
-        double g = P.g_ext ? P.g_ext[j] : bj * incident(P, P.x[j] - t1);
-        P.rhs[j] = -g - 0.5 * bj * P.clocal[j] - bj * P.uH[j];
-    }
+// right-hand side of eq. linearSystem, rhs_j = -g_j - (beta_j/2) c_j - beta_j u_H(x_j): the part
+// without the local sum is formed by k_interp (one thread per spring); the solve adds the local sum
+// c_j, assembled from the partials of the row's items (and kept for inspection)
+__device__ __forceinline__ double rhs_of(const DevPlan& P, int j) {
+    double c = 0.0;
+    for (int64_t it = P.l_item_ptr[j]; it < P.l_item_ptr[j + 1]; it++) c += P.l_part[it];
+    P.clocal[j] = c;
+    return fma(-0.5 * P.beta[j], c, P.rhs[j]);
 }
 
-// block solve sigma^{n+1} = (I + S)^{-1} rhs, one warp per block of springs closer than dt
-__global__ void k_solve(DevPlan P) {
+__device__ __forceinline__ void store_sigma(const DevPlan& P, int64_t n, int j, double v) {
+    int slot = ring_slot(n + 1, P.ring);
+    P.sig[(int64_t)slot * P.M + j] = v;
+    float hi = (float)v;
+    float lo = (float)(v - (double)hi);
+    float2 pr = make_float2(hi, lo);
+    ((float2*)P.sig2)[(int64_t)slot * P.M + j] = pr;
+    ((float2*)P.sig2)[(int64_t)(slot + P.ring) * P.M + j] = pr;
+    if (!isfinite(v)) atomicExch(P.status, (int)WAVE1D_ENONFINITE);
+    if (P.sig_hist) P.sig_hist[(n % P.chunk) * P.M + P.perm[j]] = v;
+}
+
+// block solve sigma^{n+1} = (I + S)^{-1} rhs, one warp per block of springs closer than dt.
+// The inverse is stored column-major (invT[l * s + i] = inv[i][l]) so lanes read it contiguously;
+// blocks of up to kSolveStage members stage their right-hand sides in the warp's shared memory.
+constexpr int kSolveStage = 256;
+
+__global__ void __launch_bounds__(256) k_solve(DevPlan P) {
+    __shared__ double srhs[8][kSolveStage];
     int64_t n = load_step(P);
-    int lane = threadIdx.x & 31;
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (blockIdx.x == 0 && threadIdx.x == 0) *P.item_ctr = 0ull;   // the step's local sums are done
     if (b >= P.nblocks) return;
     int64_t m0 = P.blk_ptr[b];
     int s = (int)(P.blk_ptr[b + 1] - m0);
-    const double* inv = P.inv + P.blk_inv_off[b];
-    int slot = ring_slot(n + 1, P.ring);
-    for (int i = lane; i < s; i += 32) {
-        double acc = 0.0;
-        for (int l = 0; l < s; l++) acc = fma(inv[(int64_t)i * s + l], P.rhs[P.blk_members[m0 + l]], acc);
-        int j = P.blk_members[m0 + i];
-        P.sig[(int64_t)j * P.ring + slot] = acc;
-        if (!isfinite(acc)) atomicExch(P.status, (int)WAVE1D_ENONFINITE);
-        if (P.sig_hist) P.sig_hist[(n % P.chunk) * P.M + P.perm[j]] = acc;
-    }
-}
-
-// receivers: u = 1/2 sum_l sum_{m>=0} Q_m sigma_l^{n+1-m} + u_H(x_r); the block that finishes last
-// advances the step counter (every other block has read n before it counts itself done).
-__global__ void k_receivers(DevPlan P) {
-    int64_t n = load_step(P);
-    int lane = threadIdx.x & 31;
-    int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (r < P.R) {
-        double acc = 0.0;
-        int64_t e1 = P.rrow_ptr[r + 1];
-        for (int64_t e = P.rrow_ptr[r] + lane; e < e1; e += 32) {
-            int l = P.rsrc[e];
-            int mr = P.rmrange[e];
-            int mlo = mr & 0xffff, cnt = mr >> 16;
-            const double* wq = P.rwq + P.rwoff[e];
-            const double* sl = P.sig + (int64_t)l * P.ring;
-            int slot = ring_slot(n + 1 - mlo, P.ring);
-            for (int c = 0; c < cnt; c++) {
-                acc = fma(wq[c], sl[slot], acc);
-                slot = (slot == 0) ? P.ring - 1 : slot - 1;
+    const double* invT = P.inv + P.blk_inv_off[b];
+    if (s <= kSolveStage) {
+        double* r = srhs[wid];
+        for (int i = lane; i < s; i += 32) r[i] = rhs_of(P, P.blk_members[m0 + i]);
+        __syncwarp();
+        for (int i = lane; i < s; i += 32) {
+            double a0 = 0.0, a1 = 0.0;
+            int l = 0;
+            for (; l + 1 < s; l += 2) {
+                a0 = fma(invT[(int64_t)l * s + i], r[l], a0);
+                a1 = fma(invT[(int64_t)(l + 1) * s + i], r[l + 1], a1);
             }
+            if (l < s) a0 = fma(invT[(int64_t)l * s + i], r[l], a0);
+            store_sigma(P, n, P.blk_members[m0 + i], a0 + a1);
         }
-        acc = warp_sum(acc);
-        if (lane == 0) P.rec_hist[(n % P.chunk) * P.R + r] = 0.5 * acc + P.uHr[r];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        unsigned long long done = atomicAdd((unsigned long long*)&P.step[1], 1ull);
-        if (done == gridDim.x - 1) {
-            P.step[1] = 0;
-            __threadfence();
-            P.step[0] = n + 1;
+    } else {
+        // large blocks: the full right-hand side is formed in place in P.rhs first
+        for (int i = lane; i < s; i += 32) {
+            int j = P.blk_members[m0 + i];
+            P.rhs[j] = rhs_of(P, j);
+        }
+        __syncwarp();
+        for (int i = lane; i < s; i += 32) {
+            double acc = 0.0;
+            for (int l = 0; l < s; l++)
+                acc = fma(invT[(int64_t)l * s + i], P.rhs[P.blk_members[m0 + l]], acc);
+            store_sigma(P, n, P.blk_members[m0 + i], acc);
         }
     }
 }
 
 // caller-order gathers and scatters
 __global__ void k_sigma_to_caller(DevPlan P, int64_t q, double* out) {
-    int slot = ring_slot(q, P.ring);
+    const double* sg = P.sig + (int64_t)ring_slot(q, P.ring) * P.M;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < P.M; j += (int64_t)gridDim.x * blockDim.x)
-        out[P.perm[j]] = P.sig[j * P.ring + slot];
+        out[P.perm[j]] = sg[j];
 }
 
 __global__ void k_internal_to_caller(const int32_t* perm, int64_t M, const double* in, double* out) {

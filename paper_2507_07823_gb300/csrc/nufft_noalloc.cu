@@ -154,9 +154,10 @@ extern "C" int wave1d_nufft1_noalloc(const double* x, const double* c, int64_t M
     }
     int t1 = L1 / 2 < 32 ? 32 : (L1 / 2 > 512 ? 512 : L1 / 2);
     int t2 = L2 / 2 < 32 ? 32 : (L2 / 2 > 512 ? 512 : L2 / 2);
-    wave1d::k_fft_cols<<<L2, t1, L1 * sizeof(double2), s>>>((const double2*)grid, work, tw, L, L1, L2,
-                                                            ilog2i(L1), +1);
-    wave1d::k_fft_rows<<<L1, t2, L2 * sizeof(double2), s>>>(work, spec, tw, L, L1, L2, ilog2i(L2), +1);
+    wave1d::k_fft_cols<<<L2, t1, wave1d::fft_smem_bytes(L1), s>>>((const double2*)grid, work, tw, L, L1,
+                                                                  L2, ilog2i(L1), +1);
+    wave1d::k_fft_rows<<<L1, t2, wave1d::fft_smem_bytes(L2), s>>>(work, spec, tw, L, L1, L2, ilog2i(L2),
+                                                                  +1);
     k_na_post<<<(unsigned)((K + 1 + 127) / 128), 128, 0, s>>>(spec, S, K, L, (int)nf, w, beta, h);
     return cudaGetLastError() == cudaSuccess ? WAVE1D_OK : WAVE1D_ECUDA;
 }

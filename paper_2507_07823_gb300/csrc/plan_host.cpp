@@ -502,6 +502,29 @@ int build_host_plan(const double* x_in, const double* beta_in, int64_t M, int bc
             hp.twiddle[2 * j] = std::cos(a);
             hp.twiddle[2 * j + 1] = std::sin(a);
         }
+        // per-mode factors of the real-FFT post/pre-processing folded with the deconvolution
+        hp.modefac.assign((size_t)K1 * 8, 0.0);
+        for (int k = 0; k < K1; k++) {
+            double a1 = 2.0 * kPi * (double)k / (double)P.nf;          // e^{+i a1} = w^k
+            double a2 = 2.0 * kPi * (double)(P.L - k) / (double)P.nf;  // e^{-i a2} = w'^{L-k}
+            double d1 = hp.deconv1[k], d2 = hp.deconv2[k];
+            double* f = &hp.modefac[(size_t)k * 8];
+            f[0] = d1;
+            f[1] = d1 * std::cos(a1);
+            f[2] = d1 * std::sin(a1);
+            // 1 + i e^{-i a1} = (1 + sin a1) + i cos a1
+            f[3] = d2 * (1.0 + std::sin(a1));
+            f[4] = d2 * std::cos(a1);
+            // 1 - i e^{-i a2} = (1 - sin a2) - i cos a2
+            f[5] = d2 * (1.0 - std::sin(a2));
+            f[6] = -d2 * std::cos(a2);
+        }
+        hp.tw2K.assign((size_t)4 * P.K, 0.0);
+        for (int a = 0; a < 2 * P.K; a++) {
+            double ang = kPi * (double)a / (double)P.K;
+            hp.tw2K[2 * a] = std::cos(ang);
+            hp.tw2K[2 * a + 1] = std::sin(ang);
+        }
     }
 
     // spreading weights and bins by first grid index
@@ -514,11 +537,31 @@ int build_host_plan(const double* x_in, const double* beta_in, int64_t M, int bc
         std::vector<int32_t> fill(hp.bin_ptr.begin(), hp.bin_ptr.end() - 1);
         for (int64_t j = 0; j < M; j++) hp.bin_list[fill[hp.sp_i0[j]]++] = (int32_t)j;
     }
+    // spreading as a grid-row sparse matrix: G[i] = sum_e g_w[e] sigma_{g_src[e]}
+    {
+        int w = P.nufft_w;
+        hp.g_ptr.assign(P.nf + 1, 0);
+        for (int64_t j = 0; j < M; j++)
+            for (int t = 0; t < w; t++) hp.g_ptr[(hp.sp_i0[j] + t) % P.nf + 1]++;
+        for (int i = 0; i < P.nf; i++) hp.g_ptr[i + 1] += hp.g_ptr[i];
+        hp.g_src.assign((size_t)M * w, 0);
+        hp.g_w.assign((size_t)M * w, 0.0);
+        std::vector<int32_t> fill(hp.g_ptr.begin(), hp.g_ptr.end() - 1);
+        for (int64_t j = 0; j < M; j++)
+            for (int t = 0; t < w; t++) {
+                int i = (hp.sp_i0[j] + t) % P.nf;
+                hp.g_src[fill[i]] = (int32_t)j;
+                hp.g_w[fill[i]] = hp.sp_ker[j * w + t];
+                fill[i]++;
+            }
+    }
 
     // local part (Sec. 4.1) and nearby blocks (eq. linearSystem)
     std::vector<std::vector<std::pair<int32_t, double>>> nearby;
     int rc = build_local(P, win, hp.x, hp.x, false, hp.loc, &nearby, max_local_bytes, err);
     if (rc) return rc;
+    if ((rc = build_rows(hp.loc, 1, hp.lrows, err))) return rc;
+    build_items(hp.lrows, hp.litems);
     {
         std::vector<int32_t> parent(M);
         std::iota(parent.begin(), parent.end(), 0);
@@ -578,7 +621,12 @@ int build_host_plan(const double* x_in, const double* beta_in, int64_t M, int bc
                         A[i * s + local_of[pr.first]] += 0.5 * hp.beta[j] * Q[0];
                     }
                 }
-                if (!invert((int)s, A, &hp.inv[hp.blk_inv_off[b]])) bad = 1;
+                std::vector<double> inv_rm(s * s);
+                if (!invert((int)s, A, inv_rm.data())) bad = 1;
+                // stored column-major: inv[l * s + i] = (I + S)^{-1}[i][l]
+                double* dst = &hp.inv[hp.blk_inv_off[b]];
+                for (int64_t i = 0; i < s; i++)
+                    for (int64_t l = 0; l < s; l++) dst[l * s + i] = inv_rm[i * s + l];
             }
         });
         if (bad) { err = "singular block of I + S"; return WAVE1D_EINVAL; }
@@ -609,6 +657,144 @@ int build_host_plan(const double* x_in, const double* beta_in, int64_t M, int bc
     return WAVE1D_OK;
 }
 
+// Regroup CSR local weights into m-major rows (see LocalRows).  Within a row the sources are
+// sorted by (m_lo, source); for each m the active sources are those with m_lo <= m, a prefix.
+// Entries with m above a source's last weight are stored as zeros.
+int build_rows(const LocalCSR& csr, int m_first, LocalRows& rows, std::string& err) {
+    int64_t T = (int64_t)csr.row_ptr.size() - 1;
+    int m_top = m_first;
+    for (size_t q = 0; q < csr.mrange.size(); q++) {
+        int lo = csr.mrange[q] & 0xffff, cnt = csr.mrange[q] >> 16;
+        if (cnt > 0) m_top = std::max(m_top, lo + cnt - 1);
+    }
+    rows.m_first = m_first;
+    rows.nm = m_top - m_first + 1;
+    rows.src_off.assign(T + 1, 0);
+    rows.w_off.assign(T + 1, 0);
+    rows.cnt.assign((size_t)T * rows.nm, 0);
+    rows.src.assign(csr.src.size(), 0);
+    std::vector<int64_t> nw(T, 0);
+    std::vector<std::vector<int64_t>> order(T);
+    parallel_for(T, [&](int64_t a, int64_t b) {
+        for (int64_t j = a; j < b; j++) {
+            int64_t p0 = csr.row_ptr[j], p1 = csr.row_ptr[j + 1];
+            auto& ord = order[j];
+            ord.resize(p1 - p0);
+            for (int64_t q = p0; q < p1; q++) ord[q - p0] = q;
+            std::sort(ord.begin(), ord.end(), [&](int64_t u, int64_t v) {
+                int lu = csr.mrange[u] & 0xffff, lv = csr.mrange[v] & 0xffff;
+                return lu < lv || (lu == lv && csr.src[u] < csr.src[v]);
+            });
+            int64_t total = 0;
+            for (int i = 0; i < rows.nm; i++) {
+                int m = m_first + i;
+                int64_t c = 0;
+                for (int64_t q : ord) {
+                    int lo = csr.mrange[q] & 0xffff, cnt = csr.mrange[q] >> 16;
+                    if (cnt > 0 && lo <= m) c++;
+                }
+                if (c > 65535) c = -1;
+                rows.cnt[(size_t)j * rows.nm + i] = (uint16_t)(c < 0 ? 0 : c);
+                total += c;
+            }
+            nw[j] = total;
+        }
+    });
+    for (int64_t j = 0; j < T; j++) {
+        rows.src_off[j + 1] = rows.src_off[j] + (csr.row_ptr[j + 1] - csr.row_ptr[j]);
+        rows.w_off[j + 1] = rows.w_off[j] + nw[j];
+        if (csr.row_ptr[j + 1] - csr.row_ptr[j] > 65535) {
+            err = "more than 65535 local neighbours of one target";
+            return WAVE1D_EUNSUPPORTED;
+        }
+    }
+    rows.w.assign(2 * (size_t)rows.w_off[T], 0.0f);
+    parallel_for(T, [&](int64_t a, int64_t b) {
+        for (int64_t j = a; j < b; j++) {
+            const auto& ord = order[j];
+            for (size_t r = 0; r < ord.size(); r++) rows.src[rows.src_off[j] + r] = csr.src[ord[r]];
+            int64_t off = rows.w_off[j];
+            for (int i = 0; i < rows.nm; i++) {
+                int m = m_first + i;
+                int c = rows.cnt[(size_t)j * rows.nm + i];
+                for (int r = 0; r < c; r++) {
+                    int64_t q = ord[r];
+                    int lo = csr.mrange[q] & 0xffff, cnt = csr.mrange[q] >> 16;
+                    double v = (m >= lo && m < lo + cnt) ? csr.w[csr.woff[q] + (m - lo)] : 0.0;
+                    float hi = (float)v;
+                    float lo_part = (float)(v - (double)hi);
+                    rows.w[2 * (off + r)] = hi;
+                    rows.w[2 * (off + r) + 1] = lo_part;
+                }
+                off += c;
+            }
+        }
+    });
+    return WAVE1D_OK;
+}
+
+// Cut m-major rows into chunk items (see LocalItems).  Rank r of a row is active in slice i iff
+// cnt[i] > r; cnt is non-decreasing in i, so rank r is active from first(r) on.  Elements are
+// stored in pairs: elements 2u and 2u+1 of lane l sit at w[wbase + 64 u + 2 l + {0, 1}] (one
+// 16-byte load per lane fetches both); len is rounded up to even with zero weights.
+int build_items(const LocalRows& rows, LocalItems& it) {
+    int64_t T = (int64_t)rows.src_off.size() - 1;
+    int nm = rows.nm;
+    it.m_first = rows.m_first;
+    it.item_ptr.assign(T + 1, 0);
+    for (int64_t j = 0; j < T; j++) {
+        int64_t ns = rows.src_off[j + 1] - rows.src_off[j];
+        it.item_ptr[j + 1] = it.item_ptr[j] + (ns + 31) / 32;
+    }
+    int64_t NI = it.item_ptr[T];
+    it.row.assign(NI, 0);
+    it.s0.assign(NI, 0);
+    it.len.assign(NI, 0);
+    it.wbase.assign(NI + 1, 0);
+    it.src.assign(NI * 32, 0);
+    for (int64_t j = 0; j < T; j++) {
+        const uint16_t* cnt = &rows.cnt[(size_t)j * nm];
+        for (int64_t c = it.item_ptr[j]; c < it.item_ptr[j + 1]; c++) {
+            int r0 = (int)(32 * (c - it.item_ptr[j]));
+            int first = nm;
+            for (int i = 0; i < nm; i++)
+                if (cnt[i] > r0) { first = i; break; }
+            int len = nm - first;
+            len += len & 1;
+            it.row[c] = (int32_t)j;
+            it.s0[c] = first;
+            it.len[c] = len;
+            it.wbase[c + 1] = it.wbase[c] + 32 * (int64_t)len;
+        }
+    }
+    it.w.assign(2 * (size_t)it.wbase[NI], 0.0f);
+    parallel_for(T, [&](int64_t a, int64_t b) {
+        for (int64_t j = a; j < b; j++) {
+            const uint16_t* cnt = &rows.cnt[(size_t)j * nm];
+            int64_t ns = rows.src_off[j + 1] - rows.src_off[j];
+            std::vector<int64_t> off(nm + 1, 0);
+            for (int i = 0; i < nm; i++) off[i + 1] = off[i] + cnt[i];
+            for (int64_t c = it.item_ptr[j]; c < it.item_ptr[j + 1]; c++) {
+                int r0 = (int)(32 * (c - it.item_ptr[j]));
+                for (int l = 0; l < 32; l++) {
+                    int r = r0 + l;
+                    if (r < ns) it.src[c * 32 + l] = rows.src[rows.src_off[j] + r];
+                    for (int t = 0; t < it.len[c]; t++) {
+                        int i = it.s0[c] + t;
+                        if (i < nm && r < ns && cnt[i] > r) {
+                            int64_t from = 2 * (rows.w_off[j] + off[i] + r);
+                            int64_t to = 2 * (it.wbase[c] + 64 * (int64_t)(t >> 1) + 2 * l + (t & 1));
+                            it.w[to] = rows.w[from];
+                            it.w[to + 1] = rows.w[from + 1];
+                        }
+                    }
+                }
+            }
+        }
+    });
+    return WAVE1D_OK;
+}
+
 int build_receivers(HostPlan& hp, const double* xr, int64_t R, std::string& err) {
     const Params& P = hp.P;
     hp.P.R = R;
@@ -631,6 +817,23 @@ int build_receivers(HostPlan& hp, const double* xr, int64_t R, std::string& err)
     Window win(P.delta, P.b);
     int rc = build_local(P, win, hp.xr, hp.x, true, hp.rloc, nullptr, INT64_MAX, err);
     if (rc) return rc;
+    // m >= 1 terms go to the item layout (summed concurrently with the history part); the m = 0
+    // terms of sources closer than dt need sigma^{n+1} and are kept as a short list
+    if ((rc = build_rows(hp.rloc, 1, hp.rrows, err))) return rc;
+    build_items(hp.rrows, hp.ritems);
+    hp.r0_ptr.assign(R + 1, 0);
+    hp.r0_src.clear();
+    hp.r0_w.clear();
+    for (int64_t r = 0; r < R; r++) {
+        for (int64_t q = hp.rloc.row_ptr[r]; q < hp.rloc.row_ptr[r + 1]; q++) {
+            int lo = hp.rloc.mrange[q] & 0xffff, cnt = hp.rloc.mrange[q] >> 16;
+            if (lo == 0 && cnt > 0) {
+                hp.r0_src.push_back(hp.rloc.src[q]);
+                hp.r0_w.push_back(hp.rloc.w[hp.rloc.woff[q]]);
+            }
+        }
+        hp.r0_ptr[r + 1] = (int64_t)hp.r0_src.size();
+    }
     spread_weights(P, hp.xr, hp.rc_i0, hp.rc_ker);
     return WAVE1D_OK;
 }

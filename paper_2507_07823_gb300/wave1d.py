@@ -63,7 +63,8 @@ class wave1d_info(ctypes.Structure):
                 ("delta", ctypes.c_double),
                 ("local_pairs", ctypes.c_int64), ("local_weights", ctypes.c_int64),
                 ("nearby_pairs", ctypes.c_int64), ("blocks", ctypes.c_int64),
-                ("max_block", ctypes.c_int64), ("device_bytes", ctypes.c_int64)]
+                ("max_block", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+                ("local_bytes", ctypes.c_int64)]
 
 
 _lib = None
