@@ -171,11 +171,12 @@ int wave1d_inspect(wave1d_plan_t plan, int array, double* host_out, int64_t coun
  */
 enum wave1d_stage {
     WAVE1D_STAGE_LOCAL = 0,      /* local explicit sum (Sec. 4.1)                     */
-    WAVE1D_STAGE_SPREAD = 1,     /* type-1 spreading                                  */
-    WAVE1D_STAGE_FFT_FWD = 2,    /* forward FFT                                       */
-    WAVE1D_STAGE_MODES = 3,      /* S_k, driving terms, rotation (Sec. 3)             */
+    WAVE1D_STAGE_SPREAD = 1,     /* type-1 spreading and the forward FFT's first pass */
+    WAVE1D_STAGE_FFT_FWD = 2,    /* (merged into the neighbouring stages: zero)       */
+    WAVE1D_STAGE_MODES = 3,      /* forward FFT rows, S_k, driving terms, rotation
+                                    (Sec. 3), inverse FFT rows                        */
     WAVE1D_STAGE_RBC = 4,        /* radiation projection (Sec. 4.4), projection steps */
-    WAVE1D_STAGE_FFT_INV = 5,    /* inverse FFT                                       */
+    WAVE1D_STAGE_FFT_INV = 5,    /* inverse FFT's last pass                           */
     WAVE1D_STAGE_INTERP = 6,     /* type-2 interpolation                              */
     WAVE1D_STAGE_SOLVE = 7,      /* forcing, right-hand side, block solve             */
     WAVE1D_STAGE_RECEIVERS = 8,  /* receiver readout                                  */

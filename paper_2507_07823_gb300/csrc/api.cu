@@ -18,16 +18,16 @@
 #include "../../include/wave1d.h"
 
 namespace wave1d {
-__global__ void k_spread(DevPlan P);
+__global__ void k_hist_cols(DevPlan P, double2* Y);
+__global__ void k_hist_rows(DevPlan P, const double2* Y, double2* T, int do_inverse);
+__global__ void k_hist_icols(DevPlan P, const double2* T);
 __global__ void k_fft_cols(const double2*, double2*, const double2*, int, int, int, int, int);
 __global__ void k_fft_rows(const double2*, double2*, const double2*, int, int, int, int, int);
-__global__ void k_modes(DevPlan P);
 __global__ void k_rbc_grid(DevPlan P);
 __global__ void k_rbc_update(DevPlan P, int npts);
 __global__ void k_interp(DevPlan P);
 __global__ void k_local_items(DevPlan P);
 __global__ void k_solve(DevPlan P);
-__global__ void k_receivers(DevPlan P);
 __global__ void k_sigma_to_caller(DevPlan P, int64_t q, double* out);
 __global__ void k_internal_to_caller(const int32_t* perm, int64_t M, const double* in, double* out);
 __global__ void k_caller_to_internal(const int32_t* perm, int64_t M, const double* in, double* out);
@@ -202,12 +202,13 @@ int upload_receivers(wave1d_plan_t p) {
     return WAVE1D_OK;
 }
 
-// items kernel: as many 8-warp blocks as are resident at once; warps fetch items dynamically
+// items kernel: as many 8-warp blocks as are resident at once (four per SM); warps fetch items
+// dynamically
 unsigned local_grid(const wave1d_plan_t p) {
     const DevPlan& d = p->dp;
     int64_t items = d.l_nitems + d.r_nitems;
     int64_t want = (items + 7) / 8;
-    int64_t cap = (int64_t)p->sms * 4;           // blocks resident at once (launch bounds 256, 4)
+    int64_t cap = (int64_t)p->sms * 4;
     return (unsigned)std::max<int64_t>(1, std::min(want, cap));
 }
 
@@ -229,9 +230,11 @@ int enqueue_step(wave1d_plan_t p, int64_t n, const double* g_ext, double* sig_hi
     auto mark = [&](int i) {
         if (ev) cudaEventRecord(ev[i], s);
     };
-    // the local sum needs only sigma^{<= n}: without profiling it runs on the side stream,
-    // concurrently with the history pipeline, and is joined before the solve
-    bool fork = (ev == nullptr);
+    // The local sum needs only sigma^{<= n} and could overlap the history pipeline on the side
+    // stream, but on GB300 the two slow each other down (the latency-bound history kernels wait
+    // longer on an HBM the local sum keeps busy): measured 169 us per step concurrently against
+    // 143 us back to back at M = 1e4, so they run back to back.
+    bool fork = false;
     mark(WAVE1D_STAGE_LOCAL);
     if (fork) {
         cudaEventRecord(p->ev_fork, s);
@@ -241,33 +244,41 @@ int enqueue_step(wave1d_plan_t p, int64_t n, const double* g_ext, double* sig_hi
     } else {
         k_local_items<<<local_grid(p), T, 0, s>>>(d);
     }
-    mark(WAVE1D_STAGE_SPREAD);
-    k_spread<<<blocks(P.nf, T), T, 0, s>>>(d);
-    mark(WAVE1D_STAGE_FFT_FWD);
-    int l1 = ilog2(P.L1), l2 = ilog2(P.L2);
-    int t1 = std::max(32, std::min(P.L1 / 2, 512)), t2 = std::max(32, std::min(P.L2 / 2, 512));
-    size_t sm1 = fft_smem_bytes(P.L1), sm2 = fft_smem_bytes(P.L2);
+    // history pipeline: spreading + forward columns | forward rows + modes (+ inverse rows) |
+    // [projection] | inverse columns
+    bool rbc = is_rbc_step(p, n);
+    double2* Y = (double2*)d.work;
+    double2* Tb = (double2*)d.spec;
     const double2* tw = (const double2*)d.twiddle;
-    k_fft_cols<<<P.L2, t1, sm1, s>>>((const double2*)d.grid, (double2*)d.work, tw, P.L, P.L1, P.L2, l1, +1);
-    k_fft_rows<<<P.L1, t2, sm2, s>>>((const double2*)d.work, (double2*)d.spec, tw, P.L, P.L1, P.L2, l2, +1);
+    int l1 = ilog2(P.L1), l2 = ilog2(P.L2);
+    unsigned tc = (unsigned)std::max(32, std::min(P.L1, 1024));
+    mark(WAVE1D_STAGE_SPREAD);
+    k_hist_cols<<<P.L2, hist_cols_threads(P.L1), hist_cols_smem_bytes(P.L1), s>>>(d, Y);
+    mark(WAVE1D_STAGE_FFT_FWD);
     mark(WAVE1D_STAGE_MODES);
-    k_modes<<<blocks(4 * (int64_t)(P.K + 1), T), T, 0, s>>>(d);
+    k_hist_rows<<<P.L1 / 2 + 1, T, (size_t)(2 * P.L2 + P.L2 / 2) * sizeof(double2), s>>>(d, Y, Tb, rbc ? 0 : 1);
     mark(WAVE1D_STAGE_RBC);
-    if (is_rbc_step(p, n)) {
+    if (rbc) {
         int npts = (int)p->hp.rbc_idx.size();
         k_rbc_grid<<<npts, T, 0, s>>>(d);
         k_rbc_update<<<blocks(P.K + 1, 128), 128, 0, s>>>(d, npts);
     }
     mark(WAVE1D_STAGE_FFT_INV);
-    k_fft_cols<<<P.L2, t1, sm1, s>>>((const double2*)d.spec2, (double2*)d.work, tw, P.L, P.L1, P.L2, l1, -1);
-    k_fft_rows<<<P.L1, t2, sm2, s>>>((const double2*)d.work, (double2*)d.grid, tw, P.L, P.L1, P.L2, l2, -1);
+    if (rbc) {
+        int t1 = std::max(32, std::min(P.L1 / 2, 512)), t2 = std::max(32, std::min(P.L2 / 2, 512));
+        k_fft_cols<<<P.L2, t1, fft_smem_bytes(P.L1), s>>>((const double2*)d.spec2, (double2*)d.work, tw, P.L,
+                                                          P.L1, P.L2, l1, -1);
+        k_fft_rows<<<P.L1, t2, fft_smem_bytes(P.L2), s>>>((const double2*)d.work, (double2*)d.grid, tw, P.L,
+                                                          P.L1, P.L2, l2, -1);
+    } else {
+        k_hist_icols<<<P.L2, tc, fft_smem_bytes(P.L1), s>>>(d, Tb);
+    }
     mark(WAVE1D_STAGE_INTERP);
     k_interp<<<blocks(P.M + P.R, T), T, 0, s>>>(d);
     mark(WAVE1D_STAGE_SOLVE);
     if (fork) cudaStreamWaitEvent(s, p->ev_join, 0);
     k_solve<<<blocks(d.nblocks * 32, T), T, 0, s>>>(d);
-    mark(WAVE1D_STAGE_RECEIVERS);
-    k_receivers<<<blocks(std::max<int64_t>(P.R, 1) * 32, T), T, 0, s>>>(d);
+    mark(WAVE1D_STAGE_RECEIVERS);      // the receivers are read out by the solve's last block
     mark(WAVE1D_NSTAGE);
     CK(cudaGetLastError());
     return WAVE1D_OK;
@@ -406,14 +417,21 @@ int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double d
     if (cudaGetDevice(&p->device) != cudaSuccess) return cleanup(fail(WAVE1D_ECUDA, "no CUDA device"));
     if (cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess)
         return cleanup(fail(WAVE1D_ECUDA, "cannot read the multiprocessor count"));
-    if (cudaStreamCreateWithFlags(&p->s, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&p->s2, cudaStreamNonBlocking) != cudaSuccess ||
+    // the history pipeline (main stream) has the critical path: highest priority; the local sum
+    // (side stream) fills the remaining capacity at the lowest priority
+    int prio_low = 0, prio_high = 0;
+    cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high);
+    if (cudaStreamCreateWithPriority(&p->s, cudaStreamNonBlocking, prio_high) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&p->s2, cudaStreamNonBlocking, prio_low) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming) != cudaSuccess)
         return cleanup(fail(WAVE1D_ECUDA, "stream/event creation failed"));
     if ((rc = enter(p))) return cleanup(rc);
+    if (cudaFuncSetAttribute(k_hist_cols, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)hist_cols_smem_bytes(P.L1)) != cudaSuccess)
+        return cleanup(fail(WAVE1D_ECUDA, "cannot size the shared memory of the column pass"));
 
     HostPlan& hp = p->hp;
     DevPlan& d = p->dp;

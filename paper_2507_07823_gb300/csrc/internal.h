@@ -80,7 +80,8 @@ struct HostPlan {
                                        //         Re/Im deconv2 (1 + i e^{-2 pi i k/nf}),
                                        //         Re/Im deconv2 (1 - i e^{-2 pi i (L-k)/nf}), 0
     std::vector<double> tw2K;          // [a][2] e^{i pi a / K}, a < 2K (radiation projection)
-    std::vector<int32_t> g_ptr;        // nf + 1: spreading as a sparse matrix, grid-row major
+    std::vector<int32_t> g_ptr;        // nf + 1: spreading as a sparse matrix, rows in column-pass
+                                       //   order 2 (i2 L1 + i1) + h
     std::vector<int32_t> g_src;        //   spring of each entry (internal order)
     std::vector<double> g_w;           //   kernel weight of each entry
     // spreading / interpolation
@@ -116,6 +117,10 @@ struct HostPlan {
 // Dynamic shared memory of k_fft_cols / k_fft_rows for a line of N points: the line itself and
 // its N/2 twiddles (every launch site must use this).
 inline size_t fft_smem_bytes(int N) { return (size_t)(N + N / 2) * 16; }
+// spreading products staged per pass of the column kernel, its shared memory and block size
+constexpr int kSpreadChunk = 4096;
+inline size_t hist_cols_smem_bytes(int L1) { return fft_smem_bytes(L1) + (size_t)kSpreadChunk * 8; }
+inline unsigned hist_cols_threads(int L1) { return L1 <= 512 ? 512u : (unsigned)L1; }
 
 // Returns 0 or a negative wave1d_status; fills err with a message on failure.
 int build_host_plan(const double* x, const double* beta, int64_t M, int bc, double dt, int64_t Nt,

@@ -1,14 +1,13 @@
 // Per-step kernels of the WFP march.  One time step n -> n+1:
 //   k_local_items local explicit sum over the last delta of history (Sec. 4.1, m >= 1), on a side
-//                 stream, concurrent with the history pipeline below
-//   k_spread      type-1 spreading of sigma^n onto the fine grid (eq. densco via NUFFT)
-//   k_fft_cols / k_fft_rows   forward complex FFT of the grid viewed as L = nf/2 complex points
-//   k_modes       S_k^n, FIR driving terms, exact rotation, type-2 spectrum (Sec. 3)
-//   [k_rbc_grid, k_rbc_update]  radiation projection on projection steps (Sec. 4.4)
-//   k_fft_cols / k_fft_rows   inverse FFT of the type-2 spectrum
+//                 stream, concurrent with the history pipeline
+//   history pipeline (history.cu): spreading + forward FFT columns, forward FFT rows + mode
+//                 update (Sec. 3) + inverse FFT rows, inverse FFT columns
+//   [k_rbc_grid, k_rbc_update, k_fft_cols, k_fft_rows]  on projection steps (Sec. 4.4) the
+//                 projection and the inverse FFT of the natural-order type-2 spectrum
 //   k_interp      u_H at springs and receivers (eq. historySol1 via NUFFT)
-//   k_solve       forcing, right-hand side and block solve of eq. linearSystem
-//   k_receivers   u = u_L + u_H at receivers; the last block advances the step counter
+//   k_solve       right-hand side and block solve of eq. linearSystem; its last block reads out
+//                 the receivers (u = u_L + u_H) and advances the step counter
 // Kernels read the step index n from device memory so that captured graphs can be replayed.
 //
 // GB300 runs FP64 at about 2 FMA per clock per SM and FP32 at 128, so the one kernel with a
@@ -19,30 +18,10 @@
 #include <cstdint>
 
 #include "internal.h"
+#include "device_common.cuh"
 #include "../../include/wave1d.h"
 
 namespace wave1d {
-
-__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
-
-__device__ __forceinline__ int ring_slot(int64_t q, int ring) {
-    int64_t r = q % ring;
-    return (int)(r < 0 ? r + ring : r);
-}
-
-__device__ __forceinline__ int64_t load_step(const DevPlan& P) {
-    return *((const volatile int64_t*)P.step);
-}
-
-__device__ __forceinline__ double warp_sum(double v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 
 // ---------------------------------------------------------------------------------------------
 // compensated FP32 pairs: a value is hi + lo with |lo| <= ulp(hi)/2 (error-free transformations,
@@ -149,50 +128,19 @@ __global__ void __launch_bounds__(256, 4) k_local_items(DevPlan P) {
     }
 }
 
-// receivers, after the solve: u = 1/2 (sum of the m >= 1 item partials + sum over sources closer
-// than dt of Q_0 sigma^{n+1}) + u_H; one warp per receiver.  The block that finishes last advances
-// the step counter (every other block has read n before it counts itself done).
-__global__ void __launch_bounds__(256) k_receivers(DevPlan P) {
-    int64_t n = load_step(P);
-    int lane = threadIdx.x & 31;
-    int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (r < P.R) {
+// receivers, after every density of the step is stored: u = 1/2 (sum of the m >= 1 item partials
+// + sum over sources closer than dt of Q_0 sigma^{n+1}) + u_H; one warp per receiver, run by the
+// last block of k_solve to finish.
+__device__ __forceinline__ void receivers_readout(const DevPlan& P, int64_t n) {
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const double* s1 = P.sig + (int64_t)ring_slot(n + 1, P.ring) * P.M;
+    for (int64_t r = wid; r < P.R; r += nwarps) {
         double acc = 0.0;
         for (int64_t it = P.r_item_ptr[r] + lane; it < P.r_item_ptr[r + 1]; it += 32) acc += P.r_part[it];
-        const double* s1 = P.sig + (int64_t)ring_slot(n + 1, P.ring) * P.M;
-        for (int64_t e = P.r0_ptr[r] + lane; e < P.r0_ptr[r + 1]; e += 32) acc = fma(P.r0_w[e], s1[P.r0_src[e]], acc);
+        for (int64_t e = P.r0_ptr[r] + lane; e < P.r0_ptr[r + 1]; e += 32)
+            acc = fma(P.r0_w[e], __ldcg(s1 + P.r0_src[e]), acc);
         acc = warp_sum(acc);
         if (lane == 0) P.rec_hist[(n % P.chunk) * P.R + r] = 0.5 * acc + P.uHr[r];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        unsigned long long done = atomicAdd((unsigned long long*)&P.step[1], 1ull);
-        if (done == gridDim.x - 1) {
-            P.step[1] = 0;
-            __threadfence();
-            P.step[0] = n + 1;
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------------------------
-// type-1 spreading as a sparse matrix, one thread per fine-grid point:
-//   G[i] = sum_e g_w[e] sigma^n_{g_src[e]}    (deterministic, no atomics)
-// ---------------------------------------------------------------------------------------------
-__global__ void k_spread(DevPlan P) {
-    int64_t n = load_step(P);
-    const double* sg = P.sig + (int64_t)ring_slot(n, P.ring) * P.M;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < P.nf; i += gridDim.x * blockDim.x) {
-        int e0 = P.g_ptr[i], e1 = P.g_ptr[i + 1];
-        double a0 = 0.0, a1 = 0.0;
-        int e = e0;
-        for (; e + 1 < e1; e += 2) {
-            a0 = fma(__ldg(P.g_w + e), sg[__ldg(P.g_src + e)], a0);
-            a1 = fma(__ldg(P.g_w + e + 1), sg[__ldg(P.g_src + e + 1)], a1);
-        }
-        if (e < e1) a0 = fma(__ldg(P.g_w + e), sg[__ldg(P.g_src + e)], a0);
-        P.grid[i] = a0 + a1;
     }
 }
 
@@ -203,32 +151,6 @@ __global__ void k_spread(DevPlan P) {
 // Each block transforms one line in shared memory: bit-reversed load, radix-2 DIT stages with the
 // line's N/2 twiddles staged in shared memory.  tw[j] = e^{+2 pi i j / L}.
 // ---------------------------------------------------------------------------------------------
-__device__ void fft_line(double2* a, const double2* twN, int N, int logN) {
-    for (int s = 1; s <= logN; s++) {
-        int half = 1 << (s - 1);
-        int step = N / (2 * half);
-        for (int j = threadIdx.x; j < N / 2; j += blockDim.x) {
-            int pos = j & (half - 1);
-            int i0 = ((j >> (s - 1)) << s) + pos;
-            int i1 = i0 + half;
-            double2 t = cmul(twN[pos * step], a[i1]);
-            double2 u = a[i0];
-            a[i0] = cadd(u, t);
-            a[i1] = csub(u, t);
-        }
-        __syncthreads();
-    }
-}
-
-__device__ __forceinline__ void stage_twiddles(double2* twN, const double2* tw, int L, int N, int sign) {
-    int stride = L / N;
-    for (int j = threadIdx.x; j < N / 2; j += blockDim.x) {
-        double2 w = tw[j * stride];
-        if (sign < 0) w.y = -w.y;
-        twN[j] = w;
-    }
-}
-
 __global__ void k_fft_cols(const double2* __restrict__ in, double2* __restrict__ out,
                            const double2* __restrict__ tw, int L, int L1, int L2, int logL1, int sign) {
     extern __shared__ double2 sm[];
@@ -258,69 +180,6 @@ __global__ void k_fft_rows(const double2* __restrict__ in, double2* __restrict__
     __syncthreads();
     fft_line(sm, twN, L2, logL2);
     for (int k2 = threadIdx.x; k2 < L2; k2 += blockDim.x) out[k1 + (int64_t)L1 * k2] = sm[k2];
-}
-
-// ---------------------------------------------------------------------------------------------
-// Type-2 spectrum of mode k for the inverse real FFT (factors precomputed in modefac):
-//   Zs[k] = alpha_k deconv2_k (1 + i w^k),  Zs[L-k] = conj(alpha_k) deconv2_k (1 - i w^{L-k}),
-//   w = e^{-2 pi i / nf}; entries with K < idx < L - K stay zero.
-// ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ void write_type2(const DevPlan& P, int k, double2 a, double2* Zs) {
-    const double* f = P.modefac + 8 * (int64_t)k;
-    Zs[k] = cmul(a, make_double2(f[3], f[4]));
-    if (k > 0) Zs[P.L - k] = cmul(cconj(a), make_double2(f[5], f[6]));
-}
-
-// ---------------------------------------------------------------------------------------------
-// Modes: four threads per mode k.
-//   S_k^n = deconv1_k E_k + deconv1_k e^{2 pi i k/nf} O_k from the half-length FFT Z
-//   (E = (Z_k + conj Z_{L-k})/2, O = (Z_k - conj Z_{L-k})/(2i)), stored in ring slot n mod W;
-//   h_k = sum_m dt p_k(m dt) S_k^{n-m}, g_k likewise (eq. hkcompdisc);
-//   alpha, alpha' rotated and driven (eq. alphakEvolutionFormulas); type-2 spectrum written.
-// ---------------------------------------------------------------------------------------------
-__global__ void k_modes(DevPlan P) {
-    int64_t n = load_step(P);
-    int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    int k = tid >> 2, q = tid & 3;
-    bool valid = k <= P.K;
-    int kk = valid ? k : P.K;
-    const double2* Z = (const double2*)P.spec;
-    double2 zk = Z[kk];
-    double2 zm = Z[kk == 0 ? 0 : P.L - kk];
-    const double* f = P.modefac + 8 * (int64_t)kk;
-    double2 E = make_double2(0.5 * (zk.x + zm.x), 0.5 * (zk.y - zm.y));
-    double2 D = make_double2(0.5 * (zk.x - zm.x), 0.5 * (zk.y + zm.y));
-    double2 O = make_double2(D.y, -D.x);
-    double2 Sn = cadd(make_double2(f[0] * E.x, f[0] * E.y), cmul(make_double2(f[1], f[2]), O));
-    int K1 = P.K + 1;
-    double2* Sring = (double2*)P.Sring;
-    const double2* pq = (const double2*)P.pq;
-    double2 h = make_double2(0.0, 0.0), g = make_double2(0.0, 0.0);
-    for (int m = q; m < P.W; m += 4) {
-        double2 Sm = (m == 0) ? Sn : Sring[(int64_t)ring_slot(n - m, P.W) * K1 + kk];
-        double2 w = pq[(int64_t)m * K1 + kk];
-        h.x = fma(w.x, Sm.x, h.x);
-        h.y = fma(w.x, Sm.y, h.y);
-        g.x = fma(w.y, Sm.x, g.x);
-        g.y = fma(w.y, Sm.y, g.y);
-    }
-    for (int o = 1; o < 4; o <<= 1) {
-        h.x += __shfl_xor_sync(0xffffffffu, h.x, o);
-        h.y += __shfl_xor_sync(0xffffffffu, h.y, o);
-        g.x += __shfl_xor_sync(0xffffffffu, g.x, o);
-        g.y += __shfl_xor_sync(0xffffffffu, g.y, o);
-    }
-    if (!valid || q != 0) return;
-    Sring[(int64_t)ring_slot(n, P.W) * K1 + k] = Sn;
-    double2* al = (double2*)P.alpha;
-    double2* alp = (double2*)P.alpha_p;
-    double2 a = al[k], ap = alp[k];
-    double cs = P.rot[3 * k], so = P.rot[3 * k + 1], ks = P.rot[3 * k + 2];
-    double2 an = make_double2(fma(a.x, cs, fma(ap.x, so, h.x)), fma(a.y, cs, fma(ap.y, so, h.y)));
-    double2 apn = make_double2(fma(ap.x, cs, fma(-a.x, ks, g.x)), fma(ap.y, cs, fma(-a.y, ks, g.y)));
-    al[k] = an;
-    alp[k] = apn;
-    write_type2(P, k, an, (double2*)P.spec2);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -408,22 +267,40 @@ __device__ double incident(const DevPlan& P, double s);
 // ---------------------------------------------------------------------------------------------
 __global__ void k_interp(DevPlan P) {
     int64_t total = P.M + P.R;
+    const int w = P.w, nf = P.nf;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
          t += (int64_t)gridDim.x * blockDim.x) {
         bool spring = t < P.M;
         int64_t j = spring ? t : t - P.M;
         int i0 = spring ? P.sp_i0[j] : P.rc_i0[j];
-        const double* ker = spring ? P.sp_ker + j * P.w : P.rc_ker + j * P.w;
+        const double* ker = spring ? P.sp_ker + j * w : P.rc_ker + j * w;
+        double bj = 0.0, xj = 0.0, gj = 0.0;
+        if (spring) {
+            bj = P.beta[j];
+            if (P.g_ext) gj = P.g_ext[j];
+            else xj = P.x[j];
+        }
+        // taps in batches of 16, loaded before they are summed (in tap order)
         double acc = 0.0;
-        int i = i0;
-        for (int tt = 0; tt < P.w; tt++) {
-            acc = fma(P.grid[i], ker[tt], acc);
-            i = (i + 1 == P.nf) ? 0 : i + 1;
+        for (int t0 = 0; t0 < w; t0 += 16) {
+            double gv[16], kv[16];
+#pragma unroll
+            for (int u = 0; u < 16; u++) {
+                int tt = t0 + u;
+                if (tt < w) {
+                    int i = i0 + tt;
+                    i = i >= nf ? i - nf : i;
+                    gv[u] = P.grid[i];
+                    kv[u] = ker[tt];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 16; u++)
+                if (t0 + u < w) acc = fma(gv[u], kv[u], acc);
         }
         if (spring) {
             P.uH[j] = acc;
-            double bj = P.beta[j];
-            double g = P.g_ext ? P.g_ext[j] : bj * incident(P, P.x[j] - (double)(load_step(P) + 1) * P.dt);
+            double g = P.g_ext ? gj : bj * incident(P, xj - (double)(load_step(P) + 1) * P.dt);
             P.rhs[j] = -g - bj * acc;
         } else {
             P.uHr[j] = acc;
@@ -460,10 +337,19 @@ __device__ double incident(const DevPlan& P, double s) {
 // without the local sum is formed by k_interp (one thread per spring); the solve adds the local sum
 // c_j, assembled from the partials of the row's items (and kept for inspection)
 __device__ __forceinline__ double rhs_of(const DevPlan& P, int j) {
+    int64_t a = P.l_item_ptr[j], e = P.l_item_ptr[j + 1];
+    double bj = P.beta[j], rj = P.rhs[j];
     double c = 0.0;
-    for (int64_t it = P.l_item_ptr[j]; it < P.l_item_ptr[j + 1]; it++) c += P.l_part[it];
+    for (int64_t it = a; it < e; it += 8) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) v[u] = it + u < e ? P.l_part[it + u] : 0.0;
+#pragma unroll
+        for (int u = 0; u < 8; u++)
+            if (it + u < e) c += v[u];
+    }
     P.clocal[j] = c;
-    return fma(-0.5 * P.beta[j], c, P.rhs[j]);
+    return fma(-0.5 * bj, c, rj);
 }
 
 __device__ __forceinline__ void store_sigma(const DevPlan& P, int64_t n, int j, double v) {
@@ -485,41 +371,71 @@ constexpr int kSolveStage = 256;
 
 __global__ void __launch_bounds__(256) k_solve(DevPlan P) {
     __shared__ double srhs[8][kSolveStage];
+    __shared__ bool last;
     int64_t n = load_step(P);
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int64_t b = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (blockIdx.x == 0 && threadIdx.x == 0) *P.item_ctr = 0ull;   // the step's local sums are done
-    if (b >= P.nblocks) return;
-    int64_t m0 = P.blk_ptr[b];
-    int s = (int)(P.blk_ptr[b + 1] - m0);
-    const double* invT = P.inv + P.blk_inv_off[b];
-    if (s <= kSolveStage) {
-        double* r = srhs[wid];
-        for (int i = lane; i < s; i += 32) r[i] = rhs_of(P, P.blk_members[m0 + i]);
-        __syncwarp();
-        for (int i = lane; i < s; i += 32) {
-            double a0 = 0.0, a1 = 0.0;
-            int l = 0;
-            for (; l + 1 < s; l += 2) {
-                a0 = fma(invT[(int64_t)l * s + i], r[l], a0);
-                a1 = fma(invT[(int64_t)(l + 1) * s + i], r[l + 1], a1);
+    if (b < P.nblocks) {
+        int64_t m0 = P.blk_ptr[b];
+        int s = (int)(P.blk_ptr[b + 1] - m0);
+        const double* invT = P.inv + P.blk_inv_off[b];
+        if (s <= kSolveStage) {
+            double* r = srhs[wid];
+            // the first eight inverse entries of the lane's first row load with the members
+            double pre[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) pre[u] = (lane < s && u < s) ? invT[(int64_t)u * s + lane] : 0.0;
+            for (int i = lane; i < s; i += 32) r[i] = rhs_of(P, P.blk_members[m0 + i]);
+            __syncwarp();
+            for (int i = lane; i < s; i += 32) {
+                double a0 = 0.0, a1 = 0.0;
+                for (int l0 = 0; l0 < s; l0 += 8) {
+                    double v[8];
+#pragma unroll
+                    for (int u = 0; u < 8; u++)
+                        v[u] = (l0 == 0 && i == lane) ? pre[u]
+                                                      : (l0 + u < s ? invT[(int64_t)(l0 + u) * s + i] : 0.0);
+#pragma unroll
+                    for (int u = 0; u < 8; u += 2) {
+                        if (l0 + u < s) a0 = fma(v[u], r[l0 + u], a0);
+                        if (l0 + u + 1 < s) a1 = fma(v[u + 1], r[l0 + u + 1], a1);
+                    }
+                }
+                store_sigma(P, n, P.blk_members[m0 + i], a0 + a1);
             }
-            if (l < s) a0 = fma(invT[(int64_t)l * s + i], r[l], a0);
-            store_sigma(P, n, P.blk_members[m0 + i], a0 + a1);
+        } else {
+            // large blocks: the full right-hand side is formed in place in P.rhs first
+            for (int i = lane; i < s; i += 32) {
+                int j = P.blk_members[m0 + i];
+                P.rhs[j] = rhs_of(P, j);
+            }
+            __syncwarp();
+            for (int i = lane; i < s; i += 32) {
+                double acc = 0.0;
+                for (int l = 0; l < s; l++)
+                    acc = fma(invT[(int64_t)l * s + i], P.rhs[P.blk_members[m0 + l]], acc);
+                store_sigma(P, n, P.blk_members[m0 + i], acc);
+            }
         }
-    } else {
-        // large blocks: the full right-hand side is formed in place in P.rhs first
-        for (int i = lane; i < s; i += 32) {
-            int j = P.blk_members[m0 + i];
-            P.rhs[j] = rhs_of(P, j);
-        }
-        __syncwarp();
-        for (int i = lane; i < s; i += 32) {
-            double acc = 0.0;
-            for (int l = 0; l < s; l++)
-                acc = fma(invT[(int64_t)l * s + i], P.rhs[P.blk_members[m0 + l]], acc);
-            store_sigma(P, n, P.blk_members[m0 + i], acc);
-        }
+    }
+    // the block that finishes last reads out the receivers and advances the step counter (every
+    // other block has stored its densities and read n before it counts itself done)
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long done = atomicAdd((unsigned long long*)&P.step[1], 1ull);
+        last = (done == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    receivers_readout(P, n);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        P.step[1] = 0;
+        __threadfence();
+        P.step[0] = n + 1;
     }
 }
 

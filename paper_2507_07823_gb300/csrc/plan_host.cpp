@@ -403,7 +403,7 @@ int build_host_plan(const double* x_in, const double* beta_in, int64_t M, int bc
     P.L = P.nf / 2;
     int lg = 0;
     while ((1 << lg) < P.L) lg++;
-    P.L1 = 1 << (lg / 2);
+    P.L1 = 1 << ((lg + 1) / 2);          // L1 >= L2: balances column and row-pair passes
     P.L2 = P.L / P.L1;
     if (P.L2 > 1024) { err = "fine grid too large for this build (nf > 2^21)"; return WAVE1D_EUNSUPPORTED; }
     P.h_f = 2.0 * kPi / P.nf;
@@ -537,22 +537,28 @@ int build_host_plan(const double* x_in, const double* beta_in, int64_t M, int bc
         std::vector<int32_t> fill(hp.bin_ptr.begin(), hp.bin_ptr.end() - 1);
         for (int64_t j = 0; j < M; j++) hp.bin_list[fill[hp.sp_i0[j]]++] = (int32_t)j;
     }
-    // spreading as a grid-row sparse matrix: G[i] = sum_e g_w[e] sigma_{g_src[e]}
+    // spreading as a sparse matrix, G[i] = sum_e g_w[e] sigma_{g_src[e]}, its rows in the order the
+    // column pass of the FFT reads them: real i = 2 r + h of complex point r = i2 + L2 i1 is row
+    // c = 2 (i2 L1 + i1) + h, so each column's entries form one contiguous range
     {
         int w = P.nufft_w;
+        auto row_of = [&](int i) {
+            int r = i >> 1, h = i & 1;
+            return 2 * ((r % P.L2) * P.L1 + r / P.L2) + h;
+        };
         hp.g_ptr.assign(P.nf + 1, 0);
         for (int64_t j = 0; j < M; j++)
-            for (int t = 0; t < w; t++) hp.g_ptr[(hp.sp_i0[j] + t) % P.nf + 1]++;
+            for (int t = 0; t < w; t++) hp.g_ptr[row_of((hp.sp_i0[j] + t) % P.nf) + 1]++;
         for (int i = 0; i < P.nf; i++) hp.g_ptr[i + 1] += hp.g_ptr[i];
         hp.g_src.assign((size_t)M * w, 0);
         hp.g_w.assign((size_t)M * w, 0.0);
         std::vector<int32_t> fill(hp.g_ptr.begin(), hp.g_ptr.end() - 1);
         for (int64_t j = 0; j < M; j++)
             for (int t = 0; t < w; t++) {
-                int i = (hp.sp_i0[j] + t) % P.nf;
-                hp.g_src[fill[i]] = (int32_t)j;
-                hp.g_w[fill[i]] = hp.sp_ker[j * w + t];
-                fill[i]++;
+                int c = row_of((hp.sp_i0[j] + t) % P.nf);
+                hp.g_src[fill[c]] = (int32_t)j;
+                hp.g_w[fill[c]] = hp.sp_ker[j * w + t];
+                fill[c]++;
             }
     }
 
