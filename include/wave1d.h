@@ -52,7 +52,9 @@ enum wave1d_status {
     WAVE1D_ECUDA = -4,         /* a CUDA runtime call failed                                   */
     WAVE1D_ENONFINITE = -6,    /* a density became NaN or Inf (latched on the device)          */
     WAVE1D_EDONE = -7,         /* stepping past the Nt given to wave1d_plan                    */
-    WAVE1D_EUNSUPPORTED = -9   /* a size this build does not handle (see wave1d_strerror)      */
+    WAVE1D_EUNSUPPORTED = -9,  /* a size this build does not handle (see wave1d_strerror)      */
+    WAVE1D_ETIMEOUT = -10      /* a bounded wait between the blocks of the one-launch step kernel
+                                  ran out (latched on the device); the plan cannot continue      */
 };
 
 /* Optional parameters.  wave1d_opts_default fills the paper's defaults. */
@@ -66,6 +68,8 @@ typedef struct {
     int rbc_period;     /* steps between radiation projections (Sec. 4.4); 0 = ceil(1.5 W)        */
     int max_block;      /* largest block of springs closer than dt solved directly; default 4096  */
     int64_t max_local_bytes; /* budget for stored local weights; default 16 GiB                  */
+    int step_kernel;    /* 1 (default): ordinary steps run as one cooperative launch (history,
+                           local sum and solve in one kernel); 0: one launch per stage           */
     void* stream;       /* cudaStream_t for all work of the plan; NULL = legacy default stream   */
 } wave1d_opts;
 

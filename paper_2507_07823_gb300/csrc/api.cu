@@ -15,12 +15,15 @@
 #include <vector>
 
 #include "internal.h"
+#include "phases.cuh"
 #include "../../include/wave1d.h"
 
 namespace wave1d {
+__global__ void k_step(DevPlan P);
 __global__ void k_hist_cols(DevPlan P, double2* Y);
 __global__ void k_hist_rows(DevPlan P, const double2* Y, double2* T, int do_inverse);
 __global__ void k_hist_icols(DevPlan P, const double2* T);
+__global__ void k_hist_tail(DevPlan P);
 __global__ void k_fft_cols(const double2*, double2*, const double2*, int, int, int, int, int);
 __global__ void k_fft_rows(const double2*, double2*, const double2*, int, int, int, int, int);
 __global__ void k_rbc_grid(DevPlan P);
@@ -64,6 +67,9 @@ struct wave1d_plan_s {
     double* d_sig_hist = nullptr;
     Graph graphs[2];                  // chunk graphs without / with the sigma history
     Graph step_graphs[2];             // single-step graphs: ordinary step / projection step
+    bool step_kernel = false;         // ordinary steps as one cooperative launch (k_step)
+    unsigned step_grid = 0;           // its blocks (all resident) and dynamic shared memory
+    size_t step_smem = 0;
     bool profiling = false;
     cudaEvent_t prof_ev[WAVE1D_NSTAGE + 1] = {};
     double prof_ms[WAVE1D_NSTAGE] = {};
@@ -230,6 +236,21 @@ int enqueue_step(wave1d_plan_t p, int64_t n, const double* g_ext, double* sig_hi
     auto mark = [&](int i) {
         if (ev) cudaEventRecord(ev[i], s);
     };
+    bool rbc = is_rbc_step(p, n);
+    if (p->step_kernel && !rbc && !ev) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(p->step_grid);
+        cfg.blockDim = dim3(kStepThreads);
+        cfg.dynamicSmemBytes = p->step_smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        CK(cudaLaunchKernelEx(&cfg, k_step, d));
+        return WAVE1D_OK;
+    }
     // The local sum needs only sigma^{<= n} and could overlap the history pipeline on the side
     // stream, but on GB300 the two slow each other down (the latency-bound history kernels wait
     // longer on an HBM the local sum keeps busy): measured 169 us per step concurrently against
@@ -246,17 +267,17 @@ int enqueue_step(wave1d_plan_t p, int64_t n, const double* g_ext, double* sig_hi
     }
     // history pipeline: spreading + forward columns | forward rows + modes (+ inverse rows) |
     // [projection] | inverse columns
-    bool rbc = is_rbc_step(p, n);
     double2* Y = (double2*)d.work;
     double2* Tb = (double2*)d.spec;
     const double2* tw = (const double2*)d.twiddle;
     int l1 = ilog2(P.L1), l2 = ilog2(P.L2);
     unsigned tc = (unsigned)std::max(32, std::min(P.L1, 1024));
     mark(WAVE1D_STAGE_SPREAD);
-    k_hist_cols<<<P.L2, hist_cols_threads(P.L1), hist_cols_smem_bytes(P.L1), s>>>(d, Y);
+    k_hist_cols<<<P.L2, 256, cols_phase_smem(P.L1), s>>>(d, Y);
     mark(WAVE1D_STAGE_FFT_FWD);
     mark(WAVE1D_STAGE_MODES);
-    k_hist_rows<<<P.L1 / 2 + 1, T, (size_t)(2 * P.L2 + P.L2 / 2) * sizeof(double2), s>>>(d, Y, Tb, rbc ? 0 : 1);
+    k_hist_rows<<<P.L1 / 2 + 1, T, rows_phase_smem(P.L2), s>>>(d, Y, Tb, rbc ? 0 : 1);
+    k_hist_tail<<<(P.K + 1 + kTailModes - 1) / kTailModes, 4 * kTailModes, 0, s>>>(d);
     mark(WAVE1D_STAGE_RBC);
     if (rbc) {
         int npts = (int)p->hp.rbc_idx.size();
@@ -271,7 +292,7 @@ int enqueue_step(wave1d_plan_t p, int64_t n, const double* g_ext, double* sig_hi
         k_fft_rows<<<P.L1, t2, fft_smem_bytes(P.L2), s>>>((const double2*)d.work, (double2*)d.grid, tw, P.L,
                                                           P.L1, P.L2, l2, -1);
     } else {
-        k_hist_icols<<<P.L2, tc, fft_smem_bytes(P.L1), s>>>(d, Tb);
+        k_hist_icols<<<P.L2, tc, icols_phase_smem(P.L1), s>>>(d, Tb);
     }
     mark(WAVE1D_STAGE_INTERP);
     k_interp<<<blocks(P.M + P.R, T), T, 0, s>>>(d);
@@ -288,6 +309,7 @@ int check_status(wave1d_plan_t p) {
     int st = 0;
     CK(cudaMemcpyAsync(&st, p->dp.status, sizeof(int), cudaMemcpyDeviceToHost, p->s));
     CK(cudaStreamSynchronize(p->s));
+    if (st == WAVE1D_ETIMEOUT) return fail(st, "a bounded wait between the blocks of the step kernel ran out");
     if (st != 0) return fail(st, "a density became non-finite during the march");
     return WAVE1D_OK;
 }
@@ -360,6 +382,7 @@ int wave1d_opts_default(wave1d_opts* o) {
     o->Ng = 32;
     o->max_block = 4096;
     o->max_local_bytes = (int64_t)16 << 30;
+    o->step_kernel = 1;
     return WAVE1D_OK;
 }
 
@@ -374,6 +397,7 @@ const char* wave1d_strerror(int status) {
         case WAVE1D_ENONFINITE: return "non-finite density";
         case WAVE1D_EDONE: return "all planned steps taken";
         case WAVE1D_EUNSUPPORTED: return "size not supported by this build";
+        case WAVE1D_ETIMEOUT: return "a bounded wait of the step kernel ran out";
         default: return "unknown status";
     }
 }
@@ -430,8 +454,29 @@ int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double d
         return cleanup(fail(WAVE1D_ECUDA, "stream/event creation failed"));
     if ((rc = enter(p))) return cleanup(rc);
     if (cudaFuncSetAttribute(k_hist_cols, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)hist_cols_smem_bytes(P.L1)) != cudaSuccess)
+                             (int)cols_phase_smem(P.L1)) != cudaSuccess)
         return cleanup(fail(WAVE1D_ECUDA, "cannot size the shared memory of the column pass"));
+    // one-launch step kernel: as many blocks as are resident at once, the history group one block
+    // per column / row pair
+    if (o.step_kernel) {
+        size_t sm = std::max({cols_phase_smem(P.L1), rows_phase_smem(P.L2), icols_phase_smem(P.L1),
+                              (size_t)kSolveStage * sizeof(double) * (kStepThreads / 32)});
+        int occ = 0;
+        if (cudaFuncSetAttribute(k_step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_step, kStepThreads, sm) != cudaSuccess)
+            return cleanup(fail(WAVE1D_ECUDA, "cannot configure the step kernel"));
+        int coop = 0;
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, p->device);
+        int64_t grid = (int64_t)occ * p->sms;
+        // one history block per column / row pair, at most half of the blocks
+        int units = std::max(P.L2, P.L1 / 2 + 1);
+        if (coop && occ > 0) {
+            p->step_kernel = true;
+            p->step_grid = (unsigned)grid;
+            p->step_smem = sm;
+            p->dp.hist_blocks = (int)std::max<int64_t>(1, std::min<int64_t>(units, grid / 2));
+        }
+    }
 
     HostPlan& hp = p->hp;
     DevPlan& d = p->dp;
@@ -460,6 +505,9 @@ int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double d
     if ((rc = zeros(p, &d.step, 2))) return cleanup(rc);
     if ((rc = zeros(p, &d.item_ctr, 1))) return cleanup(rc);
     if ((rc = zeros(p, &d.status, 1))) return cleanup(rc);
+    if ((rc = zeros(p, &d.bar, 16))) return cleanup(rc);
+    if ((rc = zeros(p, &d.ftail, (size_t)4 * (P.K + 1)))) return cleanup(rc);
+    if ((rc = zeros(p, &d.gforce, (size_t)P.M))) return cleanup(rc);
     UP(hp.x, x, f64);
     UP(hp.beta, beta, f64);
     UP(hp.perm, perm, i32);
@@ -506,6 +554,7 @@ int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double d
     UP(hp.blk_inv_off, blk_inv_off, i64);
     UP(hp.inv, inv, f64);
     d.nblocks = (int64_t)hp.blk_ptr.size() - 1;
+    d.inv_len = (int64_t)hp.inv.size();
     UP(hp.rbc_idx, rbc_idx, i32);
     UP(hp.rbc_x, rbc_x, f64);
     UP(hp.rbc_phi, rbc_phi, f64);

@@ -51,6 +51,42 @@ __device__ __forceinline__ void fft_line(double2* a, const double2* twN, int N, 
     }
 }
 
+// The same transform of one or two lines (b may be null) with two threads per butterfly: the
+// thread of component c (0 = real, 1 = imaginary) reads and writes only component c, taking the
+// other component of the product from its neighbour lane.  GB300 issues one FP64 warp
+// instruction per 64 cycles per SM partition, so halving the FP64 instructions of each thread and
+// doubling the warps that share them shortens every stage.  N >= 16, blockDim a multiple of 32.
+__device__ __forceinline__ void fft_lines(double2* a, double2* b, const double2* twN, int N, int logN) {
+    const int total = (b ? 2 : 1) * N;          // one thread per (line, butterfly, component)
+    if (total & 31) {                           // lines too short to fill whole warps
+        fft_line(a, twN, N, logN);
+        if (b) fft_line(b, twN, N, logN);
+        return;
+    }
+    for (int s = 1; s <= logN; s++) {
+        const int half = 1 << (s - 1);
+        const int step = N >> s;
+        for (int t = threadIdx.x; t < total; t += blockDim.x) {
+            const bool second = t >= N;
+            double* x = (double*)(second ? b : a);
+            const int tt = second ? t - N : t;
+            const int j = tt >> 1, c = tt & 1;
+            const int pos = j & (half - 1);
+            const int i0 = ((j >> (s - 1)) << s) + pos;
+            const int i1 = i0 + half;
+            const double2 w = twN[pos * step];
+            const double ac = x[2 * i1 + c];                          // own component of a[i1]
+            const double ao = __shfl_xor_sync(0xffffffffu, ac, 1);   // the other one
+            const double u = x[2 * i0 + c];
+            // c = 0: Re(w a) = w.x a.x - w.y a.y;  c = 1: Im(w a) = w.x a.y + w.y a.x
+            const double tc = c ? fma(w.x, ac, w.y * ao) : fma(w.x, ac, -(w.y * ao));
+            x[2 * i0 + c] = u + tc;
+            x[2 * i1 + c] = u - tc;
+        }
+        __syncthreads();
+    }
+}
+
 __device__ __forceinline__ void stage_twiddles(double2* twN, const double2* tw, int L, int N, int sign) {
     int stride = L / N;
     for (int j = threadIdx.x; j < N / 2; j += blockDim.x) {
@@ -72,48 +108,70 @@ __device__ __forceinline__ void write_type2(const DevPlan& P, int k, double2 a, 
 }
 
 // ---------------------------------------------------------------------------------------------
-// One mode of the history update, computed by a quad of four lanes (all four call it with the same
-// k, Z_k and Z_{L-k}; valid = false for padding quads, which still take part in the shuffles):
+// One mode of the history update (eqs. hkcompdisc, alphakEvolutionFormulas), one thread per mode:
 //   S_k^n = deconv1_k E_k + deconv1_k e^{2 pi i k/nf} O_k  (E, O from the half-length FFT),
-//   h_k = sum_m dt p_k(m dt) S_k^{n-m}, g_k likewise (eq. hkcompdisc), the m sum split over the quad,
-//   alpha, alpha' rotated and driven (eq. alphakEvolutionFormulas).
-// Lane q == 0 of a valid quad stores S_k^n, alpha_k, alpha'_k and returns alpha_k^{n+1}.
+//   h_k = dt p_k(0) S_k^n + tail_h,  g_k = dt q_k(0) S_k^n + tail_g,
+// where the tail (taps m = 1 .. W-1, which need only S^{< n}) was summed by fir_tail after the
+// previous step's mode update; then alpha, alpha' are rotated and driven.  Stores S_k^n, alpha_k,
+// alpha'_k and returns alpha_k^{n+1}.
 // ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ double2 mode_step(const DevPlan& P, int64_t n, int k, bool valid, int q,
-                                             double2 zk, double2 zm) {
-    int kk = valid ? k : P.K;
-    const double* f = P.modefac + 8 * (int64_t)kk;
+__device__ __forceinline__ double2 mode_update(const DevPlan& P, int64_t n, int k, double2 zk, double2 zm) {
+    const double* f = P.modefac + 8 * (int64_t)k;
     double2* al = (double2*)P.alpha;
     double2* alp = (double2*)P.alpha_p;
-    // everything the mode needs besides the FIR taps, loaded before them
-    double f0 = f[0], f1 = f[1], f2 = f[2];
-    double2 a = al[kk], ap = alp[kk];
-    double cs = P.rot[3 * kk], so = P.rot[3 * kk + 1], ks = P.rot[3 * kk + 2];
-    double2 E = make_double2(0.5 * (zk.x + zm.x), 0.5 * (zk.y - zm.y));
-    double2 D = make_double2(0.5 * (zk.x - zm.x), 0.5 * (zk.y + zm.y));
-    double2 O = make_double2(D.y, -D.x);
-    double2 Sn = cadd(make_double2(f0 * E.x, f0 * E.y), cmul(make_double2(f1, f2), O));
+    const int K1 = P.K + 1;
+    const double f0 = f[0], f1 = f[1], f2 = f[2];
+    const double2 a = al[k], ap = alp[k];
+    const double cs = P.rot[3 * k], so = P.rot[3 * k + 1], ks = P.rot[3 * k + 2];
+    const double2 w0 = ((const double2*)P.pq)[k];                 // dt (p_k(0), q_k(0))
+    const double4 tl = ((const double4*)P.ftail)[k];              // (tail_h, tail_g)
+    const double2 E = make_double2(0.5 * (zk.x + zm.x), 0.5 * (zk.y - zm.y));
+    const double2 D = make_double2(0.5 * (zk.x - zm.x), 0.5 * (zk.y + zm.y));
+    const double2 O = make_double2(D.y, -D.x);
+    const double2 Sn = cadd(make_double2(f0 * E.x, f0 * E.y), cmul(make_double2(f1, f2), O));
+    const double2 h = make_double2(fma(w0.x, Sn.x, tl.x), fma(w0.x, Sn.y, tl.y));
+    const double2 g = make_double2(fma(w0.y, Sn.x, tl.z), fma(w0.y, Sn.y, tl.w));
+    ((double2*)P.Sring)[(int64_t)ring_slot(n, P.W) * K1 + k] = Sn;
+    const double2 an = make_double2(fma(a.x, cs, fma(ap.x, so, h.x)), fma(a.y, cs, fma(ap.y, so, h.y)));
+    const double2 apn = make_double2(fma(ap.x, cs, fma(-a.x, ks, g.x)), fma(ap.y, cs, fma(-a.y, ks, g.y)));
+    al[k] = an;
+    alp[k] = apn;
+    return an;
+}
+
+// ---------------------------------------------------------------------------------------------
+// FIR tail for step n+1 (eq. hkcompdisc without its m = 0 term), once S^n is stored:
+//   tail_h = sum_{m=1}^{W-1} dt p_k(m dt) S_k^{n+1-m},  tail_g likewise with q_k,
+// one quad of lanes per mode (lane q takes m = 1 + q, 5 + q, ...; the four partial sums are added
+// in a fixed tree), modes kbase + (threadIdx.x >> 2).  The ring S^{n+1-m} sits in slot
+// (n+1-m) mod W; slot n was written in this step (read through L2).
+// ---------------------------------------------------------------------------------------------
+constexpr int kTapBatch = 4;
+
+__device__ __forceinline__ void fir_tail(const DevPlan& P, int64_t n, int kbase) {
+    const int q = threadIdx.x & 3;
+    const int k = kbase + (int)(threadIdx.x >> 2);
+    const bool valid = k <= P.K;
+    const int kk = valid ? k : P.K;
     const int K1 = P.K + 1, W = P.W;
-    double2* Sring = (double2*)P.Sring;
+    const double2* Sring = (const double2*)P.Sring;
     const double2* pq = (const double2*)P.pq;
     double2 h = make_double2(0.0, 0.0), g = make_double2(0.0, 0.0);
-    // taps m = q, q + 4, ...: a batch of eight is loaded before any is used
-    int slot = ring_slot(n - q, W);
-    for (int m0 = q; m0 < W; m0 += 32) {
-        double2 Sv[8], wv[8];
+    int slot = ring_slot(n - q, W);            // slot of m = 1 + q: (n + 1 - m) mod W
+    for (int m0 = 1 + q; m0 < W; m0 += 4 * kTapBatch) {
+        double2 Sv[kTapBatch], wv[kTapBatch];
 #pragma unroll
-        for (int u = 0; u < 8; u++) {
+        for (int u = 0; u < kTapBatch; u++) {
             int m = m0 + 4 * u;
             int sl = slot - 4 * u;
             sl = sl < 0 ? sl + W : sl;
-            sl = sl < 0 ? sl + W : sl;
             if (m < W) {
-                Sv[u] = (m == 0) ? Sn : Sring[(int64_t)sl * K1 + kk];
-                wv[u] = pq[(int64_t)m * K1 + kk];
+                Sv[u] = __ldcg(Sring + (int64_t)sl * K1 + kk);
+                wv[u] = __ldg(pq + (int64_t)m * K1 + kk);
             }
         }
 #pragma unroll
-        for (int u = 0; u < 8; u++) {
+        for (int u = 0; u < kTapBatch; u++) {
             if (m0 + 4 * u < W) {
                 h.x = fma(wv[u].x, Sv[u].x, h.x);
                 h.y = fma(wv[u].x, Sv[u].y, h.y);
@@ -121,7 +179,7 @@ __device__ __forceinline__ double2 mode_step(const DevPlan& P, int64_t n, int k,
                 g.y = fma(wv[u].y, Sv[u].y, g.y);
             }
         }
-        slot -= 32 % W;
+        slot -= (4 * kTapBatch) % W;
         slot = slot < 0 ? slot + W : slot;
     }
     for (int o = 1; o < 4; o <<= 1) {
@@ -130,15 +188,7 @@ __device__ __forceinline__ double2 mode_step(const DevPlan& P, int64_t n, int k,
         g.x += __shfl_xor_sync(0xffffffffu, g.x, o);
         g.y += __shfl_xor_sync(0xffffffffu, g.y, o);
     }
-    double2 an = make_double2(0.0, 0.0);
-    if (valid && q == 0) {
-        Sring[(int64_t)ring_slot(n, W) * K1 + k] = Sn;
-        an = make_double2(fma(a.x, cs, fma(ap.x, so, h.x)), fma(a.y, cs, fma(ap.y, so, h.y)));
-        double2 apn = make_double2(fma(ap.x, cs, fma(-a.x, ks, g.x)), fma(ap.y, cs, fma(-a.y, ks, g.y)));
-        al[k] = an;
-        alp[k] = apn;
-    }
-    return an;
+    if (valid && q == 0) ((double4*)P.ftail)[k] = make_double4(h.x, h.y, g.x, g.y);
 }
 
 }  // namespace wave1d

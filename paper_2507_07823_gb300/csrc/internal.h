@@ -117,10 +117,8 @@ struct HostPlan {
 // Dynamic shared memory of k_fft_cols / k_fft_rows for a line of N points: the line itself and
 // its N/2 twiddles (every launch site must use this).
 inline size_t fft_smem_bytes(int N) { return (size_t)(N + N / 2) * 16; }
-// spreading products staged per pass of the column kernel, its shared memory and block size
-constexpr int kSpreadChunk = 4096;
-inline size_t hist_cols_smem_bytes(int L1) { return fft_smem_bytes(L1) + (size_t)kSpreadChunk * 8; }
-inline unsigned hist_cols_threads(int L1) { return L1 <= 512 ? 512u : (unsigned)L1; }
+// threads of a block of the one-launch step kernel
+constexpr int kStepThreads = 256;
 
 // Returns 0 or a negative wave1d_status; fills err with a message on failure.
 int build_host_plan(const double* x, const double* beta, int64_t M, int bc, double dt, int64_t Nt,
@@ -155,6 +153,7 @@ struct DevPlan {
     const double* deconv2;
     const double* twiddle;
     double* Sring;            // [W][K+1][2]
+    double* ftail;            // [K+1][4]: FIR tail (taps m >= 1) of h_k, g_k for the next step
     double* alpha;            // [K+1][2]
     double* alpha_p;          // [K+1][2]
     // NUFFT buffers
@@ -163,6 +162,7 @@ struct DevPlan {
     double* spec2;            // L complex, type-2 spectrum (inverse FFT input; zero outside |k| <= K)
     double* work;             // L complex (between FFT stages)
     double* rhs;              // M, right-hand sides of the block solve (internal order)
+    double* gforce;           // M, forcing g_j(t_{n+1}) computed ahead by the step kernel
     const int32_t* sp_i0;
     const double* sp_ker;
     const int32_t* rc_i0;
@@ -208,7 +208,7 @@ struct DevPlan {
     const int32_t* blk_members;
     const int64_t* blk_inv_off;
     const double* inv;
-    int64_t nblocks;
+    int64_t nblocks, inv_len;
     // outputs recorded per step (chunk history, caller order for sigma)
     double* rec_hist;         // [chunk][R]
     double* sig_hist;         // [chunk][M] or null
@@ -220,6 +220,10 @@ struct DevPlan {
     const double* rbc_dphi;
     double* rbc_uv;           // [4W][4] : u, v before; du, dv
     double rbc_h;
+    // one-launch step kernel: blocks [0, hist_blocks) start with the history pipeline;
+    // bar[0..15] are its work and barrier counters (zero between steps)
+    int hist_blocks;
+    unsigned* bar;
 };
 
 }  // namespace wave1d

@@ -26,6 +26,7 @@ WAVE1D_ECUDA = -4
 WAVE1D_ENONFINITE = -6
 WAVE1D_EDONE = -7
 WAVE1D_EUNSUPPORTED = -9
+WAVE1D_ETIMEOUT = -10
 
 WAVE1D_ARR_ALPHA = 0
 WAVE1D_ARR_ALPHA_P = 1
@@ -49,7 +50,8 @@ class wave1d_opts(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("gamma", ctypes.c_double), ("W", ctypes.c_int),
                 ("NL", ctypes.c_int), ("Ng", ctypes.c_int), ("nufft_w", ctypes.c_int),
                 ("rbc_period", ctypes.c_int), ("max_block", ctypes.c_int),
-                ("max_local_bytes", ctypes.c_int64), ("stream", ctypes.c_void_p)]
+                ("max_local_bytes", ctypes.c_int64), ("step_kernel", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
 
 
 class wave1d_info(ctypes.Structure):
