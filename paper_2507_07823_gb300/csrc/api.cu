@@ -194,15 +194,34 @@ int upload_receivers(wave1d_plan_t p) {
     d.r_src = it.src;
     d.r_w = it.w;
     if ((rc = zeros(p, &d.r_part, (size_t)std::max<int64_t>(1, d.r_nitems)))) return rc;
-    int64_t* i64b;
-    if ((rc = upload(p, hp.r0_ptr, &i64b))) return rc;
-    d.r0_ptr = i64b;
+    // items of the local sum in decreasing length, so the last items taken are short ones
+    {
+        const int64_t NL = d.l_nitems, NR = d.r_nitems;
+        std::vector<int32_t> order((size_t)(NL + NR));
+        auto len = [&](int32_t o) { return o < NL ? hp.litems.len[o] : hp.ritems.len[o - NL]; };
+        for (int64_t i = 0; i < NL + NR; i++) order[i] = (int32_t)i;
+        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return len(a) > len(b); });
+        int32_t* ob;
+        if ((rc = upload(p, order, &ob))) return rc;
+        d.item_order = ob;
+    }
+    // m = 0 terms padded to a whole number of warps per receiver
+    int64_t most = 0;
+    for (int64_t r = 0; r < d.R; r++) most = std::max(most, hp.r0_ptr[r + 1] - hp.r0_ptr[r]);
+    d.r0_stride = (int)((most + 31) / 32 * 32);
+    std::vector<int32_t> psrc((size_t)d.R * d.r0_stride, 0);
+    std::vector<double> pw((size_t)d.R * d.r0_stride, 0.0);
+    for (int64_t r = 0; r < d.R; r++)
+        for (int64_t e = hp.r0_ptr[r]; e < hp.r0_ptr[r + 1]; e++) {
+            psrc[(size_t)r * d.r0_stride + (e - hp.r0_ptr[r])] = hp.r0_src[e];
+            pw[(size_t)r * d.r0_stride + (e - hp.r0_ptr[r])] = hp.r0_w[e];
+        }
     int32_t* i32b;
-    if ((rc = upload(p, hp.r0_src, &i32b))) return rc;
-    d.r0_src = i32b;
+    if ((rc = upload(p, psrc, &i32b))) return rc;
+    d.r0p_src = i32b;
     double* f64b;
-    if ((rc = upload(p, hp.r0_w, &f64b))) return rc;
-    d.r0_w = f64b;
+    if ((rc = upload(p, pw, &f64b))) return rc;
+    d.r0p_w = f64b;
     if ((rc = zeros(p, &d.uHr, (size_t)std::max<int64_t>(1, d.R)))) return rc;
     if ((rc = zeros(p, &d.rec_hist, (size_t)p->chunk * std::max<int64_t>(1, d.R)))) return rc;
     return WAVE1D_OK;
@@ -276,8 +295,8 @@ int enqueue_step(wave1d_plan_t p, int64_t n, const double* g_ext, double* sig_hi
     k_hist_cols<<<P.L2, 256, cols_phase_smem(P.L1), s>>>(d, Y);
     mark(WAVE1D_STAGE_FFT_FWD);
     mark(WAVE1D_STAGE_MODES);
+    k_hist_tail<<<(P.K + 1 + kTailModes - 1) / kTailModes, 8 * kTailModes, 0, s>>>(d);
     k_hist_rows<<<P.L1 / 2 + 1, T, rows_phase_smem(P.L2), s>>>(d, Y, Tb, rbc ? 0 : 1);
-    k_hist_tail<<<(P.K + 1 + kTailModes - 1) / kTailModes, 4 * kTailModes, 0, s>>>(d);
     mark(WAVE1D_STAGE_RBC);
     if (rbc) {
         int npts = (int)p->hp.rbc_idx.size();
@@ -295,10 +314,10 @@ int enqueue_step(wave1d_plan_t p, int64_t n, const double* g_ext, double* sig_hi
         k_hist_icols<<<P.L2, tc, icols_phase_smem(P.L1), s>>>(d, Tb);
     }
     mark(WAVE1D_STAGE_INTERP);
-    k_interp<<<blocks(P.M + P.R, T), T, 0, s>>>(d);
+    k_interp<<<blocks(P.M + P.R, kInterpPoints), 2 * kInterpPoints, 0, s>>>(d);
     mark(WAVE1D_STAGE_SOLVE);
     if (fork) cudaStreamWaitEvent(s, p->ev_join, 0);
-    k_solve<<<blocks(d.nblocks * 32, T), T, 0, s>>>(d);
+    k_solve<<<blocks((d.n_sgroups + d.n_big) * 32, T), T, 0, s>>>(d);
     mark(WAVE1D_STAGE_RECEIVERS);      // the receivers are read out by the solve's last block
     mark(WAVE1D_NSTAGE);
     CK(cudaGetLastError());
@@ -468,8 +487,9 @@ int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double d
         int coop = 0;
         cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, p->device);
         int64_t grid = (int64_t)occ * p->sms;
-        // one history block per column / row pair, at most half of the blocks
-        int units = std::max(P.L2, P.L1 / 2 + 1);
+        // one history block per column / row pair / interpolation chunk, at most half the blocks
+        int64_t units = std::max<int64_t>(std::max(P.L2, P.L1 / 2 + 1),
+                                          (P.M + kInterpPoints - 1) / kInterpPoints);
         if (coop && occ > 0) {
             p->step_kernel = true;
             p->step_grid = (unsigned)grid;
@@ -554,6 +574,17 @@ int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double d
     UP(hp.blk_inv_off, blk_inv_off, i64);
     UP(hp.inv, inv, f64);
     d.nblocks = (int64_t)hp.blk_ptr.size() - 1;
+    UP(hp.sg_j, sg_j, i32);
+    UP(hp.sg_meta, sg_meta, i32);
+    UP(hp.sg_smax, sg_smax, i32);
+    UP(hp.sg_icnt, sg_icnt, i32);
+    UP(hp.big_row0, big_row0, i32);
+    UP(hp.sg_off, sg_off, i64);
+    UP(hp.sg_ip, sg_ip, i64);
+    UP(hp.big_blk, big_blk, i64);
+    UP(hp.sg_beta, sg_beta, f64);
+    d.n_sgroups = (int64_t)hp.sg_smax.size();
+    d.n_big = (int64_t)hp.big_blk.size();
     d.inv_len = (int64_t)hp.inv.size();
     UP(hp.rbc_idx, rbc_idx, i32);
     UP(hp.rbc_x, rbc_x, f64);

@@ -78,8 +78,11 @@ __device__ __forceinline__ void fft_lines(double2* a, double2* b, const double2*
             const double ac = x[2 * i1 + c];                          // own component of a[i1]
             const double ao = __shfl_xor_sync(0xffffffffu, ac, 1);   // the other one
             const double u = x[2 * i0 + c];
-            // c = 0: Re(w a) = w.x a.x - w.y a.y;  c = 1: Im(w a) = w.x a.y + w.y a.x
-            const double tc = c ? fma(w.x, ac, w.y * ao) : fma(w.x, ac, -(w.y * ao));
+            // c = 0: Re(w a) = w.x a.x - w.y a.y;  c = 1: Im(w a) = w.x a.y + w.y a.x.  The sign of
+            // w.y is flipped with an integer XOR, which keeps it off the FP64 pipe.
+            const double wy = __longlong_as_double(__double_as_longlong(w.y) ^
+                                                   (c ? 0ll : (long long)0x8000000000000000ull));
+            const double tc = fma(w.x, ac, wy * ao);
             x[2 * i0 + c] = u + tc;
             x[2 * i1 + c] = u - tc;
         }
@@ -111,9 +114,9 @@ __device__ __forceinline__ void write_type2(const DevPlan& P, int k, double2 a, 
 // One mode of the history update (eqs. hkcompdisc, alphakEvolutionFormulas), one thread per mode:
 //   S_k^n = deconv1_k E_k + deconv1_k e^{2 pi i k/nf} O_k  (E, O from the half-length FFT),
 //   h_k = dt p_k(0) S_k^n + tail_h,  g_k = dt q_k(0) S_k^n + tail_g,
-// where the tail (taps m = 1 .. W-1, which need only S^{< n}) was summed by fir_tail after the
-// previous step's mode update; then alpha, alpha' are rotated and driven.  Stores S_k^n, alpha_k,
-// alpha'_k and returns alpha_k^{n+1}.
+// where the tail (taps m = 1 .. W-1, which need only S^{< n}) was summed by fir_tail earlier in
+// the step; then alpha, alpha' are rotated and driven.  Stores S_k^n, alpha_k, alpha'_k and
+// returns alpha_k^{n+1}.
 // ---------------------------------------------------------------------------------------------
 __device__ __forceinline__ double2 mode_update(const DevPlan& P, int64_t n, int k, double2 zk, double2 zm) {
     const double* f = P.modefac + 8 * (int64_t)k;
@@ -124,13 +127,14 @@ __device__ __forceinline__ double2 mode_update(const DevPlan& P, int64_t n, int 
     const double2 a = al[k], ap = alp[k];
     const double cs = P.rot[3 * k], so = P.rot[3 * k + 1], ks = P.rot[3 * k + 2];
     const double2 w0 = ((const double2*)P.pq)[k];                 // dt (p_k(0), q_k(0))
-    const double4 tl = ((const double4*)P.ftail)[k];              // (tail_h, tail_g)
+    const double2 th = __ldcg((const double2*)P.ftail + 2 * k);   // tail_h
+    const double2 tg = __ldcg((const double2*)P.ftail + 2 * k + 1); // tail_g
     const double2 E = make_double2(0.5 * (zk.x + zm.x), 0.5 * (zk.y - zm.y));
     const double2 D = make_double2(0.5 * (zk.x - zm.x), 0.5 * (zk.y + zm.y));
     const double2 O = make_double2(D.y, -D.x);
     const double2 Sn = cadd(make_double2(f0 * E.x, f0 * E.y), cmul(make_double2(f1, f2), O));
-    const double2 h = make_double2(fma(w0.x, Sn.x, tl.x), fma(w0.x, Sn.y, tl.y));
-    const double2 g = make_double2(fma(w0.y, Sn.x, tl.z), fma(w0.y, Sn.y, tl.w));
+    const double2 h = make_double2(fma(w0.x, Sn.x, th.x), fma(w0.x, Sn.y, th.y));
+    const double2 g = make_double2(fma(w0.y, Sn.x, tg.x), fma(w0.y, Sn.y, tg.y));
     ((double2*)P.Sring)[(int64_t)ring_slot(n, P.W) * K1 + k] = Sn;
     const double2 an = make_double2(fma(a.x, cs, fma(ap.x, so, h.x)), fma(a.y, cs, fma(ap.y, so, h.y)));
     const double2 apn = make_double2(fma(ap.x, cs, fma(-a.x, ks, g.x)), fma(ap.y, cs, fma(-a.y, ks, g.y)));
@@ -140,55 +144,56 @@ __device__ __forceinline__ double2 mode_update(const DevPlan& P, int64_t n, int 
 }
 
 // ---------------------------------------------------------------------------------------------
-// FIR tail for step n+1 (eq. hkcompdisc without its m = 0 term), once S^n is stored:
-//   tail_h = sum_{m=1}^{W-1} dt p_k(m dt) S_k^{n+1-m},  tail_g likewise with q_k,
-// one quad of lanes per mode (lane q takes m = 1 + q, 5 + q, ...; the four partial sums are added
-// in a fixed tree), modes kbase + (threadIdx.x >> 2).  The ring S^{n+1-m} sits in slot
-// (n+1-m) mod W; slot n was written in this step (read through L2).
+// FIR tail of step n (eq. hkcompdisc without its m = 0 term), from earlier steps only:
+//   tail_h = sum_{m=1}^{W-1} dt p_k(m dt) S_k^{n-m},  tail_g likewise with q_k,
+// one octet of lanes per mode: lane q of the octet takes m = 1 + q, 9 + q, ... (five taps for
+// W <= 41, loaded at once), and the eight partial sums are added in a fixed tree.  S^{n-m} sits
+// in ring slot (n-m) mod W.  All 32 lanes of the warp call it (valid = false for padding lanes).
 // ---------------------------------------------------------------------------------------------
-constexpr int kTapBatch = 4;
+constexpr int kTapBatch = 5;
 
-__device__ __forceinline__ void fir_tail(const DevPlan& P, int64_t n, int kbase) {
-    const int q = threadIdx.x & 3;
-    const int k = kbase + (int)(threadIdx.x >> 2);
-    const bool valid = k <= P.K;
+__device__ __forceinline__ void fir_tail(const DevPlan& P, int64_t n, int k, bool valid) {
+    const int q = threadIdx.x & 7;
     const int kk = valid ? k : P.K;
     const int K1 = P.K + 1, W = P.W;
     const double2* Sring = (const double2*)P.Sring;
     const double2* pq = (const double2*)P.pq;
     double2 h = make_double2(0.0, 0.0), g = make_double2(0.0, 0.0);
-    int slot = ring_slot(n - q, W);            // slot of m = 1 + q: (n + 1 - m) mod W
-    for (int m0 = 1 + q; m0 < W; m0 += 4 * kTapBatch) {
+    int slot = ring_slot(n - 1 - q, W);        // slot of m = 1 + q: (n - m) mod W
+    for (int m0 = 1 + q; m0 < W; m0 += 8 * kTapBatch) {
         double2 Sv[kTapBatch], wv[kTapBatch];
 #pragma unroll
         for (int u = 0; u < kTapBatch; u++) {
-            int m = m0 + 4 * u;
-            int sl = slot - 4 * u;
+            int m = m0 + 8 * u;
+            int sl = slot - 8 * u;
             sl = sl < 0 ? sl + W : sl;
             if (m < W) {
-                Sv[u] = __ldcg(Sring + (int64_t)sl * K1 + kk);
+                Sv[u] = __ldg(Sring + (int64_t)sl * K1 + kk);
                 wv[u] = __ldg(pq + (int64_t)m * K1 + kk);
             }
         }
 #pragma unroll
         for (int u = 0; u < kTapBatch; u++) {
-            if (m0 + 4 * u < W) {
+            if (m0 + 8 * u < W) {
                 h.x = fma(wv[u].x, Sv[u].x, h.x);
                 h.y = fma(wv[u].x, Sv[u].y, h.y);
                 g.x = fma(wv[u].y, Sv[u].x, g.x);
                 g.y = fma(wv[u].y, Sv[u].y, g.y);
             }
         }
-        slot -= (4 * kTapBatch) % W;
+        slot -= (8 * kTapBatch) % W;
         slot = slot < 0 ? slot + W : slot;
     }
-    for (int o = 1; o < 4; o <<= 1) {
+    for (int o = 1; o < 8; o <<= 1) {
         h.x += __shfl_xor_sync(0xffffffffu, h.x, o);
         h.y += __shfl_xor_sync(0xffffffffu, h.y, o);
         g.x += __shfl_xor_sync(0xffffffffu, g.x, o);
         g.y += __shfl_xor_sync(0xffffffffu, g.y, o);
     }
-    if (valid && q == 0) ((double4*)P.ftail)[k] = make_double4(h.x, h.y, g.x, g.y);
+    if (valid && q == 0) {
+        ((double2*)P.ftail)[2 * k] = h;
+        ((double2*)P.ftail)[2 * k + 1] = g;
+    }
 }
 
 }  // namespace wave1d

@@ -20,8 +20,11 @@ __global__ void k_hist_rows(DevPlan P, const double2* __restrict__ Y, double2* _
     rows_phase(P, load_step(P), Y, T, blockIdx.x, do_inverse, smraw);
 }
 
-// FIR tail for the next step, kTailModes modes per block (256 threads)
-__global__ void k_hist_tail(DevPlan P) { fir_tail(P, load_step(P), blockIdx.x * kTailModes); }
+// FIR tail of the step (before the rows), kTailModes modes per block (256 threads)
+__global__ void k_hist_tail(DevPlan P) {
+    const int k = blockIdx.x * kTailModes + (int)(threadIdx.x >> 3);
+    fir_tail(P, load_step(P), k, k <= P.K);
+}
 
 __global__ void k_hist_icols(DevPlan P, const double2* __restrict__ T) {
     extern __shared__ __align__(16) unsigned char smraw[];

@@ -107,6 +107,17 @@ struct HostPlan {
     std::vector<int64_t> blk_inv_off;  // offset of each block's inverse in inv
     std::vector<double> inv;           // column-major inverses: inv[l * s + i] = inverse[i][l]
     int64_t max_block = 0;
+    // solve groups: consecutive blocks of at most 32 members packed into the 32 lanes of a warp
+    std::vector<int32_t> sg_j;         // [group][32]: spring of the lane, -1 for an idle lane
+    std::vector<int32_t> sg_meta;      // [group][32]: first lane of the lane's block | size << 8 |
+                                       //   row in the block << 16
+    std::vector<int64_t> sg_off;       // [group][32]: offset of the lane's block inverse in inv
+    std::vector<double> sg_beta;       // [group][32]: stiffness of the lane's spring
+    std::vector<int64_t> sg_ip;        // [group][32]: first local-sum item of the lane's row
+    std::vector<int32_t> sg_icnt;      // [group][32]: its number of items
+    std::vector<int32_t> sg_smax;      // [group]: largest block of the group
+    std::vector<int64_t> big_blk;      // blocks of more than 32 members, one entry per 32 rows
+    std::vector<int32_t> big_row0;     //   (a single entry above 256 members): first row
     // radiation projection: grid points i of the 2K-point grid that are rolled off
     std::vector<int32_t> rbc_idx;      // 4W grid indices
     std::vector<double> rbc_x;         // their positions
@@ -153,7 +164,7 @@ struct DevPlan {
     const double* deconv2;
     const double* twiddle;
     double* Sring;            // [W][K+1][2]
-    double* ftail;            // [K+1][4]: FIR tail (taps m >= 1) of h_k, g_k for the next step
+    double* ftail;            // [K+1][4]: FIR tail (taps m >= 1) of h_k, g_k of the step
     double* alpha;            // [K+1][2]
     double* alpha_p;          // [K+1][2]
     // NUFFT buffers
@@ -193,10 +204,12 @@ struct DevPlan {
     const float* r_w;
     double* l_part;               // per spring item: partial local sum
     double* r_part;               // per receiver item: partial local sum (m >= 1)
-    unsigned long long* item_ctr; // items handed out in this step (reset by the solve)
-    const int64_t* r0_ptr;        // receivers: m = 0 terms (sources closer than dt)
-    const int32_t* r0_src;
-    const double* r0_w;
+    unsigned long long* item_ctr; // items handed out in this step (reset once they are done)
+    const int32_t* item_order;    // spring then receiver items (o >= l_nitems: receiver item
+                                  //   o - l_nitems), longest first
+    int r0_stride;                // receivers: m = 0 terms (sources closer than dt), padded to
+    const int32_t* r0p_src;       //   r0_stride entries per receiver (zero weight on padding)
+    const double* r0p_w;
     // spreading matrix and per-mode factors
     const int32_t* g_ptr;
     const int32_t* g_src;
@@ -207,6 +220,16 @@ struct DevPlan {
     const int64_t* blk_ptr;
     const int32_t* blk_members;
     const int64_t* blk_inv_off;
+    const int32_t* sg_j;
+    const int32_t* sg_meta;
+    const int64_t* sg_off;
+    const double* sg_beta;
+    const int64_t* sg_ip;
+    const int32_t* sg_icnt;
+    const int32_t* sg_smax;
+    const int64_t* big_blk;
+    const int32_t* big_row0;
+    int64_t n_sgroups, n_big;
     const double* inv;
     int64_t nblocks, inv_len;
     // outputs recorded per step (chunk history, caller order for sigma)

@@ -143,8 +143,8 @@ __global__ void k_rbc_update(DevPlan P, int npts) {
 
 
 __global__ void k_interp(DevPlan P) {
-    interp_points(P, load_step(P), blockIdx.x * (int64_t)blockDim.x + threadIdx.x,
-                  (int64_t)gridDim.x * blockDim.x, nullptr);
+    const int64_t n = load_step(P), nchunks = (P.M + P.R + kInterpPoints - 1) / kInterpPoints;
+    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) interp_chunk(P, n, c, nullptr);
 }
 
 __global__ void __launch_bounds__(256) k_solve(DevPlan P) {
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(256) k_solve(DevPlan P) {
     int64_t n = load_step(P);
     int wid = threadIdx.x >> 5;
     if (blockIdx.x == 0 && threadIdx.x == 0) *P.item_ctr = 0ull;   // the step's local sums are done
-    solve_blocks(P, n, (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5,
+    solve_tasks(P, n, (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5,
                  ((int64_t)gridDim.x * blockDim.x) >> 5, srhs[wid]);
     // the block that finishes last reads out the receivers and advances the step counter (every
     // other block has stored its densities and read n before it counts itself done)

@@ -96,29 +96,33 @@ __device__ __forceinline__ void local_item(const float2* __restrict__ sig2, int6
     }
 }
 
-// one warp per item, items handed out by the atomic counter item_ctr (spring items, then receiver
-// items with m >= 1); the counter is reset once every item of the step is done
+// One warp per item, items handed out by the atomic counter item_ctr in item_order (spring and
+// receiver items together, longest first, so the last items taken are short); the counter is
+// reset once every item of the step is done.  Each item's partial sum, one warp reduction of the
+// lanes' compensated pairs, goes to l_part / r_part at the item's own index, so the rows sum
+// their items' partials later in item order, whatever order the items ran in.
 __device__ __forceinline__ void local_items_loop(const DevPlan& P, int64_t n) {
-    int lane = threadIdx.x & 31;
-    int q = ring_slot(n + 1, P.ring);
-    unsigned long long total = (unsigned long long)(P.l_nitems + P.r_nitems);
+    const int lane = threadIdx.x & 31;
+    const int q = ring_slot(n + 1, P.ring);
+    const unsigned long long total = (unsigned long long)(P.l_nitems + P.r_nitems);
     for (;;) {
         unsigned long long g = 0;
         if (lane == 0) g = atomicAdd(P.item_ctr, 1ull);
         g = __shfl_sync(0xffffffffu, g, 0);
         if (g >= total) break;
+        const int64_t o = __ldg(P.item_order + g);
         float sh = 0.f, sl = 0.f;
-        if (g < (unsigned long long)P.l_nitems) {
-            int sj = __ldcs(P.l_src + g * 32 + lane);
-            local_item((const float2*)P.sig2, P.M, P.ring, q, P.l_mfirst, P.l_s0[g], P.l_len[g],
-                       (const float4*)(P.l_w + 2 * P.l_wbase[g]) + lane, sj, sh, sl);
+        if (o < P.l_nitems) {
+            const int sj = __ldcs(P.l_src + o * 32 + lane);
+            local_item((const float2*)P.sig2, P.M, P.ring, q, P.l_mfirst, __ldg(P.l_s0 + o), __ldg(P.l_len + o),
+                       (const float4*)(P.l_w + 2 * __ldg(P.l_wbase + o)) + lane, sj, sh, sl);
             pair_warp_sum(sh, sl);
-            if (lane == 0) P.l_part[g] = (double)sh + (double)sl;
+            if (lane == 0) P.l_part[o] = (double)sh + (double)sl;
         } else {
-            int64_t it = (int64_t)g - P.l_nitems;
-            int sj = __ldcs(P.r_src + it * 32 + lane);
-            local_item((const float2*)P.sig2, P.M, P.ring, q, P.r_mfirst, P.r_s0[it], P.r_len[it],
-                       (const float4*)(P.r_w + 2 * P.r_wbase[it]) + lane, sj, sh, sl);
+            const int64_t it = o - P.l_nitems;
+            const int sj = __ldcs(P.r_src + it * 32 + lane);
+            local_item((const float2*)P.sig2, P.M, P.ring, q, P.r_mfirst, __ldg(P.r_s0 + it), __ldg(P.r_len + it),
+                       (const float4*)(P.r_w + 2 * __ldg(P.r_wbase + it)) + lane, sj, sh, sl);
             pair_warp_sum(sh, sl);
             if (lane == 0) P.r_part[it] = (double)sh + (double)sl;
         }
@@ -297,8 +301,8 @@ __device__ __forceinline__ void icols_phase(const DevPlan& P, const double2* T, 
     __syncthreads();
 }
 
-// modes per unit of the FIR tail (one quad of lanes per mode: a 256-thread block)
-constexpr int kTailModes = 64;
+// modes per block of the per-stage FIR tail kernel (one octet of lanes per mode, 256 threads)
+constexpr int kTailModes = 32;
 
 // ---------------------------------------------------------------------------------------------
 // incident forcing g_j(t) = beta_j f(x_j - t), f periodised over 2 pi in the periodic box (eq. gj).
@@ -337,44 +341,50 @@ __device__ __forceinline__ double forcing(const DevPlan& P, int64_t n, int64_t j
 // type-2 interpolation: u_H(x_t) = sum_{t'} G'[(i0 + t') mod nf] psi_{t,t'} for springs, then
 // receivers; for springs also the forcing and u_H part of the right-hand side of eq. linearSystem,
 // rhs_j = -g_j(t_{n+1}) - beta_j u_H(x_j), with g_j from gpre (computed ahead) or computed here.
-// Points t = first, first + stride, ...
+// One chunk = kInterpPoints points, two threads per point (the first ceil(w/2) taps and the
+// rest, each summed in tap order with its loads in one batch, then added), 256 threads.
 // ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ void interp_points(const DevPlan& P, int64_t n, int64_t first, int64_t stride,
-                                              const double* gpre) {
+constexpr int kInterpPoints = 128;
+
+__device__ __forceinline__ void interp_chunk(const DevPlan& P, int64_t n, int64_t chunk, const double* gpre) {
+    const int64_t t = chunk * kInterpPoints + (threadIdx.x >> 1);
+    const int half = threadIdx.x & 1;
     const int64_t total = P.M + P.R;
-    const int w = P.w, nf = P.nf;
-    for (int64_t t = first; t < total; t += stride) {
-        const bool spring = t < P.M;
-        const int64_t j = spring ? t : t - P.M;
-        const int i0 = spring ? __ldg(P.sp_i0 + j) : __ldg(P.rc_i0 + j);
-        const double* ker = spring ? P.sp_ker + j * w : P.rc_ker + j * w;
-        const double bj = spring ? __ldg(P.beta + j) : 0.0;
-        const double gj = (spring && gpre) ? __ldcg(gpre + j) : 0.0;
-        // taps in batches of 8, loaded before they are summed (in tap order)
-        double acc = 0.0;
-        for (int t0 = 0; t0 < w; t0 += 8) {
-            double gv[8], kv[8];
+    const int w = P.w, nf = P.nf, wh = (w + 1) >> 1;
+    const bool in = t < total;
+    const bool spring = t < P.M;
+    const int64_t j = spring ? t : t - P.M;
+    const int i0 = in ? (spring ? __ldg(P.sp_i0 + j) : __ldg(P.rc_i0 + j)) : 0;
+    const double* ker = spring ? P.sp_ker + j * w : P.rc_ker + j * w;
+    const double bj = (in && spring) ? __ldg(P.beta + j) : 0.0;
+    const double gj = (in && spring && gpre) ? __ldcg(gpre + j) : 0.0;
+    const int tb = half ? wh : 0, te = half ? w : wh;
+    double acc = 0.0;
+    for (int t0 = tb; t0 < te; t0 += 8) {
+        double gv[8], kv[8];
 #pragma unroll
-            for (int u = 0; u < 8; u++) {
-                int tt = t0 + u;
-                if (tt < w) {
-                    int i = i0 + tt;
-                    i = i >= nf ? i - nf : i;
-                    gv[u] = __ldcg(P.grid + i);
-                    kv[u] = __ldg(ker + tt);
-                }
+        for (int u = 0; u < 8; u++) {
+            int tt = t0 + u;
+            if (in && tt < te) {
+                int i = i0 + tt;
+                i = i >= nf ? i - nf : i;
+                gv[u] = __ldcg(P.grid + i);
+                kv[u] = __ldg(ker + tt);
             }
+        }
 #pragma unroll
-            for (int u = 0; u < 8; u++)
-                if (t0 + u < w) acc = fma(gv[u], kv[u], acc);
-        }
-        if (spring) {
-            P.uH[j] = acc;
-            const double g = gpre ? gj : forcing(P, n, j);
-            P.rhs[j] = -g - bj * acc;
-        } else {
-            P.uHr[j] = acc;
-        }
+        for (int u = 0; u < 8; u++)
+            if (in && t0 + u < te) acc = fma(gv[u], kv[u], acc);
+    }
+    const double other = __shfl_xor_sync(0xffffffffu, acc, 1);
+    if (!in || half) return;
+    acc = acc + other;
+    if (spring) {
+        P.uH[j] = acc;
+        const double g = gpre ? gj : forcing(P, n, j);
+        P.rhs[j] = -g - bj * acc;
+    } else {
+        P.uHr[j] = acc;
     }
 }
 
@@ -382,9 +392,9 @@ __device__ __forceinline__ void interp_points(const DevPlan& P, int64_t n, int64
 // Implicit solve of eq. linearSystem, -(I + S) sigma^{n+1} = g + (beta/2) c + beta u_H, with the
 // local sum c_j assembled from the partials of row j's items (kept for inspection).
 // ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ double rhs_of(const DevPlan& P, int j) {
-    int64_t a = __ldg(P.l_item_ptr + j), e = __ldg(P.l_item_ptr + j + 1);
-    double bj = __ldg(P.beta + j), rj = __ldcg(P.rhs + j);
+// rhs_j from the partials of row j's items [a, e), summed in item order (kept in clocal)
+__device__ __forceinline__ double rhs_items(const DevPlan& P, int j, int64_t a, int64_t e, double bj) {
+    const double rj = __ldcg(P.rhs + j);
     double c = 0.0;
     for (int64_t it = a; it < e; it += 8) {
         double v[8];
@@ -396,6 +406,10 @@ __device__ __forceinline__ double rhs_of(const DevPlan& P, int j) {
     }
     P.clocal[j] = c;
     return fma(-0.5 * bj, c, rj);
+}
+
+__device__ __forceinline__ double rhs_of(const DevPlan& P, int j) {
+    return rhs_items(P, j, __ldg(P.l_item_ptr + j), __ldg(P.l_item_ptr + j + 1), __ldg(P.beta + j));
 }
 
 __device__ __forceinline__ void store_sigma(const DevPlan& P, int64_t n, int j, double v) {
@@ -410,36 +424,77 @@ __device__ __forceinline__ void store_sigma(const DevPlan& P, int64_t n, int j, 
     if (P.sig_hist) P.sig_hist[(n % P.chunk) * P.M + P.perm[j]] = v;
 }
 
-// block solve sigma^{n+1} = (I + S)^{-1} rhs, one warp per block of springs closer than dt (blocks
-// b = first, first + stride, ...).  The inverse is stored column-major (invT[l * s + i] =
-// inv[i][l]) so lanes read it contiguously; blocks of up to kSolveStage members stage their
-// right-hand sides in the warp's srhs (kSolveStage doubles of shared memory).
+// block solve sigma^{n+1} = (I + S)^{-1} rhs.  The inverse of each block of springs closer than
+// dt is stored column-major (invT[l * s + i] = inv[i][l]).  Tasks t = first, first + stride, ...
+// (one warp each):
+//   t < n_sgroups  a solve group: consecutive blocks of at most 32 members packed into the warp's
+//                  lanes (lane = one row); the right-hand sides of a block pass between its lanes
+//                  by shuffles, so every FP64 instruction works on up to 32 rows at once
+//   otherwise      32 rows of a block of more than 32 members (big_row0 gives the first row);
+//                  blocks of up to kSolveStage members stage all their right-hand sides in the
+//                  warp's srhs (kSolveStage doubles of shared memory); larger blocks have one
+//                  task, which forms the right-hand side in place in P.rhs
+// Each row sums over l = 0 .. s-1 in order, even l into one accumulator and odd l into another.
 constexpr int kSolveStage = 256;
+constexpr int kSolveBatch = 16;
 
-__device__ __forceinline__ void solve_blocks(const DevPlan& P, int64_t n, int64_t first, int64_t stride,
-                                             double* srhs) {
+__device__ __forceinline__ void solve_tasks(const DevPlan& P, int64_t n, int64_t first, int64_t stride,
+                                            double* srhs) {
     const int lane = threadIdx.x & 31;
-    for (int64_t b = first; b < P.nblocks; b += stride) {
-        int64_t m0 = __ldg(P.blk_ptr + b);
-        int s = (int)(__ldg(P.blk_ptr + b + 1) - m0);
+    for (int64_t task = first; task < P.n_sgroups + P.n_big; task += stride) {
+        if (task < P.n_sgroups) {
+            const int64_t e = task * 32 + lane;
+            const int j = __ldg(P.sg_j + e);
+            const int meta = __ldg(P.sg_meta + e);
+            const double* invT = P.inv + __ldg(P.sg_off + e);
+            const int smax = __ldg(P.sg_smax + task);
+            const double bj = __ldg(P.sg_beta + e);
+            const int64_t ip = __ldg(P.sg_ip + e);
+            const int icnt = __ldg(P.sg_icnt + e);
+            const int b0 = meta & 255, s = (meta >> 8) & 255, i = meta >> 16;
+            const double r = j >= 0 ? rhs_items(P, j, ip, ip + icnt, bj) : 0.0;
+            double a0 = 0.0, a1 = 0.0;
+            for (int l0 = 0; l0 < smax; l0 += kSolveBatch) {
+                double v[kSolveBatch];
+#pragma unroll
+                for (int u = 0; u < kSolveBatch; u++) v[u] = l0 + u < s ? __ldg(invT + (int64_t)(l0 + u) * s + i) : 0.0;
+#pragma unroll
+                for (int u = 0; u < kSolveBatch; u += 2) {
+                    const double r0 = __shfl_sync(0xffffffffu, r, min(b0 + l0 + u, 31));
+                    const double r1 = __shfl_sync(0xffffffffu, r, min(b0 + l0 + u + 1, 31));
+                    if (l0 + u < s) a0 = fma(v[u], r0, a0);
+                    if (l0 + u + 1 < s) a1 = fma(v[u + 1], r1, a1);
+                }
+            }
+            if (j >= 0) store_sigma(P, n, j, a0 + a1);
+            continue;
+        }
+        const int64_t bt = task - P.n_sgroups;
+        const int64_t b = __ldg(P.big_blk + bt);
+        const int r0 = __ldg(P.big_row0 + bt);
+        const int64_t m0 = __ldg(P.blk_ptr + b);
+        const int s = (int)(__ldg(P.blk_ptr + b + 1) - m0);
         const double* invT = P.inv + __ldg(P.blk_inv_off + b);
         if (s <= kSolveStage) {
-            // the first four inverse entries of the lane's first row load with the members
-            double pre[4];
-#pragma unroll
-            for (int u = 0; u < 4; u++) pre[u] = (lane < s && u < s) ? __ldg(invT + (int64_t)u * s + lane) : 0.0;
-            for (int i = lane; i < s; i += 32) srhs[i] = rhs_of(P, __ldg(P.blk_members + m0 + i));
+            for (int l0 = 0; l0 < s; l0 += 64) {           // two rows per lane per pass
+                const int la = l0 + lane, lb = l0 + 32 + lane;
+                const int ja = la < s ? __ldg(P.blk_members + m0 + la) : 0;
+                const int jb = lb < s ? __ldg(P.blk_members + m0 + lb) : 0;
+                const double ra = la < s ? rhs_of(P, ja) : 0.0;
+                const double rb = lb < s ? rhs_of(P, jb) : 0.0;
+                if (la < s) srhs[la] = ra;
+                if (lb < s) srhs[lb] = rb;
+            }
             __syncwarp();
-            for (int i = lane; i < s; i += 32) {
+            const int i = r0 + lane;
+            if (i < s) {
                 double a0 = 0.0, a1 = 0.0;
-                for (int l0 = 0; l0 < s; l0 += 8) {
-                    double v[8];
+                for (int l0 = 0; l0 < s; l0 += kSolveBatch) {
+                    double v[kSolveBatch];
 #pragma unroll
-                    for (int u = 0; u < 8; u++)
-                        v[u] = (l0 == 0 && u < 4 && i == lane) ? pre[u]
-                                                               : (l0 + u < s ? __ldg(invT + (int64_t)(l0 + u) * s + i) : 0.0);
+                    for (int u = 0; u < kSolveBatch; u++) v[u] = l0 + u < s ? __ldg(invT + (int64_t)(l0 + u) * s + i) : 0.0;
 #pragma unroll
-                    for (int u = 0; u < 8; u += 2) {
+                    for (int u = 0; u < kSolveBatch; u += 2) {
                         if (l0 + u < s) a0 = fma(v[u], srhs[l0 + u], a0);
                         if (l0 + u + 1 < s) a1 = fma(v[u + 1], srhs[l0 + u + 1], a1);
                     }
@@ -448,36 +503,47 @@ __device__ __forceinline__ void solve_blocks(const DevPlan& P, int64_t n, int64_
             }
             __syncwarp();
         } else {
-            // large blocks: the full right-hand side is formed in place in P.rhs first
+            // very large blocks (one task): the full right-hand side is formed in place in P.rhs
             for (int i = lane; i < s; i += 32) {
                 int j = __ldg(P.blk_members + m0 + i);
                 P.rhs[j] = rhs_of(P, j);
             }
             __syncwarp();
             for (int i = lane; i < s; i += 32) {
-                double acc = 0.0;
-                for (int l = 0; l < s; l++)
-                    acc = fma(__ldg(invT + (int64_t)l * s + i), __ldcg(P.rhs + __ldg(P.blk_members + m0 + l)), acc);
-                store_sigma(P, n, __ldg(P.blk_members + m0 + i), acc);
+                double a0 = 0.0, a1 = 0.0;
+                for (int l = 0; l < s; l++) {
+                    const double x = __ldg(invT + (int64_t)l * s + i);
+                    const double rl = __ldcg(P.rhs + __ldg(P.blk_members + m0 + l));
+                    if (l & 1) a1 = fma(x, rl, a1);
+                    else a0 = fma(x, rl, a0);
+                }
+                store_sigma(P, n, __ldg(P.blk_members + m0 + i), a0 + a1);
             }
             __syncwarp();
         }
     }
 }
 
-// receivers, after every density of the step is stored: u = 1/2 (sum of the m >= 1 item partials
-// + sum over sources closer than dt of Q_0 sigma^{n+1}) + u_H; one warp per receiver, run by the
-// block that finishes the step last.
+// receivers, after every density of the step is stored: u = 1/2 (sum of the receiver row's item
+// partials (m >= 1) + sum over sources closer than dt of Q_0 sigma^{n+1}) + u_H; one warp per
+// receiver, the m = 0 terms padded to r0_stride lanes (zero weight on padding), run by the block
+// that finishes the step last.
 __device__ __forceinline__ void receivers_readout(const DevPlan& P, int64_t n) {
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const double* s1 = P.sig + (int64_t)ring_slot(n + 1, P.ring) * P.M;
     for (int64_t r = wid; r < P.R; r += nwarps) {
+        const double uh = __ldcg(P.uHr + r);
+        double cr = 0.0;
+        for (int64_t it = __ldg(P.r_item_ptr + r) + lane; it < __ldg(P.r_item_ptr + r + 1); it += 32)
+            cr += __ldcg(P.r_part + it);
         double acc = 0.0;
-        for (int64_t it = P.r_item_ptr[r] + lane; it < P.r_item_ptr[r + 1]; it += 32) acc += __ldcg(P.r_part + it);
-        for (int64_t e = P.r0_ptr[r] + lane; e < P.r0_ptr[r + 1]; e += 32)
-            acc = fma(P.r0_w[e], __ldcg(s1 + P.r0_src[e]), acc);
+        for (int e = lane; e < P.r0_stride; e += 32) {
+            const int64_t idx = r * P.r0_stride + e;
+            acc = fma(__ldg(P.r0p_w + idx), __ldcg(s1 + __ldg(P.r0p_src + idx)), acc);
+        }
+        cr = warp_sum(cr);
         acc = warp_sum(acc);
-        if (lane == 0) P.rec_hist[(n % P.chunk) * P.R + r] = 0.5 * acc + __ldcg(P.uHr + r);
+        if (lane == 0) P.rec_hist[(n % P.chunk) * P.R + r] = 0.5 * (cr + acc) + uh;
     }
 }
 

@@ -636,6 +636,52 @@ int build_host_plan(const double* x_in, const double* beta_in, int64_t M, int bc
             }
         });
         if (bad) { err = "singular block of I + S"; return WAVE1D_EINVAL; }
+        // pack consecutive blocks of at most 32 members into warps of 32 lanes; larger blocks
+        // are split into tasks of 32 rows (one task above 256 members)
+        hp.sg_j.clear();
+        hp.sg_meta.clear();
+        hp.sg_off.clear();
+        hp.sg_beta.clear();
+        hp.sg_ip.clear();
+        hp.sg_icnt.clear();
+        hp.sg_smax.clear();
+        hp.big_blk.clear();
+        hp.big_row0.clear();
+        int used = 32;
+        for (int64_t b = 0; b < nb; b++) {
+            int64_t sz = hp.blk_ptr[b + 1] - hp.blk_ptr[b];
+            if (sz > 32) {
+                for (int64_t r0 = 0; r0 < sz; r0 += 32) {
+                    hp.big_blk.push_back(b);
+                    hp.big_row0.push_back((int32_t)r0);
+                    if (sz > 256) break;
+                }
+                continue;
+            }
+            if (used + sz > 32) {
+                hp.sg_j.insert(hp.sg_j.end(), 32, -1);
+                hp.sg_meta.insert(hp.sg_meta.end(), 32, 0);
+                hp.sg_off.insert(hp.sg_off.end(), 32, 0);
+                hp.sg_beta.insert(hp.sg_beta.end(), 32, 0.0);
+                hp.sg_ip.insert(hp.sg_ip.end(), 32, 0);
+                hp.sg_icnt.insert(hp.sg_icnt.end(), 32, 0);
+                hp.sg_smax.push_back(0);
+                used = 0;
+            }
+            size_t g = hp.sg_smax.size() - 1;
+            for (int64_t i = 0; i < sz; i++) {
+                size_t lane = g * 32 + used + i;
+                int32_t j = hp.blk_members[hp.blk_ptr[b] + i];
+                hp.sg_j[lane] = j;
+                hp.sg_meta[lane] = used | (int)(sz << 8) | (int)(i << 16);
+                hp.sg_off[lane] = hp.blk_inv_off[b];
+                hp.sg_beta[lane] = hp.beta[j];
+                hp.sg_ip[lane] = hp.litems.item_ptr[j];
+                hp.sg_icnt[lane] = (int32_t)(hp.litems.item_ptr[j + 1] - hp.litems.item_ptr[j]);
+            }
+            hp.sg_smax[g] = std::max<int32_t>(hp.sg_smax[g], (int32_t)sz);
+            used += (int)sz;
+        }
     }
 
     // radiation projection tables (Sec. 4.4): grid x_i = i h (i < K), (i - 2K) h (i >= K)
