@@ -32,6 +32,11 @@ if ROOT not in sys.path:
 METRIC = "scatterer-steps/s (M*N_t/s) at stated error vs FP64 oracle; % of HBM roofline"
 UNIT = "scatterer-steps/s"
 L2_FLUSH_BYTES = 512 << 20
+# DRAM bytes (read + write) of one k_step launch at this workload, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel sources it was taken
+# with: reported as roofline.traffic while their SHA-256 matches, else null
+STEP_KERNEL_SOURCES = ["step.cu", "phases.cuh", "device_common.cuh", "internal.h"]
+STEP_TRAFFIC = {"sources_sha256": "13f81524b1f7f23ee3bc3ed344078df96465877e9cb045f2d7dc0d2979f4ad1a", "bytes_per_launch": 317778176 + 4285952}
 L2_CLEAN_BYTES = 256 << 20
 
 
@@ -121,7 +126,7 @@ def run_ours(args):
     assert Wm >= 3
     stream = torch.cuda.current_stream()
     t_plan = time.perf_counter()
-    plan = wave1d.Plan.from_workload(w.with_(Nt=Wm + 3 * K + 16), stream=stream.cuda_stream)
+    plan = wave1d.Plan.from_workload(w.with_(Nt=Wm + 4 * K + 16), stream=stream.cuda_stream)
     t_plan = time.perf_counter() - t_plan
     info = plan.info
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -154,6 +159,11 @@ def run_ours(args):
         wall = time.perf_counter() - t0
     ms_steps = [a.elapsed_time(b) for a, b in evs]
     ms_total = float(sum(ms_steps))
+    # ordinary steps run as one launch of the step kernel; projection steps (every rbc_period-th)
+    # as 10 per-stage launches
+    rbc = [((Wm + i + 1) % info.rbc_period) == 0 for i in range(K)]
+    ms_ordinary = [m for m, r in zip(ms_steps, rbc) if not r]
+    n_rbc = sum(rbc)
     if world > 1:
         import torch.distributed as dist
         tt = torch.tensor([ms_total], device="cuda")
@@ -161,6 +171,17 @@ def run_ours(args):
         ms_total = float(tt.item())
         dist.barrier()
     value = w.M * K * world / (ms_total * 1e-3)
+
+    # --- the same march without the L2 flush (steady state: each step streams the 303 MB of
+    # local weights, more than the 126 MB L2, through it anyway) ------------------------------------
+    evs2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    torch.cuda.synchronize()
+    for i in range(K):
+        evs2[i][0].record(stream)
+        wave1d._check(wave1d.wave1d_step(plan.h), "wave1d_step")
+        evs2[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms_warm = float(sum(a.elapsed_time(b) for a, b in evs2))
 
     # --- per-stage device times (CUDA events between the stages, same plan, K steps) --------
     wave1d.wave1d_profile(plan.h, 1)
@@ -170,7 +191,6 @@ def run_ours(args):
     stage_ms, nprof = wave1d.wave1d_profile_read(plan.h)
     wave1d.wave1d_profile(plan.h, 0)
     per_step = {s: float(stage_ms[i] / nprof) for i, s in enumerate(wave1d.STAGES)}
-    top = max(per_step, key=per_step.get)
 
     # --- end to end through the public API with host buffers ------------------------------------
     # forcing g_j(t_{n+1}) = beta_j f(x_j - t_{n+1}) supplied from pinned host memory every step,
@@ -194,15 +214,20 @@ def run_ours(args):
     e2e_value = w.M * K * world / e2e_s
     del n0
 
-    # --- roofline of the dominant kernel -------------------------------------------------------
+    # --- roofline of the timed kernel: the one-launch step kernel -------------------------------
+    # algorithmic bytes per launch: the local-sum stream (stored weights as FP32 pairs, source
+    # lists, item headers, partial sums), which the step must read once; the history and solve
+    # state (a few MB, mostly L2-resident) is not counted
     hbm, peak_kind = _peaks()
-    bytes_per_step = stage_bytes(info, w, top)
-    achieved = bytes_per_step / (per_step[top] * 1e-3) / 1e9 if bytes_per_step else None
-    roof = {"kernel": top, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": (achieved / hbm) if achieved else None, "traffic": None,
+    bytes_per_step = stage_bytes(info, w, "local")
+    ms_k = float(np.mean(ms_ordinary))
+    achieved = bytes_per_step / (ms_k * 1e-3) / 1e9
+    roof = {"kernel": "k_step", "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": step_traffic(),
             "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s",
-            "algorithmic_bytes_per_launch": bytes_per_step}
-    launches = 13 * K + (K // info.rbc_period + 1) * 2
+            "algorithmic_bytes_per_launch": bytes_per_step,
+            "launch_ms": ms_k, "launches_averaged": len(ms_ordinary)}
+    launches = len(ms_ordinary) + 10 * n_rbc
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
@@ -213,9 +238,11 @@ def run_ours(args):
                    "nf": info.nf, "local_pairs": info.local_pairs,
                    "local_weights": info.local_weights, "local_bytes": info.local_bytes,
                    "parallelism": f"replicas x{world}",
-                   "l2": "flushed before every timed step (512 MiB write, then 256 MiB read)",
+                   "l2": "flushed before every timed step (512 MiB write, then 256 MiB read); "
+                         "value_without_l2_flush: the same steps back to back",
                    "plan_seconds": t_plan},
-        "stage_ms_per_step": per_step,
+        "value_without_l2_flush": w.M * K * world / (ms_warm * 1e-3),
+        "stage_ms_per_step_per_stage_launches": per_step,
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * w.M,
                 "d2h_bytes_per_step": 8 * w.M},
@@ -231,6 +258,16 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def step_traffic():
+    import hashlib
+    h = hashlib.sha256()
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2507_07823_gb300", "csrc")
+    for f in STEP_KERNEL_SOURCES:
+        with open(os.path.join(src, f), "rb") as fh:
+            h.update(fh.read())
+    return STEP_TRAFFIC["bytes_per_launch"] if h.hexdigest() == STEP_TRAFFIC["sources_sha256"] else None
 
 
 def stage_bytes(info, w, stage):
