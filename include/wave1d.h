@@ -190,6 +190,25 @@ int wave1d_profile(wave1d_plan_t plan, int enable);
 int wave1d_profile_read(wave1d_plan_t plan, double* ms, int nstage, int64_t* steps);
 
 /*
+ * Checkpoint and resume (no equation of the paper: the march's state between two steps).  The
+ * state is what evolves with the march: the step counter, the latched status word, the density
+ * rings (the last m_max + 1 steps of sigma, which the local part and the history part read), the
+ * Fourier coefficients alpha, alpha' with the last W steps of S_k (eq. hkcompdisc), and the
+ * receiver history of the current chunk.  Everything else is fixed by the plan's inputs.
+ *   wave1d_state_size: *bytes = size of a state buffer for this plan.
+ *   wave1d_state_save: buf: host memory of at least that size, written after the plan's queued
+ *                      work has finished (synchronises the plan's stream).
+ *   wave1d_state_load: buf: a buffer written by wave1d_state_save from a plan built with the same
+ *                      inputs (positions, stiffnesses, bc, dt, tol, options, receivers); the plan
+ *                      continues from the saved step.  WAVE1D_EINVAL if the buffer is too small,
+ *                      not a state buffer, from a plan of other sizes, or past this plan's Nt.
+ * The caller owns buf.  A resumed march reproduces the uninterrupted one bit for bit.
+ */
+int wave1d_state_size(wave1d_plan_t plan, size_t* bytes);
+int wave1d_state_save(wave1d_plan_t plan, void* buf, size_t bytes);
+int wave1d_state_load(wave1d_plan_t plan, const void* buf, size_t bytes);
+
+/*
  * Type-1 NUFFT of device arrays without any memory allocation (the paper has no counterpart; it
  * is a service for callers that cannot allocate device memory — code running under a memory
  * budget reserved up front, or in a loop that must not take the implicit device synchronisation

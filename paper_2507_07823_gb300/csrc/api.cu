@@ -728,6 +728,115 @@ int wave1d_get_sigma(wave1d_plan_t p, double* out, int on_device) {
     return check_status(p);
 }
 
+// ---------------------------------------------------------------------------------------------
+// checkpoint / resume: the state that evolves with the march (step counter, status word, density
+// rings, mode coefficients and their S history, receiver history), behind a header that names
+// the plan's sizes.  Everything else a step uses is either fixed by the plan or rebuilt each step.
+// ---------------------------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+
+struct StateHeader {
+    char magic[8];
+    uint32_t version, reserved;
+    int64_t M, R, K, W, ring, chunk, n;
+    int32_t status, pad;
+};
+
+struct StatePart {
+    void* dev;
+    size_t bytes;
+};
+
+std::vector<StatePart> state_parts(wave1d_plan_t p) {
+    const Params& P = p->hp.P;
+    const DevPlan& d = p->dp;
+    const size_t K1 = (size_t)P.K + 1;
+    return {{d.sig, sizeof(double) * (size_t)P.ring * P.M},
+            {d.sig2, sizeof(float) * 4 * (size_t)P.ring * P.M},
+            {d.Sring, sizeof(double) * 2 * (size_t)P.W * K1},
+            {d.alpha, sizeof(double) * 2 * K1},
+            {d.alpha_p, sizeof(double) * 2 * K1},
+            {d.rec_hist, sizeof(double) * (size_t)p->chunk * std::max<int64_t>(1, d.R)}};
+}
+
+void fill_header(wave1d_plan_t p, StateHeader& h) {
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, "WAVE1DS", 8);
+    h.version = 1;
+    h.M = p->hp.P.M;
+    h.R = p->dp.R;
+    h.K = p->hp.P.K;
+    h.W = p->hp.P.W;
+    h.ring = p->hp.P.ring;
+    h.chunk = p->chunk;
+    h.n = p->n;
+}
+
+}  // namespace
+
+extern "C" {
+
+int wave1d_state_size(wave1d_plan_t p, size_t* bytes) {
+    if (!p || !bytes) return fail(WAVE1D_EINVAL, "bad arguments");
+    size_t b = sizeof(StateHeader);
+    for (const StatePart& s : state_parts(p)) b += s.bytes;
+    *bytes = b;
+    return WAVE1D_OK;
+}
+
+int wave1d_state_save(wave1d_plan_t p, void* buf, size_t bytes) {
+    if (!p || !buf) return fail(WAVE1D_EINVAL, "bad arguments");
+    size_t need = 0;
+    wave1d_state_size(p, &need);
+    if (bytes < need) return fail(WAVE1D_EINVAL, "state buffer smaller than wave1d_state_size");
+    int rc = enter(p);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(p->s));
+    StateHeader h;
+    fill_header(p, h);
+    CK(cudaMemcpy(&h.status, p->dp.status, sizeof(int), cudaMemcpyDeviceToHost));
+    char* out = (char*)buf;
+    std::memcpy(out, &h, sizeof(h));
+    out += sizeof(h);
+    for (const StatePart& s : state_parts(p)) {
+        CK(cudaMemcpy(out, s.dev, s.bytes, cudaMemcpyDeviceToHost));
+        out += s.bytes;
+    }
+    return leave(p);
+}
+
+int wave1d_state_load(wave1d_plan_t p, const void* buf, size_t bytes) {
+    if (!p || !buf) return fail(WAVE1D_EINVAL, "bad arguments");
+    size_t need = 0;
+    wave1d_state_size(p, &need);
+    if (bytes < need) return fail(WAVE1D_EINVAL, "state buffer smaller than wave1d_state_size");
+    StateHeader h, mine;
+    std::memcpy(&h, buf, sizeof(h));
+    fill_header(p, mine);
+    if (std::memcmp(h.magic, mine.magic, 8) != 0 || h.version != mine.version)
+        return fail(WAVE1D_EINVAL, "not a wave1d state buffer of this version");
+    if (h.M != mine.M || h.R != mine.R || h.K != mine.K || h.W != mine.W || h.ring != mine.ring ||
+        h.chunk != mine.chunk)
+        return fail(WAVE1D_EINVAL, "state was saved from a plan of other sizes");
+    if (h.n < 0 || h.n > p->hp.P.Nt) return fail(WAVE1D_EINVAL, "saved step beyond the Nt of this plan");
+    int rc = enter(p);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(p->s));
+    const char* in = (const char*)buf + sizeof(h);
+    for (const StatePart& s : state_parts(p)) {
+        CK(cudaMemcpy(s.dev, in, s.bytes, cudaMemcpyHostToDevice));
+        in += s.bytes;
+    }
+    int64_t step[2] = {h.n, 0};
+    CK(cudaMemcpy(p->dp.step, step, sizeof(step), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(p->dp.status, &h.status, sizeof(int), cudaMemcpyHostToDevice));
+    p->n = h.n;
+    p->started = true;
+    return leave(p);
+}
+
 int wave1d_sync(wave1d_plan_t p) {
     if (!p) return fail(WAVE1D_EINVAL, "plan is NULL");
     int rc = enter(p);

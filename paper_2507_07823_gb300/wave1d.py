@@ -40,7 +40,7 @@ EXPORTED = ["wave1d_opts_default", "wave1d_plan", "wave1d_set_incident_gaussians
             "wave1d_set_receivers", "wave1d_step", "wave1d_solve", "wave1d_read_receivers",
             "wave1d_get_sigma", "wave1d_sync", "wave1d_get_info", "wave1d_inspect",
             "wave1d_destroy", "wave1d_strerror", "wave1d_profile", "wave1d_profile_read",
-            "wave1d_nufft1_noalloc"]
+            "wave1d_nufft1_noalloc", "wave1d_state_size", "wave1d_state_save", "wave1d_state_load"]
 
 WAVE1D_NSTAGE = 9
 STAGES = ["local", "spread", "fft_fwd", "modes", "rbc", "fft_inv", "interp", "solve", "receivers"]
@@ -99,6 +99,9 @@ def lib(path: str = LIB_PATH):
         L.wave1d_profile_read.argtypes = [P, _D, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)]
         L.wave1d_nufft1_noalloc.argtypes = [_D, _D, ctypes.c_int64, ctypes.c_int, ctypes.c_double,
                                             _D, ctypes.c_void_p]
+        L.wave1d_state_size.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+        L.wave1d_state_save.argtypes = [P, ctypes.c_void_p, ctypes.c_size_t]
+        L.wave1d_state_load.argtypes = [P, ctypes.c_void_p, ctypes.c_size_t]
         L.wave1d_strerror.argtypes = [ctypes.c_int]
         L.wave1d_strerror.restype = ctypes.c_char_p
         for name in EXPORTED:
@@ -165,6 +168,21 @@ def wave1d_solve(plan, nsteps, u_rec, sigma, out_on_device):
     f = _dptr if out_on_device else _hptr
     return lib().wave1d_solve(plan, int(nsteps), f(u_rec) if u_rec is not None else None,
                               f(sigma) if sigma is not None else None, int(out_on_device))
+
+
+def wave1d_state_size(plan):
+    n = ctypes.c_size_t(0)
+    _check(lib().wave1d_state_size(plan, ctypes.byref(n)), "wave1d_state_size")
+    return n.value
+
+
+def wave1d_state_save(plan, buf):
+    """buf: a contiguous numpy uint8 array of at least wave1d_state_size(plan) bytes."""
+    return lib().wave1d_state_save(plan, buf.ctypes.data_as(ctypes.c_void_p), buf.nbytes)
+
+
+def wave1d_state_load(plan, buf):
+    return lib().wave1d_state_load(plan, buf.ctypes.data_as(ctypes.c_void_p), buf.nbytes)
 
 
 def wave1d_read_receivers(plan, u, on_device):

@@ -137,6 +137,32 @@ def test_step_kernel_matches_per_stage_launches():
     assert np.array_equal(s1, s2) and np.array_equal(u1, u2)
 
 
+def test_checkpoint_resume_is_bitwise():
+    """wave1d_state_save after 150 steps, wave1d_state_load into a fresh plan built from the same
+    inputs, 150 more steps: bit for bit the uninterrupted 300-step march (free space, projection
+    steps on both sides of the checkpoint); a buffer from a plan of other sizes is refused."""
+    w = W.make("ckpt", M=300, bc=W.FREE, dt=4e-3, Nt=300, tol=1e-10, p=6, seed=11,
+               beta_range=(0.5, 20.0), beta_dist="loguniform", amp=(1.0,), center=(-math.pi - 0.4,),
+               width=(0.05,), R=3, margin=0.6)
+    a = wave1d.Plan.from_workload(w)
+    s_all, u_all = a.solve(300)
+    b = wave1d.Plan.from_workload(w)
+    s1, u1 = b.solve(150)
+    buf = np.zeros(wave1d.wave1d_state_size(b.h), dtype=np.uint8)
+    wave1d._check(wave1d.wave1d_state_save(b.h, buf), "wave1d_state_save")
+    b.close()
+    c = wave1d.Plan.from_workload(w)
+    wave1d._check(wave1d.wave1d_state_load(c.h, buf), "wave1d_state_load")
+    s2, u2 = c.solve(150)
+    assert np.array_equal(np.vstack([s1, s2]), s_all) and np.array_equal(np.vstack([u1, u2]), u_all)
+    assert np.max(np.abs(s_all[150:])) > 1e-6          # the pulse has reached the springs
+    other = wave1d.Plan.from_workload(w.with_(x=w.x[:-1], beta=w.beta[:-1]))
+    assert wave1d.wave1d_state_load(other.h, buf) == wave1d.WAVE1D_EINVAL
+    other.close()
+    a.close()
+    c.close()
+
+
 def test_host_forcing_matches_incident_forcing():
     """wave1d_step with g from the host reproduces the incident-wave forcing (eq. gj)."""
     w = W.config0(Nt=200)
