@@ -209,6 +209,37 @@ int wave1d_state_save(wave1d_plan_t plan, void* buf, size_t bytes);
 int wave1d_state_load(wave1d_plan_t plan, const void* buf, size_t bytes);
 
 /*
+ * Standalone NUFFTs of the history part (Sec. 3.1) on fixed points, with the time-step plan's
+ * Kaiser-Bessel kernel (eq. KB), fine grid and deconvolution:
+ *   type-1 (eq. densco):       S_k = (1/2 pi) sum_j c_j e^{+i k x_j},  k = 0..K
+ *   type-2 (eq. historySol1):  u_j = sum_{|k| <= K} alpha_k e^{-i k x_j},  alpha_{-k} = conj(alpha_k)
+ * and their spreading (A1: grid G from c) and interpolation (A6: u from a grid) passes alone.
+ *   wave1d_nufft_plan: x host, M positions (wrapped into [-pi, pi)); tol sets the kernel width as
+ *       in wave1d_plan; precision 0 = FP64 (kernel weights precomputed), 1 = mixed (kernel values
+ *       from FP32 polynomials fitted to about 1e-7 of the kernel's peak, compensated FP32 sums, FP64
+ *       FFT and deconvolution; for tol >= 1e-6).  stream: cudaStream_t of every call (NULL =
+ *       legacy default stream).  Allocates the plan's device arrays.
+ *   Point arrays (c, u) are device arrays of M FP64 in the plan's point order: point i is the
+ *   caller's point perm[i] (wave1d_nufft_perm, host array of M).  S and alpha: device, K + 1
+ *   complex (re, im interleaved).  grid: device, nf reals (wave1d_nufft_info).  Calls are queued on
+ *   the plan's stream and do not synchronise; the plan owns its work arrays, so calls on one plan
+ *   must not overlap.
+ * Returns WAVE1D_EINVAL for bad arguments, WAVE1D_ENOMEM / WAVE1D_ECUDA on CUDA failures
+ * (message: wave1d_nufft_strerror).
+ */
+typedef struct wave1d_nufft_s* wave1d_nufft_t;
+int wave1d_nufft_plan(const double* x, int64_t M, int K, double tol, int precision, void* stream,
+                      wave1d_nufft_t* out);
+int wave1d_nufft_info(wave1d_nufft_t plan, int* nf, int* w, int* degree, double* kernel_err);
+int wave1d_nufft_perm(wave1d_nufft_t plan, int64_t* perm);
+int wave1d_nufft_spread(wave1d_nufft_t plan, const double* c, double* grid);
+int wave1d_nufft_interp(wave1d_nufft_t plan, const double* grid, double* u);
+int wave1d_nufft_type1(wave1d_nufft_t plan, const double* c, double* S);
+int wave1d_nufft_type2(wave1d_nufft_t plan, const double* alpha, double* u);
+int wave1d_nufft_destroy(wave1d_nufft_t plan);
+const char* wave1d_nufft_strerror(void);
+
+/*
  * Type-1 NUFFT of device arrays without any memory allocation (the paper has no counterpart; it
  * is a service for callers that cannot allocate device memory — code running under a memory
  * budget reserved up front, or in a loop that must not take the implicit device synchronisation

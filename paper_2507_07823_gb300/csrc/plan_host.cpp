@@ -343,6 +343,10 @@ int64_t next_pow2(int64_t v) {
     return p;
 }
 
+}  // namespace
+
+// Kaiser-Bessel spreading weights of points x (the kernel of eq. KB on the fine grid): first grid
+// index (wrapped) and w weights per point
 void spread_weights(const Params& P, const std::vector<double>& x, std::vector<int32_t>& i0,
                     std::vector<double>& ker) {
     int64_t n = (int64_t)x.size();
@@ -366,7 +370,58 @@ void spread_weights(const Params& P, const std::vector<double>& x, std::vector<i
     });
 }
 
-}  // namespace
+// NUFFT deconvolution folded with the real-FFT pre/post-processing, per mode k = 0..K:
+//   psihat(k) = w h sinh(r)/r / I0(beta), r = sqrt(beta^2 - (k w h/2)^2)  (transform of eq. KB)
+//   modefac[k][0..2]: type-1 (deconv1 and deconv1 e^{2 pi i k/nf}); [3..6]: type-2 spectrum
+void nufft_factors(const Params& P, std::vector<double>& deconv1, std::vector<double>& deconv2,
+                   std::vector<double>& modefac) {
+    const int K1 = P.K + 1;
+    deconv1.assign(K1, 0.0);
+    deconv2.assign(K1, 0.0);
+    double i0b = bessel_i0(P.kb_beta);
+    for (int k = 0; k < K1; k++) {
+        double om = 0.5 * k * P.nufft_w * P.h_f;
+        double r = std::sqrt(P.kb_beta * P.kb_beta - om * om);
+        double ph = P.nufft_w * P.h_f * (r > 0 ? std::sinh(r) / r : 1.0) / i0b;
+        double sgn = (k % 2 == 0) ? 1.0 : -1.0;
+        deconv1[k] = sgn * P.h_f / (2.0 * kPi * ph);
+        deconv2[k] = sgn * P.h_f / ph;
+    }
+    modefac.assign((size_t)K1 * 8, 0.0);
+    for (int k = 0; k < K1; k++) {
+        double a1 = 2.0 * kPi * (double)k / (double)P.nf;          // e^{+i a1} = w^k
+        double a2 = 2.0 * kPi * (double)(P.L - k) / (double)P.nf;  // e^{-i a2} = w'^{L-k}
+        double d1 = deconv1[k], d2 = deconv2[k];
+        double* f = &modefac[(size_t)k * 8];
+        f[0] = d1;
+        f[1] = d1 * std::cos(a1);
+        f[2] = d1 * std::sin(a1);
+        // 1 + i e^{-i a1} = (1 + sin a1) + i cos a1
+        f[3] = d2 * (1.0 + std::sin(a1));
+        f[4] = d2 * std::cos(a1);
+        // 1 - i e^{-i a2} = (1 - sin a2) - i cos a2
+        f[5] = d2 * (1.0 - std::sin(a2));
+        f[6] = -d2 * std::cos(a2);
+    }
+}
+
+// fine grid and kernel for N_F = 2K + 1 modes at tolerance tol (w taps unless w_in > 0)
+void nufft_grid(Params& P, int K, double tol, int w_in) {
+    P.K = K;
+    P.nf = 1;
+    while (P.nf < 2 * (2 * K + 1)) P.nf <<= 1;
+    if (P.nf < 64) P.nf = 64;
+    P.L = P.nf / 2;
+    int lg = 0;
+    while ((1 << lg) < P.L) lg++;
+    P.L1 = 1 << ((lg + 1) / 2);          // L1 >= L2: balances column and row-pair passes
+    P.L2 = P.L / P.L1;
+    P.h_f = 2.0 * kPi / P.nf;
+    P.nufft_w = w_in > 0 ? w_in : (int)std::ceil(std::log10(1.0 / tol)) + 1;
+    P.nufft_w = std::max(4, std::min(16, P.nufft_w));
+    double upsamp = (double)P.nf / (2.0 * P.K + 1.0);
+    P.kb_beta = kPi * P.nufft_w * (1.0 - 1.0 / (2.0 * upsamp));
+}
 
 // ---------------------------------------------------------------------------------------------
 int build_host_plan(const double* x_in, const double* beta_in, int64_t M, int bc, double dt,
@@ -484,18 +539,8 @@ int build_host_plan(const double* x_in, const double* beta_in, int64_t M, int bc
             hp.rot[k * 3 + 1] = sinc_k(k, dt);
             hp.rot[k * 3 + 2] = k * std::sin(k * dt);
         }
-        // NUFFT deconvolution: psihat(k) = w h sinh(r)/r / I0(beta), r = sqrt(beta^2 - (k w h/2)^2)
-        hp.deconv1.assign(K1, 0.0);
-        hp.deconv2.assign(K1, 0.0);
-        double i0b = bessel_i0(P.kb_beta);
-        for (int k = 0; k < K1; k++) {
-            double om = 0.5 * k * P.nufft_w * P.h_f;
-            double r = std::sqrt(P.kb_beta * P.kb_beta - om * om);
-            double ph = P.nufft_w * P.h_f * (r > 0 ? std::sinh(r) / r : 1.0) / i0b;
-            double sgn = (k % 2 == 0) ? 1.0 : -1.0;
-            hp.deconv1[k] = sgn * P.h_f / (2.0 * kPi * ph);
-            hp.deconv2[k] = sgn * P.h_f / ph;
-        }
+        std::vector<double> modefac;
+        nufft_factors(P, hp.deconv1, hp.deconv2, modefac);
         hp.twiddle.assign((size_t)P.L * 2, 0.0);
         for (int j = 0; j < P.L; j++) {
             double a = 2.0 * kPi * (double)j / (double)P.L;
@@ -503,22 +548,7 @@ int build_host_plan(const double* x_in, const double* beta_in, int64_t M, int bc
             hp.twiddle[2 * j + 1] = std::sin(a);
         }
         // per-mode factors of the real-FFT post/pre-processing folded with the deconvolution
-        hp.modefac.assign((size_t)K1 * 8, 0.0);
-        for (int k = 0; k < K1; k++) {
-            double a1 = 2.0 * kPi * (double)k / (double)P.nf;          // e^{+i a1} = w^k
-            double a2 = 2.0 * kPi * (double)(P.L - k) / (double)P.nf;  // e^{-i a2} = w'^{L-k}
-            double d1 = hp.deconv1[k], d2 = hp.deconv2[k];
-            double* f = &hp.modefac[(size_t)k * 8];
-            f[0] = d1;
-            f[1] = d1 * std::cos(a1);
-            f[2] = d1 * std::sin(a1);
-            // 1 + i e^{-i a1} = (1 + sin a1) + i cos a1
-            f[3] = d2 * (1.0 + std::sin(a1));
-            f[4] = d2 * std::cos(a1);
-            // 1 - i e^{-i a2} = (1 - sin a2) - i cos a2
-            f[5] = d2 * (1.0 - std::sin(a2));
-            f[6] = -d2 * std::cos(a2);
-        }
+        hp.modefac = modefac;
         hp.tw2K.assign((size_t)4 * P.K, 0.0);
         for (int a = 0; a < 2 * P.K; a++) {
             double ang = kPi * (double)a / (double)P.K;

@@ -40,7 +40,10 @@ EXPORTED = ["wave1d_opts_default", "wave1d_plan", "wave1d_set_incident_gaussians
             "wave1d_set_receivers", "wave1d_step", "wave1d_solve", "wave1d_read_receivers",
             "wave1d_get_sigma", "wave1d_sync", "wave1d_get_info", "wave1d_inspect",
             "wave1d_destroy", "wave1d_strerror", "wave1d_profile", "wave1d_profile_read",
-            "wave1d_nufft1_noalloc", "wave1d_state_size", "wave1d_state_save", "wave1d_state_load"]
+            "wave1d_nufft1_noalloc", "wave1d_state_size", "wave1d_state_save", "wave1d_state_load",
+            "wave1d_nufft_plan", "wave1d_nufft_info", "wave1d_nufft_perm", "wave1d_nufft_spread",
+            "wave1d_nufft_interp", "wave1d_nufft_type1", "wave1d_nufft_type2", "wave1d_nufft_destroy",
+            "wave1d_nufft_strerror"]
 
 WAVE1D_NSTAGE = 9
 STAGES = ["local", "spread", "fft_fwd", "modes", "rbc", "fft_inv", "interp", "solve", "receivers"]
@@ -102,10 +105,20 @@ def lib(path: str = LIB_PATH):
         L.wave1d_state_size.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
         L.wave1d_state_save.argtypes = [P, ctypes.c_void_p, ctypes.c_size_t]
         L.wave1d_state_load.argtypes = [P, ctypes.c_void_p, ctypes.c_size_t]
+        L.wave1d_nufft_plan.argtypes = [_D, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                        ctypes.c_void_p, ctypes.POINTER(P)]
+        L.wave1d_nufft_info.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+        L.wave1d_nufft_perm.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
+        for nm in ("wave1d_nufft_spread", "wave1d_nufft_interp", "wave1d_nufft_type1", "wave1d_nufft_type2"):
+            getattr(L, nm).argtypes = [P, _D, _D]
+        L.wave1d_nufft_destroy.argtypes = [P]
+        L.wave1d_nufft_strerror.argtypes = []
+        L.wave1d_nufft_strerror.restype = ctypes.c_char_p
         L.wave1d_strerror.argtypes = [ctypes.c_int]
         L.wave1d_strerror.restype = ctypes.c_char_p
         for name in EXPORTED:
-            if name != "wave1d_strerror":
+            if name not in ("wave1d_strerror", "wave1d_nufft_strerror"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -168,6 +181,51 @@ def wave1d_solve(plan, nsteps, u_rec, sigma, out_on_device):
     f = _dptr if out_on_device else _hptr
     return lib().wave1d_solve(plan, int(nsteps), f(u_rec) if u_rec is not None else None,
                               f(sigma) if sigma is not None else None, int(out_on_device))
+
+
+class Nufft:
+    """Standalone type-1 / type-2 NUFFT plan (device arrays are torch CUDA tensors of float64;
+    point arrays in the plan's point order, see `perm`)."""
+
+    def __init__(self, x, K, tol, precision=0, stream=None):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        h = ctypes.c_void_p()
+        st = lib().wave1d_nufft_plan(_hptr(x), x.shape[0], int(K), float(tol), int(precision),
+                                     ctypes.c_void_p(stream) if stream is not None else None,
+                                     ctypes.byref(h))
+        if st != WAVE1D_OK:
+            raise Wave1DError(st, "wave1d_nufft_plan: " + lib().wave1d_nufft_strerror().decode())
+        self.h, self.M, self.K = h, x.shape[0], int(K)
+        nf, w, deg, err = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _check(lib().wave1d_nufft_info(h, ctypes.byref(nf), ctypes.byref(w), ctypes.byref(deg),
+                                       ctypes.byref(err)), "wave1d_nufft_info")
+        self.nf, self.w, self.degree, self.kernel_err = nf.value, w.value, deg.value, err.value
+        perm = np.zeros(self.M, dtype=np.int64)
+        _check(lib().wave1d_nufft_perm(h, perm.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
+               "wave1d_nufft_perm")
+        self.perm = perm
+
+    def _call(self, name, a, b):
+        st = getattr(lib(), name)(self.h, _dptr(a), _dptr(b))
+        if st != WAVE1D_OK:
+            raise Wave1DError(st, name + ": " + lib().wave1d_nufft_strerror().decode())
+
+    def spread(self, c, grid):
+        self._call("wave1d_nufft_spread", c, grid)
+
+    def interp(self, grid, u):
+        self._call("wave1d_nufft_interp", grid, u)
+
+    def type1(self, c, S):
+        self._call("wave1d_nufft_type1", c, S)
+
+    def type2(self, alpha, u):
+        self._call("wave1d_nufft_type2", alpha, u)
+
+    def close(self):
+        if self.h:
+            lib().wave1d_nufft_destroy(self.h)
+            self.h = None
 
 
 def wave1d_state_size(plan):

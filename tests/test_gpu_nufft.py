@@ -1,0 +1,114 @@
+"""The standalone NUFFTs (wave1d_nufft_*) against the oracle's direct sums.
+
+type-1 S_k = (1/2 pi) sum_j c_j e^{+ikx_j} (eq. densco) and type-2 u_j = sum_{|k|<=K} alpha_k
+e^{-ikx_j} (eq. historySol1), in FP64 (kernel weights precomputed) and in mixed precision (FP32
+kernel polynomials, compensated FP32 sums, FP64 FFT).  Error: max |gpu - direct| / max |direct|
+over the whole output.  Bars: FP64 at tol 1e-12 -> 1e-10 (the plan's NUFFT accuracy); mixed at tol
+1e-6 -> 1e-6 (the mixed mode's stated accuracy).  At M = 1e6 (the clustered periodic workload)
+the direct sums are taken at sampled modes and points.
+"""
+import numpy as np
+import pytest
+
+from oracle import wfp
+from paper_2507_07823_gb300 import build, wave1d, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    wave1d.lib()
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _inputs(M, K, seed):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(-np.pi, np.pi, M)
+    c = rng.uniform(0.5, 1.5, M) * np.where(rng.uniform(size=M) < 0.8, 1.0, -1.0)
+    decay = 1.0 / (1.0 + np.arange(K + 1) / 300.0)
+    alpha = (rng.standard_normal(K + 1) + 1j * rng.standard_normal(K + 1)) * decay
+    alpha[0] = alpha[0].real
+    return x, c, alpha
+
+
+def _run(nu, c, alpha):
+    import torch
+    K = nu.K
+    cd = torch.tensor(c[nu.perm], dtype=torch.float64, device="cuda")
+    Sd = torch.zeros(2 * (K + 1), dtype=torch.float64, device="cuda")
+    ad = torch.tensor(np.stack([alpha.real, alpha.imag], 1).reshape(-1), dtype=torch.float64, device="cuda")
+    ud = torch.zeros(nu.M, dtype=torch.float64, device="cuda")
+    nu.type1(cd, Sd)
+    nu.type2(ad, ud)
+    torch.cuda.synchronize()
+    S = Sd.cpu().numpy()
+    u = np.empty(nu.M)
+    u[nu.perm] = ud.cpu().numpy()
+    return S[0::2] + 1j * S[1::2], u
+
+
+@pytest.mark.parametrize("precision,tol,bar", [(0, 1e-12, 1e-10), (1, 1e-6, 1e-6)])
+def test_nufft_against_direct_sums(precision, tol, bar):
+    """M = 3000 random points, K = 3141 (the dt = 1e-3 mode count), both transforms, twice."""
+    M, K = 3000, 3141
+    x, c, alpha = _inputs(M, K, 2507)
+    nu = wave1d.Nufft(x, K, tol, precision)
+    try:
+        S, u = _run(nu, c, alpha)
+        S2, u2 = _run(nu, c, alpha)
+    finally:
+        nu.close()
+    assert np.array_equal(S, S2) and np.array_equal(u, u2)          # deterministic
+    eS, eu = _rel(S, wfp.type1(c, x, K)), _rel(u, wfp.type2(alpha, x))
+    print(f"precision {precision} tol {tol}: type-1 {eS:.2e} type-2 {eu:.2e}")
+    assert eS < bar and eu < bar
+    if precision == 1:
+        assert nu.kernel_err < 2e-7
+
+
+def test_nufft_small_and_ragged():
+    """M = 1 and M = 37 (not a multiple of any block), a point on the box edge, K = 5."""
+    for M in (1, 37):
+        x, c, alpha = _inputs(M, 5, 11 + M)
+        x[0] = -np.pi
+        for precision, tol, bar in ((0, 1e-12, 1e-10), (1, 1e-6, 1e-6)):
+            nu = wave1d.Nufft(x, 5, tol, precision)
+            try:
+                S, u = _run(nu, c, alpha)
+            finally:
+                nu.close()
+            assert _rel(S, wfp.type1(c, x, 5)) < bar and _rel(u, wfp.type2(alpha, x)) < bar
+
+
+def test_nufft_clustered_million_points_sampled():
+    """The M = 1e6 clustered periodic workload (16 Gaussians sigma 0.05 + 20% uniform), K = 6283:
+    type-1 at 48 sampled modes and type-2 at 400 sampled points against the direct sums, FP64
+    (tol 1e-10) and mixed (tol 1e-6)."""
+    w = W.config2()
+    K = int(np.floor(np.pi / w.dt))
+    rng = np.random.default_rng(7)
+    c = rng.uniform(0.5, 1.5, w.M)
+    alpha = (rng.standard_normal(K + 1) + 1j * rng.standard_normal(K + 1)) / (1.0 + np.arange(K + 1) / 300.0)
+    alpha[0] = alpha[0].real                  # alpha_{-k} = conj(alpha_k) makes alpha_0 real
+    ks = np.sort(rng.choice(K + 1, 48, replace=False))
+    js = rng.choice(w.M, 400, replace=False)
+    S_ref = np.array([np.sum(c * np.exp(1j * k * w.x)) for k in ks]) / (2 * np.pi)
+    u_ref = wfp.type2(alpha, w.x[js])
+    for precision, tol, bar in ((0, 1e-10, 1e-8), (1, 1e-6, 1e-6)):
+        nu = wave1d.Nufft(w.x, K, tol, precision)
+        try:
+            S, u = _run(nu, c, alpha)
+        finally:
+            nu.close()
+        eS = float(np.max(np.abs(S[ks] - S_ref)) / np.max(np.abs(S_ref)))
+        eu = _rel(u[js], u_ref)
+        print(f"M=1e6 precision {precision}: type-1 {eS:.2e} type-2 {eu:.2e}")
+        assert eS < bar and eu < bar
