@@ -138,11 +138,6 @@ int build_host_plan(const double* x, const double* beta, int64_t M, int bc, doub
                     std::string& err);
 int build_receivers(HostPlan& hp, const double* xr, int64_t R, std::string& err);
 int build_rows(const LocalCSR& csr, int m_first, LocalRows& rows, std::string& err);
-void spread_weights(const Params& P, const std::vector<double>& x, std::vector<int32_t>& i0,
-                    std::vector<double>& ker);
-void nufft_factors(const Params& P, std::vector<double>& deconv1, std::vector<double>& deconv2,
-                   std::vector<double>& modefac);
-void nufft_grid(Params& P, int K, double tol, int w_in);
 
 // ---------------------------------------------------------------------------------------------
 // Device view (passed by value to kernels)

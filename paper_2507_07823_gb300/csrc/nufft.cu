@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "nufft_host.h"
 #include "device_common.cuh"
 #include "../../include/wave1d.h"
 

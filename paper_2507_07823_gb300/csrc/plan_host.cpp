@@ -9,6 +9,7 @@
 #include <thread>
 
 #include "internal.h"
+#include "nufft_host.h"
 #include "../../include/wave1d.h"
 
 namespace wave1d {
