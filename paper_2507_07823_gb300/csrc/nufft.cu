@@ -92,149 +92,253 @@ __device__ __forceinline__ void nu_pair_add(float& sh, float& sl, float ph, floa
 }
 
 // Mixed-precision kernel: tap t (0 <= t < w) of a point with offset variable y in [-1, 1] has the
-// value sum_d c[t][d] y^d (degree D, fitted on the host).  The table is a kernel parameter, so
-// the unrolled Horner steps take their coefficients straight from the constant bank.
+// value psi_t(y) = sum_d a[t][d] T_d(y), a Chebyshev series of degree D fitted on the host (well
+// conditioned: sum_d |a[t][d]| stays near max psi_t, so FP32 evaluation loses little).  The
+// kernel is even, so psi_{w-1-t}(y) = psi_t(-y) and a[w-1-t][d] = (-1)^d a[t][d]: the host fits
+// the first half of the taps and mirrors them.  The table is a kernel parameter, so the unrolled
+// FMAs take their coefficients straight from the constant bank.
 struct NuPoly {
     float c[16][kMaxDegree + 1];
 };
 template <int D>
-__device__ __forceinline__ float nu_psi(const float (&c)[kMaxDegree + 1], float y) {
-    float r = c[D];
+struct NuCheb {                    // T_0(y) .. T_D(y) by the three-term recurrence
+    float T[D + 1];
+    __device__ __forceinline__ explicit NuCheb(float y) {
+        const float y2 = __fadd_rn(y, y);
+        T[0] = 1.f;
+        T[1] = y;
 #pragma unroll
-    for (int d = D - 1; d >= 0; d--) r = __fmaf_rn(r, y, c[d]);
-    return r;
+        for (int d = 2; d <= D; d++) T[d] = __fmaf_rn(y2, T[d - 1], -T[d - 2]);
+    }
+};
+// all w kernel values of a point: even and odd parts of the first half, mirrored
+template <int W, int D>
+__device__ __forceinline__ void nu_taps(const NuPoly& P, const NuCheb<D>& ch, float (&psi)[W]) {
+#pragma unroll
+    for (int t = 0; t < (W + 1) / 2; t++) {
+        float e = P.c[t][0], o = __fmul_rn(P.c[t][1], ch.T[1]);
+#pragma unroll
+        for (int d = 2; d <= D; d += 2) e = __fmaf_rn(P.c[t][d], ch.T[d], e);
+#pragma unroll
+        for (int d = 3; d <= D; d += 2) o = __fmaf_rn(P.c[t][d], ch.T[d], o);
+        psi[t] = __fadd_rn(e, o);
+        if (W - 1 - t != t) psi[W - 1 - t] = __fsub_rn(e, o);
+    }
 }
 
 // ---------------------------------------------------------------------------------------------
 // Spreading by units (A1).  The host cuts the sorted points into units of at most kUnitPoints
-// consecutive points whose first cells lie within kUnitCells cells.  A block takes a unit: each
-// thread forms its point's w products kernel x c in shared memory; then each cell the unit
-// reaches (its first cells plus w - 1) gets a group of G lanes (G a power of two, as many as the
-// block can give every cell, at most 32) that sum the cell's contributors in point order, lanes
-// strided, then by a fixed shuffle tree; the group stores the unit's partial for the cell.  A
-// second pass adds, per grid real, the partials of the units that reach it, in unit order.  No
-// atomics: the result does not depend on scheduling, and a dense cluster (hundreds of points per
-// cell) spreads over many units and lanes.
+// consecutive points whose first cells lie within kUnitCells cells, and lists each unit's runs
+// (the points of one first cell, contiguous in the sorted order).  A block takes a unit.  Each
+// run gets a group of G lanes (G a power of two chosen on the host: as many as the block can give
+// every run, at most 32); the lanes stride over the run's points, evaluate each
+// point's w kernel values once and accumulate w sums, one per tap, which a fixed shuffle tree
+// adds over the group.  Cell l of the unit then collects tap t of the run at first cell l - t,
+// for t < w, and stores the unit's partial for that cell.  A second pass adds, per grid real, the
+// partials of the units that reach it, in unit order.  No atomics: the result does not depend on
+// scheduling, and a dense cluster (hundreds of points per cell) spreads over many units and lanes.
+// Mixed precision keeps the sums as compensated FP32 pairs; FP64 uses the stored weights and FMAs.
 // ---------------------------------------------------------------------------------------------
-constexpr int kUnitPoints = 256;
+constexpr int kUnitPoints = 1024;
 constexpr int kUnitCells = 64;
-constexpr int kValStride = 17;       // shared-memory stride of a point's products (odd: no bank conflicts)
+constexpr int kUnitThreads = 256;
 
 struct NuUnit {
-    int32_t pa, np, ca, span;     // first point, points, first cell, cells reached (< kUnitCells + w)
-    int32_t poff, pad0, pad1, pad2; // offset of its partials
+    int32_t pa, np, ca, ncells;    // first point, points, first cell, first cells covered (<= kUnitCells)
+    int32_t span, poff, roff, lg;  // cells reached (ncells + w - 1), offset of its partials, offset of
+                                   // its run table (ncells + 1 point offsets), log2 of lanes per run
+    int32_t gap0, gap1, pad0, pad1;  // cells [gap0, gap1) (mod nf) after its span that no unit reaches
 };
 
-// first index in [lo, hi) of the sorted f[] with value >= v
-__device__ __forceinline__ int nu_lower(const int* f, int lo, int hi, int v) {
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (f[mid] < v) lo = mid + 1;
-        else hi = mid;
+// The unit's value v for grid real r, its partial slot `slot`.  A real that one unit reaches is
+// written at once.  Otherwise the unit stores its partial and counts itself in (a release:
+// fence, then the integer atomic); the unit that arrives last adds all partials of r in unit
+// order (the order the combine table lists), writes the real and clears the counter for the
+// next call.  No thread waits on another, and the sum does not depend on who arrives last.
+__device__ __forceinline__ double nu_value(double v) { return v; }
+__device__ __forceinline__ double nu_value(float2 v) { return nu_f32_to_f64(v.x) + nu_f32_to_f64(v.y); }
+__device__ __forceinline__ void nu_accum(double& a, double v) { a += v; }
+__device__ __forceinline__ void nu_accum(float2& a, float2 v) { nu_pair_add(a.x, a.y, v.x, v.y); }
+template <typename V>
+__device__ __forceinline__ void nu_emit(int r, int slot, V v, int e0, int e1, V* __restrict__ partial,
+                                        const int32_t* __restrict__ cent, int* __restrict__ cnt,
+                                        double* __restrict__ grid) {
+    if (e1 - e0 == 1) {
+        grid[r] = nu_value(v);
+        return;
     }
-    return lo;
+    partial[slot] = v;
+    __threadfence();
+    if (atomicAdd(cnt + r, 1) != e1 - e0 - 1) return;
+    __threadfence();
+    V a{};
+    for (int e = e0; e < e1; e++) nu_accum(a, __ldcg(partial + __ldg(cent + e)));
+    grid[r] = nu_value(a);
+    cnt[r] = 0;
+}
+// zeros for the uncovered cells after a unit's span
+__device__ __forceinline__ void nu_gap(const NuUnit& u, double* __restrict__ grid, int nf) {
+    for (int g = u.gap0 + (int)threadIdx.x; g < u.gap1; g += blockDim.x) grid[g % nf] = 0.0;
 }
 
-// cell ranges of a unit: cstart[l] = first point whose first cell is >= ca + l (l <= kUnitCells);
-// the G-lane group size for `span` cells
-__device__ __forceinline__ int nu_unit_cells(const NuUnit& u, const int* fl, int* cstart) {
-    if (threadIdx.x <= kUnitCells) cstart[threadIdx.x] = nu_lower(fl, 0, u.np, u.ca + (int)threadIdx.x);
-    int lg = 5;
-    while (lg > 0 && (u.span << lg) > kUnitPoints) lg--;
-    return lg;
-}
-
-template <int D>
-__global__ void __launch_bounds__(kUnitPoints) k_nu_spread_mixed(const NuUnit* __restrict__ units,
-                                                                 const double* __restrict__ c,
-                                                                 const int32_t* __restrict__ first,
-                                                                 const float* __restrict__ soff, const NuPoly P,
-                                                                 int w, float2* __restrict__ partial) {
-    __shared__ int fl[kUnitPoints];
-    __shared__ int cstart[kUnitCells + 1];
-    __shared__ float val[kUnitPoints * kValStride];
+// FP64: each run's lanes accumulate w tap sums of the stored weights times c (one FMA per point
+// and tap, four points' loads in flight per pass); cell l collects tap t of the run at l - t.
+template <int W>
+__global__ void __launch_bounds__(kUnitThreads) k_nu_spread64(const NuUnit* __restrict__ units,
+                                                              const int32_t* __restrict__ runs,
+                                                              const double* __restrict__ c,
+                                                              const double* __restrict__ ker,
+                                                              double* __restrict__ partial,
+                                                              const int32_t* __restrict__ cptr,
+                                                              const int32_t* __restrict__ cent,
+                                                              int* __restrict__ cnt, double* __restrict__ grid,
+                                                              int nf) {
+    __shared__ int rp[kUnitCells + 1];
+    __shared__ double seg[kUnitCells][W];
     const NuUnit u = units[blockIdx.x];
-    const int p = threadIdx.x;
-    if (p < u.np) {
-        const int64_t j = (int64_t)u.pa + p;
-        fl[p] = __ldg(first + j);
-        const float cj = nu_f64_to_f32(__ldcs(c + j));
-        const float y = __fmaf_rn(2.f, __ldcs(soff + j), -1.f);
+    if ((int)threadIdx.x <= u.ncells) rp[threadIdx.x] = __ldg(runs + u.roff + threadIdx.x);
+    // this thread's cell of the span (one pass: span <= kUnitCells + 15 < kUnitThreads) and its
+    // combine-table range, fetched now so the loads overlap the spreading
+    const int r_cell = (u.ca + (int)threadIdx.x) % nf;
+    const int e0 = (int)threadIdx.x < u.span ? __ldg(cptr + r_cell) : 0;
+    const int e1 = (int)threadIdx.x < u.span ? __ldg(cptr + r_cell + 1) : 0;
+    __syncthreads();
+    const int G = 1 << u.lg, f = (int)threadIdx.x >> u.lg, gl = (int)threadIdx.x & (G - 1);
+    double acc[W];
 #pragma unroll
-        for (int t = 0; t < 16; t++)
-            if (t < w) val[p * kValStride + t] = __fmul_rn(nu_psi<D>(P.c[t], y), cj);
-    }
-    __syncthreads();
-    const int lg = nu_unit_cells(u, fl, cstart);
-    __syncthreads();
-    const int G = 1 << lg, grp = p >> lg, gl = p & (G - 1);
-    float sh = 0.f, sl = 0.f;
-    if (grp < u.span) {
-        const int g = u.ca + grp;
-        const int lo = cstart[grp - w + 1 > 0 ? grp - w + 1 : 0];
-        const int hi = cstart[grp + 1 < kUnitCells ? grp + 1 : kUnitCells];
-        for (int q = lo + gl; q < hi; q += G) nu_pair_add(sh, sl, val[q * kValStride + (g - fl[q])], 0.f);
-    }
-    for (int o = G >> 1; o > 0; o >>= 1)
-        nu_pair_add(sh, sl, __shfl_xor_sync(0xffffffffu, sh, o), __shfl_xor_sync(0xffffffffu, sl, o));
-    if (gl == 0 && grp < u.span) partial[u.poff + grp] = make_float2(sh, sl);
-}
-
-__global__ void __launch_bounds__(kUnitPoints) k_nu_spread64(const NuUnit* __restrict__ units,
-                                                             const double* __restrict__ c,
-                                                             const int32_t* __restrict__ first,
-                                                             const double* __restrict__ ker, int w,
-                                                             double* __restrict__ partial) {
-    __shared__ int fl[kUnitPoints];
-    __shared__ int cstart[kUnitCells + 1];
-    __shared__ double cs[kUnitPoints];
-    __shared__ double kv[kUnitPoints * kValStride];
-    const NuUnit u = units[blockIdx.x];
-    const int p = threadIdx.x;
-    if (p < u.np) {
-        fl[p] = __ldg(first + u.pa + p);
-        cs[p] = __ldcs(c + u.pa + p);
-    }
-    // the unit's weights are one contiguous run of np w doubles: read it coalesced
-    const double* kr = ker + (int64_t)u.pa * w;
-    for (int e = p; e < u.np * w; e += kUnitPoints) {
-        const int q = e / w;
-        kv[q * kValStride + (e - q * w)] = __ldcs(kr + e);
-    }
-    __syncthreads();
-    const int lg = nu_unit_cells(u, fl, cstart);
-    __syncthreads();
-    const int G = 1 << lg, grp = p >> lg, gl = p & (G - 1);
-    double a = 0.0;
-    if (grp < u.span) {
-        const int g = u.ca + grp;
-        const int lo = cstart[grp - w + 1 > 0 ? grp - w + 1 : 0];
-        const int hi = cstart[grp + 1 < kUnitCells ? grp + 1 : kUnitCells];
-        for (int q = lo + gl; q < hi; q += G) a = fma(kv[q * kValStride + (g - fl[q])], cs[q], a);
-    }
-    for (int o = G >> 1; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    if (gl == 0 && grp < u.span) partial[u.poff + grp] = a;
-}
-
-// combine pass: grid real r = sum of the partials of the units that reach r, in unit order
-__global__ void k_nu_combine64(const double* __restrict__ partial, const int32_t* __restrict__ cptr,
-                               const int32_t* __restrict__ cent, double* __restrict__ grid, int nf) {
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nf; r += gridDim.x * blockDim.x) {
-        double a = 0.0;
-        for (int e = __ldg(cptr + r); e < __ldg(cptr + r + 1); e++) a += __ldg(partial + __ldg(cent + e));
-        grid[r] = a;
-    }
-}
-__global__ void k_nu_combine32(const float2* __restrict__ partial, const int32_t* __restrict__ cptr,
-                               const int32_t* __restrict__ cent, double* __restrict__ grid, int nf) {
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nf; r += gridDim.x * blockDim.x) {
-        float sh = 0.f, sl = 0.f;
-        for (int e = __ldg(cptr + r); e < __ldg(cptr + r + 1); e++) {
-            const float2 v = __ldg(partial + __ldg(cent + e));
-            nu_pair_add(sh, sl, v.x, v.y);
+    for (int t = 0; t < W; t++) acc[t] = 0.0;
+    if (f < u.ncells) {
+        const int q1 = rp[f + 1];
+        constexpr int B = 4;
+        for (int q = rp[f] + gl; q < q1; q += B * G) {
+            double cb[B], kb[B][W];
+#pragma unroll
+            for (int i = 0; i < B; i++) {
+                const bool ok = q + i * G < q1;
+                const int64_t j = (int64_t)u.pa + (ok ? q + i * G : q);
+                cb[i] = ok ? __ldcs(c + j) : 0.0;
+#pragma unroll
+                for (int t = 0; t < W; t++) kb[i][t] = __ldcs(ker + j * W + t);
+            }
+#pragma unroll
+            for (int i = 0; i < B; i++)
+#pragma unroll
+                for (int t = 0; t < W; t++) acc[t] = fma(kb[i][t], cb[i], acc[t]);
         }
-        grid[r] = nu_f32_to_f64(sh) + nu_f32_to_f64(sl);
     }
+    for (int o = G >> 1; o > 0; o >>= 1) {
+#pragma unroll
+        for (int t = 0; t < W; t++) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+    }
+    if (gl == 0 && f < u.ncells) {
+#pragma unroll
+        for (int t = 0; t < W; t++) seg[f][t] = acc[t];
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < u.span) {
+        const int l = threadIdx.x;
+        double a = 0.0;
+#pragma unroll
+        for (int t = 0; t < W; t++)
+            if (l - t >= 0 && l - t < u.ncells) a += seg[l - t][t];
+        nu_emit(r_cell, u.poff + l, a, e0, e1, partial, cent, cnt, grid);
+    }
+    nu_gap(u, grid, nf);
+}
+
+// Mixed precision by Chebyshev moments.  With psi_t(y) = sum_d a[t][d] T_d(y),
+//   G[g] = sum_t sum_{q: i0_q = g - t} c_q psi_t(y_q) = sum_t sum_d a[t][d] M_d(g - t),
+//   M_d(f) = sum_{q: i0_q = f} c_q T_d(y_q),
+// so a point costs D + 1 FMAs (its moments) instead of w kernel evaluations.  The unit's (c, y)
+// are staged in shared memory; each run's lanes accumulate the run's moments and a fixed shuffle
+// tree adds them; cell l of the unit then takes sum_t sum_d a[t][d] M_d(l - t).  The dominant
+// terms are compensated: M_0 (the run's plain sum of c) is an FP32 pair, and the d = 0 products
+// a[t][0] M_0 enter the cell's pair exactly (two-product by FMA); the higher moments, which
+// cancel over a run and carry small coefficients, are plain FP32 (a[t][d] sum to about max psi,
+// so the assembly is well conditioned).  The cell's partial is an FP32 pair.
+template <int W, int D>
+__global__ void __launch_bounds__(kUnitThreads) k_nu_spread_mixed(
+    const NuUnit* __restrict__ units, const int32_t* __restrict__ runs, const double* __restrict__ c,
+    const float* __restrict__ soff, const NuPoly P, float2* __restrict__ partial, const int32_t* __restrict__ cptr,
+    const int32_t* __restrict__ cent, int* __restrict__ cnt, double* __restrict__ grid, int nf) {
+    constexpr int R = (D + 2 + 3) / 4 * 4;            // moment row: M_0 (hi, lo), M_1 .. M_D, padded to float4
+    __shared__ int rp[kUnitCells + 1];
+    __shared__ float2 cy[kUnitPoints];
+    __shared__ __align__(16) float mo[kUnitCells][R];
+    const NuUnit u = units[blockIdx.x];
+    if ((int)threadIdx.x <= u.ncells) rp[threadIdx.x] = __ldg(runs + u.roff + threadIdx.x);
+    // this thread's cell of the span (one pass: span <= kUnitCells + 15 < kUnitThreads) and its
+    // combine-table range, fetched now so the loads overlap the spreading
+    const int r_cell = (u.ca + (int)threadIdx.x) % nf;
+    const int e0 = (int)threadIdx.x < u.span ? __ldg(cptr + r_cell) : 0;
+    const int e1 = (int)threadIdx.x < u.span ? __ldg(cptr + r_cell + 1) : 0;
+    {
+        // stage the unit's densities and offsets with every thread's loads in flight at once
+        float sv[kUnitPoints / kUnitThreads];
+        double cd[kUnitPoints / kUnitThreads];
+#pragma unroll
+        for (int i = 0; i < kUnitPoints / kUnitThreads; i++) {
+            const int q = (int)threadIdx.x + i * kUnitThreads;
+            if (q < u.np) {
+                cd[i] = __ldcs(c + u.pa + q);
+                sv[i] = __ldcs(soff + u.pa + q);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < kUnitPoints / kUnitThreads; i++) {
+            const int q = (int)threadIdx.x + i * kUnitThreads;
+            if (q < u.np) cy[q] = make_float2(nu_f64_to_f32(cd[i]), __fmaf_rn(2.f, sv[i], -1.f));
+        }
+    }
+    __syncthreads();
+    const int G = 1 << u.lg, f = (int)threadIdx.x >> u.lg, gl = (int)threadIdx.x & (G - 1);
+    // a lane's share of a run is about eight points: plain FP32 sums there, pairs for M_0 above
+    float m[D + 1];
+#pragma unroll
+    for (int d = 0; d <= D; d++) m[d] = 0.f;
+    if (f < u.ncells) {
+        const int q1 = rp[f + 1];
+        for (int q = rp[f] + gl; q < q1; q += G) {
+            const float2 v = cy[q];
+            const NuCheb<D> ch(v.y);
+            m[0] = __fadd_rn(m[0], v.x);
+#pragma unroll
+            for (int d = 1; d <= D; d++) m[d] = __fmaf_rn(ch.T[d], v.x, m[d]);
+        }
+    }
+    float m0l = 0.f;
+    for (int o = G >> 1; o > 0; o >>= 1) {
+        nu_pair_add(m[0], m0l, __shfl_xor_sync(0xffffffffu, m[0], o), __shfl_xor_sync(0xffffffffu, m0l, o));
+#pragma unroll
+        for (int d = 1; d <= D; d++) m[d] = __fadd_rn(m[d], __shfl_xor_sync(0xffffffffu, m[d], o));
+    }
+    if (gl == 0 && f < u.ncells) {
+        mo[f][0] = m[0];
+        mo[f][1] = m0l;
+#pragma unroll
+        for (int d = 1; d <= D; d++) mo[f][d + 1] = m[d];
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < u.span) {
+        const int l = threadIdx.x;
+        float h = 0.f, lo = 0.f, r = 0.f;
+#pragma unroll
+        for (int t = 0; t < W; t++) {
+            if (l - t >= 0 && l - t < u.ncells) {
+                float mf[R];
+#pragma unroll
+                for (int k = 0; k < R; k += 4) *reinterpret_cast<float4*>(mf + k) = *reinterpret_cast<const float4*>(&mo[l - t][k]);
+                const float p = __fmul_rn(P.c[t][0], mf[0]);
+                const float e = __fmaf_rn(P.c[t][0], mf[1], __fmaf_rn(P.c[t][0], mf[0], -p));
+                nu_pair_add(h, lo, p, e);
+#pragma unroll
+                for (int d = 1; d <= D; d++) r = __fmaf_rn(P.c[t][d], mf[d + 1], r);
+            }
+        }
+        nu_pair_add(h, lo, r, 0.f);
+        nu_emit(r_cell, u.poff + l, make_float2(h, lo), e0, e1, partial, cent, cnt, grid);
+    }
+    nu_gap(u, grid, nf);
 }
 
 // type-1 post-processing: S_k from the half-length FFT Z (E, O split) with the deconvolution
@@ -304,89 +408,121 @@ __global__ void __launch_bounds__(kInterpTile) k_nu_interp64(const double* __res
     }
 }
 
-// mixed interpolation (A6) by units: the block converts the unit's grid span to FP32 in shared
-// memory once, then each thread sums its point's w taps in FP32 (rounding errors of the order of
-// the kernel's fit, below the requested tolerance)
-template <int D>
-__global__ void __launch_bounds__(kUnitPoints) k_nu_interp_mixed(const NuUnit* __restrict__ units,
-                                                                 const double* __restrict__ grid,
-                                                                 double* __restrict__ u,
-                                                                 const int32_t* __restrict__ first,
-                                                                 const float* __restrict__ soff, const NuPoly P,
-                                                                 int w, int nf) {
-    __shared__ float gs[kUnitCells + 16];
-    const NuUnit un = units[blockIdx.x];
-    for (int l = threadIdx.x; l < un.span; l += kUnitPoints) gs[l] = nu_f64_to_f32(__ldg(grid + (un.ca + l) % nf));
-    __syncthreads();
-    const int p = threadIdx.x;
-    if (p < un.np) {
-        const int64_t j = (int64_t)un.pa + p;
-        const int a = __ldg(first + j) - un.ca;
-        const float y = __fmaf_rn(2.f, __ldcs(soff + j), -1.f);
-        float acc = 0.f;
+// mixed interpolation (A6).  With psi_t(y) = sum_d a[t][d] T_d(y),
+//   u_j = sum_t psi_t(y_j) G[i0_j + t] = sum_d T_d(y_j) H_d(i0_j),  H_d(i) = sum_t a[t][d] G[i + t],
+// and H depends only on the first cell.  A block takes 1024 consecutive points (sorted by first
+// cell, four per thread), converts the grid cells they reach to FP32 in shared memory, forms H
+// for each of their first cells (W (D + 1) FMAs per cell), and then each point costs D + 1 FMAs.
+// FP32 throughout (rounding of the order of the kernel's fit, below the requested tolerance).  A
+// block whose points start in more than kHCells cells evaluates the taps per point instead.
+constexpr int kHCells = 512;
+constexpr int kInterpPer = 4;
+template <int W, int D>
+__global__ void __launch_bounds__(256) k_nu_interp_mixed(const double* __restrict__ grid, double* __restrict__ u,
+                                                         const int32_t* __restrict__ first,
+                                                         const float* __restrict__ soff, const NuPoly P, int64_t M,
+                                                         int nf) {
+    constexpr int R = (D + 1 + 3) / 4 * 4;            // H row, padded to float4
+    __shared__ float gs[kHCells + 16];
+    __shared__ __align__(16) float H[kHCells * R];
+    __shared__ int fr[2];
+    const int64_t base = (int64_t)blockIdx.x * (256 * kInterpPer);
+    const int64_t last = M - 1 < base + 256 * kInterpPer - 1 ? M - 1 : base + 256 * kInterpPer - 1;
+    int a[kInterpPer];
+    float y[kInterpPer];
 #pragma unroll
-        for (int t = 0; t < 16; t++)
-            if (t < w) acc = __fmaf_rn(nu_psi<D>(P.c[t], y), gs[a + t], acc);
+    for (int i = 0; i < kInterpPer; i++) {
+        const int64_t j = base + threadIdx.x + i * 256;
+        a[i] = j <= last ? __ldg(first + j) : 0;
+        y[i] = j <= last ? __fmaf_rn(2.f, __ldcs(soff + j), -1.f) : 0.f;
+        if (j == base) fr[0] = a[i];
+        if (j == last) fr[1] = a[i];
+    }
+    __syncthreads();
+    const int c0 = fr[0], ncell = fr[1] - c0 + 1;
+    const bool fits = ncell <= kHCells;                 // the same in every thread of the block
+    if (fits) {
+        for (int l = threadIdx.x; l < ncell + W - 1; l += 256) gs[l] = nu_f64_to_f32(__ldg(grid + (c0 + l) % nf));
+        __syncthreads();
+        for (int l = threadIdx.x; l < ncell; l += 256) {
+            float g[W];
+#pragma unroll
+            for (int t = 0; t < W; t++) g[t] = gs[l + t];
+#pragma unroll
+            for (int d = 0; d <= D; d++) {
+                float h = __fmul_rn(P.c[0][d], g[0]);
+#pragma unroll
+                for (int t = 1; t < W; t++) h = __fmaf_rn(P.c[t][d], g[t], h);
+                H[l * R + d] = h;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < kInterpPer; i++) {
+        const int64_t j = base + threadIdx.x + i * 256;
+        if (j > last) break;
+        const NuCheb<D> ch(y[i]);
+        float acc;
+        if (fits) {
+            float h[R];
+#pragma unroll
+            for (int k = 0; k < R; k += 4) *reinterpret_cast<float4*>(h + k) = *reinterpret_cast<const float4*>(H + (a[i] - c0) * R + k);
+            acc = h[0];
+#pragma unroll
+            for (int d = 1; d <= D; d++) acc = __fmaf_rn(ch.T[d], h[d], acc);
+        } else {
+            float psi[W];
+            nu_taps<W, D>(P, ch, psi);
+            acc = 0.f;
+#pragma unroll
+            for (int t = 0; t < W; t++) {
+                const int r = a[i] + t < nf ? a[i] + t : a[i] + t - nf;
+                acc = __fmaf_rn(psi[t], nu_f64_to_f32(__ldg(grid + r)), acc);
+            }
+        }
         __stcs(u + j, nu_f32_to_f64(acc));
     }
 }
 
-// polynomial degrees the mixed kernels are built for
+// compile-time kernel widths and polynomial degrees: FP64 takes w = 4..16; mixed precision
+// (tol >= 1e-6) takes w = 4..7 with degrees 6, 8 or 10
+constexpr int kMixedMaxW = 7;
+template <int W, typename F>
+bool nu_try_w(int w, F& f) {
+    if (w != W) return false;
+    f(std::integral_constant<int, W>{});
+    return true;
+}
 template <typename F>
-bool nu_with_degree(int D, F&& f) {
-    switch (D) {
-        case 6: f(std::integral_constant<int, 6>{}); return true;
-        case 8: f(std::integral_constant<int, 8>{}); return true;
-        case 10: f(std::integral_constant<int, 10>{}); return true;
-        case 12: f(std::integral_constant<int, 12>{}); return true;
-        case 14: f(std::integral_constant<int, 14>{}); return true;
-        case 16: f(std::integral_constant<int, 16>{}); return true;
-        default: return false;
-    }
+bool nu_with_w(int w, F&& f) {
+    return nu_try_w<4>(w, f) || nu_try_w<5>(w, f) || nu_try_w<6>(w, f) || nu_try_w<7>(w, f) ||
+           nu_try_w<8>(w, f) || nu_try_w<9>(w, f) || nu_try_w<10>(w, f) || nu_try_w<11>(w, f) ||
+           nu_try_w<12>(w, f) || nu_try_w<13>(w, f) || nu_try_w<14>(w, f) || nu_try_w<15>(w, f) ||
+           nu_try_w<16>(w, f);
+}
+template <typename F>
+bool nu_with_mixed(int w, int D, F&& f) {
+    auto wd = [&](auto wc, auto dc) {
+        if (wc.value != w || dc.value != D) return false;
+        f(wc, dc);
+        return true;
+    };
+    using I4 = std::integral_constant<int, 4>;
+    using I5 = std::integral_constant<int, 5>;
+    using I6 = std::integral_constant<int, 6>;
+    using I7 = std::integral_constant<int, 7>;
+    using I8 = std::integral_constant<int, 8>;
+    using I10 = std::integral_constant<int, 10>;
+    return wd(I4{}, I6{}) || wd(I4{}, I8{}) || wd(I4{}, I10{}) || wd(I5{}, I6{}) || wd(I5{}, I8{}) ||
+           wd(I5{}, I10{}) || wd(I6{}, I6{}) || wd(I6{}, I8{}) || wd(I6{}, I10{}) || wd(I7{}, I6{}) ||
+           wd(I7{}, I8{}) || wd(I7{}, I10{});
 }
 
 int ilog2n(int v) {
     int l = 0;
     while ((1 << l) < v) l++;
     return l;
-}
-
-// least-squares monomial fit of degree D in y in [-1, 1] to f at n Chebyshev points (normal
-// equations in long double; D <= 16 and smooth f)
-std::vector<double> fit_poly(const std::vector<double>& ys, const std::vector<double>& fs, int D) {
-    const int n = (int)ys.size(), m = D + 1;
-    std::vector<long double> A((size_t)m * m, 0.0L), b(m, 0.0L);
-    for (int i = 0; i < n; i++) {
-        long double p[kMaxDegree + 1];
-        p[0] = 1.0L;
-        for (int d = 1; d < m; d++) p[d] = p[d - 1] * (long double)ys[i];
-        for (int r = 0; r < m; r++) {
-            b[r] += p[r] * (long double)fs[i];
-            for (int q = 0; q < m; q++) A[(size_t)r * m + q] += p[r] * p[q];
-        }
-    }
-    // Gaussian elimination with partial pivoting
-    for (int col = 0; col < m; col++) {
-        int piv = col;
-        for (int r = col + 1; r < m; r++)
-            if (std::fabs((double)A[(size_t)r * m + col]) > std::fabs((double)A[(size_t)piv * m + col])) piv = r;
-        if (piv != col) {
-            for (int q = 0; q < m; q++) std::swap(A[(size_t)col * m + q], A[(size_t)piv * m + q]);
-            std::swap(b[col], b[piv]);
-        }
-        for (int r = col + 1; r < m; r++) {
-            long double f = A[(size_t)r * m + col] / A[(size_t)col * m + col];
-            for (int q = col; q < m; q++) A[(size_t)r * m + q] -= f * A[(size_t)col * m + q];
-            b[r] -= f * b[col];
-        }
-    }
-    std::vector<double> c(m, 0.0);
-    for (int r = m - 1; r >= 0; r--) {
-        long double s = b[r];
-        for (int q = r + 1; q < m; q++) s -= A[(size_t)r * m + q] * (long double)c[q];
-        c[r] = (double)(s / A[(size_t)r * m + r]);
-    }
-    return c;
 }
 
 }  // namespace
@@ -410,7 +546,8 @@ struct wave1d_nufft_s {
     NuUnit* units = nullptr;
     int64_t nunits = 0;
     double* partial = nullptr;
-    int32_t *cptr = nullptr, *cent = nullptr;
+    int32_t *runs = nullptr, *cptr = nullptr, *cent = nullptr;
+    int32_t* cnt = nullptr;          // per grid real: units that have stored their partial (zero between calls)
     // FFT and deconvolution
     double *grid = nullptr, *work = nullptr, *spec = nullptr, *spec2 = nullptr, *twiddle = nullptr,
            *modefac = nullptr;
@@ -450,6 +587,7 @@ int wave1d_nufft_plan(const double* x, int64_t M, int K, double tol, int precisi
     *out = nullptr;
     if (!x || M < 1 || M > INT32_MAX / 32 || K < 1 || !(tol > 0.0 && tol < 0.1) || (precision != 0 && precision != 1))
         return nfail(WAVE1D_EINVAL, "need x, 1 <= M < 2^26, K >= 1, 0 < tol < 0.1, precision 0 or 1");
+    if (precision == 1 && tol < 1e-6) return nfail(WAVE1D_EINVAL, "mixed precision needs tol >= 1e-6");
     wave1d_nufft_t h = new (std::nothrow) wave1d_nufft_s();
     if (!h) return nfail(WAVE1D_ENOMEM, "host allocation");
     auto cleanup = [&](int code) {
@@ -513,33 +651,58 @@ int wave1d_nufft_plan(const double* x, int64_t M, int K, double tol, int precisi
             double r = 1.0 - z * z;
             return r > 0.0 ? std::cyl_bessel_i(0.0, P.kb_beta * std::sqrt(r)) * inv_i0b : 0.0;
         };
-        // degrees 6, 8, ..., 16 (the ones the kernels are built for): the first within 2e-7
+        // Chebyshev series of degree 6, 8 or 10 (the ones the kernels are built for): the first
+        // within max(3e-7, tol / 5) of the kernel (FP32 evaluation alone errs by about 1.7e-7), checked
+        // in FP32 in the device's order.  Taps
+        // t < w/2 are fitted (coefficients from the discrete Chebyshev transform at ns nodes, a
+        // near-minimax truncation); tap w-1-t mirrors t, and the middle tap of an odd w keeps only
+        // its even terms.
+        if (w > kMixedMaxW) return cleanup(nfail(WAVE1D_EINVAL, "mixed precision: kernel width above 7"));
+        const double fit_tol = std::max(3e-7, tol / 5);
         int D = 6;
         double err = 1.0;
         for (;; D += 2) {
-            err = 0.0;
-            for (int t = 0; t < w; t++) {
-                std::vector<double> fs(ns);
-                for (int i = 0; i < ns; i++) fs[i] = kernel(ys[i], t);
-                std::vector<double> c = fit_poly(ys, fs, D);
-                for (int d = 0; d <= kMaxDegree; d++) h->poly.c[t][d] = d <= D ? (float)c[d] : 0.f;
-                for (int i = 0; i <= 400; i++) {          // FP32 Horner, as on the device
-                    float y = (float)(-1.0 + 2.0 * i / 400.0);
-                    float r = h->poly.c[t][D];
-                    for (int d = D - 1; d >= 0; d--) r = std::fma(r, y, h->poly.c[t][d]);
-                    err = std::max(err, std::fabs((double)r - kernel((double)y, t)));
+            std::memset(&h->poly, 0, sizeof(h->poly));
+            for (int t = 0; t < (w + 1) / 2; t++) {
+                for (int d = 0; d <= D; d++) {
+                    double acc = 0.0;
+                    for (int i = 0; i < ns; i++) acc += kernel(ys[i], t) * std::cos(d * kPiN * (i + 0.5) / ns);
+                    double ad = (d == 0 ? 1.0 : 2.0) * acc / ns;
+                    if (2 * t + 1 == w && d % 2 == 1) ad = 0.0;
+                    h->poly.c[t][d] = (float)ad;
+                    h->poly.c[w - 1 - t][d] = (float)(d % 2 ? -ad : ad);
                 }
             }
-            if (err < 2e-7 || D == kMaxDegree) break;
+            // interior points: at y = -1 and +1 an end tap touches the support edge, where the
+            // kernel drops from 1/I0(beta) to 0 (a jump of the kernel itself, not of the fit)
+            err = 0.0;
+            for (int i = 1; i < 400; i++) {
+                const float y = (float)(-1.0 + 2.0 * i / 400.0);
+                float T[kMaxDegree + 1];
+                T[0] = 1.f;
+                T[1] = y;
+                for (int d = 2; d <= D; d++) T[d] = std::fma(y + y, T[d - 1], -T[d - 2]);
+                for (int t = 0; t < (w + 1) / 2; t++) {
+                    float e = h->poly.c[t][0], o = h->poly.c[t][1] * T[1];
+                    for (int d = 2; d <= D; d += 2) e = std::fma(h->poly.c[t][d], T[d], e);
+                    for (int d = 3; d <= D; d += 2) o = std::fma(h->poly.c[t][d], T[d], o);
+                    err = std::max(err, std::fabs((double)(e + o) - kernel((double)y, t)));
+                    err = std::max(err, std::fabs((double)(e - o) - kernel((double)y, w - 1 - t)));
+                }
+            }
+            if (err < fit_tol || D == 10) break;
         }
         h->D = D;
         h->kernel_err = err;
         if ((rc = nu_upload(h, soff, &h->soff))) return cleanup(rc);
     }
-    // spreading units: runs of at most kUnitPoints points whose first cells span < kUnitCells
-    // cells; each reaches its cells plus w - 1 (wrapped into the grid by the combine pass)
+    // spreading units: at most kUnitPoints consecutive points whose first cells lie within
+    // kUnitCells cells; each reaches its cells plus w - 1 (wrapped into the grid by the combine
+    // pass).  Run table: for each unit, the offset (from its first point) of the first point of
+    // each of its first cells, and one past the last point.
     {
         std::vector<NuUnit> units;
+        std::vector<int32_t> runs;
         int64_t poff = 0;
         for (int64_t a = 0; a < M;) {
             int64_t b = a + 1;
@@ -548,12 +711,31 @@ int wave1d_nufft_plan(const double* x, int64_t M, int K, double tol, int precisi
             u.pa = (int32_t)a;
             u.np = (int32_t)(b - a);
             u.ca = i0[a];
-            u.span = i0[b - 1] - i0[a] + w;
+            u.ncells = i0[b - 1] - i0[a] + 1;
+            u.span = u.ncells + w - 1;
             u.poff = (int32_t)poff;
+            u.roff = (int32_t)runs.size();
+            for (int f = 0, q = 0; f <= u.ncells; f++) {
+                while (q < u.np && i0[a + q] < u.ca + f) q++;
+                runs.push_back(q);
+            }
+            // lanes per run: as many as the block can give every run, at most 32 (a warp runs as
+            // long as its longest run share, so short runs gain from more lanes too)
+            u.lg = 0;
+            while (u.lg < 5 && (u.ncells << (u.lg + 1)) <= kUnitThreads) u.lg++;
             poff += u.span;
             units.push_back(u);
             a = b;
         }
+        // uncovered cells: from the end of a unit's span to the next unit's first cell (the last
+        // unit wraps round to the first one's); nobody spreads there, the unit writes zeros
+        for (size_t k = 0; k < units.size(); k++) {
+            NuUnit& u = units[k];
+            const int next = k + 1 < units.size() ? units[k + 1].ca : units[0].ca + nf;
+            u.gap0 = u.ca + u.span;
+            u.gap1 = std::max(u.gap0, next);
+        }
+        // combine table: per grid real, the partials that reach it, in unit order
         std::vector<int32_t> cptr(nf + 1, 0);
         for (const NuUnit& u : units)
             for (int l = 0; l < u.span; l++) cptr[(u.ca + l) % nf + 1]++;
@@ -562,8 +744,10 @@ int wave1d_nufft_plan(const double* x, int64_t M, int K, double tol, int precisi
         for (const NuUnit& u : units)
             for (int l = 0; l < u.span; l++) cent[fill[(u.ca + l) % nf]++] = u.poff + l;
         h->nunits = (int64_t)units.size();
-        if ((rc = nu_upload(h, units, &h->units)) || (rc = nu_upload(h, cptr, &h->cptr)) ||
+        if ((rc = nu_upload(h, units, &h->units)) || (rc = nu_upload(h, runs, &h->runs)) ||
+            (rc = nu_upload(h, cptr, &h->cptr)) ||
             (rc = nu_upload(h, cent, &h->cent)) || (rc = nu_alloc(h, (size_t)poff, &h->partial)) ||
+            (rc = nu_upload(h, std::vector<int32_t>(nf, 0), &h->cnt)) ||
             (rc = nu_upload(h, i0, &h->first)))
             return cleanup(rc);
     }
@@ -602,32 +786,37 @@ int wave1d_nufft_spread(wave1d_nufft_t h, const double* c, double* grid) {
     if (!h || !c || !grid) return nfail(WAVE1D_EINVAL, "bad arguments");
     if (cudaSetDevice(h->device) != cudaSuccess) return nfail(WAVE1D_ECUDA, "cudaSetDevice");
     const int nf = h->P.nf, w = h->P.nufft_w;
-    const unsigned nu = (unsigned)h->nunits, nc = (unsigned)((nf + 255) / 256);
+    const unsigned nu = (unsigned)h->nunits;
+    bool ok;
     if (h->precision == 0) {
-        k_nu_spread64<<<nu, kUnitPoints, 0, h->stream>>>(h->units, c, h->first, h->ker, w, h->partial);
-        k_nu_combine64<<<nc, 256, 0, h->stream>>>(h->partial, h->cptr, h->cent, grid, nf);
+        ok = nu_with_w(w, [&](auto wc) {
+            k_nu_spread64<decltype(wc)::value><<<nu, kUnitThreads, 0, h->stream>>>(
+                h->units, h->runs, c, h->ker, h->partial, h->cptr, h->cent, h->cnt, grid, nf);
+        });
     } else {
         float2* part = reinterpret_cast<float2*>(h->partial);
-        nu_with_degree(h->D, [&](auto dc) {
-            k_nu_spread_mixed<decltype(dc)::value><<<nu, kUnitPoints, 0, h->stream>>>(h->units, c, h->first, h->soff,
-                                                                                    h->poly, w, part);
+        ok = nu_with_mixed(w, h->D, [&](auto wc, auto dc) {
+            k_nu_spread_mixed<decltype(wc)::value, decltype(dc)::value><<<nu, kUnitThreads, 0, h->stream>>>(
+                h->units, h->runs, c, h->soff, h->poly, part, h->cptr, h->cent, h->cnt, grid, nf);
         });
-        k_nu_combine32<<<nc, 256, 0, h->stream>>>(part, h->cptr, h->cent, grid, nf);
     }
+    if (!ok) return nfail(WAVE1D_EUNSUPPORTED, "kernel width / degree not built");
     return cudaGetLastError() == cudaSuccess ? WAVE1D_OK : nfail(WAVE1D_ECUDA, "spread launch failed");
 }
 
 int wave1d_nufft_interp(wave1d_nufft_t h, const double* grid, double* u) {
     if (!h || !grid || !u) return nfail(WAVE1D_EINVAL, "bad arguments");
     if (cudaSetDevice(h->device) != cudaSuccess) return nfail(WAVE1D_ECUDA, "cudaSetDevice");
-    const unsigned nb = (unsigned)std::min<int64_t>((h->M + 255) / 256, 1 << 20);
-    if (h->precision == 0)
-        k_nu_interp64<<<nb, 256, 0, h->stream>>>(grid, u, h->first, h->ker, h->M, h->P.nufft_w, h->P.nf);
-    else
-        nu_with_degree(h->D, [&](auto dc) {
-            k_nu_interp_mixed<decltype(dc)::value><<<(unsigned)h->nunits, kUnitPoints, 0, h->stream>>>(
-                h->units, grid, u, h->first, h->soff, h->poly, h->P.nufft_w, h->P.nf);
-        });
+    if (h->precision == 0) {
+        k_nu_interp64<<<(unsigned)((h->M + kInterpTile - 1) / kInterpTile), kInterpTile, 0, h->stream>>>(
+            grid, u, h->first, h->ker, h->M, h->P.nufft_w, h->P.nf);
+    } else if (!nu_with_mixed(h->P.nufft_w, h->D, [&](auto wc, auto dc) {
+                   const unsigned nb = (unsigned)((h->M + 256 * kInterpPer - 1) / (256 * kInterpPer));
+                   k_nu_interp_mixed<decltype(wc)::value, decltype(dc)::value><<<nb, 256, 0, h->stream>>>(
+                       grid, u, h->first, h->soff, h->poly, h->M, h->P.nf);
+               })) {
+        return nfail(WAVE1D_EUNSUPPORTED, "kernel width / degree not built");
+    }
     return cudaGetLastError() == cudaSuccess ? WAVE1D_OK : nfail(WAVE1D_ECUDA, "interp launch failed");
 }
 

@@ -2,7 +2,8 @@
 
 type-1 S_k = (1/2 pi) sum_j c_j e^{+ikx_j} (eq. densco) and type-2 u_j = sum_{|k|<=K} alpha_k
 e^{-ikx_j} (eq. historySol1), in FP64 (kernel weights precomputed) and in mixed precision (FP32
-kernel polynomials, compensated FP32 sums, FP64 FFT).  Error: max |gpu - direct| / max |direct|
+kernel Chebyshev series, moments and sums in FP32 with the dominant terms compensated, FP64 FFT).
+Error: max |gpu - direct| / max |direct|
 over the whole output.  Bars: FP64 at tol 1e-12 -> 1e-10 (the plan's NUFFT accuracy); mixed at tol
 1e-6 -> 1e-6 (the mixed mode's stated accuracy).  At M = 1e6 (the clustered periodic workload)
 the direct sums are taken at sampled modes and points.
@@ -71,7 +72,7 @@ def test_nufft_against_direct_sums(precision, tol, bar):
     print(f"precision {precision} tol {tol}: type-1 {eS:.2e} type-2 {eu:.2e}")
     assert eS < bar and eu < bar
     if precision == 1:
-        assert nu.kernel_err < 2e-7
+        assert nu.kernel_err < 3e-7
 
 
 def test_nufft_small_and_ragged():
@@ -112,3 +113,33 @@ def test_nufft_clustered_million_points_sampled():
         eu = _rel(u[js], u_ref)
         print(f"M=1e6 precision {precision}: type-1 {eS:.2e} type-2 {eu:.2e}")
         assert eS < bar and eu < bar
+
+
+def test_nufft_dense_cells_and_wrap():
+    """Runs longer than a spreading unit: 6000 points within 1e-9 of one position, 3000 in a second
+    cell, 2000 straddling the periodic seam at -pi / +pi, 1000 uniform; K = 400."""
+    rng = np.random.default_rng(99)
+    x = np.concatenate([1.234 + 1e-9 * rng.standard_normal(6000),
+                        -0.5 + 1e-4 * rng.uniform(size=3000),
+                        np.pi - 1e-3 * rng.uniform(size=1000),
+                        -np.pi + 1e-3 * rng.uniform(size=1000),
+                        rng.uniform(-np.pi, np.pi, 1000)])
+    M, K = x.size, 400
+    c = rng.uniform(0.5, 1.5, M) * np.where(rng.uniform(size=M) < 0.7, 1.0, -1.0)
+    alpha = (rng.standard_normal(K + 1) + 1j * rng.standard_normal(K + 1)) / (1.0 + np.arange(K + 1) / 50.0)
+    alpha[0] = alpha[0].real
+    S_ref, u_ref = wfp.type1(c, x, K), wfp.type2(alpha, x)
+    for precision, tol, bar in ((0, 1e-12, 1e-10), (1, 1e-6, 1e-6)):
+        nu = wave1d.Nufft(x, K, tol, precision)
+        try:
+            S, u = _run(nu, c, alpha)
+        finally:
+            nu.close()
+        eS, eu = _rel(S, S_ref), _rel(u, u_ref)
+        print(f"dense cells precision {precision}: type-1 {eS:.2e} type-2 {eu:.2e}")
+        assert eS < bar and eu < bar
+
+
+def test_nufft_mixed_needs_tol_1e6():
+    with pytest.raises(wave1d.Wave1DError):
+        wave1d.Nufft(np.zeros(4), 8, 1e-8, 1)
