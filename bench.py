@@ -423,6 +423,26 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_spread_interp_only(args):
+    """The M = 1e6 spreading / interpolation measurement alone (one JSON line), e.g. under ncu."""
+    import torch
+
+    from paper_2507_07823_gb300 import build
+
+    build.build()
+    hbm, _ = _peaks()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    clean = torch.ones(L2_CLEAN_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def flush_l2():
+        flush.zero_()
+        clean.sum()
+
+    print(json.dumps({"spread_interp_M1e6": spread_interp_million(torch, stream, flush_l2, hbm,
+                                                                   reps=args.spread_interp_reps)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -433,8 +453,13 @@ def main():
     ap.add_argument("--ref-max-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-spread-interp", action="store_true")
+    ap.add_argument("--spread-interp-only", action="store_true",
+                    help="only the M = 1e6 spreading / interpolation timings (not a benchmark line)")
+    ap.add_argument("--spread-interp-reps", type=int, default=20)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.spread_interp_only:
+        run_spread_interp_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)
