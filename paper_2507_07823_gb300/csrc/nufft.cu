@@ -156,9 +156,7 @@ struct NuUnit {
 // order (the order the combine table lists), writes the real and clears the counter for the
 // next call.  No thread waits on another, and the sum does not depend on who arrives last.
 __device__ __forceinline__ double nu_value(double v) { return v; }
-__device__ __forceinline__ double nu_value(float2 v) { return nu_f32_to_f64(v.x) + nu_f32_to_f64(v.y); }
 __device__ __forceinline__ void nu_accum(double& a, double v) { a += v; }
-__device__ __forceinline__ void nu_accum(float2& a, float2 v) { nu_pair_add(a.x, a.y, v.x, v.y); }
 template <typename V>
 __device__ __forceinline__ void nu_emit(int r, int slot, V v, int e0, int e1, V* __restrict__ partial,
                                         const int32_t* __restrict__ cent, int* __restrict__ cnt,
@@ -249,57 +247,75 @@ __global__ void __launch_bounds__(kUnitThreads) k_nu_spread64(const NuUnit* __re
 // Mixed precision by Chebyshev moments.  With psi_t(y) = sum_d a[t][d] T_d(y),
 //   G[g] = sum_t sum_{q: i0_q = g - t} c_q psi_t(y_q) = sum_t sum_d a[t][d] M_d(g - t),
 //   M_d(f) = sum_{q: i0_q = f} c_q T_d(y_q),
-// so a point costs D + 1 FMAs (its moments) instead of w kernel evaluations.  The unit's (c, y)
-// are staged in shared memory; each run's lanes accumulate the run's moments and a fixed shuffle
-// tree adds them; cell l of the unit then takes sum_t sum_d a[t][d] M_d(l - t).  The dominant
-// terms are compensated: M_0 (the run's plain sum of c) is an FP32 pair, and the d = 0 products
-// a[t][0] M_0 enter the cell's pair exactly (two-product by FMA); the higher moments, which
-// cancel over a run and carry small coefficients, are plain FP32 (a[t][d] sum to about max psi,
-// so the assembly is well conditioned).  The cell's partial is an FP32 pair.
+// so a point costs D + 1 FMAs (its moments) and each grid real w (D + 1) multiply-adds.
+//
+// Work split: the grid is tiled by cell ranges [c0, c0 + nc) (at most kUnitCells cells, and at
+// most kRangePoints points counting the w - 1 cells before the range, the halo).  A block takes a
+// range: it stages the (c, y) of the points whose first cell lies in [c0 - w + 1, c0 + nc) in
+// shared memory (one or two slices of the sorted points: the halo of the first range wraps round
+// the periodic box), gives each of those nc + w - 1 cells a group of G lanes that accumulate the
+// cell's moments (a fixed shuffle tree closes each group), and then writes every grid real of its
+// range complete.  The halo cells' moments are computed twice, by this block and by the
+// previous one; in exchange no block depends on another (no partials, atomics or second pass),
+// each grid real is written once, and the result does not depend on scheduling.  A range whose
+// points exceed kStage (a cell holding thousands of points) reads them from global memory.
+// M_0 and the d = 0 terms are compensated FP32 pairs (they carry the magnitude); the higher
+// moments cancel over a cell and carry small coefficients, so they are plain FP32.
+constexpr int kStage = 2048;        // staging capacity (points) of a range
+constexpr int kRangePoints = 2048;  // points a range is cut at, halo included (one cell may exceed it)
+struct NuRange {
+    int32_t a0, na, b0, nb;        // staged points: slices [a0, a0 + na) then [b0, b0 + nb) of the sorted order
+    int32_t c0, nc, roff, lg;      // first cell, cells, offset of its run table (nc + w entries), log2 lanes per cell
+};
+
 template <int W, int D>
-__global__ void __launch_bounds__(kUnitThreads) k_nu_spread_mixed(
-    const NuUnit* __restrict__ units, const int32_t* __restrict__ runs, const double* __restrict__ c,
-    const float* __restrict__ soff, const NuPoly P, float2* __restrict__ partial, const int32_t* __restrict__ cptr,
-    const int32_t* __restrict__ cent, int* __restrict__ cnt, double* __restrict__ grid, int nf) {
+__global__ void __launch_bounds__(kUnitThreads) k_nu_spread_mixed(const NuRange* __restrict__ ranges,
+                                                                  const int32_t* __restrict__ runs,
+                                                                  const double* __restrict__ c,
+                                                                  const float* __restrict__ soff, const NuPoly P,
+                                                                  double* __restrict__ grid) {
     constexpr int R = (D + 2 + 3) / 4 * 4;            // moment row: M_0 (hi, lo), M_1 .. M_D, padded to float4
-    __shared__ int rp[kUnitCells + 1];
-    __shared__ float2 cy[kUnitPoints];
-    __shared__ __align__(16) float mo[kUnitCells][R];
-    const NuUnit u = units[blockIdx.x];
-    if ((int)threadIdx.x <= u.ncells) rp[threadIdx.x] = __ldg(runs + u.roff + threadIdx.x);
-    // this thread's cell of the span (one pass: span <= kUnitCells + 15 < kUnitThreads) and its
-    // combine-table range, fetched now so the loads overlap the spreading
-    const int r_cell = (u.ca + (int)threadIdx.x) % nf;
-    const int e0 = (int)threadIdx.x < u.span ? __ldg(cptr + r_cell) : 0;
-    const int e1 = (int)threadIdx.x < u.span ? __ldg(cptr + r_cell + 1) : 0;
-    {
-        // stage the unit's densities and offsets with every thread's loads in flight at once
-        float sv[kUnitPoints / kUnitThreads];
-        double cd[kUnitPoints / kUnitThreads];
+    constexpr int kPer = kStage / kUnitThreads;
+    __shared__ int rp[kUnitCells + 16 + 1];
+    __shared__ float2 cy[kStage];
+    __shared__ __align__(16) float mo[kUnitCells + 16][R];
+    const NuRange u = ranges[blockIdx.x];
+    const int nr = u.nc + W - 1, np = u.na + u.nb;
+    const bool staged = np <= kStage;
+    if ((int)threadIdx.x <= nr) rp[threadIdx.x] = __ldg(runs + u.roff + threadIdx.x);
+    if (staged) {
+        double cd[kPer];
+        float sv[kPer];
 #pragma unroll
-        for (int i = 0; i < kUnitPoints / kUnitThreads; i++) {
+        for (int i = 0; i < kPer; i++) {
             const int q = (int)threadIdx.x + i * kUnitThreads;
-            if (q < u.np) {
-                cd[i] = __ldcs(c + u.pa + q);
-                sv[i] = __ldcs(soff + u.pa + q);
+            if (q < np) {
+                const int j = q < u.na ? u.a0 + q : u.b0 + (q - u.na);
+                cd[i] = __ldcs(c + j);
+                sv[i] = __ldcs(soff + j);
             }
         }
 #pragma unroll
-        for (int i = 0; i < kUnitPoints / kUnitThreads; i++) {
+        for (int i = 0; i < kPer; i++) {
             const int q = (int)threadIdx.x + i * kUnitThreads;
-            if (q < u.np) cy[q] = make_float2(nu_f64_to_f32(cd[i]), __fmaf_rn(2.f, sv[i], -1.f));
+            if (q < np) cy[q] = make_float2(nu_f64_to_f32(cd[i]), __fmaf_rn(2.f, sv[i], -1.f));
         }
     }
     __syncthreads();
     const int G = 1 << u.lg, f = (int)threadIdx.x >> u.lg, gl = (int)threadIdx.x & (G - 1);
-    // a lane's share of a run is about eight points: plain FP32 sums there, pairs for M_0 above
     float m[D + 1];
 #pragma unroll
     for (int d = 0; d <= D; d++) m[d] = 0.f;
-    if (f < u.ncells) {
+    if (f < nr) {
         const int q1 = rp[f + 1];
         for (int q = rp[f] + gl; q < q1; q += G) {
-            const float2 v = cy[q];
+            float2 v;
+            if (staged) {
+                v = cy[q];
+            } else {
+                const int j = q < u.na ? u.a0 + q : u.b0 + (q - u.na);
+                v = make_float2(nu_f64_to_f32(__ldcs(c + j)), __fmaf_rn(2.f, __ldcs(soff + j), -1.f));
+            }
             const NuCheb<D> ch(v.y);
             m[0] = __fadd_rn(m[0], v.x);
 #pragma unroll
@@ -312,33 +328,32 @@ __global__ void __launch_bounds__(kUnitThreads) k_nu_spread_mixed(
 #pragma unroll
         for (int d = 1; d <= D; d++) m[d] = __fadd_rn(m[d], __shfl_xor_sync(0xffffffffu, m[d], o));
     }
-    if (gl == 0 && f < u.ncells) {
+    if (gl == 0 && f < nr) {
         mo[f][0] = m[0];
         mo[f][1] = m0l;
 #pragma unroll
         for (int d = 1; d <= D; d++) mo[f][d + 1] = m[d];
     }
     __syncthreads();
-    if ((int)threadIdx.x < u.span) {
+    if ((int)threadIdx.x < u.nc) {
+        // grid real c0 + l takes tap t of cell c0 + l - t, i.e. run (l + w - 1) - t
         const int l = threadIdx.x;
         float h = 0.f, lo = 0.f, r = 0.f;
 #pragma unroll
         for (int t = 0; t < W; t++) {
-            if (l - t >= 0 && l - t < u.ncells) {
-                float mf[R];
+            float mf[R];
 #pragma unroll
-                for (int k = 0; k < R; k += 4) *reinterpret_cast<float4*>(mf + k) = *reinterpret_cast<const float4*>(&mo[l - t][k]);
-                const float p = __fmul_rn(P.c[t][0], mf[0]);
-                const float e = __fmaf_rn(P.c[t][0], mf[1], __fmaf_rn(P.c[t][0], mf[0], -p));
-                nu_pair_add(h, lo, p, e);
+            for (int k = 0; k < R; k += 4)
+                *reinterpret_cast<float4*>(mf + k) = *reinterpret_cast<const float4*>(&mo[l + W - 1 - t][k]);
+            const float p = __fmul_rn(P.c[t][0], mf[0]);
+            const float e = __fmaf_rn(P.c[t][0], mf[1], __fmaf_rn(P.c[t][0], mf[0], -p));
+            nu_pair_add(h, lo, p, e);
 #pragma unroll
-                for (int d = 1; d <= D; d++) r = __fmaf_rn(P.c[t][d], mf[d + 1], r);
-            }
+            for (int d = 1; d <= D; d++) r = __fmaf_rn(P.c[t][d], mf[d + 1], r);
         }
         nu_pair_add(h, lo, r, 0.f);
-        nu_emit(r_cell, u.poff + l, make_float2(h, lo), e0, e1, partial, cent, cnt, grid);
+        grid[u.c0 + l] = nu_f32_to_f64(h) + nu_f32_to_f64(lo);
     }
-    nu_gap(u, grid, nf);
 }
 
 // type-1 post-processing: S_k from the half-length FFT Z (E, O split) with the deconvolution
@@ -543,7 +558,8 @@ struct wave1d_nufft_s {
     NuPoly poly{};                   // tap polynomials (mixed), passed to the kernels by value
     double* ker = nullptr;
     // spreading units and the cells' partials
-    NuUnit* units = nullptr;
+    NuUnit* units = nullptr;         // FP64 spreading units
+    NuRange* ranges = nullptr;       // mixed spreading ranges
     int64_t nunits = 0;
     double* partial = nullptr;
     int32_t *runs = nullptr, *cptr = nullptr, *cent = nullptr;
@@ -696,11 +712,11 @@ int wave1d_nufft_plan(const double* x, int64_t M, int K, double tol, int precisi
         h->kernel_err = err;
         if ((rc = nu_upload(h, soff, &h->soff))) return cleanup(rc);
     }
-    // spreading units: at most kUnitPoints consecutive points whose first cells lie within
+    // FP64 spreading units: at most kUnitPoints consecutive points whose first cells lie within
     // kUnitCells cells; each reaches its cells plus w - 1 (wrapped into the grid by the combine
     // pass).  Run table: for each unit, the offset (from its first point) of the first point of
     // each of its first cells, and one past the last point.
-    {
+    if (precision == 0) {
         std::vector<NuUnit> units;
         std::vector<int32_t> runs;
         int64_t poff = 0;
@@ -750,6 +766,56 @@ int wave1d_nufft_plan(const double* x, int64_t M, int K, double tol, int precisi
             (rc = nu_upload(h, std::vector<int32_t>(nf, 0), &h->cnt)) ||
             (rc = nu_upload(h, i0, &h->first)))
             return cleanup(rc);
+    } else {
+        // mixed spreading ranges: consecutive cell ranges tiling the grid, each at most
+        // kUnitCells cells and (where a single cell allows) at most kRangePoints points counting
+        // the w - 1 halo cells before it.  ps[f] = first point (sorted order) whose first cell is >= f.
+        std::vector<int32_t> ps(nf + 1, 0);
+        for (int64_t i = 0; i < M; i++) ps[i0[i] + 1]++;
+        for (int f = 0; f < nf; f++) ps[f + 1] += ps[f];
+        auto pts = [&](int f0, int f1) {          // points whose first cell is in [f0, f1), f0 may be < 0
+            if (f0 >= 0) return ps[f1] - ps[f0];
+            return (ps[nf] - ps[nf + f0]) + ps[f1];
+        };
+        std::vector<NuRange> ranges;
+        std::vector<int32_t> runs;
+        for (int c0 = 0; c0 < nf;) {
+            int c1 = c0 + 1;
+            while (c1 < nf && c1 - c0 < kUnitCells && pts(c0 - w + 1, c1 + 1) <= kRangePoints) c1++;
+            NuRange r{};
+            r.c0 = c0;
+            r.nc = c1 - c0;
+            const int h0 = c0 - w + 1;            // first halo cell (negative: wraps to the end)
+            if (h0 >= 0) {
+                r.a0 = ps[h0];
+                r.na = ps[c1] - ps[h0];
+                r.b0 = 0;
+                r.nb = 0;
+            } else {
+                r.a0 = ps[nf + h0];
+                r.na = ps[nf] - ps[nf + h0];
+                r.b0 = 0;
+                r.nb = ps[c1];
+            }
+            r.roff = (int32_t)runs.size();
+            for (int k = 0; k <= r.nc + w - 1; k++) {        // run starts in staging order, then the end
+                const int f = h0 + k;
+                int off;
+                if (k == r.nc + w - 1) off = r.na + r.nb;
+                else if (f >= 0) off = (h0 >= 0 ? ps[f] - r.a0 : r.na + ps[f]);
+                else off = ps[nf + f] - r.a0;
+                runs.push_back(off);
+            }
+            const int nr = r.nc + w - 1;
+            r.lg = 0;
+            while (r.lg < 5 && (nr << (r.lg + 1)) <= kUnitThreads) r.lg++;
+            ranges.push_back(r);
+            c0 = c1;
+        }
+        h->nunits = (int64_t)ranges.size();
+        if ((rc = nu_upload(h, ranges, &h->ranges)) || (rc = nu_upload(h, runs, &h->runs)) ||
+            (rc = nu_upload(h, i0, &h->first)))
+            return cleanup(rc);
     }
     std::vector<double> d1, d2, mf, tw((size_t)P.L * 2);
     nufft_factors(P, d1, d2, mf);
@@ -794,10 +860,9 @@ int wave1d_nufft_spread(wave1d_nufft_t h, const double* c, double* grid) {
                 h->units, h->runs, c, h->ker, h->partial, h->cptr, h->cent, h->cnt, grid, nf);
         });
     } else {
-        float2* part = reinterpret_cast<float2*>(h->partial);
         ok = nu_with_mixed(w, h->D, [&](auto wc, auto dc) {
             k_nu_spread_mixed<decltype(wc)::value, decltype(dc)::value><<<nu, kUnitThreads, 0, h->stream>>>(
-                h->units, h->runs, c, h->soff, h->poly, part, h->cptr, h->cent, h->cnt, grid, nf);
+                h->ranges, h->runs, c, h->soff, h->poly, grid);
         });
     }
     if (!ok) return nfail(WAVE1D_EUNSUPPORTED, "kernel width / degree not built");
