@@ -282,6 +282,7 @@ def run_ours(args):
     plan.close()
     if not args.no_spread_interp:
         line["spread_interp_M1e6"] = spread_interp_million(torch, stream, flush_l2, hbm)
+        line["spread_interp_batched"] = spread_interp_batched(torch, stream, flush_l2, hbm)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_steps)
     if rank == 0:
@@ -335,6 +336,50 @@ def spread_interp_million(torch, stream, flush_l2, hbm, reps=20):
                      "kernel": ("precomputed FP64 weights (8 B per point and tap read in each pass)"
                                 if precision == 0 else
                                 f"FP32 polynomials of degree {nu.degree} (max error {nu.kernel_err:.1e})")}
+        nu.close()
+    return out
+
+
+def spread_interp_batched(torch, stream, flush_l2, hbm, reps=10):
+    """A1 and A6 of the batched workload's instances (256 periodic instances, M log-uniform in
+    [1e2, 1e5], dt = 1e-3: K = 3141) in one batched plan: one launch per pass over all instances,
+    FP64 (tol 1e-12, as the workload) and mixed (tol 1e-6).  Each pass is timed with events after
+    an L2 flush.  Algorithmic bytes: 32 per point (all instances)."""
+    from paper_2507_07823_gb300 import wave1d, workloads
+    inst = workloads.config3_instances()
+    K = int(np.floor(np.pi / inst[0].dt))
+    sets = [w.x for w in inst]
+    Mtot = int(sum(v.size for v in sets))
+    out = {"workload": f"{len(sets)} periodic instances, M log-uniform in [1e2, 1e5] (sum {Mtot}), K = {K}",
+           "instances": len(sets), "M_total": Mtot, "K": K, "algorithmic_bytes": 32 * Mtot}
+    for name, precision, tol in (("fp64", 0, 1e-12), ("mixed", 1, 1e-6)):
+        t0 = time.perf_counter()
+        nu = wave1d.Nufft(sets, K, tol, precision, stream=stream.cuda_stream)
+        t_plan = time.perf_counter() - t0
+        c = torch.rand(Mtot, dtype=torch.float64, device="cuda") + 0.5
+        grid = torch.zeros(len(sets) * nu.nf, dtype=torch.float64, device="cuda")
+        u = torch.zeros(Mtot, dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            nu.spread(c, grid)
+            nu.interp(grid, u)
+        ts, ti = [], []
+        for _ in range(reps):
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            flush_l2()
+            ev[0].record(stream)
+            nu.spread(c, grid)
+            ev[1].record(stream)
+            flush_l2()
+            ev[2].record(stream)
+            nu.interp(grid, u)
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+            ts.append(ev[0].elapsed_time(ev[1]))
+            ti.append(ev[2].elapsed_time(ev[3]))
+        t_s, t_i = float(np.median(ts)), float(np.median(ti))
+        achieved = 32 * Mtot / ((t_s + t_i) * 1e-3) / 1e9
+        out[name] = {"tol": tol, "kernel_width": nu.w, "spread_us": 1e3 * t_s, "interp_us": 1e3 * t_i,
+                     "achieved_GBps": achieved, "frac_of_hbm": achieved / hbm, "plan_seconds": t_plan}
         nu.close()
     return out
 
@@ -440,7 +485,9 @@ def run_spread_interp_only(args):
         clean.sum()
 
     print(json.dumps({"spread_interp_M1e6": spread_interp_million(torch, stream, flush_l2, hbm,
-                                                                   reps=args.spread_interp_reps)}))
+                                                                   reps=args.spread_interp_reps),
+                      "spread_interp_batched": spread_interp_batched(torch, stream, flush_l2, hbm,
+                                                                     reps=args.spread_interp_reps)}))
 
 
 def main():

@@ -216,9 +216,10 @@ int wave1d_state_load(wave1d_plan_t plan, const void* buf, size_t bytes);
  * and their spreading (A1: grid G from c) and interpolation (A6: u from a grid) passes alone.
  *   wave1d_nufft_plan: x host, M positions (wrapped into [-pi, pi)); tol sets the kernel width as
  *       in wave1d_plan; precision 0 = FP64 (kernel weights precomputed), 1 = mixed (kernel values
- *       from FP32 polynomials fitted to about 1e-7 of the kernel's peak, compensated FP32 sums, FP64
- *       FFT and deconvolution; for tol >= 1e-6).  stream: cudaStream_t of every call (NULL =
- *       legacy default stream).  Allocates the plan's device arrays.
+ *       from FP32 Chebyshev series fitted to about 2e-7 of the kernel's peak, FP32 sums with the
+ *       dominant terms compensated, FP64 FFT and deconvolution; tol >= 1e-6, else
+ *       WAVE1D_EINVAL).  stream: cudaStream_t of every call (NULL = legacy default stream).
+ *       Allocates the plan's device arrays.
  *   Point arrays (c, u) are device arrays of M FP64 in the plan's point order: point i is the
  *   caller's point perm[i] (wave1d_nufft_perm, host array of M).  S and alpha: device, K + 1
  *   complex (re, im interleaved).  grid: device, nf reals (wave1d_nufft_info).  Calls are queued on
@@ -230,6 +231,17 @@ int wave1d_state_load(wave1d_plan_t plan, const void* buf, size_t bytes);
 typedef struct wave1d_nufft_s* wave1d_nufft_t;
 int wave1d_nufft_plan(const double* x, int64_t M, int K, double tol, int precision, void* stream,
                       wave1d_nufft_t* out);
+/*
+ * Batched form: n_instances independent point sets with the same K and tol, one launch per pass
+ * over all of them (the batched workload's instances, Sec. 6 shapes).  x: host, the instances'
+ * positions one after another, instance i being x[offsets[i] .. offsets[i+1]) (offsets: host,
+ * n_instances + 1 values, offsets[0] = 0, every instance with at least one point).  Point arrays
+ * (c, u) hold all instances' points in the plan's order (perm keeps each instance within its
+ * own segment); grid: n_instances x nf reals, instance-major; S and alpha: n_instances x (K + 1)
+ * complex.  wave1d_nufft_plan(x, M, ...) is the one-instance case.
+ */
+int wave1d_nufft_plan_many(const double* x, const int64_t* offsets, int n_instances, int K, double tol,
+                           int precision, void* stream, wave1d_nufft_t* out);
 int wave1d_nufft_info(wave1d_nufft_t plan, int* nf, int* w, int* degree, double* kernel_err);
 int wave1d_nufft_perm(wave1d_nufft_t plan, int64_t* perm);
 int wave1d_nufft_spread(wave1d_nufft_t plan, const double* c, double* grid);

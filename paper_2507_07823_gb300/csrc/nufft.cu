@@ -127,129 +127,19 @@ __device__ __forceinline__ void nu_taps(const NuPoly& P, const NuCheb<D>& ch, fl
 }
 
 // ---------------------------------------------------------------------------------------------
-// Spreading by units (A1).  The host cuts the sorted points into units of at most kUnitPoints
-// consecutive points whose first cells lie within kUnitCells cells, and lists each unit's runs
-// (the points of one first cell, contiguous in the sorted order).  A block takes a unit.  Each
-// run gets a group of G lanes (G a power of two chosen on the host: as many as the block can give
-// every run, at most 32); the lanes stride over the run's points, evaluate each
-// point's w kernel values once and accumulate w sums, one per tap, which a fixed shuffle tree
-// adds over the group.  Cell l of the unit then collects tap t of the run at first cell l - t,
-// for t < w, and stores the unit's partial for that cell.  A second pass adds, per grid real, the
-// partials of the units that reach it, in unit order.  No atomics: the result does not depend on
-// scheduling, and a dense cluster (hundreds of points per cell) spreads over many units and lanes.
-// Mixed precision keeps the sums as compensated FP32 pairs; FP64 uses the stored weights and FMAs.
+// Spreading (A1).  The points are sorted by first cell; the grid is cut into cell ranges, each
+// range handled by one block that writes its grid reals complete (below).  No atomics: the result
+// does not depend on scheduling, and a dense cluster (hundreds of points per cell) spreads over
+// many ranges and lanes.
 // ---------------------------------------------------------------------------------------------
-constexpr int kUnitPoints = 1024;
-constexpr int kUnitCells = 64;
 constexpr int kUnitThreads = 256;
-
-struct NuUnit {
-    int32_t pa, np, ca, ncells;    // first point, points, first cell, first cells covered (<= kUnitCells)
-    int32_t span, poff, roff, lg;  // cells reached (ncells + w - 1), offset of its partials, offset of
-                                   // its run table (ncells + 1 point offsets), log2 of lanes per run
-    int32_t gap0, gap1, pad0, pad1;  // cells [gap0, gap1) (mod nf) after its span that no unit reaches
-};
-
-// The unit's value v for grid real r, its partial slot `slot`.  A real that one unit reaches is
-// written at once.  Otherwise the unit stores its partial and counts itself in (a release:
-// fence, then the integer atomic); the unit that arrives last adds all partials of r in unit
-// order (the order the combine table lists), writes the real and clears the counter for the
-// next call.  No thread waits on another, and the sum does not depend on who arrives last.
-__device__ __forceinline__ double nu_value(double v) { return v; }
-__device__ __forceinline__ void nu_accum(double& a, double v) { a += v; }
-template <typename V>
-__device__ __forceinline__ void nu_emit(int r, int slot, V v, int e0, int e1, V* __restrict__ partial,
-                                        const int32_t* __restrict__ cent, int* __restrict__ cnt,
-                                        double* __restrict__ grid) {
-    if (e1 - e0 == 1) {
-        grid[r] = nu_value(v);
-        return;
-    }
-    partial[slot] = v;
-    __threadfence();
-    if (atomicAdd(cnt + r, 1) != e1 - e0 - 1) return;
-    __threadfence();
-    V a{};
-    for (int e = e0; e < e1; e++) nu_accum(a, __ldcg(partial + __ldg(cent + e)));
-    grid[r] = nu_value(a);
-    cnt[r] = 0;
-}
-// zeros for the uncovered cells after a unit's span
-__device__ __forceinline__ void nu_gap(const NuUnit& u, double* __restrict__ grid, int nf) {
-    for (int g = u.gap0 + (int)threadIdx.x; g < u.gap1; g += blockDim.x) grid[g % nf] = 0.0;
-}
-
-// FP64: each run's lanes accumulate w tap sums of the stored weights times c (one FMA per point
-// and tap, four points' loads in flight per pass); cell l collects tap t of the run at l - t.
-template <int W>
-__global__ void __launch_bounds__(kUnitThreads) k_nu_spread64(const NuUnit* __restrict__ units,
-                                                              const int32_t* __restrict__ runs,
-                                                              const double* __restrict__ c,
-                                                              const double* __restrict__ ker,
-                                                              double* __restrict__ partial,
-                                                              const int32_t* __restrict__ cptr,
-                                                              const int32_t* __restrict__ cent,
-                                                              int* __restrict__ cnt, double* __restrict__ grid,
-                                                              int nf) {
-    __shared__ int rp[kUnitCells + 1];
-    __shared__ double seg[kUnitCells][W];
-    const NuUnit u = units[blockIdx.x];
-    if ((int)threadIdx.x <= u.ncells) rp[threadIdx.x] = __ldg(runs + u.roff + threadIdx.x);
-    // this thread's cell of the span (one pass: span <= kUnitCells + 15 < kUnitThreads) and its
-    // combine-table range, fetched now so the loads overlap the spreading
-    const int r_cell = (u.ca + (int)threadIdx.x) % nf;
-    const int e0 = (int)threadIdx.x < u.span ? __ldg(cptr + r_cell) : 0;
-    const int e1 = (int)threadIdx.x < u.span ? __ldg(cptr + r_cell + 1) : 0;
-    __syncthreads();
-    const int G = 1 << u.lg, f = (int)threadIdx.x >> u.lg, gl = (int)threadIdx.x & (G - 1);
-    double acc[W];
-#pragma unroll
-    for (int t = 0; t < W; t++) acc[t] = 0.0;
-    if (f < u.ncells) {
-        const int q1 = rp[f + 1];
-        constexpr int B = 4;
-        for (int q = rp[f] + gl; q < q1; q += B * G) {
-            double cb[B], kb[B][W];
-#pragma unroll
-            for (int i = 0; i < B; i++) {
-                const bool ok = q + i * G < q1;
-                const int64_t j = (int64_t)u.pa + (ok ? q + i * G : q);
-                cb[i] = ok ? __ldcs(c + j) : 0.0;
-#pragma unroll
-                for (int t = 0; t < W; t++) kb[i][t] = __ldcs(ker + j * W + t);
-            }
-#pragma unroll
-            for (int i = 0; i < B; i++)
-#pragma unroll
-                for (int t = 0; t < W; t++) acc[t] = fma(kb[i][t], cb[i], acc[t]);
-        }
-    }
-    for (int o = G >> 1; o > 0; o >>= 1) {
-#pragma unroll
-        for (int t = 0; t < W; t++) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
-    }
-    if (gl == 0 && f < u.ncells) {
-#pragma unroll
-        for (int t = 0; t < W; t++) seg[f][t] = acc[t];
-    }
-    __syncthreads();
-    if ((int)threadIdx.x < u.span) {
-        const int l = threadIdx.x;
-        double a = 0.0;
-#pragma unroll
-        for (int t = 0; t < W; t++)
-            if (l - t >= 0 && l - t < u.ncells) a += seg[l - t][t];
-        nu_emit(r_cell, u.poff + l, a, e0, e1, partial, cent, cnt, grid);
-    }
-    nu_gap(u, grid, nf);
-}
 
 // Mixed precision by Chebyshev moments.  With psi_t(y) = sum_d a[t][d] T_d(y),
 //   G[g] = sum_t sum_{q: i0_q = g - t} c_q psi_t(y_q) = sum_t sum_d a[t][d] M_d(g - t),
 //   M_d(f) = sum_{q: i0_q = f} c_q T_d(y_q),
 // so a point costs D + 1 FMAs (its moments) and each grid real w (D + 1) multiply-adds.
 //
-// Work split: the grid is tiled by cell ranges [c0, c0 + nc) (at most kUnitCells cells, and at
+// Work split: the grid is tiled by cell ranges [c0, c0 + nc) (at most kRangeCells cells, and at
 // most kRangePoints points counting the w - 1 cells before the range, the halo).  A block takes a
 // range: it stages the (c, y) of the points whose first cell lies in [c0 - w + 1, c0 + nc) in
 // shared memory (one or two slices of the sorted points: the halo of the first range wraps round
@@ -263,9 +153,14 @@ __global__ void __launch_bounds__(kUnitThreads) k_nu_spread64(const NuUnit* __re
 // moments cancel over a cell and carry small coefficients, so they are plain FP32.
 constexpr int kStage = 2048;        // staging capacity (points) of a range
 constexpr int kRangePoints = 2048;  // points a range is cut at, halo included (one cell may exceed it)
+constexpr int kRangeCells = 240;    // cells of a mixed range (w - 1 halo cells more fit one thread each)
+constexpr int kRangeCells64 = 128;  // cells of an FP64 range (its w tap sums per cell live in shared memory)
+constexpr int kRangePoints64 = 4096;  // FP64: its halo costs FP64 FMAs, so fewer, larger ranges
+constexpr int kEmptyCells = 8192;   // cells of a range no point reaches (zeros only)
 struct NuRange {
     int32_t a0, na, b0, nb;        // staged points: slices [a0, a0 + na) then [b0, b0 + nb) of the sorted order
-    int32_t c0, nc, roff, lg;      // first cell, cells, offset of its run table (nc + w entries), log2 lanes per cell
+    int32_t c0, nc, roff, lg;      // first grid real (instance x nf + cell), cells, offset of its run table
+                                   // (nc + w entries), log2 lanes per cell
 };
 
 template <int W, int D>
@@ -276,11 +171,15 @@ __global__ void __launch_bounds__(kUnitThreads) k_nu_spread_mixed(const NuRange*
                                                                   double* __restrict__ grid) {
     constexpr int R = (D + 2 + 3) / 4 * 4;            // moment row: M_0 (hi, lo), M_1 .. M_D, padded to float4
     constexpr int kPer = kStage / kUnitThreads;
-    __shared__ int rp[kUnitCells + 16 + 1];
+    __shared__ int rp[kRangeCells + 16 + 1];
     __shared__ float2 cy[kStage];
-    __shared__ __align__(16) float mo[kUnitCells + 16][R];
+    __shared__ __align__(16) float mo[kRangeCells + 16][R];
     const NuRange u = ranges[blockIdx.x];
     const int nr = u.nc + W - 1, np = u.na + u.nb;
+    if (np == 0) {                                    // no point reaches the range: zeros
+        for (int l = threadIdx.x; l < u.nc; l += kUnitThreads) grid[u.c0 + l] = 0.0;
+        return;
+    }
     const bool staged = np <= kStage;
     if ((int)threadIdx.x <= nr) rp[threadIdx.x] = __ldg(runs + u.roff + threadIdx.x);
     if (staged) {
@@ -356,6 +255,68 @@ __global__ void __launch_bounds__(kUnitThreads) k_nu_spread_mixed(const NuRange*
     }
 }
 
+// FP64 spreading on the same cell ranges: each cell's lanes accumulate the w tap sums
+// S_t(f) = sum_{q: i0_q = f} ker_q[t] c_q (one FMA per point and tap, the stored weights and the
+// densities read from global memory four points at a time), a fixed shuffle tree closes each
+// group, and grid real c0 + l = sum_t S_t(c0 + l - t).  Like the mixed pass, no block depends on
+// another.
+template <int W>
+__global__ void __launch_bounds__(kUnitThreads) k_nu_spread64(const NuRange* __restrict__ ranges,
+                                                              const int32_t* __restrict__ runs,
+                                                              const double* __restrict__ c,
+                                                              const double* __restrict__ ker,
+                                                              double* __restrict__ grid) {
+    __shared__ int rp[kRangeCells64 + 16 + 1];
+    __shared__ double seg[kRangeCells64 + 16][W];
+    const NuRange u = ranges[blockIdx.x];
+    const int nr = u.nc + W - 1, np = u.na + u.nb;
+    if (np == 0) {
+        for (int l = threadIdx.x; l < u.nc; l += kUnitThreads) grid[u.c0 + l] = 0.0;
+        return;
+    }
+    if ((int)threadIdx.x <= nr) rp[threadIdx.x] = __ldg(runs + u.roff + threadIdx.x);
+    __syncthreads();
+    const int G = 1 << u.lg, f = (int)threadIdx.x >> u.lg, gl = (int)threadIdx.x & (G - 1);
+    double acc[W];
+#pragma unroll
+    for (int t = 0; t < W; t++) acc[t] = 0.0;
+    if (f < nr) {
+        const int q1 = rp[f + 1];
+        constexpr int B = 4;
+        for (int q = rp[f] + gl; q < q1; q += B * G) {
+            double cb[B], kb[B][W];
+#pragma unroll
+            for (int i = 0; i < B; i++) {
+                const int qi = q + i * G < q1 ? q + i * G : q;
+                const int64_t j = qi < u.na ? u.a0 + qi : u.b0 + (qi - u.na);
+                cb[i] = q + i * G < q1 ? __ldcs(c + j) : 0.0;
+#pragma unroll
+                for (int t = 0; t < W; t++) kb[i][t] = __ldcs(ker + j * W + t);
+            }
+#pragma unroll
+            for (int i = 0; i < B; i++)
+#pragma unroll
+                for (int t = 0; t < W; t++) acc[t] = fma(kb[i][t], cb[i], acc[t]);
+        }
+    }
+    for (int o = G >> 1; o > 0; o >>= 1) {
+#pragma unroll
+        for (int t = 0; t < W; t++) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+    }
+    if (gl == 0 && f < nr) {
+#pragma unroll
+        for (int t = 0; t < W; t++) seg[f][t] = acc[t];
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < u.nc) {
+        const int l = threadIdx.x;
+        double a = 0.0;
+#pragma unroll
+        for (int t = 0; t < W; t++) a += seg[l + W - 1 - t][t];
+        grid[u.c0 + l] = a;
+    }
+}
+
 // type-1 post-processing: S_k from the half-length FFT Z (E, O split) with the deconvolution
 // factors: S_k = f0 E_k + (f1 + i f2) O_k
 __global__ void k_nu_post1(const double2* __restrict__ Z, double* __restrict__ S, const double* __restrict__ modefac,
@@ -390,7 +351,7 @@ __global__ void k_nu_pre2(const double* __restrict__ alpha, double2* __restrict_
     }
 }
 
-// FP64 interpolation: u_j = sum_t G[(i0_j + t) mod nf] ker[j][t].  A block takes 256 consecutive
+// FP64 interpolation: u_j = sum_t G[(i0_j + t) mod nf] ker[j][t] (i0_j: instance x nf + cell).  A block takes 256 consecutive
 // points; their weights (one contiguous run of 256 w doubles) are staged through shared memory
 // with coalesced streaming loads, and all w grid loads of a point are issued before any is used.
 constexpr int kInterpTile = 256;
@@ -406,14 +367,10 @@ __global__ void __launch_bounds__(kInterpTile) k_nu_interp64(const double* __res
         __syncthreads();
         if (threadIdx.x < np) {
             const int64_t j = base + threadIdx.x;
-            const int a = __ldg(i0 + j);
+            const int a = __ldg(i0 + j), base = a & ~(nf - 1);   // instance x nf + cell
             double g[16];
 #pragma unroll
-            for (int t = 0; t < 16; t++) {
-                int i = a + t;
-                i = i >= nf ? i - nf : i;
-                g[t] = t < w ? __ldg(grid + i) : 0.0;
-            }
+            for (int t = 0; t < 16; t++) g[t] = t < w ? __ldg(grid + (base | ((a + t) & (nf - 1)))) : 0.0;
             double acc = 0.0;
 #pragma unroll
             for (int t = 0; t < 16; t++)
@@ -454,10 +411,13 @@ __global__ void __launch_bounds__(256) k_nu_interp_mixed(const double* __restric
         if (j == last) fr[1] = a[i];
     }
     __syncthreads();
-    const int c0 = fr[0], ncell = fr[1] - c0 + 1;
-    const bool fits = ncell <= kHCells;                 // the same in every thread of the block
+    // cells are instance x nf + cell (nf a power of two): a block within one instance wraps inside
+    // it; a block that straddles two instances takes the per-point path
+    const int c0 = fr[0], ncell = fr[1] - c0 + 1, gbase = c0 & ~(nf - 1);
+    const bool fits = ncell <= kHCells && (fr[1] & ~(nf - 1)) == gbase;   // the same in every thread
     if (fits) {
-        for (int l = threadIdx.x; l < ncell + W - 1; l += 256) gs[l] = nu_f64_to_f32(__ldg(grid + (c0 + l) % nf));
+        for (int l = threadIdx.x; l < ncell + W - 1; l += 256)
+            gs[l] = nu_f64_to_f32(__ldg(grid + (gbase | ((c0 + l) & (nf - 1)))));
         __syncthreads();
         for (int l = threadIdx.x; l < ncell; l += 256) {
             float g[W];
@@ -490,11 +450,10 @@ __global__ void __launch_bounds__(256) k_nu_interp_mixed(const double* __restric
             float psi[W];
             nu_taps<W, D>(P, ch, psi);
             acc = 0.f;
+            const int pb = a[i] & ~(nf - 1);
 #pragma unroll
-            for (int t = 0; t < W; t++) {
-                const int r = a[i] + t < nf ? a[i] + t : a[i] + t - nf;
-                acc = __fmaf_rn(psi[t], nu_f64_to_f32(__ldg(grid + r)), acc);
-            }
+            for (int t = 0; t < W; t++)
+                acc = __fmaf_rn(psi[t], nu_f64_to_f32(__ldg(grid + (pb | ((a[i] + t) & (nf - 1))))), acc);
         }
         __stcs(u + j, nu_f32_to_f64(acc));
     }
@@ -545,10 +504,11 @@ int ilog2n(int v) {
 struct wave1d_nufft_s {
     int device = 0;
     int precision = 0;
-    int64_t M = 0;
+    int64_t M = 0;                   // points over all instances
+    int B = 1;                       // instances (each with its own grid of nf reals)
     Params P{};
     int D = 0;                       // polynomial degree (mixed)
-    double kernel_err = 0.0;         // max |polynomial (FP32 Horner) - kernel| over the taps (mixed)
+    double kernel_err = 0.0;         // max |Chebyshev series (FP32) - kernel| over the taps (mixed)
     cudaStream_t stream = nullptr;
     std::vector<int64_t> perm;       // internal point i -> caller index
     std::vector<void*> allocs;
@@ -557,13 +517,10 @@ struct wave1d_nufft_s {
     float* soff = nullptr;
     NuPoly poly{};                   // tap polynomials (mixed), passed to the kernels by value
     double* ker = nullptr;
-    // spreading units and the cells' partials
-    NuUnit* units = nullptr;         // FP64 spreading units
-    NuRange* ranges = nullptr;       // mixed spreading ranges
+    // spreading ranges (cell ranges tiling every instance's grid) and their run tables
+    NuRange* ranges = nullptr;
     int64_t nunits = 0;
-    double* partial = nullptr;
-    int32_t *runs = nullptr, *cptr = nullptr, *cent = nullptr;
-    int32_t* cnt = nullptr;          // per grid real: units that have stored their partial (zero between calls)
+    int32_t* runs = nullptr;
     // FFT and deconvolution
     double *grid = nullptr, *work = nullptr, *spec = nullptr, *spec2 = nullptr, *twiddle = nullptr,
            *modefac = nullptr;
@@ -601,8 +558,21 @@ int wave1d_nufft_plan(const double* x, int64_t M, int K, double tol, int precisi
                       wave1d_nufft_t* out) {
     if (!out) return nfail(WAVE1D_EINVAL, "out is NULL");
     *out = nullptr;
-    if (!x || M < 1 || M > INT32_MAX / 32 || K < 1 || !(tol > 0.0 && tol < 0.1) || (precision != 0 && precision != 1))
-        return nfail(WAVE1D_EINVAL, "need x, 1 <= M < 2^26, K >= 1, 0 < tol < 0.1, precision 0 or 1");
+    const int64_t off[2] = {0, M};
+    return wave1d_nufft_plan_many(x, off, 1, K, tol, precision, stream, out);
+}
+
+int wave1d_nufft_plan_many(const double* x, const int64_t* offsets, int n_inst, int K, double tol, int precision,
+                           void* stream, wave1d_nufft_t* out) {
+    if (!out) return nfail(WAVE1D_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!x || !offsets || n_inst < 1 || K < 1 || !(tol > 0.0 && tol < 0.1) || (precision != 0 && precision != 1))
+        return nfail(WAVE1D_EINVAL, "need x, offsets, n_instances >= 1, K >= 1, 0 < tol < 0.1, precision 0 or 1");
+    if (offsets[0] != 0) return nfail(WAVE1D_EINVAL, "offsets[0] must be 0");
+    for (int b = 0; b < n_inst; b++)
+        if (offsets[b + 1] <= offsets[b]) return nfail(WAVE1D_EINVAL, "every instance needs at least one point");
+    const int64_t M = offsets[n_inst];
+    if (M > INT32_MAX / 32) return nfail(WAVE1D_EINVAL, "at most 2^26 points in all");
     if (precision == 1 && tol < 1e-6) return nfail(WAVE1D_EINVAL, "mixed precision needs tol >= 1e-6");
     wave1d_nufft_t h = new (std::nothrow) wave1d_nufft_s();
     if (!h) return nfail(WAVE1D_ENOMEM, "host allocation");
@@ -612,13 +582,16 @@ int wave1d_nufft_plan(const double* x, int64_t M, int K, double tol, int precisi
     };
     h->precision = precision;
     h->M = M;
+    h->B = n_inst;
     h->stream = (cudaStream_t)stream;
     if (cudaGetDevice(&h->device) != cudaSuccess) return cleanup(nfail(WAVE1D_ECUDA, "no CUDA device"));
     Params& P = h->P;
     nufft_grid(P, K, tol, 0);
     if (P.L2 > 1024) return cleanup(nfail(WAVE1D_EUNSUPPORTED, "fine grid too large for this build (nf > 2^21)"));
+    if ((int64_t)n_inst * P.nf > INT32_MAX / 2) return cleanup(nfail(WAVE1D_EINVAL, "instances x fine grid above 2^30"));
     const int w = P.nufft_w, nf = P.nf;
-    // positions wrapped into [-pi, pi), kernel weights, internal order by first cell
+    // positions wrapped into [-pi, pi), kernel weights, internal order: instance by instance, each
+    // sorted by first cell
     std::vector<double> xw(M);
     for (int64_t j = 0; j < M; j++) {
         double v = x[j];
@@ -634,15 +607,18 @@ int wave1d_nufft_plan(const double* x, int64_t M, int K, double tol, int precisi
     spread_weights(P, xw, i0c, kerc);
     h->perm.resize(M);
     std::iota(h->perm.begin(), h->perm.end(), 0);
-    std::stable_sort(h->perm.begin(), h->perm.end(), [&](int64_t a, int64_t b) {
-        return i0c[a] != i0c[b] ? i0c[a] < i0c[b] : xw[a] < xw[b];
-    });
-    std::vector<int32_t> i0(M);
+    for (int b = 0; b < n_inst; b++)
+        std::stable_sort(h->perm.begin() + offsets[b], h->perm.begin() + offsets[b + 1], [&](int64_t p, int64_t q) {
+            return i0c[p] != i0c[q] ? i0c[p] < i0c[q] : xw[p] < xw[q];
+        });
+    std::vector<int32_t> i0(M), gfirst(M);           // cell in the instance; instance x nf + cell
     std::vector<double> xs(M);
-    for (int64_t i = 0; i < M; i++) {
-        i0[i] = i0c[h->perm[i]];
-        xs[i] = xw[h->perm[i]];
-    }
+    for (int b = 0; b < n_inst; b++)
+        for (int64_t i = offsets[b]; i < offsets[b + 1]; i++) {
+            i0[i] = i0c[h->perm[i]];
+            gfirst[i] = b * nf + i0[i];
+            xs[i] = xw[h->perm[i]];
+        }
     int rc;
     if (precision == 0) {
         std::vector<double> ker((size_t)M * w);
@@ -653,8 +629,8 @@ int wave1d_nufft_plan(const double* x, int64_t M, int K, double tol, int precisi
         // offsets s = first - u + w/2 in [0, 1), y = 2 s - 1; tap t's kernel as a polynomial in y
         std::vector<float> soff(M);
         for (int64_t i = 0; i < M; i++) {
-            double u = (xs[i] + kPiN) / P.h_f;
-            double fst = std::ceil(u - 0.5 * w);
+            const double u = (xs[i] + kPiN) / P.h_f;
+            const double fst = std::ceil(u - 0.5 * w);
             soff[i] = (float)(fst - u + 0.5 * w);
         }
         const int ns = 96;
@@ -712,120 +688,81 @@ int wave1d_nufft_plan(const double* x, int64_t M, int K, double tol, int precisi
         h->kernel_err = err;
         if ((rc = nu_upload(h, soff, &h->soff))) return cleanup(rc);
     }
-    // FP64 spreading units: at most kUnitPoints consecutive points whose first cells lie within
-    // kUnitCells cells; each reaches its cells plus w - 1 (wrapped into the grid by the combine
-    // pass).  Run table: for each unit, the offset (from its first point) of the first point of
-    // each of its first cells, and one past the last point.
-    if (precision == 0) {
-        std::vector<NuUnit> units;
-        std::vector<int32_t> runs;
-        int64_t poff = 0;
-        for (int64_t a = 0; a < M;) {
-            int64_t b = a + 1;
-            while (b < M && b - a < kUnitPoints && i0[b] - i0[a] < kUnitCells) b++;
-            NuUnit u{};
-            u.pa = (int32_t)a;
-            u.np = (int32_t)(b - a);
-            u.ca = i0[a];
-            u.ncells = i0[b - 1] - i0[a] + 1;
-            u.span = u.ncells + w - 1;
-            u.poff = (int32_t)poff;
-            u.roff = (int32_t)runs.size();
-            for (int f = 0, q = 0; f <= u.ncells; f++) {
-                while (q < u.np && i0[a + q] < u.ca + f) q++;
-                runs.push_back(q);
-            }
-            // lanes per run: as many as the block can give every run, at most 32 (a warp runs as
-            // long as its longest run share, so short runs gain from more lanes too)
-            u.lg = 0;
-            while (u.lg < 5 && (u.ncells << (u.lg + 1)) <= kUnitThreads) u.lg++;
-            poff += u.span;
-            units.push_back(u);
-            a = b;
-        }
-        // uncovered cells: from the end of a unit's span to the next unit's first cell (the last
-        // unit wraps round to the first one's); nobody spreads there, the unit writes zeros
-        for (size_t k = 0; k < units.size(); k++) {
-            NuUnit& u = units[k];
-            const int next = k + 1 < units.size() ? units[k + 1].ca : units[0].ca + nf;
-            u.gap0 = u.ca + u.span;
-            u.gap1 = std::max(u.gap0, next);
-        }
-        // combine table: per grid real, the partials that reach it, in unit order
-        std::vector<int32_t> cptr(nf + 1, 0);
-        for (const NuUnit& u : units)
-            for (int l = 0; l < u.span; l++) cptr[(u.ca + l) % nf + 1]++;
-        for (int r = 0; r < nf; r++) cptr[r + 1] += cptr[r];
-        std::vector<int32_t> cent(cptr[nf]), fill(cptr.begin(), cptr.end() - 1);
-        for (const NuUnit& u : units)
-            for (int l = 0; l < u.span; l++) cent[fill[(u.ca + l) % nf]++] = u.poff + l;
-        h->nunits = (int64_t)units.size();
-        if ((rc = nu_upload(h, units, &h->units)) || (rc = nu_upload(h, runs, &h->runs)) ||
-            (rc = nu_upload(h, cptr, &h->cptr)) ||
-            (rc = nu_upload(h, cent, &h->cent)) || (rc = nu_alloc(h, (size_t)poff, &h->partial)) ||
-            (rc = nu_upload(h, std::vector<int32_t>(nf, 0), &h->cnt)) ||
-            (rc = nu_upload(h, i0, &h->first)))
-            return cleanup(rc);
-    } else {
-        // mixed spreading ranges: consecutive cell ranges tiling the grid, each at most
-        // kUnitCells cells and (where a single cell allows) at most kRangePoints points counting
-        // the w - 1 halo cells before it.  ps[f] = first point (sorted order) whose first cell is >= f.
-        std::vector<int32_t> ps(nf + 1, 0);
-        for (int64_t i = 0; i < M; i++) ps[i0[i] + 1]++;
-        for (int f = 0; f < nf; f++) ps[f + 1] += ps[f];
-        auto pts = [&](int f0, int f1) {          // points whose first cell is in [f0, f1), f0 may be < 0
-            if (f0 >= 0) return ps[f1] - ps[f0];
-            return (ps[nf] - ps[nf + f0]) + ps[f1];
-        };
+    {
+        // spreading ranges, per instance: consecutive cell ranges tiling its grid, each at most
+        // kRangeCells (mixed) or kRangeCells64 (FP64) cells and, where a single cell allows, at
+        // most kRangePoints (mixed) or kRangePoints64 (FP64) points counting the w - 1 halo cells
+        // before it; a stretch of cells that no point reaches is one range of zeros.  ps[f] = first point
+        // of the instance (sorted order) whose first cell is >= f.
+        const int max_cells = precision == 1 ? kRangeCells : kRangeCells64;
+        const int max_points = precision == 1 ? kRangePoints : kRangePoints64;
         std::vector<NuRange> ranges;
         std::vector<int32_t> runs;
-        for (int c0 = 0; c0 < nf;) {
-            int c1 = c0 + 1;
-            while (c1 < nf && c1 - c0 < kUnitCells && pts(c0 - w + 1, c1 + 1) <= kRangePoints) c1++;
-            NuRange r{};
-            r.c0 = c0;
-            r.nc = c1 - c0;
-            const int h0 = c0 - w + 1;            // first halo cell (negative: wraps to the end)
-            if (h0 >= 0) {
-                r.a0 = ps[h0];
-                r.na = ps[c1] - ps[h0];
-                r.b0 = 0;
-                r.nb = 0;
-            } else {
-                r.a0 = ps[nf + h0];
-                r.na = ps[nf] - ps[nf + h0];
-                r.b0 = 0;
-                r.nb = ps[c1];
+        std::vector<int32_t> ps(nf + 1);
+        for (int b = 0; b < n_inst; b++) {
+            const int64_t o = offsets[b], mb = offsets[b + 1] - o;
+            std::fill(ps.begin(), ps.end(), 0);
+            for (int64_t i = 0; i < mb; i++) ps[i0[o + i] + 1]++;
+            for (int f = 0; f < nf; f++) ps[f + 1] += ps[f];
+            auto pts = [&](int f0, int f1) {      // points whose first cell is in [f0, f1), f0 may be < 0
+                if (f0 >= 0) return ps[f1] - ps[f0];
+                return (ps[nf] - ps[nf + f0]) + ps[f1];
+            };
+            for (int c0 = 0; c0 < nf;) {
+                int c1 = c0 + 1;
+                if (pts(c0 - w + 1, c0 + 1) == 0) {
+                    // cells no point reaches: one range of zeros up to the next reached cell
+                    while (c1 < nf && c1 - c0 < kEmptyCells && pts(c1 - w + 1, c1 + 1) == 0) c1++;
+                } else {
+                    while (c1 < nf && c1 - c0 < max_cells && pts(c0 - w + 1, c1 + 1) <= max_points) c1++;
+                }
+                NuRange r{};
+                r.c0 = b * nf + c0;
+                r.nc = c1 - c0;
+                const int h0 = c0 - w + 1;        // first halo cell (negative: wraps to the end)
+                if (h0 >= 0) {
+                    r.a0 = (int32_t)(o + ps[h0]);
+                    r.na = ps[c1] - ps[h0];
+                    r.b0 = (int32_t)o;
+                    r.nb = 0;
+                } else {
+                    r.a0 = (int32_t)(o + ps[nf + h0]);
+                    r.na = ps[nf] - ps[nf + h0];
+                    r.b0 = (int32_t)o;
+                    r.nb = ps[c1];
+                }
+                r.roff = (int32_t)runs.size();
+                if (r.na + r.nb > 0) {
+                    for (int k = 0; k <= r.nc + w - 1; k++) {    // run starts in staging order, then the end
+                        const int f = h0 + k;
+                        int off;
+                        if (k == r.nc + w - 1) off = r.na + r.nb;
+                        else if (f >= 0) off = (h0 >= 0 ? ps[f] - ps[h0] : r.na + ps[f]);
+                        else off = ps[nf + f] - ps[nf + h0];
+                        runs.push_back(off);
+                    }
+                }
+                const int nr = r.nc + w - 1;
+                r.lg = 0;
+                while (r.lg < 5 && (nr << (r.lg + 1)) <= kUnitThreads) r.lg++;
+                ranges.push_back(r);
+                c0 = c1;
             }
-            r.roff = (int32_t)runs.size();
-            for (int k = 0; k <= r.nc + w - 1; k++) {        // run starts in staging order, then the end
-                const int f = h0 + k;
-                int off;
-                if (k == r.nc + w - 1) off = r.na + r.nb;
-                else if (f >= 0) off = (h0 >= 0 ? ps[f] - r.a0 : r.na + ps[f]);
-                else off = ps[nf + f] - r.a0;
-                runs.push_back(off);
-            }
-            const int nr = r.nc + w - 1;
-            r.lg = 0;
-            while (r.lg < 5 && (nr << (r.lg + 1)) <= kUnitThreads) r.lg++;
-            ranges.push_back(r);
-            c0 = c1;
         }
         h->nunits = (int64_t)ranges.size();
         if ((rc = nu_upload(h, ranges, &h->ranges)) || (rc = nu_upload(h, runs, &h->runs)) ||
-            (rc = nu_upload(h, i0, &h->first)))
+            (rc = nu_upload(h, gfirst, &h->first)))
             return cleanup(rc);
     }
     std::vector<double> d1, d2, mf, tw((size_t)P.L * 2);
     nufft_factors(P, d1, d2, mf);
     for (int j = 0; j < P.L; j++) {
-        double a = 2.0 * kPiN * (double)j / (double)P.L;
-        tw[2 * j] = std::cos(a);
-        tw[2 * j + 1] = std::sin(a);
+        double ang = 2.0 * kPiN * (double)j / (double)P.L;
+        tw[2 * j] = std::cos(ang);
+        tw[2 * j + 1] = std::sin(ang);
     }
     if ((rc = nu_upload(h, mf, &h->modefac)) || (rc = nu_upload(h, tw, &h->twiddle)) ||
-        (rc = nu_alloc(h, (size_t)nf, &h->grid)) || (rc = nu_alloc(h, (size_t)nf, &h->work)) ||
+        (rc = nu_alloc(h, (size_t)n_inst * nf, &h->grid)) || (rc = nu_alloc(h, (size_t)nf, &h->work)) ||
         (rc = nu_alloc(h, (size_t)nf, &h->spec)) || (rc = nu_alloc(h, (size_t)nf, &h->spec2)))
         return cleanup(rc);
     if (cudaDeviceSynchronize() != cudaSuccess) return cleanup(nfail(WAVE1D_ECUDA, "upload failed"));
@@ -851,13 +788,13 @@ int wave1d_nufft_perm(wave1d_nufft_t h, int64_t* perm) {
 int wave1d_nufft_spread(wave1d_nufft_t h, const double* c, double* grid) {
     if (!h || !c || !grid) return nfail(WAVE1D_EINVAL, "bad arguments");
     if (cudaSetDevice(h->device) != cudaSuccess) return nfail(WAVE1D_ECUDA, "cudaSetDevice");
-    const int nf = h->P.nf, w = h->P.nufft_w;
+    const int w = h->P.nufft_w;
     const unsigned nu = (unsigned)h->nunits;
     bool ok;
     if (h->precision == 0) {
         ok = nu_with_w(w, [&](auto wc) {
-            k_nu_spread64<decltype(wc)::value><<<nu, kUnitThreads, 0, h->stream>>>(
-                h->units, h->runs, c, h->ker, h->partial, h->cptr, h->cent, h->cnt, grid, nf);
+            k_nu_spread64<decltype(wc)::value><<<nu, kUnitThreads, 0, h->stream>>>(h->ranges, h->runs, c, h->ker,
+                                                                                    grid);
         });
     } else {
         ok = nu_with_mixed(w, h->D, [&](auto wc, auto dc) {
@@ -891,13 +828,16 @@ int wave1d_nufft_type1(wave1d_nufft_t h, const double* c, double* S) {
     if (rc) return rc;
     const Params& P = h->P;
     const int t1 = std::max(32, std::min(P.L1 / 2, 512)), t2 = std::max(32, std::min(P.L2 / 2, 512));
-    k_fft_cols<<<P.L2, t1, fft_smem_bytes(P.L1), h->stream>>>((const double2*)h->grid, (double2*)h->work,
-                                                              (const double2*)h->twiddle, P.L, P.L1, P.L2,
-                                                              ilog2n(P.L1), +1);
-    k_fft_rows<<<P.L1, t2, fft_smem_bytes(P.L2), h->stream>>>((const double2*)h->work, (double2*)h->spec,
-                                                              (const double2*)h->twiddle, P.L, P.L1, P.L2,
-                                                              ilog2n(P.L2), +1);
-    k_nu_post1<<<(P.K + 1 + 127) / 128, 128, 0, h->stream>>>((const double2*)h->spec, S, h->modefac, P.K, P.L);
+    for (int b = 0; b < h->B; b++) {              // the instances' FFTs one after another
+        k_fft_cols<<<P.L2, t1, fft_smem_bytes(P.L1), h->stream>>>((const double2*)(h->grid + (size_t)b * P.nf),
+                                                                  (double2*)h->work, (const double2*)h->twiddle, P.L,
+                                                                  P.L1, P.L2, ilog2n(P.L1), +1);
+        k_fft_rows<<<P.L1, t2, fft_smem_bytes(P.L2), h->stream>>>((const double2*)h->work, (double2*)h->spec,
+                                                                  (const double2*)h->twiddle, P.L, P.L1, P.L2,
+                                                                  ilog2n(P.L2), +1);
+        k_nu_post1<<<(P.K + 1 + 127) / 128, 128, 0, h->stream>>>((const double2*)h->spec,
+                                                                 S + (size_t)b * 2 * (P.K + 1), h->modefac, P.K, P.L);
+    }
     return cudaGetLastError() == cudaSuccess ? WAVE1D_OK : nfail(WAVE1D_ECUDA, "type-1 launch failed");
 }
 
@@ -905,14 +845,18 @@ int wave1d_nufft_type2(wave1d_nufft_t h, const double* alpha, double* u) {
     if (!h || !alpha || !u) return nfail(WAVE1D_EINVAL, "bad arguments");
     if (cudaSetDevice(h->device) != cudaSuccess) return nfail(WAVE1D_ECUDA, "cudaSetDevice");
     const Params& P = h->P;
-    k_nu_pre2<<<(P.L + 255) / 256, 256, 0, h->stream>>>(alpha, (double2*)h->spec2, h->modefac, P.K, P.L);
     const int t1 = std::max(32, std::min(P.L1 / 2, 512)), t2 = std::max(32, std::min(P.L2 / 2, 512));
-    k_fft_cols<<<P.L2, t1, fft_smem_bytes(P.L1), h->stream>>>((const double2*)h->spec2, (double2*)h->work,
-                                                              (const double2*)h->twiddle, P.L, P.L1, P.L2,
-                                                              ilog2n(P.L1), -1);
-    k_fft_rows<<<P.L1, t2, fft_smem_bytes(P.L2), h->stream>>>((const double2*)h->work, (double2*)h->grid,
-                                                              (const double2*)h->twiddle, P.L, P.L1, P.L2,
-                                                              ilog2n(P.L2), -1);
+    for (int b = 0; b < h->B; b++) {
+        k_nu_pre2<<<(P.L + 255) / 256, 256, 0, h->stream>>>(alpha + (size_t)b * 2 * (P.K + 1), (double2*)h->spec2,
+                                                             h->modefac, P.K, P.L);
+        k_fft_cols<<<P.L2, t1, fft_smem_bytes(P.L1), h->stream>>>((const double2*)h->spec2, (double2*)h->work,
+                                                                  (const double2*)h->twiddle, P.L, P.L1, P.L2,
+                                                                  ilog2n(P.L1), -1);
+        k_fft_rows<<<P.L1, t2, fft_smem_bytes(P.L2), h->stream>>>((const double2*)h->work,
+                                                                  (double2*)(h->grid + (size_t)b * P.nf),
+                                                                  (const double2*)h->twiddle, P.L, P.L1, P.L2,
+                                                                  ilog2n(P.L2), -1);
+    }
     if (cudaGetLastError() != cudaSuccess) return nfail(WAVE1D_ECUDA, "type-2 launch failed");
     return wave1d_nufft_interp(h, h->grid, u);
 }

@@ -41,7 +41,8 @@ EXPORTED = ["wave1d_opts_default", "wave1d_plan", "wave1d_set_incident_gaussians
             "wave1d_get_sigma", "wave1d_sync", "wave1d_get_info", "wave1d_inspect",
             "wave1d_destroy", "wave1d_strerror", "wave1d_profile", "wave1d_profile_read",
             "wave1d_nufft1_noalloc", "wave1d_state_size", "wave1d_state_save", "wave1d_state_load",
-            "wave1d_nufft_plan", "wave1d_nufft_info", "wave1d_nufft_perm", "wave1d_nufft_spread",
+            "wave1d_nufft_plan", "wave1d_nufft_plan_many", "wave1d_nufft_info", "wave1d_nufft_perm",
+            "wave1d_nufft_spread",
             "wave1d_nufft_interp", "wave1d_nufft_type1", "wave1d_nufft_type2", "wave1d_nufft_destroy",
             "wave1d_nufft_strerror"]
 
@@ -107,6 +108,8 @@ def lib(path: str = LIB_PATH):
         L.wave1d_state_load.argtypes = [P, ctypes.c_void_p, ctypes.c_size_t]
         L.wave1d_nufft_plan.argtypes = [_D, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                         ctypes.c_void_p, ctypes.POINTER(P)]
+        L.wave1d_nufft_plan_many.argtypes = [_D, ctypes.POINTER(ctypes.c_int64), ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_double, ctypes.c_int, P, ctypes.POINTER(P)]
         L.wave1d_nufft_info.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
         L.wave1d_nufft_perm.argtypes = [P, ctypes.POINTER(ctypes.c_int64)]
@@ -185,17 +188,29 @@ def wave1d_solve(plan, nsteps, u_rec, sigma, out_on_device):
 
 class Nufft:
     """Standalone type-1 / type-2 NUFFT plan (device arrays are torch CUDA tensors of float64;
-    point arrays in the plan's point order, see `perm`)."""
+    point arrays in the plan's point order, see `perm`).  `x` is one point set, or a list of
+    point sets (the batched form: grids, S and alpha are then instance-major)."""
 
     def __init__(self, x, K, tol, precision=0, stream=None):
-        x = np.ascontiguousarray(x, dtype=np.float64)
         h = ctypes.c_void_p()
-        st = lib().wave1d_nufft_plan(_hptr(x), x.shape[0], int(K), float(tol), int(precision),
-                                     ctypes.c_void_p(stream) if stream is not None else None,
-                                     ctypes.byref(h))
+        st_ptr = ctypes.c_void_p(stream) if stream is not None else None
+        if isinstance(x, (list, tuple)):
+            sets = [np.ascontiguousarray(v, dtype=np.float64).ravel() for v in x]
+            offsets = np.zeros(len(sets) + 1, dtype=np.int64)
+            offsets[1:] = np.cumsum([v.size for v in sets])
+            xa = np.ascontiguousarray(np.concatenate(sets))
+            st = lib().wave1d_nufft_plan_many(_hptr(xa), offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                              len(sets), int(K), float(tol), int(precision), st_ptr,
+                                              ctypes.byref(h))
+            name, self.B, self.offsets = "wave1d_nufft_plan_many", len(sets), offsets
+        else:
+            xa = np.ascontiguousarray(x, dtype=np.float64)
+            st = lib().wave1d_nufft_plan(_hptr(xa), xa.shape[0], int(K), float(tol), int(precision), st_ptr,
+                                         ctypes.byref(h))
+            name, self.B, self.offsets = "wave1d_nufft_plan", 1, np.array([0, xa.shape[0]], dtype=np.int64)
         if st != WAVE1D_OK:
-            raise Wave1DError(st, "wave1d_nufft_plan: " + lib().wave1d_nufft_strerror().decode())
-        self.h, self.M, self.K = h, x.shape[0], int(K)
+            raise Wave1DError(st, name + ": " + lib().wave1d_nufft_strerror().decode())
+        self.h, self.M, self.K = h, xa.shape[0], int(K)
         nf, w, deg, err = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
         _check(lib().wave1d_nufft_info(h, ctypes.byref(nf), ctypes.byref(w), ctypes.byref(deg),
                                        ctypes.byref(err)), "wave1d_nufft_info")

@@ -143,3 +143,46 @@ def test_nufft_dense_cells_and_wrap():
 def test_nufft_mixed_needs_tol_1e6():
     with pytest.raises(wave1d.Wave1DError):
         wave1d.Nufft(np.zeros(4), 8, 1e-8, 1)
+
+
+def test_nufft_batched_instances():
+    """wave1d_nufft_plan_many: five instances of different sizes and layouts (1 point, a cluster,
+    points on the periodic seam, uniform, a ragged 37) in one plan, K = 300; each instance's
+    type-1 and type-2 against its own direct sums, FP64 and mixed."""
+    rng = np.random.default_rng(5)
+    K = 300
+    sets = [np.array([0.3]),
+            -1.0 + 0.01 * rng.standard_normal(2500),
+            np.concatenate([np.pi - 1e-3 * rng.uniform(size=400), -np.pi + 1e-3 * rng.uniform(size=400)]),
+            rng.uniform(-np.pi, np.pi, 3000),
+            rng.uniform(-np.pi, np.pi, 37)]
+    cs = [rng.uniform(0.5, 1.5, v.size) * np.where(rng.uniform(size=v.size) < 0.8, 1.0, -1.0) for v in sets]
+    alphas = []
+    for _ in sets:
+        a = (rng.standard_normal(K + 1) + 1j * rng.standard_normal(K + 1)) / (1.0 + np.arange(K + 1) / 50.0)
+        a[0] = a[0].real
+        alphas.append(a)
+    import torch
+    for precision, tol, bar in ((0, 1e-12, 1e-10), (1, 1e-6, 1e-6)):
+        nu = wave1d.Nufft(sets, K, tol, precision)
+        try:
+            off = nu.offsets
+            c_all = np.concatenate(cs)
+            cd = torch.tensor(c_all[nu.perm], dtype=torch.float64, device="cuda")
+            Sd = torch.zeros(len(sets) * 2 * (K + 1), dtype=torch.float64, device="cuda")
+            ad = torch.tensor(np.concatenate([np.stack([a.real, a.imag], 1).reshape(-1) for a in alphas]),
+                              dtype=torch.float64, device="cuda")
+            ud = torch.zeros(nu.M, dtype=torch.float64, device="cuda")
+            nu.type1(cd, Sd)
+            nu.type2(ad, ud)
+            torch.cuda.synchronize()
+            S = Sd.cpu().numpy().reshape(len(sets), K + 1, 2)
+            u = np.empty(nu.M)
+            u[nu.perm] = ud.cpu().numpy()
+        finally:
+            nu.close()
+        for i, (x, c, a) in enumerate(zip(sets, cs, alphas)):
+            eS = _rel(S[i, :, 0] + 1j * S[i, :, 1], wfp.type1(c, x, K))
+            eu = _rel(u[off[i]:off[i + 1]], wfp.type2(a, x))
+            print(f"batched precision {precision} instance {i} (M={x.size}): type-1 {eS:.2e} type-2 {eu:.2e}")
+            assert eS < bar and eu < bar
