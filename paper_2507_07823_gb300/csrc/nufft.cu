@@ -1,22 +1,25 @@
-// Standalone NUFFTs of the history part (Sec. 3.1) on a fixed set of points: the type-1 transform
+// Standalone NUFFTs of the history part (Sec. 3.1) on fixed points: the type-1 transform
 // S_k = (1/2 pi) sum_j c_j e^{+i k x_j}, k = 0..K (eq. densco), and the type-2 transform
 // u_j = sum_{|k| <= K} alpha_k e^{-i k x_j} with alpha_{-k} = conj(alpha_k) (eq. historySol1), each
 // split into its spreading (A1) or interpolation (A6) pass and the FFT, with the same Kaiser-Bessel
-// kernel, fine grid and deconvolution as the time-step plan.
+// kernel, fine grid and deconvolution as the time-step plan.  A plan may hold many point sets
+// (instances) with the same K; one launch per pass covers all of them.
 //
 // Two precisions:
 //   FP64   kernel weights precomputed (w per point) and streamed from HBM.  Relative accuracy set
 //          by tol, like the time-step plan.
-//   mixed  kernel values computed on the fly in FP32 from per-tap polynomials in the point's
-//          offset within its first cell (fitted on the host to about 1e-7 of the kernel's peak),
-//          sums in compensated FP32 pairs; the FFT and the deconvolution stay FP64.  GB300 runs
-//          FP32 about 60 times faster than FP64, so these passes read little more than the points'
-//          cells, offsets and values.
-// Points are kept in an internal order sorted by first grid cell (wave1d_nufft_perm gives it).
-// Spreading works on units of consecutive points (products in shared memory, one warp per cell,
-// then a per-cell combine of the units' partials), so clustered points, with hundreds per cell,
-// spread over many warps; the interpolation is one thread per point.  Neither uses atomics: the
-// results do not depend on scheduling.
+//   mixed  each tap's kernel a Chebyshev series in the point's offset within its first cell
+//          (fitted on the host to about 2e-7 of the kernel's peak); spreading by per-cell
+//          Chebyshev moments and interpolation by per-cell Chebyshev sums of the grid, in FP32
+//          with the dominant terms compensated; the FFT and the deconvolution stay FP64.  GB300
+//          runs FP32 about 60 times faster than FP64, so these passes read little more than the
+//          points' cells, offsets and values.
+// Points are kept in an internal order sorted by first grid cell, instance by instance
+// (wave1d_nufft_perm gives it).  Spreading: each instance's grid is cut into cell ranges, one
+// block per range writes its grid reals complete (recomputing the sums of the w - 1 cells before
+// the range), so clustered points, with hundreds per cell, spread over many blocks and lanes.
+// Interpolation: blocks of consecutive points.  Neither uses atomics: the results do not depend
+// on scheduling.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -519,7 +522,7 @@ struct wave1d_nufft_s {
     double* ker = nullptr;
     // spreading ranges (cell ranges tiling every instance's grid) and their run tables
     NuRange* ranges = nullptr;
-    int64_t nunits = 0;
+    int64_t nunits = 0;              // ranges
     int32_t* runs = nullptr;
     // FFT and deconvolution
     double *grid = nullptr, *work = nullptr, *spec = nullptr, *spec2 = nullptr, *twiddle = nullptr,

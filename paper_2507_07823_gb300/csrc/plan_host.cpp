@@ -764,8 +764,14 @@ int build_rows(const LocalCSR& csr, int m_first, LocalRows& rows, std::string& e
             auto& ord = order[j];
             ord.resize(p1 - p0);
             for (int64_t q = p0; q < p1; q++) ord[q - p0] = q;
+            // sources by the first m they need; a source without weights (a pair inside delta by
+            // rounding only, every Q_m zero) goes last, so the sources active at each m stay a
+            // prefix of the list, which the counts below assume
+            auto first_m = [&](int64_t q) {
+                return (csr.mrange[q] >> 16) > 0 ? (csr.mrange[q] & 0xffff) : 0x7fffffff;
+            };
             std::sort(ord.begin(), ord.end(), [&](int64_t u, int64_t v) {
-                int lu = csr.mrange[u] & 0xffff, lv = csr.mrange[v] & 0xffff;
+                int lu = first_m(u), lv = first_m(v);
                 return lu < lv || (lu == lv && csr.src[u] < csr.src[v]);
             });
             int64_t total = 0;

@@ -200,4 +200,37 @@ def config4(**over) -> Workload:
     return make("free_M1e5_dt1e-3", **kw)
 
 
+def _gaussian_pulse_width(mu: float) -> float:
+    """exp(-mu s^2) as exp(-s^2 / (2 width^2))."""
+    return 1.0 / math.sqrt(2.0 * mu)
+
+
+def fabry_perot(dt: float = 0.005, **over) -> Workload:
+    """Sec. 6 (scattering by arrays of springs): two springs beta = 100 a unit distance apart at
+    x = -0.5, 0.5 in free space, incident pulse exp(-mu (s - t0)^2) with mu = 5, t0 = -3 (eq.
+    incidentPulse), over the paper's T = 94.26 (9426 steps of 0.01), p = 8; receivers at -1.8
+    (reflected) and 1.8 (transmitted).  dt defaults to 0.005: with these stiffnesses the p = 8
+    scheme is unstable at 0.01 (beta dt / 2 = 0.5)."""
+    kw = dict(name="fabry_perot_M2", bc=FREE, x=np.array([-0.5, 0.5]), beta=np.array([100.0, 100.0]),
+              amp=np.array([1.0]), center=np.array([-3.0]), width=np.array([_gaussian_pulse_width(5.0)]),
+              dt=dt, Nt=int(round(94.26 / dt)), tol=1e-12, p=8, xr=np.array([-1.8, 1.8]), seed=0,
+              description=f"free space, 2 springs beta=100 at +-0.5, mu=5, t0=-3, dt={dt}, T=94.26")
+    kw.update(over)
+    return Workload(**kw)
+
+
+def uniform_array(M: int, beta: float, dt: float = 0.01, **over) -> Workload:
+    """Sec. 6: M equally spaced springs of equal stiffness (the paper's examples: M = 10 with
+    beta = 100 and M = 200 with beta = 1), here spanning [-1, 1] end to end (spacing 2 / (M - 1),
+    which keeps pair distances off multiples of dt), in free space; pulse mu = 5, t0 = -4, over the
+    paper's T = 251.34 (25134 steps of 0.01), p = 8; receivers at -1.8 and 1.8."""
+    x = np.linspace(-1.0, 1.0, M)
+    kw = dict(name=f"uniform_array_M{M}", bc=FREE, x=x, beta=np.full(M, float(beta)), amp=np.array([1.0]),
+              center=np.array([-4.0]), width=np.array([_gaussian_pulse_width(5.0)]), dt=dt,
+              Nt=int(round(251.34 / dt)), tol=1e-12, p=8, xr=np.array([-1.8, 1.8]), seed=0,
+              description=f"free space, {M} springs beta={beta} evenly in [-1, 1], mu=5, t0=-4, dt={dt}")
+    kw.update(over)
+    return Workload(**kw)
+
+
 CONFIGS = {0: config0, 1: config1, 2: config2, 4: config4}

@@ -186,3 +186,44 @@ def test_nufft_batched_instances():
             eu = _rel(u[off[i]:off[i + 1]], wfp.type2(a, x))
             print(f"batched precision {precision} instance {i} (M={x.size}): type-1 {eS:.2e} type-2 {eu:.2e}")
             assert eS < bar and eu < bar
+
+
+@pytest.mark.parametrize("precision,tol,bar_pass,bar_full", [(0, 1e-12, 1e-13, 1e-10), (1, 1e-6, 2e-6, 2e-6)])
+def test_nufft_adjoint_identities(precision, tol, bar_pass, bar_full):
+    """Interpolation is the transpose of spreading (same kernel values): <spread c, g> = <c, interp g>
+    for any c, g.  And for real c, sum_j c_j u_j with u = type-2(alpha) equals
+    2 pi (alpha_0 S_0 + 2 Re sum_{k>=1} alpha_k conj(S_k)) with S = type-1(c) (both transforms
+    approximate exact adjoints to the tolerance).  Clustered points with a dense cell, M = 4000."""
+    import torch
+    rng = np.random.default_rng(17)
+    x = np.concatenate([0.7 + 1e-3 * rng.standard_normal(1500), rng.uniform(-np.pi, np.pi, 2500)])
+    K = 500
+    nu = wave1d.Nufft(x, K, tol, precision)
+    try:
+        c = torch.tensor(rng.standard_normal(x.size), dtype=torch.float64, device="cuda")
+        g = torch.tensor(rng.standard_normal(nu.nf), dtype=torch.float64, device="cuda")
+        sc = torch.zeros(nu.nf, dtype=torch.float64, device="cuda")
+        ig = torch.zeros(x.size, dtype=torch.float64, device="cuda")
+        nu.spread(c, sc)
+        nu.interp(g, ig)
+        lhs, rhs = float(torch.dot(sc, g)), float(torch.dot(c, ig))
+        scale = float(torch.linalg.norm(sc) * torch.linalg.norm(g))
+        e_pass = abs(lhs - rhs) / scale
+        alpha = (rng.standard_normal(K + 1) + 1j * rng.standard_normal(K + 1)) / (1.0 + np.arange(K + 1) / 100.0)
+        alpha[0] = alpha[0].real
+        ad = torch.tensor(np.stack([alpha.real, alpha.imag], 1).reshape(-1), dtype=torch.float64, device="cuda")
+        S = torch.zeros(2 * (K + 1), dtype=torch.float64, device="cuda")
+        u = torch.zeros(x.size, dtype=torch.float64, device="cuda")
+        nu.type1(c, S)
+        nu.type2(ad, u)
+        torch.cuda.synchronize()
+        Sh = S.cpu().numpy()
+        Sc = Sh[0::2] + 1j * Sh[1::2]
+        lhs2 = float(torch.dot(c, u))
+        rhs2 = 2 * np.pi * float(np.real(alpha[0] * Sc[0] + 2 * np.sum(alpha[1:] * np.conj(Sc[1:]))))
+        scale2 = float(torch.linalg.norm(c) * torch.linalg.norm(u))
+        e_full = abs(lhs2 - rhs2) / scale2
+    finally:
+        nu.close()
+    print(f"adjoint precision {precision}: spread/interp {e_pass:.2e}, type-1/type-2 {e_full:.2e}")
+    assert e_pass < bar_pass and e_full < bar_full

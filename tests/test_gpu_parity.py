@@ -255,3 +255,21 @@ def test_config1_first_steps_against_oracle():
     assert _rel(sg, so) < TOL
     assert np.max(np.abs(uo)) > 1e-6          # the comparison is not on noise
     assert _rel(ug, uo) < TOL
+
+
+def test_pairs_at_distance_dt_within_rounding():
+    """Springs spaced exactly dt apart in exact arithmetic (centres of 200 cells of [-1, 1],
+    dt = 0.01): rounding puts some neighbour distances just below dt (nearby: the implicit
+    coupling) and others at or above it, and pairs 36 spacings apart sit at delta = 0.36 within
+    rounding, inside the local part with every weight zero (such a source once broke the
+    m-ordered rows of the local sum).  Every density and receiver value against the oracle of the
+    scheme over 2000 steps, free space."""
+    w = W.uniform_array(200, 1.0, Nt=2000).with_(x=-1.0 + (np.arange(200) + 0.5) * (2.0 / 200),
+                                                 xr=np.array([-1.8, -0.95, 0.95, 1.8]))
+    d = np.abs(np.diff(w.x))
+    assert (d < w.dt).any() and (d >= w.dt).any()     # both kinds of tie are present
+    sg, ug, _ = _gpu_run(w)
+    so, uo, _ = _oracle_run(w)
+    es, eu = _rel(sg, so), _rel(ug, uo)
+    print(f"pairs at dt: sigma {es:.2e}, receivers {eu:.2e}")
+    assert es < TOL and eu < TOL

@@ -111,6 +111,26 @@ def test_two_spring_stability_bound():
     assert np.linalg.norm(s) <= np.linalg.norm(g) / (1 - L * beta / 2)
 
 
+def test_single_spring_stiffness_limit_of_high_order_stencils():
+    """The p-point stencil of the newest interval uses the p nearest available samples, i.e. the
+    newest sample and p - 1 older ones (Sec. 4.1), so a single spring behaves like an implicit
+    Adams method for sigma' = -(beta/2) sigma: p = 2 is unconditionally stable (Sec. 5), high p
+    has a bounded interval.  Observed for p = 8: stable at beta dt / 2 = 0.25, growth by many
+    orders at 0.5 (where the paper runs its beta = 100, dt = 0.01 array examples); p = 6 is
+    still stable at 0.5.  A change of the stencil rule moves these."""
+    dt, Nt = 0.01, 1500
+    w = 1.0 / math.sqrt(10.0)
+
+    def peak(beta, p):
+        _, u = volterra.march([-0.5], [beta], False, dt, Nt, p, [1.0], [-3.0], [w], None, [1.8])
+        return float(np.nanmax(np.abs(u)))
+
+    assert peak(50.0, 8) < 1.5
+    assert peak(100.0, 8) > 1e6
+    assert peak(100.0, 6) < 1.5
+    assert peak(100.0, 2) < 1.5
+
+
 def test_manufactured_solution_order():
     """Sec. 6.1 manufactured solution: error O(dt^{p+1})-ish down to rounding."""
     rng = np.random.default_rng(11)
