@@ -233,4 +233,23 @@ def uniform_array(M: int, beta: float, dt: float = 0.01, **over) -> Workload:
     return Workload(**kw)
 
 
+def disordered_media(beta_max: float, seed: int = 7823 + 150, **over) -> Workload:
+    """Sec. 6 (scattering in 1D disordered media): M = 150 springs at random positions in [-2, 2]
+    with every pair at least 1e-4 apart, stiffnesses uniform in [0.1, beta_max] (the paper: 3, 5 and
+    10), free space, pulse mu = 30, t0 = -3, dt = 3.703e-3 up to T = 10 pi (8484 steps), p = 8; the
+    paper's 400 x 400 space-time readout as 100 receivers evenly across [-2.7, 2.7] at every step."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = np.sort(rng.uniform(-2.0, 2.0, 150))
+    while np.min(np.diff(x)) < 1e-4:                   # redraw the points that crowd a neighbour
+        bad = np.nonzero(np.diff(x) < 1e-4)[0] + 1
+        x[bad] = rng.uniform(-2.0, 2.0, bad.size)
+        x = np.sort(x)
+    kw = dict(name=f"disordered_M150_beta{beta_max:g}", bc=FREE, x=x, beta=rng.uniform(0.1, beta_max, 150),
+              amp=np.array([1.0]), center=np.array([-3.0]), width=np.array([_gaussian_pulse_width(30.0)]),
+              dt=3.703e-3, Nt=8484, tol=1e-12, p=8, xr=np.linspace(-2.7, 2.7, 100), seed=seed,
+              description=f"free space, 150 random springs in [-2, 2], beta in [0.1, {beta_max:g}], mu=30, t0=-3")
+    kw.update(over)
+    return Workload(**kw)
+
+
 CONFIGS = {0: config0, 1: config1, 2: config2, 4: config4}
