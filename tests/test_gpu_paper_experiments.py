@@ -79,3 +79,43 @@ def test_disordered_media(beta_max):
     print(msg)
     assert np.max(np.abs(u)) > 0.1
     assert digits >= 8.0
+
+
+def test_manufactured_solution_convergence():
+    """Sec. 6.1 manufactured solution on the GPU path, measured as the paper measures it: the
+    scattered field u against u_ex on a 10 x 10 space-time grid over 0 < t < 6 pi (receivers across
+    [-1.5, 1.5]), ten springs in [-1, 1] (free space) with sigma_j(t) = exp(-mu_j (t - t0_j)^2) and
+    the forcing g_j = -sigma_j - beta_j u(x_j) from the closed form passed from the host each step.
+    The paper observes O(dt^(p+1)) down to about M eps; so do we: p = 2 and 4 converge at order
+    p + 1 or better between dt = 0.01 and 0.005, p = 6 and 8 reach the floor (M eps = 1e-11)."""
+    import closed_forms as cf
+    rng = np.random.default_rng(61)
+    M = 10
+    x = np.sort(rng.uniform(-1.0, 1.0, M))
+    beta = rng.uniform(0.1, 3.0, M)
+    mu = rng.uniform(40.0, 50.0, M)
+    t0 = rng.uniform(1.0, 3.0, M)
+    _, u_ex, g_ex = cf.mms(x, beta, mu, t0)
+    T, xr = 6 * math.pi, np.linspace(-1.5, 1.5, 10)
+    for p in (2, 4, 6, 8):
+        errs = []
+        for dt in (0.01, 0.005):
+            Nt = int(round(T / dt))
+            sample = set(np.linspace(0, Nt, 11).astype(int)[1:].tolist())
+            plan = wave1d.Plan(x, beta, W.FREE, dt, Nt, 1e-12, xr=xr, p=p)
+            t = np.arange(Nt + 1) * dt
+            g = g_ex(t)
+            err = 0.0
+            for n in range(1, Nt + 1):
+                plan.step(g[n])
+                if n in sample:
+                    ue = u_ex(xr, np.full(xr.size, t[n]))
+                    err = max(err, float(np.max(np.abs(plan.receivers() - ue))))
+            plan.close()
+            errs.append(err)
+        order = math.log2(errs[0] / errs[1])
+        print(f"p = {p}: max error {errs[0]:.2e} (dt 0.01), {errs[1]:.2e} (dt 0.005), order {order:.2f}")
+        if p <= 4:
+            assert order > p + 0.5
+        else:
+            assert errs[1] < 1e-9
