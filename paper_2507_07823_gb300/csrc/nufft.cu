@@ -160,12 +160,6 @@ constexpr int kRangeCells = 240;    // cells of a mixed range (w - 1 halo cells 
 constexpr int kRangeCells64 = 128;  // cells of an FP64 range (its w tap sums per cell live in shared memory)
 constexpr int kRangePoints64 = 4096;  // FP64: its halo costs FP64 FMAs, so fewer, larger ranges
 constexpr int kEmptyCells = 8192;   // cells of a range no point reaches (zeros only)
-struct NuRange {
-    int32_t a0, na, b0, nb;        // staged points: slices [a0, a0 + na) then [b0, b0 + nb) of the sorted order
-    int32_t c0, nc, roff, lg;      // first grid real (instance x nf + cell), cells, offset of its run table
-                                   // (nc + w entries), log2 lanes per cell
-};
-
 template <int W, int D>
 __global__ void __launch_bounds__(kUnitThreads) k_nu_spread_mixed(const NuRange* __restrict__ ranges,
                                                                   const int32_t* __restrict__ runs,
@@ -692,66 +686,10 @@ int wave1d_nufft_plan_many(const double* x, const int64_t* offsets, int n_inst, 
         if ((rc = nu_upload(h, soff, &h->soff))) return cleanup(rc);
     }
     {
-        // spreading ranges, per instance: consecutive cell ranges tiling its grid, each at most
-        // kRangeCells (mixed) or kRangeCells64 (FP64) cells and, where a single cell allows, at
-        // most kRangePoints (mixed) or kRangePoints64 (FP64) points counting the w - 1 halo cells
-        // before it; a stretch of cells that no point reaches is one range of zeros.  ps[f] = first point
-        // of the instance (sorted order) whose first cell is >= f.
-        const int max_cells = precision == 1 ? kRangeCells : kRangeCells64;
-        const int max_points = precision == 1 ? kRangePoints : kRangePoints64;
         std::vector<NuRange> ranges;
         std::vector<int32_t> runs;
-        std::vector<int32_t> ps(nf + 1);
-        for (int b = 0; b < n_inst; b++) {
-            const int64_t o = offsets[b], mb = offsets[b + 1] - o;
-            std::fill(ps.begin(), ps.end(), 0);
-            for (int64_t i = 0; i < mb; i++) ps[i0[o + i] + 1]++;
-            for (int f = 0; f < nf; f++) ps[f + 1] += ps[f];
-            auto pts = [&](int f0, int f1) {      // points whose first cell is in [f0, f1), f0 may be < 0
-                if (f0 >= 0) return ps[f1] - ps[f0];
-                return (ps[nf] - ps[nf + f0]) + ps[f1];
-            };
-            for (int c0 = 0; c0 < nf;) {
-                int c1 = c0 + 1;
-                if (pts(c0 - w + 1, c0 + 1) == 0) {
-                    // cells no point reaches: one range of zeros up to the next reached cell
-                    while (c1 < nf && c1 - c0 < kEmptyCells && pts(c1 - w + 1, c1 + 1) == 0) c1++;
-                } else {
-                    while (c1 < nf && c1 - c0 < max_cells && pts(c0 - w + 1, c1 + 1) <= max_points) c1++;
-                }
-                NuRange r{};
-                r.c0 = b * nf + c0;
-                r.nc = c1 - c0;
-                const int h0 = c0 - w + 1;        // first halo cell (negative: wraps to the end)
-                if (h0 >= 0) {
-                    r.a0 = (int32_t)(o + ps[h0]);
-                    r.na = ps[c1] - ps[h0];
-                    r.b0 = (int32_t)o;
-                    r.nb = 0;
-                } else {
-                    r.a0 = (int32_t)(o + ps[nf + h0]);
-                    r.na = ps[nf] - ps[nf + h0];
-                    r.b0 = (int32_t)o;
-                    r.nb = ps[c1];
-                }
-                r.roff = (int32_t)runs.size();
-                if (r.na + r.nb > 0) {
-                    for (int k = 0; k <= r.nc + w - 1; k++) {    // run starts in staging order, then the end
-                        const int f = h0 + k;
-                        int off;
-                        if (k == r.nc + w - 1) off = r.na + r.nb;
-                        else if (f >= 0) off = (h0 >= 0 ? ps[f] - ps[h0] : r.na + ps[f]);
-                        else off = ps[nf + f] - ps[nf + h0];
-                        runs.push_back(off);
-                    }
-                }
-                const int nr = r.nc + w - 1;
-                r.lg = 0;
-                while (r.lg < 5 && (nr << (r.lg + 1)) <= kUnitThreads) r.lg++;
-                ranges.push_back(r);
-                c0 = c1;
-            }
-        }
+        nufft_ranges(i0, offsets, n_inst, nf, w, precision == 1 ? kRangeCells : kRangeCells64,
+                     precision == 1 ? kRangePoints : kRangePoints64, kEmptyCells, kUnitThreads, ranges, runs);
         h->nunits = (int64_t)ranges.size();
         if ((rc = nu_upload(h, ranges, &h->ranges)) || (rc = nu_upload(h, runs, &h->runs)) ||
             (rc = nu_upload(h, gfirst, &h->first)))

@@ -424,6 +424,63 @@ void nufft_grid(Params& P, int K, double tol, int w_in) {
     P.kb_beta = kPi * P.nufft_w * (1.0 - 1.0 / (2.0 * upsamp));
 }
 
+void nufft_ranges(const std::vector<int32_t>& i0, const int64_t* offsets, int n_inst, int nf, int w,
+                  int max_cells, int max_points, int empty_cells, int threads, std::vector<NuRange>& ranges,
+                  std::vector<int32_t>& runs) {
+    ranges.clear();
+    runs.clear();
+    std::vector<int32_t> ps(nf + 1);
+    for (int b = 0; b < n_inst; b++) {
+        const int64_t o = offsets[b], mb = offsets[b + 1] - o;
+        std::fill(ps.begin(), ps.end(), 0);
+        for (int64_t i = 0; i < mb; i++) ps[i0[o + i] + 1]++;
+        for (int f = 0; f < nf; f++) ps[f + 1] += ps[f];
+        auto pts = [&](int f0, int f1) {              // points whose first cell is in [f0, f1), f0 may be < 0
+            if (f0 >= 0) return ps[f1] - ps[f0];
+            return (ps[nf] - ps[nf + f0]) + ps[f1];
+        };
+        for (int c0 = 0; c0 < nf;) {
+            int c1 = c0 + 1;
+            if (pts(c0 - w + 1, c0 + 1) == 0) {
+                while (c1 < nf && c1 - c0 < empty_cells && pts(c1 - w + 1, c1 + 1) == 0) c1++;
+            } else {
+                while (c1 < nf && c1 - c0 < max_cells && pts(c0 - w + 1, c1 + 1) <= max_points) c1++;
+            }
+            NuRange r{};
+            r.c0 = b * nf + c0;
+            r.nc = c1 - c0;
+            const int h0 = c0 - w + 1;                // first halo cell (negative: wraps to the end)
+            if (h0 >= 0) {
+                r.a0 = (int32_t)(o + ps[h0]);
+                r.na = ps[c1] - ps[h0];
+                r.b0 = (int32_t)o;
+                r.nb = 0;
+            } else {
+                r.a0 = (int32_t)(o + ps[nf + h0]);
+                r.na = ps[nf] - ps[nf + h0];
+                r.b0 = (int32_t)o;
+                r.nb = ps[c1];
+            }
+            r.roff = (int32_t)runs.size();
+            if (r.na + r.nb > 0) {
+                for (int k = 0; k <= r.nc + w - 1; k++) {    // run starts in staging order, then the end
+                    const int f = h0 + k;
+                    int off;
+                    if (k == r.nc + w - 1) off = r.na + r.nb;
+                    else if (f >= 0) off = (h0 >= 0 ? ps[f] - ps[h0] : r.na + ps[f]);
+                    else off = ps[nf + f] - ps[nf + h0];
+                    runs.push_back(off);
+                }
+            }
+            const int nr = r.nc + w - 1;
+            r.lg = 0;
+            while (r.lg < 5 && (nr << (r.lg + 1)) <= threads) r.lg++;
+            ranges.push_back(r);
+            c0 = c1;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------------------------
 int build_host_plan(const double* x_in, const double* beta_in, int64_t M, int bc, double dt,
                     int64_t Nt, double tol, int p, double gamma, int W, int NL, int Ng, int nufft_w,
