@@ -56,3 +56,32 @@ def test_argument_validation_without_gpu(lib):
     assert wave1d.wave1d_plan(bad, b, 2, 0, 0.01, 10, 1e-10)[0] == wave1d.WAVE1D_EINVAL
     assert wave1d.wave1d_plan(x, np.array([1.0, -1.0]), 2, 0, 0.01, 10, 1e-10)[0] == wave1d.WAVE1D_EINVAL
     assert wave1d.wave1d_destroy(None) == 0
+
+
+def test_nufft_argument_validation_without_gpu(lib):
+    """wave1d_nufft_plan / wave1d_nufft_plan_many reject bad arguments before any CUDA call."""
+    L = lib
+    x = np.array([0.1, 0.2, 0.3])
+    h = ctypes.c_void_p()
+    xp = x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+    def plan(M, K, tol, prec):
+        return L.wave1d_nufft_plan(xp, M, K, tol, prec, None, ctypes.byref(h))
+
+    assert plan(0, 10, 1e-10, 0) == wave1d.WAVE1D_EINVAL                 # no points
+    assert plan(3, 0, 1e-10, 0) == wave1d.WAVE1D_EINVAL                  # no modes
+    assert plan(3, 10, 0.5, 0) == wave1d.WAVE1D_EINVAL                   # tolerance out of (0, 0.1)
+    assert plan(3, 10, 1e-10, 2) == wave1d.WAVE1D_EINVAL                 # unknown precision
+    assert plan(3, 10, 1e-8, 1) == wave1d.WAVE1D_EINVAL                  # mixed precision below 1e-6
+    assert L.wave1d_nufft_plan(None, 3, 10, 1e-10, 0, None, ctypes.byref(h)) == wave1d.WAVE1D_EINVAL
+
+    def many(offsets, n):
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        return L.wave1d_nufft_plan_many(xp, off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), n, 10, 1e-10, 0,
+                                        None, ctypes.byref(h))
+
+    assert many([1, 3], 1) == wave1d.WAVE1D_EINVAL                       # offsets[0] != 0
+    assert many([0, 2, 2, 3], 3) == wave1d.WAVE1D_EINVAL                 # an empty instance
+    assert many([0, 3], 0) == wave1d.WAVE1D_EINVAL                       # no instances
+    assert isinstance(L.wave1d_nufft_strerror(), bytes)
+    assert L.wave1d_nufft_destroy(None) == 0
