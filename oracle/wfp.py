@@ -16,7 +16,7 @@ One time step n -> n+1 (t_{n+1} = (n+1) dt), in the paper's order:
     -(I + S) sigma^{n+1} = g^{n+1} + sum_m C^(m) sigma^{n+1-m} + E alpha^{n+1}      linearSystem)
  7. receivers: u = u_L + u_H with sigma^{n+1} known                       (eq. localSol2)
 
-Readings where the paper is silent or inconsistent (each is listed in the design doc):
+Readings where the paper is silent or inconsistent:
  * K = floor(pi/dt) (eq. Kdt assumes pi/dt is an integer); W = ceil(2b/(pi gamma)), b = ln 1/eps.
  * The history term of eqs. periodicIE_AS / periodicIE_disc and E_jk is printed with beta_j/2; the
    representation u = u_L + u_H with eq. periodicIE fixes it as beta_j, which is used here.
