@@ -12,4 +12,7 @@ these files, and they share no code with it; both sides only read inputs drawn b
   written step by step with direct Fourier sums, a plain sparse matrix for the local
   part and a direct sparse solve.  The CUDA path is compared against it element by
   element.
+* `adjoint`: the reverse-time transposed march of Oracle B's scheme, giving the gradient of
+  a receiver misfit with respect to the stiffnesses (and to a host forcing); pinned by
+  central differences of Oracle B.
 """
