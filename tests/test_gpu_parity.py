@@ -273,3 +273,20 @@ def test_pairs_at_distance_dt_within_rounding():
     es, eu = _rel(sg, so), _rel(ug, uo)
     print(f"pairs at dt: sigma {es:.2e}, receivers {eu:.2e}")
     assert es < TOL and eu < TOL
+
+
+def test_large_implicit_blocks():
+    """Blocks of springs closer than dt with 300 members (the solve's single-task path above 256
+    members) and 40 members (32-row tasks), free space, every density and receiver value against
+    the oracle of the scheme over 300 steps."""
+    dt = 0.01
+    x = np.concatenate([-1.5 + 0.004 * np.arange(300), 0.5 + 0.004 * np.arange(40)])
+    beta = np.random.default_rng(8).uniform(0.5, 3.0, x.size)
+    w = W.config0().with_(bc=W.FREE, x=x, beta=beta, center=np.array([-2.6]), width=np.array([0.08]),
+                          dt=dt, Nt=300, tol=1e-10, xr=np.array([-1.8, 0.0, 1.2]))
+    sg, ug, info = _gpu_run(w)
+    so, uo, _ = _oracle_run(w)
+    print(f"large blocks: max block {info.max_block}, sigma {_rel(sg, so):.2e}, receivers {_rel(ug, uo):.2e}")
+    assert info.max_block == 300
+    assert np.max(np.abs(so)) > 1e-3
+    assert _rel(sg, so) < TOL and _rel(ug, uo) < TOL
