@@ -1,5 +1,6 @@
 """Host logic of the local sum (Sec. 4.1) without a GPU: the m-ordered rows and the 32-source work
-items the step kernel reads must reproduce the plain weight table row by row (to the FP32-pair
+items the step kernel reads must reproduce the plain weight table row by row, for the springs
+(m >= 1) and for the receivers (m >= 0) (to the FP32-pair
 rounding of the stored weights, about 2^-48 of the sum of the terms' magnitudes).  Layouts: random
 springs, springs spaced exactly dt apart (pair distances on dt and on delta within rounding, where
 a source with no weights once broke the rows), a dense cluster, and a periodic box."""
@@ -28,9 +29,9 @@ def checker():
     return out
 
 
-def _worst(checker, x, beta, dt, tol, bc):
-    text = f"{len(x)} {dt!r} {tol!r} {bc}\n" + " ".join(repr(float(v)) for v in x) + "\n" + \
-        " ".join(repr(float(v)) for v in beta) + "\n"
+def _worst(checker, x, beta, dt, tol, bc, xr):
+    text = f"{len(x)} {dt!r} {tol!r} {bc} {len(xr)}\n" + " ".join(repr(float(v)) for v in x) + "\n" + \
+        " ".join(repr(float(v)) for v in beta) + "\n" + " ".join(repr(float(v)) for v in xr) + "\n"
     r = subprocess.run([checker], input=text, capture_output=True, text=True, check=True)
     return float(r.stdout.split()[0])
 
@@ -48,4 +49,6 @@ def test_rows_and_items_reproduce_the_weight_table(checker, layout):
     else:
         x, bc = np.sort(rng.uniform(-np.pi, np.pi, 300)), 0
     beta = rng.uniform(1.0, 10.0, x.size)
-    assert _worst(checker, x, beta, dt, tol, bc) < 1e-13
+    # receivers: among the springs, one exactly on a spring, one a spacing away
+    xr = np.array([-1.2, float(x[5]), float(x[5]) + 0.01, 0.0, 1.3])
+    assert _worst(checker, x, beta, dt, tol, bc, xr) < 1e-13
