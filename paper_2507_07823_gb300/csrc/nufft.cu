@@ -231,7 +231,9 @@ __global__ void __launch_bounds__(kUnitThreads) k_nu_spread_mixed(const NuRange*
         for (int d = 1; d <= D; d++) mo[f][d + 1] = m[d];
     }
     __syncthreads();
-    if ((int)threadIdx.x < u.nc) {
+    if ((int)threadIdx.x < u.nc && rp[threadIdx.x + W] == rp[threadIdx.x]) {
+        grid[u.c0 + threadIdx.x] = 0.0;               // none of the w cells feeding it holds a point
+    } else if ((int)threadIdx.x < u.nc) {
         // grid real c0 + l takes tap t of cell c0 + l - t, i.e. run (l + w - 1) - t
         const int l = threadIdx.x;
         float h = 0.f, lo = 0.f, r = 0.f;
@@ -308,8 +310,10 @@ __global__ void __launch_bounds__(kUnitThreads) k_nu_spread64(const NuRange* __r
     if ((int)threadIdx.x < u.nc) {
         const int l = threadIdx.x;
         double a = 0.0;
+        if (rp[l + W] != rp[l]) {                     // else none of the w cells feeding it holds a point
 #pragma unroll
-        for (int t = 0; t < W; t++) a += seg[l + W - 1 - t][t];
+            for (int t = 0; t < W; t++) a += seg[l + W - 1 - t][t];
+        }
         grid[u.c0 + l] = a;
     }
 }
