@@ -17,8 +17,8 @@ def _setup(bc, seed=5):
     x[3] = x[2] + 0.013                       # one pair closer than dt: an implicit block
     beta = rng.uniform(1.0, 6.0, M)
     w = W.Workload(name="adjoint", bc=bc, x=x, beta=beta, amp=np.array([1.0]), center=np.array([-1.6]),
-                   width=np.array([0.12]), dt=0.02, Nt=400, tol=1e-10, p=6, xr=np.array([-0.95, 0.1, 0.95]),
-                   seed=seed)
+                   width=np.array([0.12]), dt=0.02, Nt=400, tol=1e-10, p=6,
+                   xr=np.array([-0.95, 0.1, x[5], 0.95]), seed=seed)   # one receiver on a spring (m = 0 terms)
     # targets: the receivers of the same layout with perturbed stiffnesses
     w_true = w.with_(beta=beta * (1.0 + 0.1 * rng.standard_normal(M)))
     _, d = wfp.from_workload(w_true).run(w.Nt)
