@@ -14,5 +14,6 @@ these files, and they share no code with it; both sides only read inputs drawn b
   element.
 * `adjoint`: the reverse-time transposed march of Oracle B's scheme, giving the gradient of
   a receiver misfit with respect to the stiffnesses (and to a host forcing); pinned by
-  central differences of Oracle B.
+  central differences of Oracle B and by the complex-step derivative of Oracle A (its
+  complex build, `volterra.march_complex_step`).
 """

@@ -31,10 +31,29 @@
  *
  * Receivers: u(x_r, t_{n+1}) = 1/2 sum_l sum_images I_l(t_{n+1} - |x_r - x_l - 2 pi m|)
  * (eq. singleLayerSol / SLPp), evaluated after sigma^{n+1} is known, with the same stencil rule.
+ *
+ * Complex-step build (compiled a second time with -DORACLE_COMPLEX_STEP): the stiffnesses,
+ * densities, prefix sums, receiver fields and the block solve hold complex numbers, the geometry
+ * and quadrature stay real, and the entry point is oracle_volterra_march_cs.  Every operation on
+ * the complex values is a sum or a product, so with beta_j + i h the imaginary part of any output
+ * divided by h is its derivative with respect to beta_j up to O(h^2), free of cancellation
+ * (Squire and Trapp, SIAM Rev. 40, 1998).  Pivots are chosen by the real part, the same choice
+ * as the real build.
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+
+#ifdef ORACLE_COMPLEX_STEP
+#include <complex.h>
+typedef double _Complex scalar_t;
+#define PIVOT_MAG(v) fabs(creal(v))
+#define MARCH_ENTRY oracle_volterra_march_cs
+#else
+typedef double scalar_t;
+#define PIVOT_MAG(v) fabs(v)
+#define MARCH_ENTRY oracle_volterra_march
+#endif
 
 #define TWO_PI 6.283185307179586476925286766559
 
@@ -81,11 +100,11 @@ static long stencil_top(long a, int p)
  * coefficient multiplying the sample with index `imp` is returned in *cimp instead of being
  * multiplied by sig (pass imp = -1 to use sig for every index).  Result is in units of dt.
  */
-static double interval_integral(const double* sig, long a, double theta, int p, long newest,
+static scalar_t interval_integral(const scalar_t* sig, long a, double theta, int p, long newest,
                                 long imp, double* cimp, int ng, const double* gx, const double* gw)
 {
     long q0 = stencil_start(a, p, newest);
-    double acc = 0.0;
+    scalar_t acc = 0.0;
     for (int i = 0; i < ng; i++) {
         double y = (double)a + 0.5 * theta * (1.0 + gx[i]);
         double wt = 0.5 * theta * gw[i];
@@ -117,30 +136,30 @@ static long uf_find(long* parent, long i)
 }
 
 /* dense Gaussian elimination with partial pivoting, A is n x n row-major, b overwritten */
-static int dense_solve(int n, double* A, double* b)
+static int dense_solve(int n, scalar_t* A, scalar_t* b)
 {
     for (int k = 0; k < n; k++) {
         int piv = k;
-        double best = fabs(A[k * n + k]);
+        double best = PIVOT_MAG(A[k * n + k]);
         for (int i = k + 1; i < n; i++) {
-            if (fabs(A[i * n + k]) > best) { best = fabs(A[i * n + k]); piv = i; }
+            if (PIVOT_MAG(A[i * n + k]) > best) { best = PIVOT_MAG(A[i * n + k]); piv = i; }
         }
         if (best == 0.0) return -1;
         if (piv != k) {
             for (int c = 0; c < n; c++) {
-                double t = A[k * n + c]; A[k * n + c] = A[piv * n + c]; A[piv * n + c] = t;
+                scalar_t t = A[k * n + c]; A[k * n + c] = A[piv * n + c]; A[piv * n + c] = t;
             }
-            double t = b[k]; b[k] = b[piv]; b[piv] = t;
+            scalar_t t = b[k]; b[k] = b[piv]; b[piv] = t;
         }
         for (int i = k + 1; i < n; i++) {
-            double f = A[i * n + k] / A[k * n + k];
+            scalar_t f = A[i * n + k] / A[k * n + k];
             if (f == 0.0) continue;
             for (int c = k; c < n; c++) A[i * n + c] -= f * A[k * n + c];
             b[i] -= f * b[k];
         }
     }
     for (int k = n - 1; k >= 0; k--) {
-        double s = b[k];
+        scalar_t s = b[k];
         for (int c = k + 1; c < n; c++) s -= A[k * n + c] * b[c];
         b[k] = s / A[k * n + k];
     }
@@ -175,7 +194,7 @@ static long collect_pairs(double xt, long M, const double* x, int periodic, doub
  * sig_l: samples of spring l (index q at sig_l[q]); P_l: prefix sums of final intervals;
  * afin: number of final intervals stored in P_l.
  */
-static double running_integral(const double* sig_l, const double* P_l, long afin, long n,
+static scalar_t running_integral(const scalar_t* sig_l, const scalar_t* P_l, long afin, long n,
                                double d, double dt, int p, int use_imp, double* cimp, int ng,
                                const double* gx, const double* gw)
 {
@@ -186,7 +205,7 @@ static double running_integral(const double* sig_l, const double* P_l, long afin
     long newest = (d < dt) ? n + 1 : n;
     long imp = use_imp ? n + 1 : -1;
     long a0 = as < afin ? as : afin;
-    double acc = P_l[a0];
+    scalar_t acc = P_l[a0];
     for (long a = a0; a < as; a++)
         acc += interval_integral(sig_l, a, 1.0, p, newest, imp, cimp, ng, gx, gw);
     if (theta > 0.0)
@@ -200,20 +219,20 @@ static double running_integral(const double* sig_l, const double* P_l, long afin
  * gx, gw: Gauss-Legendre nodes/weights on [-1, 1] with ng >= p/2 + 1.
  * Returns 0, or -1 on a singular block, -2 on bad arguments, -3 on allocation failure.
  */
-int oracle_volterra_march(long M, const double* x, const double* beta, int periodic, double dt,
+int MARCH_ENTRY(long M, const double* x, const scalar_t* beta, int periodic, double dt,
                           long Nt, int p, int npulse, const double* amp, const double* center,
                           const double* width, const double* g_in, long R, const double* xr,
-                          int ng, const double* gx, const double* gw, double* sigma_out,
-                          double* u_out)
+                          int ng, const double* gx, const double* gw, scalar_t* sigma_out,
+                          scalar_t* u_out)
 {
     if (M < 1 || Nt < 0 || dt <= 0.0 || p < 1 || (p > 1 && (p % 2) != 0)) return -2;
     long stride = Nt + 2;                       /* sig[l * stride + q], q = 0..Nt+1 */
     long pstride = Nt + 3;                      /* P[l * pstride + a],  a = 0..Nt+2 */
     double T = (double)Nt * dt;
     long per_src = periodic ? (long)floor(T / (0.5 * TWO_PI)) + 3 : 1;
-    double* sig = (double*)calloc((size_t)M * stride, sizeof(double));
-    double* P = (double*)calloc((size_t)M * pstride, sizeof(double));
-    double* rhs = (double*)malloc(sizeof(double) * (size_t)M);
+    scalar_t* sig = (scalar_t*)calloc((size_t)M * stride, sizeof(scalar_t));
+    scalar_t* P = (scalar_t*)calloc((size_t)M * pstride, sizeof(scalar_t));
+    scalar_t* rhs = (scalar_t*)malloc(sizeof(scalar_t) * (size_t)M);
     /* nearby pairs (distance < dt over the nearest image), CSR by target; geometry only */
     long* nb_ptr = (long*)calloc((size_t)M + 1, sizeof(long));
     if (!sig || !P || !rhs || !nb_ptr) return -3;
@@ -227,7 +246,7 @@ int oracle_volterra_march(long M, const double* x, const double* beta, int perio
     long nnb = nb_ptr[M];
     long* nb_l = (long*)malloc(sizeof(long) * (size_t)(nnb + 1));
     double* nb_d = (double*)malloc(sizeof(double) * (size_t)(nnb + 1));
-    double* nb_c = (double*)malloc(sizeof(double) * (size_t)(nnb + 1));
+    scalar_t* nb_c = (scalar_t*)malloc(sizeof(scalar_t) * (size_t)(nnb + 1));
     if (!nb_l || !nb_d || !nb_c) return -3;
     for (long j = 0; j < M; j++) {
         long e = nb_ptr[j];
@@ -273,7 +292,7 @@ int oracle_volterra_march(long M, const double* x, const double* beta, int perio
             #pragma omp for schedule(dynamic, 4)
             for (long j = 0; j < M; j++) {
                 long np_ = collect_pairs(x[j], M, x, periodic, t1, pairs);
-                double known = 0.0;
+                scalar_t known = 0.0;
                 for (long e = 0; e < np_; e++) {
                     if (pairs[e].d < dt) continue;          /* nearby images handled below */
                     double cimp = 0.0;
@@ -286,7 +305,7 @@ int oracle_volterra_march(long M, const double* x, const double* beta, int perio
                                               n, nb_d[e], dt, p, 1, &cimp, ng, gx, gw);
                     nb_c[e] = 0.5 * beta[j] * dt * cimp;
                 }
-                double g = g_in ? g_in[(n + 1) * M + j]
+                scalar_t g = g_in ? g_in[(n + 1) * M + j]
                                 : beta[j] * incident(x[j] - t1, npulse, amp, center, width, periodic);
                 rhs[j] = -g - 0.5 * beta[j] * dt * known;
             }
@@ -297,8 +316,8 @@ int oracle_volterra_march(long M, const double* x, const double* beta, int perio
         for (long rt = 0; rt < M; rt++) {
             long b0 = bstart[rt], nbk = bstart[rt + 1] - b0;
             if (nbk == 0) continue;
-            double* A = (double*)calloc((size_t)nbk * nbk, sizeof(double));
-            double* bb = (double*)malloc(sizeof(double) * (size_t)nbk);
+            scalar_t* A = (scalar_t*)calloc((size_t)nbk * nbk, sizeof(scalar_t));
+            scalar_t* bb = (scalar_t*)malloc(sizeof(scalar_t) * (size_t)nbk);
             for (long i = 0; i < nbk; i++) {
                 long j = members[b0 + i];
                 A[i * nbk + i] = 1.0;
@@ -320,7 +339,7 @@ int oracle_volterra_march(long M, const double* x, const double* beta, int perio
             #pragma omp for
             for (long r = 0; r < R; r++) {
                 long np_ = collect_pairs(xr[r], M, x, periodic, t1, pairs);
-                double u = 0.0;
+                scalar_t u = 0.0;
                 for (long e = 0; e < np_; e++) {
                     double dummy = 0.0;
                     u += running_integral(sig + pairs[e].l * stride, P + pairs[e].l * pstride, afin,
@@ -336,7 +355,7 @@ int oracle_volterra_march(long M, const double* x, const double* beta, int perio
             #pragma omp parallel for
             for (long l = 0; l < M; l++) {
                 double dummy = 0.0;
-                double F = interval_integral(sig + l * stride, afin, 1.0, p, n + 1, -1, &dummy,
+                scalar_t F = interval_integral(sig + l * stride, afin, 1.0, p, n + 1, -1, &dummy,
                                              ng, gx, gw);
                 P[l * pstride + afin + 1] = P[l * pstride + afin] + F;
             }
