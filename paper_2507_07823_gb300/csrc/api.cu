@@ -34,6 +34,20 @@ __global__ void k_solve(DevPlan P);
 __global__ void k_sigma_to_caller(DevPlan P, int64_t q, double* out);
 __global__ void k_internal_to_caller(const int32_t* perm, int64_t M, const double* in, double* out);
 __global__ void k_caller_to_internal(const int32_t* perm, int64_t M, const double* in, double* out);
+__global__ void k_adj_receivers(DevPlan P, int64_t n, const double* ubar, double* sb);
+__global__ void k_adj_take(int64_t M, double* slot_vals, double* out);
+__global__ void k_adj_solve(DevPlan P, const int32_t* blk_of, const double* sigbar, const double* sigma_next,
+                            double* grad, double* cbar, double* uHbar);
+__global__ void k_adj_local(DevPlan P, int64_t n, const double* cbar, double* sb);
+__global__ void k_adj_gather(int64_t M, const int64_t* perm, const double* in, double* out);
+__global__ void k_adj_scatter_add(int64_t M, const int64_t* perm, const double* in, double* acc);
+__global__ void k_adj_modes_in(int K, const double* S1, const double* xr, const double* ubar, int64_t R, double* ab);
+__global__ void k_adj_rbc_grid(int K, int npts, const int32_t* idx, const double* tw2K, const double* phi,
+                               const double* dphi, const double* ab, const double* apb, double* uvbar);
+__global__ void k_adj_rbc_update(int K, int npts, const int32_t* idx, const double* tw2K, const double* uvbar,
+                                 double* ab, double* apb);
+__global__ void k_adj_modes(int K, int W, int64_t n, const double* rot, const double* pq, double* ab, double* apb,
+                            double* Sb, double* a2);
 }  // namespace wave1d
 
 using namespace wave1d;
@@ -955,6 +969,109 @@ int wave1d_profile_read(wave1d_plan_t p, double* ms, int nstage, int64_t* steps)
     for (int i = 0; i < WAVE1D_NSTAGE; i++) ms[i] = p->prof_ms[i];
     if (steps) *steps = p->prof_steps;
     return WAVE1D_OK;
+}
+
+}  // extern "C"
+
+namespace {
+// work arrays of one adjoint call, released (after the stream drains) when the call returns
+struct AdjointWork {
+    cudaStream_t s = nullptr;
+    std::vector<void*> ptrs;
+    wave1d_nufft_t nu = nullptr;
+    ~AdjointWork() {
+        if (s) cudaStreamSynchronize(s);
+        for (void* q : ptrs) cudaFree(q);
+        if (nu) wave1d_nufft_destroy(nu);
+    }
+    template <typename T>
+    int zeros(T** out, size_t count) {
+        void* q = nullptr;
+        count = std::max<size_t>(count, 1);
+        cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+        if (e != cudaSuccess) return fail(WAVE1D_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        ptrs.push_back(q);
+        *out = (T*)q;
+        CK(cudaMemsetAsync(q, 0, count * sizeof(T), s));
+        return WAVE1D_OK;
+    }
+    template <typename T>
+    int upload(const std::vector<T>& v, T** out) {
+        int rc = zeros(out, v.size());
+        if (rc || v.empty()) return rc;
+        CK(cudaMemcpyAsync(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+        return WAVE1D_OK;
+    }
+};
+
+unsigned blocks_for(int64_t threads, int per_block, int64_t cap) {
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((threads + per_block - 1) / per_block, cap));
+}
+}  // namespace
+
+extern "C" {
+
+int wave1d_adjoint(wave1d_plan_t p, int64_t nsteps, const double* sigma, const double* ubar, double* grad) {
+    if (!p || !sigma || !grad || nsteps < 1) return fail(WAVE1D_EINVAL, "need a plan, sigma, grad and nsteps >= 1");
+    const HostPlan& hp = p->hp;
+    const Params& P = hp.P;
+    if (nsteps > P.Nt) return fail(WAVE1D_EINVAL, "nsteps beyond the Nt of the plan");
+    if (P.R > 0 && !ubar) return fail(WAVE1D_EINVAL, "ubar is NULL");
+    for (double b : hp.beta)
+        if (!(b > 0.0)) return fail(WAVE1D_EINVAL, "the adjoint needs every stiffness > 0 (its gradient term is sigma_j / beta_j)");
+    int rc = enter(p);
+    if (rc) return rc;
+    const int64_t M = P.M, R = P.R;
+    const int K = P.K, K1 = P.K + 1, ring = P.ring;
+    const DevPlan& d = p->dp;
+    AdjointWork wk;
+    wk.s = p->s;
+    if ((rc = wave1d_nufft_plan(hp.x.data(), M, K, P.tol, 0, (void*)p->s, &wk.nu)))
+        return fail(rc, std::string("NUFFT plan of the springs: ") + wave1d_nufft_strerror());
+    std::vector<int64_t> nperm(M);
+    if ((rc = wave1d_nufft_perm(wk.nu, nperm.data()))) return fail(rc, wave1d_nufft_strerror());
+    std::vector<int32_t> blk_of(M);
+    for (size_t b = 0; b + 1 < hp.blk_ptr.size(); b++)
+        for (int64_t e = hp.blk_ptr[b]; e < hp.blk_ptr[b + 1]; e++) blk_of[e] = (int32_t)b;
+    const int npts = (int)hp.rbc_idx.size();
+    double *sb, *Sb, *ab, *apb, *a2, *S1, *tmp, *cbar, *uHbar, *gsum, *cnu, *unu, *xr, *uvbar;
+    int32_t* dblk;
+    int64_t* dperm;
+    if ((rc = wk.zeros(&sb, (size_t)ring * M)) || (rc = wk.zeros(&Sb, (size_t)P.W * K1 * 2)) ||
+        (rc = wk.zeros(&ab, 2 * (size_t)K1)) || (rc = wk.zeros(&apb, 2 * (size_t)K1)) ||
+        (rc = wk.zeros(&a2, 2 * (size_t)K1)) || (rc = wk.zeros(&S1, 2 * (size_t)K1)) ||
+        (rc = wk.zeros(&tmp, (size_t)M)) || (rc = wk.zeros(&cbar, (size_t)M)) || (rc = wk.zeros(&uHbar, (size_t)M)) ||
+        (rc = wk.zeros(&gsum, (size_t)M)) || (rc = wk.zeros(&cnu, (size_t)M)) || (rc = wk.zeros(&unu, (size_t)M)) ||
+        (rc = wk.zeros(&uvbar, 2 * (size_t)std::max(npts, 1))) || (rc = wk.upload(hp.xr, &xr)) ||
+        (rc = wk.upload(blk_of, &dblk)) || (rc = wk.upload(nperm, &dperm)))
+        return rc;
+    const int64_t cap = (int64_t)p->sms * 8;
+    const unsigned gM = blocks_for(M, 256, cap), gK = blocks_for(K1, 256, INT32_MAX);
+    cudaStream_t s = p->s;
+    for (int64_t n = nsteps - 1; n >= 0; n--) {
+        const double* ub = R > 0 ? ubar + n * R : nullptr;
+        if (R > 0) k_adj_receivers<<<blocks_for((d.r_nitems + R) * 32, 256, INT32_MAX), 256, 0, s>>>(d, n, ub, sb);
+        k_adj_take<<<gM, 256, 0, s>>>(M, sb + (int64_t)(((n + 1) % ring)) * M, tmp);
+        k_adj_solve<<<gM, 256, 0, s>>>(d, dblk, tmp, sigma + n * M, gsum, cbar, uHbar);
+        if (n == 0) break;
+        if (d.l_nitems > 0) k_adj_local<<<blocks_for(d.l_nitems * 32, 256, INT32_MAX), 256, 0, s>>>(d, n, cbar, sb);
+        k_adj_gather<<<gM, 256, 0, s>>>(M, dperm, uHbar, cnu);
+        if ((rc = wave1d_nufft_type1(wk.nu, cnu, S1))) return fail(rc, wave1d_nufft_strerror());
+        k_adj_modes_in<<<gK, 256, 0, s>>>(K, S1, xr, ub, R, ab);
+        if (P.bc == WAVE1D_FREE && (n + 1) % P.rbc_period == 0 && npts > 0) {
+            k_adj_rbc_grid<<<blocks_for(npts, 64, INT32_MAX), 64, 0, s>>>(K, npts, d.rbc_idx, d.tw2K, d.rbc_phi,
+                                                                         d.rbc_dphi, ab, apb, uvbar);
+            k_adj_rbc_update<<<gK, 256, 0, s>>>(K, npts, d.rbc_idx, d.tw2K, uvbar, ab, apb);
+        }
+        k_adj_modes<<<gK, 256, 0, s>>>(K, P.W, n, d.rot, d.pq, ab, apb, Sb, a2);
+        if ((rc = wave1d_nufft_type2(wk.nu, a2, unu))) return fail(rc, wave1d_nufft_strerror());
+        k_adj_scatter_add<<<gM, 256, 0, s>>>(M, dperm, unu, sb + (int64_t)(n % ring) * M);
+        CK(cudaGetLastError());
+    }
+    k_internal_to_caller<<<gM, 256, 0, s>>>(d.perm, M, gsum, grad);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(s));
+    return leave(p);
 }
 
 int wave1d_destroy(wave1d_plan_t p) {

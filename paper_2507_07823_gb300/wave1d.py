@@ -44,7 +44,7 @@ EXPORTED = ["wave1d_opts_default", "wave1d_plan", "wave1d_set_incident_gaussians
             "wave1d_nufft_plan", "wave1d_nufft_plan_many", "wave1d_nufft_info", "wave1d_nufft_perm",
             "wave1d_nufft_spread",
             "wave1d_nufft_interp", "wave1d_nufft_type1", "wave1d_nufft_type2", "wave1d_nufft_destroy",
-            "wave1d_nufft_strerror"]
+            "wave1d_nufft_strerror", "wave1d_adjoint"]
 
 WAVE1D_NSTAGE = 9
 STAGES = ["local", "spread", "fft_fwd", "modes", "rbc", "fft_inv", "interp", "solve", "receivers"]
@@ -116,6 +116,7 @@ def lib(path: str = LIB_PATH):
         for nm in ("wave1d_nufft_spread", "wave1d_nufft_interp", "wave1d_nufft_type1", "wave1d_nufft_type2"):
             getattr(L, nm).argtypes = [P, _D, _D]
         L.wave1d_nufft_destroy.argtypes = [P]
+        L.wave1d_adjoint.argtypes = [P, ctypes.c_int64, _D, _D, _D]
         L.wave1d_nufft_strerror.argtypes = []
         L.wave1d_nufft_strerror.restype = ctypes.c_char_p
         L.wave1d_strerror.argtypes = [ctypes.c_int]
@@ -184,6 +185,12 @@ def wave1d_solve(plan, nsteps, u_rec, sigma, out_on_device):
     f = _dptr if out_on_device else _hptr
     return lib().wave1d_solve(plan, int(nsteps), f(u_rec) if u_rec is not None else None,
                               f(sigma) if sigma is not None else None, int(out_on_device))
+
+
+def wave1d_adjoint(plan, nsteps, sigma, ubar, grad):
+    """sigma (nsteps x M), ubar (nsteps x R, or None when R = 0), grad (M): device tensors."""
+    return lib().wave1d_adjoint(plan, int(nsteps), _dptr(sigma), _dptr(ubar) if ubar is not None else None,
+                                _dptr(grad))
 
 
 class Nufft:
@@ -341,6 +348,23 @@ class Plan:
         _check(wave1d_solve(self.h, nsteps, u if self.R else None, s, 0), "wave1d_solve")
         return (s, u[:, :self.R])
 
+    def solve_device(self, nsteps):
+        """The march with device outputs: (sigma, u) torch CUDA tensors, rows s = step s + 1."""
+        import torch
+        s = torch.empty((nsteps, self.M), dtype=torch.float64, device="cuda")
+        u = torch.empty((nsteps, max(self.R, 1)), dtype=torch.float64, device="cuda")
+        _check(wave1d_solve(self.h, nsteps, u if self.R else None, s, 1), "wave1d_solve")
+        return s, u[:, :self.R]
+
+    def adjoint(self, sigma, ubar):
+        """dL/dbeta (torch CUDA tensor, caller order) from the march's densities sigma (nsteps x M)
+        and the receiver adjoints ubar = dL/du (nsteps x R), both torch CUDA tensors."""
+        import torch
+        g = torch.empty(self.M, dtype=torch.float64, device=sigma.device)
+        ub = ubar.contiguous() if self.R else None
+        _check(wave1d_adjoint(self.h, sigma.shape[0], sigma.contiguous(), ub, g), "wave1d_adjoint")
+        return g
+
     def step(self, g=None):
         _check(wave1d_step(self.h, g, 0), "wave1d_step")
 
@@ -378,3 +402,30 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def receiver_fields(beta, w, nsteps):
+    """The receiver fields u (nsteps x R, torch CUDA float64) of an nsteps march of workload `w`
+    with stiffnesses `beta` (torch CUDA float64 tensor), differentiable in beta: the backward pass
+    is the library's reverse-time march (wave1d_adjoint).  Each call builds and frees a plan."""
+    import torch
+
+    class _ReceiverFields(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, b):
+            plan = Plan(w.x, b.detach().cpu().numpy(), w.bc, w.dt, max(w.Nt, nsteps), w.tol, w.amp,
+                        w.center, w.width, w.xr, p=w.p)
+            sigma, u = plan.solve_device(nsteps)
+            ctx.plan = plan
+            ctx.save_for_backward(sigma)
+            return u
+
+        @staticmethod
+        def backward(ctx, gu):
+            (sigma,) = ctx.saved_tensors
+            try:
+                return ctx.plan.adjoint(sigma, gu)
+            finally:
+                ctx.plan.close()
+
+    return _ReceiverFields.apply(beta)

@@ -85,3 +85,9 @@ def test_nufft_argument_validation_without_gpu(lib):
     assert many([0, 3], 0) == wave1d.WAVE1D_EINVAL                       # no instances
     assert isinstance(L.wave1d_nufft_strerror(), bytes)
     assert L.wave1d_nufft_destroy(None) == 0
+
+
+def test_adjoint_argument_validation_without_gpu(lib):
+    """wave1d_adjoint refuses a missing plan before touching any device memory."""
+    L = wave1d.lib()
+    assert L.wave1d_adjoint(None, 1, None, None, None) == wave1d.WAVE1D_EINVAL

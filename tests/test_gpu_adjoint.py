@@ -1,0 +1,101 @@
+"""GPU reverse-time march (wave1d_adjoint): dL/dbeta of a receiver misfit against the adjoint
+oracle (oracle/adjoint.py) at 1e-9 of the largest component, the same gradient through the
+torch.autograd wrapper, and central differences of the GPU forward march on a larger free-space
+layout (several projections, hundreds of springs).
+
+The kernels' bodies are checked on the CPU against the same oracle by tests/test_host_adjoint.py;
+these tests are their first run on a GPU and stay skipped until that run has been made."""
+import numpy as np
+import pytest
+
+from oracle import adjoint, wfp
+from paper_2507_07823_gb300 import wave1d
+from paper_2507_07823_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skip(reason="first GPU run of the reverse-march kernels pending")]
+
+
+def _layout(bc, seed=5, M=10, p=6, dt=0.02, Nt=400):
+    rng = np.random.default_rng(seed)
+    x = np.sort(rng.uniform(-0.8, 0.8, M))
+    x[3] = x[2] + 0.4 * dt                       # an implicit block
+    beta = rng.uniform(1.0, 6.0, M)
+    xr = np.array([-0.95, 0.1, x[5], 0.95])      # one receiver on a spring (m = 0 terms)
+    return W.Workload(name="adjoint", bc=bc, x=x, beta=beta, amp=np.array([1.0]), center=np.array([-1.6]),
+                      width=np.array([0.12]), dt=dt, Nt=Nt, tol=1e-10, p=p, xr=xr, seed=seed)
+
+
+def _targets(w):
+    t = np.arange(w.Nt + 1)[:, None] * w.dt
+    return 0.3 * np.sin(3.0 * t + w.xr[None, :])
+
+
+@pytest.mark.parametrize("bc", [W.PERIODIC, W.FREE])
+def test_gradient_matches_the_adjoint_oracle(bc):
+    w = _layout(bc)
+    d = _targets(w)
+    _, g_oracle = adjoint.misfit_and_gradient(wfp.from_workload(w), w.Nt, d)
+    plan = wave1d.Plan.from_workload(w)
+    try:
+        sigma, u = plan.solve_device(w.Nt)
+        ubar = u - torch.from_numpy(d[1:]).cuda()
+        g = plan.adjoint(sigma, ubar).cpu().numpy()
+    finally:
+        plan.close()
+    assert np.max(np.abs(g - g_oracle)) <= 1e-9 * np.max(np.abs(g_oracle)), (g, g_oracle)
+
+
+def test_autograd_wrapper_gives_the_same_gradient():
+    w = _layout(W.FREE, seed=9)
+    d = torch.from_numpy(_targets(w)[1:]).cuda()
+    beta = torch.tensor(w.beta, dtype=torch.float64, device="cuda", requires_grad=True)
+    u = wave1d.receiver_fields(beta, w, w.Nt)
+    loss = 0.5 * torch.sum((u - d) ** 2)
+    loss.backward()
+    L, g_oracle = adjoint.misfit_and_gradient(wfp.from_workload(w), w.Nt, _targets(w))
+    assert abs(loss.item() - L) <= 1e-9 * L
+    g = beta.grad.cpu().numpy()
+    assert np.max(np.abs(g - g_oracle)) <= 1e-9 * np.max(np.abs(g_oracle))
+
+
+def test_gradient_matches_central_differences_of_the_gpu_march():
+    """Free space, 400 springs in [-2.5, 2.5], dt = 5e-3, 600 steps (projections every
+    ceil(1.5 W) steps), 4 receivers: the adjoint gradient on 8 stiffnesses against central
+    differences of the GPU forward march (step 1e-4 beta_j)."""
+    rng = np.random.default_rng(2024)
+    M, dt, Nt = 400, 5e-3, 600
+    x = np.sort(rng.uniform(-2.5, 2.5, M))
+    beta = rng.uniform(1.0, 10.0, M)
+    xr = np.array([-2.6, -0.3, 0.4, 2.6])                  # inside |x| <= pi - 3 delta (delta = 0.15)
+    w = W.Workload(name="adjoint-fd", bc=W.FREE, x=x, beta=beta, amp=np.array([1.0]), center=np.array([-3.3]),
+                   width=np.array([0.1]), dt=dt, Nt=Nt, tol=1e-10, p=8, xr=xr, seed=2024)
+    d = torch.from_numpy(_targets(w)[1:]).cuda()
+
+    def loss_of(b):
+        plan = wave1d.Plan(w.x, b, w.bc, w.dt, w.Nt, w.tol, w.amp, w.center, w.width, w.xr, p=w.p)
+        try:
+            sigma, u = plan.solve_device(Nt)
+            return 0.5 * float(torch.sum((u - d) ** 2)), sigma, u, plan
+        except Exception:
+            plan.close()
+            raise
+
+    L, sigma, u, plan = loss_of(beta)
+    try:
+        g = plan.adjoint(sigma, u - d).cpu().numpy()
+    finally:
+        plan.close()
+    for j in rng.choice(M, 8, replace=False):
+        h = 1e-4 * beta[j]
+        bp, bm = beta.copy(), beta.copy()
+        bp[j] += h
+        bm[j] -= h
+        Lp, *rest = loss_of(bp)
+        rest[-1].close()
+        Lm, *rest = loss_of(bm)
+        rest[-1].close()
+        fd = (Lp - Lm) / (2 * h)
+        assert abs(g[j] - fd) <= 1e-6 * np.max(np.abs(g)), (j, g[j], fd)

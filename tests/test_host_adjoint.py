@@ -1,0 +1,69 @@
+"""The bodies of the GPU reverse-time march (csrc/adjoint.cuh) checked without a GPU: a host
+harness runs them, one element at a time in the kernels' launch order, over the tables the plan
+builder makes (local-sum items of springs and receivers, m = 0 receiver terms, block inverses,
+FIR and rotation tables, projection tables), with exact Fourier sums in place of the library's
+NUFFT plan, and its dL/dbeta must equal the adjoint oracle's (oracle/adjoint.py), which is
+pinned by finite differences and by the complex-step derivative of the direct march."""
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import adjoint, wfp
+from paper_2507_07823_gb300 import workloads as W
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "..", "paper_2507_07823_gb300", "csrc")
+INCLUDE = os.path.join(HERE, "..", "include")
+
+
+@pytest.fixture(scope="module")
+def harness():
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    build_dir = os.path.join(HERE, "native", "_build")         # git-ignored, inside the repository
+    os.makedirs(build_dir, exist_ok=True)
+    out = os.path.join(build_dir, "adjoint_check")
+    cmd = ["g++", "-O2", "-std=c++17", "-I", CSRC, "-I", INCLUDE, "-o", out,
+           os.path.join(HERE, "native", "adjoint_check.cpp"), os.path.join(CSRC, "plan_host.cpp"), "-lpthread"]
+    subprocess.run(cmd, check=True, capture_output=True)
+    return out
+
+
+def _run(harness, w, sigma, ubar):
+    text = f"{w.M} {len(w.xr)} {w.bc} {w.dt!r} {w.tol!r} {w.p} {w.Nt}\n"
+    for arr in (w.x, w.beta, w.xr, sigma.ravel(), ubar.ravel()):
+        text += " ".join(repr(float(v)) for v in arr) + "\n"
+    r = subprocess.run([harness], input=text, capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
+    return np.array([float(v) for v in r.stdout.split()[1:]])
+
+
+def _layout(bc, seed, M, p, dt, Nt, block):
+    rng = np.random.default_rng(seed)
+    x = np.sort(rng.uniform(-0.8, 0.8, M))
+    for i in range(1, block):                       # a block of `block` springs closer than dt
+        x[2 + i] = x[2] + 0.4 * dt * i
+    x = np.sort(x)
+    beta = rng.uniform(1.0, 6.0, M)
+    xr = np.array([-0.95, 0.1, x[M // 2], 0.95])    # one receiver on a spring (m = 0 terms)
+    return W.Workload(name="adjoint", bc=bc, x=x, beta=beta, amp=np.array([1.0]), center=np.array([-1.6]),
+                      width=np.array([0.12]), dt=dt, Nt=Nt, tol=1e-10, p=p, xr=xr, seed=seed)
+
+
+@pytest.mark.parametrize("bc,p,block", [(W.PERIODIC, 6, 2), (W.FREE, 6, 2), (W.PERIODIC, 8, 3),
+                                        (W.FREE, 4, 4)])
+def test_adjoint_bodies_match_the_oracle_gradient(harness, bc, p, block):
+    w = _layout(bc, seed=11 + p + block, M=10, p=p, dt=0.02, Nt=400, block=block)
+    sigma, u = wfp.from_workload(w).run(w.Nt)
+    t = np.arange(w.Nt + 1)[:, None] * w.dt
+    d = 0.3 * np.sin(3.0 * t + w.xr[None, :])
+    ubar = u[1:] - d[1:]
+    o = wfp.from_workload(w)
+    if bc == W.FREE:
+        assert w.Nt >= 2 * o.P.rbc_period                 # several projections inside the march
+    _, g_oracle = adjoint.misfit_and_gradient(o, w.Nt, d)
+    g = _run(harness, w, sigma[1:], ubar)
+    assert np.max(np.abs(g - g_oracle)) <= 1e-12 * np.max(np.abs(g_oracle)), (g, g_oracle)
