@@ -62,7 +62,9 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join("/tmp", f"wave1d_clocks_{os.getpid()}.csv")
+        out_dir = os.path.join(ROOT, "paper_2507_07823_gb300", "_build")      # git-ignored
+        os.makedirs(out_dir, exist_ok=True)
+        self.path = os.path.join(out_dir, f"clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -111,6 +113,10 @@ class ClockSampler:
         if sm:
             out.update(sm_mhz=float(np.median(sm)), sm_max_mhz=float(max(mx)), samples=len(sm))
         out["reasons"] = sorted(reasons)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
         return out
 
 
@@ -490,6 +496,53 @@ def run_spread_interp_only(args):
                                                                      reps=args.spread_interp_reps)}))
 
 
+def run_adjoint_only(args):
+    """Forward march and reverse-time march (wave1d_adjoint) on the adjoint workload (free space,
+    M = 1e5, dt = 1e-3, 8 receivers) over args.adjoint_steps steps; one JSON line with both
+    rates.  Not part of the default benchmark line."""
+    import torch
+
+    from paper_2507_07823_gb300 import build, wave1d, workloads
+
+    build.build()
+    nsteps = args.adjoint_steps
+    w = workloads.config4(Nt=nsteps)
+    t0 = time.perf_counter()
+    plan = wave1d.Plan.from_workload(w, max_local_bytes=64 << 30)
+    t_plan = time.perf_counter() - t0
+    rng = np.random.default_rng(w.seed)
+    d = torch.from_numpy(0.01 * rng.standard_normal((nsteps, len(w.xr)))).cuda()
+    stream = torch.cuda.current_stream()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e[0].record(stream)
+    sigma, u = plan.solve_device(nsteps)
+    e[1].record(stream)
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    ubar = u - d
+    t0 = time.perf_counter()
+    e[2].record(stream)
+    g = plan.adjoint(sigma, ubar)
+    e[3].record(stream)
+    torch.cuda.synchronize()
+    t_adj = time.perf_counter() - t0
+    ms_fwd, ms_adj = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
+    info = plan.info
+    line = {"metric": "scatterer-steps/s of the reverse-time march (dL/dbeta)", "unit": "scatterer-steps/s",
+            "adjoint_value": w.M * nsteps / (ms_adj * 1e-3), "forward_value": w.M * nsteps / (ms_fwd * 1e-3),
+            "adjoint_ms_per_step": ms_adj / nsteps, "forward_ms_per_step": ms_fwd / nsteps,
+            "adjoint_wall_s": t_adj, "forward_wall_s": t_fwd, "plan_seconds": t_plan,
+            "grad_norm": float(torch.linalg.vector_norm(g)), "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{w.name}: {w.description}", "M": w.M, "steps": nsteps, "K": info.K,
+                       "W": info.W, "local_weights": info.local_weights, "R": len(w.xr),
+                       "timed": "one wave1d_solve of all steps (densities recorded on the device), then one "
+                                "wave1d_adjoint call (its work arrays and NUFFT plan included)"}}
+    plan.close()
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -503,9 +556,14 @@ def main():
     ap.add_argument("--spread-interp-only", action="store_true",
                     help="only the M = 1e6 spreading / interpolation timings (not a benchmark line)")
     ap.add_argument("--spread-interp-reps", type=int, default=20)
+    ap.add_argument("--adjoint-only", action="store_true",
+                    help="only the forward and reverse-time march on the adjoint workload (not a benchmark line)")
+    ap.add_argument("--adjoint-steps", type=int, default=200)
     args = ap.parse_args()
     if args.spread_interp_only:
         run_spread_interp_only(args)
+    elif args.adjoint_only:
+        run_adjoint_only(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
