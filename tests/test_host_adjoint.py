@@ -67,3 +67,37 @@ def test_adjoint_bodies_match_the_oracle_gradient(harness, bc, p, block):
     _, g_oracle = adjoint.misfit_and_gradient(o, w.Nt, d)
     g = _run(harness, w, sigma[1:], ubar)
     assert np.max(np.abs(g - g_oracle)) <= 1e-12 * np.max(np.abs(g_oracle)), (g, g_oracle)
+
+
+PI = np.pi
+EDGE_LAYOUTS = {
+    # a pair closer than dt across the periodic seam, a receiver on the seam
+    "seam_pair": (W.PERIODIC, [-PI + 0.003, -0.5, 0.1, 0.4, 1.0, PI - 0.004], 6, [PI - 0.001, 0.2, -PI + 0.01], 300),
+    # springs at one position (distance 0 between distinct springs), a receiver on them
+    "duplicates": (W.FREE, [-0.5, -0.2, -0.2, -0.19, 0.3, 0.7], 6, [-0.2, 0.5], 300),
+    # a chain of six springs 0.9 dt apart: one block of six
+    "chain": (W.FREE, list(-0.3 + 0.018 * np.arange(6)) + [0.5, 0.9], 8, [-0.95, 0.1, 0.95], 300),
+    # springs dt apart: pair distances on the near / far switch within rounding
+    "spacing_dt": (W.FREE, list(-0.4 + 0.02 * np.arange(8)), 4, [-0.95, 0.1, 0.95], 300),
+    # thirty springs filling the periodic box
+    "periodic_dense": (W.PERIODIC, list(np.sort(np.random.default_rng(4).uniform(-PI, PI, 30))), 8,
+                       [-0.95, 0.1, 0.95], 200),
+}
+
+
+@pytest.mark.parametrize("name", sorted(EDGE_LAYOUTS))
+def test_adjoint_bodies_on_edge_layouts(harness, name):
+    """The same comparison on layouts whose tables have edge cases: implicit blocks across the
+    periodic seam, coincident springs, a long chain, distances on the near / far switch."""
+    bc, x, p, xr, Nt = EDGE_LAYOUTS[name]
+    x = np.array(x, dtype=np.float64)
+    beta = np.random.default_rng(1).uniform(1.0, 6.0, x.size)
+    w = W.Workload(name=name, bc=bc, x=x, beta=beta, amp=np.array([1.0]), center=np.array([-1.6]),
+                   width=np.array([0.12]), dt=0.02, Nt=Nt, tol=1e-10, p=p, xr=np.array(xr, dtype=np.float64),
+                   seed=1)
+    sigma, u = wfp.from_workload(w).run(w.Nt)
+    t = np.arange(w.Nt + 1)[:, None] * w.dt
+    d = 0.3 * np.sin(3.0 * t + w.xr[None, :])
+    _, g_oracle = adjoint.misfit_and_gradient(wfp.from_workload(w), w.Nt, d)
+    g = _run(harness, w, sigma[1:], u[1:] - d[1:])
+    assert np.max(np.abs(g - g_oracle)) <= 1e-12 * np.max(np.abs(g_oracle)), (g, g_oracle)
