@@ -6,8 +6,8 @@
 //   sb   ring of m_max + 1 slots x M: sigmabar^q in slot q mod (m_max + 1)
 //   Sb   ring of W slots x (K + 1) complex: Sbar^q in slot q mod W
 //   ab, apb  alphabar, alpha'bar (K + 1 complex)
-// Contributions to sb from different targets or receivers meet at the same source, so they are
-// added with atomics (the gradient is then reproducible to rounding, not bit for bit).
+// Every launch has one writer per output element and sums in a fixed order: no atomics, and the
+// gradient is the same bit for bit from run to run.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -17,34 +17,15 @@
 
 namespace wave1d {
 
-// receivers: warps [0, r_nitems) take one receiver item each (m >= 1 slices), warps
-// [r_nitems, r_nitems + R) the m = 0 terms of one receiver (sources closer than dt).  The row of
-// an item is found in r_item_ptr (R + 1 offsets) by bisection.
-__global__ void k_adj_receivers(DevPlan P, int64_t n, const double* __restrict__ ubar, double* sb) {
-    const int lane = threadIdx.x & 31;
-    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t q = n + 1;
-    if (gw < P.r_nitems) {
-        int64_t lo = 0, hi = P.R;                   // r_item_ptr[lo] <= gw < r_item_ptr[hi]
-        while (hi - lo > 1) {
-            const int64_t mid = (lo + hi) >> 1;
-            if (P.r_item_ptr[mid] <= gw) lo = mid;
-            else hi = mid;
-        }
-        const double coef = 0.5 * ubar[lo];
-        if (coef == 0.0) return;
-        const int src = P.r_src[gw * 32 + lane];
-        adj::item_lane_T(P.r_w, P.r_wbase[gw], P.r_s0[gw], P.r_len[gw], lane, src, P.r_mfirst, coef, q,
-                         P.ring, [&](int s, int j, double v) { atomicAdd(sb + (int64_t)s * P.M + j, v); });
-    } else if (gw < P.r_nitems + P.R) {
-        const int64_t r = gw - P.r_nitems;
-        const double coef = 0.5 * ubar[r];
-        double* s1 = sb + (int64_t)adj::slot(q, P.ring) * P.M;
-        for (int e = lane; e < P.r0_stride; e += 32) {
-            const double w = P.r0p_w[r * P.r0_stride + e];
-            if (w != 0.0) atomicAdd(s1 + P.r0p_src[r * P.r0_stride + e], w * coef);
-        }
-    }
+// receivers' transposed readout, one thread per source over the receiver weights regrouped by
+// source (m >= 0: the m = 0 terms of sources closer than dt included)
+__global__ void k_adj_receivers(int64_t M, int ring, int64_t n, const int64_t* __restrict__ ptr,
+                                const int32_t* __restrict__ rcv, const int32_t* __restrict__ mrange,
+                                const int64_t* __restrict__ woff, const double* __restrict__ w,
+                                const double* __restrict__ ubar, double* sb) {
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < M; l += (int64_t)gridDim.x * blockDim.x)
+        adj::receivers_T_source(l, ptr, rcv, mrange, woff, w, ubar, n + 1, ring,
+                                [&](int s, double v) { sb[(int64_t)s * M + l] += v; });
 }
 
 // sigmabar^{n+1} is complete: move it out of its ring slot (which becomes sigma^{n-m_max}'s)
@@ -73,17 +54,35 @@ __global__ void k_adj_solve(DevPlan P, const int32_t* __restrict__ blk_of, const
     }
 }
 
-// transposed local sum of the springs: one warp per item of the step layout
+// transposed local sum of the springs, one warp per row l (the row's items read in the transposed
+// direction, Q_m being symmetric in the pair): each lane accumulates its slices into the warp's
+// shared array acc[m][lane] (row stride kAdjAccStride), then lane i sums m = i, i + 32, ... over
+// the 32 lanes in lane order and adds the result to sigmabar^{n+1-m}[l].  Dynamic shared memory:
+// warps per block x (m_max + 1) x kAdjAccStride doubles.
+constexpr int kAdjAccStride = 33;
+
 __global__ void k_adj_local(DevPlan P, int64_t n, const double* __restrict__ cbar, double* sb) {
+    extern __shared__ double adj_acc[];
     const int lane = threadIdx.x & 31;
-    const int64_t o = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (o >= P.l_nitems) return;
-    const double coef = cbar[P.l_row[o]];
-    if (coef == 0.0) return;
-    const int src = P.l_src[o * 32 + lane];
-    adj::item_lane_T(P.l_w, P.l_wbase[o], P.l_s0[o], P.l_len[o], lane, src, P.l_mfirst, coef, n + 1, P.ring,
-                     [&](int s, int j, double v) { atomicAdd(sb + (int64_t)s * P.M + j, v); });
+    const int nm = P.m_max + 1;
+    double* acc = adj_acc + (int64_t)(threadIdx.x >> 5) * nm * kAdjAccStride;
+    const int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (l >= P.M) return;                                  // the whole warp: l is the warp's row
+    for (int m = 0; m < nm; m++) acc[m * kAdjAccStride + lane] = 0.0;
+    for (int64_t it = P.l_item_ptr[l]; it < P.l_item_ptr[l + 1]; it++) {
+        const double cs = cbar[P.l_src[it * 32 + lane]];
+        adj::item_lane_gather(P.l_w, P.l_wbase[it], P.l_s0[it], P.l_len[it], lane, P.l_mfirst, cs,
+                              [&](int m, double v) { acc[m * kAdjAccStride + lane] += v; });
+    }
+    __syncwarp();
+    for (int m = lane; m < nm; m += 32) {
+        double s = 0.0;
+        for (int i = 0; i < 32; i++) s += acc[m * kAdjAccStride + i];
+        if (s != 0.0) sb[(int64_t)adj::slot(n + 1 - m, P.ring) * P.M + l] += s;
+    }
 }
+
+size_t adj_local_smem(int m_max, int warps) { return (size_t)warps * (m_max + 1) * kAdjAccStride * sizeof(double); }
 
 // out[i] = in[perm[i]] (spring order -> NUFFT point order)
 __global__ void k_adj_gather(int64_t M, const int64_t* __restrict__ perm, const double* __restrict__ in,

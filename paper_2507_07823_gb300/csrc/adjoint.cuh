@@ -40,19 +40,38 @@ WAVE1D_HD int slot(int64_t q, int ring) {
     return (int)(r < 0 ? r + ring : r);
 }
 
-// One lane of a transposed local-sum item (the LocalItems layout: lane `lane` holds source rank
-// 32 c + lane of the item's row, slice t of the item is m = mfirst + s0 + t, the weight of slice
-// t is the (hi, lo) float pair at weight index wbase + 64 (t / 2) + 2 lane + (t % 2)).  The row
-// read sigma^{q - m}; its adjoint coefficient is coef, so
-//   sigmabar^{q - m}[src] += Q_m coef   for every slice with a non-zero weight,
-// delivered as add(ring slot, src, value).
-template <class Add>
-WAVE1D_HD void item_lane_T(const float* w, int64_t wbase, int s0, int len, int lane, int src,
-                           int mfirst, double coef, int64_t q, int ring, Add add) {
+// One lane of a local-sum item of row l, read in the transposed direction.  The LocalItems
+// layout: lane `lane` holds source rank 32 c + lane of the row, slice t of the item is
+// m = mfirst + s0 + t, and the weight of slice t is the (hi, lo) float pair at weight index
+// wbase + 64 (t / 2) + 2 lane + (t % 2).  Q_m(d) depends on the pair only through its distance,
+// so row l's weight for source j is row j's weight for source l, and the transposed local sum
+// at l is
+//   sigmabar^{q - m}[l] += sum_{j in row l} Q_m(d_lj) cbar_j .
+// The lane delivers acc(m, Q_m cbar_src) for every slice with a non-zero weight; its caller owns
+// the sums of row l, so no two writers meet.
+template <class Acc>
+WAVE1D_HD void item_lane_gather(const float* w, int64_t wbase, int s0, int len, int lane, int mfirst,
+                                double cbar_src, Acc acc) {
     for (int t = 0; t < len; t++) {
         const float* e = w + 2 * (wbase + 64 * (int64_t)(t >> 1) + 2 * lane + (t & 1));
         const double wq = (double)e[0] + (double)e[1];
-        if (wq != 0.0) add(slot(q - mfirst - s0 - t, ring), src, wq * coef);
+        if (wq != 0.0) acc(mfirst + s0 + t, wq * cbar_src);
+    }
+}
+
+// The receivers' transposed readout at source l, from the receiver weights regrouped by source
+// (ReceiverColumns: entries [ptr[l], ptr[l + 1]), receiver rcv[e], m range mrange[e] = m_lo |
+// count << 16, weights w[woff[e] ..]):
+//   sigmabar^{q - m}[l] += 1/2 Q_m(d_rl) ubar_r   for m >= 0, delivered as add(ring slot, value).
+template <class Add>
+WAVE1D_HD void receivers_T_source(int64_t l, const int64_t* ptr, const int32_t* rcv, const int32_t* mrange,
+                                  const int64_t* woff, const double* w, const double* ubar, int64_t q,
+                                  int ring, Add add) {
+    for (int64_t e = ptr[l]; e < ptr[l + 1]; e++) {
+        const double coef = 0.5 * ubar[rcv[e]];
+        if (coef == 0.0) continue;
+        const int mlo = mrange[e] & 0xffff, cnt = mrange[e] >> 16;
+        for (int c = 0; c < cnt; c++) add(slot(q - mlo - c, ring), w[woff[e] + c] * coef);
     }
 }
 

@@ -14,6 +14,7 @@
 #include <string>
 #include <vector>
 
+#include "adjoint_host.h"
 #include "internal.h"
 #include "phases.cuh"
 #include "../../include/wave1d.h"
@@ -34,7 +35,10 @@ __global__ void k_solve(DevPlan P);
 __global__ void k_sigma_to_caller(DevPlan P, int64_t q, double* out);
 __global__ void k_internal_to_caller(const int32_t* perm, int64_t M, const double* in, double* out);
 __global__ void k_caller_to_internal(const int32_t* perm, int64_t M, const double* in, double* out);
-__global__ void k_adj_receivers(DevPlan P, int64_t n, const double* ubar, double* sb);
+__global__ void k_adj_receivers(int64_t M, int ring, int64_t n, const int64_t* ptr, const int32_t* rcv,
+                                const int32_t* mrange, const int64_t* woff, const double* w, const double* ubar,
+                                double* sb);
+size_t adj_local_smem(int m_max, int warps);
 __global__ void k_adj_take(int64_t M, double* slot_vals, double* out);
 __global__ void k_adj_solve(DevPlan P, const int32_t* blk_of, const double* sigbar, const double* sigma_next,
                             double* grad, double* cbar, double* uHbar);
@@ -1034,27 +1038,40 @@ int wave1d_adjoint(wave1d_plan_t p, int64_t nsteps, const double* sigma, const d
     for (size_t b = 0; b + 1 < hp.blk_ptr.size(); b++)
         for (int64_t e = hp.blk_ptr[b]; e < hp.blk_ptr[b + 1]; e++) blk_of[e] = (int32_t)b;
     const int npts = (int)hp.rbc_idx.size();
-    double *sb, *Sb, *ab, *apb, *a2, *S1, *tmp, *cbar, *uHbar, *gsum, *cnu, *unu, *xr, *uvbar;
-    int32_t* dblk;
-    int64_t* dperm;
+    ReceiverColumns rcol;
+    receiver_columns(hp.rloc, M, rcol);
+    double *sb, *Sb, *ab, *apb, *a2, *S1, *tmp, *cbar, *uHbar, *gsum, *cnu, *unu, *xr, *uvbar, *rw;
+    int32_t *dblk, *rrcv, *rmr;
+    int64_t *dperm, *rptr, *rwoff;
     if ((rc = wk.zeros(&sb, (size_t)ring * M)) || (rc = wk.zeros(&Sb, (size_t)P.W * K1 * 2)) ||
         (rc = wk.zeros(&ab, 2 * (size_t)K1)) || (rc = wk.zeros(&apb, 2 * (size_t)K1)) ||
         (rc = wk.zeros(&a2, 2 * (size_t)K1)) || (rc = wk.zeros(&S1, 2 * (size_t)K1)) ||
         (rc = wk.zeros(&tmp, (size_t)M)) || (rc = wk.zeros(&cbar, (size_t)M)) || (rc = wk.zeros(&uHbar, (size_t)M)) ||
         (rc = wk.zeros(&gsum, (size_t)M)) || (rc = wk.zeros(&cnu, (size_t)M)) || (rc = wk.zeros(&unu, (size_t)M)) ||
         (rc = wk.zeros(&uvbar, 2 * (size_t)std::max(npts, 1))) || (rc = wk.upload(hp.xr, &xr)) ||
-        (rc = wk.upload(blk_of, &dblk)) || (rc = wk.upload(nperm, &dperm)))
+        (rc = wk.upload(blk_of, &dblk)) || (rc = wk.upload(nperm, &dperm)) ||
+        (rc = wk.upload(rcol.src_ptr, &rptr)) || (rc = wk.upload(rcol.rcv, &rrcv)) ||
+        (rc = wk.upload(rcol.mrange, &rmr)) || (rc = wk.upload(rcol.woff, &rwoff)) ||
+        (rc = wk.upload(hp.rloc.w, &rw)))
         return rc;
+    // the transposed local sum: one warp per spring row, 4 warps per block
+    constexpr int kLocalWarps = 4;
+    const size_t lsmem = adj_local_smem(P.m_max, kLocalWarps);
+    if (lsmem > 227 * 1024) return fail(WAVE1D_EUNSUPPORTED, "window too long for the adjoint's local-sum accumulators");
+    if (lsmem > 48 * 1024)
+        CK(cudaFuncSetAttribute(k_adj_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem));
     const int64_t cap = (int64_t)p->sms * 8;
     const unsigned gM = blocks_for(M, 256, cap), gK = blocks_for(K1, 256, INT32_MAX);
     cudaStream_t s = p->s;
     for (int64_t n = nsteps - 1; n >= 0; n--) {
         const double* ub = R > 0 ? ubar + n * R : nullptr;
-        if (R > 0) k_adj_receivers<<<blocks_for((d.r_nitems + R) * 32, 256, INT32_MAX), 256, 0, s>>>(d, n, ub, sb);
+        if (R > 0 && !rcol.rcv.empty())
+            k_adj_receivers<<<gM, 256, 0, s>>>(M, ring, n, rptr, rrcv, rmr, rwoff, rw, ub, sb);
         k_adj_take<<<gM, 256, 0, s>>>(M, sb + (int64_t)(((n + 1) % ring)) * M, tmp);
         k_adj_solve<<<gM, 256, 0, s>>>(d, dblk, tmp, sigma + n * M, gsum, cbar, uHbar);
         if (n == 0) break;
-        if (d.l_nitems > 0) k_adj_local<<<blocks_for(d.l_nitems * 32, 256, INT32_MAX), 256, 0, s>>>(d, n, cbar, sb);
+        if (d.l_nitems > 0)
+            k_adj_local<<<blocks_for(M * 32, 32 * kLocalWarps, INT32_MAX), 32 * kLocalWarps, lsmem, s>>>(d, n, cbar, sb);
         k_adj_gather<<<gM, 256, 0, s>>>(M, dperm, uHbar, cnu);
         if ((rc = wave1d_nufft_type1(wk.nu, cnu, S1))) return fail(rc, wave1d_nufft_strerror());
         k_adj_modes_in<<<gK, 256, 0, s>>>(K, S1, xr, ub, R, ab);

@@ -8,6 +8,7 @@
 #include <numeric>
 #include <thread>
 
+#include "adjoint_host.h"
 #include "internal.h"
 #include "nufft_host.h"
 #include "../../include/wave1d.h"
@@ -982,6 +983,25 @@ int build_receivers(HostPlan& hp, const double* xr, int64_t R, std::string& err)
     }
     spread_weights(P, hp.xr, hp.rc_i0, hp.rc_ker);
     return WAVE1D_OK;
+}
+
+void receiver_columns(const LocalCSR& rloc, int64_t M, ReceiverColumns& out) {
+    const int64_t R = rloc.row_ptr.empty() ? 0 : (int64_t)rloc.row_ptr.size() - 1;
+    const int64_t n = R > 0 ? rloc.row_ptr[R] : 0;
+    out.src_ptr.assign(M + 1, 0);
+    for (int64_t e = 0; e < n; e++) out.src_ptr[rloc.src[e] + 1]++;
+    for (int64_t l = 0; l < M; l++) out.src_ptr[l + 1] += out.src_ptr[l];
+    out.rcv.assign(n, 0);
+    out.mrange.assign(n, 0);
+    out.woff.assign(n, 0);
+    std::vector<int64_t> fill(out.src_ptr.begin(), out.src_ptr.end() - 1);
+    for (int64_t r = 0; r < R; r++)                  // receivers in order: each source's list ascends in r
+        for (int64_t e = rloc.row_ptr[r]; e < rloc.row_ptr[r + 1]; e++) {
+            const int64_t f = fill[rloc.src[e]]++;
+            out.rcv[f] = (int32_t)r;
+            out.mrange[f] = rloc.mrange[e];
+            out.woff[f] = rloc.woff[e];
+        }
 }
 
 }  // namespace wave1d

@@ -5,12 +5,14 @@
 // dL/dbeta (caller order).
 // Input: M R bc dt tol p Nt, then M positions, M stiffnesses, R receiver positions, Nt x M
 // densities (row s = sigma^{s+1}, caller order) and Nt x R receiver adjoints (row s = dL/du^{s+1}).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <string>
 #include <vector>
 
 #include "adjoint.cuh"
+#include "adjoint_host.h"
 #include "internal.h"
 #include "wave1d.h"
 
@@ -77,21 +79,27 @@ int main() {
     const int npts = (int)hp.rbc_idx.size();
     std::vector<double> uvbar(2 * (size_t)std::max(npts, 1));
     const double two_pi = 6.283185307179586476925286766559;
-    auto add = [&](int s, int j, double v) { sb[(size_t)s * M + j] += v; };
+    ReceiverColumns rcol;
+    receiver_columns(hp.rloc, M, rcol);
+    for (size_t e = 0; ok && e < rcol.rcv.size(); e++) {
+        const int lo = rcol.mrange[e] & 0xffff, cnt = rcol.mrange[e] >> 16;
+        ok = rcol.rcv[e] >= 0 && rcol.rcv[e] < R && lo >= 0 && lo + cnt - 1 <= P.m_max &&
+             rcol.woff[e] + cnt <= (int64_t)hp.rloc.w.size();
+    }
+    if (!ok || (int64_t)rcol.src_ptr.size() != M + 1) {
+        std::printf("index out of bounds\n");
+        return 1;
+    }
+    const int nm = P.m_max + 1, stride = 33;
+    std::vector<double> acc((size_t)nm * stride);
 
     for (int64_t n = Nt - 1; n >= 0; n--) {
         const double* ub = ubar.data() + n * R;
-        // receivers: items (m >= 1), then the m = 0 terms
-        const LocalItems& ri = hp.ritems;
-        for (int64_t r = 0; r < R; r++)
-            for (int64_t it = ri.item_ptr[r]; it < ri.item_ptr[r + 1]; it++)
-                for (int lane = 0; lane < 32; lane++)
-                    if (0.5 * ub[r] != 0.0)
-                        adj::item_lane_T(ri.w.data(), ri.wbase[it], ri.s0[it], ri.len[it], lane, ri.src[it * 32 + lane],
-                                         ri.m_first, 0.5 * ub[r], n + 1, ring, add);
-        for (int64_t r = 0; r < R; r++)
-            for (int64_t e = hp.r0_ptr[r]; e < hp.r0_ptr[r + 1]; e++)
-                sb[(size_t)adj::slot(n + 1, ring) * M + hp.r0_src[e]] += hp.r0_w[e] * (0.5 * ub[r]);
+        // receivers: one writer per source, m >= 0
+        for (long l = 0; l < M; l++)
+            adj::receivers_T_source(l, rcol.src_ptr.data(), rcol.rcv.data(), rcol.mrange.data(), rcol.woff.data(),
+                                    hp.rloc.w.data(), ub, n + 1, ring,
+                                    [&](int s, double v) { sb[(size_t)s * M + l] += v; });
         // take sigmabar^{n+1}
         double* s1 = sb.data() + (size_t)adj::slot(n + 1, ring) * M;
         for (long j = 0; j < M; j++) { tmp[j] = s1[j]; s1[j] = 0.0; }
@@ -108,14 +116,20 @@ int main() {
             uHbar[j] = -hp.beta[j] * rb;
         }
         if (n == 0) break;
-        // transposed local sum
+        // transposed local sum: row l's items read in the transposed direction, per-m lane sums
         const LocalItems& li = hp.litems;
-        for (int64_t o = 0; o < (int64_t)li.row.size(); o++) {
-            const double coef = cbar[li.row[o]];
-            if (coef == 0.0) continue;
-            for (int lane = 0; lane < 32; lane++)
-                adj::item_lane_T(li.w.data(), li.wbase[o], li.s0[o], li.len[o], lane, li.src[o * 32 + lane],
-                                 li.m_first, coef, n + 1, ring, add);
+        for (long l = 0; l < M; l++) {
+            std::fill(acc.begin(), acc.end(), 0.0);
+            for (int64_t it = li.item_ptr[l]; it < li.item_ptr[l + 1]; it++)
+                for (int lane = 0; lane < 32; lane++)
+                    adj::item_lane_gather(li.w.data(), li.wbase[it], li.s0[it], li.len[it], lane, li.m_first,
+                                          cbar[li.src[it * 32 + lane]],
+                                          [&](int m, double v) { acc[(size_t)m * stride + lane] += v; });
+            for (int m = 0; m < nm; m++) {
+                double sm = 0.0;
+                for (int i = 0; i < 32; i++) sm += acc[(size_t)m * stride + i];
+                if (sm != 0.0) sb[(size_t)adj::slot(n + 1 - m, ring) * M + l] += sm;
+            }
         }
         // type-1 of u_Hbar (exact): S1_k = (1/2 pi) sum_j u_Hbar_j e^{i k x_j}
         for (int k = 0; k <= K; k++) {

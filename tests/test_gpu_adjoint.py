@@ -48,6 +48,20 @@ def test_gradient_matches_the_adjoint_oracle(bc):
     assert np.max(np.abs(g - g_oracle)) <= 1e-9 * np.max(np.abs(g_oracle)), (g, g_oracle)
 
 
+def test_gradient_is_bitwise_reproducible():
+    """No launch of the reverse march uses atomics: two calls give the same bits."""
+    w = _layout(W.FREE, seed=7)
+    d = torch.from_numpy(_targets(w)[1:]).cuda()
+    plan = wave1d.Plan.from_workload(w)
+    try:
+        sigma, u = plan.solve_device(w.Nt)
+        g1 = plan.adjoint(sigma, u - d)
+        g2 = plan.adjoint(sigma, u - d)
+    finally:
+        plan.close()
+    assert torch.equal(g1, g2)
+
+
 def test_autograd_wrapper_gives_the_same_gradient():
     w = _layout(W.FREE, seed=9)
     d = torch.from_numpy(_targets(w)[1:]).cuda()
