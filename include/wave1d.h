@@ -209,27 +209,32 @@ int wave1d_state_save(wave1d_plan_t plan, void* buf, size_t bytes);
 int wave1d_state_load(wave1d_plan_t plan, const void* buf, size_t bytes);
 
 /*
- * Reverse-time (adjoint) march of the discrete scheme: the gradient of a scalar loss L of the
- * receiver fields with respect to the stiffnesses, for a march of nsteps steps from n = 0 driven
- * by an incident wave (g_j = beta_j f(x_j - t), eq. gj; not a wave1d_step forcing vector).  Each
- * piece of a step is transposed in the real inner product and the steps are taken in reverse
- * order: the receiver readout (eq. localSol2), the implicit solve (eq. linearSystem, transposed
- * block inverses), the local sum (Sec. 4.1, transposed), the type-2 and type-1 NUFFTs swapped
- * (eqs. historySol1, densco), the projection of Sec. 4.4 and the mode update (eqs.
- * alphakEvolutionFormulas, hkcompdisc) transposed.  The stiffness enters a step through rhs and
- * S = diag(beta/2) Q_0, and the step's residual derivative reduces to sigma_j^{n+1} / beta_j, so
- *   grad_j = sum_n rhsbar_j^n sigma_j^{n+1} / beta_j.
- *   nsteps : steps of the forward march, 1 <= nsteps <= Nt of the plan.
- *   sigma  : device, nsteps x M, row s = sigma^{s+1} in caller order (as wave1d_solve records it).
- *   ubar   : device, nsteps x R, row s = dL/du_r(t_{s+1}) (NULL allowed when R = 0).
- *   grad   : device, M values, dL/dbeta_j in caller order (overwritten).
- * The plan's tables are read and its march state is left alone.  Every stiffness must be > 0
- * (WAVE1D_EINVAL otherwise).  Work arrays (a ring of m_max + 1 density adjoints, the adjoint S
- * ring and modes, an FP64 NUFFT plan of the springs) are allocated for the call and freed before
- * it returns.  Synchronises the plan's stream.
+ * Reverse-time (adjoint) march of the discrete scheme: the gradients of a scalar loss L of the
+ * receiver fields with respect to the stiffnesses and to the forcing, for a march of nsteps
+ * steps from n = 0.  Each piece of a step is transposed in the real inner product and the steps
+ * are taken in reverse order: the receiver readout (eq. localSol2), the implicit solve (eq.
+ * linearSystem, transposed block inverses), the local sum (Sec. 4.1, transposed), the type-2 and
+ * type-1 NUFFTs swapped (eqs. historySol1, densco), the projection of Sec. 4.4 and the mode
+ * update (eqs. alphakEvolutionFormulas, hkcompdisc) transposed.  With rhsbar the adjoint of a
+ * step's right-hand side, dL/dg^{n+1} = -rhsbar^n, and the stiffness, which enters a step through
+ * rhs and S = diag(beta/2) Q_0, gives
+ *   grad_beta_j = sum_n rhsbar_j^n sigma_j^{n+1} / beta_j                 (incident wave, eq. gj)
+ *   grad_beta_j = sum_n rhsbar_j^n (sigma_j^{n+1} + g_j^{n+1}) / beta_j   (forcing vectors g)
+ *   nsteps    : steps of the forward march, 1 <= nsteps <= Nt of the plan.
+ *   sigma     : device, nsteps x M, row s = sigma^{s+1} in caller order (as wave1d_solve records it).
+ *   g         : device, nsteps x M, row s = the forcing vector of step s + 1 given to wave1d_step
+ *               (caller order), or NULL for a march driven by the incident wave.
+ *   ubar      : device, nsteps x R, row s = dL/du_r(t_{s+1}) (NULL allowed when R = 0).
+ *   grad_beta : device, M values, dL/dbeta_j in caller order (overwritten), or NULL.
+ *   grad_g    : device, nsteps x M, row s = dL/dg^{s+1} in caller order (overwritten), or NULL.
+ * At least one of grad_beta, grad_g.  grad_beta needs every stiffness > 0 (WAVE1D_EINVAL
+ * otherwise).  The plan's tables are read and its march state is left alone.  Work arrays (a
+ * ring of m_max + 1 density adjoints, the adjoint S ring and modes, an FP64 NUFFT plan of the
+ * springs) are allocated for the call and freed before it returns.  No launch uses atomics: the
+ * results are the same bit for bit from call to call.  Synchronises the plan's stream.
  */
-int wave1d_adjoint(wave1d_plan_t plan, int64_t nsteps, const double* sigma, const double* ubar,
-                   double* grad);
+int wave1d_adjoint(wave1d_plan_t plan, int64_t nsteps, const double* sigma, const double* g,
+                   const double* ubar, double* grad_beta, double* grad_g);
 
 /*
  * Standalone NUFFTs of the history part (Sec. 3.1) on fixed points, with the time-step plan's

@@ -37,18 +37,25 @@ __global__ void k_adj_take(int64_t M, double* __restrict__ slot_vals, double* __
 }
 
 // transposed block solve, one thread per member position e of blk_members (blk_of[e] = its
-// block), then the step's gradient term and the adjoints of the local sum and of u_H:
-//   grad_j += rhsbar_j sigma_j^{n+1} / beta_j,  cbar_j = -beta_j rhsbar_j / 2,  u_Hbar_j = -beta_j rhsbar_j
+// block), then the step's gradient terms and the adjoints of the local sum and of u_H:
+//   grad_j += rhsbar_j (sigma_j^{n+1} + g_j^{n+1}) / beta_j   (g: a forcing that does not scale
+//             with beta; for the incident wave g = beta f is part of rhs and the term is
+//             rhsbar_j sigma_j^{n+1} / beta_j),
+//   gbar_j^{n+1} = -rhsbar_j,  cbar_j = -beta_j rhsbar_j / 2,  u_Hbar_j = -beta_j rhsbar_j.
+// sigma_next, g_next and gbar_next are rows in caller order; g_next, grad and gbar_next may be null.
 __global__ void k_adj_solve(DevPlan P, const int32_t* __restrict__ blk_of, const double* __restrict__ sigbar,
-                            const double* __restrict__ sigma_next, double* grad, double* cbar, double* uHbar) {
+                            const double* __restrict__ sigma_next, const double* __restrict__ g_next, double* grad,
+                            double* __restrict__ gbar_next, double* cbar, double* uHbar) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P.M; e += (int64_t)gridDim.x * blockDim.x) {
         const int b = blk_of[e];
         const int64_t m0 = P.blk_ptr[b];
         const int s = (int)(P.blk_ptr[b + 1] - m0);
         const double rb = adj::solve_T(P.inv + P.blk_inv_off[b], P.blk_members, m0, s, (int)(e - m0), sigbar);
         const int j = P.blk_members[e];
+        const int jc = P.perm[j];
         const double bj = P.beta[j];
-        grad[j] += rb * sigma_next[P.perm[j]] / bj;
+        if (grad) grad[j] += rb * (g_next ? sigma_next[jc] + g_next[jc] : sigma_next[jc]) / bj;
+        if (gbar_next) gbar_next[jc] = -rb;
         cbar[j] = -0.5 * bj * rb;
         uHbar[j] = -bj * rb;
     }

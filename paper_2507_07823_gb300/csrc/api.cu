@@ -41,7 +41,7 @@ __global__ void k_adj_receivers(int64_t M, int ring, int64_t n, const int64_t* p
 size_t adj_local_smem(int m_max, int warps);
 __global__ void k_adj_take(int64_t M, double* slot_vals, double* out);
 __global__ void k_adj_solve(DevPlan P, const int32_t* blk_of, const double* sigbar, const double* sigma_next,
-                            double* grad, double* cbar, double* uHbar);
+                            const double* g_next, double* grad, double* gbar_next, double* cbar, double* uHbar);
 __global__ void k_adj_local(DevPlan P, int64_t n, const double* cbar, double* sb);
 __global__ void k_adj_gather(int64_t M, const int64_t* perm, const double* in, double* out);
 __global__ void k_adj_scatter_add(int64_t M, const int64_t* perm, const double* in, double* acc);
@@ -1015,14 +1015,18 @@ unsigned blocks_for(int64_t threads, int per_block, int64_t cap) {
 
 extern "C" {
 
-int wave1d_adjoint(wave1d_plan_t p, int64_t nsteps, const double* sigma, const double* ubar, double* grad) {
-    if (!p || !sigma || !grad || nsteps < 1) return fail(WAVE1D_EINVAL, "need a plan, sigma, grad and nsteps >= 1");
+int wave1d_adjoint(wave1d_plan_t p, int64_t nsteps, const double* sigma, const double* g, const double* ubar,
+                   double* grad_beta, double* grad_g) {
+    if (!p || !sigma || nsteps < 1 || (!grad_beta && !grad_g))
+        return fail(WAVE1D_EINVAL, "need a plan, sigma, nsteps >= 1 and grad_beta or grad_g");
     const HostPlan& hp = p->hp;
     const Params& P = hp.P;
     if (nsteps > P.Nt) return fail(WAVE1D_EINVAL, "nsteps beyond the Nt of the plan");
     if (P.R > 0 && !ubar) return fail(WAVE1D_EINVAL, "ubar is NULL");
-    for (double b : hp.beta)
-        if (!(b > 0.0)) return fail(WAVE1D_EINVAL, "the adjoint needs every stiffness > 0 (its gradient term is sigma_j / beta_j)");
+    if (grad_beta)
+        for (double b : hp.beta)
+            if (!(b > 0.0))
+                return fail(WAVE1D_EINVAL, "dL/dbeta needs every stiffness > 0 (its gradient term divides by beta_j)");
     int rc = enter(p);
     if (rc) return rc;
     const int64_t M = P.M, R = P.R;
@@ -1068,7 +1072,8 @@ int wave1d_adjoint(wave1d_plan_t p, int64_t nsteps, const double* sigma, const d
         if (R > 0 && !rcol.rcv.empty())
             k_adj_receivers<<<gM, 256, 0, s>>>(M, ring, n, rptr, rrcv, rmr, rwoff, rw, ub, sb);
         k_adj_take<<<gM, 256, 0, s>>>(M, sb + (int64_t)(((n + 1) % ring)) * M, tmp);
-        k_adj_solve<<<gM, 256, 0, s>>>(d, dblk, tmp, sigma + n * M, gsum, cbar, uHbar);
+        k_adj_solve<<<gM, 256, 0, s>>>(d, dblk, tmp, sigma + n * M, g ? g + n * M : nullptr, grad_beta ? gsum : nullptr,
+                                       grad_g ? grad_g + n * M : nullptr, cbar, uHbar);
         if (n == 0) break;
         if (d.l_nitems > 0)
             k_adj_local<<<blocks_for(M * 32, 32 * kLocalWarps, INT32_MAX), 32 * kLocalWarps, lsmem, s>>>(d, n, cbar, sb);
@@ -1085,7 +1090,7 @@ int wave1d_adjoint(wave1d_plan_t p, int64_t nsteps, const double* sigma, const d
         k_adj_scatter_add<<<gM, 256, 0, s>>>(M, dperm, unu, sb + (int64_t)(n % ring) * M);
         CK(cudaGetLastError());
     }
-    k_internal_to_caller<<<gM, 256, 0, s>>>(d.perm, M, gsum, grad);
+    if (grad_beta) k_internal_to_caller<<<gM, 256, 0, s>>>(d.perm, M, gsum, grad_beta);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(s));
     return leave(p);

@@ -116,7 +116,7 @@ def lib(path: str = LIB_PATH):
         for nm in ("wave1d_nufft_spread", "wave1d_nufft_interp", "wave1d_nufft_type1", "wave1d_nufft_type2"):
             getattr(L, nm).argtypes = [P, _D, _D]
         L.wave1d_nufft_destroy.argtypes = [P]
-        L.wave1d_adjoint.argtypes = [P, ctypes.c_int64, _D, _D, _D]
+        L.wave1d_adjoint.argtypes = [P, ctypes.c_int64, _D, _D, _D, _D, _D]
         L.wave1d_nufft_strerror.argtypes = []
         L.wave1d_nufft_strerror.restype = ctypes.c_char_p
         L.wave1d_strerror.argtypes = [ctypes.c_int]
@@ -187,10 +187,12 @@ def wave1d_solve(plan, nsteps, u_rec, sigma, out_on_device):
                               f(sigma) if sigma is not None else None, int(out_on_device))
 
 
-def wave1d_adjoint(plan, nsteps, sigma, ubar, grad):
-    """sigma (nsteps x M), ubar (nsteps x R, or None when R = 0), grad (M): device tensors."""
-    return lib().wave1d_adjoint(plan, int(nsteps), _dptr(sigma), _dptr(ubar) if ubar is not None else None,
-                                _dptr(grad))
+def wave1d_adjoint(plan, nsteps, sigma, g, ubar, grad_beta, grad_g):
+    """sigma, g (nsteps x M), ubar (nsteps x R), grad_beta (M), grad_g (nsteps x M): device tensors;
+    g, ubar (when R = 0), grad_beta and grad_g may be None."""
+    def opt(t):
+        return _dptr(t) if t is not None else None
+    return lib().wave1d_adjoint(plan, int(nsteps), _dptr(sigma), opt(g), opt(ubar), opt(grad_beta), opt(grad_g))
 
 
 class Nufft:
@@ -356,14 +358,19 @@ class Plan:
         _check(wave1d_solve(self.h, nsteps, u if self.R else None, s, 1), "wave1d_solve")
         return s, u[:, :self.R]
 
-    def adjoint(self, sigma, ubar):
+    def adjoint(self, sigma, ubar, g=None, forcing_gradient=False):
         """dL/dbeta (torch CUDA tensor, caller order) from the march's densities sigma (nsteps x M)
-        and the receiver adjoints ubar = dL/du (nsteps x R), both torch CUDA tensors."""
+        and the receiver adjoints ubar = dL/du (nsteps x R), both torch CUDA tensors.  g: the
+        forcing vectors of a march driven by `step(g)` (nsteps x M), None for the incident wave.
+        With forcing_gradient=True, returns (dL/dbeta, dL/dg) with dL/dg of shape nsteps x M."""
         import torch
-        g = torch.empty(self.M, dtype=torch.float64, device=sigma.device)
+        n = sigma.shape[0]
+        gb = torch.empty(self.M, dtype=torch.float64, device=sigma.device)
+        gg = torch.empty((n, self.M), dtype=torch.float64, device=sigma.device) if forcing_gradient else None
         ub = ubar.contiguous() if self.R else None
-        _check(wave1d_adjoint(self.h, sigma.shape[0], sigma.contiguous(), ub, g), "wave1d_adjoint")
-        return g
+        gin = g.contiguous() if g is not None else None
+        _check(wave1d_adjoint(self.h, n, sigma.contiguous(), gin, ub, gb, gg), "wave1d_adjoint")
+        return (gb, gg) if forcing_gradient else gb
 
     def step(self, g=None):
         _check(wave1d_step(self.h, g, 0), "wave1d_step")

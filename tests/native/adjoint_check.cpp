@@ -1,10 +1,11 @@
 // Host-side check of the reverse-time (adjoint) step (no GPU).  Builds the plan tables for a
 // layout read from stdin and runs the bodies the adjoint kernels run (adjoint.cuh) over them, one
 // element at a time, in the kernels' launch order; the two transforms of the reverse step are
-// exact Fourier sums here (the library uses its NUFFT plan).  Prints "ok" and the gradient
-// dL/dbeta (caller order).
-// Input: M R bc dt tol p Nt, then M positions, M stiffnesses, R receiver positions, Nt x M
-// densities (row s = sigma^{s+1}, caller order) and Nt x R receiver adjoints (row s = dL/du^{s+1}).
+// exact Fourier sums here (the library uses its NUFFT plan).  Prints "ok", the gradient dL/dbeta
+// (caller order) and, for a march driven by forcing vectors, dL/dg (Nt x M, caller order).
+// Input: M R bc dt tol p Nt has_g, then M positions, M stiffnesses, R receiver positions, Nt x M
+// densities (row s = sigma^{s+1}, caller order), Nt x R receiver adjoints (row s = dL/du^{s+1})
+// and, if has_g, Nt x M forcing vectors (row s = g^{s+1}, caller order).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -20,15 +21,17 @@ using namespace wave1d;
 
 int main() {
     long M, R, Nt;
-    int bc, p;
+    int bc, p, has_g;
     double dt, tol;
-    if (std::scanf("%ld %ld %d %lf %lf %d %ld", &M, &R, &bc, &dt, &tol, &p, &Nt) != 7) return 2;
-    std::vector<double> x(M), beta(M), xr(R), sig((size_t)Nt * M), ubar((size_t)Nt * R);
+    if (std::scanf("%ld %ld %d %lf %lf %d %ld %d", &M, &R, &bc, &dt, &tol, &p, &Nt, &has_g) != 8) return 2;
+    std::vector<double> x(M), beta(M), xr(R), sig((size_t)Nt * M), ubar((size_t)Nt * R),
+        gin(has_g ? (size_t)Nt * M : 0), gbar(has_g ? (size_t)Nt * M : 0);
     for (auto& v : x) if (std::scanf("%lf", &v) != 1) return 2;
     for (auto& v : beta) if (std::scanf("%lf", &v) != 1) return 2;
     for (auto& v : xr) if (std::scanf("%lf", &v) != 1) return 2;
     for (auto& v : sig) if (std::scanf("%lf", &v) != 1) return 2;
     for (auto& v : ubar) if (std::scanf("%lf", &v) != 1) return 2;
+    for (auto& v : gin) if (std::scanf("%lf", &v) != 1) return 2;
     HostPlan hp;
     std::string err;
     int rc = build_host_plan(x.data(), beta.data(), M, bc, dt, Nt, tol, p, 0.5, 0, 0, 32, 0, 0, 4096,
@@ -111,7 +114,10 @@ int main() {
             const double rb = adj::solve_T(hp.inv.data() + hp.blk_inv_off[b], hp.blk_members.data(), m0, s,
                                            (int)(e - m0), tmp.data());
             const int j = hp.blk_members[e];
-            grad[j] += rb * sig[(size_t)n * M + hp.perm[j]] / hp.beta[j];
+            const int jc = hp.perm[j];
+            const double term = has_g ? sig[(size_t)n * M + jc] + gin[(size_t)n * M + jc] : sig[(size_t)n * M + jc];
+            grad[j] += rb * term / hp.beta[j];
+            if (has_g) gbar[(size_t)n * M + jc] = -rb;
             cbar[j] = -0.5 * hp.beta[j] * rb;
             uHbar[j] = -hp.beta[j] * rb;
         }
@@ -164,6 +170,7 @@ int main() {
     for (long j = 0; j < M; j++) out[hp.perm[j]] = grad[j];
     std::printf("ok");
     for (long j = 0; j < M; j++) std::printf(" %.17g", out[j]);
+    for (double v : gbar) std::printf(" %.17g", v);
     std::printf("\n");
     return 0;
 }

@@ -90,4 +90,4 @@ def test_nufft_argument_validation_without_gpu(lib):
 def test_adjoint_argument_validation_without_gpu(lib):
     """wave1d_adjoint refuses a missing plan before touching any device memory."""
     L = wave1d.lib()
-    assert L.wave1d_adjoint(None, 1, None, None, None) == wave1d.WAVE1D_EINVAL
+    assert L.wave1d_adjoint(None, 1, None, None, None, None, None) == wave1d.WAVE1D_EINVAL

@@ -1,7 +1,8 @@
 """GPU reverse-time march (wave1d_adjoint): dL/dbeta of a receiver misfit against the adjoint
 oracle (oracle/adjoint.py) at 1e-9 of the largest component, the same gradient through the
-torch.autograd wrapper, and central differences of the GPU forward march on a larger free-space
-layout (several projections, hundreds of springs).
+torch.autograd wrapper, dL/dbeta and dL/dg of a march driven by forcing vectors, bitwise
+reproducibility, and central differences of the GPU forward march on a larger free-space layout
+(several projections, hundreds of springs).
 
 The kernels' bodies are checked on the CPU against the same oracle by tests/test_host_adjoint.py;
 these tests are their first run on a GPU and stay skipped until that run has been made."""
@@ -60,6 +61,29 @@ def test_gradient_is_bitwise_reproducible():
     finally:
         plan.close()
     assert torch.equal(g1, g2)
+
+
+def test_forcing_vector_march_gradients_match_the_oracle():
+    """A march driven by forcing vectors (wave1d_step(g)): dL/dbeta and dL/dg against the oracle."""
+    w = _layout(W.PERIODIC, seed=13)
+    rng = np.random.default_rng(6)
+    g = 0.2 * rng.standard_normal((w.Nt + 1, w.M))
+    d = _targets(w)
+    plan = wave1d.Plan(w.x, w.beta, w.bc, w.dt, w.Nt, w.tol, (), (), (), w.xr, p=w.p)
+    try:
+        sig, u = np.zeros((w.Nt, w.M)), np.zeros((w.Nt, len(w.xr)))
+        for n in range(w.Nt):
+            plan.step(np.ascontiguousarray(g[n + 1]))
+            sig[n], u[n] = plan.sigma(), plan.receivers()
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()   # noqa: E731
+        gb, gg = plan.adjoint(dev(sig), dev(u - d[1:]), g=dev(g[1:]), forcing_gradient=True)
+    finally:
+        plan.close()
+    _, gb_oracle = adjoint.misfit_and_gradient(wfp.from_workload(w), w.Nt, d, g=g)
+    gg_oracle = adjoint.forcing_gradient(wfp.from_workload(w), w.Nt, d, g)[1:]
+    gb, gg = gb.cpu().numpy(), gg.cpu().numpy()
+    assert np.max(np.abs(gb - gb_oracle)) <= 1e-9 * np.max(np.abs(gb_oracle))
+    assert np.max(np.abs(gg - gg_oracle)) <= 1e-9 * np.max(np.abs(gg_oracle))
 
 
 def test_autograd_wrapper_gives_the_same_gradient():

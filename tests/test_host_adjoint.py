@@ -32,13 +32,19 @@ def harness():
     return out
 
 
-def _run(harness, w, sigma, ubar):
-    text = f"{w.M} {len(w.xr)} {w.bc} {w.dt!r} {w.tol!r} {w.p} {w.Nt}\n"
-    for arr in (w.x, w.beta, w.xr, sigma.ravel(), ubar.ravel()):
+def _run(harness, w, sigma, ubar, g=None):
+    """dL/dbeta (and dL/dg, Nt x M, when the march is driven by forcing vectors g) from the
+    harness; sigma, ubar and g hold rows 1 .. Nt."""
+    text = f"{w.M} {len(w.xr)} {w.bc} {w.dt!r} {w.tol!r} {w.p} {w.Nt} {int(g is not None)}\n"
+    arrays = (w.x, w.beta, w.xr, sigma.ravel(), ubar.ravel()) + ((g.ravel(),) if g is not None else ())
+    for arr in arrays:
         text += " ".join(repr(float(v)) for v in arr) + "\n"
     r = subprocess.run([harness], input=text, capture_output=True, text=True)
     assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
-    return np.array([float(v) for v in r.stdout.split()[1:]])
+    out = np.array([float(v) for v in r.stdout.split()[1:]])
+    if g is None:
+        return out
+    return out[:w.M], out[w.M:].reshape(w.Nt, w.M)
 
 
 def _layout(bc, seed, M, p, dt, Nt, block):
@@ -101,3 +107,20 @@ def test_adjoint_bodies_on_edge_layouts(harness, name):
     _, g_oracle = adjoint.misfit_and_gradient(wfp.from_workload(w), w.Nt, d)
     g = _run(harness, w, sigma[1:], u[1:] - d[1:])
     assert np.max(np.abs(g - g_oracle)) <= 1e-12 * np.max(np.abs(g_oracle)), (g, g_oracle)
+
+
+@pytest.mark.parametrize("bc", [W.PERIODIC, W.FREE])
+def test_adjoint_bodies_with_forcing_vectors(harness, bc):
+    """A march driven by forcing vectors g (not scaled by beta): dL/dbeta with the term
+    (sigma_j + g_j) / beta_j and dL/dg = -rhsbar against the adjoint oracle."""
+    w = _layout(bc, seed=21, M=10, p=6, dt=0.02, Nt=300, block=2)
+    rng = np.random.default_rng(5)
+    g = 0.2 * rng.standard_normal((w.Nt + 1, w.M))
+    sigma, u = wfp.from_workload(w).run(w.Nt, g)
+    t = np.arange(w.Nt + 1)[:, None] * w.dt
+    d = 0.3 * np.sin(3.0 * t + w.xr[None, :])
+    _, gb_oracle = adjoint.misfit_and_gradient(wfp.from_workload(w), w.Nt, d, g=g)
+    gg_oracle = adjoint.forcing_gradient(wfp.from_workload(w), w.Nt, d, g)
+    gb, gg = _run(harness, w, sigma[1:], u[1:] - d[1:], g[1:])
+    assert np.max(np.abs(gb - gb_oracle)) <= 1e-12 * np.max(np.abs(gb_oracle)), (gb, gb_oracle)
+    assert np.max(np.abs(gg - gg_oracle[1:])) <= 1e-12 * np.max(np.abs(gg_oracle[1:]))
