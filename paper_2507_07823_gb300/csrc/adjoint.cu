@@ -62,34 +62,39 @@ __global__ void k_adj_solve(DevPlan P, const int32_t* __restrict__ blk_of, const
 }
 
 // transposed local sum of the springs, one warp per row l (the row's items read in the transposed
-// direction, Q_m being symmetric in the pair): each lane accumulates its slices into the warp's
-// shared array acc[m][lane] (row stride kAdjAccStride), then lane i sums m = i, i + 32, ... over
-// the 32 lanes in lane order and adds the result to sigmabar^{n+1-m}[l].  Dynamic shared memory:
-// warps per block x (m_max + 1) x kAdjAccStride doubles.
+// direction, Q_m being symmetric in the pair), in the compensated FP32 arithmetic of the forward
+// local sum: each lane accumulates its slices into the warp's shared pairs acc[m][lane] (row
+// stride kAdjAccStride), then lane i adds m = i, i + 32, ... over the 32 lanes in lane order (in
+// FP64) and adds the result to sigmabar^{n+1-m}[l].  Dynamic shared memory: warps per block x
+// (m_max + 1) x kAdjAccStride float pairs.
 constexpr int kAdjAccStride = 33;
 
 __global__ void k_adj_local(DevPlan P, int64_t n, const double* __restrict__ cbar, double* sb) {
-    extern __shared__ double adj_acc[];
+    extern __shared__ float2 adj_acc[];
     const int lane = threadIdx.x & 31;
     const int nm = P.m_max + 1;
-    double* acc = adj_acc + (int64_t)(threadIdx.x >> 5) * nm * kAdjAccStride;
+    float2* acc = adj_acc + (int64_t)(threadIdx.x >> 5) * nm * kAdjAccStride;
     const int64_t l = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (l >= P.M) return;                                  // the whole warp: l is the warp's row
-    for (int m = 0; m < nm; m++) acc[m * kAdjAccStride + lane] = 0.0;
+    for (int m = 0; m < nm; m++) acc[m * kAdjAccStride + lane] = make_float2(0.f, 0.f);
     for (int64_t it = P.l_item_ptr[l]; it < P.l_item_ptr[l + 1]; it++) {
-        const double cs = cbar[P.l_src[it * 32 + lane]];
-        adj::item_lane_gather(P.l_w, P.l_wbase[it], P.l_s0[it], P.l_len[it], lane, P.l_mfirst, cs,
-                              [&](int m, double v) { acc[m * kAdjAccStride + lane] += v; });
+        float ch, cl;
+        adj::split_pair(cbar[P.l_src[it * 32 + lane]], ch, cl);
+        adj::item_lane_gather(P.l_w, P.l_wbase[it], P.l_s0[it], P.l_len[it], lane, P.l_mfirst, ch, cl,
+                              [&](int m) { return (float*)(acc + m * kAdjAccStride + lane); });
     }
     __syncwarp();
     for (int m = lane; m < nm; m += 32) {
         double s = 0.0;
-        for (int i = 0; i < 32; i++) s += acc[m * kAdjAccStride + i];
+        for (int i = 0; i < 32; i++) {
+            const float2 a = acc[m * kAdjAccStride + i];
+            s += (double)a.x + (double)a.y;
+        }
         if (s != 0.0) sb[(int64_t)adj::slot(n + 1 - m, P.ring) * P.M + l] += s;
     }
 }
 
-size_t adj_local_smem(int m_max, int warps) { return (size_t)warps * (m_max + 1) * kAdjAccStride * sizeof(double); }
+size_t adj_local_smem(int m_max, int warps) { return (size_t)warps * (m_max + 1) * kAdjAccStride * sizeof(float2); }
 
 // out[i] = in[perm[i]] (spring order -> NUFFT point order)
 __global__ void k_adj_gather(int64_t M, const int64_t* __restrict__ perm, const double* __restrict__ in,

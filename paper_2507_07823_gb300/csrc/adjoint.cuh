@@ -34,6 +34,35 @@
 namespace wave1d {
 namespace adj {
 
+// FP32 operations rounded to nearest without contraction or reassociation (rounding intrinsics on
+// the GPU; on the host, ISO C++ float arithmetic, which compilers do not contract by default)
+#ifdef __CUDA_ARCH__
+WAVE1D_HD float f_add(float a, float b) { return __fadd_rn(a, b); }
+WAVE1D_HD float f_sub(float a, float b) { return __fsub_rn(a, b); }
+WAVE1D_HD float f_mul(float a, float b) { return __fmul_rn(a, b); }
+WAVE1D_HD float f_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+#else
+WAVE1D_HD float f_add(float a, float b) { return a + b; }
+WAVE1D_HD float f_sub(float a, float b) { return a - b; }
+WAVE1D_HD float f_mul(float a, float b) { return a * b; }
+WAVE1D_HD float f_fma(float a, float b, float c) { return std::fma(a, b, c); }
+#endif
+
+// Compensated FP32 pairs: a value is hi + lo with |lo| <= ulp(hi)/2.  (sh, sl) += (wh + wl)(vh + vl)
+// with the product's rounding error recovered by fused multiply-adds and the sum's by a two-sum
+// (Knuth), dropping wl vl (relative 2^-48): the arithmetic of the forward local sum.
+WAVE1D_HD void pair_mac(float& sh, float& sl, float wh, float wl, float vh, float vl) {
+    const float p = f_mul(wh, vh);
+    float e = f_fma(wh, vh, -p);
+    e = f_fma(wh, vl, e);
+    e = f_fma(wl, vh, e);
+    const float s = f_add(sh, p);
+    const float bb = f_sub(s, sh);
+    const float t = f_add(f_sub(sh, f_sub(s, bb)), f_sub(p, bb));
+    sh = s;
+    sl = f_add(sl, f_add(t, e));
+}
+
 // slot of time index q in a ring of `ring` slots (q may be negative)
 WAVE1D_HD int slot(int64_t q, int ring) {
     int64_t r = q % ring;
@@ -47,16 +76,25 @@ WAVE1D_HD int slot(int64_t q, int ring) {
 // so row l's weight for source j is row j's weight for source l, and the transposed local sum
 // at l is
 //   sigmabar^{q - m}[l] += sum_{j in row l} Q_m(d_lj) cbar_j .
-// The lane delivers acc(m, Q_m cbar_src) for every slice with a non-zero weight; its caller owns
-// the sums of row l, so no two writers meet.
+// The lane adds Q_m (cbh + cbl) (cbar of its source as an FP32 pair) into the pair accumulator
+// acc(m) for every slice with a non-zero weight; its caller owns the sums of row l, so no two
+// writers meet.
 template <class Acc>
 WAVE1D_HD void item_lane_gather(const float* w, int64_t wbase, int s0, int len, int lane, int mfirst,
-                                double cbar_src, Acc acc) {
+                                float cbh, float cbl, Acc acc) {
     for (int t = 0; t < len; t++) {
         const float* e = w + 2 * (wbase + 64 * (int64_t)(t >> 1) + 2 * lane + (t & 1));
-        const double wq = (double)e[0] + (double)e[1];
-        if (wq != 0.0) acc(mfirst + s0 + t, wq * cbar_src);
+        if (e[0] != 0.0f) {
+            float* a = acc(mfirst + s0 + t);
+            pair_mac(a[0], a[1], e[0], e[1], cbh, cbl);
+        }
     }
+}
+
+// an FP64 value as an FP32 pair (hi = fl(v), lo = fl(v - hi))
+WAVE1D_HD void split_pair(double v, float& hi, float& lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
 }
 
 // The receivers' transposed readout at source l, from the receiver weights regrouped by source

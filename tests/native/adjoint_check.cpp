@@ -94,7 +94,7 @@ int main() {
         return 1;
     }
     const int nm = P.m_max + 1, stride = 33;
-    std::vector<double> acc((size_t)nm * stride);
+    std::vector<float> acc(2 * (size_t)nm * stride);
 
     for (int64_t n = Nt - 1; n >= 0; n--) {
         const double* ub = ubar.data() + n * R;
@@ -122,18 +122,22 @@ int main() {
             uHbar[j] = -hp.beta[j] * rb;
         }
         if (n == 0) break;
-        // transposed local sum: row l's items read in the transposed direction, per-m lane sums
+        // transposed local sum: row l's items read in the transposed direction, compensated FP32
+        // pairs per (m, lane), then FP64 lane sums in lane order
         const LocalItems& li = hp.litems;
         for (long l = 0; l < M; l++) {
-            std::fill(acc.begin(), acc.end(), 0.0);
+            std::fill(acc.begin(), acc.end(), 0.0f);
             for (int64_t it = li.item_ptr[l]; it < li.item_ptr[l + 1]; it++)
-                for (int lane = 0; lane < 32; lane++)
-                    adj::item_lane_gather(li.w.data(), li.wbase[it], li.s0[it], li.len[it], lane, li.m_first,
-                                          cbar[li.src[it * 32 + lane]],
-                                          [&](int m, double v) { acc[(size_t)m * stride + lane] += v; });
+                for (int lane = 0; lane < 32; lane++) {
+                    float ch, cl;
+                    adj::split_pair(cbar[li.src[it * 32 + lane]], ch, cl);
+                    adj::item_lane_gather(li.w.data(), li.wbase[it], li.s0[it], li.len[it], lane, li.m_first, ch, cl,
+                                          [&](int m) { return &acc[2 * ((size_t)m * stride + lane)]; });
+                }
             for (int m = 0; m < nm; m++) {
                 double sm = 0.0;
-                for (int i = 0; i < 32; i++) sm += acc[(size_t)m * stride + i];
+                for (int i = 0; i < 32; i++)
+                    sm += (double)acc[2 * ((size_t)m * stride + i)] + (double)acc[2 * ((size_t)m * stride + i) + 1];
                 if (sm != 0.0) sb[(size_t)adj::slot(n + 1 - m, ring) * M + l] += sm;
             }
         }
