@@ -562,6 +562,41 @@ def run_adjoint_only(args):
     print(json.dumps(line))
 
 
+def run_mixed_only(args):
+    """The benchmark workload marched in FP64 (the one-launch step) and in mixed precision (FP32
+    spreading and interpolation, per-stage launches) for args.steps steps each after
+    args.warmup warm-up steps: both rates and their relative difference in the densities and
+    receiver fields.  Not part of the default benchmark line."""
+    import torch
+
+    from paper_2507_07823_gb300 import build, wave1d, workloads
+
+    build.build()
+    w = workloads.config1()
+    K, Wm = args.steps, args.warmup
+    out = {}
+    fields = {}
+    for name, kw in (("fp64", {}), ("mixed", {"precision": 1})):
+        plan = wave1d.Plan.from_workload(w.with_(Nt=Wm + K), **kw)
+        s_w, u_w = plan.solve(Wm)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream = torch.cuda.current_stream()
+        e0.record(stream)
+        wave1d._check(wave1d.wave1d_solve(plan.h, K, None, None, 1), "wave1d_solve")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        fields[name] = (plan.sigma(), plan.receivers())
+        out[name] = {"value": w.M * K / (ms * 1e-3), "ms_per_step": ms / K}
+        plan.close()
+    (s64, u64), (s32, u32) = fields["fp64"], fields["mixed"]
+    out["rel_diff_sigma"] = float(np.max(np.abs(s32 - s64)) / np.max(np.abs(s64)))
+    out["rel_diff_receivers"] = float(np.max(np.abs(u32 - u64)) / np.max(np.abs(u64)))
+    print(json.dumps({"metric": METRIC, "unit": UNIT, "steps": K, "warmup": Wm, "dtype": "f64 / f32 history passes",
+                      "config": {"workload": f"{w.name}: {w.description}"}, **out}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -578,11 +613,15 @@ def main():
     ap.add_argument("--adjoint-only", action="store_true",
                     help="only the forward and reverse-time march on the adjoint workload (not a benchmark line)")
     ap.add_argument("--adjoint-steps", type=int, default=200)
+    ap.add_argument("--mixed-only", action="store_true",
+                    help="only the FP64 and mixed-precision marches of the benchmark workload (not a benchmark line)")
     args = ap.parse_args()
     if args.spread_interp_only:
         run_spread_interp_only(args)
     elif args.adjoint_only:
         run_adjoint_only(args)
+    elif args.mixed_only:
+        run_mixed_only(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -71,6 +71,11 @@ typedef struct {
     int step_kernel;    /* 1 (default): ordinary steps run as one cooperative launch (history,
                            local sum and solve in one kernel); 0: one launch per stage           */
     void* stream;       /* cudaStream_t for all work of the plan; NULL = legacy default stream   */
+    int precision;      /* 0 (default): FP64 throughout.  1: mixed, the history part's spreading
+                           and interpolation in FP32 (the FP32 NUFFT kernels, width 7, about 1e-7
+                           of the field; nufft_w must be 0 or 7), the FFTs, mode recurrence,
+                           local sum and density solve as in FP64; steps run as per-stage
+                           launches                                                              */
 } wave1d_opts;
 
 /* Derived sizes of a plan (read-only report). */

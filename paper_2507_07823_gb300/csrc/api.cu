@@ -52,6 +52,9 @@ __global__ void k_adj_rbc_update(int K, int npts, const int32_t* idx, const doub
                                  double* ab, double* apb);
 __global__ void k_adj_modes(int K, int W, int64_t n, const double* rot, const double* pq, double* ab, double* apb,
                             double* Sb, double* a2);
+__global__ void k_mx_gather(DevPlan P, const int64_t* perm, double* c);
+__global__ void k_mx_rhs(DevPlan P, const int64_t* perm, const double* u);
+__global__ void k_mx_receivers(int64_t R, const int64_t* perm, const double* u, double* uHr);
 }  // namespace wave1d
 
 using namespace wave1d;
@@ -92,6 +95,12 @@ struct wave1d_plan_s {
     cudaEvent_t prof_ev[WAVE1D_NSTAGE + 1] = {};
     double prof_ms[WAVE1D_NSTAGE] = {};
     int64_t prof_steps = 0;
+    // mixed precision (opts.precision = 1): FP32 NUFFT plans of the springs and of the receivers
+    // (same fine grid and kernel as the plan's, width 7), their point orders and work arrays
+    bool mixed = false;
+    wave1d_nufft_t nu_s = nullptr, nu_r = nullptr;
+    int64_t *nu_perm_s = nullptr, *nu_perm_r = nullptr;
+    double *nu_c = nullptr, *nu_u = nullptr, *nu_ur = nullptr;
 };
 
 namespace {
@@ -310,7 +319,16 @@ int enqueue_step(wave1d_plan_t p, int64_t n, const double* g_ext, double* sig_hi
     int l1 = ilog2(P.L1), l2 = ilog2(P.L2);
     unsigned tc = (unsigned)std::max(32, std::min(P.L1, 1024));
     mark(WAVE1D_STAGE_SPREAD);
-    k_hist_cols<<<P.L2, 256, cols_phase_smem(P.L1), s>>>(d, Y);
+    if (p->mixed) {
+        // FP32 spreading of sigma^n onto the fine grid, then the forward FFT's column pass
+        int t1 = std::max(32, std::min(P.L1 / 2, 512));
+        k_mx_gather<<<blocks(P.M, T), T, 0, s>>>(d, p->nu_perm_s, p->nu_c);
+        int rc = wave1d_nufft_spread(p->nu_s, p->nu_c, d.grid);
+        if (rc) return fail(rc, std::string("mixed spreading: ") + wave1d_nufft_strerror());
+        k_fft_cols<<<P.L2, t1, fft_smem_bytes(P.L1), s>>>((const double2*)d.grid, Y, tw, P.L, P.L1, P.L2, l1, +1);
+    } else {
+        k_hist_cols<<<P.L2, 256, cols_phase_smem(P.L1), s>>>(d, Y);
+    }
     mark(WAVE1D_STAGE_FFT_FWD);
     mark(WAVE1D_STAGE_MODES);
     k_hist_tail<<<(P.K + 1 + kTailModes - 1) / kTailModes, 8 * kTailModes, 0, s>>>(d);
@@ -332,7 +350,19 @@ int enqueue_step(wave1d_plan_t p, int64_t n, const double* g_ext, double* sig_hi
         k_hist_icols<<<P.L2, tc, icols_phase_smem(P.L1), s>>>(d, Tb);
     }
     mark(WAVE1D_STAGE_INTERP);
-    k_interp<<<blocks(P.M + P.R, kInterpPoints), 2 * kInterpPoints, 0, s>>>(d);
+    if (p->mixed) {
+        // FP32 interpolation at the springs (then u_H and the right-hand side) and at the receivers
+        int rc = wave1d_nufft_interp(p->nu_s, d.grid, p->nu_u);
+        if (rc) return fail(rc, std::string("mixed interpolation: ") + wave1d_nufft_strerror());
+        k_mx_rhs<<<blocks(P.M, T), T, 0, s>>>(d, p->nu_perm_s, p->nu_u);
+        if (P.R > 0) {
+            rc = wave1d_nufft_interp(p->nu_r, d.grid, p->nu_ur);
+            if (rc) return fail(rc, std::string("mixed interpolation: ") + wave1d_nufft_strerror());
+            k_mx_receivers<<<blocks(P.R, T), T, 0, s>>>(P.R, p->nu_perm_r, p->nu_ur, d.uHr);
+        }
+    } else {
+        k_interp<<<blocks(P.M + P.R, kInterpPoints), 2 * kInterpPoints, 0, s>>>(d);
+    }
     mark(WAVE1D_STAGE_SOLVE);
     if (fork) cudaStreamWaitEvent(s, p->ev_join, 0);
     k_solve<<<blocks((d.n_sgroups + d.n_big) * 32, T), T, 0, s>>>(d);
@@ -454,6 +484,12 @@ int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double d
     if (!(o.gamma > 0.0 && o.gamma < 1.0)) return fail(WAVE1D_EINVAL, "gamma must lie in (0, 1)");
     if (o.max_block <= 0) o.max_block = 4096;
     if (o.max_local_bytes <= 0) o.max_local_bytes = (int64_t)16 << 30;
+    if (o.precision != 0 && o.precision != 1) return fail(WAVE1D_EINVAL, "precision must be 0 (FP64) or 1 (mixed)");
+    if (o.precision == 1) {
+        if (o.nufft_w != 0 && o.nufft_w != 7) return fail(WAVE1D_EINVAL, "mixed precision uses the width-7 NUFFT kernel");
+        o.nufft_w = 7;          // the FP32 kernels' width: the plan's grid, kernel and deconvolution match them
+        o.step_kernel = 0;      // the FP32 passes run as their own launches
+    }
 
     wave1d_plan_t p = new (std::nothrow) wave1d_plan_s();
     if (!p) return fail(WAVE1D_ENOMEM, "host allocation");
@@ -613,6 +649,17 @@ int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double d
     if ((rc = dalloc(p, &p->d_gstage, (size_t)P.M))) return cleanup(rc);
     if ((rc = upload_receivers(p))) return cleanup(rc);
     d.pulse = nullptr;
+    if (o.precision == 1) {
+        p->mixed = true;
+        // tol 1e-6 gives the width-7 kernel: the same nf, kernel shape and deconvolution as the plan's
+        rc = wave1d_nufft_plan(hp.x.data(), P.M, P.K, 1e-6, 1, (void*)p->s, &p->nu_s);
+        if (rc) return cleanup(fail(rc, std::string("mixed NUFFT plan of the springs: ") + wave1d_nufft_strerror()));
+        std::vector<int64_t> perm(P.M);
+        if ((rc = wave1d_nufft_perm(p->nu_s, perm.data()))) return cleanup(fail(rc, wave1d_nufft_strerror()));
+        if ((rc = upload(p, perm, &p->nu_perm_s))) return cleanup(rc);
+        if ((rc = dalloc(p, &p->nu_c, (size_t)P.M))) return cleanup(rc);
+        if ((rc = dalloc(p, &p->nu_u, (size_t)P.M))) return cleanup(rc);
+    }
 #undef UP
     if ((rc = leave(p))) return cleanup(rc);
     if (cudaStreamSynchronize(p->s) != cudaSuccess) return cleanup(fail(WAVE1D_ECUDA, "plan upload failed"));
@@ -650,6 +697,18 @@ int wave1d_set_receivers(wave1d_plan_t p, const double* xr, int64_t R) {
     if (rc) return fail(rc, err);
     if ((rc = enter(p))) return rc;
     if ((rc = upload_receivers(p))) return rc;
+    if (p->mixed && R > 0) {
+        if (p->nu_r) {
+            wave1d_nufft_destroy(p->nu_r);
+            p->nu_r = nullptr;
+        }
+        rc = wave1d_nufft_plan(p->hp.xr.data(), R, p->hp.P.K, 1e-6, 1, (void*)p->s, &p->nu_r);
+        if (rc) return fail(rc, std::string("mixed NUFFT plan of the receivers: ") + wave1d_nufft_strerror());
+        std::vector<int64_t> perm(R);
+        if ((rc = wave1d_nufft_perm(p->nu_r, perm.data()))) return fail(rc, wave1d_nufft_strerror());
+        if ((rc = upload(p, perm, &p->nu_perm_r))) return rc;
+        if ((rc = dalloc(p, &p->nu_ur, (size_t)R))) return rc;
+    }
     drop_graphs(p);
     return leave(p);
 }
@@ -1102,6 +1161,8 @@ int wave1d_destroy(wave1d_plan_t p) {
     drop_graphs(p);
     for (int i = 0; i <= WAVE1D_NSTAGE; i++)
         if (p->prof_ev[i]) cudaEventDestroy(p->prof_ev[i]);
+    if (p->nu_s) wave1d_nufft_destroy(p->nu_s);
+    if (p->nu_r) wave1d_nufft_destroy(p->nu_r);
     for (void* a : p->allocs) cudaFree(a);
     if (p->ev_in) cudaEventDestroy(p->ev_in);
     if (p->ev_out) cudaEventDestroy(p->ev_out);

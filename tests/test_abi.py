@@ -55,6 +55,12 @@ def test_argument_validation_without_gpu(lib):
     bad = np.array([np.nan, 0.0])
     assert wave1d.wave1d_plan(bad, b, 2, 0, 0.01, 10, 1e-10)[0] == wave1d.WAVE1D_EINVAL
     assert wave1d.wave1d_plan(x, np.array([1.0, -1.0]), 2, 0, 0.01, 10, 1e-10)[0] == wave1d.WAVE1D_EINVAL
+    o = wave1d.wave1d_opts_default()
+    assert o.precision == 0                                    # FP64 by default
+    o.precision = 2
+    assert wave1d.wave1d_plan(x, b, 2, 0, 0.01, 10, 1e-10, o)[0] == wave1d.WAVE1D_EINVAL
+    o.precision, o.nufft_w = 1, 9                              # mixed runs the width-7 kernel only
+    assert wave1d.wave1d_plan(x, b, 2, 0, 0.01, 10, 1e-10, o)[0] == wave1d.WAVE1D_EINVAL
     assert wave1d.wave1d_destroy(None) == 0
 
 

@@ -1,0 +1,66 @@
+"""Mixed-precision time step (opts.precision = 1): the history part's spreading and interpolation
+through the FP32 NUFFT kernels (width 7), everything else as in FP64.  Checked against the discrete
+scheme's oracle (exact Fourier sums, FP64) over a whole march, with the error recorded along the
+march, against the FP64 plan of the same kernel width (what FP32 alone changes), with receivers,
+bit for bit from run to run, and through a projection step in free space.
+
+These tests are the path's first run on a GPU and stay skipped until that run has been made."""
+import numpy as np
+import pytest
+
+from oracle import wfp
+from paper_2507_07823_gb300 import wave1d
+from paper_2507_07823_gb300 import workloads as W
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skip(reason="first GPU run of the mixed-precision step pending")]
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+@pytest.mark.parametrize("bc", [W.PERIODIC, W.FREE])
+def test_mixed_march_against_the_oracle_along_the_march(bc):
+    w = W.config0(Nt=600) if bc == W.PERIODIC else W.config1(M=400, Nt=600, dt=0.005, margin=0.6)
+    s_ref, u_ref = wfp.from_workload(w).run(w.Nt)
+    plan = wave1d.Plan.from_workload(w, precision=1)
+    try:
+        s, u = plan.solve(w.Nt)
+    finally:
+        plan.close()
+    err = [_rel(s[: n + 1], s_ref[1: n + 2]) for n in range(99, w.Nt, 100)]
+    # the width-7 kernel's error (about 1e-7 of the field per transform) stays bounded along the march
+    assert max(err) < 1e-5, err
+    assert err[-1] < 10 * err[0] + 1e-6, err
+    if len(w.xr):
+        assert _rel(u, u_ref[1:]) < 1e-5
+
+
+def test_fp32_changes_little_beyond_the_kernel_width():
+    """The FP64 plan with the same width-7 kernel against the mixed plan: FP32 arithmetic alone."""
+    w = W.config0(Nt=400)
+    s_ref, _ = wfp.from_workload(w).run(w.Nt)
+    p64 = wave1d.Plan.from_workload(w, nufft_w=7)
+    p32 = wave1d.Plan.from_workload(w, precision=1)
+    try:
+        s64, _ = p64.solve(w.Nt)
+        s32, _ = p32.solve(w.Nt)
+    finally:
+        p64.close()
+        p32.close()
+    e64, e32, d = _rel(s64, s_ref[1:]), _rel(s32, s_ref[1:]), _rel(s32, s64)
+    assert e64 < 1e-5 and e32 < 1e-5
+    assert d < 1e-5, (e64, e32, d)
+
+
+def test_mixed_march_is_bitwise_reproducible():
+    w = W.config0(Nt=200)
+    out = []
+    for _ in range(2):
+        plan = wave1d.Plan.from_workload(w, precision=1)
+        try:
+            out.append(plan.solve(w.Nt))
+        finally:
+            plan.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
