@@ -12,7 +12,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libwave1d.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["api.cu", "kernels.cu", "history.cu", "step.cu", "nufft.cu", "nufft_noalloc.cu", "adjoint.cu", "mixed.cu"]
-CPP_SOURCES = ["plan_host.cpp"]
+CPP_SOURCES = ["plan_host.cpp", "batch_host.cpp"]
 
 
 def _nvcc():

@@ -1,0 +1,131 @@
+// Joining the tables of independent instances into one batched plan (see batch_host.h).
+#include "batch_host.h"
+
+#include <algorithm>
+
+#include "../../include/wave1d.h"
+
+namespace wave1d {
+
+namespace {
+
+// items of every instance, rows and sources moved by the instances' row / spring offsets and
+// weights by the weights before them
+void join_items(const std::vector<const LocalItems*>& parts, const std::vector<int64_t>& row_off,
+                const std::vector<int64_t>& src_off, LocalItems& out) {
+    out = LocalItems();
+    out.m_first = parts.empty() ? 1 : parts[0]->m_first;
+    out.item_ptr.assign(1, 0);
+    int64_t items = 0, weights = 0;
+    for (size_t b = 0; b < parts.size(); b++) {
+        const LocalItems& L = *parts[b];
+        const int64_t rows = (int64_t)L.item_ptr.size() - 1;
+        for (int64_t r = 0; r < rows; r++) out.item_ptr.push_back(L.item_ptr[r + 1] + items);
+        for (int32_t r : L.row) out.row.push_back((int32_t)(r + row_off[b]));
+        out.s0.insert(out.s0.end(), L.s0.begin(), L.s0.end());
+        out.len.insert(out.len.end(), L.len.begin(), L.len.end());
+        const int64_t ni = (int64_t)L.row.size();       // wbase holds ni + 1 entries: the last is the total
+        for (int64_t c = 0; c < ni; c++) out.wbase.push_back(L.wbase[c] + weights);
+        for (int32_t s : L.src) out.src.push_back((int32_t)(s + src_off[b]));
+        out.w.insert(out.w.end(), L.w.begin(), L.w.end());
+        items += ni;
+        weights += (int64_t)L.w.size() / 2;
+    }
+    out.wbase.push_back(weights);
+}
+
+}  // namespace
+
+int join_instances(const std::vector<HostPlan>& inst, BatchTables& out, std::string& err) {
+    const size_t B = inst.size();
+    if (B == 0) { err = "no instances"; return WAVE1D_EINVAL; }
+    const Params& P0 = inst[0].P;
+    for (const HostPlan& h : inst) {
+        const Params& P = h.P;
+        if (P.K != P0.K || P.W != P0.W || P.m_max != P0.m_max || P.nf != P0.nf || P.L1 != P0.L1 ||
+            P.nufft_w != P0.nufft_w || P.p != P0.p || P.ring != P0.ring || P.bc != P0.bc ||
+            h.litems.m_first != inst[0].litems.m_first || h.ritems.m_first != inst[0].ritems.m_first) {
+            err = "instances with different derived sizes";
+            return WAVE1D_EINVAL;
+        }
+    }
+    out = BatchTables();
+    HostPlan& g = out.g;
+    out.moff.assign(B + 1, 0);
+    out.roff.assign(B + 1, 0);
+    for (size_t b = 0; b < B; b++) {
+        out.moff[b + 1] = out.moff[b] + inst[b].P.M;
+        out.roff[b + 1] = out.roff[b] + inst[b].P.R;
+    }
+    const int64_t M = out.moff[B], R = out.roff[B];
+    g.P = P0;
+    g.P.M = M;
+    g.P.R = R;
+    // shared history tables
+    g.pq = inst[0].pq;
+    g.rot = inst[0].rot;
+    g.deconv1 = inst[0].deconv1;
+    g.deconv2 = inst[0].deconv2;
+    g.twiddle = inst[0].twiddle;
+    g.modefac = inst[0].modefac;
+    g.tw2K = inst[0].tw2K;
+    out.inst_of.assign(M, 0);
+    for (size_t b = 0; b < B; b++) {
+        const HostPlan& h = inst[b];
+        const int64_t mo = out.moff[b];
+        for (int64_t j = 0; j < h.P.M; j++) {
+            g.x.push_back(h.x[j]);
+            g.beta.push_back(h.beta[j]);
+            g.perm.push_back((int32_t)(h.perm[j] + mo));
+            out.inst_of[mo + j] = (int32_t)b;
+        }
+        g.xr.insert(g.xr.end(), h.xr.begin(), h.xr.end());
+    }
+    // local-sum items of the springs (rows: springs) and of the receivers (rows: receivers)
+    std::vector<const LocalItems*> lp, rp;
+    for (const HostPlan& h : inst) {
+        lp.push_back(&h.litems);
+        rp.push_back(&h.ritems);
+    }
+    join_items(lp, out.moff, out.moff, g.litems);
+    join_items(rp, out.roff, out.moff, g.ritems);
+    // receivers' m = 0 terms
+    g.r0_ptr.assign(1, 0);
+    for (size_t b = 0; b < B; b++) {
+        const HostPlan& h = inst[b];
+        const int64_t base = (int64_t)g.r0_src.size();
+        for (int64_t r = 0; r < h.P.R; r++) g.r0_ptr.push_back(h.r0_ptr[r + 1] + base);
+        for (int32_t s : h.r0_src) g.r0_src.push_back((int32_t)(s + out.moff[b]));
+        g.r0_w.insert(g.r0_w.end(), h.r0_w.begin(), h.r0_w.end());
+    }
+    // blocks of I + S, their inverses and the packed solve groups
+    g.blk_ptr.assign(1, 0);
+    std::vector<int64_t> item_off(B + 1, 0), blk_off(B + 1, 0);
+    for (size_t b = 0; b < B; b++) {
+        item_off[b + 1] = item_off[b] + (int64_t)inst[b].litems.row.size();
+        blk_off[b + 1] = blk_off[b] + (int64_t)inst[b].blk_ptr.size() - 1;
+    }
+    for (size_t b = 0; b < B; b++) {
+        const HostPlan& h = inst[b];
+        const int64_t mo = out.moff[b], io = (int64_t)g.inv.size();
+        for (size_t k = 1; k < h.blk_ptr.size(); k++) g.blk_ptr.push_back(h.blk_ptr[k] + mo);
+        for (int32_t j : h.blk_members) g.blk_members.push_back((int32_t)(j + mo));
+        const int64_t nb = (int64_t)h.blk_ptr.size() - 1;    // blk_inv_off holds nb + 1 entries (last: total)
+        for (int64_t k = 0; k < nb; k++) g.blk_inv_off.push_back(h.blk_inv_off[k] + io);
+        g.inv.insert(g.inv.end(), h.inv.begin(), h.inv.end());
+        for (int32_t j : h.sg_j) g.sg_j.push_back(j >= 0 ? (int32_t)(j + mo) : j);
+        g.sg_meta.insert(g.sg_meta.end(), h.sg_meta.begin(), h.sg_meta.end());
+        for (int64_t o : h.sg_off) g.sg_off.push_back(o + io);
+        g.sg_beta.insert(g.sg_beta.end(), h.sg_beta.begin(), h.sg_beta.end());
+        for (int64_t ip : h.sg_ip) g.sg_ip.push_back(ip + item_off[b]);
+        g.sg_icnt.insert(g.sg_icnt.end(), h.sg_icnt.begin(), h.sg_icnt.end());
+        g.sg_smax.insert(g.sg_smax.end(), h.sg_smax.begin(), h.sg_smax.end());
+        for (int64_t k : h.big_blk) g.big_blk.push_back(k + blk_off[b]);
+        g.big_row0.insert(g.big_row0.end(), h.big_row0.begin(), h.big_row0.end());
+        g.max_block = std::max(g.max_block, h.max_block);
+    }
+    g.blk_inv_off.push_back((int64_t)g.inv.size());
+    return WAVE1D_OK;
+}
+
+}  // namespace wave1d

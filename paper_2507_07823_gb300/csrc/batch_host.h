@@ -1,0 +1,28 @@
+// Host tables of a batched plan: many independent periodic instances (own springs, stiffnesses,
+// incident pulse and receivers) sharing dt, N_t, tol and p, marched together.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace wave1d {
+
+// The instances' own plans (built by build_host_plan / build_receivers) joined into one table set
+// in instance-major order: spring j of instance b is global spring moff[b] + j (both in the
+// instance's internal, position-sorted order and in the caller's order), receiver r of instance b
+// is roff[b] + r.  The joined plan `g` holds what the local sum, the block solve and the receivers
+// read (items, m = 0 receiver terms, blocks, solve groups, stiffnesses, permutation) with every
+// index moved by its instance's offsets; its history tables (FIR, rotation, mode factors,
+// twiddles) are instance 0's, which all instances share.  inst_of: the instance of each global
+// spring.  Returns 0, or WAVE1D_EINVAL (err set) if the instances' derived sizes differ.
+struct BatchTables {
+    HostPlan g;
+    std::vector<int64_t> moff, roff;
+    std::vector<int32_t> inst_of;
+};
+int join_instances(const std::vector<HostPlan>& inst, BatchTables& out, std::string& err);
+
+}  // namespace wave1d
