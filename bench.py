@@ -597,6 +597,38 @@ def run_mixed_only(args):
                       "config": {"workload": f"{w.name}: {w.description}"}, **out}))
 
 
+def run_batched_only(args):
+    """The batched workload's instances (256 periodic instances, M log-uniform up to
+    args.batch_mmax) marched together through wave1d_batch_solve for args.steps steps after
+    args.warmup: whole-batch scatterer-steps/s.  Not part of the default benchmark line."""
+    import torch
+
+    from paper_2507_07823_gb300 import build, wave1d, workloads
+
+    build.build()
+    ws = workloads.config3_instances(m_range=(1e2, args.batch_mmax), Nt=args.warmup + args.steps + 1)
+    t0 = time.perf_counter()
+    batch = wave1d.Batch(ws)
+    t_plan = time.perf_counter() - t0
+    batch.solve(args.warmup, with_sigma=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    e0.record(stream)
+    st = wave1d.lib().wave1d_batch_solve(batch.h, args.steps, None, None, 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if st != 0:
+        raise RuntimeError(wave1d.lib().wave1d_batch_strerror().decode())
+    ms = e0.elapsed_time(e1)
+    batch.close()
+    print(json.dumps({"metric": METRIC, "unit": UNIT, "value": batch.M * args.steps / (ms * 1e-3),
+                      "ms_per_step": ms / args.steps, "steps": args.steps, "warmup": args.warmup, "dtype": "f64",
+                      "config": {"workload": f"{len(ws)} periodic instances, M log-uniform in [1e2, {args.batch_mmax:g}], "
+                                             f"dt = 1e-3, tol 1e-12, p = 8", "M_total": batch.M, "R_total": batch.R,
+                                 "plan_seconds": t_plan}}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -615,6 +647,9 @@ def main():
     ap.add_argument("--adjoint-steps", type=int, default=200)
     ap.add_argument("--mixed-only", action="store_true",
                     help="only the FP64 and mixed-precision marches of the benchmark workload (not a benchmark line)")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="only the batched march of the batched workload's instances (not a benchmark line)")
+    ap.add_argument("--batch-mmax", type=float, default=1e4)
     args = ap.parse_args()
     if args.spread_interp_only:
         run_spread_interp_only(args)
@@ -622,6 +657,8 @@ def main():
         run_adjoint_only(args)
     elif args.mixed_only:
         run_mixed_only(args)
+    elif args.batched_only:
+        run_batched_only(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -303,6 +303,38 @@ const char* wave1d_nufft_strerror(void);
 int wave1d_nufft1_noalloc(const double* x, const double* c, int64_t M, int K, double tol,
                           double* S, void* stream);
 
+/*
+ * Batched march: n_inst independent instances in the periodic box, each with its own springs,
+ * stiffnesses, one incident Gaussian (eq. gj) and receivers, sharing dt, Nt, tol and the options,
+ * advance together.  One step of all instances is one pass of launches: the local sum (Sec. 4.1)
+ * and the block solve (eq. linearSystem) over the instances' joined tables, and each instance's
+ * history part (Sec. 3) with the spreading and interpolation of all instances in one launch each
+ * (the batched NUFFT plan above).  The step is captured once in a CUDA graph and replayed.
+ *   offsets : host, n_inst + 1 values, offsets[0] = 0; instance i holds springs
+ *             [offsets[i], offsets[i+1]) of x and beta (host, positions wrapped into [-pi, pi)),
+ *             at least one spring each.
+ *   pulse   : host, n_inst x 3: amplitude, centre, width of instance i's incident Gaussian.
+ *   r_offsets, xr : host receivers, instance i's being xr[r_offsets[i] .. r_offsets[i+1]) (at
+ *             least one each), or r_offsets = NULL for none.
+ *   dt, Nt, tol : as wave1d_plan.  opts: NULL or as wave1d_plan with precision 0 and nufft_w 0.
+ * Every instance's derived sizes (K, W, fine grid) are the same, since they depend on dt, tol and
+ * p only.  The springs' and receivers' global order is instance-major in the caller's order.
+ * Returns WAVE1D_EINVAL / EDOMAIN / ENOMEM / ECUDA like wave1d_plan (message: wave1d_batch_strerror).
+ */
+typedef struct wave1d_batch_s* wave1d_batch_t;
+int wave1d_batch_plan(int n_inst, const int64_t* offsets, const double* x, const double* beta,
+                      const double* pulse, const int64_t* r_offsets, const double* xr, double dt,
+                      int64_t Nt, double tol, const wave1d_opts* opts, wave1d_batch_t* out);
+/*
+ * Advance nsteps steps; u_rec[s * R + r] (R: all receivers) and, if sigma is not NULL,
+ * sigma[s * M + j] (M: all springs) after step s + 1, device or host pointers as out_on_device.
+ * Synchronises; WAVE1D_EDONE past Nt, WAVE1D_ENONFINITE if a density became non-finite.
+ */
+int wave1d_batch_solve(wave1d_batch_t plan, int64_t nsteps, double* u_rec, double* sigma,
+                       int out_on_device);
+int wave1d_batch_destroy(wave1d_batch_t plan);
+const char* wave1d_batch_strerror(void);
+
 /* Free the plan and its device memory (synchronises).  NULL is accepted. */
 int wave1d_destroy(wave1d_plan_t plan);
 

@@ -44,7 +44,8 @@ EXPORTED = ["wave1d_opts_default", "wave1d_plan", "wave1d_set_incident_gaussians
             "wave1d_nufft_plan", "wave1d_nufft_plan_many", "wave1d_nufft_info", "wave1d_nufft_perm",
             "wave1d_nufft_spread",
             "wave1d_nufft_interp", "wave1d_nufft_type1", "wave1d_nufft_type2", "wave1d_nufft_destroy",
-            "wave1d_nufft_strerror", "wave1d_adjoint"]
+            "wave1d_nufft_strerror", "wave1d_adjoint", "wave1d_batch_plan", "wave1d_batch_solve",
+            "wave1d_batch_destroy", "wave1d_batch_strerror"]
 
 WAVE1D_NSTAGE = 9
 STAGES = ["local", "spread", "fft_fwd", "modes", "rbc", "fft_inv", "interp", "solve", "receivers"]
@@ -117,12 +118,19 @@ def lib(path: str = LIB_PATH):
             getattr(L, nm).argtypes = [P, _D, _D]
         L.wave1d_nufft_destroy.argtypes = [P]
         L.wave1d_adjoint.argtypes = [P, ctypes.c_int64, _D, _D, _D, _D, _D]
+        _I64 = ctypes.POINTER(ctypes.c_int64)
+        L.wave1d_batch_plan.argtypes = [ctypes.c_int, _I64, _D, _D, _D, _I64, _D, ctypes.c_double, ctypes.c_int64,
+                                        ctypes.c_double, ctypes.POINTER(wave1d_opts), ctypes.POINTER(ctypes.c_void_p)]
+        L.wave1d_batch_solve.argtypes = [P, ctypes.c_int64, _D, _D, ctypes.c_int]
+        L.wave1d_batch_destroy.argtypes = [P]
+        L.wave1d_batch_strerror.argtypes = []
+        L.wave1d_batch_strerror.restype = ctypes.c_char_p
         L.wave1d_nufft_strerror.argtypes = []
         L.wave1d_nufft_strerror.restype = ctypes.c_char_p
         L.wave1d_strerror.argtypes = [ctypes.c_int]
         L.wave1d_strerror.restype = ctypes.c_char_p
         for name in EXPORTED:
-            if name not in ("wave1d_strerror", "wave1d_nufft_strerror"):
+            if name not in ("wave1d_strerror", "wave1d_nufft_strerror", "wave1d_batch_strerror"):
                 getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -436,3 +444,56 @@ def receiver_fields(beta, w, nsteps):
                 ctx.plan.close()
 
     return _ReceiverFields.apply(beta)
+
+
+class Batch:
+    """Batched march of independent periodic instances (`wave1d_batch_plan`): `instances` is a list
+    of `workloads.Workload` sharing dt, tol and p (one incident Gaussian each, at least one
+    receiver each or none at all).  `solve(n)` returns (sigma, u): n x (all springs) and
+    n x (all receivers), instance-major in each workload's own order; `offsets` / `r_offsets`
+    split them."""
+
+    def __init__(self, instances, Nt=None, **opt):
+        w0 = instances[0]
+        o = wave1d_opts_default()
+        o.p = w0.p
+        for k, v in opt.items():
+            setattr(o, k, v)
+        x = np.ascontiguousarray(np.concatenate([w.x for w in instances]), dtype=np.float64)
+        beta = np.ascontiguousarray(np.concatenate([w.beta for w in instances]), dtype=np.float64)
+        self.offsets = np.zeros(len(instances) + 1, dtype=np.int64)
+        self.offsets[1:] = np.cumsum([w.x.size for w in instances])
+        self.r_offsets = np.zeros(len(instances) + 1, dtype=np.int64)
+        self.r_offsets[1:] = np.cumsum([len(w.xr) for w in instances])
+        pulse = np.ascontiguousarray([[w.amp[0], w.center[0], w.width[0]] for w in instances], dtype=np.float64)
+        xr = np.ascontiguousarray(np.concatenate([np.asarray(w.xr, dtype=np.float64) for w in instances]))
+        has_r = self.r_offsets[-1] > 0
+        I64 = ctypes.POINTER(ctypes.c_int64)
+        h = ctypes.c_void_p()
+        st = lib().wave1d_batch_plan(len(instances), self.offsets.ctypes.data_as(I64), _hptr(x), _hptr(beta),
+                                     _hptr(pulse), self.r_offsets.ctypes.data_as(I64) if has_r else None,
+                                     _hptr(xr) if has_r else None, float(w0.dt), int(Nt or w0.Nt), float(w0.tol),
+                                     ctypes.byref(o), ctypes.byref(h))
+        if st != WAVE1D_OK:
+            raise Wave1DError(st, "wave1d_batch_plan: " + lib().wave1d_batch_strerror().decode())
+        self.h, self.M, self.R = h, int(self.offsets[-1]), int(self.r_offsets[-1])
+
+    def solve(self, nsteps, with_sigma=True):
+        u = np.zeros((nsteps, max(self.R, 1)))
+        s = np.zeros((nsteps, self.M)) if with_sigma else None
+        st = lib().wave1d_batch_solve(self.h, int(nsteps), _hptr(u) if self.R else None,
+                                      _hptr(s) if s is not None else None, 0)
+        if st != WAVE1D_OK:
+            raise Wave1DError(st, "wave1d_batch_solve: " + lib().wave1d_batch_strerror().decode())
+        return s, u[:, :self.R]
+
+    def close(self):
+        if self.h:
+            lib().wave1d_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -176,10 +176,10 @@ def config2(**over) -> Workload:
     return make("periodic_M1e6_clustered_dt5e-4", **kw)
 
 
-def config3_instances(n_instances: int = 256, **over):
-    """Batched: independent periodic instances, M log-uniform in [1e2, 1e5], dt=1e-3."""
+def config3_instances(n_instances: int = 256, m_range=(1e2, 1e5), **over):
+    """Batched: independent periodic instances, M log-uniform in m_range (default [1e2, 1e5]), dt=1e-3."""
     rng = np.random.Generator(np.random.PCG64(7823 + 3))
-    Ms = np.exp(rng.uniform(math.log(1e2), math.log(1e5), size=n_instances)).astype(int)
+    Ms = np.exp(rng.uniform(math.log(m_range[0]), math.log(m_range[1]), size=n_instances)).astype(int)
     widths = rng.uniform(0.05, 0.2, size=n_instances)
     out = []
     for i in range(n_instances):

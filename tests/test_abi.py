@@ -97,3 +97,30 @@ def test_adjoint_argument_validation_without_gpu(lib):
     """wave1d_adjoint refuses a missing plan before touching any device memory."""
     L = wave1d.lib()
     assert L.wave1d_adjoint(None, 1, None, None, None, None, None) == wave1d.WAVE1D_EINVAL
+
+
+def test_batch_argument_validation_without_gpu(lib):
+    """wave1d_batch_plan refuses bad instance layouts before touching the GPU."""
+    L = wave1d.lib()
+    I64 = ctypes.POINTER(ctypes.c_int64)
+    x = np.array([0.1, 0.5, -0.3])
+    b = np.array([1.0, 2.0, 3.0])
+    pulse = np.array([[1.0, -2.0, 0.1], [1.0, -2.0, 0.1]])
+
+    def plan(offsets, n, pl=pulse, opts=None):
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        h = ctypes.c_void_p()
+        return L.wave1d_batch_plan(n, off.ctypes.data_as(I64), x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   np.ascontiguousarray(pl).ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   None, None, 0.01, 10, 1e-10, ctypes.byref(opts) if opts else None,
+                                   ctypes.byref(h))
+    assert plan([0, 3], 0) == wave1d.WAVE1D_EINVAL                       # no instances
+    assert plan([1, 3], 1) == wave1d.WAVE1D_EINVAL                       # offsets[0] != 0
+    assert plan([0, 0, 3], 2) == wave1d.WAVE1D_EINVAL                    # an instance without springs
+    assert plan([0, 1, 3], 2, pl=np.array([[1.0, -2.0, 0.1], [1.0, -2.0, 0.0]])) == wave1d.WAVE1D_EINVAL
+    o = wave1d.wave1d_opts_default()
+    o.precision = 1                                                     # the batched march is FP64
+    assert plan([0, 1, 3], 2, opts=o) == wave1d.WAVE1D_EINVAL
+    assert L.wave1d_batch_destroy(None) == 0
+    assert isinstance(L.wave1d_batch_strerror(), bytes)
