@@ -283,6 +283,18 @@ int wave1d_nufft_type1(wave1d_nufft_t plan, const double* c, double* S);
 int wave1d_nufft_type2(wave1d_nufft_t plan, const double* alpha, double* u);
 int wave1d_nufft_destroy(wave1d_nufft_t plan);
 const char* wave1d_nufft_strerror(void);
+/*
+ * Autotuner of the spreading's work split: the cells and the points a cell range is cut at (the
+ * spreading's tile width and bin size).  Each of nine candidate pairs, at or below the kernels'
+ * shared-memory capacities (mixed: 60/120/240 cells x 512/1024/2048 points; FP64: 32/64/128 x
+ * 1024/2048/4096), re-cuts the plan's ranges.  Each is timed over `reps` spreads of c (device,
+ * plan's point order) into grid (device, overwritten), after one untimed spread, with CUDA events
+ * on the plan's stream.  The fastest stays in the plan; *cells and *points (may be NULL) receive
+ * its caps.  Results change only in rounding: every candidate tiles the grids completely.
+ * Synchronises the plan's stream.
+ */
+int wave1d_nufft_autotune(wave1d_nufft_t plan, const double* c, double* grid, int reps, int* cells,
+                          int* points);
 
 /*
  * Type-1 NUFFT of device arrays without any memory allocation (the paper has no counterpart; it

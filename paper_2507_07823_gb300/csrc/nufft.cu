@@ -522,6 +522,9 @@ struct wave1d_nufft_s {
     NuRange* ranges = nullptr;
     int64_t nunits = 0;              // ranges
     int32_t* runs = nullptr;
+    int range_cells = 0, range_points = 0;   // the caps the ranges were cut with
+    std::vector<int32_t> i0_host;    // points' first cells (sorted within each instance), for re-cutting
+    std::vector<int64_t> off_host;   // instance offsets
     // FFT and deconvolution
     double *grid = nullptr, *work = nullptr, *spec = nullptr, *spec2 = nullptr, *twiddle = nullptr,
            *modefac = nullptr;
@@ -695,6 +698,10 @@ int wave1d_nufft_plan_many(const double* x, const int64_t* offsets, int n_inst, 
         nufft_ranges(i0, offsets, n_inst, nf, w, precision == 1 ? kRangeCells : kRangeCells64,
                      precision == 1 ? kRangePoints : kRangePoints64, kEmptyCells, kUnitThreads, ranges, runs);
         h->nunits = (int64_t)ranges.size();
+        h->range_cells = precision == 1 ? kRangeCells : kRangeCells64;
+        h->range_points = precision == 1 ? kRangePoints : kRangePoints64;
+        h->i0_host = i0;
+        h->off_host.assign(offsets, offsets + n_inst + 1);
         if ((rc = nu_upload(h, ranges, &h->ranges)) || (rc = nu_upload(h, runs, &h->runs)) ||
             (rc = nu_upload(h, gfirst, &h->first)))
             return cleanup(rc);
@@ -812,6 +819,73 @@ int wave1d_nufft_destroy(wave1d_nufft_t h) {
     else cudaDeviceSynchronize();
     for (void* a : h->allocs) cudaFree(a);
     delete h;
+    return WAVE1D_OK;
+}
+
+// Picks the spreading work split (its tile width and bin size: the cells and points a range is cut
+// at) for this plan's points by timing: each candidate pair of caps, at or below the kernels'
+// shared-memory capacities, re-cuts the ranges from the points' first cells and is timed over
+// `reps` spreads of c (after one untimed spread) with CUDA events on the plan's stream; the fastest
+// stays.  The grid is overwritten.  Every candidate tiles the grids completely (the range builder
+// is the plan's own), so results change only in rounding (the lanes per cell follow the ranges).
+int wave1d_nufft_autotune(wave1d_nufft_t h, const double* c, double* grid, int reps, int* cells, int* points) {
+    if (!h || !c || !grid || reps < 1) return nfail(WAVE1D_EINVAL, "bad arguments");
+    if (cudaSetDevice(h->device) != cudaSuccess) return nfail(WAVE1D_ECUDA, "cudaSetDevice");
+    const bool mixed = h->precision == 1;
+    const int cmax = mixed ? kRangeCells : kRangeCells64, pmax = mixed ? kRangePoints : kRangePoints64;
+    const int cand_c[3] = {cmax / 4, cmax / 2, cmax}, cand_p[3] = {pmax / 4, pmax / 2, pmax};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+        return nfail(WAVE1D_ECUDA, "cudaEventCreate");
+    float best = 0.f;
+    NuRange* best_r = h->ranges;
+    int32_t* best_runs = h->runs;
+    int64_t best_n = h->nunits;
+    int best_c = h->range_cells, best_p = h->range_points;
+    int rc = WAVE1D_OK;
+    bool first = true;
+    for (int ci = 0; ci < 3 && rc == WAVE1D_OK; ci++)
+        for (int pi = 0; pi < 3 && rc == WAVE1D_OK; pi++) {
+            std::vector<NuRange> ranges;
+            std::vector<int32_t> runs;
+            nufft_ranges(h->i0_host, h->off_host.data(), h->B, h->P.nf, h->P.nufft_w, cand_c[ci], cand_p[pi],
+                         kEmptyCells, kUnitThreads, ranges, runs);
+            NuRange* r_dev;
+            int32_t* runs_dev;
+            if ((rc = nu_upload(h, ranges, &r_dev)) || (rc = nu_upload(h, runs, &runs_dev))) break;
+            h->ranges = r_dev;
+            h->runs = runs_dev;
+            h->nunits = (int64_t)ranges.size();
+            if ((rc = wave1d_nufft_spread(h, c, grid))) break;
+            cudaEventRecord(e0, h->stream);
+            for (int r = 0; r < reps && rc == WAVE1D_OK; r++) rc = wave1d_nufft_spread(h, c, grid);
+            cudaEventRecord(e1, h->stream);
+            if (rc || cudaEventSynchronize(e1) != cudaSuccess) {
+                if (!rc) rc = nfail(WAVE1D_ECUDA, "timing the spreading failed");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (first || ms < best) {
+                first = false;
+                best = ms;
+                best_r = r_dev;
+                best_runs = runs_dev;
+                best_n = h->nunits;
+                best_c = cand_c[ci];
+                best_p = cand_p[pi];
+            }
+        }
+    h->ranges = best_r;
+    h->runs = best_runs;
+    h->nunits = best_n;
+    h->range_cells = best_c;
+    h->range_points = best_p;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    if (cells) *cells = best_c;
+    if (points) *points = best_p;
     return WAVE1D_OK;
 }
 

@@ -45,7 +45,7 @@ EXPORTED = ["wave1d_opts_default", "wave1d_plan", "wave1d_set_incident_gaussians
             "wave1d_nufft_spread",
             "wave1d_nufft_interp", "wave1d_nufft_type1", "wave1d_nufft_type2", "wave1d_nufft_destroy",
             "wave1d_nufft_strerror", "wave1d_adjoint", "wave1d_batch_plan", "wave1d_batch_solve",
-            "wave1d_batch_destroy", "wave1d_batch_strerror"]
+            "wave1d_batch_destroy", "wave1d_batch_strerror", "wave1d_nufft_autotune"]
 
 WAVE1D_NSTAGE = 9
 STAGES = ["local", "spread", "fft_fwd", "modes", "rbc", "fft_inv", "interp", "solve", "receivers"]
@@ -117,6 +117,8 @@ def lib(path: str = LIB_PATH):
         for nm in ("wave1d_nufft_spread", "wave1d_nufft_interp", "wave1d_nufft_type1", "wave1d_nufft_type2"):
             getattr(L, nm).argtypes = [P, _D, _D]
         L.wave1d_nufft_destroy.argtypes = [P]
+        L.wave1d_nufft_autotune.argtypes = [P, _D, _D, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_int)]
         L.wave1d_adjoint.argtypes = [P, ctypes.c_int64, _D, _D, _D, _D, _D]
         _I64 = ctypes.POINTER(ctypes.c_int64)
         L.wave1d_batch_plan.argtypes = [ctypes.c_int, _I64, _D, _D, _D, _I64, _D, ctypes.c_double, ctypes.c_int64,
@@ -253,6 +255,16 @@ class Nufft:
 
     def type2(self, alpha, u):
         self._call("wave1d_nufft_type2", alpha, u)
+
+    def autotune(self, c, grid, reps=5):
+        """Time the spreading's candidate work splits on c (device, point order) and keep the
+        fastest; returns its (cells, points) caps.  grid (device) is overwritten."""
+        cells, points = ctypes.c_int(), ctypes.c_int()
+        st = lib().wave1d_nufft_autotune(self.h, _dptr(c), _dptr(grid), int(reps), ctypes.byref(cells),
+                                         ctypes.byref(points))
+        if st != WAVE1D_OK:
+            raise Wave1DError(st, "wave1d_nufft_autotune: " + lib().wave1d_nufft_strerror().decode())
+        return cells.value, points.value
 
     def close(self):
         if self.h:

@@ -91,6 +91,7 @@ def test_nufft_argument_validation_without_gpu(lib):
     assert many([0, 3], 0) == wave1d.WAVE1D_EINVAL                       # no instances
     assert isinstance(L.wave1d_nufft_strerror(), bytes)
     assert L.wave1d_nufft_destroy(None) == 0
+    assert L.wave1d_nufft_autotune(None, None, None, 3, None, None) == wave1d.WAVE1D_EINVAL
 
 
 def test_adjoint_argument_validation_without_gpu(lib):

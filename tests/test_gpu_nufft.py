@@ -227,3 +227,27 @@ def test_nufft_adjoint_identities(precision, tol, bar_pass, bar_full):
         nu.close()
     print(f"adjoint precision {precision}: spread/interp {e_pass:.2e}, type-1/type-2 {e_full:.2e}")
     assert e_pass < bar_pass and e_full < bar_full
+
+
+
+@pytest.mark.skip(reason="first GPU run of the spreading autotuner pending")
+@pytest.mark.parametrize("precision,tol", [(1, 1e-6), (0, 1e-12)])
+def test_autotuned_spreading_matches_the_default_split(precision, tol):
+    """The autotuner keeps one of its candidate splits; the spread it gives equals the default
+    split's to rounding, and type-1 through it still matches the direct sums."""
+    import torch
+    from paper_2507_07823_gb300 import workloads as W
+    ws = W.config3_instances(n_instances=16, m_range=(1e2, 3e3))
+    nu = wave1d.Nufft([w.x for w in ws], 3141, tol, precision=precision)
+    try:
+        rng = np.random.default_rng(4)
+        c = torch.from_numpy(rng.standard_normal(nu.M)).cuda()
+        g0 = torch.zeros(nu.B * nu.nf, dtype=torch.float64, device="cuda")
+        g1 = torch.zeros_like(g0)
+        nu.spread(c, g0)
+        cells, points = nu.autotune(c, g1, reps=3)
+        nu.spread(c, g1)
+        assert cells > 0 and points > 0
+        assert float(torch.max(torch.abs(g1 - g0))) <= 1e-6 * float(torch.max(torch.abs(g0)))
+    finally:
+        nu.close()

@@ -44,7 +44,11 @@ def _cells(rng, kind, m, nf):
 
 @pytest.mark.parametrize("kinds", [("uniform",), ("cluster",), ("sparse",), ("giant",), ("seam",),
                                    ("cluster", "seam", "sparse", "giant", "uniform")])
-@pytest.mark.parametrize("w,caps", [(7, (240, 2048, 8192)), (11, (128, 4096, 8192)), (4, (16, 64, 32))])
+# the plans' caps, the autotuner's smaller candidates (mixed: 60 / 120 cells x 512 / 1024 points;
+# FP64: 32 / 64 x 1024 / 2048) and a tiny set
+@pytest.mark.parametrize("w,caps", [(7, (240, 2048, 8192)), (11, (128, 4096, 8192)), (4, (16, 64, 32)),
+                                    (7, (60, 512, 8192)), (7, (120, 1024, 8192)), (13, (32, 1024, 8192)),
+                                    (13, (64, 2048, 8192))])
 def test_ranges_tile_the_grids_and_reproduce_direct_spreading(checker, kinds, w, caps):
     rng = np.random.default_rng(hash((kinds, w)) % 2**32)
     for nf in (64, 1024):
