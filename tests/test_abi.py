@@ -125,3 +125,21 @@ def test_batch_argument_validation_without_gpu(lib):
     assert plan([0, 1, 3], 2, opts=o) == wave1d.WAVE1D_EINVAL
     assert L.wave1d_batch_destroy(None) == 0
     assert isinstance(L.wave1d_batch_strerror(), bytes)
+
+
+def test_budget_and_block_limits_without_gpu(lib):
+    """Host-side fault injection: a local-weight budget too small for the layout gives
+    WAVE1D_ENOMEM, and a block of springs closer than dt larger than opts.max_block gives
+    WAVE1D_EUNSUPPORTED, both before any device work."""
+    x = np.array([-0.5, 0.1, 0.103, 0.106, 0.6])          # three springs within dt = 0.01 of each other
+    b = np.array([1.0, 2.0, 3.0, 4.0, 5.0])
+    o = wave1d.wave1d_opts_default()
+    o.max_local_bytes = 1024
+    st, _ = wave1d.wave1d_plan(x, b, 5, 0, 0.01, 10, 1e-10, o)
+    assert st == wave1d.WAVE1D_ENOMEM
+    assert "budget" in wave1d.wave1d_strerror(st)
+    o = wave1d.wave1d_opts_default()
+    o.max_block = 2
+    st, _ = wave1d.wave1d_plan(x, b, 5, 0, 0.01, 10, 1e-10, o)
+    assert st == wave1d.WAVE1D_EUNSUPPORTED
+    assert "max_block" in wave1d.wave1d_strerror(st)
