@@ -10,6 +10,7 @@
 
 #include "adjoint_host.h"
 #include "internal.h"
+#include "local_fit.h"
 #include "nufft_host.h"
 #include "../../include/wave1d.h"
 
@@ -983,6 +984,73 @@ int build_receivers(HostPlan& hp, const double* xr, int64_t R, std::string& err)
     }
     spread_weights(P, hp.xr, hp.rc_i0, hp.rc_ker);
     return WAVE1D_OK;
+}
+
+void local_weights_exact(const Params& P, const std::vector<double>& d, std::vector<double>& Q) {
+    Window win(P.delta, P.b);
+    LocalRule rule;
+    rule.init(P, win);
+    const int nm = P.m_max + 1;
+    Q.assign(d.size() * (size_t)nm, 0.0);
+    for (size_t i = 0; i < d.size(); i++) rule.weights(d[i], &Q[i * nm]);
+}
+
+void build_local_fit(const Params& P, int deg, LocalFit& out) {
+    out = LocalFit();
+    out.deg = deg;
+    out.nm = P.m_max + 1;
+    // breakpoints: node i of the rule, d + (delta - d) c_i with c_i = (x_i + 1) / 2, on k dt
+    std::vector<double> gx, gw;
+    gauss_legendre(P.NL, gx, gw);
+    std::vector<double> bp = {0.0, P.dt, P.delta};
+    for (double x : gx) {
+        const double c = 0.5 * (x + 1.0);
+        for (int k = 0; k <= P.W + 1; k++) {
+            const double d = ((double)k * P.dt - P.delta * c) / (1.0 - c);
+            if (d > 0.0 && d < P.delta) bp.push_back(d);
+        }
+    }
+    std::sort(bp.begin(), bp.end());
+    for (double v : bp)
+        if (out.bp.empty() || v - out.bp.back() > 1e-15 * P.delta) out.bp.push_back(v);
+    out.bp.back() = P.delta;
+    // Chebyshev series on every interval, fitted at its first-kind Chebyshev points
+    const int n = (int)out.bp.size() - 1, np = deg + 1, nm = out.nm;
+    std::vector<double> dn((size_t)n * np);
+    for (int iv = 0; iv < n; iv++)
+        for (int j = 0; j < np; j++) {
+            const double z = std::cos(kPi * (j + 0.5) / np);
+            dn[(size_t)iv * np + j] = out.bp[iv] + 0.5 * (out.bp[iv + 1] - out.bp[iv]) * (z + 1.0);
+        }
+    std::vector<double> Q;
+    local_weights_exact(P, dn, Q);
+    out.coef.assign((size_t)n * nm * np, 0.0);
+    for (int iv = 0; iv < n; iv++)
+        for (int m = 0; m < nm; m++)
+            for (int r = 0; r < np; r++) {
+                double s = 0.0;
+                for (int j = 0; j < np; j++)
+                    s += Q[((size_t)iv * np + j) * nm + m] * std::cos(kPi * r * (j + 0.5) / np);
+                out.coef[((size_t)iv * nm + m) * np + r] = s * (r == 0 ? 1.0 : 2.0) / np;
+            }
+}
+
+void local_fit_eval(const LocalFit& f, double d, double* Q) {
+    for (int m = 0; m < f.nm; m++) Q[m] = 0.0;
+    if (!(d >= 0.0) || !(d < f.bp.back())) return;
+    const int iv = (int)(std::upper_bound(f.bp.begin(), f.bp.end(), d) - f.bp.begin()) - 1;
+    const double a = f.bp[iv], b = f.bp[iv + 1], z = 2.0 * (d - a) / (b - a) - 1.0;
+    const int np = f.deg + 1;
+    for (int m = 0; m < f.nm; m++) {
+        const double* c = &f.coef[((size_t)iv * f.nm + m) * np];
+        double b0 = 0.0, b1 = 0.0;                      // Clenshaw
+        for (int r = f.deg; r >= 1; r--) {
+            const double b2 = b1;
+            b1 = b0;
+            b0 = 2.0 * z * b1 - b2 + c[r];
+        }
+        Q[m] = z * b0 - b1 + c[0];
+    }
 }
 
 void receiver_columns(const LocalCSR& rloc, int64_t M, ReceiverColumns& out) {
