@@ -5,6 +5,8 @@ march, against the FP64 plan of the same kernel width (what FP32 alone changes),
 bit for bit from run to run, and through a projection step in free space.
 
 These tests are the path's first run on a GPU and stay skipped until that run has been made."""
+import os
+
 import numpy as np
 import pytest
 
@@ -13,7 +15,8 @@ from paper_2507_07823_gb300 import wave1d
 from paper_2507_07823_gb300 import workloads as W
 
 pytestmark = [pytest.mark.gpu,
-              pytest.mark.skip(reason="first GPU run of the mixed-precision step pending")]
+              pytest.mark.skipif(os.environ.get("WAVE1D_RUN_PENDING") != "1",
+                                 reason="first GPU run of the mixed-precision step pending (WAVE1D_RUN_PENDING=1 runs it)")]
 
 
 def _rel(a, b):
