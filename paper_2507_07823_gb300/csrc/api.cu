@@ -97,6 +97,9 @@ struct wave1d_plan_s {
     int64_t prof_steps = 0;
     // mixed precision (opts.precision = 1): FP32 NUFFT plans of the springs and of the receivers
     // (same fine grid and kernel as the plan's, width 7), their point orders and work arrays
+    // sizes of the local-sum tables, kept for wave1d_get_info once the host copies of the weights
+    // (FP64 CSR, m-ordered rows, work-item weights) are released after the upload
+    int64_t info_pairs = 0, info_weights = 0, info_nearby = 0, info_local_bytes = 0;
     bool mixed = false;
     wave1d_nufft_t nu_s = nullptr, nu_r = nullptr;
     int64_t *nu_perm_s = nullptr, *nu_perm_r = nullptr;
@@ -649,6 +652,18 @@ int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double d
     if ((rc = dalloc(p, &p->d_gstage, (size_t)P.M))) return cleanup(rc);
     if ((rc = upload_receivers(p))) return cleanup(rc);
     d.pulse = nullptr;
+    {
+        // sizes for wave1d_get_info, then the host copies of the weights go (the device holds them;
+        // the items' lengths stay, for ordering the receivers' items when receivers are set)
+        const LocalItems& L = hp.litems;
+        p->info_pairs = (int64_t)hp.loc.src.size();
+        p->info_weights = (int64_t)hp.lrows.w.size() / 2;
+        p->info_nearby = hp.loc.nearby;
+        p->info_local_bytes = (int64_t)(L.w.size() * sizeof(float) + L.src.size() * sizeof(int32_t) +
+                                        (L.s0.size() + L.len.size()) * sizeof(int32_t) +
+                                        L.wbase.size() * sizeof(int64_t)) +
+                              8 * (int64_t)L.row.size();
+    }
     if (o.precision == 1) {
         p->mixed = true;
         // tol 1e-6 gives the width-7 kernel: the same nf, kernel shape and deconvolution as the plan's
@@ -663,6 +678,10 @@ int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double d
 #undef UP
     if ((rc = leave(p))) return cleanup(rc);
     if (cudaStreamSynchronize(p->s) != cudaSuccess) return cleanup(fail(WAVE1D_ECUDA, "plan upload failed"));
+    // the uploads have completed: release the host copies of the weights
+    hp.loc = LocalCSR();
+    hp.lrows = LocalRows();
+    std::vector<float>().swap(hp.litems.w);
     *out = p;
     return WAVE1D_OK;
 }
@@ -944,17 +963,13 @@ int wave1d_get_info(wave1d_plan_t p, wave1d_info* info) {
     info->tol = P.tol;
     info->b = P.b;
     info->delta = P.delta;
-    info->local_pairs = (int64_t)p->hp.loc.src.size();
-    info->local_weights = (int64_t)p->hp.lrows.w.size() / 2;
-    info->nearby_pairs = p->hp.loc.nearby;
+    info->local_pairs = p->info_pairs;
+    info->local_weights = p->info_weights;
+    info->nearby_pairs = p->info_nearby;
     info->blocks = (int64_t)p->hp.blk_ptr.size() - 1;
     info->max_block = p->hp.max_block;
     info->device_bytes = p->bytes;
-    const LocalItems& L = p->hp.litems;
-    info->local_bytes = (int64_t)(L.w.size() * sizeof(float) + L.src.size() * sizeof(int32_t) +
-                                  (L.s0.size() + L.len.size()) * sizeof(int32_t) +
-                                  L.wbase.size() * sizeof(int64_t)) +
-                        8 * (int64_t)L.row.size();
+    info->local_bytes = p->info_local_bytes;
     return WAVE1D_OK;
 }
 
