@@ -422,6 +422,10 @@ int wave1d_batch_plan(int n_inst, const int64_t* offsets, const double* x, const
             cudaSuccess)
         return cleanup(bfail(WAVE1D_ECUDA, "cannot size the shared memory of the history passes"));
     if (cudaStreamSynchronize(p->s) != cudaSuccess) return cleanup(bfail(WAVE1D_ECUDA, "plan upload failed"));
+    // the device holds the joined weights now: release the host copies
+    std::vector<float>().swap(p->bt.g.litems.w);
+    std::vector<float>().swap(p->bt.g.ritems.w);
+    std::vector<double>().swap(p->bt.g.inv);
     *out = p;
     return WAVE1D_OK;
 }
