@@ -4,10 +4,8 @@ torch.autograd wrapper, dL/dbeta and dL/dg of a march driven by forcing vectors,
 reproducibility, and central differences of the GPU forward march on a larger free-space layout
 (several projections, hundreds of springs).
 
-The kernels' bodies are checked on the CPU against the same oracle by tests/test_host_adjoint.py;
-these tests are their first run on a GPU and stay skipped until that run has been made."""
-import os
-
+The kernels' bodies are also checked on the CPU against the same oracle by
+tests/test_host_adjoint.py."""
 import numpy as np
 import pytest
 
@@ -17,9 +15,7 @@ from paper_2507_07823_gb300 import workloads as W
 
 torch = pytest.importorskip("torch")
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("WAVE1D_RUN_PENDING") != "1",
-                                 reason="first GPU run of the reverse-march kernels pending (WAVE1D_RUN_PENDING=1 runs it)")]
+pytestmark = pytest.mark.gpu
 
 
 def _layout(bc, seed=5, M=10, p=6, dt=0.02, Nt=400):

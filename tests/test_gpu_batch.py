@@ -2,11 +2,7 @@
 incident Gaussian and receivers, advanced together.  Each instance's densities and receiver fields
 against its own one-instance plan (the same scheme; the history part's spreading runs through the
 batched NUFFT instead of the step's spreading matrix, so agreement is to rounding) and against the
-discrete scheme's oracle at 1e-9; bit for bit from run to run.
-
-These tests are the path's first run on a GPU and stay skipped until that run has been made."""
-import os
-
+discrete scheme's oracle at 1e-9; bit for bit from run to run."""
 import numpy as np
 import pytest
 
@@ -14,9 +10,7 @@ from oracle import wfp
 from paper_2507_07823_gb300 import wave1d
 from paper_2507_07823_gb300 import workloads as W
 
-pytestmark = [pytest.mark.gpu,
-              pytest.mark.skipif(os.environ.get("WAVE1D_RUN_PENDING") != "1",
-                                 reason="first GPU run of the batched march pending (WAVE1D_RUN_PENDING=1 runs it)")]
+pytestmark = pytest.mark.gpu
 
 
 def _instances():
@@ -28,7 +22,9 @@ def _instances():
 
 
 def _rel(a, b):
-    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+    # relative to the reference's size, floored at 1e-20: an instance the pulse never reaches carries
+    # only Gaussian tails below e^-72 of the amplitude, which the library's forcing cuts to zero
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-20))
 
 
 def test_each_instance_matches_its_own_plan_and_the_oracle():

@@ -1,19 +1,14 @@
 """Failure detection without a GPU fault: a non-finite value injected from the host (a NaN in the
 forcing vector of one step) makes the step's densities non-finite; the kernels latch
 WAVE1D_ENONFINITE in the plan's status word, the next synchronising call reports it, and the
-context stays usable (a new plan marches normally afterwards).
-
-First GPU run pending: skipped until then."""
-import os
-
+context stays usable (a new plan marches normally afterwards)."""
 import numpy as np
 import pytest
 
 from paper_2507_07823_gb300 import wave1d
 from paper_2507_07823_gb300 import workloads as W
 
-pytestmark = [pytest.mark.gpu, pytest.mark.skipif(os.environ.get("WAVE1D_RUN_PENDING") != "1",
-                                 reason="first GPU run pending (WAVE1D_RUN_PENDING=1 runs it)")]
+pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("step_kernel", [1, 0])

@@ -8,8 +8,6 @@ over the whole output.  Bars: FP64 at tol 1e-12 -> 1e-10 (the plan's NUFFT accur
 1e-6 -> 1e-6 (the mixed mode's stated accuracy).  At M = 1e6 (the clustered periodic workload)
 the direct sums are taken at sampled modes and points.
 """
-import os
-
 import numpy as np
 import pytest
 
@@ -232,8 +230,6 @@ def test_nufft_adjoint_identities(precision, tol, bar_pass, bar_full):
 
 
 
-@pytest.mark.skipif(os.environ.get("WAVE1D_RUN_PENDING") != "1",
-                    reason="first GPU run of the spreading autotuner pending (WAVE1D_RUN_PENDING=1 runs it)")
 @pytest.mark.parametrize("precision,tol", [(1, 1e-6), (0, 1e-12)])
 def test_autotuned_spreading_matches_the_default_split(precision, tol):
     """The autotuner keeps one of its candidate splits; the spread it gives equals the default
