@@ -308,6 +308,11 @@ def run_ours(args):
     if not args.no_spread_interp:
         line["spread_interp_M1e6"] = spread_interp_million(torch, stream, flush_l2, hbm)
         line["spread_interp_batched"] = spread_interp_batched(torch, stream, flush_l2, hbm)
+    if world == 1 and not args.no_forms:
+        try:
+            line["forms_beside_fp64"] = forms_beside_fp64(torch, w)
+        except Exception as e:                               # recorded, never fatal to the line
+            line["forms_beside_fp64"] = {"error": repr(e)[:300]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, args.cpu_steps)
     if rank == 0:
@@ -406,6 +411,81 @@ def spread_interp_batched(torch, stream, flush_l2, hbm, reps=10):
         out[name] = {"tol": tol, "kernel_width": nu.w, "spread_us": 1e3 * t_s, "interp_us": 1e3 * t_i,
                      "achieved_GBps": achieved, "frac_of_hbm": achieved / hbm, "plan_seconds": t_plan}
         nu.close()
+    return out
+
+
+def forms_beside_fp64(torch, w, steps=200, warmup=20):
+    """The mixed-precision step, the reverse-time march and the batched march, each timed with CUDA
+    events beside the FP64 march, on small cases (a few seconds in all).  Each form is measured on its
+    own and a failure is recorded as a string, so the benchmark line never depends on them."""
+    from paper_2507_07823_gb300 import wave1d, workloads
+
+    out = {}
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    # mixed precision: the benchmark workload, FP64 (one-launch step) and mixed (per-stage)
+    try:
+        res, fields = {}, {}
+        for name, kw in (("fp64", {}), ("mixed", {"precision": 1})):
+            plan = wave1d.Plan.from_workload(w.with_(Nt=warmup + steps), **kw)
+            try:
+                plan.solve(warmup, with_sigma=False)
+                ms = timed(lambda: wave1d._check(wave1d.wave1d_solve(plan.h, steps, None, None, 1), "wave1d_solve"))
+                fields[name] = (plan.sigma(), plan.receivers())
+                res[name] = {"value": w.M * steps / (ms * 1e-3), "ms_per_step": ms / steps}
+            finally:
+                plan.close()
+        (s64, u64), (s32, u32) = fields["fp64"], fields["mixed"]
+        res["rel_diff_sigma"] = float(np.max(np.abs(s32 - s64)) / np.max(np.abs(s64)))
+        res["rel_diff_receivers"] = float(np.max(np.abs(u32 - u64)) / np.max(np.abs(u64)))
+        res["workload"] = f"{w.name}, {steps} steps after {warmup}"
+        out["mixed_precision"] = res
+    except Exception as e:                                   # recorded, never fatal to the line
+        out["mixed_precision"] = {"error": repr(e)[:300]}
+
+    # reverse-time march: dL/dbeta over the same march, beside the forward march that records sigma
+    try:
+        plan = wave1d.Plan.from_workload(w.with_(Nt=steps))
+        try:
+            holder = {}
+            ms_f = timed(lambda: holder.update(zip(("sigma", "u"), plan.solve_device(steps))))
+            ubar = holder["u"] - 0.5 * holder["u"]
+            ms_a = timed(lambda: holder.update(g=plan.adjoint(holder["sigma"], ubar)))
+            out["adjoint"] = {"forward_value": w.M * steps / (ms_f * 1e-3), "adjoint_value": w.M * steps / (ms_a * 1e-3),
+                              "forward_ms_per_step": ms_f / steps, "adjoint_ms_per_step": ms_a / steps,
+                              "grad_finite": bool(torch.isfinite(holder["g"]).all()),
+                              "workload": f"{w.name}, {steps} steps, L = 1/4 sum u^2 (ubar = u / 2); the adjoint call's "
+                                          "work arrays and NUFFT plan included"}
+        finally:
+            plan.close()
+    except Exception as e:
+        out["adjoint"] = {"error": repr(e)[:300]}
+
+    # batched march: 64 periodic instances of the batched workload's shape, M log-uniform in [1e2, 2e3]
+    try:
+        ws = workloads.config3_instances(n_instances=64, m_range=(1e2, 2e3), Nt=warmup + steps + 1)
+        batch = wave1d.Batch(ws)
+        try:
+            batch.solve(warmup, with_sigma=False)
+            st = {}
+            ms = timed(lambda: st.update(rc=wave1d.lib().wave1d_batch_solve(batch.h, steps, None, None, 1)))
+            if st["rc"] != 0:
+                raise RuntimeError(wave1d.lib().wave1d_batch_strerror().decode())
+            out["batched"] = {"value": batch.M * steps / (ms * 1e-3), "ms_per_step": ms / steps, "M_total": batch.M,
+                              "workload": f"64 periodic instances, M log-uniform in [1e2, 2e3], dt = 1e-3, {steps} steps"}
+        finally:
+            batch.close()
+    except Exception as e:
+        out["batched"] = {"error": repr(e)[:300]}
     return out
 
 
@@ -639,6 +719,7 @@ def main():
     ap.add_argument("--ref-max-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-spread-interp", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the mixed / adjoint / batched forms beside FP64")
     ap.add_argument("--spread-interp-only", action="store_true",
                     help="only the M = 1e6 spreading / interpolation timings (not a benchmark line)")
     ap.add_argument("--spread-interp-reps", type=int, default=20)
