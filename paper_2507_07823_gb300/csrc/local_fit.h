@@ -17,6 +17,7 @@ struct LocalFit {
     int nm = 0;                  // m = 0 .. nm - 1 (m_max + 1)
     std::vector<double> bp;      // breakpoints 0 = bp[0] < ... < bp[n] = delta
     std::vector<double> coef;    // [interval][m][deg + 1]
+    std::vector<int> mlo, mhi;   // per interval: the first and last m with a non-zero series
 };
 
 // Breakpoints of the plan's rule and degree-`deg` series on every interval (fitted at the

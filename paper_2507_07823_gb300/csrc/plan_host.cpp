@@ -1033,6 +1033,15 @@ void build_local_fit(const Params& P, int deg, LocalFit& out) {
                     s += Q[((size_t)iv * np + j) * nm + m] * std::cos(kPi * r * (j + 0.5) / np);
                 out.coef[((size_t)iv * nm + m) * np + r] = s * (r == 0 ? 1.0 : 2.0) / np;
             }
+    out.mlo.assign(n, nm);
+    out.mhi.assign(n, -1);
+    for (int iv = 0; iv < n; iv++)
+        for (int m = 0; m < nm; m++)
+            for (int r = 0; r < np; r++)
+                if (out.coef[((size_t)iv * nm + m) * np + r] != 0.0) {
+                    out.mlo[iv] = std::min(out.mlo[iv], m);
+                    out.mhi[iv] = std::max(out.mhi[iv], m);
+                }
 }
 
 void local_fit_eval(const LocalFit& f, double d, double* Q) {

@@ -38,3 +38,36 @@ def test_piecewise_fit_reproduces_the_plan_rule(checker, dt, tol, deg, bar):
         # about N_L W / 2 intervals (W = N_L = 36): the oracle's breakpoints give 636, the builder
         # merges the few closer than 1e-15 delta
         assert 600 <= int(n) <= 640, r.stdout
+
+
+@pytest.fixture(scope="module")
+def rows_checker():
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    build_dir = os.path.join(HERE, "native", "_build")
+    os.makedirs(build_dir, exist_ok=True)
+    out = os.path.join(build_dir, "local_fit_rows_check")
+    cmd = ["g++", "-O2", "-std=c++17", "-I", CSRC, "-I", INCLUDE, "-o", out,
+           os.path.join(HERE, "native", "local_fit_rows_check.cpp"), os.path.join(CSRC, "plan_host.cpp"), "-lpthread"]
+    subprocess.run(cmd, check=True, capture_output=True)
+    return out
+
+
+@pytest.mark.parametrize("bc,dt,layout", [(1, 1e-3, "uniform"), (0, 1e-3, "cluster"), (0, 0.01, "seam")])
+def test_local_sums_from_pair_distances_match_stored_weights(rows_checker, bc, dt, layout):
+    """Every spring row's local sum (m >= 1) with weights evaluated per pair (bisection into the
+    breakpoints, the interval's non-zero m range, Clenshaw) at distances recomputed from the
+    positions, against the plan's stored FP64 weights: within 1e-12 of the largest row sum."""
+    import numpy as np
+    rng = np.random.default_rng(9)
+    if layout == "uniform":
+        x = np.sort(rng.uniform(-2.5, 2.5, 2000))
+    elif layout == "cluster":
+        x = np.sort(np.concatenate([0.4 + 0.01 * rng.standard_normal(600), rng.uniform(-np.pi, np.pi, 400)]))
+    else:                                           # pairs across the periodic seam
+        x = np.sort(np.concatenate([np.pi - 0.05 * rng.random(40), -np.pi + 0.05 * rng.random(40), rng.uniform(-3, 3, 200)]))
+    text = f"{x.size} {dt!r} 1e-12 {bc} 7\n" + " ".join(repr(float(v)) for v in x) + "\n"
+    r = subprocess.run([rows_checker], input=text, capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout
+    _, err, pairs = r.stdout.split()
+    assert float(err) < 1e-12 and int(pairs) > x.size, r.stdout
