@@ -76,6 +76,11 @@ typedef struct {
                            of the field; nufft_w must be 0 or 7), the FFTs, mode recurrence,
                            local sum and density solve as in FP64; steps run as per-stage
                            launches                                                              */
+    int local_weights;  /* 0 (default): the local weights Q_m stored per pair and streamed every
+                           step.  1: computed per pair from its distance by piecewise Chebyshev
+                           series of degree 7 between the rule's breakpoints (FP64, within about
+                           1e-13 of max |Q|), so the device holds no weights; steps run as
+                           per-stage launches, and wave1d_adjoint is not available              */
 } wave1d_opts;
 
 /* Derived sizes of a plan (read-only report). */

@@ -15,7 +15,9 @@
 #include <vector>
 
 #include "adjoint_host.h"
+#include "fly.h"
 #include "internal.h"
+#include "local_fit.h"
 #include "phases.cuh"
 #include "../../include/wave1d.h"
 
@@ -55,6 +57,7 @@ __global__ void k_adj_modes(int K, int W, int64_t n, const double* rot, const do
 __global__ void k_mx_gather(DevPlan P, const int64_t* perm, double* c);
 __global__ void k_mx_rhs(DevPlan P, const int64_t* perm, const double* u);
 __global__ void k_mx_receivers(int64_t R, const int64_t* perm, const double* u, double* uHr);
+__global__ void k_local_fly(DevPlan P, FlyTables F);
 }  // namespace wave1d
 
 using namespace wave1d;
@@ -100,6 +103,8 @@ struct wave1d_plan_s {
     // sizes of the local-sum tables, kept for wave1d_get_info once the host copies of the weights
     // (FP64 CSR, m-ordered rows, work-item weights) are released after the upload
     int64_t info_pairs = 0, info_weights = 0, info_nearby = 0, info_local_bytes = 0;
+    bool fly = false;                 // local weights computed per pair (opts.local_weights = 1)
+    FlyTables fly_t{};
     bool mixed = false;
     wave1d_nufft_t nu_s = nullptr, nu_r = nullptr;
     int64_t *nu_perm_s = nullptr, *nu_perm_r = nullptr;
@@ -254,6 +259,15 @@ int upload_receivers(wave1d_plan_t p) {
     d.r0p_w = f64b;
     if ((rc = zeros(p, &d.uHr, (size_t)std::max<int64_t>(1, d.R)))) return rc;
     if ((rc = zeros(p, &d.rec_hist, (size_t)p->chunk * std::max<int64_t>(1, d.R)))) return rc;
+    if (p->fly) {
+        std::vector<int8_t> rn;
+        item_source_counts(hp.rrows, hp.ritems, rn);
+        int8_t* rnd;
+        double* xrd;
+        if ((rc = upload(p, rn, &rnd)) || (rc = upload(p, hp.xr, &xrd))) return rc;
+        p->fly_t.r_nsrc = rnd;
+        p->fly_t.xr = xrd;
+    }
     return WAVE1D_OK;
 }
 
@@ -311,6 +325,8 @@ int enqueue_step(wave1d_plan_t p, int64_t n, const double* g_ext, double* sig_hi
         cudaStreamWaitEvent(p->s2, p->ev_fork, 0);
         k_local_items<<<local_grid(p), T, 0, p->s2>>>(d);
         cudaEventRecord(p->ev_join, p->s2);
+    } else if (p->fly) {
+        k_local_fly<<<local_grid(p), T, 0, s>>>(d, p->fly_t);
     } else {
         k_local_items<<<local_grid(p), T, 0, s>>>(d);
     }
@@ -488,6 +504,9 @@ int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double d
     if (o.max_block <= 0) o.max_block = 4096;
     if (o.max_local_bytes <= 0) o.max_local_bytes = (int64_t)16 << 30;
     if (o.precision != 0 && o.precision != 1) return fail(WAVE1D_EINVAL, "precision must be 0 (FP64) or 1 (mixed)");
+    if (o.local_weights != 0 && o.local_weights != 1)
+        return fail(WAVE1D_EINVAL, "local_weights must be 0 (stored) or 1 (computed per pair)");
+    if (o.local_weights == 1) o.step_kernel = 0;   // the computed weights run in their own launch
     if (o.precision == 1) {
         if (o.nufft_w != 0 && o.nufft_w != 7) return fail(WAVE1D_EINVAL, "mixed precision uses the width-7 NUFFT kernel");
         o.nufft_w = 7;          // the FP32 kernels' width: the plan's grid, kernel and deconvolution match them
@@ -609,6 +628,30 @@ int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double d
     UP(hp.sp_i0, sp_i0, i32);
     UP(hp.sp_ker, sp_ker, f64);
     if ((rc = zeros(p, &d.uH, (size_t)P.M))) return cleanup(rc);
+    if (o.local_weights == 1) {
+        // weights computed per pair: the series table and the items' real source counts go to the
+        // device instead of the stored weights
+        p->fly = true;
+        LocalFit fit;
+        build_local_fit(P, 7, fit);
+        std::vector<int8_t> ln;
+        item_source_counts(hp.lrows, hp.litems, ln);
+        double *bpd, *cd;
+        int *mlod, *mhid;
+        int8_t* lnd;
+        if ((rc = upload(p, fit.bp, &bpd)) || (rc = upload(p, fit.coef, &cd)) || (rc = upload(p, fit.mlo, &mlod)) ||
+            (rc = upload(p, fit.mhi, &mhid)) || (rc = upload(p, ln, &lnd)))
+            return cleanup(rc);
+        p->fly_t.bp = bpd;
+        p->fly_t.coef = cd;
+        p->fly_t.mlo = mlod;
+        p->fly_t.mhi = mhid;
+        p->fly_t.nint = (int)fit.bp.size() - 1;
+        p->fly_t.deg = fit.deg;
+        p->fly_t.nm = fit.nm;
+        p->fly_t.l_nsrc = lnd;
+        std::vector<float>().swap(hp.litems.w);          // no stored spring weights on the device
+    }
     {
         ItemsDev it;
         if ((rc = upload_items(p, hp.litems, it))) return cleanup(rc);
@@ -1093,6 +1136,7 @@ int wave1d_adjoint(wave1d_plan_t p, int64_t nsteps, const double* sigma, const d
                    double* grad_beta, double* grad_g) {
     if (!p || !sigma || nsteps < 1 || (!grad_beta && !grad_g))
         return fail(WAVE1D_EINVAL, "need a plan, sigma, nsteps >= 1 and grad_beta or grad_g");
+    if (p->fly) return fail(WAVE1D_EUNSUPPORTED, "the reverse march reads stored local weights (local_weights = 0)");
     const HostPlan& hp = p->hp;
     const Params& P = hp.P;
     if (nsteps > P.Nt) return fail(WAVE1D_EINVAL, "nsteps beyond the Nt of the plan");

@@ -25,6 +25,9 @@ struct LocalFit {
 void build_local_fit(const Params& P, int deg, LocalFit& out);
 // Q[0 .. nm-1] at distance d in [0, delta) from the series (zeros for d >= delta).
 void local_fit_eval(const LocalFit& f, double d, double* Q);
+// Real sources of every item of a LocalItems table built from `rows` (item c of a row holds the
+// row's source ranks 32 c .. 32 c + 31, of which min(32, n - 32 c) exist).
+void item_source_counts(const LocalRows& rows, const LocalItems& items, std::vector<int8_t>& nsrc);
 // The plan's stored-weight rule itself at each distance, Q[i * (m_max + 1) + m] (for checks).
 void local_weights_exact(const Params& P, const std::vector<double>& d, std::vector<double>& Q);
 

@@ -986,6 +986,16 @@ int build_receivers(HostPlan& hp, const double* xr, int64_t R, std::string& err)
     return WAVE1D_OK;
 }
 
+void item_source_counts(const LocalRows& rows, const LocalItems& items, std::vector<int8_t>& nsrc) {
+    const int64_t T = (int64_t)items.item_ptr.size() - 1;
+    nsrc.assign(items.row.size(), 0);
+    for (int64_t j = 0; j < T; j++) {
+        const int64_t ns = rows.src_off[j + 1] - rows.src_off[j];
+        for (int64_t c = items.item_ptr[j]; c < items.item_ptr[j + 1]; c++)
+            nsrc[c] = (int8_t)std::min<int64_t>(32, ns - 32 * (c - items.item_ptr[j]));
+    }
+}
+
 void local_weights_exact(const Params& P, const std::vector<double>& d, std::vector<double>& Q) {
     Window win(P.delta, P.b);
     LocalRule rule;

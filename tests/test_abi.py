@@ -61,6 +61,10 @@ def test_argument_validation_without_gpu(lib):
     assert wave1d.wave1d_plan(x, b, 2, 0, 0.01, 10, 1e-10, o)[0] == wave1d.WAVE1D_EINVAL
     o.precision, o.nufft_w = 1, 9                              # mixed runs the width-7 kernel only
     assert wave1d.wave1d_plan(x, b, 2, 0, 0.01, 10, 1e-10, o)[0] == wave1d.WAVE1D_EINVAL
+    o = wave1d.wave1d_opts_default()
+    assert o.local_weights == 0                                # stored weights by default
+    o.local_weights = 2
+    assert wave1d.wave1d_plan(x, b, 2, 0, 0.01, 10, 1e-10, o)[0] == wave1d.WAVE1D_EINVAL
     assert wave1d.wave1d_destroy(None) == 0
 
 

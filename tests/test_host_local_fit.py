@@ -71,3 +71,33 @@ def test_local_sums_from_pair_distances_match_stored_weights(rows_checker, bc, d
     assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout
     _, err, pairs = r.stdout.split()
     assert float(err) < 1e-12 and int(pairs) > x.size, r.stdout
+
+
+@pytest.fixture(scope="module")
+def fly_checker():
+    if shutil.which("g++") is None:
+        pytest.skip("g++ not available")
+    build_dir = os.path.join(HERE, "native", "_build")
+    os.makedirs(build_dir, exist_ok=True)
+    out = os.path.join(build_dir, "fly_items_check")
+    cmd = ["g++", "-O2", "-std=c++17", "-I", CSRC, "-I", INCLUDE, "-o", out,
+           os.path.join(HERE, "native", "fly_items_check.cpp"), os.path.join(CSRC, "plan_host.cpp"), "-lpthread"]
+    subprocess.run(cmd, check=True, capture_output=True)
+    return out
+
+
+@pytest.mark.parametrize("bc,dt", [(1, 1e-3), (0, 0.01)])
+def test_computed_weight_items_match_stored_rows(fly_checker, bc, dt):
+    """The traversal of the local sum with weights computed per pair (the step's items, their real
+    source counts, distances from the positions, m >= 1), for spring rows and receiver rows, against
+    the stored FP64 weights: within 1e-12 of the largest row sum."""
+    import numpy as np
+    rng = np.random.default_rng(13)
+    lim = 2.5 if bc == 1 else np.pi
+    x = np.sort(np.concatenate([rng.uniform(-lim, lim, 700), 0.2 + 0.003 * rng.standard_normal(100)]))
+    xr = np.array([-1.0, 0.2, float(x[10]), 1.7])                # one receiver on a spring
+    text = f"{x.size} {xr.size} {dt!r} 1e-12 {bc}\n" + " ".join(repr(float(v)) for v in x) + "\n" + \
+        " ".join(repr(float(v)) for v in xr) + "\n"
+    r = subprocess.run([fly_checker], input=text, capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout
+    assert float(r.stdout.split()[1]) < 1e-12, r.stdout
