@@ -50,6 +50,8 @@ enum wave1d_status {
     WAVE1D_EDOMAIN = -2,       /* delta >= pi, or a free-space spring/receiver outside Omega   */
     WAVE1D_ENOMEM = -3,        /* device or host allocation failed / over the memory budget    */
     WAVE1D_ECUDA = -4,         /* a CUDA runtime call failed                                   */
+    WAVE1D_ENOTCONV = -5,      /* the Jacobi sweeps of the implicit solve (local_weights = 1) did
+                                  not converge within their limit (latched on the device)        */
     WAVE1D_ENONFINITE = -6,    /* a density became NaN or Inf (latched on the device)          */
     WAVE1D_EDONE = -7,         /* stepping past the Nt given to wave1d_plan                    */
     WAVE1D_EUNSUPPORTED = -9,  /* a size this build does not handle (see wave1d_strerror)      */
@@ -77,10 +79,17 @@ typedef struct {
                            local sum and density solve as in FP64; steps run as per-stage
                            launches                                                              */
     int local_weights;  /* 0 (default): the local weights Q_m stored per pair and streamed every
-                           step.  1: computed per pair from its distance by piecewise Chebyshev
-                           series of degree 7 between the rule's breakpoints (FP64, within about
-                           1e-13 of max |Q|), so the device holds no weights; steps run as
-                           per-stage launches, and wave1d_adjoint is not available              */
+                           step, the implicit blocks of I + S inverted at plan time.
+                           1: no per-pair data.  The sources within delta of a spring are an index
+                           window of the sorted springs; Q_m(d) comes from degree-7 polynomials in
+                           d between the breakpoints of the rule (Sec. 4.1; within 1e-12 of
+                           max |Q|), folded with each source's densities once per interval and
+                           evaluated per pair in compensated FP32 pairs (local sums within about
+                           2e-11 of the FP64 rule).  The implicit part is solved by Jacobi sweeps
+                           until the largest change is below 1e-14 of the largest density
+                           (WAVE1D_ENOTCONV after 40).  For layouts whose weights or blocks do
+                           not fit (a million clustered springs: 1.3e10 pairs); steps run as
+                           per-stage launches; wave1d_adjoint is not available                 */
 } wave1d_opts;
 
 /* Derived sizes of a plan (read-only report). */

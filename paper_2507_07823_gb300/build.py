@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libwave1d.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["api.cu", "kernels.cu", "history.cu", "step.cu", "nufft.cu", "nufft_noalloc.cu", "adjoint.cu", "mixed.cu", "batch.cu", "fly.cu"]
+CU_SOURCES = ["api.cu", "kernels.cu", "history.cu", "step.cu", "nufft.cu", "nufft_noalloc.cu", "adjoint.cu", "mixed.cu", "batch.cu", "range.cu"]
 CPP_SOURCES = ["plan_host.cpp", "batch_host.cpp"]
 
 

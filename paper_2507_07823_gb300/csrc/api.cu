@@ -15,9 +15,7 @@
 #include <vector>
 
 #include "adjoint_host.h"
-#include "fly.h"
 #include "internal.h"
-#include "local_fit.h"
 #include "phases.cuh"
 #include "../../include/wave1d.h"
 
@@ -57,7 +55,14 @@ __global__ void k_adj_modes(int K, int W, int64_t n, const double* rot, const do
 __global__ void k_mx_gather(DevPlan P, const int64_t* perm, double* c);
 __global__ void k_mx_rhs(DevPlan P, const int64_t* perm, const double* u);
 __global__ void k_mx_receivers(int64_t R, const int64_t* perm, const double* u, double* uHr);
-__global__ void k_local_fly(DevPlan P, FlyTables F);
+__global__ void k_rs_local(DevPlan P, RangeDev R);
+__global__ void k_rs_nearby_weights(DevPlan P, RangeDev R);
+__global__ void k_rs_solve_init(DevPlan P, RangeDev R);
+__global__ void k_rs_jacobi(DevPlan P, RangeDev R, int it);
+__global__ void k_rs_store(DevPlan P, RangeDev R);
+__global__ void k_rs_receivers(DevPlan P, RangeDev R);
+__global__ void k_rs_finish(DevPlan P, RangeDev R);
+size_t rs_local_smem(int nint, int nm);
 }  // namespace wave1d
 
 using namespace wave1d;
@@ -103,8 +108,12 @@ struct wave1d_plan_s {
     // sizes of the local-sum tables, kept for wave1d_get_info once the host copies of the weights
     // (FP64 CSR, m-ordered rows, work-item weights) are released after the upload
     int64_t info_pairs = 0, info_weights = 0, info_nearby = 0, info_local_bytes = 0;
-    bool fly = false;                 // local weights computed per pair (opts.local_weights = 1)
-    FlyTables fly_t{};
+    // no pair lists (opts.local_weights = 1): local sum over sorted index windows with the weights
+    // from their polynomials in the distance, implicit part solved by Jacobi sweeps (range.cu)
+    bool range = false;
+    RangeDev rd{};
+    size_t rs_smem = 0;
+    int64_t info_range_pairs = 0;
     bool mixed = false;
     wave1d_nufft_t nu_s = nullptr, nu_r = nullptr;
     int64_t *nu_perm_s = nullptr, *nu_perm_r = nullptr;
@@ -218,6 +227,21 @@ int upload_receivers(wave1d_plan_t p) {
     d.rc_i0 = i32;
     if ((rc = upload(p, hp.rc_ker, &f64))) return rc;
     d.rc_ker = f64;
+    if (p->range) {
+        // receivers' local part over index windows: their positions, windows and chunk partials
+        if ((rc = upload(p, hp.xr, &f64))) return rc;
+        d.xr = f64;
+        if ((rc = upload(p, hp.r_win, &i32))) return rc;
+        p->rd.r_win = i32;
+        int64_t most = 1;
+        for (int64_t r = 0; r < d.R; r++) most = std::max<int64_t>(most, hp.r_win[2 * r + 1] - hp.r_win[2 * r]);
+        p->rd.rchunks = (int)((most + 255) / 256);
+        if ((rc = zeros(p, &p->rd.r_part, (size_t)p->rd.rchunks * std::max<int64_t>(1, d.R)))) return rc;
+        if ((rc = zeros(p, &d.uHr, (size_t)std::max<int64_t>(1, d.R)))) return rc;
+        if ((rc = zeros(p, &d.rec_hist, (size_t)p->chunk * std::max<int64_t>(1, d.R)))) return rc;
+        d.r_nitems = 0;
+        return WAVE1D_OK;
+    }
     ItemsDev it;
     if ((rc = upload_items(p, hp.ritems, it))) return rc;
     d.r_mfirst = hp.ritems.m_first;
@@ -259,15 +283,6 @@ int upload_receivers(wave1d_plan_t p) {
     d.r0p_w = f64b;
     if ((rc = zeros(p, &d.uHr, (size_t)std::max<int64_t>(1, d.R)))) return rc;
     if ((rc = zeros(p, &d.rec_hist, (size_t)p->chunk * std::max<int64_t>(1, d.R)))) return rc;
-    if (p->fly) {
-        std::vector<int8_t> rn;
-        item_source_counts(hp.rrows, hp.ritems, rn);
-        int8_t* rnd;
-        double* xrd;
-        if ((rc = upload(p, rn, &rnd)) || (rc = upload(p, hp.xr, &xrd))) return rc;
-        p->fly_t.r_nsrc = rnd;
-        p->fly_t.xr = xrd;
-    }
     return WAVE1D_OK;
 }
 
@@ -325,8 +340,8 @@ int enqueue_step(wave1d_plan_t p, int64_t n, const double* g_ext, double* sig_hi
         cudaStreamWaitEvent(p->s2, p->ev_fork, 0);
         k_local_items<<<local_grid(p), T, 0, p->s2>>>(d);
         cudaEventRecord(p->ev_join, p->s2);
-    } else if (p->fly) {
-        k_local_fly<<<local_grid(p), T, 0, s>>>(d, p->fly_t);
+    } else if (p->range) {
+        k_rs_local<<<p->rd.nblk, kRsTargets, p->rs_smem, s>>>(d, p->rd);
     } else {
         k_local_items<<<local_grid(p), T, 0, s>>>(d);
     }
@@ -384,6 +399,18 @@ int enqueue_step(wave1d_plan_t p, int64_t n, const double* g_ext, double* sig_hi
     }
     mark(WAVE1D_STAGE_SOLVE);
     if (fork) cudaStreamWaitEvent(s, p->ev_join, 0);
+    if (p->range) {
+        const unsigned rows = blocks(P.M, T), sweeps = (unsigned)std::min<int64_t>(blocks(P.M * 32, T), 16 * (int64_t)p->sms);
+        k_rs_solve_init<<<rows, T, 0, s>>>(d, p->rd);
+        for (int it = 1; it <= kRsMaxIter; it++) k_rs_jacobi<<<sweeps, T, 0, s>>>(d, p->rd, it);
+        k_rs_store<<<rows, T, 0, s>>>(d, p->rd);
+        mark(WAVE1D_STAGE_RECEIVERS);
+        if (P.R > 0) k_rs_receivers<<<dim3((unsigned)p->rd.rchunks, (unsigned)P.R), T, 0, s>>>(d, p->rd);
+        k_rs_finish<<<1, 32, 0, s>>>(d, p->rd);
+        mark(WAVE1D_NSTAGE);
+        CK(cudaGetLastError());
+        return WAVE1D_OK;
+    }
     k_solve<<<blocks((d.n_sgroups + d.n_big) * 32, T), T, 0, s>>>(d);
     mark(WAVE1D_STAGE_RECEIVERS);      // the receivers are read out by the solve's last block
     mark(WAVE1D_NSTAGE);
@@ -396,6 +423,8 @@ int check_status(wave1d_plan_t p) {
     CK(cudaMemcpyAsync(&st, p->dp.status, sizeof(int), cudaMemcpyDeviceToHost, p->s));
     CK(cudaStreamSynchronize(p->s));
     if (st == WAVE1D_ETIMEOUT) return fail(st, "a bounded wait between the blocks of the step kernel ran out");
+    if (st == WAVE1D_ENOTCONV)
+        return fail(st, "the Jacobi sweeps of the implicit solve did not converge (local_weights = 1)");
     if (st != 0) return fail(st, "a density became non-finite during the march");
     return WAVE1D_OK;
 }
@@ -484,6 +513,7 @@ const char* wave1d_strerror(int status) {
         case WAVE1D_EDONE: return "all planned steps taken";
         case WAVE1D_EUNSUPPORTED: return "size not supported by this build";
         case WAVE1D_ETIMEOUT: return "a bounded wait of the step kernel ran out";
+        case WAVE1D_ENOTCONV: return "the iterative implicit solve did not converge";
         default: return "unknown status";
     }
 }
@@ -506,7 +536,7 @@ int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double d
     if (o.precision != 0 && o.precision != 1) return fail(WAVE1D_EINVAL, "precision must be 0 (FP64) or 1 (mixed)");
     if (o.local_weights != 0 && o.local_weights != 1)
         return fail(WAVE1D_EINVAL, "local_weights must be 0 (stored) or 1 (computed per pair)");
-    if (o.local_weights == 1) o.step_kernel = 0;   // the computed weights run in their own launch
+    if (o.local_weights == 1) o.step_kernel = 0;   // the range-mode step is its own sequence of launches
     if (o.precision == 1) {
         if (o.nufft_w != 0 && o.nufft_w != 7) return fail(WAVE1D_EINVAL, "mixed precision uses the width-7 NUFFT kernel");
         o.nufft_w = 7;          // the FP32 kernels' width: the plan's grid, kernel and deconvolution match them
@@ -517,7 +547,11 @@ int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double d
     if (!p) return fail(WAVE1D_ENOMEM, "host allocation");
     std::string err;
     int rc = build_host_plan(x, beta, M, bc, dt, Nt, tol, o.p, o.gamma, o.W, o.NL, o.Ng, o.nufft_w,
-                             o.rbc_period, o.max_block, o.max_local_bytes, p->hp, err);
+                             o.rbc_period, o.max_block, o.max_local_bytes, p->hp, err, o.local_weights == 1);
+    if (rc == WAVE1D_OK && o.local_weights == 1 && p->hp.rt.iv_dt >= p->hp.rt.nint) {
+        rc = WAVE1D_EINVAL;
+        err = "local_weights = 1 needs a window of at least two steps (W >= 2)";
+    }
     if (rc == WAVE1D_OK) {
         double none = 0.0;
         rc = build_receivers(p->hp, &none, 0, err);
@@ -528,6 +562,7 @@ int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double d
     }
     const Params& P = p->hp.P;
     p->chunk = P.bc == WAVE1D_FREE ? P.rbc_period : 32;
+    p->range = o.local_weights == 1;
     p->user = (cudaStream_t)o.stream;
     auto cleanup = [&](int code) {
         wave1d_destroy(p);
@@ -628,29 +663,62 @@ int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double d
     UP(hp.sp_i0, sp_i0, i32);
     UP(hp.sp_ker, sp_ker, f64);
     if ((rc = zeros(p, &d.uH, (size_t)P.M))) return cleanup(rc);
-    if (o.local_weights == 1) {
-        // weights computed per pair: the series table and the items' real source counts go to the
-        // device instead of the stored weights
-        p->fly = true;
-        LocalFit fit;
-        build_local_fit(P, 7, fit);
-        std::vector<int8_t> ln;
-        item_source_counts(hp.lrows, hp.litems, ln);
-        double *bpd, *cd;
-        int *mlod, *mhid;
-        int8_t* lnd;
-        if ((rc = upload(p, fit.bp, &bpd)) || (rc = upload(p, fit.coef, &cd)) || (rc = upload(p, fit.mlo, &mlod)) ||
-            (rc = upload(p, fit.mhi, &mhid)) || (rc = upload(p, ln, &lnd)))
-            return cleanup(rc);
-        p->fly_t.bp = bpd;
-        p->fly_t.coef = cd;
-        p->fly_t.mlo = mlod;
-        p->fly_t.mhi = mhid;
-        p->fly_t.nint = (int)fit.bp.size() - 1;
-        p->fly_t.deg = fit.deg;
-        p->fly_t.nm = fit.nm;
-        p->fly_t.l_nsrc = lnd;
-        std::vector<float>().swap(hp.litems.w);          // no stored spring weights on the device
+    if (p->range) {
+        // the weights' polynomials, positions as float pairs, index windows, the implicit part's
+        // weights (computed on the device below) and the solver's work arrays
+        const RangeTables& rt = hp.rt;
+        RangeDev& rd = p->rd;
+        rd.nint = rt.nint;
+        rd.nm = rt.nm;
+        rd.iv_dt = rt.iv_dt;
+        rd.nblk = (int)((P.M + kRsTargets - 1) / kRsTargets);
+        rd.delta = P.delta;
+        float* f32;
+        int32_t* r32;
+        int64_t* r64;
+        double* r64f;
+        std::vector<int32_t> mr(rt.mr.begin(), rt.mr.end()), mr0(rt.mr0.begin(), rt.mr0.end());
+        if ((rc = upload(p, rt.bp2, &f32))) return cleanup(rc);
+        rd.bp2 = f32;
+        if ((rc = upload(p, rt.mid2, &f32))) return cleanup(rc);
+        rd.mid2 = f32;
+        if ((rc = upload(p, rt.ih, &f32))) return cleanup(rc);
+        rd.ih = f32;
+        if ((rc = upload(p, rt.coef, &f32))) return cleanup(rc);
+        rd.coef = f32;
+        if ((rc = upload(p, mr, &r32))) return cleanup(rc);
+        rd.mr = r32;
+        if ((rc = upload(p, mr0, &r32))) return cleanup(rc);
+        rd.mr0 = r32;
+        if ((rc = upload(p, rt.bp, &r64f))) return cleanup(rc);
+        rd.bp = r64f;
+        if ((rc = upload(p, rt.mid, &r64f))) return cleanup(rc);
+        rd.mid = r64f;
+        if ((rc = upload(p, rt.cheb, &r64f))) return cleanup(rc);
+        rd.cheb = r64f;
+        if ((rc = upload(p, hp.x2, &f32))) return cleanup(rc);
+        rd.x2 = f32;
+        if ((rc = upload(p, hp.blk_win, &r32))) return cleanup(rc);
+        rd.blk_win = r32;
+        if ((rc = upload(p, hp.nb_lo, &r32))) return cleanup(rc);
+        rd.nb_lo = r32;
+        if ((rc = upload(p, hp.nb_cnt, &r32))) return cleanup(rc);
+        rd.nb_cnt = r32;
+        if ((rc = upload(p, hp.nb_off, &r64))) return cleanup(rc);
+        rd.nb_off = r64;
+        if ((rc = dalloc(p, &rd.nb_w, 2 * (size_t)std::max<int64_t>(1, hp.nb_off[P.M])))) return cleanup(rc);
+        if ((rc = dalloc(p, &rd.diag, (size_t)P.M))) return cleanup(rc);
+        for (int i = 0; i < 2; i++) {
+            if ((rc = zeros(p, &rd.it64[i], (size_t)P.M))) return cleanup(rc);
+            if ((rc = zeros(p, &rd.it2[i], 2 * (size_t)P.M))) return cleanup(rc);
+        }
+        if ((rc = zeros(p, &rd.stats, 2 * (size_t)(kRsMaxIter + 1)))) return cleanup(rc);
+        if ((rc = zeros(p, &rd.iters, 1))) return cleanup(rc);
+        p->rs_smem = rs_local_smem(rt.nint, rt.nm);
+        if (cudaFuncSetAttribute(k_rs_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->rs_smem) !=
+            cudaSuccess)
+            return cleanup(fail(WAVE1D_ECUDA, "cannot size the shared memory of the range-mode local sum"));
+        p->info_range_pairs = hp.range_pairs;
     }
     {
         ItemsDev it;
@@ -719,6 +787,11 @@ int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double d
         if ((rc = dalloc(p, &p->nu_u, (size_t)P.M))) return cleanup(rc);
     }
 #undef UP
+    if (p->range) {
+        // the implicit part's weights (beta_j / 2) Q_0(d_jl) of every spring's dt-window
+        k_rs_nearby_weights<<<(unsigned)std::min<int64_t>((P.M + 7) / 8, 64 * (int64_t)p->sms), 256, 0, p->s>>>(d, p->rd);
+        if (cudaGetLastError() != cudaSuccess) return cleanup(fail(WAVE1D_ECUDA, "nearby weights kernel"));
+    }
     if ((rc = leave(p))) return cleanup(rc);
     if (cudaStreamSynchronize(p->s) != cudaSuccess) return cleanup(fail(WAVE1D_ECUDA, "plan upload failed"));
     // the uploads have completed: release the host copies of the weights
@@ -1006,9 +1079,9 @@ int wave1d_get_info(wave1d_plan_t p, wave1d_info* info) {
     info->tol = P.tol;
     info->b = P.b;
     info->delta = P.delta;
-    info->local_pairs = p->info_pairs;
+    info->local_pairs = p->range ? p->info_range_pairs : p->info_pairs;
     info->local_weights = p->info_weights;
-    info->nearby_pairs = p->info_nearby;
+    info->nearby_pairs = p->range ? p->hp.nb_off[p->hp.P.M] : p->info_nearby;
     info->blocks = (int64_t)p->hp.blk_ptr.size() - 1;
     info->max_block = p->hp.max_block;
     info->device_bytes = p->bytes;
@@ -1136,7 +1209,7 @@ int wave1d_adjoint(wave1d_plan_t p, int64_t nsteps, const double* sigma, const d
                    double* grad_beta, double* grad_g) {
     if (!p || !sigma || nsteps < 1 || (!grad_beta && !grad_g))
         return fail(WAVE1D_EINVAL, "need a plan, sigma, nsteps >= 1 and grad_beta or grad_g");
-    if (p->fly) return fail(WAVE1D_EUNSUPPORTED, "the reverse march reads stored local weights (local_weights = 0)");
+    if (p->range) return fail(WAVE1D_EUNSUPPORTED, "the reverse march reads stored local weights (local_weights = 0)");
     const HostPlan& hp = p->hp;
     const Params& P = hp.P;
     if (nsteps > P.Nt) return fail(WAVE1D_EINVAL, "nsteps beyond the Nt of the plan");

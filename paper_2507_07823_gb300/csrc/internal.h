@@ -65,6 +65,30 @@ struct LocalItems {
 };
 int build_items(const LocalRows& rows, LocalItems& items);
 
+// Local weights as polynomials of the pair distance (plans opened with opts.local_weights = 1,
+// which hold no per-pair data).  Q_m(d) is smooth between the breakpoints of the Gauss-Legendre
+// rule (a node crossing a multiple of dt, and d = dt, Sec. 4.1); on interval iv it is a degree-7
+// polynomial of z = (d - mid_iv) ih_iv with ih_iv = fl32(1 / half-width): the device computes z
+// with that single-precision scale, and the series are fitted for exactly that map.
+struct RangeTables {
+    int nint = 0, nm = 0, iv_dt = 0;   // intervals, m = 0 .. nm - 1, index of the breakpoint dt
+    std::vector<double> bp;            // nint + 1 breakpoints, bp[0] = 0, bp[iv_dt] = dt, bp[nint] = delta
+    std::vector<float> bp2;            // the same as (hi, lo) pairs
+    std::vector<double> mid;           // per interval: midpoint (the value of its pair mid2)
+    std::vector<float> mid2;           // per interval: (hi, lo)
+    std::vector<float> ih;             // per interval: fl32(1 / half-width)
+    std::vector<int32_t> mr;           // per interval: first and last m >= 1 with a non-zero series
+    std::vector<int32_t> mr0;          // per interval: first and last m >= 0 with a non-zero series
+    std::vector<float> coef;           // [iv][m][12]: monomial coefficients of z, a0 .. a3 as (hi, lo)
+                                       //   pairs, a4 .. a7 single
+    std::vector<double> cheb;          // [iv][m][8]: Chebyshev coefficients in z (FP64)
+};
+void build_range_tables(const Params& P, RangeTables& out);
+// The plan's weight rule itself at each distance, Q[i * (m_max + 1) + m] (for checks).
+void local_weights_exact(const Params& P, const std::vector<double>& d, std::vector<double>& Q);
+// targets per block of the range-mode local sum (one per thread)
+constexpr int kRsTargets = 256;
+
 struct HostPlan {
     Params P;
     std::vector<int32_t> perm;         // internal index -> caller index
@@ -118,6 +142,21 @@ struct HostPlan {
     std::vector<int32_t> sg_smax;      // [group]: largest block of the group
     std::vector<int64_t> big_blk;      // blocks of more than 32 members, one entry per 32 rows
     std::vector<int32_t> big_row0;     //   (a single entry above 256 members): first row
+    // no pair lists (opts.local_weights = 1): the weights as polynomials of the distance, the
+    // positions as (hi, lo) float pairs, and index windows into the sorted springs.  Windows are
+    // "extended" indices e in [-M, 2M) in the periodic box (spring e mod M shifted by
+    // 2 pi floor(e / M)), in [0, M) in free space.
+    bool range = false;
+    RangeTables rt;
+    std::vector<float> x2;             // springs: (hi, lo)
+    std::vector<int32_t> nb_lo, nb_cnt;// springs: window of the sources closer than dt (FP64 test
+                                       //   |x_e - x_j| < dt), the implicit part of eq. linearSystem
+    std::vector<int64_t> nb_off;       // M + 1: offsets of their weights
+    std::vector<int32_t> blk_win;      // per block of kRsTargets targets: first source of the delta
+                                       //   window, first source at or right of the first target,
+                                       //   first source right of the last target, end of the window
+    std::vector<int32_t> r_win;        // receivers: [lo, hi) window of sources within delta
+    int64_t range_pairs = 0;           // (target, source) pairs closer than delta (springs)
     // radiation projection: grid points i of the 2K-point grid that are rolled off
     std::vector<int32_t> rbc_idx;      // 4W grid indices
     std::vector<double> rbc_x;         // their positions
@@ -135,7 +174,7 @@ constexpr int kStepThreads = 256;
 int build_host_plan(const double* x, const double* beta, int64_t M, int bc, double dt, int64_t Nt,
                     double tol, int p, double gamma, int W, int NL, int Ng, int nufft_w,
                     int rbc_period, int max_block, int64_t max_local_bytes, HostPlan& hp,
-                    std::string& err);
+                    std::string& err, bool range = false);
 int build_receivers(HostPlan& hp, const double* xr, int64_t R, std::string& err);
 int build_rows(const LocalCSR& csr, int m_first, LocalRows& rows, std::string& err);
 
@@ -243,10 +282,47 @@ struct DevPlan {
     const double* rbc_dphi;
     double* rbc_uv;           // [4W][4] : u, v before; du, dv
     double rbc_h;
+    // receivers' positions (device copy)
+    const double* xr;
     // one-launch step kernel: blocks [0, hist_blocks) start with the history pipeline;
     // bar[0..15] are its work and barrier counters (zero between steps)
     int hist_blocks;
     unsigned* bar;
 };
+
+// Device view of the range-mode tables (plans opened with opts.local_weights = 1), passed by value
+// beside DevPlan.
+struct RangeDev {
+    int nint, nm, iv_dt, nblk;
+    double delta;
+    const float* bp2;           // nint + 1 breakpoints (hi, lo)
+    const float* mid2;          // nint midpoints (hi, lo)
+    const float* ih;            // nint scales
+    const int32_t* mr;          // nint x 2: m range of the local sum (m >= 1)
+    const int32_t* mr0;         // nint x 2: m range with m = 0
+    const float* coef;          // [iv][m][12]: a0 .. a3 as (hi, lo) pairs, a4 .. a7
+    const double* bp;           // nint + 1 breakpoints (FP64)
+    const double* mid;          // nint midpoints (FP64 value of mid2)
+    const double* cheb;         // [iv][m][8] Chebyshev coefficients in z (FP64)
+    const float* x2;            // M positions (hi, lo)
+    const int32_t* blk_win;     // [block][4] (see HostPlan::blk_win)
+    const int32_t* nb_lo;       // M
+    const int32_t* nb_cnt;      // M
+    const int64_t* nb_off;      // M + 1
+    float* nb_w;                // (beta_j / 2) Q_0(d_jl) as (hi, lo), the entry l = j zero
+    double* diag;               // M: 1 + (beta_j / 2) Q_0(0)
+    double* it64[2];            // Jacobi iterates (FP64) and the same as (hi, lo) pairs
+    float* it2[2];
+    unsigned long long* stats;  // [kRsMaxIter + 1][2]: max |change|, max |sigma| of each iterate (bits)
+    int* iters;                 // Jacobi sweeps of the last step
+    const int32_t* r_win;       // [R][2]
+    double* r_part;             // [R][rchunks]: receivers' local sums by source chunk
+    int rchunks;
+};
+// Jacobi sweeps of the implicit solve at most, and the stopping rule: max |change| <=
+// kRsTol max |sigma| (the sweeps contract by max_j sum_l |S_jl| / (1 + S_jj), about 0.14 for a
+// million clustered springs at dt = 5e-4)
+constexpr int kRsMaxIter = 40;
+constexpr double kRsTol = 1e-14;
 
 }  // namespace wave1d

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <numeric>
@@ -10,7 +11,6 @@
 
 #include "adjoint_host.h"
 #include "internal.h"
-#include "local_fit.h"
 #include "nufft_host.h"
 #include "../../include/wave1d.h"
 
@@ -483,11 +483,17 @@ void nufft_ranges(const std::vector<int32_t>& i0, const int64_t* offsets, int n_
     }
 }
 
+namespace {
+int build_local_and_blocks(const Params& P, const Window& win, HostPlan& hp, int max_block,
+                           int64_t max_local_bytes, std::string& err);
+void range_windows(HostPlan& hp);
+}  // namespace
+
 // ---------------------------------------------------------------------------------------------
 int build_host_plan(const double* x_in, const double* beta_in, int64_t M, int bc, double dt,
                     int64_t Nt, double tol, int p, double gamma, int W, int NL, int Ng, int nufft_w,
                     int rbc_period, int max_block, int64_t max_local_bytes, HostPlan& hp,
-                    std::string& err) {
+                    std::string& err, bool range) {
     Params& P = hp.P;
     P.M = M;
     P.Nt = Nt;
@@ -652,7 +658,53 @@ int build_host_plan(const double* x_in, const double* beta_in, int64_t M, int bc
             }
     }
 
-    // local part (Sec. 4.1) and nearby blocks (eq. linearSystem)
+    if (range) {
+        // no pair lists: positions as float pairs, index windows, the weights as polynomials
+        hp.range = true;
+        build_range_tables(P, hp.rt);
+        hp.x2.resize(2 * (size_t)M);
+        for (int64_t j = 0; j < M; j++) {
+            const float h = (float)hp.x[j];
+            hp.x2[2 * j] = h;
+            hp.x2[2 * j + 1] = (float)(hp.x[j] - (double)h);
+        }
+        range_windows(hp);
+    } else {
+        int rc = build_local_and_blocks(P, win, hp, max_block, max_local_bytes, err);
+        if (rc) return rc;
+    }
+
+    // radiation projection tables (Sec. 4.4): grid x_i = i h (i < K), (i - 2K) h (i >= K)
+    if (bc == WAVE1D_FREE) {
+        Window swin(P.delta_s, P.b);
+        hp.rbc_idx.clear();
+        hp.rbc_x.clear();
+        hp.rbc_phi.clear();
+        hp.rbc_dphi.clear();
+        for (int i = P.K - 2 * P.W; i < P.K; i++) {
+            double xg = i * P.h_rbc, arg = kPi - P.delta_s - xg;
+            hp.rbc_idx.push_back(i);
+            hp.rbc_x.push_back(xg);
+            hp.rbc_phi.push_back(swin.phi(arg));
+            hp.rbc_dphi.push_back(swin.dphi(arg));
+        }
+        for (int i = P.K; i < P.K + 2 * P.W; i++) {
+            double xg = (i - 2 * P.K) * P.h_rbc, arg = kPi - P.delta_s + xg;
+            hp.rbc_idx.push_back(i);
+            hp.rbc_x.push_back(xg);
+            hp.rbc_phi.push_back(swin.phi(arg));
+            hp.rbc_dphi.push_back(swin.dphi(arg));
+        }
+    }
+    return WAVE1D_OK;
+}
+
+namespace {
+// Local part (Sec. 4.1) with stored weights and the inverted blocks of springs closer than dt
+// (eq. linearSystem).
+int build_local_and_blocks(const Params& P, const Window& win, HostPlan& hp, int max_block,
+                           int64_t max_local_bytes, std::string& err) {
+    const int64_t M = P.M;
     std::vector<std::vector<std::pair<int32_t, double>>> nearby;
     int rc = build_local(P, win, hp.x, hp.x, false, hp.loc, &nearby, max_local_bytes, err);
     if (rc) return rc;
@@ -773,31 +825,79 @@ int build_host_plan(const double* x_in, const double* beta_in, int64_t M, int bc
             used += (int)sz;
         }
     }
-
-    // radiation projection tables (Sec. 4.4): grid x_i = i h (i < K), (i - 2K) h (i >= K)
-    if (bc == WAVE1D_FREE) {
-        Window swin(P.delta_s, P.b);
-        hp.rbc_idx.clear();
-        hp.rbc_x.clear();
-        hp.rbc_phi.clear();
-        hp.rbc_dphi.clear();
-        for (int i = P.K - 2 * P.W; i < P.K; i++) {
-            double xg = i * P.h_rbc, arg = kPi - P.delta_s - xg;
-            hp.rbc_idx.push_back(i);
-            hp.rbc_x.push_back(xg);
-            hp.rbc_phi.push_back(swin.phi(arg));
-            hp.rbc_dphi.push_back(swin.dphi(arg));
-        }
-        for (int i = P.K; i < P.K + 2 * P.W; i++) {
-            double xg = (i - 2 * P.K) * P.h_rbc, arg = kPi - P.delta_s + xg;
-            hp.rbc_idx.push_back(i);
-            hp.rbc_x.push_back(xg);
-            hp.rbc_phi.push_back(swin.phi(arg));
-            hp.rbc_dphi.push_back(swin.dphi(arg));
-        }
-    }
     return WAVE1D_OK;
 }
+
+// position of extended source index e (periodic: spring e mod M shifted by 2 pi floor(e / M));
+// every window test of the range mode uses this expression, on the host and on the device
+inline double x_ext(const std::vector<double>& x, int64_t M, int64_t e) {
+    if (e < 0) return x[e + M] - 2.0 * kPi;
+    if (e >= M) return x[e - M] + 2.0 * kPi;
+    return x[e];
+}
+
+// first extended index in [lo, hi) whose position satisfies pred (pred false .. true in index order)
+template <class F>
+int64_t first_true(int64_t lo, int64_t hi, F pred) {
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (pred(mid)) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+// Index windows of the range mode: per spring the sources closer than dt (the implicit block of
+// eq. linearSystem, decided by |x_e - x_j| < dt in FP64 exactly as the device evaluates it), and
+// per block of kRsTargets targets the sources within delta of any of them (a superset: the device
+// decides each pair from the float-pair positions).
+void range_windows(HostPlan& hp) {
+    const Params& P = hp.P;
+    const int64_t M = P.M;
+    const bool per = P.bc == WAVE1D_PERIODIC;
+    const int64_t elo = per ? -M : 0, ehi = per ? 2 * M : M;
+    const std::vector<double>& x = hp.x;
+    hp.nb_lo.assign(M, 0);
+    hp.nb_cnt.assign(M, 0);
+    parallel_for(M, [&](int64_t a, int64_t b) {
+        for (int64_t j = a; j < b; j++) {
+            // |x_e - x_j| < dt is monotone on each side of j
+            const int64_t lo = first_true(std::max(elo, j - M), j + 1,
+                                          [&](int64_t e) { return std::fabs(x_ext(x, M, e) - x[j]) < P.dt; });
+            const int64_t hi = first_true(j, std::min(ehi, j + M),
+                                          [&](int64_t e) { return !(std::fabs(x_ext(x, M, e) - x[j]) < P.dt); });
+            hp.nb_lo[j] = (int32_t)lo;
+            hp.nb_cnt[j] = (int32_t)(hi - lo);
+        }
+    });
+    hp.nb_off.assign(M + 1, 0);
+    for (int64_t j = 0; j < M; j++) hp.nb_off[j + 1] = hp.nb_off[j] + hp.nb_cnt[j];
+    // pairs closer than delta (reported; the device never lists them)
+    std::vector<int64_t> cnt(M, 0);
+    parallel_for(M, [&](int64_t a, int64_t b) {
+        for (int64_t j = a; j < b; j++) {
+            const int64_t lo = first_true(std::max(elo, j - M), j + 1,
+                                          [&](int64_t e) { return std::fabs(x_ext(x, M, e) - x[j]) < P.delta; });
+            const int64_t hi = first_true(j, std::min(ehi, j + M),
+                                          [&](int64_t e) { return !(std::fabs(x_ext(x, M, e) - x[j]) < P.delta); });
+            cnt[j] = hi - lo;
+        }
+    });
+    hp.range_pairs = 0;
+    for (int64_t j = 0; j < M; j++) hp.range_pairs += cnt[j];
+    const int64_t nblk = (M + kRsTargets - 1) / kRsTargets;
+    const double reach = P.delta * (1.0 + 1e-12) + 1e-13;
+    hp.blk_win.assign(4 * nblk, 0);
+    for (int64_t b = 0; b < nblk; b++) {
+        const int64_t j0 = b * kRsTargets, j1 = std::min(M, j0 + kRsTargets) - 1;
+        const double xa = x[j0], xb = x[j1];
+        hp.blk_win[4 * b + 0] = (int32_t)first_true(elo, ehi, [&](int64_t e) { return x_ext(x, M, e) > xa - reach; });
+        hp.blk_win[4 * b + 1] = (int32_t)first_true(elo, ehi, [&](int64_t e) { return x_ext(x, M, e) >= xa; });
+        hp.blk_win[4 * b + 2] = (int32_t)first_true(elo, ehi, [&](int64_t e) { return x_ext(x, M, e) > xb; });
+        hp.blk_win[4 * b + 3] = (int32_t)first_true(elo, ehi, [&](int64_t e) { return x_ext(x, M, e) >= xb + reach; });
+    }
+}
+}  // namespace
 
 // Regroup CSR local weights into m-major rows (see LocalRows).  Within a row the sources are
 // sorted by (m_lo, source); for each m the active sources are those with m_lo <= m, a prefix.
@@ -962,6 +1062,21 @@ int build_receivers(HostPlan& hp, const double* xr, int64_t R, std::string& err)
         }
         hp.xr[r] = v;
     }
+    if (hp.range) {
+        // the receivers' local part is summed over index windows (sources within delta)
+        const int64_t M = P.M;
+        const bool per = P.bc == WAVE1D_PERIODIC;
+        const int64_t elo = per ? -M : 0, ehi = per ? 2 * M : M;
+        const double reach = P.delta * (1.0 + 1e-12) + 1e-13;
+        hp.r_win.assign(2 * (size_t)R, 0);
+        for (int64_t r = 0; r < R; r++) {
+            const double xv = hp.xr[r];
+            hp.r_win[2 * r] = (int32_t)first_true(elo, ehi, [&](int64_t e) { return x_ext(hp.x, M, e) > xv - reach; });
+            hp.r_win[2 * r + 1] = (int32_t)first_true(elo, ehi, [&](int64_t e) { return x_ext(hp.x, M, e) >= xv + reach; });
+        }
+        spread_weights(P, hp.xr, hp.rc_i0, hp.rc_ker);
+        return WAVE1D_OK;
+    }
     Window win(P.delta, P.b);
     int rc = build_local(P, win, hp.xr, hp.x, true, hp.rloc, nullptr, INT64_MAX, err);
     if (rc) return rc;
@@ -986,16 +1101,6 @@ int build_receivers(HostPlan& hp, const double* xr, int64_t R, std::string& err)
     return WAVE1D_OK;
 }
 
-void item_source_counts(const LocalRows& rows, const LocalItems& items, std::vector<int8_t>& nsrc) {
-    const int64_t T = (int64_t)items.item_ptr.size() - 1;
-    nsrc.assign(items.row.size(), 0);
-    for (int64_t j = 0; j < T; j++) {
-        const int64_t ns = rows.src_off[j + 1] - rows.src_off[j];
-        for (int64_t c = items.item_ptr[j]; c < items.item_ptr[j + 1]; c++)
-            nsrc[c] = (int8_t)std::min<int64_t>(32, ns - 32 * (c - items.item_ptr[j]));
-    }
-}
-
 void local_weights_exact(const Params& P, const std::vector<double>& d, std::vector<double>& Q) {
     Window win(P.delta, P.b);
     LocalRule rule;
@@ -1005,70 +1110,128 @@ void local_weights_exact(const Params& P, const std::vector<double>& d, std::vec
     for (size_t i = 0; i < d.size(); i++) rule.weights(d[i], &Q[i * nm]);
 }
 
-void build_local_fit(const Params& P, int deg, LocalFit& out) {
-    out = LocalFit();
-    out.deg = deg;
-    out.nm = P.m_max + 1;
-    // breakpoints: node i of the rule, d + (delta - d) c_i with c_i = (x_i + 1) / 2, on k dt
+// Breakpoints of the local rule (Sec. 4.1): node i of the N_L-point Gauss-Legendre rule over
+// [d, delta] sits at s = d + (delta - d) c_i, c_i = (x_i + 1) / 2, and switches its p-point stencil
+// where s crosses a multiple of dt; d = dt switches m_min.  Breakpoints closer than 1e-9 dt are
+// merged (the kink between them moves a weight by at most ~1e-11 of its size, for distances
+// within 1e-9 dt of it); dt itself is kept exactly.  On every interval each Q_m (m = 0 .. m_max)
+// is interpolated at the 8 Chebyshev points of the first kind of z = (d - mid) ih, where ih =
+// fl32(1 / half-width) is the scale the device uses, then written in monomials of z.
+constexpr double kRangeMaxWidth = 0.15;
+
+void build_range_tables(const Params& P, RangeTables& rt) {
+    rt = RangeTables();
+    rt.nm = P.m_max + 1;
     std::vector<double> gx, gw;
     gauss_legendre(P.NL, gx, gw);
-    std::vector<double> bp = {0.0, P.dt, P.delta};
-    for (double x : gx) {
-        const double c = 0.5 * (x + 1.0);
+    std::vector<double> cand = {P.dt};
+    for (double xg : gx) {
+        const double c = 0.5 * (xg + 1.0);
         for (int k = 0; k <= P.W + 1; k++) {
             const double d = ((double)k * P.dt - P.delta * c) / (1.0 - c);
-            if (d > 0.0 && d < P.delta) bp.push_back(d);
+            if (d > 0.0 && d < P.delta) cand.push_back(d);
         }
     }
-    std::sort(bp.begin(), bp.end());
-    for (double v : bp)
-        if (out.bp.empty() || v - out.bp.back() > 1e-15 * P.delta) out.bp.push_back(v);
-    out.bp.back() = P.delta;
-    // Chebyshev series on every interval, fitted at its first-kind Chebyshev points
-    const int n = (int)out.bp.size() - 1, np = deg + 1, nm = out.nm;
-    std::vector<double> dn((size_t)n * np);
-    for (int iv = 0; iv < n; iv++)
-        for (int j = 0; j < np; j++) {
-            const double z = std::cos(kPi * (j + 0.5) / np);
-            dn[(size_t)iv * np + j] = out.bp[iv] + 0.5 * (out.bp[iv + 1] - out.bp[iv]) * (z + 1.0);
+    std::sort(cand.begin(), cand.end());
+    const double gap = 1e-9 * P.dt;
+    rt.bp.push_back(0.0);
+    for (double v : cand) {
+        if (std::fabs(v - P.dt) <= gap && v != P.dt) continue;       // dt stays exact
+        if (v - rt.bp.back() <= gap) {
+            if (v == P.dt) rt.bp.back() = P.dt;                       // replace a neighbour by dt
+            continue;
         }
+        if (P.delta - v <= gap) continue;
+        rt.bp.push_back(v);
+    }
+    rt.bp.push_back(P.delta);
+    {
+        // intervals wider than kRangeMaxWidth dt are cut into equal parts: the curvature
+        // coefficients (single floats on the device) shrink with the width as width^r
+        const char* env = std::getenv("WAVE1D_RANGE_WIDTH");
+        const double cap = (env ? std::atof(env) : kRangeMaxWidth) * P.dt;
+        std::vector<double> cut = {rt.bp[0]};
+        for (size_t i = 1; i < rt.bp.size(); i++) {
+            const double a = rt.bp[i - 1], b = rt.bp[i];
+            const int parts = (int)std::ceil((b - a) / cap - 1e-9);
+            for (int q = 1; q < parts; q++) cut.push_back(a + (b - a) * q / parts);
+            cut.push_back(b);
+        }
+        rt.bp.swap(cut);
+    }
+    rt.nint = (int)rt.bp.size() - 1;
+    rt.iv_dt = (int)(std::find(rt.bp.begin(), rt.bp.end(), P.dt) - rt.bp.begin());
+    const int n = rt.nint, nm = rt.nm, np = 8;
+    rt.bp2.resize(2 * (size_t)(n + 1));
+    for (int i = 0; i <= n; i++) {
+        const float h = (float)rt.bp[i];
+        rt.bp2[2 * i] = h;
+        rt.bp2[2 * i + 1] = (float)(rt.bp[i] - (double)h);
+    }
+    rt.mid.resize(n);
+    rt.mid2.resize(2 * (size_t)n);
+    rt.ih.resize(n);
+    std::vector<double> dn((size_t)n * np);
+    double zk[np];
+    for (int k = 0; k < np; k++) zk[k] = std::cos(kPi * (k + 0.5) / np);
+    for (int iv = 0; iv < n; iv++) {
+        const double a = rt.bp[iv], b = rt.bp[iv + 1], mid = 0.5 * (a + b);
+        const float mh = (float)mid, ml = (float)(mid - (double)mh);
+        rt.mid2[2 * iv] = mh;
+        rt.mid2[2 * iv + 1] = ml;
+        rt.mid[iv] = (double)mh + (double)ml;
+        rt.ih[iv] = (float)(2.0 / (b - a));
+        for (int k = 0; k < np; k++) dn[(size_t)iv * np + k] = rt.mid[iv] + zk[k] / (double)rt.ih[iv];
+    }
     std::vector<double> Q;
     local_weights_exact(P, dn, Q);
-    out.coef.assign((size_t)n * nm * np, 0.0);
-    for (int iv = 0; iv < n; iv++)
-        for (int m = 0; m < nm; m++)
+    // Chebyshev coefficients, then monomials: T_{r+1} = 2 z T_r - T_{r-1}
+    double T[np][np] = {};
+    T[0][0] = 1.0;
+    T[1][1] = 1.0;
+    for (int r = 1; r + 1 < np; r++)
+        for (int q = 0; q < np; q++) T[r + 1][q] = (q > 0 ? 2.0 * T[r][q - 1] : 0.0) - T[r - 1][q];
+    rt.cheb.assign((size_t)n * nm * np, 0.0);
+    rt.coef.assign((size_t)n * nm * 12, 0.0f);
+    rt.mr.assign(2 * (size_t)n, 0);
+    rt.mr0.assign(2 * (size_t)n, 0);
+    for (int iv = 0; iv < n; iv++) {
+        int lo = nm, hi = -1, lo1 = nm, hi1 = -1;
+        for (int m = 0; m < nm; m++) {
+            double c[np], a[np];
+            bool nz = false;
             for (int r = 0; r < np; r++) {
-                double s = 0.0;
-                for (int j = 0; j < np; j++)
-                    s += Q[((size_t)iv * np + j) * nm + m] * std::cos(kPi * r * (j + 0.5) / np);
-                out.coef[((size_t)iv * nm + m) * np + r] = s * (r == 0 ? 1.0 : 2.0) / np;
+                double sum = 0.0;
+                for (int k = 0; k < np; k++) sum += Q[((size_t)iv * np + k) * nm + m] * std::cos(kPi * r * (k + 0.5) / np);
+                c[r] = sum * (r == 0 ? 1.0 : 2.0) / np;
+                nz = nz || c[r] != 0.0;
             }
-    out.mlo.assign(n, nm);
-    out.mhi.assign(n, -1);
-    for (int iv = 0; iv < n; iv++)
-        for (int m = 0; m < nm; m++)
-            for (int r = 0; r < np; r++)
-                if (out.coef[((size_t)iv * nm + m) * np + r] != 0.0) {
-                    out.mlo[iv] = std::min(out.mlo[iv], m);
-                    out.mhi[iv] = std::max(out.mhi[iv], m);
+            for (int q = 0; q < np; q++) {
+                a[q] = 0.0;
+                for (int r = q; r < np; r++) a[q] += c[r] * T[r][q];
+            }
+            double* cd = &rt.cheb[((size_t)iv * nm + m) * np];
+            for (int r = 0; r < np; r++) cd[r] = c[r];
+            float* cf = &rt.coef[((size_t)iv * nm + m) * 12];
+            for (int q = 0; q < 4; q++) {
+                const float h = (float)a[q];
+                cf[2 * q] = h;
+                cf[2 * q + 1] = (float)(a[q] - (double)h);
+            }
+            for (int q = 4; q < np; q++) cf[4 + q] = (float)a[q];
+            if (nz) {
+                lo = std::min(lo, m);
+                hi = std::max(hi, m);
+                if (m >= 1) {
+                    lo1 = std::min(lo1, m);
+                    hi1 = std::max(hi1, m);
                 }
-}
-
-void local_fit_eval(const LocalFit& f, double d, double* Q) {
-    for (int m = 0; m < f.nm; m++) Q[m] = 0.0;
-    if (!(d >= 0.0) || !(d < f.bp.back())) return;
-    const int iv = (int)(std::upper_bound(f.bp.begin(), f.bp.end(), d) - f.bp.begin()) - 1;
-    const double a = f.bp[iv], b = f.bp[iv + 1], z = 2.0 * (d - a) / (b - a) - 1.0;
-    const int np = f.deg + 1;
-    for (int m = 0; m < f.nm; m++) {
-        const double* c = &f.coef[((size_t)iv * f.nm + m) * np];
-        double b0 = 0.0, b1 = 0.0;                      // Clenshaw
-        for (int r = f.deg; r >= 1; r--) {
-            const double b2 = b1;
-            b1 = b0;
-            b0 = 2.0 * z * b1 - b2 + c[r];
+            }
         }
-        Q[m] = z * b0 - b1 + c[0];
+        rt.mr0[2 * iv] = lo;
+        rt.mr0[2 * iv + 1] = hi;
+        rt.mr[2 * iv] = lo1;
+        rt.mr[2 * iv + 1] = hi1;
     }
 }
 

@@ -1,0 +1,471 @@
+// Time step of plans opened with opts.local_weights = 1: no per-pair data on the device.  The
+// springs are sorted, so the sources within delta of a target are an index window, and the local
+// weights Q_m(d) (Sec. 4.1) come from their polynomials in the distance (range.cuh).  One step:
+//
+//   k_rs_local      local explicit sum c_j over m >= 1 (Sec. 4.1), compensated FP32 pairs
+//   history pipeline (type-1 NUFFT, mode update, [projection], type-2 NUFFT): the per-stage
+//                   kernels of every plan; the interpolation leaves rhs_j = -g_j - beta_j u_H(x_j)
+//   k_rs_solve_init rhs_j -= (beta_j / 2) c_j; first iterate extrapolated from sigma^{n-7..n}
+//   k_rs_jacobi     Jacobi sweeps of (I + S) sigma^{n+1} = rhs (eq. linearSystem), S_jl =
+//                   (beta_j / 2) Q_0(d_jl) over the sources closer than dt, until the largest
+//                   change is below kRsTol of the largest density (launches after that return at
+//                   once, so the step is a fixed sequence of launches and can be captured)
+//   k_rs_store      sigma^{n+1} into the rings (status WAVE1D_ENOTCONV if no sweep converged)
+//   k_rs_receivers  u_L at the receivers (eq. localSol2, all m including m = 0), FP64
+//   k_rs_finish     u = u_L + u_H at the receivers, step counter
+//
+// Every kernel reads the step index from the device counter (graphs of steps are replayed).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "internal.h"
+#include "phases.cuh"
+#include "range.cuh"
+#include "../../include/wave1d.h"
+
+namespace wave1d {
+
+namespace {
+constexpr double kPiR = 3.14159265358979323846264338327950288;
+constexpr int kRsChunk = 32;      // sources per chunk (one per lane of warp 0 in the set-up)
+constexpr int kRsIvCap = 32;      // intervals whose e-vectors are held at once
+}  // namespace
+
+// shared memory of k_rs_local (bytes)
+size_t rs_local_smem(int nint, int nm) {
+    return (size_t)kRsIvCap * kRsChunk * rs::kERecord * sizeof(float) + (size_t)nm * kRsChunk * sizeof(float2) +
+           (size_t)(2 * (nint + 1) + 3 * nint) * sizeof(float);
+}
+
+// position of extended source index e: the same expression as the host's window tests
+__device__ __forceinline__ double rs_xext(const DevPlan& P, int64_t e) {
+    if (e < 0) return P.x[e + P.M] - 2.0 * kPiR;
+    if (e >= P.M) return P.x[e - P.M] + 2.0 * kPiR;
+    return P.x[e];
+}
+
+__device__ __forceinline__ int64_t rs_spring(int64_t e, int64_t M) { return e < 0 ? e + M : (e >= M ? e - M : e); }
+
+// float-pair position of extended index e
+__device__ __forceinline__ rs::Pair rs_xpair(const RangeDev& R, int64_t e, int64_t M) {
+    const int64_t l = rs_spring(e, M);
+    rs::Pair X{R.x2[2 * l], R.x2[2 * l + 1]};
+    if (e != l) {
+        const float th = (float)(2.0 * kPiR), tl = (float)(2.0 * kPiR - (double)(float)(2.0 * kPiR));
+        X = rs::pair_add(X, e < 0 ? rs::Pair{-th, -tl} : rs::Pair{th, tl});
+    }
+    return X;
+}
+
+// interval of a normalised pair distance d: bp[iv] <= d < bp[iv + 1], clamped to [0, nint)
+__device__ __forceinline__ int rs_locate(const float* bp2, int nint, rs::Pair d) {
+    int lo = 0, hi = nint;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (rs::pair_lt(d, rs::Pair{bp2[2 * mid], bp2[2 * mid + 1]})) hi = mid;
+        else lo = mid;
+    }
+    return lo;
+}
+
+// interval of an FP64 distance
+__device__ __forceinline__ int rs_locate64(const RangeDev& R, double d) {
+    int lo = 0, hi = R.nint;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (d < __ldg(R.bp + mid)) hi = mid;
+        else lo = mid;
+    }
+    return lo;
+}
+
+// Chebyshev series of degree 7 (Clenshaw), FP64
+__device__ __forceinline__ double rs_cheb(const double* c, double z) {
+    double b0 = 0.0, b1 = 0.0;
+    for (int r = 7; r >= 1; r--) {
+        const double b2 = b1;
+        b1 = b0;
+        b0 = fma(2.0 * z, b1, __ldg(c + r) - b2);
+    }
+    return fma(z, b0, __ldg(c) - b1);
+}
+
+// Q_0(d) from its series (zero at d >= dt, where m_min = 1)
+__device__ __forceinline__ double rs_q0(const RangeDev& R, double d) {
+    const int iv = rs_locate64(R, d);
+    if (iv >= R.iv_dt) return 0.0;
+    const double z = (d - __ldg(R.mid + iv)) * (double)__ldg(R.ih + iv);
+    return rs_cheb(R.cheb + (size_t)iv * R.nm * 8, z);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Local explicit sum, one block per kRsTargets consecutive targets (thread t: target j0 + t).
+// The block's sources (window [wlo, whi) of extended indices) are visited twice over as
+// "left" sources (strictly left of the target: d = x_j - x_e) and "right" sources (at or right
+// of it: d = x_e - x_j), in chunks of 32.  Per chunk:
+//   1. warp 0: each source's position and the interval range its distances to the block's
+//      targets can fall in (one interval of slack on each side);
+//   2. the chunk's densities sigma^{n+1-m}, m = 1 .. m_max, into shared memory;
+//   3. for each interval of the chunk's range (at most kRsIvCap at a time), one warp folds the
+//      densities of all 32 sources into their e-vectors (coefficients are warp-uniform loads);
+//   4. each thread walks the 32 sources: distance interval (tracked from the previous source of
+//      the same side, which moves it by about one interval), z, and the polynomial of the
+//      source's e-vector at z into the thread's compensated accumulator.
+// Near pairs (|x_e - x_j| < dt in FP64, the spring's implicit window) use the intervals below
+// dt, the others those above, so the near/far rule matches the implicit solve exactly.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kRsTargets, 2) k_rs_local(DevPlan P, RangeDev R) {
+    extern __shared__ __align__(16) float rs_sm[];
+    float* sE = rs_sm;
+    float2* sSig = (float2*)(sE + kRsIvCap * kRsChunk * rs::kERecord);
+    float* sBp = (float*)(sSig + (size_t)R.nm * kRsChunk);
+    float* sMid = sBp + 2 * (R.nint + 1);
+    float* sIh = sMid + 2 * R.nint;
+    __shared__ float sXh[kRsChunk], sXl[kRsChunk];
+    __shared__ int sEi[kRsChunk], sLo[kRsChunk], sHi[kRsChunk], sType[kRsChunk];
+    __shared__ int sU0, sU1;
+
+    const int64_t M = P.M;
+    const int64_t n = load_step(P);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5, nwarps = blockDim.x >> 5;
+    const int b = blockIdx.x;
+    const int64_t j0 = (int64_t)b * kRsTargets;
+    const int nT = (int)min((int64_t)kRsTargets, M - j0);
+    for (int i = t; i < 2 * (R.nint + 1); i += blockDim.x) sBp[i] = __ldg(R.bp2 + i);
+    for (int i = t; i < 2 * R.nint; i += blockDim.x) sMid[i] = __ldg(R.mid2 + i);
+    for (int i = t; i < R.nint; i += blockDim.x) sIh[i] = __ldg(R.ih + i);
+
+    const bool valid = t < nT;
+    const int64_t j = j0 + (valid ? t : 0);
+    const rs::Pair Xj{__ldg(R.x2 + 2 * j), __ldg(R.x2 + 2 * j + 1)};
+    const int nbl = __ldg(R.nb_lo + j), nbc = __ldg(R.nb_cnt + j);
+    const int64_t jl = j0 + nT - 1;
+    const rs::Pair Xa{__ldg(R.x2 + 2 * j0), __ldg(R.x2 + 2 * j0 + 1)};
+    const rs::Pair Xb{__ldg(R.x2 + 2 * jl), __ldg(R.x2 + 2 * jl + 1)};
+    const int wlo = __ldg(R.blk_win + 4 * b), inlo = __ldg(R.blk_win + 4 * b + 1);
+    const int inhi = __ldg(R.blk_win + 4 * b + 2), whi = __ldg(R.blk_win + 4 * b + 3);
+    const int nL = max(0, inhi - wlo), total = nL + max(0, whi - inlo);
+    const rs::Pair zero{0.f, 0.f};
+    const rs::Pair dlim{__ldg(R.bp2 + 2 * R.nint), __ldg(R.bp2 + 2 * R.nint + 1)};     // delta
+
+    float ah = 0.f, al = 0.f;
+    int tiv[2] = {-1, -1};              // tracked interval of the last left / right source
+    rs::Pair Y[2] = {zero, zero};       // x_j - mid (left) and x_j + mid (right) of that interval
+
+    for (int base = 0; base < total; base += kRsChunk) {
+        __syncthreads();
+        if (warp == 0) {
+            const int v = base + lane;
+            int lo = 1, hi = 0, type = 0, e = 0;
+            rs::Pair X = zero;
+            if (v < total) {
+                type = v < nL ? 0 : 1;
+                e = type == 0 ? wlo + v : inlo + (v - nL);
+                X = rs_xpair(R, e, M);
+                rs::Pair dmin, dmax;
+                if (type == 0) {
+                    dmin = rs::pair_sub(Xa, X);
+                    dmax = rs::pair_sub(Xb, X);
+                } else {
+                    dmin = rs::pair_sub(X, Xb);
+                    dmax = rs::pair_sub(X, Xa);
+                }
+                if (rs::pair_lt(dmin, zero)) dmin = zero;
+                if (!rs::pair_lt(dmax, zero) && rs::pair_lt(dmin, dlim)) {
+                    lo = max(0, rs_locate(sBp, R.nint, dmin) - 1);
+                    hi = min(R.nint - 1, rs_locate(sBp, R.nint, dmax) + 1);
+                }
+            }
+            sXh[lane] = X.hi;
+            sXl[lane] = X.lo;
+            sEi[lane] = e;
+            sLo[lane] = lo;
+            sHi[lane] = hi;
+            sType[lane] = type;
+            int u0 = lo <= hi ? lo : 0x7fffffff, u1 = lo <= hi ? hi : -1;
+            for (int o = 16; o > 0; o >>= 1) {
+                u0 = min(u0, __shfl_xor_sync(0xffffffffu, u0, o));
+                u1 = max(u1, __shfl_xor_sync(0xffffffffu, u1, o));
+            }
+            if (lane == 0) {
+                sU0 = u0;
+                sU1 = u1;
+            }
+        }
+        __syncthreads();
+        // the chunk's densities, sigma^{n+1-m} of source k at sSig[m][k] (pairs)
+        for (int i = t; i < (R.nm - 1) * kRsChunk; i += blockDim.x) {
+            const int k = i & (kRsChunk - 1), m = 1 + i / kRsChunk;
+            float2 s = make_float2(0.f, 0.f);
+            if (base + k < total) {
+                const int64_t l = rs_spring(sEi[k], M);
+                s = __ldg((const float2*)P.sig2 + (int64_t)ring_slot(n + 1 - m, P.ring) * M + l);
+            }
+            sSig[m * kRsChunk + k] = s;
+        }
+        __syncthreads();
+        const int U0 = sU0, U1 = sU1;
+        for (int W0 = U0; W0 <= U1; W0 += kRsIvCap) {
+            const int W1 = min(U1, W0 + kRsIvCap - 1);
+            // e-vectors of the intervals [W0, W1]: warp per interval, lane per source
+            for (int iv = W0 + warp; iv <= W1; iv += nwarps) {
+                const bool act = base + lane < total && sLo[lane] <= iv && iv <= sHi[lane];
+                if (!__any_sync(0xffffffffu, act)) continue;
+                rs::EVec ev;
+                rs::evec_zero(ev);
+                const int m0 = __ldg(R.mr + 2 * iv), m1 = __ldg(R.mr + 2 * iv + 1);
+                const float4* c = (const float4*)R.coef + (size_t)iv * R.nm * 3;
+                for (int m = m0; m <= m1; m++) {
+                    const float4 c01 = __ldg(c + 3 * m), c23 = __ldg(c + 3 * m + 1), c47 = __ldg(c + 3 * m + 2);
+                    const float2 s = sSig[m * kRsChunk + lane];
+                    const float a01[4] = {c01.x, c01.y, c01.z, c01.w}, a23[4] = {c23.x, c23.y, c23.z, c23.w},
+                                a47[4] = {c47.x, c47.y, c47.z, c47.w};
+                    rs::evec_mac(ev, a01, a23, a47, s.x, s.y);
+                }
+                float4* rec = (float4*)(sE + ((iv - W0) * kRsChunk + lane) * rs::kERecord);
+                rec[0] = make_float4(ev.e0h, ev.e0l, ev.e1h, ev.e1l);
+                rec[1] = make_float4(ev.e2, ev.e3, ev.e4, ev.e5);
+                rec[2] = make_float4(ev.e6, ev.e7, 0.f, 0.f);
+            }
+            __syncthreads();
+            if (W0 > U0) tiv[0] = tiv[1] = -1;       // a second pass over the chunk: search afresh
+            if (valid) {
+                const int kend = min(kRsChunk, total - base);
+                for (int k = 0; k < kend; k++) {
+                    const int lo = sLo[k], hi = sHi[k];
+                    if (lo > hi) continue;
+                    const int type = sType[k];
+                    const rs::Pair X{sXh[k], sXl[k]};
+                    // left sources strictly left of x_j, right sources at or right of it
+                    if (type == 0 ? !rs::pair_lt(X, Xj) : rs::pair_lt(X, Xj)) continue;
+                    const bool near = (unsigned)(sEi[k] - nbl) < (unsigned)nbc;
+                    // the tracked interval, on the pair's side of dt (near pairs below it, far
+                    // pairs at or above it)
+                    int iv = tiv[type];
+                    if (iv >= 0 && (near ? iv >= R.iv_dt : iv < R.iv_dt)) iv = near ? R.iv_dt - 1 : R.iv_dt;
+                    if (iv < 0) iv = rs_locate(sBp, R.nint, type == 0 ? rs::pair_sub(Xj, X) : rs::pair_sub(X, Xj));
+                    iv = near ? min(iv, R.iv_dt - 1) : max(iv, R.iv_dt);
+                    if (iv != tiv[type]) {
+                        const rs::Pair mid{sMid[2 * iv], sMid[2 * iv + 1]};
+                        Y[type] = rs::pair_add(Xj, type == 0 ? rs::Pair{-mid.hi, -mid.lo} : mid);
+                    }
+                    // walk to the interval whose z lies in [-1, 1] (to rounding), in one direction
+                    // only, so the walk ends even where rounding leaves z just outside two
+                    // neighbouring intervals; far off, search instead
+                    float zh, zl;
+                    int dir = 0;
+                    for (int pass = 0;; pass++) {
+                        const float s = sIh[iv];
+                        if (type == 0) rs::scaled_diff(Y[0], X, s, zh, zl);
+                        else rs::scaled_diff(X, Y[1], s, zh, zl);
+                        if (pass == 0 && fabsf(zh) > 4.f) {
+                            int nv = rs_locate(sBp, R.nint, type == 0 ? rs::pair_sub(Xj, X) : rs::pair_sub(X, Xj));
+                            nv = near ? min(nv, R.iv_dt - 1) : max(nv, R.iv_dt);
+                            if (nv != iv) {
+                                iv = nv;
+                                const rs::Pair mid{sMid[2 * iv], sMid[2 * iv + 1]};
+                                Y[type] = rs::pair_add(Xj, type == 0 ? rs::Pair{-mid.hi, -mid.lo} : mid);
+                                continue;
+                            }
+                        }
+                        const int want = zh > 1.000001f ? 1 : (zh < -1.000001f ? -1 : 0);
+                        if (want == 0 || (dir != 0 && want != dir)) break;
+                        const int nv = iv + want;
+                        // near pairs stay below dt, far pairs at or above it
+                        if (nv < 0 || nv >= R.nint || (near ? nv >= R.iv_dt : nv < R.iv_dt)) break;
+                        dir = want;
+                        iv = nv;
+                        const rs::Pair mid{sMid[2 * iv], sMid[2 * iv + 1]};
+                        Y[type] = rs::pair_add(Xj, type == 0 ? rs::Pair{-mid.hi, -mid.lo} : mid);
+                    }
+                    tiv[type] = iv;
+                    if (zh > 1.000001f && iv == R.nint - 1) continue;     // d >= delta
+                    if (iv < W0 || iv > W1 || iv < lo || iv > hi) continue;
+                    rs::evec_eval(sE + ((iv - W0) * kRsChunk + k) * rs::kERecord, zh, zl, ah, al);
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (valid) P.clocal[j] = (double)ah + (double)al;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Implicit solve of eq. linearSystem: (I + S) sigma^{n+1} = rhs by Jacobi sweeps
+// ---------------------------------------------------------------------------------------------
+
+// plan time: S_jl = (beta_j / 2) Q_0(d_jl) for the sources of spring j's window (warp per spring)
+__global__ void k_rs_nearby_weights(DevPlan P, RangeDev R) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < P.M; j += nw) {
+        const double xj = P.x[j], hb = 0.5 * P.beta[j];
+        const int lo = R.nb_lo[j], cnt = R.nb_cnt[j];
+        const int64_t off = R.nb_off[j];
+        for (int k = lane; k < cnt; k += 32) {
+            const int64_t e = (int64_t)lo + k;
+            const double w = e == j ? 0.0 : hb * rs_q0(R, fabs(rs_xext(P, e) - xj));
+            const rs::Pair pw = rs::split(w);
+            R.nb_w[2 * (off + k)] = pw.hi;
+            R.nb_w[2 * (off + k) + 1] = pw.lo;
+        }
+        if (lane == 0) R.diag[j] = 1.0 + hb * rs_q0(R, 0.0);
+    }
+}
+
+__device__ __forceinline__ double rs_from_bits(unsigned long long v) { return __longlong_as_double((long long)v); }
+
+// right-hand side and first iterate: sigma^{n+1} extrapolated from sigma^{n-7..n} (the
+// degree-7 polynomial through them), or rhs / (1 + S_jj) in the first steps
+__global__ void k_rs_solve_init(DevPlan P, RangeDev R) {
+    const int64_t n = load_step(P);
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < 2 * (kRsMaxIter + 1); i += blockDim.x) R.stats[i] = 0ull;
+    const double ex[8] = {8.0, -28.0, 56.0, -70.0, 56.0, -28.0, 8.0, -1.0};
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < P.M; j += (int64_t)gridDim.x * blockDim.x) {
+        const double rhs = fma(-0.5 * P.beta[j], P.clocal[j], __ldcg(P.rhs + j));
+        P.rhs[j] = rhs;
+        double x0;
+        if (n >= 8) {
+            x0 = 0.0;
+            for (int q = 0; q < 8; q++) x0 = fma(ex[q], P.sig[(int64_t)ring_slot(n - q, P.ring) * P.M + j], x0);
+        } else {
+            x0 = rhs / R.diag[j];
+        }
+        R.it64[0][j] = x0;
+        const rs::Pair p2 = rs::split(x0);
+        R.it2[0][2 * j] = p2.hi;
+        R.it2[0][2 * j + 1] = p2.lo;
+    }
+}
+
+// sweep `it` (1 .. kRsMaxIter): iterate it from iterate it - 1, unless sweep it - 1 converged.
+// Warp per spring; the row sum sum_{l != j} S_jl sigma_l in compensated pairs.
+__global__ void __launch_bounds__(256) k_rs_jacobi(DevPlan P, RangeDev R, int it) {
+    if (it >= 2) {
+        const double dmax = rs_from_bits(__ldcg(R.stats + 2 * (it - 1)));
+        const double smax = rs_from_bits(__ldcg(R.stats + 2 * (it - 1) + 1));
+        if (dmax <= kRsTol * smax) return;
+    }
+    __shared__ double red[2][8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const float* src2 = R.it2[(it - 1) & 1];
+    const double* src = R.it64[(it - 1) & 1];
+    double* dst = R.it64[it & 1];
+    float* dst2 = R.it2[it & 1];
+    double dmax = 0.0, smax = 0.0;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < P.M; j += nw) {
+        const int lo = __ldg(R.nb_lo + j), cnt = __ldg(R.nb_cnt + j);
+        const int64_t off = __ldg(R.nb_off + j);
+        float ah = 0.f, al = 0.f;
+        for (int k = lane; k < cnt; k += 32) {
+            const float2 w = __ldcs((const float2*)R.nb_w + off + k);
+            const int64_t l = rs_spring((int64_t)lo + k, P.M);
+            const float2 s = __ldcg((const float2*)src2 + l);
+            rs::acc_mac(ah, al, w.x, w.y, s.x, s.y);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, ah, o), ol = __shfl_xor_sync(0xffffffffu, al, o);
+            rs::acc_add(ah, al, oh, ol);
+        }
+        if (lane == 0) {
+            const double x = (__ldcg(P.rhs + j) - ((double)ah + (double)al)) / R.diag[j];
+            dmax = fmax(dmax, fabs(x - __ldcg(src + j)));
+            smax = fmax(smax, fabs(x));
+            dst[j] = x;
+            const rs::Pair p2 = rs::split(x);
+            dst2[2 * j] = p2.hi;
+            dst2[2 * j + 1] = p2.lo;
+        }
+    }
+    if (lane == 0) {
+        red[0][wid] = dmax;
+        red[1][wid] = smax;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
+            dmax = fmax(dmax, red[0][w]);
+            smax = fmax(smax, red[1][w]);
+        }
+        // non-negative doubles order as their bit patterns (a NaN sorts above every number)
+        atomicMax(R.stats + 2 * it, (unsigned long long)__double_as_longlong(dmax));
+        atomicMax(R.stats + 2 * it + 1, (unsigned long long)__double_as_longlong(smax));
+    }
+}
+
+// the converged iterate into the rings: the first sweep whose record meets the stopping rule
+// (sweeps after it did not run and left zero records)
+__global__ void k_rs_store(DevPlan P, RangeDev R) {
+    const int64_t n = load_step(P);
+    int fin = kRsMaxIter;
+    bool ok = false;
+    for (int it = 1; it <= kRsMaxIter; it++) {
+        const double dmax = rs_from_bits(__ldcg(R.stats + 2 * it)), smax = rs_from_bits(__ldcg(R.stats + 2 * it + 1));
+        if (dmax <= kRsTol * smax) {
+            fin = it;
+            ok = true;
+            break;
+        }
+    }
+    const double* x = R.it64[fin & 1];
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < P.M; j += (int64_t)gridDim.x * blockDim.x)
+        store_sigma(P, n, (int)j, __ldcg(x + j));
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *R.iters = fin;
+        if (!ok) atomicCAS(P.status, 0, (int)WAVE1D_ENOTCONV);
+    }
+}
+
+// receivers' local part (eq. localSol2), block (chunk c of 256 sources, receiver r): every m of
+// the pair's interval, m = 0 with sigma^{n+1} (already stored), FP64; block sums in a fixed order
+__global__ void __launch_bounds__(256) k_rs_receivers(DevPlan P, RangeDev R) {
+    __shared__ double red[8];
+    const int64_t n = load_step(P);
+    const int r = blockIdx.y, c = blockIdx.x;
+    const int lo = R.r_win[2 * r], hi = R.r_win[2 * r + 1];
+    const int64_t e = (int64_t)lo + (int64_t)c * blockDim.x + threadIdx.x;
+    double v = 0.0;
+    if (e < hi) {
+        const int64_t l = rs_spring(e, P.M);
+        const double d = fabs(rs_xext(P, e) - P.xr[r]);
+        if (d < R.delta) {
+            const int iv = rs_locate64(R, d);
+            const double z = (d - __ldg(R.mid + iv)) * (double)__ldg(R.ih + iv);
+            const int m0 = __ldg(R.mr0 + 2 * iv), m1 = __ldg(R.mr0 + 2 * iv + 1);
+            for (int m = m0; m <= m1; m++) {
+                const double q = rs_cheb(R.cheb + ((size_t)iv * R.nm + m) * 8, z);
+                v = fma(q, __ldcg(P.sig + (int64_t)ring_slot(n + 1 - m, P.ring) * P.M + l), v);
+            }
+        }
+    }
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += red[w];
+        R.r_part[(size_t)r * R.rchunks + c] = s;
+    }
+}
+
+// u = u_L + u_H at the receivers (chunk partials in order), then the step counter
+__global__ void k_rs_finish(DevPlan P, RangeDev R) {
+    const int64_t n = load_step(P);
+    for (int64_t r = threadIdx.x; r < P.R; r += blockDim.x) {
+        double s = 0.0;
+        for (int c = 0; c < R.rchunks; c++) s += __ldcg(R.r_part + r * R.rchunks + c);
+        P.rec_hist[(n % P.chunk) * P.R + r] = 0.5 * s + __ldcg(P.uHr + r);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        *P.item_ctr = 0ull;
+        P.step[1] = 0;
+        __threadfence();
+        P.step[0] = n + 1;
+    }
+}
+
+}  // namespace wave1d

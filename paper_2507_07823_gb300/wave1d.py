@@ -23,6 +23,7 @@ WAVE1D_EINVAL = -1
 WAVE1D_EDOMAIN = -2
 WAVE1D_ENOMEM = -3
 WAVE1D_ECUDA = -4
+WAVE1D_ENOTCONV = -5
 WAVE1D_ENONFINITE = -6
 WAVE1D_EDONE = -7
 WAVE1D_EUNSUPPORTED = -9
