@@ -104,6 +104,8 @@ typedef struct {
     int64_t device_bytes;     /* device memory owned by the plan                                     */
     int64_t local_bytes;      /* bytes the local-sum kernel streams per step: weights, source lists,
                                  per-m counts, row offsets and its output                         */
+    int64_t local_terms;      /* multiply-adds Q_m(d_jl) sigma_l^{n+1-m} of the local sum per step
+                                 (pairs closer than delta times their non-zero m >= 1)            */
 } wave1d_info;
 
 /* Fill *o with defaults.  Returns WAVE1D_EINVAL if o is NULL. */
@@ -316,7 +318,10 @@ int wave1d_nufft_autotune(wave1d_nufft_t plan, const double* c, double* grid, in
  * budget reserved up front, or in a loop that must not take the implicit device synchronisation
  * cudaMalloc/cudaFree can cause).
  *   S[2k], S[2k+1] = Re, Im of (1/2 pi) sum_j c[j] e^{i k x[j]},  k = 0..K
- * computed with the spreading kernel, fine grid and FFT a plan of the same K and tol uses.
+ * computed with the spreading kernel, fine grid and FFT a plan of the same K and tol uses.  The
+ * spreading adds into the fine grid with FP64 atomics, so the order of those additions, and the
+ * last bits of S (about 1e-16 of max |S|), can differ from call to call: unlike every other call
+ * of this library, the result is not bitwise reproducible.
  *   x, c : device, M values (x read periodically on [-pi, pi)); S: device, 2 (K+1) values.
  *   stream: cudaStream_t (NULL = legacy default stream).  Asynchronous.
  * All intermediates live in one file-scope device array of 2 MiB that every GPU loading the
@@ -342,7 +347,8 @@ int wave1d_nufft1_noalloc(const double* x, const double* c, int64_t M, int K, do
  *   pulse   : host, n_inst x 3: amplitude, centre, width of instance i's incident Gaussian.
  *   r_offsets, xr : host receivers, instance i's being xr[r_offsets[i] .. r_offsets[i+1]) (at
  *             least one each), or r_offsets = NULL for none.
- *   dt, Nt, tol : as wave1d_plan.  opts: NULL or as wave1d_plan with precision 0 and nufft_w 0.
+ *   dt, Nt, tol : as wave1d_plan.  opts: NULL or as wave1d_plan with precision 0, nufft_w 0 and
+ *                 local_weights 0 (others: WAVE1D_EINVAL).
  * Every instance's derived sizes (K, W, fine grid) are the same, since they depend on dt, tol and
  * p only.  The springs' and receivers' global order is instance-major in the caller's order.
  * Returns WAVE1D_EINVAL / EDOMAIN / ENOMEM / ECUDA like wave1d_plan (message: wave1d_batch_strerror).

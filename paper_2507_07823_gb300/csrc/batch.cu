@@ -352,6 +352,8 @@ int wave1d_batch_plan(int n_inst, const int64_t* offsets, const double* x, const
     if (o.p < 2 || o.p > 16 || (o.p % 2) != 0) return bfail(WAVE1D_EINVAL, "p must be even, 2..16");
     if (o.precision != 0 || o.nufft_w != 0)
         return bfail(WAVE1D_EINVAL, "the batched march runs in FP64 with the kernel width of its tolerance");
+    if (o.local_weights != 0)
+        return bfail(WAVE1D_EINVAL, "the batched march stores its local weights (local_weights = 0)");
     if (o.max_block <= 0) o.max_block = 4096;
     if (o.max_local_bytes <= 0) o.max_local_bytes = (int64_t)16 << 30;
 

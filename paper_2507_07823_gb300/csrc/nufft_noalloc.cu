@@ -122,14 +122,15 @@ extern "C" int wave1d_nufft1_noalloc(const double* x, const double* c, int64_t M
     const double kPi = 3.14159265358979323846;
     if ((M > 0 && (!x || !c)) || !S || M < 0 || K < 1 || !(tol > 0.0 && tol < 0.1))
         return WAVE1D_EINVAL;
-    // fine grid and kernel exactly as a plan chooses them for this K and tol
+    // fine grid, kernel and FFT split (L = L1 L2, L1 >= L2) as a plan chooses them for this K and
+    // tol; the spreading's atomic additions make the last bits differ from call to call
     int64_t nf = 1;
     while (nf < 2 * (2 * (int64_t)K + 1)) nf <<= 1;
     if (nf < 64) nf = 64;
     if (nf > kMaxNf) return WAVE1D_EUNSUPPORTED;       // beyond the fixed scratch array
     int L = (int)(nf / 2);
     int lg = ilog2i(L);
-    int L1 = 1 << (lg / 2), L2 = L / L1;
+    int L1 = 1 << ((lg + 1) / 2), L2 = L / L1;
     int w = (int)std::ceil(std::log10(1.0 / tol)) + 1;
     w = w < 4 ? 4 : (w > 16 ? 16 : w);
     double upsamp = (double)nf / (2.0 * K + 1.0);

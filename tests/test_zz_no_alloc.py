@@ -1,12 +1,14 @@
 """wave1d_nufft1_noalloc: the type-1 NUFFT for callers that cannot allocate device memory.
 
-It must give the spectrum S_k a plan computes inside a step (the spreading + FFT stages, read back
-with wave1d_inspect) for the same densities, on two calls in a row, within the parity tolerance.
-Collected last so that a failure here leaves every other test already run.
+On two calls in a row it must give the direct sums S_k = (1/2 pi) sum_j c_j e^{i k x_j} of the
+oracle (eq. densco) within the parity tolerance, and the spectrum S_k a plan computes inside a step
+(the spreading + FFT stages, read back with wave1d_inspect) for the same densities.  Collected last
+so that a failure here leaves every other test already run.
 """
 import numpy as np
 import pytest
 
+from oracle import wfp
 from paper_2507_07823_gb300 import build, wave1d, workloads as W
 
 pytestmark = pytest.mark.gpu
@@ -55,6 +57,12 @@ def test_noalloc_type1_matches_plan(torch, cfg):
     r1 = a1[0::2] + 1j * a1[1::2]
     r2 = a2[0::2] + 1j * a2[1::2]
     assert np.max(np.abs(S_prev)) > 0 and np.max(np.abs(S_now)) > 0
+    # the oracle's direct sums of the same densities
+    d1 = wfp.type1(ring[1], w.x, K)
+    d2 = wfp.type1(ring[0], w.x, K)
+    assert np.max(np.abs(r1 - d1)) <= TOL * np.max(np.abs(d1))
+    assert np.max(np.abs(r2 - d2)) <= TOL * np.max(np.abs(d2))
+    # and the plan's own spectrum of them
     assert np.max(np.abs(r1 - S_prev)) <= TOL * np.max(np.abs(S_prev))
     assert np.max(np.abs(r2 - S_now)) <= TOL * np.max(np.abs(S_now))
 
