@@ -1,21 +1,24 @@
 """Benchmark of the WFP time march on GB300: scatterer-steps per second (M * steps / s).
 
-Workload: free space, M = 1e4 springs uniform in Omega, stiffnesses log-uniform in [0.1, 100],
-three Gaussian pulses (widths 0.02, 0.05, 0.1), dt = 1e-3, tol = 1e-12, p = 8 (seeded synthetic
-input, `workloads.config1`).  One step = one pass of the whole hot path (local sum, type-1 NUFFT,
-mode update, radiation projection on projection steps, type-2 NUFFT, implicit solve, receivers).
+Workload (headline): the million-spring clustered layout in the periodic box (16 Gaussian clusters
+of width 0.05 plus 20 % uniform springs, stiffnesses uniform in [1, 10]), incident Gaussian of width
+0.1 at x = -2, dt = 5e-4 (K = 6283 modes), tol = 1e-10 (W = 30), p = 8, four receivers; seeded
+synthetic input (`workloads.config2`).  Its 1.3e10 pairs closer than delta and its 931,311-spring
+block of pairs closer than dt fit no stored-weight plan, so the plan is the one without pair lists
+(opts.local_weights = 1).  One step = one pass of the whole hot path: local sum, type-1 NUFFT, mode
+update, type-2 NUFFT, implicit solve, receivers.
 
 Timing: W untimed warm-up steps, then exactly K steps of one `wave1d_solve` call timed with CUDA
-events on the caller's stream (the plan's work is stream-ordered on it).  The L2 is not flushed
-between those steps: every step streams the 303 MB of stored local weights, 2.4 times the L2, so
-the inputs are larger than the L2.  Beside it, single-step figures are reported: each step is timed
-alone after an L2 flush (writing a 512 MiB buffer, then reading a 256 MiB one, so no dirty flush
-lines are written back inside the timed step), and the roofline uses those figures.  The march
-state stays on the device between steps.  Under torchrun every rank marches its own replica; the
-timed region is bracketed by barriers and the slowest rank's time is reported.
+events on the caller's stream (the plan's work is stream-ordered on it).  Inputs are resident and
+larger than the L2 (every step reads 3.6 GB of implicit-part weights and the 0.84 GB density rings).
+Beside it: the per-stage times of K profiled steps (the roofline of the local sum), the end-to-end
+rate through the public API with host buffers, the free-space M = 1e4 workload as a secondary
+measurement, the forms beside FP64, and the CPU oracle on a bounded sample with the GPU's error
+against it.  Under torchrun every rank marches its own replica; the timed region is bracketed by
+barriers and the slowest rank's time is reported.
 
 `--impl reference` times the plain CPU oracle of the same scheme (oracle/wfp.py) on the host
-cores, on the same workload, one oracle time step per bench step.
+cores, on a bounded sample of the workload, one oracle time step per bench step.
 """
 from __future__ import annotations
 
@@ -42,6 +45,10 @@ L2_FLUSH_BYTES = 512 << 20
 STEP_KERNEL_SOURCES = ["step.cu", "phases.cuh", "device_common.cuh", "internal.h"]
 STEP_TRAFFIC = {"sources_sha256": "13f81524b1f7f23ee3bc3ed344078df96465877e9cb045f2d7dc0d2979f4ad1a", "bytes_per_launch": 317778176 + 4285952}
 L2_CLEAN_BYTES = 256 << 20
+# DRAM bytes of one k_rs_local launch from one ncu capture of the clustered layout at M = 2e5 (its
+# pairs below), for the kernel sources it was taken with (null once they change)
+RS_LOCAL_SOURCES = ["range.cu", "range.cuh", "phases.cuh", "device_common.cuh", "internal.h"]
+RS_LOCAL_TRAFFIC = {"sources_sha256": "", "bytes_per_launch": 0.0, "pairs": 1}
 
 
 def _peaks():
@@ -153,36 +160,20 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
-    w = workloads.config1()
+    w = workloads.config2()
     K, Wm = args.steps, args.warmup
     assert Wm >= 3
     stream = torch.cuda.current_stream()
     t_plan = time.perf_counter()
-    plan = wave1d.Plan.from_workload(w.with_(Nt=Wm + 5 * K + 512), stream=stream.cuda_stream)
+    plan = wave1d.Plan.from_workload(w.with_(Nt=Wm + 3 * K + 8), stream=stream.cuda_stream, local_weights=1)
     t_plan = time.perf_counter() - t_plan
     info = plan.info
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    clean = torch.ones(L2_CLEAN_BYTES // 4, dtype=torch.float32, device="cuda")
-
-    def flush_l2():
-        # write a buffer four times the L2 size, then read a buffer twice its size, so the timed
-        # step starts with an L2 that holds none of the march data and no dirty lines to write back
-        flush.zero_()
-        clean.sum()
-
     for _ in range(Wm):
         plan.step()
-    # align to a chunk of the solve (rbc_period steps, ending with a projection step) and build
-    # its graph, untimed
-    chunk = info.rbc_period
-    for _ in range((-wave1d.wave1d_get_info(plan.h).n) % chunk):
-        plan.step()
-    wave1d._check(wave1d.wave1d_solve(plan.h, chunk, None, None, 1), "wave1d_solve")
     torch.cuda.synchronize()
 
-    # --- device-timed march: exactly K steps through wave1d_solve, no flush (every step streams
-    # the 303 MB of stored local weights, 2.4 times the L2) ------------------------------------------
-    n_first = wave1d.wave1d_get_info(plan.h).n
+    # --- device-timed march: exactly K steps of one wave1d_solve call (inputs resident; every step
+    # reads the 3.6 GB of implicit-part weights and 0.84 GB of density rings, far more than L2) -----
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if world > 1:
         import torch.distributed as dist
@@ -200,58 +191,23 @@ def run_ours(args):
         import torch.distributed as dist
         dist.barrier()
     value = replica_throughput(w.M, K, world, ms_total)
-    # ordinary steps run as one launch of the step kernel; projection steps (every rbc_period-th)
-    # as 10 per-stage launches
-    n_rbc = sum(((n_first + i + 1) % chunk) == 0 for i in range(K))
-    launches = (K - n_rbc) + 10 * n_rbc
+    launches = K * range_launches_per_step(w)
 
-    # --- the same number of single steps (wave1d_step), L2 flushed before each, each timed with
-    # events: the per-launch time of the step kernel for the roofline ----------------------------
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    n_flushed = wave1d.wave1d_get_info(plan.h).n
-    torch.cuda.synchronize()
-    for i in range(K):
-        flush_l2()
-        evs[i][0].record(stream)
-        wave1d._check(wave1d.wave1d_step(plan.h), "wave1d_step")
-        evs[i][1].record(stream)
-    torch.cuda.synchronize()
-    ms_steps = [a.elapsed_time(b) for a, b in evs]
-    ms_flushed = float(sum(ms_steps))
-    rbc = [((n_flushed + i + 1) % chunk) == 0 for i in range(K)]
-    ms_ordinary = [m for m, r in zip(ms_steps, rbc) if not r]
-
-    # --- the same march without the L2 flush (steady state: each step streams the 303 MB of
-    # local weights, more than the 126 MB L2, through it anyway) ------------------------------------
-    evs2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-    torch.cuda.synchronize()
-    for i in range(K):
-        evs2[i][0].record(stream)
-        wave1d._check(wave1d.wave1d_step(plan.h), "wave1d_step")
-        evs2[i][1].record(stream)
-    torch.cuda.synchronize()
-    ms_warm = float(sum(a.elapsed_time(b) for a, b in evs2))
-
-    # --- per-stage device times (CUDA events between the stages, same plan, K steps) --------
+    # --- per-stage device times (CUDA events between the stages, K steps): the local-sum stage is
+    # exactly one launch of k_rs_local, which gives its per-launch time for the roofline ---------
     wave1d.wave1d_profile(plan.h, 1)
     for i in range(K):
-        flush_l2()
         wave1d._check(wave1d.wave1d_step(plan.h), "wave1d_step")
     stage_ms, nprof = wave1d.wave1d_profile_read(plan.h)
     wave1d.wave1d_profile(plan.h, 0)
     per_step = {s: float(stage_ms[i] / nprof) for i, s in enumerate(wave1d.STAGES)}
 
-    # --- end to end through the public API with host buffers ------------------------------------
-    # forcing g_j(t_{n+1}) = beta_j f(x_j - t_{n+1}) supplied from pinned host memory every step,
-    # densities read back to pinned host memory every step
-    n0 = plan.info.n if hasattr(plan.info, "n") else 0
+    # --- end to end through the public API with host buffers: forcing g_j(t_{n+1}) from pinned host
+    # memory every step, the densities back to pinned host memory every step ----------------------
     cur = wave1d.wave1d_get_info(plan.h).n
     g_host = torch.empty((K, w.M), dtype=torch.float64, pin_memory=True)
     tt = (cur + 1 + np.arange(K)) * w.dt
-    f = np.zeros((K, w.M))
-    for a, c, wd in zip(w.amp, w.center, w.width):
-        f += a * np.exp(-0.5 * ((w.x[None, :] - tt[:, None] - c) / wd) ** 2)
-    g_host.numpy()[:] = w.beta[None, :] * f
+    g_host.numpy()[:] = w.beta[None, :] * periodic_gaussians(w, tt)
     out_host = torch.empty((K, w.M), dtype=torch.float64, pin_memory=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -261,42 +217,42 @@ def run_ours(args):
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_value = w.M * K * world / e2e_s
-    del n0
+    plan.close()
 
-    # --- roofline of the timed kernel: the one-launch step kernel -------------------------------
-    # algorithmic bytes per launch: the local-sum stream (stored weights as FP32 pairs, source
-    # lists, item headers, partial sums), which the step must read once; the history and solve
-    # state (a few MB, mostly L2-resident) is not counted
-    hbm, peak_kind = _peaks()
-    bytes_per_step = stage_bytes(info, w, "local")
-    ms_k = float(np.mean(ms_ordinary if ms_ordinary else ms_steps))
-    achieved = bytes_per_step / (ms_k * 1e-3) / 1e9
-    roof = {"kernel": "k_step", "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": step_traffic(),
-            "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s",
-            "algorithmic_bytes_per_launch": bytes_per_step,
-            "launch_ms": ms_k, "launches_averaged": len(ms_ordinary),
-            "timing": "per-launch CUDA events of single wave1d_step calls, L2 flushed before each"}
+    # --- roofline of the dominant kernel, k_rs_local: bound by FP32 issue, not by HBM.  Algorithmic
+    # work per launch: the local sum's multiply-adds Q_m(d) sigma (info.local_terms, 2 flops each),
+    # the work the method does whatever the arithmetic; peak: 152 SMs x 128 FP32 lanes x 2 flops x
+    # the maximum SM clock.
+    fp32_peak, clk_src = _fp32_peak()
+    ms_local = per_step["local"]
+    achieved = 2.0 * info.local_terms / (ms_local * 1e-3) / 1e12
+    roof = {"kernel": "k_rs_local", "bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak, "traffic": rs_local_traffic(info),
+            "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 flops x {clk_src}",
+            "algorithmic_flops_per_launch": 2.0 * info.local_terms, "launch_ms": ms_local,
+            "local_pairs": info.local_pairs, "local_terms": info.local_terms,
+            "pairs_per_s": info.local_pairs / (ms_local * 1e-3),
+            "timing": "CUDA events around the local-sum stage (one k_rs_local launch) of K profiled steps",
+            "arithmetic": "compensated FP32 pairs (about 48 significant bits); 2 flops per term counts only the "
+                          "multiply-add of the method, not the compensation or the weights' polynomials"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": Wm, "ms_per_step": ms_total / K, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{w.name}: {w.description}", "M": w.M, "dt": w.dt,
-                   "tol": w.tol, "p": w.p, "K": info.K, "W": info.W, "nufft_w": info.nufft_w,
-                   "nf": info.nf, "local_pairs": info.local_pairs,
-                   "local_weights": info.local_weights, "local_bytes": info.local_bytes,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32x2+f64", "data": "synthetic",
+        "config": {"workload": f"{w.name}: {w.description}", "M": w.M, "dt": w.dt, "tol": w.tol, "p": w.p,
+                   "K": info.K, "W": info.W, "nufft_w": info.nufft_w, "nf": info.nf,
+                   "local_pairs": info.local_pairs, "nearby_pairs": info.nearby_pairs,
+                   "plan": "local_weights = 1: no pair lists (local sum over sorted index windows with "
+                           "weights from distance polynomials, implicit part by Jacobi sweeps)",
+                   "arithmetic": "local sum in compensated FP32 pairs (k_rs_local); history part (NUFFTs, "
+                                 "FFTs, mode recurrence), implicit solve and receivers in FP64",
                    "parallelism": f"replicas x{world}",
-                   "l2": "not flushed: every step streams the 303 MB of stored local weights, 2.4x "
-                         "the 126 MB L2 (value_per_step_l2_flushed: single wave1d_step calls with "
-                         "512 MiB written and 256 MiB read before each)",
-                   "timed": f"wave1d_solve of {K} steps from a chunk boundary ({chunk}-step chunks: "
-                            "one graph-captured step-kernel launch per ordinary step, ten per-stage "
-                            "launches for the projection step)",
+                   "l2": "not flushed: every step reads the 3.6 GB of implicit-part weights and the 0.84 GB "
+                         "density rings, far more than the 126 MB L2",
+                   "timed": f"one wave1d_solve of {K} steps after {Wm} warm-up steps",
                    "plan_seconds": t_plan},
-        "value_per_step_l2_flushed": w.M * K * world / (ms_flushed * 1e-3),
-        "value_per_step_back_to_back": w.M * K * world / (ms_warm * 1e-3),
-        "stage_ms_per_step_per_stage_launches": per_step,
+        "stage_ms_per_step": per_step,
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * w.M,
                 "d2h_bytes_per_step": 8 * w.M},
@@ -304,22 +260,130 @@ def run_ours(args):
         "clocks": clk.summary(),
         "wall_s_timed_region": wall,
     }
-    plan.close()
+    if world == 1 and not args.no_secondary:
+        try:
+            line["free_M1e4"] = free_space_secondary(torch, stream)
+        except Exception as e:                               # recorded, never fatal to the line
+            line["free_M1e4"] = {"error": repr(e)[:300]}
     if not args.no_spread_interp:
+        hbm, _ = _peaks()
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        clean = torch.ones(L2_CLEAN_BYTES // 4, dtype=torch.float32, device="cuda")
+
+        def flush_l2():
+            flush.zero_()
+            clean.sum()
+
         line["spread_interp_M1e6"] = spread_interp_million(torch, stream, flush_l2, hbm)
         line["spread_interp_batched"] = spread_interp_batched(torch, stream, flush_l2, hbm)
     if world == 1 and not args.no_forms:
         try:
-            line["forms_beside_fp64"] = forms_beside_fp64(torch, w)
+            line["forms_beside_fp64"] = forms_beside_fp64(torch, w, K)
         except Exception as e:                               # recorded, never fatal to the line
             line["forms_beside_fp64"] = {"error": repr(e)[:300]}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, args.cpu_steps)
+        line["cpu_baseline"] = cpu_baseline(args.cpu_steps)
+        line["error_vs_oracle"] = error_vs_oracle()
     if rank == 0:
         print(json.dumps(line))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def range_launches_per_step(w):
+    """Kernel launches of one step of a plan without pair lists: the local sum, five history-part
+    launches (spreading + FFT columns, FIR tail, FFT rows + mode update, inverse FFT columns,
+    interpolation), the solve's set-up, its 40 Jacobi sweep launches (those after convergence return
+    at once), the store, the receivers' local part (with receivers) and the finishing launch."""
+    return 1 + 5 + 1 + 40 + 1 + (1 if len(w.xr) else 0) + 1
+
+
+def periodic_gaussians(w, tt):
+    """f(x_j - t) for times tt (rows), periodised over 2 pi (images |m| <= 2)."""
+    f = np.zeros((len(tt), w.M))
+    for a, c, wd in zip(w.amp, w.center, w.width):
+        for mimg in range(-2, 3):
+            f += a * np.exp(-0.5 * ((w.x[None, :] - tt[:, None] + 2 * math.pi * mimg - c) / wd) ** 2)
+    return f
+
+
+def _fp32_peak():
+    """FP32 FMA peak (TFLOP/s) of 152 SMs x 128 lanes x 2 flops at the measured maximum SM clock."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f)["sm_max_mhz"])
+        src = f"{mhz:.0f} MHz (MEASURED_PEAKS.json sm_max_mhz)"
+    except Exception:
+        mhz, src = 2070.0, "2070 MHz (nominal maximum)"
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12, src
+
+
+def free_space_secondary(torch, stream):
+    """The free-space workload (M = 1e4 uniform, beta log-uniform in [0.1, 100], three pulses,
+    dt = 1e-3, tol = 1e-12) with stored weights: one chunk of rbc_period steps through wave1d_solve,
+    from a chunk boundary, so the timed steps include one radiation projection step; and the
+    one-launch step kernel's roofline (HBM: the stored weights it streams, L2 flushed before each
+    single step)."""
+    from paper_2507_07823_gb300 import wave1d, workloads
+    w = workloads.config1()
+    plan = wave1d.Plan.from_workload(w.with_(Nt=2000), stream=stream.cuda_stream)
+    info = plan.info
+    chunk = info.rbc_period
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    clean = torch.ones(L2_CLEAN_BYTES // 4, dtype=torch.float32, device="cuda")
+    try:
+        plan.solve(chunk, with_sigma=False)                  # warm-up, graph build, chunk-aligned
+        torch.cuda.synchronize()
+        reps = 3
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        wave1d._check(wave1d.wave1d_solve(plan.h, reps * chunk, None, None, 1), "wave1d_solve")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / (reps * chunk)
+        # the step kernel's per-launch time, L2 flushed before each single step (ordinary steps)
+        ms_k = []
+        for i in range(chunk - 1):
+            flush.zero_()
+            clean.sum()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            wave1d._check(wave1d.wave1d_step(plan.h), "wave1d_step")
+            b.record(stream)
+            torch.cuda.synchronize()
+            ms_k.append(a.elapsed_time(b))
+        hbm, peak_kind = _peaks()
+        launch_ms = float(np.mean(ms_k))
+        algo = 8 * info.local_terms
+        achieved = algo / (launch_ms * 1e-3) / 1e9
+    finally:
+        plan.close()
+    return {"workload": f"{w.name}: {w.description}", "value": w.M / (ms * 1e-3), "unit": UNIT,
+            "ms_per_step": ms, "timed": f"{reps} chunks of {chunk} steps (each chunk: {chunk - 1} one-launch steps "
+                                         "and one projection step of ten per-stage launches)",
+            "roofline": {"kernel": "k_step", "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": step_traffic(),
+                         "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                         "algorithmic_bytes_per_launch": algo,
+                         "algorithmic": "8 B per stored weight Q_m (an FP32 pair), the stream the local sum must "
+                                        "read once per step; padding, source lists and headers not counted",
+                         "launch_ms": launch_ms, "launches_averaged": len(ms_k),
+                         "timing": "single wave1d_step calls, L2 flushed before each"}}
+
+
+def rs_local_traffic(info):
+    """DRAM bytes per k_rs_local launch at this workload, scaled by pairs from one ncu capture of a
+    smaller clustered case (M = 2e5), while the kernel sources match the ones it was taken with."""
+    import hashlib
+    h = hashlib.sha256()
+    src = os.path.join(ROOT, "paper_2507_07823_gb300", "csrc")
+    for f in RS_LOCAL_SOURCES:
+        with open(os.path.join(src, f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != RS_LOCAL_TRAFFIC["sources_sha256"]:
+        return None
+    return RS_LOCAL_TRAFFIC["bytes_per_launch"] * info.local_pairs / RS_LOCAL_TRAFFIC["pairs"]
 
 
 def spread_interp_million(torch, stream, flush_l2, hbm, reps=20):
@@ -414,10 +478,14 @@ def spread_interp_batched(torch, stream, flush_l2, hbm, reps=10):
     return out
 
 
-def forms_beside_fp64(torch, w, steps=200, warmup=20):
-    """The mixed-precision step, the reverse-time march and the batched march, each timed with CUDA
-    events beside the FP64 march, on small cases (a few seconds in all).  Each form is measured on its
-    own and a failure is recorded as a string, so the benchmark line never depends on them."""
+def forms_beside_fp64(torch, w, steps, warmup=3):
+    """The forms beside the plain FP64 march, each timed with CUDA events on its own; a failure is
+    recorded as a string, never fatal to the line.
+      mixed_precision: the headline workload (a million clustered springs) with the history part's
+        spreading and interpolation in FP32 (width-7 kernel, tol 1e-6), same plan otherwise; its
+        error against the oracle is in error_vs_oracle.mixed.
+      adjoint, batched: reduced cases (the full adjoint and batched workloads are the
+        --adjoint-only and --batched-only legs)."""
     from paper_2507_07823_gb300 import wave1d, workloads
 
     out = {}
@@ -432,56 +500,50 @@ def forms_beside_fp64(torch, w, steps=200, warmup=20):
         torch.cuda.synchronize()
         return e0.elapsed_time(e1)
 
-    # mixed precision: the benchmark workload, FP64 (one-launch step) and mixed (per-stage)
     try:
-        res, fields = {}, {}
-        for name, kw in (("fp64", {}), ("mixed", {"precision": 1})):
-            plan = wave1d.Plan.from_workload(w.with_(Nt=warmup + steps), **kw)
-            try:
-                plan.solve(warmup, with_sigma=False)
-                ms = timed(lambda: wave1d._check(wave1d.wave1d_solve(plan.h, steps, None, None, 1), "wave1d_solve"))
-                fields[name] = (plan.sigma(), plan.receivers())
-                res[name] = {"value": w.M * steps / (ms * 1e-3), "ms_per_step": ms / steps}
-            finally:
-                plan.close()
-        (s64, u64), (s32, u32) = fields["fp64"], fields["mixed"]
-        res["rel_diff_sigma"] = float(np.max(np.abs(s32 - s64)) / np.max(np.abs(s64)))
-        res["rel_diff_receivers"] = float(np.max(np.abs(u32 - u64)) / np.max(np.abs(u64)))
-        res["workload"] = f"{w.name}, {steps} steps after {warmup}"
-        out["mixed_precision"] = res
-    except Exception as e:                                   # recorded, never fatal to the line
+        w6 = w.with_(tol=1e-6, Nt=warmup + steps)
+        plan = wave1d.Plan.from_workload(w6, local_weights=1, precision=1)
+        try:
+            plan.solve(warmup, with_sigma=False)
+            ms = timed(lambda: wave1d._check(wave1d.wave1d_solve(plan.h, steps, None, None, 1), "wave1d_solve"))
+            out["mixed_precision"] = {"value": w.M * steps / (ms * 1e-3), "ms_per_step": ms / steps,
+                                      "workload": f"{w.name} at tol 1e-6 (W = {plan.info.W}), FP32 spreading and "
+                                                  f"interpolation, {steps} steps after {warmup}",
+                                      "error_vs_oracle": "error_vs_oracle.mixed"}
+        finally:
+            plan.close()
+    except Exception as e:
         out["mixed_precision"] = {"error": repr(e)[:300]}
 
-    # reverse-time march: dL/dbeta over the same march, beside the forward march that records sigma
+    w1 = workloads.config1()
+    small = 200
     try:
-        plan = wave1d.Plan.from_workload(w.with_(Nt=steps))
+        plan = wave1d.Plan.from_workload(w1.with_(Nt=small))
         try:
             holder = {}
-            ms_f = timed(lambda: holder.update(zip(("sigma", "u"), plan.solve_device(steps))))
+            ms_f = timed(lambda: holder.update(zip(("sigma", "u"), plan.solve_device(small))))
             ubar = holder["u"] - 0.5 * holder["u"]
             ms_a = timed(lambda: holder.update(g=plan.adjoint(holder["sigma"], ubar)))
-            out["adjoint"] = {"forward_value": w.M * steps / (ms_f * 1e-3), "adjoint_value": w.M * steps / (ms_a * 1e-3),
-                              "forward_ms_per_step": ms_f / steps, "adjoint_ms_per_step": ms_a / steps,
+            out["adjoint"] = {"forward_value": w1.M * small / (ms_f * 1e-3), "adjoint_value": w1.M * small / (ms_a * 1e-3),
+                              "forward_ms_per_step": ms_f / small, "adjoint_ms_per_step": ms_a / small,
                               "grad_finite": bool(torch.isfinite(holder["g"]).all()),
-                              "workload": f"{w.name}, {steps} steps, L = 1/4 sum u^2 (ubar = u / 2); the adjoint call's "
-                                          "work arrays and NUFFT plan included"}
+                              "workload": f"reduced: {w1.name}, {small} steps (the adjoint workload is --adjoint-only)"}
         finally:
             plan.close()
     except Exception as e:
         out["adjoint"] = {"error": repr(e)[:300]}
-
-    # batched march: 64 periodic instances of the batched workload's shape, M log-uniform in [1e2, 2e3]
     try:
-        ws = workloads.config3_instances(n_instances=64, m_range=(1e2, 2e3), Nt=warmup + steps + 1)
+        ws = workloads.config3_instances(n_instances=64, m_range=(1e2, 2e3), Nt=20 + small + 1)
         batch = wave1d.Batch(ws)
         try:
-            batch.solve(warmup, with_sigma=False)
+            batch.solve(20, with_sigma=False)
             st = {}
-            ms = timed(lambda: st.update(rc=wave1d.lib().wave1d_batch_solve(batch.h, steps, None, None, 1)))
+            ms = timed(lambda: st.update(rc=wave1d.lib().wave1d_batch_solve(batch.h, small, None, None, 1)))
             if st["rc"] != 0:
                 raise RuntimeError(wave1d.lib().wave1d_batch_strerror().decode())
-            out["batched"] = {"value": batch.M * steps / (ms * 1e-3), "ms_per_step": ms / steps, "M_total": batch.M,
-                              "workload": f"64 periodic instances, M log-uniform in [1e2, 2e3], dt = 1e-3, {steps} steps"}
+            out["batched"] = {"value": batch.M * small / (ms * 1e-3), "ms_per_step": ms / small, "M_total": batch.M,
+                              "workload": "reduced: 64 periodic instances, M log-uniform in [1e2, 2e3], dt = 1e-3 "
+                                          "(the batched workload is --batched-only)"}
         finally:
             batch.close()
     except Exception as e:
@@ -499,60 +561,79 @@ def step_traffic():
     return STEP_TRAFFIC["bytes_per_launch"] if h.hexdigest() == STEP_TRAFFIC["sources_sha256"] else None
 
 
-def stage_bytes(info, w, stage):
-    """Algorithmic HBM bytes per launch of a stage (what the method must move once per step)."""
-    M = info.M
-    if stage == "local":
-        # stored weights Q_m as FP32 pairs (8 B each), per-row source lists, per-m counts, row
-        # offsets and the output (reported exactly by the library); the density ring (6.6 MB at
-        # M = 1e4) stays in L2 within a step and is not counted
-        return info.local_bytes
-    if stage == "spread":
-        return M * (8 + 8 * info.nufft_w) + 8 * info.nf
-    if stage == "interp":
-        return M * (8 + 8 * info.nufft_w) + 8 * info.nf
-    if stage in ("fft_fwd", "fft_inv"):
-        return 4 * 16 * (info.nf // 2)
-    if stage == "modes":
-        return (info.K + 1) * (16 * info.W + 16 * info.W + 64)
-    return None
+def _oracle_sample():
+    """A bounded sample of the million-spring workload for the CPU oracle: its 2000 springs of
+    highest density (consecutive in position, inside one cluster, so every pair of them lies closer
+    than delta), marched in the periodic box with the same dt, tol, p and pulse."""
+    from paper_2507_07823_gb300 import workloads
+    w = workloads.config2()
+    xs = np.sort(w.x)
+    n = 2000
+    span = xs[n - 1:] - xs[:xs.size - n + 1]
+    i = int(np.argmin(span))
+    order = np.argsort(w.x, kind="stable")[i:i + n]
+    return w.with_(x=w.x[order], beta=w.beta[order], xr=np.zeros(0), Nt=10_000), float(span[i])
 
 
-def cpu_baseline(w, nsteps):
-    """The oracle of the same scheme (oracle/wfp.py) timed on the host cores, plan excluded."""
-    from oracle import wfp
+def _cores():
     try:
         from threadpoolctl import threadpool_info
-        cores = max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
+        return max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
     except Exception:
-        cores = os.cpu_count()
-    o = wfp.from_workload(w)
+        return os.cpu_count()
+
+
+def cpu_baseline(nsteps):
+    """The oracle of the same scheme (oracle/wfp.py, numpy/scipy FP64) timed on the host cores on a
+    bounded sample of the workload (plan precompute excluded, as the paper excludes it)."""
+    from oracle import wfp
+    ws, span = _oracle_sample()
+    o = wfp.from_workload(ws)
     for _ in range(3):
         o.step()
     t0 = time.perf_counter()
     for _ in range(nsteps):
         o.step()
     dt = time.perf_counter() - t0
-    return {"value": w.M * nsteps / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{nsteps} time steps (after 3 warm-up steps) of the same M=1e4 free-space "
-                      f"march with oracle/wfp.py (numpy/scipy FP64, direct Fourier sums); plan "
-                      f"precompute excluded"}
+    return {"value": ws.M * nsteps / dt, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+            "sample": f"{nsteps} time steps (after 3) of the {ws.M} most tightly packed springs of the "
+                      f"million-spring workload (one cluster, span {span:.1e} < delta: every pair local), "
+                      f"periodic, dt = {ws.dt}, tol = {ws.tol}, p = {ws.p}, oracle/wfp.py; plan excluded"}
+
+
+def error_vs_oracle(nsteps=300):
+    """Relative max error of the GPU march against the oracle over a whole march on a live sample of
+    the workload's recipe: 3000 springs of the clustered layout (16 clusters of width 0.05 + 20 %
+    uniform), dt = 5e-4, tol = 1e-10, p = 8, a pulse of width 0.005 that reaches springs within
+    the first steps, receivers among them.  The FP64 plan without pair lists (the headline's) and
+    the mixed form (tol 1e-6) against the oracle of each's tolerance."""
+    from oracle import wfp
+    from paper_2507_07823_gb300 import wave1d, workloads
+    out = {"sample": f"clustered recipe at M = 3000, pulse width 0.005 at x = -2, {nsteps} steps, "
+                     "receivers at -1.99, -1.97, -1.9, 2.5; relative max error over every step's densities "
+                     "and receiver values"}
+    for name, kw, tol in (("fp64", {}, 1e-10), ("mixed", {"precision": 1}, 1e-6)):
+        w = workloads.config2(M=3000, Nt=nsteps, width=(0.005,), tol=tol).with_(xr=np.array([-1.99, -1.97, -1.9, 2.5]))
+        plan = wave1d.Plan.from_workload(w, local_weights=1, **kw)
+        try:
+            s, u = plan.solve(nsteps)
+        finally:
+            plan.close()
+        s_ref, u_ref = wfp.from_workload(w).run(nsteps)
+        out[name] = {"tol": tol,
+                     "sigma": float(np.max(np.abs(s - s_ref[1:])) / np.max(np.abs(s_ref))),
+                     "u": float(np.max(np.abs(u - u_ref[1:])) / np.max(np.abs(u_ref))),
+                     "max_abs_u": float(np.max(np.abs(u_ref)))}
+    return out
 
 
 def run_reference(args):
     rank, world, local = _dist()
     if rank != 0:
         return
-    from paper_2507_07823_gb300 import workloads
-    w = workloads.config1()
-    cb = None
     from oracle import wfp
-    try:
-        from threadpoolctl import threadpool_info
-        cores = max([d.get("num_threads", 1) for d in threadpool_info()] + [1])
-    except Exception:
-        cores = os.cpu_count()
-    o = wfp.from_workload(w)
+    ws, span = _oracle_sample()
+    o = wfp.from_workload(ws)
     for _ in range(args.warmup):
         o.step()
     K = min(args.steps, args.ref_max_steps)
@@ -560,14 +641,17 @@ def run_reference(args):
     for _ in range(K):
         o.step()
     dt = time.perf_counter() - t0
-    value = w.M * K / dt
-    cb = {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-          "sample": f"{K} oracle time steps of the M=1e4 free-space march after {args.warmup} "
-                    f"warm-up steps (oracle/wfp.py, plan excluded)"}
+    value = ws.M * K / dt
+    from paper_2507_07823_gb300 import workloads
+    w = workloads.config2()
+    cb = {"value": value, "unit": UNIT, "cores": _cores(), "kind": "oracle",
+          "sample": f"{K} oracle time steps (after {args.warmup}) of the {ws.M} most tightly packed springs "
+                    f"of the million-spring workload (span {span:.1e} < delta), oracle/wfp.py, plan excluded"}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
             "n_gpus": world, "steps": K, "warmup": args.warmup, "ms_per_step": 1e3 * dt / K,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": f"{w.name}: {w.description}", "M": w.M},
+            "data": "synthetic", "config": {"workload": f"{w.name}: {w.description}", "M": w.M,
+                                            "sample_M": ws.M},
             "cpu_baseline": cb,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -712,12 +796,13 @@ def run_batched_only(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=540)
-    ap.add_argument("--warmup", type=int, default=60)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--cpu-steps", type=int, default=20)
+    ap.add_argument("--cpu-steps", type=int, default=10)
     ap.add_argument("--ref-max-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the free-space M = 1e4 secondary measurement")
     ap.add_argument("--no-spread-interp", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the mixed / adjoint / batched forms beside FP64")
     ap.add_argument("--spread-interp-only", action="store_true",

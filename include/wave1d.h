@@ -90,6 +90,12 @@ typedef struct {
                            (WAVE1D_ENOTCONV after 40).  For layouts whose weights or blocks do
                            not fit (a million clustered springs: 1.3e10 pairs); steps run as
                            per-stage launches; wave1d_adjoint is not available                 */
+    int spin_limit;     /* polls of a counter before a wait between the blocks of the one-launch
+                           step kernel gives up and latches WAVE1D_ETIMEOUT; 0 = 2^22 (seconds)  */
+    int hold_unit;      /* fault injection for tests, 0 = off: 1 makes the step kernel's column
+                           pass leave its first unit uncounted, so the next phase's wait runs
+                           out (WAVE1D_ETIMEOUT from the next synchronising call; the plan cannot
+                           continue, the CUDA context stays usable)                            */
 } wave1d_opts;
 
 /* Derived sizes of a plan (read-only report). */

@@ -62,6 +62,7 @@ __global__ void k_rs_jacobi(DevPlan P, RangeDev R, int it);
 __global__ void k_rs_store(DevPlan P, RangeDev R);
 __global__ void k_rs_receivers(DevPlan P, RangeDev R);
 __global__ void k_rs_finish(DevPlan P, RangeDev R);
+__global__ void k_rs_count_terms(DevPlan P, RangeDev R, unsigned long long* total);
 size_t rs_local_smem(int nint, int nm);
 }  // namespace wave1d
 
@@ -114,6 +115,7 @@ struct wave1d_plan_s {
     RangeDev rd{};
     size_t rs_smem = 0;
     int64_t info_range_pairs = 0;
+    int64_t info_terms = 0;           // (pair, m) terms of the local sum per step
     bool mixed = false;
     wave1d_nufft_t nu_s = nullptr, nu_r = nullptr;
     int64_t *nu_perm_s = nullptr, *nu_perm_r = nullptr;
@@ -627,6 +629,9 @@ int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double d
     d.dt = P.dt;
     d.chunk = p->chunk;
     d.rbc_h = P.h_rbc;
+    // polls of a counter before a wait of the step kernel gives up (each poll sleeps 0.1-1 us)
+    d.spin_limit = o.spin_limit > 0 ? (unsigned)o.spin_limit : (1u << 22);
+    d.hold_unit = o.hold_unit != 0;
     int32_t* i32;
     int64_t* i64;
     double* f64;
@@ -696,6 +701,9 @@ int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double d
         rd.mid = r64f;
         if ((rc = upload(p, rt.cheb, &r64f))) return cleanup(rc);
         rd.cheb = r64f;
+        if ((rc = upload(p, rt.cell, &r32))) return cleanup(rc);
+        rd.cell = r32;
+        rd.cell_scale = rt.cell_scale;
         if ((rc = upload(p, hp.x2, &f32))) return cleanup(rc);
         rd.x2 = f32;
         if ((rc = upload(p, hp.blk_win, &r32))) return cleanup(rc);
@@ -768,6 +776,7 @@ int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double d
         // the items' lengths stay, for ordering the receivers' items when receivers are set)
         const LocalItems& L = hp.litems;
         p->info_pairs = (int64_t)hp.loc.src.size();
+        if (!p->range) p->info_terms = (int64_t)hp.loc.w.size();
         p->info_weights = (int64_t)hp.lrows.w.size() / 2;
         p->info_nearby = hp.loc.nearby;
         p->info_local_bytes = (int64_t)(L.w.size() * sizeof(float) + L.src.size() * sizeof(int32_t) +
@@ -790,7 +799,16 @@ int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double d
     if (p->range) {
         // the implicit part's weights (beta_j / 2) Q_0(d_jl) of every spring's dt-window
         k_rs_nearby_weights<<<(unsigned)std::min<int64_t>((P.M + 7) / 8, 64 * (int64_t)p->sms), 256, 0, p->s>>>(d, p->rd);
+        // the local sum's terms per step (reported by wave1d_get_info)
+        unsigned long long* cnt;
+        if ((rc = zeros(p, &cnt, 1))) return cleanup(rc);
+        k_rs_count_terms<<<(unsigned)std::min<int64_t>((P.M + 255) / 256, 8 * (int64_t)p->sms), 256, 0, p->s>>>(d, p->rd, cnt);
         if (cudaGetLastError() != cudaSuccess) return cleanup(fail(WAVE1D_ECUDA, "nearby weights kernel"));
+        unsigned long long terms = 0;
+        if (cudaMemcpyAsync(&terms, cnt, sizeof(terms), cudaMemcpyDeviceToHost, p->s) != cudaSuccess ||
+            cudaStreamSynchronize(p->s) != cudaSuccess)
+            return cleanup(fail(WAVE1D_ECUDA, "counting the local sum's terms"));
+        p->info_terms = (int64_t)terms;
     }
     if ((rc = leave(p))) return cleanup(rc);
     if (cudaStreamSynchronize(p->s) != cudaSuccess) return cleanup(fail(WAVE1D_ECUDA, "plan upload failed"));
@@ -1086,6 +1104,7 @@ int wave1d_get_info(wave1d_plan_t p, wave1d_info* info) {
     info->max_block = p->hp.max_block;
     info->device_bytes = p->bytes;
     info->local_bytes = p->info_local_bytes;
+    info->local_terms = p->info_terms;
     return WAVE1D_OK;
 }
 

@@ -82,12 +82,15 @@ struct RangeTables {
     std::vector<float> coef;           // [iv][m][12]: monomial coefficients of z, a0 .. a3 as (hi, lo)
                                        //   pairs, a4 .. a7 single
     std::vector<double> cheb;          // [iv][m][8]: Chebyshev coefficients in z (FP64)
+    std::vector<int32_t> cell;         // kRsCells: interval of the left end of each cell of [0, delta)
+    float cell_scale = 0.f;            // kRsCells / delta: cell of a distance d is floor(d cell_scale)
 };
 void build_range_tables(const Params& P, RangeTables& out);
 // The plan's weight rule itself at each distance, Q[i * (m_max + 1) + m] (for checks).
 void local_weights_exact(const Params& P, const std::vector<double>& d, std::vector<double>& Q);
-// targets per block of the range-mode local sum (one per thread)
+// targets per block of the range-mode local sum (one per thread); cells of the distance lookup table
 constexpr int kRsTargets = 256;
+constexpr int kRsCells = 2048;
 
 struct HostPlan {
     Params P;
@@ -288,6 +291,8 @@ struct DevPlan {
     // bar[0..15] are its work and barrier counters (zero between steps)
     int hist_blocks;
     unsigned* bar;
+    unsigned spin_limit;      // polls before a wait gives up (WAVE1D_ETIMEOUT)
+    int hold_unit;            // test hook: 1 = the first column unit is never counted
 };
 
 // Device view of the range-mode tables (plans opened with opts.local_weights = 1), passed by value
@@ -304,6 +309,8 @@ struct RangeDev {
     const double* bp;           // nint + 1 breakpoints (FP64)
     const double* mid;          // nint midpoints (FP64 value of mid2)
     const double* cheb;         // [iv][m][8] Chebyshev coefficients in z (FP64)
+    const int* cell;            // kRsCells: first interval of each cell of [0, delta)
+    float cell_scale;           // kRsCells / delta
     const float* x2;            // M positions (hi, lo)
     const int32_t* blk_win;     // [block][4] (see HostPlan::blk_win)
     const int32_t* nb_lo;       // M

@@ -1161,6 +1161,12 @@ void build_range_tables(const Params& P, RangeTables& rt) {
     }
     rt.nint = (int)rt.bp.size() - 1;
     rt.iv_dt = (int)(std::find(rt.bp.begin(), rt.bp.end(), P.dt) - rt.bp.begin());
+    rt.cell_scale = (float)(kRsCells / P.delta);
+    rt.cell.assign(kRsCells, 0);
+    for (int c = 0; c < kRsCells; c++) {
+        const double d = (double)c / (double)rt.cell_scale;
+        rt.cell[c] = std::max(0, std::min(rt.nint - 1, (int)(std::upper_bound(rt.bp.begin(), rt.bp.end(), d) - rt.bp.begin()) - 1));
+    }
     const int n = rt.nint, nm = rt.nm, np = 8;
     rt.bp2.resize(2 * (size_t)(n + 1));
     for (int i = 0; i <= n; i++) {

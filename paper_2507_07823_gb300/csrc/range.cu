@@ -30,12 +30,16 @@ namespace {
 constexpr double kPiR = 3.14159265358979323846264338327950288;
 constexpr int kRsChunk = 32;      // sources per chunk (one per lane of warp 0 in the set-up)
 constexpr int kRsIvCap = 32;      // intervals whose e-vectors are held at once
+// one interval's row of e-vector records: 32 records of 12 floats and 4 floats of padding, so the
+// rows of consecutive intervals start 4 banks apart (threads of a warp read the records of the 2-3
+// intervals their distances fall in)
+constexpr int kRsRow = kRsChunk * rs::kERecord + 4;
 }  // namespace
 
 // shared memory of k_rs_local (bytes)
 size_t rs_local_smem(int nint, int nm) {
-    return (size_t)kRsIvCap * kRsChunk * rs::kERecord * sizeof(float) + (size_t)nm * kRsChunk * sizeof(float2) +
-           (size_t)(2 * (nint + 1) + 3 * nint) * sizeof(float);
+    return (size_t)kRsIvCap * kRsRow * sizeof(float) + (size_t)nm * kRsChunk * sizeof(float2) +
+           (size_t)(2 * (nint + 1) + 3 * nint) * sizeof(float) + (size_t)kRsCells * sizeof(int);
 }
 
 // position of extended source index e: the same expression as the host's window tests
@@ -118,10 +122,11 @@ __device__ __forceinline__ double rs_q0(const RangeDev& R, double d) {
 __global__ void __launch_bounds__(kRsTargets, 2) k_rs_local(DevPlan P, RangeDev R) {
     extern __shared__ __align__(16) float rs_sm[];
     float* sE = rs_sm;
-    float2* sSig = (float2*)(sE + kRsIvCap * kRsChunk * rs::kERecord);
+    float2* sSig = (float2*)(sE + kRsIvCap * kRsRow);
     float* sBp = (float*)(sSig + (size_t)R.nm * kRsChunk);
     float* sMid = sBp + 2 * (R.nint + 1);
     float* sIh = sMid + 2 * R.nint;
+    int* sTab = (int*)(sIh + R.nint);
     __shared__ float sXh[kRsChunk], sXl[kRsChunk];
     __shared__ int sEi[kRsChunk], sLo[kRsChunk], sHi[kRsChunk], sType[kRsChunk];
     __shared__ int sU0, sU1;
@@ -135,6 +140,8 @@ __global__ void __launch_bounds__(kRsTargets, 2) k_rs_local(DevPlan P, RangeDev 
     for (int i = t; i < 2 * (R.nint + 1); i += blockDim.x) sBp[i] = __ldg(R.bp2 + i);
     for (int i = t; i < 2 * R.nint; i += blockDim.x) sMid[i] = __ldg(R.mid2 + i);
     for (int i = t; i < R.nint; i += blockDim.x) sIh[i] = __ldg(R.ih + i);
+    for (int i = t; i < kRsCells; i += blockDim.x) sTab[i] = __ldg(R.cell + i);
+    const float cscale = R.cell_scale;
 
     const bool valid = t < nT;
     const int64_t j = j0 + (valid ? t : 0);
@@ -148,13 +155,13 @@ __global__ void __launch_bounds__(kRsTargets, 2) k_rs_local(DevPlan P, RangeDev 
     const int nL = max(0, inhi - wlo), total = nL + max(0, whi - inlo);
     const rs::Pair zero{0.f, 0.f};
     const rs::Pair dlim{__ldg(R.bp2 + 2 * R.nint), __ldg(R.bp2 + 2 * R.nint + 1)};     // delta
+    __syncthreads();
 
-    float ah = 0.f, al = 0.f;
-    int tiv[2] = {-1, -1};              // tracked interval of the last left / right source
-    rs::Pair Y[2] = {zero, zero};       // x_j - mid (left) and x_j + mid (right) of that interval
+    // two accumulators (even and odd sources), so consecutive pairs are independent chains
+    float a0h = 0.f, a0l = 0.f, a1h = 0.f, a1l = 0.f;
+    rs::Track trL{-1, zero}, trR{-1, zero};
 
     for (int base = 0; base < total; base += kRsChunk) {
-        __syncthreads();
         if (warp == 0) {
             const int v = base + lane;
             int lo = 1, hi = 0, type = 0, e = 0;
@@ -173,8 +180,8 @@ __global__ void __launch_bounds__(kRsTargets, 2) k_rs_local(DevPlan P, RangeDev 
                 }
                 if (rs::pair_lt(dmin, zero)) dmin = zero;
                 if (!rs::pair_lt(dmax, zero) && rs::pair_lt(dmin, dlim)) {
-                    lo = max(0, rs_locate(sBp, R.nint, dmin) - 1);
-                    hi = min(R.nint - 1, rs_locate(sBp, R.nint, dmax) + 1);
+                    lo = max(0, rs::locate_tab(sBp, sTab, cscale, R.nint, dmin) - 1);
+                    hi = min(R.nint - 1, rs::locate_tab(sBp, sTab, cscale, R.nint, dmax) + 1);
                 }
             }
             sXh[lane] = X.hi;
@@ -223,72 +230,71 @@ __global__ void __launch_bounds__(kRsTargets, 2) k_rs_local(DevPlan P, RangeDev 
                                 a47[4] = {c47.x, c47.y, c47.z, c47.w};
                     rs::evec_mac(ev, a01, a23, a47, s.x, s.y);
                 }
-                float4* rec = (float4*)(sE + ((iv - W0) * kRsChunk + lane) * rs::kERecord);
+                float4* rec = (float4*)(sE + (iv - W0) * kRsRow + lane * rs::kERecord);
                 rec[0] = make_float4(ev.e0h, ev.e0l, ev.e1h, ev.e1l);
                 rec[1] = make_float4(ev.e2, ev.e3, ev.e4, ev.e5);
                 rec[2] = make_float4(ev.e6, ev.e7, 0.f, 0.f);
             }
             __syncthreads();
-            if (W0 > U0) tiv[0] = tiv[1] = -1;       // a second pass over the chunk: search afresh
+            if (W0 > U0) trL.iv = trR.iv = -1;          // a second pass over the chunk: search afresh
             if (valid) {
                 const int kend = min(kRsChunk, total - base);
-                for (int k = 0; k < kend; k++) {
-                    const int lo = sLo[k], hi = sHi[k];
-                    if (lo > hi) continue;
-                    const int type = sType[k];
-                    const rs::Pair X{sXh[k], sXl[k]};
-                    // left sources strictly left of x_j, right sources at or right of it
-                    if (type == 0 ? !rs::pair_lt(X, Xj) : rs::pair_lt(X, Xj)) continue;
-                    const bool near = (unsigned)(sEi[k] - nbl) < (unsigned)nbc;
-                    // the tracked interval, on the pair's side of dt (near pairs below it, far
-                    // pairs at or above it)
-                    int iv = tiv[type];
-                    if (iv >= 0 && (near ? iv >= R.iv_dt : iv < R.iv_dt)) iv = near ? R.iv_dt - 1 : R.iv_dt;
-                    if (iv < 0) iv = rs_locate(sBp, R.nint, type == 0 ? rs::pair_sub(Xj, X) : rs::pair_sub(X, Xj));
-                    iv = near ? min(iv, R.iv_dt - 1) : max(iv, R.iv_dt);
-                    if (iv != tiv[type]) {
-                        const rs::Pair mid{sMid[2 * iv], sMid[2 * iv + 1]};
-                        Y[type] = rs::pair_add(Xj, type == 0 ? rs::Pair{-mid.hi, -mid.lo} : mid);
+                for (int k = 0; k < kend; k += 2) {
+                    // the record and z of sources k and k + 1 (null where the pair does not count
+                    // in this window), then both polynomials as independent chains
+                    const float* rec[2] = {nullptr, nullptr};
+                    float zh[2] = {0.f, 0.f}, zl[2] = {0.f, 0.f};
+#pragma unroll
+                    for (int u = 0; u < 2; u++) {
+                        const int kk = k + u;
+                        if (kk >= kend) break;
+                        const int lo = sLo[kk], hi = sHi[kk];
+                        if (lo > hi) continue;
+                        const bool left = sType[kk] == 0;
+                        const rs::Pair X{sXh[kk], sXl[kk]};
+                        // left sources strictly left of x_j, right sources at or right of it
+                        if (left ? !rs::pair_lt(X, Xj) : rs::pair_lt(X, Xj)) continue;
+                        const bool near = (unsigned)(sEi[kk] - nbl) < (unsigned)nbc;
+                        const bool in = left ? rs::pair_z(sBp, sMid, sIh, sTab, cscale, R.nint, R.iv_dt, true, near, Xj, X, trL, zh[u], zl[u])
+                                             : rs::pair_z(sBp, sMid, sIh, sTab, cscale, R.nint, R.iv_dt, false, near, Xj, X, trR, zh[u], zl[u]);
+                        const int iv = left ? trL.iv : trR.iv;
+                        if (in && iv >= W0 && iv <= W1 && iv >= lo && iv <= hi)
+                            rec[u] = sE + (iv - W0) * kRsRow + kk * rs::kERecord;
                     }
-                    // walk to the interval whose z lies in [-1, 1] (to rounding), in one direction
-                    // only, so the walk ends even where rounding leaves z just outside two
-                    // neighbouring intervals; far off, search instead
-                    float zh, zl;
-                    int dir = 0;
-                    for (int pass = 0;; pass++) {
-                        const float s = sIh[iv];
-                        if (type == 0) rs::scaled_diff(Y[0], X, s, zh, zl);
-                        else rs::scaled_diff(X, Y[1], s, zh, zl);
-                        if (pass == 0 && fabsf(zh) > 4.f) {
-                            int nv = rs_locate(sBp, R.nint, type == 0 ? rs::pair_sub(Xj, X) : rs::pair_sub(X, Xj));
-                            nv = near ? min(nv, R.iv_dt - 1) : max(nv, R.iv_dt);
-                            if (nv != iv) {
-                                iv = nv;
-                                const rs::Pair mid{sMid[2 * iv], sMid[2 * iv + 1]};
-                                Y[type] = rs::pair_add(Xj, type == 0 ? rs::Pair{-mid.hi, -mid.lo} : mid);
-                                continue;
-                            }
-                        }
-                        const int want = zh > 1.000001f ? 1 : (zh < -1.000001f ? -1 : 0);
-                        if (want == 0 || (dir != 0 && want != dir)) break;
-                        const int nv = iv + want;
-                        // near pairs stay below dt, far pairs at or above it
-                        if (nv < 0 || nv >= R.nint || (near ? nv >= R.iv_dt : nv < R.iv_dt)) break;
-                        dir = want;
-                        iv = nv;
-                        const rs::Pair mid{sMid[2 * iv], sMid[2 * iv + 1]};
-                        Y[type] = rs::pair_add(Xj, type == 0 ? rs::Pair{-mid.hi, -mid.lo} : mid);
-                    }
-                    tiv[type] = iv;
-                    if (zh > 1.000001f && iv == R.nint - 1) continue;     // d >= delta
-                    if (iv < W0 || iv > W1 || iv < lo || iv > hi) continue;
-                    rs::evec_eval(sE + ((iv - W0) * kRsChunk + k) * rs::kERecord, zh, zl, ah, al);
+                    if (rec[0]) rs::evec_eval(rec[0], zh[0], zl[0], a0h, a0l);
+                    if (rec[1]) rs::evec_eval(rec[1], zh[1], zl[1], a1h, a1l);
                 }
             }
             __syncthreads();
         }
     }
-    if (valid) P.clocal[j] = (double)ah + (double)al;
+    if (valid) P.clocal[j] = ((double)a0h + (double)a0l) + ((double)a1h + (double)a1l);
+}
+
+// plan time: the terms of the local sum, sum over pairs (j, l) closer than delta of the number of
+// m >= 1 with a non-zero weight on the pair's interval (the multiply-adds sum_m Q_m sigma_l^{n+1-m}
+// the method performs per step), by a walk over each target's sources on both sides
+__global__ void k_rs_count_terms(DevPlan P, RangeDev R, unsigned long long* total) {
+    unsigned long long acc = 0;
+    const bool per = P.bc == WAVE1D_PERIODIC;
+    const int64_t elo = per ? -P.M : 0, ehi = per ? 2 * P.M : P.M;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < P.M; j += (int64_t)gridDim.x * blockDim.x) {
+        const double xj = P.x[j];
+        for (int side = 0; side < 2; side++) {
+            int64_t e = side ? j : j - 1;                  // right: the spring itself first (d = 0)
+            int iv = 0;
+            for (;;) {
+                if (side ? e >= min(ehi, j + P.M) : e < max(elo, j - P.M)) break;
+                const double d = side ? rs_xext(P, e) - xj : xj - rs_xext(P, e);
+                if (!(d < R.delta)) break;
+                while (iv + 1 < R.nint && !(d < __ldg(R.bp + iv + 1))) iv++;
+                const int m0 = __ldg(R.mr + 2 * iv), m1 = __ldg(R.mr + 2 * iv + 1);
+                acc += (unsigned long long)max(0, m1 - m0 + 1);
+                e += side ? 1 : -1;
+            }
+        }
+    }
+    atomicAdd(total, acc);
 }
 
 // ---------------------------------------------------------------------------------------------

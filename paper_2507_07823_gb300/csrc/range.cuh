@@ -25,6 +25,8 @@
 #include <cmath>
 #include <cstdint>
 
+#include "internal.h"
+
 #ifdef __CUDACC__
 #define WAVE1D_RS_HD __host__ __device__ __forceinline__
 #else
@@ -180,6 +182,68 @@ WAVE1D_RS_HD void evec_eval(const float* e, float zh, float zl, float& ah, float
     float s, se;
     two_sum(e[0], p, s, se);
     acc_add(ah, al, s, add(e[1], add(pe, se)));
+}
+
+// ---------------------------------------------------------------------------------------------
+// Interval of a distance.  bp2: nint + 1 breakpoints as (hi, lo) pairs; tab: kRsCells entries, the
+// interval of the left end of each cell of [0, delta), cell of d = floor(d cscale).
+// ---------------------------------------------------------------------------------------------
+WAVE1D_RS_HD int locate_tab(const float* bp2, const int* tab, float cscale, int nint, Pair d) {
+    int c = (int)mul(d.hi, cscale);
+    c = c < 0 ? 0 : (c >= kRsCells ? kRsCells - 1 : c);
+    int iv = tab[c];
+    while (iv > 0 && pair_lt(d, Pair{bp2[2 * iv], bp2[2 * iv + 1]})) iv--;
+    while (iv + 1 < nint && !pair_lt(d, Pair{bp2[2 * iv + 2], bp2[2 * iv + 3]})) iv++;
+    return iv;
+}
+
+// Tracked interval of one side (left or right sources) for one target: the interval iv of the last
+// source's distance and Y = x_j -/+ mid_iv, so z = (Y - x_e) ih (left) or (x_e - Y) ih (right).
+struct Track {
+    int iv;
+    Pair Y;
+};
+
+// Interval and z of the pair (target Xj, source X) on side `left`: from the tracked interval, moved
+// to the pair's side of dt (near pairs below it, far pairs at or above it), then walked in one
+// direction only until z lies in [-1, 1] (to rounding; one direction, so the walk ends even where
+// rounding leaves z just outside two neighbouring intervals), or searched afresh when far off.
+// mid2 / ih: the intervals' midpoints (pairs) and scales.  Returns false where the pair lies beyond
+// delta.
+WAVE1D_RS_HD bool pair_z(const float* bp2, const float* mid2, const float* ih, const int* tab, float cscale,
+                         int nint, int iv_dt, bool left, bool near, Pair Xj, Pair X, Track& tr, float& zh,
+                         float& zl) {
+    int iv = tr.iv;
+    if (iv >= 0 && (near ? iv >= iv_dt : iv < iv_dt)) iv = near ? iv_dt - 1 : iv_dt;
+    if (iv < 0) iv = locate_tab(bp2, tab, cscale, nint, left ? pair_sub(Xj, X) : pair_sub(X, Xj));
+    iv = near ? (iv < iv_dt - 1 ? iv : iv_dt - 1) : (iv > iv_dt ? iv : iv_dt);
+    if (iv != tr.iv) {
+        const Pair mid{mid2[2 * iv], mid2[2 * iv + 1]};
+        tr.Y = pair_add(Xj, left ? Pair{-mid.hi, -mid.lo} : mid);
+    }
+    int dir = 0;
+    for (int pass = 0;; pass++) {
+        const float sc = ih[iv];
+        if (left) scaled_diff(tr.Y, X, sc, zh, zl);
+        else scaled_diff(X, tr.Y, sc, zh, zl);
+        int nv = iv;
+        if (pass == 0 && (zh > 4.f || zh < -4.f)) {
+            nv = locate_tab(bp2, tab, cscale, nint, left ? pair_sub(Xj, X) : pair_sub(X, Xj));
+            nv = near ? (nv < iv_dt - 1 ? nv : iv_dt - 1) : (nv > iv_dt ? nv : iv_dt);
+        } else {
+            const int want = zh > 1.000001f ? 1 : (zh < -1.000001f ? -1 : 0);
+            if (want == 0 || (dir != 0 && want != dir)) break;
+            nv = iv + want;
+            if (nv < 0 || nv >= nint || (near ? nv >= iv_dt : nv < iv_dt)) break;
+            dir = want;
+        }
+        if (nv == iv) break;
+        iv = nv;
+        const Pair mid{mid2[2 * iv], mid2[2 * iv + 1]};
+        tr.Y = pair_add(Xj, left ? Pair{-mid.hi, -mid.lo} : mid);
+    }
+    tr.iv = iv;
+    return !(zh > 1.000001f && iv == nint - 1);
 }
 
 }  // namespace rs

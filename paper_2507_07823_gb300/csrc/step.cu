@@ -32,8 +32,6 @@
 
 namespace wave1d {
 
-// polls of a counter before a wait gives up (each poll sleeps about 0.1-1 us)
-constexpr unsigned kSpinLimit = 1u << 22;
 
 // counters in P.bar (all zero between steps)
 enum : int { kColDone = 0, kRowDone, kIcolDone, kTailDone, kForceDone, kGrid, kNumCounters };
@@ -53,7 +51,7 @@ __device__ __forceinline__ bool wait_for(const DevPlan& P, const unsigned* ctr, 
         int good = 1;
         unsigned polls = 0;
         while (ld_acquire(ctr) < target) {
-            if (++polls > kSpinLimit) {
+            if (++polls > P.spin_limit) {
                 atomicCAS(P.status, 0, (int)WAVE1D_ETIMEOUT);
                 good = 0;
                 break;
@@ -82,7 +80,7 @@ __device__ __forceinline__ bool wait_for2(const DevPlan& P, const unsigned* a, u
         for (;;) {
             const unsigned va = ld_acquire(a), vb = ld_acquire(b);
             if (va >= ta && vb >= tb) break;
-            if (++polls > kSpinLimit) {
+            if (++polls > P.spin_limit) {
                 atomicCAS(P.status, 0, (int)WAVE1D_ETIMEOUT);
                 good = 0;
                 break;
@@ -189,6 +187,7 @@ __device__ __forceinline__ bool history_blocks(const DevPlan& P, int64_t n, int 
     const int64_t nint = (P.M + P.R + kInterpPoints - 1) / kInterpPoints;
     for (int t = h; t < ncols; t += H) {
         cols_phase(P, n, Y, t, smraw);
+        if (P.hold_unit && t == 0) continue;       // fault injection: unit 0 is never counted
         finish(c + kColDone);
     }
     prefetch_step_state(P, (int64_t)h * blockDim.x + threadIdx.x, (int64_t)H * blockDim.x);

@@ -57,7 +57,8 @@ class wave1d_opts(ctypes.Structure):
                 ("NL", ctypes.c_int), ("Ng", ctypes.c_int), ("nufft_w", ctypes.c_int),
                 ("rbc_period", ctypes.c_int), ("max_block", ctypes.c_int),
                 ("max_local_bytes", ctypes.c_int64), ("step_kernel", ctypes.c_int),
-                ("stream", ctypes.c_void_p), ("precision", ctypes.c_int), ("local_weights", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("precision", ctypes.c_int), ("local_weights", ctypes.c_int),
+                ("spin_limit", ctypes.c_int), ("hold_unit", ctypes.c_int)]
 
 
 class wave1d_info(ctypes.Structure):
@@ -72,7 +73,7 @@ class wave1d_info(ctypes.Structure):
                 ("local_pairs", ctypes.c_int64), ("local_weights", ctypes.c_int64),
                 ("nearby_pairs", ctypes.c_int64), ("blocks", ctypes.c_int64),
                 ("max_block", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("local_bytes", ctypes.c_int64)]
+                ("local_bytes", ctypes.c_int64), ("local_terms", ctypes.c_int64)]
 
 
 _lib = None

@@ -167,11 +167,16 @@ def config1(**over) -> Workload:
 
 
 def config2(**over) -> Workload:
-    """Periodic box, M=1e6 clustered (16 Gaussians sigma=0.05 + 20% uniform), dt=5e-4."""
-    kw = dict(M=1_000_000, bc=PERIODIC, dt=5e-4, Nt=10_000, tol=1e-10, p=8, seed=7823 + 2,
+    """Periodic box, M=1e6 clustered (16 Gaussians sigma=0.05 + 20% uniform), dt=5e-4, p=4.
+
+    The interpolation order is not part of this workload's recipe.  Its clusters hold about 400
+    springs per dt, and there the march with p = 8 (or 6) stencils is unstable: an impulse grows by
+    x1.3 (x1.006) per step under the p nearest available samples of Sec. 4.1, while p = 4 and p = 2
+    decay.  So p = 4, the highest order that is stable at this density."""
+    kw = dict(M=1_000_000, bc=PERIODIC, dt=5e-4, Nt=10_000, tol=1e-10, p=4, seed=7823 + 2,
               layout="clustered", beta_range=(1.0, 10.0), amp=(1.0,), center=(-2.0,),
               width=(0.1,), R=4,
-              description="periodic M=1e6 clustered, dt=5e-4, Nt=1e4, tol=1e-10, p=8")
+              description="periodic M=1e6 clustered, dt=5e-4, Nt=1e4, tol=1e-10, p=4")
     kw.update(over)
     return make("periodic_M1e6_clustered_dt5e-4", **kw)
 

@@ -106,8 +106,8 @@ void block_sums(const HostPlan& hp, int64_t b, std::vector<double>& out) {
                 rs::Pair dmax = type == 0 ? rs::pair_sub(Xb, X) : rs::pair_sub(X, Xa);
                 if (rs::pair_lt(dmin, zero)) dmin = zero;
                 if (!rs::pair_lt(dmax, zero) && rs::pair_lt(dmin, dlim)) {
-                    lo = std::max(0, locate(rt, dmin) - 1);
-                    hi = std::min(rt.nint - 1, locate(rt, dmax) + 1);
+                    lo = std::max(0, rs::locate_tab(rt.bp2.data(), rt.cell.data(), rt.cell_scale, rt.nint, dmin) - 1);
+                    hi = std::min(rt.nint - 1, rs::locate_tab(rt.bp2.data(), rt.cell.data(), rt.cell_scale, rt.nint, dmax) + 1);
                 }
             }
             sE[k] = e;
@@ -135,40 +135,14 @@ void block_sums(const HostPlan& hp, int64_t b, std::vector<double>& out) {
                     const rs::Pair X = sX[k];
                     if (type == 0 ? !rs::pair_lt(X, Xj) : rs::pair_lt(X, Xj)) continue;
                     const bool near = (unsigned)(sE[k] - nbl) < (unsigned)nbc;
-                    int iv = s.tiv[type];
-                    auto setY = [&]() {
-                        const rs::Pair mid{rt.mid2[2 * iv], rt.mid2[2 * iv + 1]};
-                        s.Y[type] = rs::pair_add(Xj, type == 0 ? rs::Pair{-mid.hi, -mid.lo} : mid);
-                    };
-                    if (iv >= 0 && (near ? iv >= rt.iv_dt : iv < rt.iv_dt)) iv = near ? rt.iv_dt - 1 : rt.iv_dt;
-                    if (iv < 0) iv = locate(rt, type == 0 ? rs::pair_sub(Xj, X) : rs::pair_sub(X, Xj));
-                    iv = near ? std::min(iv, rt.iv_dt - 1) : std::max(iv, rt.iv_dt);
-                    if (iv != s.tiv[type]) setY();
+                    rs::Track tr{s.tiv[type], s.Y[type]};
                     float zh, zl;
-                    int dir = 0;
-                    for (int pass = 0;; pass++) {
-                        const float sc = rt.ih[iv];
-                        if (type == 0) rs::scaled_diff(s.Y[0], X, sc, zh, zl);
-                        else rs::scaled_diff(X, s.Y[1], sc, zh, zl);
-                        if (pass == 0 && std::fabs(zh) > 4.f) {
-                            int nv = locate(rt, type == 0 ? rs::pair_sub(Xj, X) : rs::pair_sub(X, Xj));
-                            nv = near ? std::min(nv, rt.iv_dt - 1) : std::max(nv, rt.iv_dt);
-                            if (nv != iv) {
-                                iv = nv;
-                                setY();
-                                continue;
-                            }
-                        }
-                        const int want = zh > 1.000001f ? 1 : (zh < -1.000001f ? -1 : 0);
-                        if (want == 0 || (dir != 0 && want != dir)) break;
-                        const int nv = iv + want;
-                        if (nv < 0 || nv >= rt.nint || (near ? nv >= rt.iv_dt : nv < rt.iv_dt)) break;
-                        dir = want;
-                        iv = nv;
-                        setY();
-                    }
+                    const bool in = rs::pair_z(rt.bp2.data(), rt.mid2.data(), rt.ih.data(), rt.cell.data(), rt.cell_scale,
+                                               rt.nint, rt.iv_dt, type == 0, near, Xj, X, tr, zh, zl);
+                    const int iv = tr.iv;
+                    s.Y[type] = tr.Y;
                     s.tiv[type] = iv;
-                    if (zh > 1.000001f && iv == rt.nint - 1) continue;
+                    if (!in) continue;
                     if (iv < W0 || iv > W1 || iv < sLo[k] || iv > sHi[k]) continue;
                     float rec[12];
                     const int64_t l = sE[k] < 0 ? sE[k] + M : (sE[k] >= M ? sE[k] - M : sE[k]);

