@@ -29,7 +29,7 @@ namespace wave1d {
 namespace {
 constexpr double kPiR = 3.14159265358979323846264338327950288;
 constexpr int kRsChunk = 32;      // sources per chunk (one per lane of warp 0 in the set-up)
-constexpr int kRsIvCap = 32;      // intervals whose e-vectors are held at once
+constexpr int kRsIvCap = 24;      // intervals whose e-vectors are held at once (3 blocks of 256 threads per SM)
 // one interval's row of e-vector records: 32 records of 12 floats and 4 floats of padding, so the
 // rows of consecutive intervals start 4 banks apart (threads of a warp read the records of the 2-3
 // intervals their distances fall in)
@@ -119,7 +119,7 @@ __device__ __forceinline__ double rs_q0(const RangeDev& R, double d) {
 // Near pairs (|x_e - x_j| < dt in FP64, the spring's implicit window) use the intervals below
 // dt, the others those above, so the near/far rule matches the implicit solve exactly.
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kRsTargets, 2) k_rs_local(DevPlan P, RangeDev R) {
+__global__ void __launch_bounds__(kRsTargets, 3) k_rs_local(DevPlan P, RangeDev R) {
     extern __shared__ __align__(16) float rs_sm[];
     float* sE = rs_sm;
     float2* sSig = (float2*)(sE + kRsIvCap * kRsRow);
