@@ -554,6 +554,10 @@ int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double d
         rc = WAVE1D_EINVAL;
         err = "local_weights = 1 needs a window of at least two steps (W >= 2)";
     }
+    if (rc == WAVE1D_OK && o.local_weights == 1 && p->hp.rt.nint >= 32768) {
+        rc = WAVE1D_EUNSUPPORTED;
+        err = "local_weights = 1: more than 32767 distance intervals (tolerance too small for dt)";
+    }
     if (rc == WAVE1D_OK) {
         double none = 0.0;
         rc = build_receivers(p->hp, &none, 0, err);
@@ -685,8 +689,6 @@ int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double d
         std::vector<int32_t> mr(rt.mr.begin(), rt.mr.end()), mr0(rt.mr0.begin(), rt.mr0.end());
         if ((rc = upload(p, rt.bp2, &f32))) return cleanup(rc);
         rd.bp2 = f32;
-        if ((rc = upload(p, rt.mid2, &f32))) return cleanup(rc);
-        rd.mid2 = f32;
         if ((rc = upload(p, rt.ih, &f32))) return cleanup(rc);
         rd.ih = f32;
         if ((rc = upload(p, rt.coef, &f32))) return cleanup(rc);
@@ -704,8 +706,6 @@ int wave1d_plan(const double* x, const double* beta, int64_t M, int bc, double d
         if ((rc = upload(p, rt.cell, &r32))) return cleanup(rc);
         rd.cell = r32;
         rd.cell_scale = rt.cell_scale;
-        if ((rc = upload(p, hp.x2, &f32))) return cleanup(rc);
-        rd.x2 = f32;
         if ((rc = upload(p, hp.blk_win, &r32))) return cleanup(rc);
         rd.blk_win = r32;
         if ((rc = upload(p, hp.nb_lo, &r32))) return cleanup(rc);

@@ -74,8 +74,7 @@ struct RangeTables {
     int nint = 0, nm = 0, iv_dt = 0;   // intervals, m = 0 .. nm - 1, index of the breakpoint dt
     std::vector<double> bp;            // nint + 1 breakpoints, bp[0] = 0, bp[iv_dt] = dt, bp[nint] = delta
     std::vector<float> bp2;            // the same as (hi, lo) pairs
-    std::vector<double> mid;           // per interval: midpoint (the value of its pair mid2)
-    std::vector<float> mid2;           // per interval: (hi, lo)
+    std::vector<double> mid;           // per interval: midpoint (rounded to a float pair's 48 bits)
     std::vector<float> ih;             // per interval: fl32(1 / half-width)
     std::vector<int32_t> mr;           // per interval: first and last m >= 1 with a non-zero series
     std::vector<int32_t> mr0;          // per interval: first and last m >= 0 with a non-zero series
@@ -151,7 +150,6 @@ struct HostPlan {
     // 2 pi floor(e / M)), in [0, M) in free space.
     bool range = false;
     RangeTables rt;
-    std::vector<float> x2;             // springs: (hi, lo)
     std::vector<int32_t> nb_lo, nb_cnt;// springs: window of the sources closer than dt (FP64 test
                                        //   |x_e - x_j| < dt), the implicit part of eq. linearSystem
     std::vector<int64_t> nb_off;       // M + 1: offsets of their weights
@@ -301,17 +299,15 @@ struct RangeDev {
     int nint, nm, iv_dt, nblk;
     double delta;
     const float* bp2;           // nint + 1 breakpoints (hi, lo)
-    const float* mid2;          // nint midpoints (hi, lo)
     const float* ih;            // nint scales
     const int32_t* mr;          // nint x 2: m range of the local sum (m >= 1)
     const int32_t* mr0;         // nint x 2: m range with m = 0
     const float* coef;          // [iv][m][12]: a0 .. a3 as (hi, lo) pairs, a4 .. a7
     const double* bp;           // nint + 1 breakpoints (FP64)
-    const double* mid;          // nint midpoints (FP64 value of mid2)
+    const double* mid;          // nint midpoints
     const double* cheb;         // [iv][m][8] Chebyshev coefficients in z (FP64)
     const int* cell;            // kRsCells: first interval of each cell of [0, delta)
     float cell_scale;           // kRsCells / delta
-    const float* x2;            // M positions (hi, lo)
     const int32_t* blk_win;     // [block][4] (see HostPlan::blk_win)
     const int32_t* nb_lo;       // M
     const int32_t* nb_cnt;      // M

@@ -659,15 +659,9 @@ int build_host_plan(const double* x_in, const double* beta_in, int64_t M, int bc
     }
 
     if (range) {
-        // no pair lists: positions as float pairs, index windows, the weights as polynomials
+        // no pair lists: index windows, the weights as polynomials of the distance
         hp.range = true;
         build_range_tables(P, hp.rt);
-        hp.x2.resize(2 * (size_t)M);
-        for (int64_t j = 0; j < M; j++) {
-            const float h = (float)hp.x[j];
-            hp.x2[2 * j] = h;
-            hp.x2[2 * j + 1] = (float)(hp.x[j] - (double)h);
-        }
         range_windows(hp);
     } else {
         int rc = build_local_and_blocks(P, win, hp, max_block, max_local_bytes, err);
@@ -1175,16 +1169,14 @@ void build_range_tables(const Params& P, RangeTables& rt) {
         rt.bp2[2 * i + 1] = (float)(rt.bp[i] - (double)h);
     }
     rt.mid.resize(n);
-    rt.mid2.resize(2 * (size_t)n);
     rt.ih.resize(n);
     std::vector<double> dn((size_t)n * np);
     double zk[np];
     for (int k = 0; k < np; k++) zk[k] = std::cos(kPi * (k + 0.5) / np);
     for (int iv = 0; iv < n; iv++) {
         const double a = rt.bp[iv], b = rt.bp[iv + 1], mid = 0.5 * (a + b);
+        // the reference point of the interval's polynomials (the midpoint to 48 bits)
         const float mh = (float)mid, ml = (float)(mid - (double)mh);
-        rt.mid2[2 * iv] = mh;
-        rt.mid2[2 * iv + 1] = ml;
         rt.mid[iv] = (double)mh + (double)ml;
         rt.ih[iv] = (float)(2.0 / (b - a));
         for (int k = 0; k < np; k++) dn[(size_t)iv * np + k] = rt.mid[iv] + zk[k] / (double)rt.ih[iv];

@@ -29,17 +29,17 @@ namespace wave1d {
 namespace {
 constexpr double kPiR = 3.14159265358979323846264338327950288;
 constexpr int kRsChunk = 32;      // sources per chunk (one per lane of warp 0 in the set-up)
-constexpr int kRsIvCap = 24;      // intervals whose e-vectors are held at once (3 blocks of 256 threads per SM)
+constexpr int kRsIvCap = 32;      // intervals whose e-vectors are held at once (3 blocks of 256 threads per SM)
 // one interval's row of e-vector records: 32 records of 12 floats and 4 floats of padding, so the
 // rows of consecutive intervals start 4 banks apart (threads of a warp read the records of the 2-3
 // intervals their distances fall in)
 constexpr int kRsRow = kRsChunk * rs::kERecord + 4;
 }  // namespace
 
-// shared memory of k_rs_local (bytes)
+// shared memory of k_rs_local (bytes): e-vector rows, the chunk's densities, the interval table
 size_t rs_local_smem(int nint, int nm) {
     return (size_t)kRsIvCap * kRsRow * sizeof(float) + (size_t)nm * kRsChunk * sizeof(float2) +
-           (size_t)(2 * (nint + 1) + 3 * nint) * sizeof(float) + (size_t)kRsCells * sizeof(int);
+           (size_t)4 * nint * sizeof(float);
 }
 
 // position of extended source index e: the same expression as the host's window tests
@@ -50,28 +50,6 @@ __device__ __forceinline__ double rs_xext(const DevPlan& P, int64_t e) {
 }
 
 __device__ __forceinline__ int64_t rs_spring(int64_t e, int64_t M) { return e < 0 ? e + M : (e >= M ? e - M : e); }
-
-// float-pair position of extended index e
-__device__ __forceinline__ rs::Pair rs_xpair(const RangeDev& R, int64_t e, int64_t M) {
-    const int64_t l = rs_spring(e, M);
-    rs::Pair X{R.x2[2 * l], R.x2[2 * l + 1]};
-    if (e != l) {
-        const float th = (float)(2.0 * kPiR), tl = (float)(2.0 * kPiR - (double)(float)(2.0 * kPiR));
-        X = rs::pair_add(X, e < 0 ? rs::Pair{-th, -tl} : rs::Pair{th, tl});
-    }
-    return X;
-}
-
-// interval of a normalised pair distance d: bp[iv] <= d < bp[iv + 1], clamped to [0, nint)
-__device__ __forceinline__ int rs_locate(const float* bp2, int nint, rs::Pair d) {
-    int lo = 0, hi = nint;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (rs::pair_lt(d, rs::Pair{bp2[2 * mid], bp2[2 * mid + 1]})) hi = mid;
-        else lo = mid;
-    }
-    return lo;
-}
 
 // interval of an FP64 distance
 __device__ __forceinline__ int rs_locate64(const RangeDev& R, double d) {
@@ -108,27 +86,60 @@ __device__ __forceinline__ double rs_q0(const RangeDev& R, double d) {
 // The block's sources (window [wlo, whi) of extended indices) are visited twice over as
 // "left" sources (strictly left of the target: d = x_j - x_e) and "right" sources (at or right
 // of it: d = x_e - x_j), in chunks of 32.  Per chunk:
-//   1. warp 0: each source's position and the interval range its distances to the block's
-//      targets can fall in (one interval of slack on each side);
+//   1. warp 0: each source's position on the block grid (range.cuh) and the interval range its
+//      distances to the block's targets fall in;
 //   2. the chunk's densities sigma^{n+1-m}, m = 1 .. m_max, into shared memory;
 //   3. for each interval of the chunk's range (at most kRsIvCap at a time), one warp folds the
 //      densities of all 32 sources into their e-vectors (coefficients are warp-uniform loads);
-//   4. each thread walks the 32 sources: distance interval (tracked from the previous source of
-//      the same side, which moves it by about one interval), z, and the polynomial of the
-//      source's e-vector at z into the thread's compensated accumulator.
-// Near pairs (|x_e - x_j| < dt in FP64, the spring's implicit window) use the intervals below
-// dt, the others those above, so the near/far rule matches the implicit solve exactly.
+//   4. each thread walks the 32 sources: z on the tracked interval of the side (it moves by about
+//      one interval from one source to the next), and the polynomial of the source's e-vector at z
+//      into the thread's compensated accumulator.
+// Which side counts a source is decided by index: e < lb_j (the first spring at x_j's position) is
+// strictly left.  Q_m is continuous across the breakpoints other than dt, so a pair within
+// rounding of one takes either neighbouring interval's polynomial; at dt the spring's FP64 window
+// of near sources decides (near_side in range.cuh).
 // ---------------------------------------------------------------------------------------------
+template <int S>
+__device__ __forceinline__ void rs_pairs(const float* sE, const float4* sMeta, const float* ivt, const int* cell,
+                                         float cscale, int nint, int iv_dt, int k0, int k1, int W0, int W1, int lbj,
+                                         int nbl, int nbc, float bh, float bl, rs::Track& tr, float& a0h, float& a0l,
+                                         float& a1h, float& a1l) {
+    for (int k = k0; k < k1; k += 2) {
+        // the record and z of sources k and k + 1 (null where the pair does not count in this
+        // window), then both polynomials as independent chains
+        const float* rec[2] = {nullptr, nullptr};
+        float zh[2] = {0.f, 0.f}, zl[2] = {0.f, 0.f};
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+            const int kk = k + u;
+            if (kk >= k1) break;
+            const float4 mt = sMeta[kk];
+            const int e = __float_as_int(mt.z), lohi = __float_as_int(mt.w);
+            const int lo = max(lohi & 0x7fff, W0), hi = min(lohi >> 16, W1);
+            if (lo > hi || (S < 0 ? e >= lbj : e < lbj)) continue;
+            float h0, l0;
+            rs::z_of<S>(tr, mt.x, mt.y, h0, l0);
+            if (fabsf(h0) > rs::kZTol) rs::walk<S>(ivt, cell, cscale, nint, bh, bl, mt.x, mt.y, tr, h0, l0);
+            if (lohi & 0x8000)
+                rs::near_side<S>(ivt, iv_dt, (unsigned)(e - nbl) < (unsigned)nbc, bh, bl, mt.x, mt.y, tr, h0, l0);
+            if (fabsf(h0) <= rs::kZTol && tr.iv >= lo && tr.iv <= hi) {
+                rec[u] = sE + (tr.iv - W0) * kRsRow + kk * rs::kERecord;
+                zh[u] = h0;
+                zl[u] = l0;
+            }
+        }
+        if (rec[0]) rs::evec_eval(rec[0], zh[0], zl[0], a0h, a0l);
+        if (rec[1]) rs::evec_eval(rec[1], zh[1], zl[1], a1h, a1l);
+    }
+}
+
 __global__ void __launch_bounds__(kRsTargets, 3) k_rs_local(DevPlan P, RangeDev R) {
     extern __shared__ __align__(16) float rs_sm[];
     float* sE = rs_sm;
     float2* sSig = (float2*)(sE + kRsIvCap * kRsRow);
-    float* sBp = (float*)(sSig + (size_t)R.nm * kRsChunk);
-    float* sMid = sBp + 2 * (R.nint + 1);
-    float* sIh = sMid + 2 * R.nint;
-    int* sTab = (int*)(sIh + R.nint);
-    __shared__ float sXh[kRsChunk], sXl[kRsChunk];
-    __shared__ int sEi[kRsChunk], sLo[kRsChunk], sHi[kRsChunk], sType[kRsChunk];
+    float* sIv = (float*)(sSig + (size_t)R.nm * kRsChunk);
+    // per source of the chunk: (h, l, extended index, lo | hi << 16)
+    __shared__ float4 sMeta[kRsChunk];
     __shared__ int sU0, sU1;
 
     const int64_t M = P.M;
@@ -137,59 +148,63 @@ __global__ void __launch_bounds__(kRsTargets, 3) k_rs_local(DevPlan P, RangeDev 
     const int b = blockIdx.x;
     const int64_t j0 = (int64_t)b * kRsTargets;
     const int nT = (int)min((int64_t)kRsTargets, M - j0);
-    for (int i = t; i < 2 * (R.nint + 1); i += blockDim.x) sBp[i] = __ldg(R.bp2 + i);
-    for (int i = t; i < 2 * R.nint; i += blockDim.x) sMid[i] = __ldg(R.mid2 + i);
-    for (int i = t; i < R.nint; i += blockDim.x) sIh[i] = __ldg(R.ih + i);
-    for (int i = t; i < kRsCells; i += blockDim.x) sTab[i] = __ldg(R.cell + i);
+    const double xa = P.x[j0], span = P.x[j0 + nT - 1] - xa;
+    const rs::Grid G = rs::grid_of(span, R.delta);
+    for (int iv = t; iv < R.nint; iv += blockDim.x) rs::interval_on_grid(__ldg(R.mid + iv), __ldg(R.ih + iv), G, sIv + 4 * iv);
     const float cscale = R.cell_scale;
 
     const bool valid = t < nT;
     const int64_t j = j0 + (valid ? t : 0);
-    const rs::Pair Xj{__ldg(R.x2 + 2 * j), __ldg(R.x2 + 2 * j + 1)};
+    const double xj = P.x[j];
+    float hj, lj;
+    rs::grid_split(xj - xa, G, hj, lj);
+    // lb_j: the first spring at x_j's position (sources below it are strictly left of x_j)
+    int64_t lbj = j;
+    if (j > 0 && P.x[j - 1] == xj) {
+        int64_t lo = 0;
+        while (lo < lbj) {
+            const int64_t mid = (lo + lbj) >> 1;
+            if (P.x[mid] < xj) lo = mid + 1;
+            else lbj = mid;
+        }
+    }
     const int nbl = __ldg(R.nb_lo + j), nbc = __ldg(R.nb_cnt + j);
-    const int64_t jl = j0 + nT - 1;
-    const rs::Pair Xa{__ldg(R.x2 + 2 * j0), __ldg(R.x2 + 2 * j0 + 1)};
-    const rs::Pair Xb{__ldg(R.x2 + 2 * jl), __ldg(R.x2 + 2 * jl + 1)};
     const int wlo = __ldg(R.blk_win + 4 * b), inlo = __ldg(R.blk_win + 4 * b + 1);
     const int inhi = __ldg(R.blk_win + 4 * b + 2), whi = __ldg(R.blk_win + 4 * b + 3);
     const int nL = max(0, inhi - wlo), total = nL + max(0, whi - inlo);
-    const rs::Pair zero{0.f, 0.f};
-    const rs::Pair dlim{__ldg(R.bp2 + 2 * R.nint), __ldg(R.bp2 + 2 * R.nint + 1)};     // delta
     __syncthreads();
 
     // two accumulators (even and odd sources), so consecutive pairs are independent chains
     float a0h = 0.f, a0l = 0.f, a1h = 0.f, a1l = 0.f;
-    rs::Track trL{-1, zero}, trR{-1, zero};
+    rs::Track trL, trR;
+    rs::track_to(sIv, 0, hj, lj, trL);
+    rs::track_to(sIv, 0, -hj, -lj, trR);
 
     for (int base = 0; base < total; base += kRsChunk) {
+        // the chunk's densities, sigma^{n+1-m} of source k at sSig[m][k] (pairs): every thread
+        // issues its loads while warp 0 places the sources
+        for (int i = t; i < (R.nm - 1) * kRsChunk; i += blockDim.x) {
+            const int k = i & (kRsChunk - 1), m = 1 + i / kRsChunk, v = base + k;
+            float2 s = make_float2(0.f, 0.f);
+            if (v < total) {
+                const int64_t l = rs_spring(v < nL ? wlo + v : inlo + (v - nL), M);
+                s = __ldg((const float2*)P.sig2 + (int64_t)ring_slot(n + 1 - m, P.ring) * M + l);
+            }
+            sSig[m * kRsChunk + k] = s;
+        }
         if (warp == 0) {
             const int v = base + lane;
-            int lo = 1, hi = 0, type = 0, e = 0;
-            rs::Pair X = zero;
+            int lohi = 1, e = 0;
+            float h = 0.f, l = 0.f;
             if (v < total) {
-                type = v < nL ? 0 : 1;
-                e = type == 0 ? wlo + v : inlo + (v - nL);
-                X = rs_xpair(R, e, M);
-                rs::Pair dmin, dmax;
-                if (type == 0) {
-                    dmin = rs::pair_sub(Xa, X);
-                    dmax = rs::pair_sub(Xb, X);
-                } else {
-                    dmin = rs::pair_sub(X, Xb);
-                    dmax = rs::pair_sub(X, Xa);
-                }
-                if (rs::pair_lt(dmin, zero)) dmin = zero;
-                if (!rs::pair_lt(dmax, zero) && rs::pair_lt(dmin, dlim)) {
-                    lo = max(0, rs::locate_tab(sBp, sTab, cscale, R.nint, dmin) - 1);
-                    hi = min(R.nint - 1, rs::locate_tab(sBp, sTab, cscale, R.nint, dmax) + 1);
-                }
+                const bool left = v < nL;
+                e = left ? wlo + v : inlo + (v - nL);
+                const double xr = rs_xext(P, e) - xa;
+                rs::grid_split(xr, G, h, l);
+                lohi = rs::source_range(xr, left, span, R.delta, P.dt, R.bp2, R.cell, cscale, R.nint);
             }
-            sXh[lane] = X.hi;
-            sXl[lane] = X.lo;
-            sEi[lane] = e;
-            sLo[lane] = lo;
-            sHi[lane] = hi;
-            sType[lane] = type;
+            sMeta[lane] = make_float4(h, l, __int_as_float(e), __int_as_float(lohi));
+            const int lo = lohi & 0x7fff, hi = lohi >> 16;
             int u0 = lo <= hi ? lo : 0x7fffffff, u1 = lo <= hi ? hi : -1;
             for (int o = 16; o > 0; o >>= 1) {
                 u0 = min(u0, __shfl_xor_sync(0xffffffffu, u0, o));
@@ -201,23 +216,14 @@ __global__ void __launch_bounds__(kRsTargets, 3) k_rs_local(DevPlan P, RangeDev 
             }
         }
         __syncthreads();
-        // the chunk's densities, sigma^{n+1-m} of source k at sSig[m][k] (pairs)
-        for (int i = t; i < (R.nm - 1) * kRsChunk; i += blockDim.x) {
-            const int k = i & (kRsChunk - 1), m = 1 + i / kRsChunk;
-            float2 s = make_float2(0.f, 0.f);
-            if (base + k < total) {
-                const int64_t l = rs_spring(sEi[k], M);
-                s = __ldg((const float2*)P.sig2 + (int64_t)ring_slot(n + 1 - m, P.ring) * M + l);
-            }
-            sSig[m * kRsChunk + k] = s;
-        }
-        __syncthreads();
         const int U0 = sU0, U1 = sU1;
+        const int lohi_lane = __float_as_int(sMeta[lane].w);
+        const int lo_lane = lohi_lane & 0x7fff, hi_lane = lohi_lane >> 16;
         for (int W0 = U0; W0 <= U1; W0 += kRsIvCap) {
             const int W1 = min(U1, W0 + kRsIvCap - 1);
             // e-vectors of the intervals [W0, W1]: warp per interval, lane per source
             for (int iv = W0 + warp; iv <= W1; iv += nwarps) {
-                const bool act = base + lane < total && sLo[lane] <= iv && iv <= sHi[lane];
+                const bool act = lo_lane <= iv && iv <= hi_lane;
                 if (!__any_sync(0xffffffffu, act)) continue;
                 rs::EVec ev;
                 rs::evec_zero(ev);
@@ -236,34 +242,12 @@ __global__ void __launch_bounds__(kRsTargets, 3) k_rs_local(DevPlan P, RangeDev 
                 rec[2] = make_float4(ev.e6, ev.e7, 0.f, 0.f);
             }
             __syncthreads();
-            if (W0 > U0) trL.iv = trR.iv = -1;          // a second pass over the chunk: search afresh
             if (valid) {
-                const int kend = min(kRsChunk, total - base);
-                for (int k = 0; k < kend; k += 2) {
-                    // the record and z of sources k and k + 1 (null where the pair does not count
-                    // in this window), then both polynomials as independent chains
-                    const float* rec[2] = {nullptr, nullptr};
-                    float zh[2] = {0.f, 0.f}, zl[2] = {0.f, 0.f};
-#pragma unroll
-                    for (int u = 0; u < 2; u++) {
-                        const int kk = k + u;
-                        if (kk >= kend) break;
-                        const int lo = sLo[kk], hi = sHi[kk];
-                        if (lo > hi) continue;
-                        const bool left = sType[kk] == 0;
-                        const rs::Pair X{sXh[kk], sXl[kk]};
-                        // left sources strictly left of x_j, right sources at or right of it
-                        if (left ? !rs::pair_lt(X, Xj) : rs::pair_lt(X, Xj)) continue;
-                        const bool near = (unsigned)(sEi[kk] - nbl) < (unsigned)nbc;
-                        const bool in = left ? rs::pair_z(sBp, sMid, sIh, sTab, cscale, R.nint, R.iv_dt, true, near, Xj, X, trL, zh[u], zl[u])
-                                             : rs::pair_z(sBp, sMid, sIh, sTab, cscale, R.nint, R.iv_dt, false, near, Xj, X, trR, zh[u], zl[u]);
-                        const int iv = left ? trL.iv : trR.iv;
-                        if (in && iv >= W0 && iv <= W1 && iv >= lo && iv <= hi)
-                            rec[u] = sE + (iv - W0) * kRsRow + kk * rs::kERecord;
-                    }
-                    if (rec[0]) rs::evec_eval(rec[0], zh[0], zl[0], a0h, a0l);
-                    if (rec[1]) rs::evec_eval(rec[1], zh[1], zl[1], a1h, a1l);
-                }
+                const int kend = min(kRsChunk, total - base), kL = min(kend, max(0, nL - base));
+                rs_pairs<-1>(sE, sMeta, sIv, R.cell, cscale, R.nint, R.iv_dt, 0, kL, W0, W1, (int)lbj, nbl, nbc, hj, lj, trL,
+                             a0h, a0l, a1h, a1l);
+                rs_pairs<1>(sE, sMeta, sIv, R.cell, cscale, R.nint, R.iv_dt, kL, kend, W0, W1, (int)lbj, nbl, nbc, -hj, -lj,
+                            trR, a0h, a0l, a1h, a1l);
             }
             __syncthreads();
         }

@@ -15,8 +15,9 @@
 // Precision.  Values are compensated FP32 pairs hi + lo (error-free two-sum and FMA residuals,
 // about 48 significant bits); GB300 issues FP32 61 times faster than FP64.  The terms that carry
 // the magnitude (r = 0, 1: the interval mean and slope) are pairs throughout; the curvature terms
-// r >= 2 (below 2 % of max |Q|) are single floats.  Positions are pairs (x = hi + lo exactly to
-// about 1e-14), so pair distances and z keep about 1e-14 absolute.
+// r >= 2 (below 2 % of max |Q|) are single floats.  Positions are split on a grid of the target
+// block (below), so that d - mid_iv is one exact FP32 difference plus a small rounded part, and z
+// carries about 3e-11 absolute error.
 //
 // Every operation is written with round-to-nearest intrinsics on the device, and plainly on the
 // host (host checks compile with -ffp-contract=off), so both give the same bits.
@@ -74,34 +75,6 @@ WAVE1D_RS_HD void two_sum(float a, float b, float& s, float& e) {
     s = add(a, b);
     const float bb = sub(s, a);
     e = add(sub(a, sub(s, bb)), sub(b, bb));
-}
-
-// (h, l) + (bh, bl) into a normalised pair
-WAVE1D_RS_HD Pair pair_add(Pair a, Pair b) {
-    float s, e;
-    two_sum(a.hi, b.hi, s, e);
-    e = add(e, add(a.lo, b.lo));
-    float h, l;
-    two_sum(s, e, h, l);
-    return {h, l};
-}
-
-WAVE1D_RS_HD Pair pair_sub(Pair a, Pair b) { return pair_add(a, Pair{-b.hi, -b.lo}); }
-
-// a < b for normalised pairs
-WAVE1D_RS_HD bool pair_lt(Pair a, Pair b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
-
-// z = (a - b) s as a pair (zh, zl) with |zl| within a couple of ulp of zh: the difference through
-// two-sum and renormalised (the high parts of nearby positions cancel, so the difference's low
-// part can be as large as its high part), the product through its FMA residual (a, b normalised
-// pairs, s a float scale)
-WAVE1D_RS_HD void scaled_diff(Pair a, Pair b, float s, float& zh, float& zl) {
-    float d, e;
-    two_sum(a.hi, -b.hi, d, e);
-    float th, tl;
-    two_sum(d, add(e, sub(a.lo, b.lo)), th, tl);
-    zh = mul(th, s);
-    zl = fma_(tl, s, fma_(th, s, -zh));
 }
 
 // acc += (vh + vl), acc kept as an unnormalised pair (hi carries the sum, lo the residuals)
@@ -162,7 +135,7 @@ WAVE1D_RS_HD void evec_mac(EVec& v, const float* c01, const float* c23, const fl
 constexpr int kERecord = 12;
 
 // acc += e0 + z (e1 + z P(z)),  P(z) = e2 + z (e3 + z (e4 + z (e5 + z (e6 + z e7)))),
-// z = zh + zl; e is a packed record
+// z = zh + zl normalised; e is a packed record
 WAVE1D_RS_HD void evec_eval(const float* e, float zh, float zl, float& ah, float& al) {
     float P = fma_(e[9], zh, e[8]);                 // e7 z + e6
     P = fma_(P, zh, e[7]);                          // + e5
@@ -185,65 +158,139 @@ WAVE1D_RS_HD void evec_eval(const float* e, float zh, float zl, float& ah, float
 }
 
 // ---------------------------------------------------------------------------------------------
-// Interval of a distance.  bp2: nint + 1 breakpoints as (hi, lo) pairs; tab: kRsCells entries, the
-// interval of the left end of each cell of [0, delta), cell of d = floor(d cscale).
+// Distances on the grid of a target block.  The targets x_a .. x_b of a block and their sources
+// lie within span + delta of x_a (span = x_b - x_a), so positions relative to x_a are split as
+// x - x_a = h + l, h a multiple of the grid step g = 2^(k - 24) with 2^k > 4 (span + delta) and
+// l = fl(x - x_a - h), |l| <= g / 2; interval midpoints the same way.  Sums and differences of two
+// such h stay below 2^24 g, so they are exact in FP32: for a source (h, l) and the tracked
+// interval's Y = b - mid (b = target for left sources, minus the target for right ones)
+//   z = (d - mid) ih = (Y_h -/+ h) ih + (Y_l -/+ l) ih,
+// the first product exact through its FMA residual, the second rounded (|Y_l -/+ l| <= 1.5 g).
 // ---------------------------------------------------------------------------------------------
-WAVE1D_RS_HD int locate_tab(const float* bp2, const int* tab, float cscale, int nint, Pair d) {
-    int c = (int)mul(d.hi, cscale);
+struct Grid {
+    double g, ig;
+};
+
+WAVE1D_RS_HD Grid grid_of(double span, double delta) {
+    int k;
+    (void)frexp(4.0 * (span + delta), &k);          // 4 (span + delta) < 2^k
+    return {ldexp(1.0, k - 24), ldexp(1.0, 24 - k)};
+}
+
+// v = h + l on the grid (|v| < 2^k: h is an integer multiple of g below 2^24 g, exact in FP32)
+WAVE1D_RS_HD void grid_split(double v, Grid G, float& h, float& l) {
+    const double hd = rint(v * G.ig) * G.g;
+    h = (float)hd;
+    l = (float)(v - hd);
+}
+
+// an interval on the block grid: (mid_h, mid_l, ih, 0)
+WAVE1D_RS_HD void interval_on_grid(double mid, float ih, Grid G, float* out4) {
+    grid_split(mid, G, out4[0], out4[1]);
+    out4[2] = ih;
+    out4[3] = 0.f;
+}
+
+// |z| above which a distance lies outside the tracked interval (z carries about 3e-11; the slack
+// lets the walk end where rounding puts a distance on a breakpoint)
+constexpr float kZTol = 1.000001f;
+// margin of the interval ranges of a source, relative to delta: it covers the FP32 rounding of the
+// ranges' end distances and the walk's slack, so every pair's interval lies inside its source's range
+constexpr double kRangeMargin = 4e-7;
+
+// Tracked interval of one side (left or right sources) for one target: iv, Y = b - mid_iv, ih_iv.
+struct Track {
+    int iv;
+    float Yh, Yl, ih;
+};
+
+// ivt: the block's interval table, 4 floats per interval (interval_on_grid)
+WAVE1D_RS_HD void track_to(const float* ivt, int iv, float bh, float bl, Track& t) {
+    t.iv = iv;
+    t.Yh = sub(bh, ivt[4 * iv]);
+    t.Yl = sub(bl, ivt[4 * iv + 1]);
+    t.ih = ivt[4 * iv + 2];
+}
+
+// z = zh + zl (normalised) of the source (h, l) on side S (-1: left sources, d = x_j - x; +1:
+// right sources, d = x - x_j) against the tracked interval.  The rounded part (Y_l -/+ l) ih
+// reaches about 1e-3, so the two parts are renormalised: the curvature terms of the polynomial
+// take zh alone.
+template <int S>
+WAVE1D_RS_HD void z_of(const Track& t, float h, float l, float& zh, float& zl) {
+    const float A = S < 0 ? sub(t.Yh, h) : add(t.Yh, h);    // exact
+    const float B = S < 0 ? sub(t.Yl, l) : add(t.Yl, l);
+    const float p = mul(A, t.ih);
+    two_sum(p, fma_(B, t.ih, fma_(A, t.ih, -p)), zh, zl);
+}
+
+// Move the tracked interval to the source's distance: searched afresh through the cell table when
+// far off (|z| > 4), then walked in one direction only until |zh| <= kZTol (one direction, so the
+// walk ends even where rounding leaves z just outside two neighbouring intervals) or the end of
+// [0, delta) is reached (the caller then finds |zh| > kZTol: the pair lies beyond delta).
+// cell: kRsCells entries, the interval of the left end of each cell of [0, delta), cell of d =
+// floor(d cscale).
+template <int S>
+WAVE1D_RS_HD void walk(const float* ivt, const int* cell, float cscale, int nint, float bh, float bl, float h, float l,
+                       Track& t, float& zh, float& zl) {
+    if ((zh > 4.f || zh < -4.f) && !(zh > 0.f && t.iv == nint - 1)) {
+        const float dh = S < 0 ? sub(bh, h) : add(bh, h);
+        const float d = add(dh, S < 0 ? sub(bl, l) : add(bl, l));
+        int c = (int)mul(d, cscale);
+        c = c < 0 ? 0 : (c >= kRsCells ? kRsCells - 1 : c);
+        track_to(ivt, cell[c], bh, bl, t);
+        z_of<S>(t, h, l, zh, zl);
+    }
+    int dir = 0;
+    while (zh > kZTol || zh < -kZTol) {
+        const int want = zh > 0.f ? 1 : -1;
+        if (dir != 0 && want != dir) break;
+        const int nv = t.iv + want;
+        if (nv < 0 || nv >= nint) break;
+        dir = want;
+        track_to(ivt, nv, bh, bl, t);
+        z_of<S>(t, h, l, zh, zl);
+    }
+}
+
+// interval of a float distance: the cell table, then the breakpoints' high parts (bp2 pairs)
+WAVE1D_RS_HD int locate_f(const float* bp2, const int* cell, float cscale, int nint, float d) {
+    int c = (int)mul(d, cscale);
     c = c < 0 ? 0 : (c >= kRsCells ? kRsCells - 1 : c);
-    int iv = tab[c];
-    while (iv > 0 && pair_lt(d, Pair{bp2[2 * iv], bp2[2 * iv + 1]})) iv--;
-    while (iv + 1 < nint && !pair_lt(d, Pair{bp2[2 * iv + 2], bp2[2 * iv + 3]})) iv++;
+    int iv = cell[c];
+    while (iv > 0 && d < bp2[2 * iv]) iv--;
+    while (iv + 1 < nint && !(d < bp2[2 * iv + 2])) iv++;
     return iv;
 }
 
-// Tracked interval of one side (left or right sources) for one target: the interval iv of the last
-// source's distance and Y = x_j -/+ mid_iv, so z = (Y - x_e) ih (left) or (x_e - Y) ih (right).
-struct Track {
-    int iv;
-    Pair Y;
-};
+// Interval range [lo, hi] of a source's distances to the block's targets (xr = x_e - x_a; left:
+// d = x_j - x_e, right: d = x_e - x_j, x_j in [x_a, x_a + span]), lo > hi where none is below
+// delta, and whether some distance may lie within rounding of dt (near = 1).  Packed as
+// lo | near << 15 | hi << 16 (intervals below 2^15).
+WAVE1D_RS_HD int source_range(double xr, bool left, double span, double delta, double dt, const float* bp2,
+                              const int* cell, float cscale, int nint) {
+    const double marg = kRangeMargin * delta;
+    const double dmin = left ? -xr : xr - span, dmax = left ? span - xr : xr;
+    if (dmax < 0.0 || !(dmin - marg < delta)) return 1;
+    const double d0 = dmin - marg;
+    const int lo = locate_f(bp2, cell, cscale, nint, (float)(d0 > 0.0 ? d0 : 0.0));
+    const int hi = locate_f(bp2, cell, cscale, nint, (float)(dmax + marg));
+    const int near = dmin - marg < dt && dt < dmax + marg ? 1 : 0;
+    return lo | near << 15 | hi << 16;
+}
 
-// Interval and z of the pair (target Xj, source X) on side `left`: from the tracked interval, moved
-// to the pair's side of dt (near pairs below it, far pairs at or above it), then walked in one
-// direction only until z lies in [-1, 1] (to rounding; one direction, so the walk ends even where
-// rounding leaves z just outside two neighbouring intervals), or searched afresh when far off.
-// mid2 / ih: the intervals' midpoints (pairs) and scales.  Returns false where the pair lies beyond
-// delta.
-WAVE1D_RS_HD bool pair_z(const float* bp2, const float* mid2, const float* ih, const int* tab, float cscale,
-                         int nint, int iv_dt, bool left, bool near, Pair Xj, Pair X, Track& tr, float& zh,
-                         float& zl) {
-    int iv = tr.iv;
-    if (iv >= 0 && (near ? iv >= iv_dt : iv < iv_dt)) iv = near ? iv_dt - 1 : iv_dt;
-    if (iv < 0) iv = locate_tab(bp2, tab, cscale, nint, left ? pair_sub(Xj, X) : pair_sub(X, Xj));
-    iv = near ? (iv < iv_dt - 1 ? iv : iv_dt - 1) : (iv > iv_dt ? iv : iv_dt);
-    if (iv != tr.iv) {
-        const Pair mid{mid2[2 * iv], mid2[2 * iv + 1]};
-        tr.Y = pair_add(Xj, left ? Pair{-mid.hi, -mid.lo} : mid);
+// The rule of the implicit part: a pair is near when |x_e - x_j| < dt in FP64 (the spring's window
+// of sources), and Q_m, m >= 1, of near pairs comes from the intervals below dt, of the others from
+// those at or above it (the interpolation stencils of the two cases differ, so Q_m jumps at
+// d = dt).  Where the walk ended on the other side of dt (the distance within rounding of dt), the
+// pair moves to the interval next to dt on its side.
+template <int S>
+WAVE1D_RS_HD void near_side(const float* ivt, int iv_dt, bool near, float bh, float bl, float h, float l, Track& t,
+                            float& zh, float& zl) {
+    if (near != (t.iv < iv_dt)) {
+        track_to(ivt, near ? iv_dt - 1 : iv_dt, bh, bl, t);
+        z_of<S>(t, h, l, zh, zl);
     }
-    int dir = 0;
-    for (int pass = 0;; pass++) {
-        const float sc = ih[iv];
-        if (left) scaled_diff(tr.Y, X, sc, zh, zl);
-        else scaled_diff(X, tr.Y, sc, zh, zl);
-        int nv = iv;
-        if (pass == 0 && (zh > 4.f || zh < -4.f)) {
-            nv = locate_tab(bp2, tab, cscale, nint, left ? pair_sub(Xj, X) : pair_sub(X, Xj));
-            nv = near ? (nv < iv_dt - 1 ? nv : iv_dt - 1) : (nv > iv_dt ? nv : iv_dt);
-        } else {
-            const int want = zh > 1.000001f ? 1 : (zh < -1.000001f ? -1 : 0);
-            if (want == 0 || (dir != 0 && want != dir)) break;
-            nv = iv + want;
-            if (nv < 0 || nv >= nint || (near ? nv >= iv_dt : nv < iv_dt)) break;
-            dir = want;
-        }
-        if (nv == iv) break;
-        iv = nv;
-        const Pair mid{mid2[2 * iv], mid2[2 * iv + 1]};
-        tr.Y = pair_add(Xj, left ? Pair{-mid.hi, -mid.lo} : mid);
-    }
-    tr.iv = iv;
-    return !(zh > 1.000001f && iv == nint - 1);
 }
 
 }  // namespace rs

@@ -40,26 +40,6 @@ double xext(const HostPlan& hp, int64_t e) {
     return hp.x[e];
 }
 
-rs::Pair xpair(const HostPlan& hp, int64_t e) {
-    const int64_t M = hp.P.M, l = e < 0 ? e + M : (e >= M ? e - M : e);
-    rs::Pair X{hp.x2[2 * l], hp.x2[2 * l + 1]};
-    if (e != l) {
-        const float th = (float)(2.0 * kPi), tl = (float)(2.0 * kPi - (double)(float)(2.0 * kPi));
-        X = rs::pair_add(X, e < 0 ? rs::Pair{-th, -tl} : rs::Pair{th, tl});
-    }
-    return X;
-}
-
-int locate(const RangeTables& rt, rs::Pair d) {
-    int lo = 0, hi = rt.nint;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (rs::pair_lt(d, rs::Pair{rt.bp2[2 * mid], rt.bp2[2 * mid + 1]})) hi = mid;
-        else lo = mid;
-    }
-    return lo;
-}
-
 void evec_of(const RangeTables& rt, int iv, int64_t l, float* rec) {
     rs::EVec ev;
     rs::evec_zero(ev);
@@ -72,6 +52,35 @@ void evec_of(const RangeTables& rt, int iv, int64_t l, float* rec) {
     std::memcpy(rec, r, sizeof(r));
 }
 
+// the pairs of one side for one target, sources [k0, k1) of the chunk (rs_pairs of the kernel)
+template <int S>
+void side_pairs(const HostPlan& hp, const std::vector<float>& ivt, const float* meta, int k0, int k1, int W0, int W1,
+                int64_t lbj, int nbl, int nbc, float bh, float bl, rs::Track& tr, float acc[4]) {
+    const RangeTables& rt = hp.rt;
+    const int64_t M = hp.P.M;
+    for (int k = k0; k < k1; k++) {
+        const float* mt = meta + 4 * k;
+        int e, lohi;
+        std::memcpy(&e, mt + 2, 4);
+        std::memcpy(&lohi, mt + 3, 4);
+        const int lo = std::max(lohi & 0x7fff, W0), hi = std::min(lohi >> 16, W1);
+        if (lo > hi || (S < 0 ? e >= lbj : e < lbj)) continue;
+        float zh, zl;
+        rs::z_of<S>(tr, mt[0], mt[1], zh, zl);
+        if (std::fabs(zh) > rs::kZTol)
+            rs::walk<S>(ivt.data(), rt.cell.data(), rt.cell_scale, rt.nint, bh, bl, mt[0], mt[1], tr, zh, zl);
+        if (lohi & 0x8000)
+            rs::near_side<S>(ivt.data(), rt.iv_dt, (unsigned)(e - nbl) < (unsigned)nbc, bh, bl, mt[0], mt[1], tr, zh,
+                             zl);
+        if (!(std::fabs(zh) <= rs::kZTol && tr.iv >= lo && tr.iv <= hi)) continue;
+        float rec[12];
+        const int64_t l = e < 0 ? e + M : (e >= M ? e - M : e);
+        evec_of(rt, tr.iv, l, rec);
+        float* a = acc + 2 * (k & 1);
+        rs::evec_eval(rec, zh, zl, a[0], a[1]);
+    }
+}
+
 // the kernel's traversal for one block, every target of it
 void block_sums(const HostPlan& hp, int64_t b, std::vector<double>& out) {
     const RangeTables& rt = hp.rt;
@@ -80,80 +89,66 @@ void block_sums(const HostPlan& hp, int64_t b, std::vector<double>& out) {
     const int wlo = hp.blk_win[4 * b], inlo = hp.blk_win[4 * b + 1], inhi = hp.blk_win[4 * b + 2],
               whi = hp.blk_win[4 * b + 3];
     const int nL = std::max(0, inhi - wlo), total = nL + std::max(0, whi - inlo);
-    const rs::Pair Xa{hp.x2[2 * j0], hp.x2[2 * j0 + 1]};
-    const rs::Pair Xb{hp.x2[2 * (j0 + nT - 1)], hp.x2[2 * (j0 + nT - 1) + 1]};
-    const rs::Pair zero{0.f, 0.f}, dlim{rt.bp2[2 * rt.nint], rt.bp2[2 * rt.nint + 1]};
+    const double xa = hp.x[j0], span = hp.x[j0 + nT - 1] - xa;
+    const rs::Grid G = rs::grid_of(span, hp.P.delta);
+    std::vector<float> ivt(4 * (size_t)rt.nint);
+    for (int iv = 0; iv < rt.nint; iv++) rs::interval_on_grid(rt.mid[iv], rt.ih[iv], G, &ivt[4 * (size_t)iv]);
     struct T {
-        float ah = 0.f, al = 0.f;
-        int tiv[2] = {-1, -1};
-        rs::Pair Y[2] = {{0.f, 0.f}, {0.f, 0.f}};
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        float hj = 0.f, lj = 0.f;
+        int64_t lbj = 0;
+        rs::Track trL{}, trR{};
     };
     std::vector<T> st(nT);
+    for (int t = 0; t < nT; t++) {
+        const int64_t j = j0 + t;
+        rs::grid_split(hp.x[j] - xa, G, st[t].hj, st[t].lj);
+        int64_t lbj = j;
+        while (lbj > 0 && hp.x[lbj - 1] == hp.x[j]) lbj--;
+        st[t].lbj = lbj;
+        rs::track_to(ivt.data(), 0, st[t].hj, st[t].lj, st[t].trL);
+        rs::track_to(ivt.data(), 0, -st[t].hj, -st[t].lj, st[t].trR);
+    }
     const int C = 32, CAP = 32;
     for (int base = 0; base < total; base += C) {
-        int sE[32], sLo[32], sHi[32], sType[32];
-        rs::Pair sX[32];
+        float meta[4 * 32];
         int U0 = INT_MAX, U1 = -1;
         for (int k = 0; k < C; k++) {
             const int v = base + k;
-            int lo = 1, hi = 0, type = 0, e = 0;
-            rs::Pair X = zero;
+            int lohi = 1, e = 0;
+            float h = 0.f, l = 0.f;
             if (v < total) {
-                type = v < nL ? 0 : 1;
-                e = type == 0 ? wlo + v : inlo + (v - nL);
-                X = xpair(hp, e);
-                rs::Pair dmin = type == 0 ? rs::pair_sub(Xa, X) : rs::pair_sub(X, Xb);
-                rs::Pair dmax = type == 0 ? rs::pair_sub(Xb, X) : rs::pair_sub(X, Xa);
-                if (rs::pair_lt(dmin, zero)) dmin = zero;
-                if (!rs::pair_lt(dmax, zero) && rs::pair_lt(dmin, dlim)) {
-                    lo = std::max(0, rs::locate_tab(rt.bp2.data(), rt.cell.data(), rt.cell_scale, rt.nint, dmin) - 1);
-                    hi = std::min(rt.nint - 1, rs::locate_tab(rt.bp2.data(), rt.cell.data(), rt.cell_scale, rt.nint, dmax) + 1);
-                }
+                const bool left = v < nL;
+                e = left ? wlo + v : inlo + (v - nL);
+                const double xr = xext(hp, e) - xa;
+                rs::grid_split(xr, G, h, l);
+                lohi = rs::source_range(xr, left, span, hp.P.delta, hp.P.dt, rt.bp2.data(), rt.cell.data(),
+                                        rt.cell_scale, rt.nint);
             }
-            sE[k] = e;
-            sLo[k] = lo;
-            sHi[k] = hi;
-            sType[k] = type;
-            sX[k] = X;
+            const int lo = lohi & 0x7fff, hi = lohi >> 16;
+            meta[4 * k] = h;
+            meta[4 * k + 1] = l;
+            std::memcpy(&meta[4 * k + 2], &e, 4);
+            std::memcpy(&meta[4 * k + 3], &lohi, 4);
             if (lo <= hi) {
                 U0 = std::min(U0, lo);
                 U1 = std::max(U1, hi);
             }
         }
+        const int kend = std::min(C, total - base), kL = std::min(kend, std::max(0, nL - base));
         for (int W0 = U0; W0 <= U1; W0 += CAP) {
             const int W1 = std::min(U1, W0 + CAP - 1);
             for (int t = 0; t < nT; t++) {
                 T& s = st[t];
-                if (W0 > U0) s.tiv[0] = s.tiv[1] = -1;
                 const int64_t j = j0 + t;
-                const rs::Pair Xj{hp.x2[2 * j], hp.x2[2 * j + 1]};
-                const int nbl = hp.nb_lo[j], nbc = hp.nb_cnt[j];
-                const int kend = std::min(C, total - base);
-                for (int k = 0; k < kend; k++) {
-                    if (sLo[k] > sHi[k]) continue;
-                    const int type = sType[k];
-                    const rs::Pair X = sX[k];
-                    if (type == 0 ? !rs::pair_lt(X, Xj) : rs::pair_lt(X, Xj)) continue;
-                    const bool near = (unsigned)(sE[k] - nbl) < (unsigned)nbc;
-                    rs::Track tr{s.tiv[type], s.Y[type]};
-                    float zh, zl;
-                    const bool in = rs::pair_z(rt.bp2.data(), rt.mid2.data(), rt.ih.data(), rt.cell.data(), rt.cell_scale,
-                                               rt.nint, rt.iv_dt, type == 0, near, Xj, X, tr, zh, zl);
-                    const int iv = tr.iv;
-                    s.Y[type] = tr.Y;
-                    s.tiv[type] = iv;
-                    if (!in) continue;
-                    if (iv < W0 || iv > W1 || iv < sLo[k] || iv > sHi[k]) continue;
-                    float rec[12];
-                    const int64_t l = sE[k] < 0 ? sE[k] + M : (sE[k] >= M ? sE[k] - M : sE[k]);
-                    evec_of(rt, iv, l, rec);
-                    if (getenv("RS_DEBUG")) fprintf(stderr, "j=%ld e=%d type=%d near=%d iv=%d [%g,%g) z=%g+%g rec0=%g\n", (long)j, sE[k], type, (int)near, iv, rt.bp[iv], rt.bp[iv+1], zh, zl, rec[0]);
-                    rs::evec_eval(rec, zh, zl, s.ah, s.al);
-                }
+                side_pairs<-1>(hp, ivt, meta, 0, kL, W0, W1, s.lbj, hp.nb_lo[j], hp.nb_cnt[j], s.hj, s.lj, s.trL, s.acc);
+                side_pairs<1>(hp, ivt, meta, kL, kend, W0, W1, s.lbj, hp.nb_lo[j], hp.nb_cnt[j], -s.hj, -s.lj, s.trR,
+                              s.acc);
             }
         }
     }
-    for (int t = 0; t < nT; t++) out[j0 + t] = (double)st[t].ah + (double)st[t].al;
+    for (int t = 0; t < nT; t++)
+        out[j0 + t] = ((double)st[t].acc[0] + (double)st[t].acc[1]) + ((double)st[t].acc[2] + (double)st[t].acc[3]);
 }
 
 }  // namespace
