@@ -86,8 +86,8 @@ __device__ __forceinline__ double rs_q0(const RangeDev& R, double d) {
 // The block's sources (window [wlo, whi) of extended indices) are visited twice over as
 // "left" sources (strictly left of the target: d = x_j - x_e) and "right" sources (at or right
 // of it: d = x_e - x_j), in chunks of 32.  Per chunk:
-//   1. warp 0: each source's position on the block grid (range.cuh) and the interval range its
-//      distances to the block's targets fall in;
+//   1. once per 8 chunks, one thread per source: its position on the block grid (range.cuh) and
+//      the interval range its distances to the block's targets fall in;
 //   2. the chunk's densities sigma^{n+1-m}, m = 1 .. m_max, into shared memory;
 //   3. for each interval of the chunk's range (at most kRsIvCap at a time), one warp folds the
 //      densities of all 32 sources into their e-vectors (coefficients are warp-uniform loads);
@@ -138,9 +138,10 @@ __global__ void __launch_bounds__(kRsTargets, 3) k_rs_local(DevPlan P, RangeDev 
     float* sE = rs_sm;
     float2* sSig = (float2*)(sE + kRsIvCap * kRsRow);
     float* sIv = (float*)(sSig + (size_t)R.nm * kRsChunk);
-    // per source of the chunk: (h, l, extended index, lo | hi << 16)
-    __shared__ float4 sMeta[kRsChunk];
-    __shared__ int sU0, sU1;
+    // per source of a group of kRsTargets sources (8 chunks): (h, l, extended index, packed
+    // interval range), and the interval union of each chunk
+    __shared__ float4 sMeta[kRsTargets];
+    __shared__ int sU[2][kRsTargets / kRsChunk];
 
     const int64_t M = P.M;
     const int64_t n = load_step(P);
@@ -181,19 +182,12 @@ __global__ void __launch_bounds__(kRsTargets, 3) k_rs_local(DevPlan P, RangeDev 
     rs::track_to(sIv, 0, -hj, -lj, trR);
 
     for (int base = 0; base < total; base += kRsChunk) {
-        // the chunk's densities, sigma^{n+1-m} of source k at sSig[m][k] (pairs): every thread
-        // issues its loads while warp 0 places the sources
-        for (int i = t; i < (R.nm - 1) * kRsChunk; i += blockDim.x) {
-            const int k = i & (kRsChunk - 1), m = 1 + i / kRsChunk, v = base + k;
-            float2 s = make_float2(0.f, 0.f);
-            if (v < total) {
-                const int64_t l = rs_spring(v < nL ? wlo + v : inlo + (v - nL), M);
-                s = __ldg((const float2*)P.sig2 + (int64_t)ring_slot(n + 1 - m, P.ring) * M + l);
-            }
-            sSig[m * kRsChunk + k] = s;
-        }
-        if (warp == 0) {
-            const int v = base + lane;
+        const int grp = base & (kRsTargets - 1);       // the chunk's place in its group of 8
+        if (grp == 0) {
+            // set-up of the group's 256 sources, one per thread: position on the block grid and
+            // interval range; warp w reduces the union of chunk w
+            if (base > 0) __syncthreads();             // the previous group's last chunk is done
+            const int v = base + t;
             int lohi = 1, e = 0;
             float h = 0.f, l = 0.f;
             if (v < total) {
@@ -203,7 +197,7 @@ __global__ void __launch_bounds__(kRsTargets, 3) k_rs_local(DevPlan P, RangeDev 
                 rs::grid_split(xr, G, h, l);
                 lohi = rs::source_range(xr, left, span, R.delta, P.dt, R.bp2, R.cell, cscale, R.nint);
             }
-            sMeta[lane] = make_float4(h, l, __int_as_float(e), __int_as_float(lohi));
+            sMeta[t] = make_float4(h, l, __int_as_float(e), __int_as_float(lohi));
             const int lo = lohi & 0x7fff, hi = lohi >> 16;
             int u0 = lo <= hi ? lo : 0x7fffffff, u1 = lo <= hi ? hi : -1;
             for (int o = 16; o > 0; o >>= 1) {
@@ -211,13 +205,24 @@ __global__ void __launch_bounds__(kRsTargets, 3) k_rs_local(DevPlan P, RangeDev 
                 u1 = max(u1, __shfl_xor_sync(0xffffffffu, u1, o));
             }
             if (lane == 0) {
-                sU0 = u0;
-                sU1 = u1;
+                sU[0][warp] = u0;
+                sU[1][warp] = u1;
             }
         }
+        // the chunk's densities, sigma^{n+1-m} of source k at sSig[m][k] (pairs)
+        for (int i = t; i < (R.nm - 1) * kRsChunk; i += blockDim.x) {
+            const int k = i & (kRsChunk - 1), m = 1 + i / kRsChunk, v = base + k;
+            float2 s = make_float2(0.f, 0.f);
+            if (v < total) {
+                const int64_t l = rs_spring(v < nL ? wlo + v : inlo + (v - nL), M);
+                s = __ldg((const float2*)P.sig2 + (int64_t)ring_slot(n + 1 - m, P.ring) * M + l);
+            }
+            sSig[m * kRsChunk + k] = s;
+        }
         __syncthreads();
-        const int U0 = sU0, U1 = sU1;
-        const int lohi_lane = __float_as_int(sMeta[lane].w);
+        const float4* meta = sMeta + grp;
+        const int U0 = sU[0][grp / kRsChunk], U1 = sU[1][grp / kRsChunk];
+        const int lohi_lane = __float_as_int(meta[lane].w);
         const int lo_lane = lohi_lane & 0x7fff, hi_lane = lohi_lane >> 16;
         for (int W0 = U0; W0 <= U1; W0 += kRsIvCap) {
             const int W1 = min(U1, W0 + kRsIvCap - 1);
@@ -229,7 +234,20 @@ __global__ void __launch_bounds__(kRsTargets, 3) k_rs_local(DevPlan P, RangeDev 
                 rs::evec_zero(ev);
                 const int m0 = __ldg(R.mr + 2 * iv), m1 = __ldg(R.mr + 2 * iv + 1);
                 const float4* c = (const float4*)R.coef + (size_t)iv * R.nm * 3;
-                for (int m = m0; m <= m1; m++) {
+                // two m per iteration: six coefficient loads in flight (they come from L2)
+                int m = m0;
+                for (; m < m1; m += 2) {
+                    const float4 c01 = __ldg(c + 3 * m), c23 = __ldg(c + 3 * m + 1), c47 = __ldg(c + 3 * m + 2);
+                    const float4 d01 = __ldg(c + 3 * m + 3), d23 = __ldg(c + 3 * m + 4), d47 = __ldg(c + 3 * m + 5);
+                    const float2 s = sSig[m * kRsChunk + lane], s2 = sSig[(m + 1) * kRsChunk + lane];
+                    const float a01[4] = {c01.x, c01.y, c01.z, c01.w}, a23[4] = {c23.x, c23.y, c23.z, c23.w},
+                                a47[4] = {c47.x, c47.y, c47.z, c47.w};
+                    rs::evec_mac(ev, a01, a23, a47, s.x, s.y);
+                    const float b01[4] = {d01.x, d01.y, d01.z, d01.w}, b23[4] = {d23.x, d23.y, d23.z, d23.w},
+                                b47[4] = {d47.x, d47.y, d47.z, d47.w};
+                    rs::evec_mac(ev, b01, b23, b47, s2.x, s2.y);
+                }
+                if (m == m1) {
                     const float4 c01 = __ldg(c + 3 * m), c23 = __ldg(c + 3 * m + 1), c47 = __ldg(c + 3 * m + 2);
                     const float2 s = sSig[m * kRsChunk + lane];
                     const float a01[4] = {c01.x, c01.y, c01.z, c01.w}, a23[4] = {c23.x, c23.y, c23.z, c23.w},
@@ -244,9 +262,9 @@ __global__ void __launch_bounds__(kRsTargets, 3) k_rs_local(DevPlan P, RangeDev 
             __syncthreads();
             if (valid) {
                 const int kend = min(kRsChunk, total - base), kL = min(kend, max(0, nL - base));
-                rs_pairs<-1>(sE, sMeta, sIv, R.cell, cscale, R.nint, R.iv_dt, 0, kL, W0, W1, (int)lbj, nbl, nbc, hj, lj, trL,
+                rs_pairs<-1>(sE, meta, sIv, R.cell, cscale, R.nint, R.iv_dt, 0, kL, W0, W1, (int)lbj, nbl, nbc, hj, lj, trL,
                              a0h, a0l, a1h, a1l);
-                rs_pairs<1>(sE, sMeta, sIv, R.cell, cscale, R.nint, R.iv_dt, kL, kend, W0, W1, (int)lbj, nbl, nbc, -hj, -lj,
+                rs_pairs<1>(sE, meta, sIv, R.cell, cscale, R.nint, R.iv_dt, kL, kend, W0, W1, (int)lbj, nbl, nbc, -hj, -lj,
                             trR, a0h, a0l, a1h, a1l);
             }
             __syncthreads();
