@@ -264,6 +264,36 @@ int wave1d_adjoint(wave1d_plan_t plan, int64_t nsteps, const double* sigma, cons
                    const double* ubar, double* grad_beta, double* grad_g);
 
 /*
+ * The reverse march without the stored densities: the forward march keeps its state every
+ * `interval` steps (checkpoints), and the reverse pass marches each segment again from its
+ * checkpoint, recording that segment's densities, before taking the segment's transposed steps.
+ * Memory: ceil(nsteps / interval) checkpoints of the march state (the FP64 density ring of m_max + 1
+ * rows, the S ring and the modes: about (m_max + 1) M + 2 (W + 2)(K + 1) doubles each) plus one
+ * segment of interval x M densities, against nsteps x M for wave1d_adjoint; time: one more forward
+ * march.  interval ~ sqrt(nsteps (m_max + 1)) balances the two terms.  Marches driven by the
+ * incident wave (wave1d_solve); a march driven by forcing vectors takes wave1d_adjoint.
+ *   wave1d_checkpoint_size:    *bytes = size of the device buffer of the checkpoints.
+ *   wave1d_solve_checkpointed: from step 0 (a fresh plan, or one reloaded with a step-0 state),
+ *       nsteps steps as wave1d_solve with sigma = NULL, recording u into u_rec (nsteps x R, device
+ *       if u_on_device, else host; NULL allowed) and the checkpoints into ckpt (device, bytes >=
+ *       wave1d_checkpoint_size).  Synchronises.
+ *   wave1d_adjoint_checkpointed: the plan at the step its checkpointed march ended on, ckpt as
+ *       written by that march (same nsteps and interval, WAVE1D_EINVAL otherwise): dL/dbeta and
+ *       dL/dg as wave1d_adjoint with g = NULL (ubar, grad_beta, grad_g the same arrays).  The
+ *       recomputed densities are those of the first march bit for bit, so the gradients equal
+ *       wave1d_adjoint's from the stored densities bit for bit.  The plan's march state is put
+ *       back to the end of the march before the call returns.  Work arrays (those of
+ *       wave1d_adjoint, one segment of densities and a copy of the march state) are allocated for
+ *       the call.  Synchronises.
+ * The caller owns ckpt.
+ */
+int wave1d_checkpoint_size(wave1d_plan_t plan, int64_t nsteps, int64_t interval, size_t* bytes);
+int wave1d_solve_checkpointed(wave1d_plan_t plan, int64_t nsteps, int64_t interval, double* u_rec,
+                              int u_on_device, void* ckpt, size_t bytes);
+int wave1d_adjoint_checkpointed(wave1d_plan_t plan, int64_t nsteps, int64_t interval, const void* ckpt,
+                                size_t bytes, const double* ubar, double* grad_beta, double* grad_g);
+
+/*
  * Standalone NUFFTs of the history part (Sec. 3.1) on fixed points, with the time-step plan's
  * Kaiser-Bessel kernel (eq. KB), fine grid and deconvolution:
  *   type-1 (eq. densco):       S_k = (1/2 pi) sum_j c_j e^{+i k x_j},  k = 0..K

@@ -136,4 +136,23 @@ __global__ void k_adj_modes(int K, int W, int64_t n, const double* __restrict__ 
     if (k <= K) adj::modes_T(k, K + 1, W, n, rot, pq, ab, apb, Sb, a2);
 }
 
+// Checkpoint restore (wave1d_adjoint_checkpointed): the float-pair copy of the density ring
+// (both halves of its doubled ring) from the FP64 ring, the same split store_sigma makes, so a
+// march resumed from a checkpoint of the FP64 ring alone repeats the original bit for bit
+__global__ void k_ck_sig2(int64_t n, const double* __restrict__ sig, float2* __restrict__ sig2) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = sig[i];
+        const float hi = (float)v;
+        const float2 pr = make_float2(hi, (float)(v - (double)hi));
+        sig2[i] = pr;
+        sig2[i + n] = pr;
+    }
+}
+
+// the device step counter of a restored march
+__global__ void k_ck_step(int64_t* step, int64_t n) {
+    step[0] = n;
+    step[1] = 0;
+}
+
 }  // namespace wave1d

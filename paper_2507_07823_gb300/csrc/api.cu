@@ -52,6 +52,8 @@ __global__ void k_adj_rbc_update(int K, int npts, const int32_t* idx, const doub
                                  double* ab, double* apb);
 __global__ void k_adj_modes(int K, int W, int64_t n, const double* rot, const double* pq, double* ab, double* apb,
                             double* Sb, double* a2);
+__global__ void k_ck_sig2(int64_t n, const double* sig, float2* sig2);
+__global__ void k_ck_step(int64_t* step, int64_t n);
 __global__ void k_mx_gather(DevPlan P, const int64_t* perm, double* c);
 __global__ void k_mx_rhs(DevPlan P, const int64_t* perm, const double* u);
 __global__ void k_mx_receivers(int64_t R, const int64_t* perm, const double* u, double* uHr);
@@ -887,12 +889,13 @@ int wave1d_step(wave1d_plan_t p, const double* g_next, int g_on_device) {
     return leave(p);
 }
 
-int wave1d_solve(wave1d_plan_t p, int64_t nsteps, double* u_rec, double* sigma, int out_on_device) {
-    if (!p || nsteps < 0) return fail(WAVE1D_EINVAL, "bad solve arguments");
-    if (p->n + nsteps > p->hp.P.Nt) return fail(WAVE1D_EDONE, "nsteps beyond the Nt of the plan");
+}  // extern "C"
+
+namespace {
+// nsteps steps of wave1d_solve, queued (the caller holds the plan's device)
+int solve_steps(wave1d_plan_t p, int64_t nsteps, double* u_rec, double* sigma, int out_on_device) {
     const Params& P = p->hp.P;
-    int rc = enter(p);
-    if (rc) return rc;
+    int rc;
     p->started = true;
     if (sigma && !p->d_sig_hist) {
         if ((rc = dalloc(p, &p->d_sig_hist, (size_t)p->chunk * P.M))) return rc;
@@ -921,6 +924,18 @@ int wave1d_solve(wave1d_plan_t p, int64_t nsteps, double* u_rec, double* sigma, 
         p->n += cnt;
         done += cnt;
     }
+    return WAVE1D_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int wave1d_solve(wave1d_plan_t p, int64_t nsteps, double* u_rec, double* sigma, int out_on_device) {
+    if (!p || nsteps < 0) return fail(WAVE1D_EINVAL, "bad solve arguments");
+    if (p->n + nsteps > p->hp.P.Nt) return fail(WAVE1D_EDONE, "nsteps beyond the Nt of the plan");
+    int rc = enter(p);
+    if (rc) return rc;
+    if ((rc = solve_steps(p, nsteps, u_rec, sigma, out_on_device))) return rc;
     if ((rc = leave(p))) return rc;
     return check_status(p);
 }
@@ -1224,86 +1239,287 @@ unsigned blocks_for(int64_t threads, int per_block, int64_t cap) {
 
 extern "C" {
 
-int wave1d_adjoint(wave1d_plan_t p, int64_t nsteps, const double* sigma, const double* g, const double* ubar,
-                   double* grad_beta, double* grad_g) {
-    if (!p || !sigma || nsteps < 1 || (!grad_beta && !grad_g))
-        return fail(WAVE1D_EINVAL, "need a plan, sigma, nsteps >= 1 and grad_beta or grad_g");
-    if (p->range) return fail(WAVE1D_EUNSUPPORTED, "the reverse march reads stored local weights (local_weights = 0)");
-    const HostPlan& hp = p->hp;
-    const Params& P = hp.P;
-    if (nsteps > P.Nt) return fail(WAVE1D_EINVAL, "nsteps beyond the Nt of the plan");
-    if (P.R > 0 && !ubar) return fail(WAVE1D_EINVAL, "ubar is NULL");
-    if (grad_beta)
-        for (double b : hp.beta)
-            if (!(b > 0.0))
-                return fail(WAVE1D_EINVAL, "dL/dbeta needs every stiffness > 0 (its gradient term divides by beta_j)");
-    int rc = enter(p);
-    if (rc) return rc;
-    const int64_t M = P.M, R = P.R;
-    const int K = P.K, K1 = P.K + 1, ring = P.ring;
-    const DevPlan& d = p->dp;
+}  // extern "C"
+
+namespace {
+// The reverse march of one call: its work arrays and tables (allocated by init, released with wk)
+// and the transposed steps.  The adjoint state (sb, Sb, ab, apb) carries from one call of steps()
+// to the next, so the reverse march can be taken in segments.
+struct Reverse {
     AdjointWork wk;
-    wk.s = p->s;
-    if ((rc = wave1d_nufft_plan(hp.x.data(), M, K, P.tol, 0, (void*)p->s, &wk.nu)))
-        return fail(rc, std::string("NUFFT plan of the springs: ") + wave1d_nufft_strerror());
-    std::vector<int64_t> nperm(M);
-    if ((rc = wave1d_nufft_perm(wk.nu, nperm.data()))) return fail(rc, wave1d_nufft_strerror());
-    std::vector<int32_t> blk_of(M);
-    for (size_t b = 0; b + 1 < hp.blk_ptr.size(); b++)
-        for (int64_t e = hp.blk_ptr[b]; e < hp.blk_ptr[b + 1]; e++) blk_of[e] = (int32_t)b;
-    const int npts = (int)hp.rbc_idx.size();
-    ReceiverColumns rcol;
-    receiver_columns(hp.rloc, M, rcol);
+    wave1d_plan_t p = nullptr;
     double *sb, *Sb, *ab, *apb, *a2, *S1, *tmp, *cbar, *uHbar, *gsum, *cnu, *unu, *xr, *uvbar, *rw;
     int32_t *dblk, *rrcv, *rmr;
     int64_t *dperm, *rptr, *rwoff;
-    if ((rc = wk.zeros(&sb, (size_t)ring * M)) || (rc = wk.zeros(&Sb, (size_t)P.W * K1 * 2)) ||
-        (rc = wk.zeros(&ab, 2 * (size_t)K1)) || (rc = wk.zeros(&apb, 2 * (size_t)K1)) ||
-        (rc = wk.zeros(&a2, 2 * (size_t)K1)) || (rc = wk.zeros(&S1, 2 * (size_t)K1)) ||
-        (rc = wk.zeros(&tmp, (size_t)M)) || (rc = wk.zeros(&cbar, (size_t)M)) || (rc = wk.zeros(&uHbar, (size_t)M)) ||
-        (rc = wk.zeros(&gsum, (size_t)M)) || (rc = wk.zeros(&cnu, (size_t)M)) || (rc = wk.zeros(&unu, (size_t)M)) ||
-        (rc = wk.zeros(&uvbar, 2 * (size_t)std::max(npts, 1))) || (rc = wk.upload(hp.xr, &xr)) ||
-        (rc = wk.upload(blk_of, &dblk)) || (rc = wk.upload(nperm, &dperm)) ||
-        (rc = wk.upload(rcol.src_ptr, &rptr)) || (rc = wk.upload(rcol.rcv, &rrcv)) ||
-        (rc = wk.upload(rcol.mrange, &rmr)) || (rc = wk.upload(rcol.woff, &rwoff)) ||
-        (rc = wk.upload(hp.rloc.w, &rw)))
-        return rc;
-    // the transposed local sum: one warp per spring row, 4 warps per block
-    constexpr int kLocalWarps = 4;
-    const size_t lsmem = adj_local_smem(P.m_max, kLocalWarps);
-    if (lsmem > 227 * 1024) return fail(WAVE1D_EUNSUPPORTED, "window too long for the adjoint's local-sum accumulators");
-    if (lsmem > 48 * 1024)
-        CK(cudaFuncSetAttribute(k_adj_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem));
-    const int64_t cap = (int64_t)p->sms * 8;
-    const unsigned gM = blocks_for(M, 256, cap), gK = blocks_for(K1, 256, INT32_MAX);
-    cudaStream_t s = p->s;
-    for (int64_t n = nsteps - 1; n >= 0; n--) {
-        const double* ub = R > 0 ? ubar + n * R : nullptr;
-        if (R > 0 && !rcol.rcv.empty())
-            k_adj_receivers<<<gM, 256, 0, s>>>(M, ring, n, rptr, rrcv, rmr, rwoff, rw, ub, sb);
-        k_adj_take<<<gM, 256, 0, s>>>(M, sb + (int64_t)(((n + 1) % ring)) * M, tmp);
-        k_adj_solve<<<gM, 256, 0, s>>>(d, dblk, tmp, sigma + n * M, g ? g + n * M : nullptr, grad_beta ? gsum : nullptr,
-                                       grad_g ? grad_g + n * M : nullptr, cbar, uHbar);
-        if (n == 0) break;
-        if (d.l_nitems > 0)
-            k_adj_local<<<blocks_for(M * 32, 32 * kLocalWarps, INT32_MAX), 32 * kLocalWarps, lsmem, s>>>(d, n, cbar, sb);
-        k_adj_gather<<<gM, 256, 0, s>>>(M, dperm, uHbar, cnu);
-        if ((rc = wave1d_nufft_type1(wk.nu, cnu, S1))) return fail(rc, wave1d_nufft_strerror());
-        k_adj_modes_in<<<gK, 256, 0, s>>>(K, S1, xr, ub, R, ab);
-        if (P.bc == WAVE1D_FREE && (n + 1) % P.rbc_period == 0 && npts > 0) {
-            k_adj_rbc_grid<<<blocks_for(npts, 64, INT32_MAX), 64, 0, s>>>(K, npts, d.rbc_idx, d.tw2K, d.rbc_phi,
-                                                                         d.rbc_dphi, ab, apb, uvbar);
-            k_adj_rbc_update<<<gK, 256, 0, s>>>(K, npts, d.rbc_idx, d.tw2K, uvbar, ab, apb);
-        }
-        k_adj_modes<<<gK, 256, 0, s>>>(K, P.W, n, d.rot, d.pq, ab, apb, Sb, a2);
-        if ((rc = wave1d_nufft_type2(wk.nu, a2, unu))) return fail(rc, wave1d_nufft_strerror());
-        k_adj_scatter_add<<<gM, 256, 0, s>>>(M, dperm, unu, sb + (int64_t)(n % ring) * M);
-        CK(cudaGetLastError());
+    bool have_rcv = false;
+    int npts = 0;
+    size_t lsmem = 0;
+    static constexpr int kLocalWarps = 4;     // the transposed local sum: one warp per spring row
+
+    int init(wave1d_plan_t pl) {
+        p = pl;
+        wk.s = p->s;
+        const HostPlan& hp = p->hp;
+        const Params& P = hp.P;
+        const int64_t M = P.M;
+        const int K1 = P.K + 1;
+        int rc;
+        if ((rc = wave1d_nufft_plan(hp.x.data(), M, P.K, P.tol, 0, (void*)p->s, &wk.nu)))
+            return fail(rc, std::string("NUFFT plan of the springs: ") + wave1d_nufft_strerror());
+        std::vector<int64_t> nperm(M);
+        if ((rc = wave1d_nufft_perm(wk.nu, nperm.data()))) return fail(rc, wave1d_nufft_strerror());
+        std::vector<int32_t> blk_of(M);
+        for (size_t b = 0; b + 1 < hp.blk_ptr.size(); b++)
+            for (int64_t e = hp.blk_ptr[b]; e < hp.blk_ptr[b + 1]; e++) blk_of[e] = (int32_t)b;
+        npts = (int)hp.rbc_idx.size();
+        ReceiverColumns rcol;
+        receiver_columns(hp.rloc, M, rcol);
+        have_rcv = P.R > 0 && !rcol.rcv.empty();
+        if ((rc = wk.zeros(&sb, (size_t)P.ring * M)) || (rc = wk.zeros(&Sb, (size_t)P.W * K1 * 2)) ||
+            (rc = wk.zeros(&ab, 2 * (size_t)K1)) || (rc = wk.zeros(&apb, 2 * (size_t)K1)) ||
+            (rc = wk.zeros(&a2, 2 * (size_t)K1)) || (rc = wk.zeros(&S1, 2 * (size_t)K1)) ||
+            (rc = wk.zeros(&tmp, (size_t)M)) || (rc = wk.zeros(&cbar, (size_t)M)) || (rc = wk.zeros(&uHbar, (size_t)M)) ||
+            (rc = wk.zeros(&gsum, (size_t)M)) || (rc = wk.zeros(&cnu, (size_t)M)) || (rc = wk.zeros(&unu, (size_t)M)) ||
+            (rc = wk.zeros(&uvbar, 2 * (size_t)std::max(npts, 1))) || (rc = wk.upload(hp.xr, &xr)) ||
+            (rc = wk.upload(blk_of, &dblk)) || (rc = wk.upload(nperm, &dperm)) ||
+            (rc = wk.upload(rcol.src_ptr, &rptr)) || (rc = wk.upload(rcol.rcv, &rrcv)) ||
+            (rc = wk.upload(rcol.mrange, &rmr)) || (rc = wk.upload(rcol.woff, &rwoff)) ||
+            (rc = wk.upload(hp.rloc.w, &rw)))
+            return rc;
+        lsmem = adj_local_smem(P.m_max, kLocalWarps);
+        if (lsmem > 227 * 1024) return fail(WAVE1D_EUNSUPPORTED, "window too long for the adjoint's local-sum accumulators");
+        if (lsmem > 48 * 1024)
+            CK(cudaFuncSetAttribute(k_adj_local, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsmem));
+        return WAVE1D_OK;
     }
-    if (grad_beta) k_internal_to_caller<<<gM, 256, 0, s>>>(d.perm, M, gsum, grad_beta);
-    CK(cudaGetLastError());
-    CK(cudaStreamSynchronize(s));
+
+    // transposed steps n = n_hi - 1 down to n_lo; sig_rows: the device row of sigma^{n+1} (caller
+    // order) is sig_rows + (n - row0) M; g, ubar, grad_g: full nsteps-row arrays (or null)
+    int steps(int64_t n_hi, int64_t n_lo, const double* sig_rows, int64_t row0, const double* g, const double* ubar,
+              bool want_beta, double* grad_g) {
+        const Params& P = p->hp.P;
+        const int64_t M = P.M, R = P.R;
+        const int K = P.K, K1 = P.K + 1, ring = P.ring;
+        const DevPlan& d = p->dp;
+        const int64_t cap = (int64_t)p->sms * 8;
+        const unsigned gM = blocks_for(M, 256, cap), gK = blocks_for(K1, 256, INT32_MAX);
+        cudaStream_t s = p->s;
+        int rc;
+        for (int64_t n = n_hi - 1; n >= n_lo; n--) {
+            const double* ub = R > 0 ? ubar + n * R : nullptr;
+            if (have_rcv) k_adj_receivers<<<gM, 256, 0, s>>>(M, ring, n, rptr, rrcv, rmr, rwoff, rw, ub, sb);
+            k_adj_take<<<gM, 256, 0, s>>>(M, sb + (int64_t)(((n + 1) % ring)) * M, tmp);
+            k_adj_solve<<<gM, 256, 0, s>>>(d, dblk, tmp, sig_rows + (n - row0) * M, g ? g + n * M : nullptr,
+                                           want_beta ? gsum : nullptr, grad_g ? grad_g + n * M : nullptr, cbar, uHbar);
+            if (n == 0) break;
+            if (d.l_nitems > 0)
+                k_adj_local<<<blocks_for(M * 32, 32 * kLocalWarps, INT32_MAX), 32 * kLocalWarps, lsmem, s>>>(d, n, cbar, sb);
+            k_adj_gather<<<gM, 256, 0, s>>>(M, dperm, uHbar, cnu);
+            if ((rc = wave1d_nufft_type1(wk.nu, cnu, S1))) return fail(rc, wave1d_nufft_strerror());
+            k_adj_modes_in<<<gK, 256, 0, s>>>(K, S1, xr, ub, R, ab);
+            if (P.bc == WAVE1D_FREE && (n + 1) % P.rbc_period == 0 && npts > 0) {
+                k_adj_rbc_grid<<<blocks_for(npts, 64, INT32_MAX), 64, 0, s>>>(K, npts, d.rbc_idx, d.tw2K, d.rbc_phi,
+                                                                             d.rbc_dphi, ab, apb, uvbar);
+                k_adj_rbc_update<<<gK, 256, 0, s>>>(K, npts, d.rbc_idx, d.tw2K, uvbar, ab, apb);
+            }
+            k_adj_modes<<<gK, 256, 0, s>>>(K, P.W, n, d.rot, d.pq, ab, apb, Sb, a2);
+            if ((rc = wave1d_nufft_type2(wk.nu, a2, unu))) return fail(rc, wave1d_nufft_strerror());
+            k_adj_scatter_add<<<gM, 256, 0, s>>>(M, dperm, unu, sb + (int64_t)(n % ring) * M);
+            CK(cudaGetLastError());
+        }
+        return WAVE1D_OK;
+    }
+
+    int finish(double* grad_beta) {
+        if (grad_beta)
+            k_internal_to_caller<<<blocks_for(p->hp.P.M, 256, (int64_t)p->sms * 8), 256, 0, p->s>>>(p->dp.perm, p->hp.P.M,
+                                                                                                  gsum, grad_beta);
+        CK(cudaGetLastError());
+        CK(cudaStreamSynchronize(p->s));
+        return WAVE1D_OK;
+    }
+};
+
+int adjoint_checks(wave1d_plan_t p, int64_t nsteps, const double* ubar, double* grad_beta, double* grad_g) {
+    if (nsteps < 1 || (!grad_beta && !grad_g))
+        return fail(WAVE1D_EINVAL, "need nsteps >= 1 and grad_beta or grad_g");
+    if (p->range) return fail(WAVE1D_EUNSUPPORTED, "the reverse march reads stored local weights (local_weights = 0)");
+    const Params& P = p->hp.P;
+    if (nsteps > P.Nt) return fail(WAVE1D_EINVAL, "nsteps beyond the Nt of the plan");
+    if (P.R > 0 && !ubar) return fail(WAVE1D_EINVAL, "ubar is NULL");
+    if (grad_beta)
+        for (double b : p->hp.beta)
+            if (!(b > 0.0))
+                return fail(WAVE1D_EINVAL, "dL/dbeta needs every stiffness > 0 (its gradient term divides by beta_j)");
+    return WAVE1D_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Checkpoints of the march for the reverse pass: a header, then per checkpoint k (the state at
+// step k * interval) the FP64 density ring, the S ring and the modes alpha, alpha'.  The float-pair
+// density ring is rebuilt from the FP64 one on restore; the receiver history is not needed to
+// march again.
+// ---------------------------------------------------------------------------------------------
+struct CkptHeader {
+    char magic[8];
+    int64_t M, K, W, ring, nsteps, interval, count, stride;
+};
+constexpr size_t kCkptHead = 256;
+
+struct CkptPart {
+    void* dev;
+    size_t bytes;
+};
+
+std::vector<CkptPart> ckpt_parts(wave1d_plan_t p) {
+    const Params& P = p->hp.P;
+    const DevPlan& d = p->dp;
+    const size_t K1 = (size_t)P.K + 1;
+    return {{d.sig, sizeof(double) * (size_t)P.ring * P.M},
+            {d.Sring, sizeof(double) * 2 * (size_t)P.W * K1},
+            {d.alpha, sizeof(double) * 2 * K1},
+            {d.alpha_p, sizeof(double) * 2 * K1}};
+}
+
+size_t ckpt_stride(wave1d_plan_t p) {
+    size_t b = 0;
+    for (const CkptPart& c : ckpt_parts(p)) b += (c.bytes + 255) / 256 * 256;
+    return b;
+}
+
+void ckpt_header(wave1d_plan_t p, int64_t nsteps, int64_t interval, CkptHeader& h) {
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, "WAVE1DC", 8);
+    const Params& P = p->hp.P;
+    h.M = P.M;
+    h.K = P.K;
+    h.W = P.W;
+    h.ring = P.ring;
+    h.nsteps = nsteps;
+    h.interval = interval;
+    h.count = (nsteps + interval - 1) / interval;
+    h.stride = (int64_t)ckpt_stride(p);
+}
+
+// queue copies between the plan's march state and checkpoint k of buf (save: state -> buf)
+int ckpt_copy(wave1d_plan_t p, char* buf, int64_t k, bool save) {
+    char* at = buf + kCkptHead + (size_t)k * ckpt_stride(p);
+    for (const CkptPart& c : ckpt_parts(p)) {
+        if (save) CK(cudaMemcpyAsync(at, c.dev, c.bytes, cudaMemcpyDeviceToDevice, p->s));
+        else CK(cudaMemcpyAsync(c.dev, at, c.bytes, cudaMemcpyDeviceToDevice, p->s));
+        at += (c.bytes + 255) / 256 * 256;
+    }
+    return WAVE1D_OK;
+}
+
+// the march state of a plan (every part wave1d_state_save writes), kept on the device
+struct DeviceState {
+    std::vector<void*> bufs;
+    int64_t n = 0;
+    ~DeviceState() {
+        for (void* b : bufs) cudaFree(b);
+    }
+};
+}  // namespace
+
+extern "C" {
+
+int wave1d_adjoint(wave1d_plan_t p, int64_t nsteps, const double* sigma, const double* g, const double* ubar,
+                   double* grad_beta, double* grad_g) {
+    if (!p || !sigma) return fail(WAVE1D_EINVAL, "need a plan and sigma");
+    int rc = adjoint_checks(p, nsteps, ubar, grad_beta, grad_g);
+    if (rc) return rc;
+    if ((rc = enter(p))) return rc;
+    Reverse r;
+    if ((rc = r.init(p))) return rc;
+    if ((rc = r.steps(nsteps, 0, sigma, 0, g, ubar, grad_beta != nullptr, grad_g))) return rc;
+    if ((rc = r.finish(grad_beta))) return rc;
     return leave(p);
+}
+
+int wave1d_checkpoint_size(wave1d_plan_t p, int64_t nsteps, int64_t interval, size_t* bytes) {
+    if (!p || !bytes || nsteps < 1 || interval < 1) return fail(WAVE1D_EINVAL, "bad arguments");
+    CkptHeader h;
+    ckpt_header(p, nsteps, interval, h);
+    *bytes = kCkptHead + (size_t)h.count * (size_t)h.stride;
+    return WAVE1D_OK;
+}
+
+int wave1d_solve_checkpointed(wave1d_plan_t p, int64_t nsteps, int64_t interval, double* u_rec, int u_on_device,
+                              void* ckpt, size_t bytes) {
+    if (!p || !ckpt || nsteps < 1 || interval < 1) return fail(WAVE1D_EINVAL, "bad arguments");
+    if (p->n != 0) return fail(WAVE1D_EINVAL, "the checkpointed march starts at step 0 (a fresh or reloaded plan)");
+    if (nsteps > p->hp.P.Nt) return fail(WAVE1D_EDONE, "nsteps beyond the Nt of the plan");
+    size_t need = 0;
+    wave1d_checkpoint_size(p, nsteps, interval, &need);
+    if (bytes < need) return fail(WAVE1D_EINVAL, "checkpoint buffer smaller than wave1d_checkpoint_size");
+    int rc = enter(p);
+    if (rc) return rc;
+    CkptHeader h;
+    ckpt_header(p, nsteps, interval, h);
+    CK(cudaMemcpy(ckpt, &h, sizeof(h), cudaMemcpyHostToDevice));
+    const int64_t R = p->hp.P.R;
+    for (int64_t k = 0; k < h.count; k++) {
+        if ((rc = ckpt_copy(p, (char*)ckpt, k, true))) return rc;
+        const int64_t n0 = k * interval, cnt = std::min(interval, nsteps - n0);
+        if ((rc = solve_steps(p, cnt, u_rec ? u_rec + n0 * R : nullptr, nullptr, u_on_device))) return rc;
+    }
+    if ((rc = leave(p))) return rc;
+    return check_status(p);
+}
+
+int wave1d_adjoint_checkpointed(wave1d_plan_t p, int64_t nsteps, int64_t interval, const void* ckpt, size_t bytes,
+                                const double* ubar, double* grad_beta, double* grad_g) {
+    if (!p || !ckpt || interval < 1) return fail(WAVE1D_EINVAL, "bad arguments");
+    int rc = adjoint_checks(p, nsteps, ubar, grad_beta, grad_g);
+    if (rc) return rc;
+    size_t need = 0;
+    wave1d_checkpoint_size(p, nsteps, interval, &need);
+    if (bytes < need) return fail(WAVE1D_EINVAL, "checkpoint buffer smaller than wave1d_checkpoint_size");
+    CkptHeader h, mine;
+    ckpt_header(p, nsteps, interval, mine);
+    if (cudaMemcpy(&h, ckpt, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess || std::memcmp(&h, &mine, sizeof(h)) != 0)
+        return fail(WAVE1D_EINVAL, "not checkpoints of this plan, nsteps and interval (wave1d_solve_checkpointed)");
+    if (p->n != nsteps) return fail(WAVE1D_EINVAL, "the plan is not at the step its checkpointed march ended on");
+    if ((rc = enter(p))) return rc;
+    const Params& P = p->hp.P;
+    const int64_t M = P.M;
+    // the march's final state, put back at the end
+    DeviceState fin;
+    for (const StatePart& sp : state_parts(p)) {
+        void* b = nullptr;
+        if (cudaMalloc(&b, sp.bytes) != cudaSuccess) return fail(WAVE1D_ENOMEM, "final-state copy");
+        fin.bufs.push_back(b);
+        CK(cudaMemcpyAsync(b, sp.dev, sp.bytes, cudaMemcpyDeviceToDevice, p->s));
+    }
+    fin.n = p->n;
+    Reverse r;
+    if ((rc = r.init(p))) return rc;
+    double* seg = nullptr;
+    if ((rc = r.wk.zeros(&seg, (size_t)std::min(interval, nsteps) * M))) return rc;
+    const unsigned gS = blocks_for((int64_t)P.ring * M, 256, (int64_t)p->sms * 8);
+    for (int64_t k = h.count - 1; k >= 0; k--) {
+        // restore checkpoint k, march its segment again recording the densities, then the
+        // segment's reverse steps
+        const int64_t n0 = k * interval, n1 = std::min(nsteps, n0 + interval);
+        if ((rc = ckpt_copy(p, (char*)const_cast<void*>(ckpt), k, false))) return rc;
+        k_ck_sig2<<<gS, 256, 0, p->s>>>((int64_t)P.ring * M, p->dp.sig, (float2*)p->dp.sig2);
+        k_ck_step<<<1, 1, 0, p->s>>>(p->dp.step, n0);
+        CK(cudaGetLastError());
+        p->n = n0;
+        if ((rc = solve_steps(p, n1 - n0, nullptr, seg, 1))) return rc;
+        if ((rc = r.steps(n1, n0, seg, n0, nullptr, ubar, grad_beta != nullptr, grad_g))) return rc;
+    }
+    if ((rc = r.finish(grad_beta))) return rc;
+    size_t i = 0;
+    for (const StatePart& sp : state_parts(p))
+        CK(cudaMemcpyAsync(sp.dev, fin.bufs[i++], sp.bytes, cudaMemcpyDeviceToDevice, p->s));
+    k_ck_step<<<1, 1, 0, p->s>>>(p->dp.step, fin.n);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(p->s));
+    p->n = fin.n;
+    if ((rc = leave(p))) return rc;
+    return check_status(p);
 }
 
 int wave1d_destroy(wave1d_plan_t p) {

@@ -45,7 +45,8 @@ EXPORTED = ["wave1d_opts_default", "wave1d_plan", "wave1d_set_incident_gaussians
             "wave1d_nufft_plan", "wave1d_nufft_plan_many", "wave1d_nufft_info", "wave1d_nufft_perm",
             "wave1d_nufft_spread",
             "wave1d_nufft_interp", "wave1d_nufft_type1", "wave1d_nufft_type2", "wave1d_nufft_destroy",
-            "wave1d_nufft_strerror", "wave1d_adjoint", "wave1d_batch_plan", "wave1d_batch_solve",
+            "wave1d_nufft_strerror", "wave1d_adjoint", "wave1d_checkpoint_size", "wave1d_solve_checkpointed",
+            "wave1d_adjoint_checkpointed", "wave1d_batch_plan", "wave1d_batch_solve",
             "wave1d_batch_destroy", "wave1d_batch_strerror", "wave1d_nufft_autotune"]
 
 WAVE1D_NSTAGE = 9
@@ -122,6 +123,10 @@ def lib(path: str = LIB_PATH):
         L.wave1d_nufft_autotune.argtypes = [P, _D, _D, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                             ctypes.POINTER(ctypes.c_int)]
         L.wave1d_adjoint.argtypes = [P, ctypes.c_int64, _D, _D, _D, _D, _D]
+        L.wave1d_checkpoint_size.argtypes = [P, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]
+        L.wave1d_solve_checkpointed.argtypes = [P, ctypes.c_int64, ctypes.c_int64, _D, ctypes.c_int, P,
+                                                ctypes.c_size_t]
+        L.wave1d_adjoint_checkpointed.argtypes = [P, ctypes.c_int64, ctypes.c_int64, P, ctypes.c_size_t, _D, _D, _D]
         _I64 = ctypes.POINTER(ctypes.c_int64)
         L.wave1d_batch_plan.argtypes = [ctypes.c_int, _I64, _D, _D, _D, _I64, _D, ctypes.c_double, ctypes.c_int64,
                                         ctypes.c_double, ctypes.POINTER(wave1d_opts), ctypes.POINTER(ctypes.c_void_p)]
@@ -205,6 +210,27 @@ def wave1d_adjoint(plan, nsteps, sigma, g, ubar, grad_beta, grad_g):
     def opt(t):
         return _dptr(t) if t is not None else None
     return lib().wave1d_adjoint(plan, int(nsteps), _dptr(sigma), opt(g), opt(ubar), opt(grad_beta), opt(grad_g))
+
+
+def wave1d_checkpoint_size(plan, nsteps, interval):
+    b = ctypes.c_size_t()
+    _check(lib().wave1d_checkpoint_size(plan, int(nsteps), int(interval), ctypes.byref(b)), "wave1d_checkpoint_size")
+    return b.value
+
+
+def wave1d_solve_checkpointed(plan, nsteps, interval, u_rec, ckpt):
+    """u_rec: device tensor (nsteps x R) or None; ckpt: device tensor of wave1d_checkpoint_size bytes."""
+    return lib().wave1d_solve_checkpointed(plan, int(nsteps), int(interval),
+                                           _dptr(u_rec) if u_rec is not None else None, 1,
+                                           ctypes.c_void_p(ckpt.data_ptr()), ckpt.numel() * ckpt.element_size())
+
+
+def wave1d_adjoint_checkpointed(plan, nsteps, interval, ckpt, ubar, grad_beta, grad_g):
+    def opt(t):
+        return _dptr(t) if t is not None else None
+    return lib().wave1d_adjoint_checkpointed(plan, int(nsteps), int(interval), ctypes.c_void_p(ckpt.data_ptr()),
+                                             ckpt.numel() * ckpt.element_size(), opt(ubar), opt(grad_beta),
+                                             opt(grad_g))
 
 
 class Nufft:
@@ -392,6 +418,26 @@ class Plan:
         ub = ubar.contiguous() if self.R else None
         gin = g.contiguous() if g is not None else None
         _check(wave1d_adjoint(self.h, n, sigma.contiguous(), gin, ub, gb, gg), "wave1d_adjoint")
+        return (gb, gg) if forcing_gradient else gb
+
+    def solve_checkpointed(self, nsteps, interval):
+        """The march from step 0 keeping its state every `interval` steps: (u, ckpt), u the
+        receiver fields (nsteps x R torch CUDA tensor), ckpt the checkpoints (a uint8 CUDA tensor)."""
+        import torch
+        ckpt = torch.empty(wave1d_checkpoint_size(self.h, nsteps, interval), dtype=torch.uint8, device="cuda")
+        u = torch.empty((nsteps, max(self.R, 1)), dtype=torch.float64, device="cuda")
+        _check(wave1d_solve_checkpointed(self.h, nsteps, interval, u if self.R else None, ckpt),
+               "wave1d_solve_checkpointed")
+        return u[:, :self.R], ckpt
+
+    def adjoint_checkpointed(self, ckpt, nsteps, interval, ubar, forcing_gradient=False):
+        """dL/dbeta (and dL/dg with forcing_gradient=True) from the checkpoints of
+        solve_checkpointed(nsteps, interval) and ubar = dL/du (nsteps x R torch CUDA tensor)."""
+        import torch
+        gb = torch.empty(self.M, dtype=torch.float64, device="cuda")
+        gg = torch.empty((nsteps, self.M), dtype=torch.float64, device="cuda") if forcing_gradient else None
+        ub = ubar.contiguous() if self.R else None
+        _check(wave1d_adjoint_checkpointed(self.h, nsteps, interval, ckpt, ub, gb, gg), "wave1d_adjoint_checkpointed")
         return (gb, gg) if forcing_gradient else gb
 
     def step(self, g=None):

@@ -136,3 +136,51 @@ def test_gradient_matches_central_differences_of_the_gpu_march():
         rest[-1].close()
         fd = (Lp - Lm) / (2 * h)
         assert abs(g[j] - fd) <= 1e-6 * np.max(np.abs(g)), (j, g[j], fd)
+
+
+@pytest.mark.parametrize("interval", [37, 64, 1000])
+def test_checkpointed_gradient_equals_the_stored_density_gradient(interval):
+    """wave1d_solve_checkpointed + wave1d_adjoint_checkpointed (the march state kept every
+    `interval` steps, each segment marched again in the reverse pass) against wave1d_adjoint from
+    the stored densities: the same dL/dbeta and dL/dg bit for bit (intervals that do and do not
+    divide the march, one longer than it), and the plan back at the end of its march."""
+    w = _layout(W.FREE, seed=21, M=40, dt=0.02, Nt=400)
+    rng = np.random.default_rng(3)
+    w = w.with_(x=np.sort(rng.uniform(-0.9, 0.9, w.M)), beta=rng.uniform(1.0, 6.0, w.M))
+    nsteps = 300
+    d = torch.from_numpy(_targets(w)[1:nsteps + 1]).cuda()
+    ref = wave1d.Plan.from_workload(w)
+    plan = wave1d.Plan.from_workload(w)
+    try:
+        sigma, u = ref.solve_device(nsteps)
+        gb, gg = ref.adjoint(sigma, u - d, forcing_gradient=True)
+        u2, ckpt = plan.solve_checkpointed(nsteps, interval)
+        assert torch.equal(u, u2)
+        gb2, gg2 = plan.adjoint_checkpointed(ckpt, nsteps, interval, u2 - d, forcing_gradient=True)
+        assert torch.equal(gb, gb2) and torch.equal(gg, gg2)
+        assert float(torch.max(torch.abs(gb))) > 0.0
+        # the plan continues from the end of its march as the uninterrupted one does
+        for _ in range(5):
+            ref.step()
+            plan.step()
+        assert np.array_equal(ref.sigma(), plan.sigma())
+        assert np.array_equal(ref.receivers(), plan.receivers())
+    finally:
+        ref.close()
+        plan.close()
+
+
+def test_checkpointed_march_rejects_mismatched_calls():
+    w = _layout(W.PERIODIC, seed=4, Nt=100)
+    plan = wave1d.Plan.from_workload(w)
+    try:
+        u, ckpt = plan.solve_checkpointed(60, 16)
+        ubar = torch.zeros_like(u)
+        # other interval or length than the march that wrote the checkpoints
+        for n, iv in ((60, 15), (59, 16)):
+            gb = torch.empty(w.M, dtype=torch.float64, device="cuda")
+            assert wave1d.wave1d_adjoint_checkpointed(plan.h, n, iv, ckpt, ubar, gb, None) == wave1d.WAVE1D_EINVAL
+        # a march that does not start at step 0
+        assert wave1d.wave1d_solve_checkpointed(plan.h, 10, 5, None, ckpt) == wave1d.WAVE1D_EINVAL
+    finally:
+        plan.close()
