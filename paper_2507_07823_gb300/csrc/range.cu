@@ -106,27 +106,27 @@ __device__ __forceinline__ void rs_pairs(const float* sE, const float4* sMeta, c
                                          float& a1h, float& a1l) {
     for (int k = k0; k < k1; k += 2) {
         // the record and z of sources k and k + 1 (null where the pair does not count in this
-        // window), then both polynomials as independent chains
-        const float* rec[2] = {nullptr, nullptr};
-        float zh[2] = {0.f, 0.f}, zl[2] = {0.f, 0.f};
+        // window), then both polynomials as independent chains.  z is computed for every slot
+        // (the group's meta holds 256 defined entries, so slot k + 1 >= k1 reads one); only a
+        // pair that counts moves the tracked interval.
+        const float* rec[2];
+        float zh[2], zl[2];
 #pragma unroll
         for (int u = 0; u < 2; u++) {
             const int kk = k + u;
-            if (kk >= k1) break;
             const float4 mt = sMeta[kk];
             const int e = __float_as_int(mt.z), lohi = __float_as_int(mt.w);
             const int lo = max(lohi & 0x7fff, W0), hi = min(lohi >> 16, W1);
-            if (lo > hi || (S < 0 ? e >= lbj : e < lbj)) continue;
+            const bool valid = kk < k1 && lo <= hi && (S < 0 ? e < lbj : e >= lbj);
             float h0, l0;
             rs::z_of<S>(tr, mt.x, mt.y, h0, l0);
-            if (fabsf(h0) > rs::kZTol) rs::walk<S>(ivt, cell, cscale, nint, bh, bl, mt.x, mt.y, tr, h0, l0);
-            if (lohi & 0x8000)
+            if (valid && fabsf(h0) > rs::kZTol) rs::walk<S>(ivt, cell, cscale, nint, bh, bl, mt.x, mt.y, tr, h0, l0);
+            if (valid && (lohi & 0x8000))
                 rs::near_side<S>(ivt, iv_dt, (unsigned)(e - nbl) < (unsigned)nbc, bh, bl, mt.x, mt.y, tr, h0, l0);
-            if (fabsf(h0) <= rs::kZTol && tr.iv >= lo && tr.iv <= hi) {
-                rec[u] = sE + (tr.iv - W0) * kRsRow + kk * rs::kERecord;
-                zh[u] = h0;
-                zl[u] = l0;
-            }
+            const bool ok = valid && fabsf(h0) <= rs::kZTol && tr.iv >= lo && tr.iv <= hi;
+            rec[u] = ok ? sE + (tr.iv - W0) * kRsRow + kk * rs::kERecord : nullptr;
+            zh[u] = h0;
+            zl[u] = l0;
         }
         if (rec[0]) rs::evec_eval(rec[0], zh[0], zl[0], a0h, a0l);
         if (rec[1]) rs::evec_eval(rec[1], zh[1], zl[1], a1h, a1l);

@@ -134,18 +134,32 @@ WAVE1D_RS_HD void evec_mac(EVec& v, const float* c01, const float* c23, const fl
 // Packed record of an e-vector in shared memory (12 floats: e0h e0l e1h e1l e2..e7, two spare).
 constexpr int kERecord = 12;
 
+// four consecutive floats from a 16-byte aligned address (one vector load on the device)
+struct F4 {
+    float x, y, z, w;
+};
+WAVE1D_RS_HD F4 load4(const float* p) {
+#ifdef __CUDA_ARCH__
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    return {v.x, v.y, v.z, v.w};
+#else
+    return {p[0], p[1], p[2], p[3]};
+#endif
+}
+
 // acc += e0 + z (e1 + z P(z)),  P(z) = e2 + z (e3 + z (e4 + z (e5 + z (e6 + z e7)))),
 // z = zh + zl normalised; e is a packed record
 WAVE1D_RS_HD void evec_eval(const float* e, float zh, float zl, float& ah, float& al) {
-    float P = fma_(e[9], zh, e[8]);                 // e7 z + e6
-    P = fma_(P, zh, e[7]);                          // + e5
-    P = fma_(P, zh, e[6]);
-    P = fma_(P, zh, e[5]);
-    P = fma_(P, zh, e[4]);                          // P(z)
+    const F4 r0 = load4(e), r1 = load4(e + 4), r2 = load4(e + 8);   // (e0h e0l e1h e1l) (e2..e5) (e6 e7 - -)
+    float P = fma_(r2.y, zh, r2.x);                 // e7 z + e6
+    P = fma_(P, zh, r1.w);                          // + e5
+    P = fma_(P, zh, r1.z);
+    P = fma_(P, zh, r1.y);
+    P = fma_(P, zh, r1.x);                          // P(z)
     // w = e1 + z P as a pair
     float wh, we;
-    two_sum(e[2], mul(zh, P), wh, we);
-    const float wl = add(e[3], we);
+    two_sum(r0.z, mul(zh, P), wh, we);
+    const float wl = add(r0.w, we);
     // z w as a pair (p, pe)
     const float p = mul(zh, wh);
     float pe = fma_(zh, wh, -p);
@@ -153,8 +167,8 @@ WAVE1D_RS_HD void evec_eval(const float* e, float zh, float zl, float& ah, float
     pe = fma_(zl, wh, pe);
     // acc += e0 + z w
     float s, se;
-    two_sum(e[0], p, s, se);
-    acc_add(ah, al, s, add(e[1], add(pe, se)));
+    two_sum(r0.x, p, s, se);
+    acc_add(ah, al, s, add(r0.y, add(pe, se)));
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -206,10 +220,11 @@ struct Track {
 
 // ivt: the block's interval table, 4 floats per interval (interval_on_grid)
 WAVE1D_RS_HD void track_to(const float* ivt, int iv, float bh, float bl, Track& t) {
+    const F4 v = load4(ivt + 4 * iv);
     t.iv = iv;
-    t.Yh = sub(bh, ivt[4 * iv]);
-    t.Yl = sub(bl, ivt[4 * iv + 1]);
-    t.ih = ivt[4 * iv + 2];
+    t.Yh = sub(bh, v.x);
+    t.Yl = sub(bl, v.y);
+    t.ih = v.z;
 }
 
 // z = zh + zl (normalised) of the source (h, l) on side S (-1: left sources, d = x_j - x; +1:
