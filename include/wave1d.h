@@ -112,6 +112,8 @@ typedef struct {
                                  per-m counts, row offsets and its output                         */
     int64_t local_terms;      /* multiply-adds Q_m(d_jl) sigma_l^{n+1-m} of the local sum per step
                                  (pairs closer than delta times their non-zero m >= 1)            */
+    int64_t solve_sweeps;     /* local_weights = 1: Jacobi sweeps of the last step's implicit solve
+                                 (read from the device; waits for the plan's queued work), else 0 */
 } wave1d_info;
 
 /* Fill *o with defaults.  Returns WAVE1D_EINVAL if o is NULL. */

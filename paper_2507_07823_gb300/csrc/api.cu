@@ -1120,6 +1120,14 @@ int wave1d_get_info(wave1d_plan_t p, wave1d_info* info) {
     info->device_bytes = p->bytes;
     info->local_bytes = p->info_local_bytes;
     info->local_terms = p->info_terms;
+    info->solve_sweeps = 0;
+    if (p->range && p->n > 0) {
+        int it = 0;
+        if (cudaStreamSynchronize(p->s) != cudaSuccess ||
+            cudaMemcpy(&it, p->rd.iters, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return fail(WAVE1D_ECUDA, "reading the solve's sweep count");
+        info->solve_sweeps = it;
+    }
     return WAVE1D_OK;
 }
 

@@ -74,7 +74,8 @@ class wave1d_info(ctypes.Structure):
                 ("local_pairs", ctypes.c_int64), ("local_weights", ctypes.c_int64),
                 ("nearby_pairs", ctypes.c_int64), ("blocks", ctypes.c_int64),
                 ("max_block", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
-                ("local_bytes", ctypes.c_int64), ("local_terms", ctypes.c_int64)]
+                ("local_bytes", ctypes.c_int64), ("local_terms", ctypes.c_int64),
+                ("solve_sweeps", ctypes.c_int64)]
 
 
 _lib = None
