@@ -48,7 +48,7 @@ L2_CLEAN_BYTES = 256 << 20
 # DRAM bytes of one k_rs_local launch from one ncu capture of the clustered layout at M = 2e5 (its
 # pairs below), for the kernel sources it was taken with (null once they change)
 RS_LOCAL_SOURCES = ["range.cu", "range.cuh", "phases.cuh", "device_common.cuh", "internal.h"]
-RS_LOCAL_TRAFFIC = {"sources_sha256": "", "bytes_per_launch": 0.0, "pairs": 1}
+RS_LOCAL_TRAFFIC = {"sources_sha256": "de4d7f3226f9a8b860e5982cd0bd675157d1a81ff94b20cfafbe582e7f25ec38", "bytes_per_launch": 71748096.0, "pairs": 2935880666}
 
 
 def _peaks():
@@ -374,7 +374,9 @@ def free_space_secondary(torch, stream):
 
 def rs_local_traffic(info):
     """DRAM bytes per k_rs_local launch at this workload, scaled by pairs from one ncu capture of a
-    smaller clustered case (M = 2e5), while the kernel sources match the ones it was taken with."""
+    smaller clustered case (M = 2.5e5 in 4 clusters, the million-spring cluster density; the
+    kernel's DRAM bytes are the window densities and positions it reads, which grow with the pairs),
+    while the kernel sources match the ones it was taken with."""
     import hashlib
     h = hashlib.sha256()
     src = os.path.join(ROOT, "paper_2507_07823_gb300", "csrc")
@@ -431,6 +433,23 @@ def spread_interp_million(torch, stream, flush_l2, hbm, reps=20):
                                 if precision == 0 else
                                 f"FP32 polynomials of degree {nu.degree} (max error {nu.kernel_err:.1e})")}
         nu.close()
+    # the same event protocol around a plain device copy of 8 MB (16 MB of traffic, one pass's
+    # algorithmic bytes): the ceiling of an isolated pass this small, launch and ramp included
+    a = torch.rand(w2.M, dtype=torch.float64, device="cuda")
+    b = torch.empty_like(a)
+    tc = []
+    for _ in range(reps):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        flush_l2()
+        ev[0].record(stream)
+        b.copy_(a)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        tc.append(ev[0].elapsed_time(ev[1]))
+    t_c = float(np.median(tc))
+    out["copy_reference"] = {"bytes": 16 * w2.M, "us": 1e3 * t_c,
+                             "frac_of_hbm": 16 * w2.M / (t_c * 1e-3) / 1e9 / hbm,
+                             "what": "torch device copy of M doubles after the same L2 flush, one launch"}
     return out
 
 
@@ -679,51 +698,132 @@ def run_spread_interp_only(args):
                                                                      reps=args.spread_interp_reps)}))
 
 
+def _adjoint_plan(wave1d, w, beta=None):
+    b = w.beta if beta is None else beta
+    return wave1d.Plan(w.x, b, w.bc, w.dt, w.Nt, w.tol, w.amp, w.center, w.width, w.xr, p=w.p,
+                       max_local_bytes=64 << 30)
+
+
 def run_adjoint_only(args):
-    """Forward march and reverse-time march (wave1d_adjoint) on the adjoint workload (free space,
-    M = 1e5, dt = 1e-3, 8 receivers) over args.adjoint_steps steps; one JSON line with both
-    rates.  Not part of the default benchmark line."""
+    """The reverse-time march on the adjoint workload's recipe (free space, dt = 1e-3, tol = 1e-12,
+    p = 8, beta ~ U[1, 10], 8 receivers): both strategies (stored densities, wave1d_adjoint; the
+    march state checkpointed every `interval` steps and recomputed, wave1d_adjoint_checkpointed,
+    which must give the same gradient bit for bit), and central differences of the loss
+    L = 1/2 sum (u - d)^2 (d a seeded target trace) on 32 random stiffnesses.  The workload's own
+    M = 1e5 is tried first; it puts all springs in one implicit block (18.5 springs per dt), which the stored-weight plan the
+    reverse march needs does not solve, so the line records that and runs the largest M of the
+    recipe given by --adjoint-M.  One JSON line; not part of the default benchmark line."""
     import torch
 
     from paper_2507_07823_gb300 import build, wave1d, workloads
 
     build.build()
     nsteps = args.adjoint_steps
-    w = workloads.config4(Nt=nsteps)
-    t0 = time.perf_counter()
-    plan = wave1d.Plan.from_workload(w, max_local_bytes=64 << 30)
-    t_plan = time.perf_counter() - t0
-    rng = np.random.default_rng(w.seed)
-    d = torch.from_numpy(0.01 * rng.standard_normal((nsteps, len(w.xr)))).cuda()
-    stream = torch.cuda.current_stream()
-    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    e[0].record(stream)
-    sigma, u = plan.solve_device(nsteps)
-    e[1].record(stream)
-    torch.cuda.synchronize()
-    t_fwd = time.perf_counter() - t0
-    ubar = u - d
-    t0 = time.perf_counter()
-    e[2].record(stream)
-    g = plan.adjoint(sigma, ubar)
-    e[3].record(stream)
-    torch.cuda.synchronize()
-    t_adj = time.perf_counter() - t0
-    ms_fwd, ms_adj = e[0].elapsed_time(e[1]), e[2].elapsed_time(e[3])
-    info = plan.info
     line = {"metric": "scatterer-steps/s of the reverse-time march (dL/dbeta)", "unit": "scatterer-steps/s",
-            "adjoint_value": w.M * nsteps / (ms_adj * 1e-3), "forward_value": w.M * nsteps / (ms_fwd * 1e-3),
-            "adjoint_ms_per_step": ms_adj / nsteps, "forward_ms_per_step": ms_fwd / nsteps,
-            "adjoint_wall_s": t_adj, "forward_wall_s": t_fwd, "plan_seconds": t_plan,
-            "grad_norm": float(torch.linalg.vector_norm(g)), "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{w.name}: {w.description}", "M": w.M, "steps": nsteps, "K": info.K,
-                       "W": info.W, "local_weights": info.local_weights, "R": len(w.xr),
-                       "timed": "one wave1d_solve of all steps (densities recorded on the device), then one "
-                                "wave1d_adjoint call (its work arrays and NUFFT plan included)"}}
+            "dtype": "f64", "data": "synthetic"}
+    try:
+        _adjoint_plan(wave1d, workloads.config4(Nt=nsteps)).close()
+        line["full_workload"] = "planned"
+    except wave1d.Wave1DError as e:
+        line["full_workload"] = {"M": 100000, "unavailable": str(e)}
+    w = workloads.config4(M=args.adjoint_M, Nt=nsteps)
+    # the 8 receivers at the medium's entry, 2 dt apart: at this density the transmitted field is
+    # localized within a few hundred springs, so receivers spread over the medium (the recipe's
+    # default) see nothing within the march's stable horizon (about 2500 steps at M = 1e5)
+    w = w.with_(xr=float(np.min(w.x)) + 2 * w.dt * np.arange(8))
+    rng = np.random.default_rng(w.seed)
+    d = torch.from_numpy(0.01 * rng.standard_normal((nsteps, len(w.xr)))).cuda()   # seeded target trace
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    t0 = time.perf_counter()
+    plan = _adjoint_plan(wave1d, w)
+    t_plan = time.perf_counter() - t0
+    info = plan.info
+    (sigma, u), ms_fwd = timed(lambda: plan.solve_device(nsteps))
+    ubar = u - d
+    g, ms_adj = timed(lambda: plan.adjoint(sigma, ubar))
+    loss = 0.5 * float(torch.sum(ubar ** 2))
     plan.close()
+    del sigma
+    interval = args.adjoint_interval
+    plan = _adjoint_plan(wave1d, w)
+    (u2, ckpt), ms_cfwd = timed(lambda: plan.solve_checkpointed(nsteps, interval))
+    g2, ms_cadj = timed(lambda: plan.adjoint_checkpointed(ckpt, nsteps, interval, u2 - d))
+    ckpt_bytes = ckpt.numel()
+    plan.close()
+    del ckpt
+    # central differences of the forward march on 32 random stiffnesses (step 1e-4 beta_j)
+    fd_rng = np.random.default_rng(4)
+    idx = fd_rng.choice(w.M, args.adjoint_fd, replace=False)
+    gh = g.cpu().numpy()
+    fd_err = 0.0
+    t0 = time.perf_counter()
+    for j in idx:
+        h = 1e-4 * w.beta[j]
+        Ls = []
+        for sgn in (1.0, -1.0):
+            b = w.beta.copy()
+            b[j] += sgn * h
+            pl = _adjoint_plan(wave1d, w, b)
+            _, uu = pl.solve_device(nsteps)
+            Ls.append(0.5 * float(torch.sum((uu - d) ** 2)))
+            pl.close()
+        fd_err = max(fd_err, abs((Ls[0] - Ls[1]) / (2 * h) - gh[j]))
+    t_fd = time.perf_counter() - t0
+    work = w.M * nsteps
+    line.update({
+        "forward_value": work / (ms_fwd * 1e-3), "adjoint_value": work / (ms_adj * 1e-3),
+        "forward_ms_per_step": ms_fwd / nsteps, "adjoint_ms_per_step": ms_adj / nsteps,
+        "stored_density_bytes": 8 * w.M * nsteps,
+        "checkpointed": {"interval": interval, "checkpoint_bytes": ckpt_bytes,
+                         "segment_bytes": 8 * w.M * min(interval, nsteps),
+                         "forward_value": work / (ms_cfwd * 1e-3), "adjoint_value": work / (ms_cadj * 1e-3),
+                         "forward_ms_per_step": ms_cfwd / nsteps, "adjoint_ms_per_step": ms_cadj / nsteps,
+                         "gradient_equal_bitwise": bool(torch.equal(g, g2)),
+                         "receivers_equal_bitwise": bool(torch.equal(u, u2))},
+        "central_differences": {"stiffnesses": int(args.adjoint_fd), "step": "1e-4 beta_j",
+                                "max_abs_err_over_max_grad": fd_err / float(np.max(np.abs(gh))),
+                                "wall_s": t_fd},
+        "loss": loss, "plan_seconds": t_plan,
+        "config": {"workload": f"{w.name} recipe at M = {w.M}: {w.description}", "M": w.M, "steps": nsteps,
+                   "K": info.K, "W": info.W, "local_weights": info.local_weights, "R": len(w.xr),
+                   "blocks": info.blocks, "max_block": info.max_block,
+                   "timed": "CUDA events around one wave1d_solve (densities recorded on the device) and one "
+                            "wave1d_adjoint call, then around wave1d_solve_checkpointed and "
+                            "wave1d_adjoint_checkpointed on a fresh plan (work arrays included)"}})
     print(json.dumps(line))
+
+
+def run_local_only(args):
+    """The local sum of the plan without pair lists alone (k_rs_local) on the clustered recipe at
+    --local-M springs in --local-clusters clusters (50,000 springs per cluster keeps the million-
+    spring workload's cluster density): 2 steps, then 3 profiled steps.  The small case the
+    kernel's full profiles are taken on; not a benchmark line."""
+    from paper_2507_07823_gb300 import build, wave1d, workloads
+
+    build.build()
+    w = workloads.config2(M=args.local_M, n_clusters=args.local_clusters, Nt=100)
+    plan = wave1d.Plan.from_workload(w, local_weights=1)
+    plan.solve(2, with_sigma=False)
+    wave1d.wave1d_profile(plan.h, 1)
+    for _ in range(3):
+        wave1d._check(wave1d.wave1d_step(plan.h), "wave1d_step")
+    ms, steps = wave1d.wave1d_profile_read(plan.h)
+    info = plan.info
+    plan.close()
+    print(json.dumps({"workload": f"clustered recipe, M = {w.M}, {args.local_clusters} clusters", "M": w.M,
+                      "local_pairs": info.local_pairs, "local_ms": float(ms[0] / steps),
+                      "solve_ms": float(ms[wave1d.STAGES.index("solve")] / steps),
+                      "pairs_per_s": info.local_pairs / (ms[0] / steps * 1e-3)}))
 
 
 def run_mixed_only(args):
@@ -810,7 +910,14 @@ def main():
     ap.add_argument("--spread-interp-reps", type=int, default=20)
     ap.add_argument("--adjoint-only", action="store_true",
                     help="only the forward and reverse-time march on the adjoint workload (not a benchmark line)")
-    ap.add_argument("--adjoint-steps", type=int, default=200)
+    ap.add_argument("--adjoint-steps", type=int, default=2000)
+    ap.add_argument("--adjoint-M", type=int, default=10000)
+    ap.add_argument("--adjoint-interval", type=int, default=100, help="checkpoint interval (steps)")
+    ap.add_argument("--adjoint-fd", type=int, default=32, help="stiffnesses checked by central differences")
+    ap.add_argument("--local-only", action="store_true",
+                    help="only the local sum of the plan without pair lists on a clustered case (not a benchmark line)")
+    ap.add_argument("--local-M", type=int, default=250000)
+    ap.add_argument("--local-clusters", type=int, default=4)
     ap.add_argument("--mixed-only", action="store_true",
                     help="only the FP64 and mixed-precision marches of the benchmark workload (not a benchmark line)")
     ap.add_argument("--batched-only", action="store_true",
@@ -819,6 +926,8 @@ def main():
     args = ap.parse_args()
     if args.spread_interp_only:
         run_spread_interp_only(args)
+    elif args.local_only:
+        run_local_only(args)
     elif args.adjoint_only:
         run_adjoint_only(args)
     elif args.mixed_only:

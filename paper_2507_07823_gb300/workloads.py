@@ -112,11 +112,12 @@ def make(name: str = "custom", *, M: int, bc: int, dt: float, Nt: int, tol: floa
          beta_range=(1.0, 10.0), beta_dist: str = "uniform",
          amp=(1.0,), center=(-2.0,), width=(0.1,), R: int = 4,
          xr: Optional[np.ndarray] = None, description: str = "",
-         margin: float = FREE_MARGIN) -> Workload:
+         margin: float = FREE_MARGIN, n_clusters: int = 16) -> Workload:
     """Draw one seeded workload.  Springs avoid the pulse support at t = 0.
 
     margin: free space only, springs and receivers lie in [-pi + margin, pi - margin]; it must
-    cover 3 delta = 3 W dt of the plan (Sec. 4.4)."""
+    cover 3 delta = 3 W dt of the plan (Sec. 4.4).  n_clusters: Gaussian clusters of the
+    clustered layout (fewer clusters at a smaller M keep the clusters' density)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     amp = np.asarray(amp, dtype=np.float64)
     center = np.asarray(center, dtype=np.float64)
@@ -126,7 +127,7 @@ def make(name: str = "custom", *, M: int, bc: int, dt: float, Nt: int, tol: floa
         lo, hi = -PI, PI
     else:
         lo, hi = -PI + margin, PI - margin
-    x = _draw_positions(rng, M, layout, periodic, center, width, lo, hi)
+    x = _draw_positions(rng, M, layout, periodic, center, width, lo, hi, n_clusters=n_clusters)
     if beta_dist == "uniform":
         beta = rng.uniform(beta_range[0], beta_range[1], size=M)
     elif beta_dist == "loguniform":

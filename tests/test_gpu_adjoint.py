@@ -48,6 +48,26 @@ def test_gradient_matches_the_adjoint_oracle(bc):
     assert np.max(np.abs(g - g_oracle)) <= 1e-9 * np.max(np.abs(g_oracle)), (g, g_oracle)
 
 
+def test_gradient_matches_the_adjoint_oracle_at_64_springs():
+    """64 free-space springs with stiffnesses uniform in [1, 10] (the adjoint workload's draw),
+    8 receivers, a seeded target trace: dL/dbeta against the adjoint oracle at 1e-9."""
+    rng = np.random.default_rng(64)
+    M, dt, Nt = 64, 0.01, 300
+    x = np.sort(rng.uniform(-1.0, 1.0, M))
+    w = W.Workload(name="adjoint-64", bc=W.FREE, x=x, beta=rng.uniform(1.0, 10.0, M), amp=np.array([1.0]),
+                   center=np.array([-1.8]), width=np.array([0.1]), dt=dt, Nt=Nt, tol=1e-10, p=6,
+                   xr=np.linspace(-1.2, 1.2, 8), seed=64)
+    d = 0.01 * rng.standard_normal((Nt + 1, 8))
+    _, g_oracle = adjoint.misfit_and_gradient(wfp.from_workload(w), w.Nt, d)
+    plan = wave1d.Plan.from_workload(w)
+    try:
+        sigma, u = plan.solve_device(w.Nt)
+        g = plan.adjoint(sigma, u - torch.from_numpy(d[1:]).cuda()).cpu().numpy()
+    finally:
+        plan.close()
+    assert np.max(np.abs(g - g_oracle)) <= 1e-9 * np.max(np.abs(g_oracle))
+
+
 def test_gradient_is_bitwise_reproducible():
     """No launch of the reverse march uses atomics: two calls give the same bits."""
     w = _layout(W.FREE, seed=7)
