@@ -367,13 +367,27 @@ __global__ void __launch_bounds__(256) k_rs_jacobi(DevPlan P, RangeDev R, int it
     for (int64_t j = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < P.M; j += nw) {
         const int lo = __ldg(R.nb_lo + j), cnt = __ldg(R.nb_cnt + j);
         const int64_t off = __ldg(R.nb_off + j);
-        float ah = 0.f, al = 0.f;
-        for (int k = lane; k < cnt; k += 32) {
+        // four entries per lane in flight (their weight and iterate loads issued together), two
+        // accumulators; the row's entries are streamed once per sweep
+        float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f;
+        int k = lane;
+        for (; k + 96 < cnt; k += 128) {
+            float2 w[4], sv[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) w[u] = __ldcs((const float2*)R.nb_w + off + k + 32 * u);
+#pragma unroll
+            for (int u = 0; u < 4; u++) sv[u] = __ldcg((const float2*)src2 + rs_spring((int64_t)lo + k + 32 * u, P.M));
+            rs::acc_mac(ah, al, w[0].x, w[0].y, sv[0].x, sv[0].y);
+            rs::acc_mac(bh, bl, w[1].x, w[1].y, sv[1].x, sv[1].y);
+            rs::acc_mac(ah, al, w[2].x, w[2].y, sv[2].x, sv[2].y);
+            rs::acc_mac(bh, bl, w[3].x, w[3].y, sv[3].x, sv[3].y);
+        }
+        for (; k < cnt; k += 32) {
             const float2 w = __ldcs((const float2*)R.nb_w + off + k);
-            const int64_t l = rs_spring((int64_t)lo + k, P.M);
-            const float2 s = __ldcg((const float2*)src2 + l);
+            const float2 s = __ldcg((const float2*)src2 + rs_spring((int64_t)lo + k, P.M));
             rs::acc_mac(ah, al, w.x, w.y, s.x, s.y);
         }
+        rs::acc_add(ah, al, bh, bl);
         for (int o = 16; o > 0; o >>= 1) {
             const float oh = __shfl_xor_sync(0xffffffffu, ah, o), ol = __shfl_xor_sync(0xffffffffu, al, o);
             rs::acc_add(ah, al, oh, ol);
