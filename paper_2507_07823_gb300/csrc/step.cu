@@ -223,8 +223,10 @@ __global__ void __launch_bounds__(kStepThreads, 4) k_step(DevPlan P) {
     // grid barrier: every item partial and right-hand side of the step is stored
     finish(c + kGrid);
     if (!wait_for(P, c + kGrid, (unsigned)G)) return;
+    // solve tasks interleaved over the blocks (task t on block t mod G), so the few hundred
+    // tasks' FP64 work spreads over every SM instead of queueing on the first blocks' FP64 units
     const int nw = blockDim.x >> 5;
-    solve_tasks(P, n, (int64_t)b * nw + (threadIdx.x >> 5), (int64_t)G * nw,
+    solve_tasks(P, n, (int64_t)(threadIdx.x >> 5) * G + b, (int64_t)G * nw,
                  (double*)smraw + (threadIdx.x >> 5) * kSolveStage);
     // the block that finishes last (every other block has stored its densities and is past every
     // wait) resets the counters, reads out the receivers and advances the step counter
