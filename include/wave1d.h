@@ -378,7 +378,11 @@ int wave1d_nufft1_noalloc(const double* x, const double* c, int64_t M, int K, do
  * advance together.  One step of all instances is one pass of launches: the local sum (Sec. 4.1)
  * and the block solve (eq. linearSystem) over the instances' joined tables, and each instance's
  * history part (Sec. 3) with the spreading and interpolation of all instances in one launch each
- * (the batched NUFFT plan above).  The step is captured once in a CUDA graph and replayed.
+ * (the batched NUFFT plan above).  With opts.step_kernel = 1 (the default), where the device
+ * launches cooperative grids and the kernel width is 7 .. 14 (tol 1e-6 .. 1e-13), the whole step
+ * of every instance is one persistent cooperative launch instead (the same unit bodies in the same
+ * order, so the same bits); its waits between blocks are bounded by opts.spin_limit and latch
+ * WAVE1D_ETIMEOUT.  Either way the step is captured once in a CUDA graph and replayed.
  *   offsets : host, n_inst + 1 values, offsets[0] = 0; instance i holds springs
  *             [offsets[i], offsets[i+1]) of x and beta (host, positions wrapped into [-pi, pi)),
  *             at least one spring each.
@@ -404,6 +408,9 @@ int wave1d_batch_solve(wave1d_batch_t plan, int64_t nsteps, double* u_rec, doubl
                        int out_on_device);
 int wave1d_batch_destroy(wave1d_batch_t plan);
 const char* wave1d_batch_strerror(void);
+/* 1 if the plan's steps run as one persistent launch (see wave1d_batch_plan), 0 if as one launch
+ * per pass, WAVE1D_EINVAL for a NULL plan. */
+int wave1d_batch_step_kernel(wave1d_batch_t plan);
 
 /* Free the plan and its device memory (synchronises).  NULL is accepted. */
 int wave1d_destroy(wave1d_plan_t plan);

@@ -21,6 +21,8 @@
 
 #include "batch_host.h"
 #include "internal.h"
+#include "grid_sync.cuh"
+#include "nufft_units.cuh"
 #include "phases.cuh"
 #include "../../include/wave1d.h"
 
@@ -30,21 +32,25 @@ __global__ void k_solve(DevPlan P);
 __global__ void k_mx_gather(DevPlan P, const int64_t* perm, double* c);
 __global__ void k_mx_receivers(int64_t R, const int64_t* perm, const double* u, double* uHr);
 
-// forward FFT column pass of every instance's fine grid (blockIdx.y = instance): for column i2,
-// FFT over i1 of z[i2 + L2 i1] (sign +), times e^{+2 pi i i2 k1 / L}  ->  Y[k1 L2 + i2]
-__global__ void k_bfft_cols(const double2* __restrict__ grids, double2* __restrict__ Ys,
-                            const double2* __restrict__ tw, int L, int L1, int L2, int logL1) {
-    extern __shared__ double2 sm[];
+// forward FFT column pass of one instance's fine grid: for column i2, FFT over i1 of
+// z[i2 + L2 i1] (sign +), times e^{+2 pi i i2 k1 / L}  ->  Y[k1 L2 + i2]; sm: L1 + L1/2 points
+__device__ __forceinline__ void bfft_col(const double2* __restrict__ in, double2* __restrict__ out,
+                                         const double2* __restrict__ tw, int L, int L1, int L2, int logL1, int i2,
+                                         double2* sm) {
     double2* twN = sm + L1;
-    const int i2 = blockIdx.x;
-    const double2* in = grids + (int64_t)blockIdx.y * L;
-    double2* out = Ys + (int64_t)blockIdx.y * L;
     for (int j = threadIdx.x; j < L1 / 2; j += blockDim.x) twN[j] = tw[j * (L / L1)];
     for (int i1 = threadIdx.x; i1 < L1; i1 += blockDim.x) sm[__brev(i1) >> (32 - logL1)] = in[i2 + (int64_t)L2 * i1];
     __syncthreads();
     fft_lines(sm, nullptr, twN, L1, logL1);
     for (int k1 = threadIdx.x; k1 < L1; k1 += blockDim.x)
         out[(int64_t)k1 * L2 + i2] = cmul(sm[k1], tw[((int64_t)i2 * k1) & (L - 1)]);
+}
+
+// the column pass of every instance's fine grid (blockIdx.y = instance)
+__global__ void k_bfft_cols(const double2* __restrict__ grids, double2* __restrict__ Ys,
+                            const double2* __restrict__ tw, int L, int L1, int L2, int logL1) {
+    extern __shared__ double2 sm[];
+    bfft_col(grids + (int64_t)blockIdx.y * L, Ys + (int64_t)blockIdx.y * L, tw, L, L1, L2, logL1, blockIdx.x, sm);
 }
 
 // FIR tails, rows (FFT + mode update + first inverse pass) and inverse columns of every
@@ -70,27 +76,167 @@ __global__ void k_bhist_icols(const DevPlan* __restrict__ views) {
 // u_H at spring perm[i] and the right-hand side rhs_j = -g_j(t_{n+1}) - beta_j u_H(x_j) with the
 // incident wave of the spring's instance: g_j = beta_j f_b(x_j - t), f_b one Gaussian periodised
 // over 2 pi (eq. gj; the same sum, with the same 12-width cut, as the one-plan forcing)
-__global__ void k_b_rhs(DevPlan P, const int64_t* __restrict__ perm, const double* __restrict__ u,
-                        const int32_t* __restrict__ inst_of, const double* __restrict__ pulse) {
-    const int64_t n = load_step(P);
+__device__ __forceinline__ void b_rhs_point(const DevPlan& P, int64_t n, int64_t i, const int64_t* __restrict__ perm,
+                                            const double* __restrict__ u, const int32_t* __restrict__ inst_of,
+                                            const double* __restrict__ pulse) {
     const double kTwoPi = 6.283185307179586476925286766559;
     const double kInvTwoPi = 0.15915494309189533576888376337251;
     const double t = (double)(n + 1) * P.dt;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.M; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = perm[i];
-        const double* pl = pulse + 3 * (int64_t)inst_of[j];
-        const double amp = pl[0], cen = pl[1], iw = pl[2];
-        const double s = P.x[j] - t, span = 12.0 / iw;
-        const int64_t m0 = (int64_t)floor((cen - s - span) * kInvTwoPi);
-        const int64_t m1 = (int64_t)ceil((cen - s + span) * kInvTwoPi);
-        double f = 0.0;
-        for (int64_t m = m0; m <= m1; m++) {
-            const double z = (s + kTwoPi * (double)m - cen) * iw;
-            if (fabs(z) <= 12.0) f += amp * exp(-0.5 * z * z);
+    const int64_t j = perm[i];
+    const double* pl = pulse + 3 * (int64_t)inst_of[j];
+    const double amp = pl[0], cen = pl[1], iw = pl[2];
+    const double s = P.x[j] - t, span = 12.0 / iw;
+    const int64_t m0 = (int64_t)floor((cen - s - span) * kInvTwoPi);
+    const int64_t m1 = (int64_t)ceil((cen - s + span) * kInvTwoPi);
+    double f = 0.0;
+    for (int64_t m = m0; m <= m1; m++) {
+        const double z = (s + kTwoPi * (double)m - cen) * iw;
+        if (fabs(z) <= 12.0) f += amp * exp(-0.5 * z * z);
+    }
+    const double uh = u[i], bj = P.beta[j];
+    P.uH[j] = uh;
+    P.rhs[j] = -bj * f - bj * uh;
+}
+
+__global__ void k_b_rhs(DevPlan P, const int64_t* __restrict__ perm, const double* __restrict__ u,
+                        const int32_t* __restrict__ inst_of, const double* __restrict__ pulse) {
+    const int64_t n = load_step(P);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.M; i += (int64_t)gridDim.x * blockDim.x)
+        b_rhs_point(P, n, i, perm, u, inst_of, pulse);
+}
+
+// ---------------------------------------------------------------------------------------------
+// The batched step as one cooperative launch (all blocks resident), the persistent form of the
+// per-pass launches of enqueue_batch_step with the same unit bodies and sums, so both give the
+// same bits:
+//   blocks [0, H)   the history chain of every instance: FP64 spreading (one NUFFT range per
+//                   unit), FFT columns (instance, column), row pairs (instance, row pair: FFT,
+//                   mode update, first inverse pass), inverse columns, then interpolation tiles
+//                   of the springs (each followed by their right-hand sides) and of the receivers;
+//                   each phase waits for the one before; then local-sum items
+//   blocks [H, G)   the prologue (sigma^n gathered into the NUFFT's point order, the FIR tails of
+//                   every instance's modes: both read only earlier steps), then local-sum items
+//   all blocks      grid barrier; block solve; the block that finishes last resets the counters,
+//                   reads out the receivers and advances the step counter
+// Every wait is bounded (DevPlan.spin_limit): one that runs out latches WAVE1D_ETIMEOUT.
+// ---------------------------------------------------------------------------------------------
+enum : int { kBGather = 0, kBTail, kBSpread, kBCol, kBRow, kBIcol, kBGrid, kBNumCounters };
+constexpr int kBStepThreads = 256;
+
+struct BatchStep {
+    DevPlan g;                  // joined view (local sum, solve, receivers), sig_hist set per graph
+    const DevPlan* views;       // per instance (history phases)
+    int B, H;                   // instances, history blocks
+    NuDev64 ns, nr;             // NUFFT of the springs and of the receivers (nr.M = 0: none)
+    const int64_t *perm_s, *perm_r;
+    const int32_t* inst_of;
+    const double* pulse;
+    double *c, *u, *ur;
+    unsigned* bar;              // kBNumCounters counters, zero between steps
+};
+
+template <int W>
+__global__ void __launch_bounds__(kBStepThreads, 4) k_batch_step(BatchStep A) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ bool last;
+    const DevPlan& P = A.g;
+    const int64_t n = load_step(P);
+    const int G = gridDim.x, b = blockIdx.x, H = A.H;
+    unsigned* c = A.bar;
+    const int L = P.L, L1 = P.L1, L2 = P.L2, nrows = P.L1 / 2 + 1, K1 = P.K + 1;
+    const int64_t ngather = (A.ns.M + kBStepThreads - 1) / kBStepThreads;
+    const int ntail = (K1 + kTailModes - 1) / kTailModes;
+    if (b < H) {
+        const DevPlan* V = A.views;
+        // spreading of sigma^n (gathered by the prologue) onto every instance's fine grid
+        if (!wait_for(P, c + kBGather, (unsigned)ngather)) return;
+        for (int64_t t = b; t < A.ns.nunits; t += H) {
+            spread64_unit<W>(A.ns.ranges[t], A.ns.runs, A.c, A.ns.ker, (double*)V[0].grid,
+                             (double(*)[W])smraw, (int*)(smraw + (size_t)(kRangeCells64 + 16) * W * sizeof(double)));
+            finish(c + kBSpread);
         }
-        const double uh = u[i], bj = P.beta[j];
-        P.uH[j] = uh;
-        P.rhs[j] = -bj * f - bj * uh;
+        if (!wait_for(P, c + kBSpread, (unsigned)A.ns.nunits)) return;
+        const int logL1 = 31 - __clz(L1);
+        for (int64_t t = b; t < (int64_t)A.B * L2; t += H) {
+            const int ib = (int)(t / L2), i2 = (int)(t % L2);
+            __syncthreads();
+            bfft_col((const double2*)V[ib].grid, (double2*)V[ib].work, (const double2*)P.twiddle, L, L1, L2, logL1, i2,
+                     (double2*)smraw);
+            finish(c + kBCol);
+        }
+        if (!wait_for2(P, c + kBCol, (unsigned)(A.B * L2), c + kBTail, (unsigned)(A.B * ntail))) return;
+        for (int64_t t = b; t < (int64_t)A.B * nrows; t += H) {
+            const int ib = (int)(t / nrows), k1 = (int)(t % nrows);
+            __syncthreads();
+            rows_phase(V[ib], n, (const double2*)V[ib].work, (double2*)V[ib].spec, k1, 1, smraw);
+            finish(c + kBRow);
+        }
+        if (!wait_for(P, c + kBRow, (unsigned)(A.B * nrows))) return;
+        for (int64_t t = b; t < (int64_t)A.B * L2; t += H) {
+            const int ib = (int)(t / L2), i2 = (int)(t % L2);
+            __syncthreads();
+            icols_phase(V[ib], (const double2*)V[ib].spec, i2, smraw);
+            finish(c + kBIcol);
+        }
+        if (!wait_for(P, c + kBIcol, (unsigned)(A.B * L2))) return;
+        // interpolation tiles: the springs' (then their right-hand sides, point by point in the
+        // thread that interpolated it) and the receivers' (then their u_H)
+        const int64_t ts = (A.ns.M + kInterpTile - 1) / kInterpTile, tr = (A.nr.M + kInterpTile - 1) / kInterpTile;
+        for (int64_t t = b; t < ts + tr; t += H) {
+            if (t < ts) {
+                interp64_unit(t, (const double*)V[0].grid, A.u, A.ns.i0, A.ns.ker, A.ns.M, A.ns.w, A.ns.nf,
+                              (double*)smraw);
+                const int64_t i = t * kInterpTile + threadIdx.x;
+                if (threadIdx.x < kInterpTile && i < A.ns.M) b_rhs_point(P, n, i, A.perm_s, A.u, A.inst_of, A.pulse);
+            } else {
+                const int64_t tt = t - ts;
+                interp64_unit(tt, (const double*)V[0].grid, A.ur, A.nr.i0, A.nr.ker, A.nr.M, A.nr.w, A.nr.nf,
+                              (double*)smraw);
+                const int64_t i = tt * kInterpTile + threadIdx.x;
+                if (threadIdx.x < kInterpTile && i < A.nr.M) P.uHr[A.perm_r[i]] = A.ur[i];
+            }
+        }
+    } else {
+        // prologue on blocks H .. G - 1 (rank r of nl): gather chunks, then FIR-tail units
+        const int r = b - H, nl = G - H;
+        const double* sg = P.sig + (int64_t)ring_slot(n, P.ring) * P.M;
+        for (int64_t t = r; t < ngather; t += nl) {
+            const int64_t i = t * kBStepThreads + threadIdx.x;
+            if (i < A.ns.M) A.c[i] = sg[A.perm_s[i]];
+            finish(c + kBGather);
+        }
+        for (int64_t t = r; t < (int64_t)A.B * ntail; t += nl) {
+            const int ib = (int)(t / ntail), ch = (int)(t % ntail);
+            const int k = ch * kTailModes + (int)(threadIdx.x >> 3);
+            fir_tail(A.views[ib], n, k, k <= P.K);
+            finish(c + kBTail);
+        }
+    }
+    local_items_loop(P, n);
+    // grid barrier: every item partial and right-hand side of the step is stored
+    finish(c + kBGrid);
+    if (!wait_for(P, c + kBGrid, (unsigned)G)) return;
+    const int nw = blockDim.x >> 5;
+    solve_tasks(P, n, (int64_t)(threadIdx.x >> 5) * G + b, (int64_t)G * nw, (double*)smraw + (threadIdx.x >> 5) * kSolveStage);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long done = atomicAdd((unsigned long long*)&P.step[1], 1ull);
+        last = (done == (unsigned long long)G - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kBNumCounters; i++) c[i] = 0u;
+        *P.item_ctr = 0ull;
+    }
+    receivers_readout(P, n);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        P.step[1] = 0;
+        __threadfence();
+        P.step[0] = n + 1;
     }
 }
 
@@ -129,6 +275,14 @@ struct wave1d_batch_s {
     double *pulse = nullptr, *c = nullptr, *u = nullptr, *ur = nullptr, *grids = nullptr, *work = nullptr,
            *sig_hist = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};   // one step without / with the density history
+    // the one-launch step (k_batch_step): used when the kernel width has an instance and the
+    // device launches cooperative grids (opts.step_kernel)
+    bool persist = false;
+    int W = 0, H = 0;
+    unsigned pgrid = 0;
+    size_t psmem = 0;
+    unsigned* bar = nullptr;
+    NuDev64 ns{}, nr{};
 };
 
 namespace {
@@ -289,8 +443,103 @@ int upload_views(wave1d_batch_t p) {
     return bupload(p, views, &p->d_views);
 }
 
+// kernel widths the one-launch batched step is built for (tol 1e-6 .. 1e-13); others take the
+// per-pass launches
+constexpr int kBStepWMin = 7, kBStepWMax = 14;
+
+template <int W>
+const void* batch_step_fn() {
+    return (const void*)k_batch_step<W>;
+}
+
+const void* batch_step_kernel(int w) {
+    switch (w) {
+        case 7: return batch_step_fn<7>();
+        case 8: return batch_step_fn<8>();
+        case 9: return batch_step_fn<9>();
+        case 10: return batch_step_fn<10>();
+        case 11: return batch_step_fn<11>();
+        case 12: return batch_step_fn<12>();
+        case 13: return batch_step_fn<13>();
+        case 14: return batch_step_fn<14>();
+        default: return nullptr;
+    }
+}
+
+// size the one-launch step: shared memory of its largest unit, as many blocks as are resident, the
+// history group one block per unit of its widest phase, at most half the blocks
+int setup_batch_step(wave1d_batch_t p, const wave1d_opts& o) {
+    const Params& P = p->bt.g.P;
+    p->persist = false;
+    if (!o.step_kernel) return WAVE1D_OK;
+    if (nufft_dev64(p->nu_s, p->ns) != WAVE1D_OK) return WAVE1D_OK;
+    if (P.R > 0 && nufft_dev64(p->nu_r, p->nr) != WAVE1D_OK) return WAVE1D_OK;
+    if (P.R == 0) p->nr = NuDev64{nullptr, nullptr, 0, nullptr, nullptr, 0, p->ns.w, p->ns.nf};
+    const int w = p->ns.w;
+    const void* fn = batch_step_kernel(w);
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, p->device);
+    if (!fn || !coop) return WAVE1D_OK;
+    const size_t spread = (size_t)(kRangeCells64 + 16) * w * sizeof(double) + (size_t)(kSpread64Runs + 1) * sizeof(int);
+    const size_t sm = std::max({spread, kInterp64Smem, fft_smem_bytes(P.L1), rows_phase_smem(P.L2),
+                                icols_phase_smem(P.L1), (size_t)kSolveStage * sizeof(double) * (kBStepThreads / 32)});
+    int occ = 0;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kBStepThreads, sm) != cudaSuccess)
+        return bfail(WAVE1D_ECUDA, "cannot configure the batched step kernel");
+    if (occ < 1) return WAVE1D_OK;
+    const int64_t grid = (int64_t)occ * p->sms;
+    const int64_t B = p->B, nrows = P.L1 / 2 + 1;
+    const int64_t tiles = (p->ns.M + kInterpTile - 1) / kInterpTile + (p->nr.M + kInterpTile - 1) / kInterpTile;
+    const int64_t units = std::max({p->ns.nunits, B * P.L2, B * nrows, tiles});
+    if (grid < 2) return WAVE1D_OK;
+    int rc = balloc(p, &p->bar, (size_t)kBNumCounters);
+    if (rc) return rc;
+    if (cudaMemsetAsync(p->bar, 0, kBNumCounters * sizeof(unsigned), p->s) != cudaSuccess)
+        return bfail(WAVE1D_ECUDA, "counter initialisation");
+    p->W = w;
+    p->pgrid = (unsigned)grid;
+    p->psmem = sm;
+    p->H = (int)std::max<int64_t>(1, std::min<int64_t>(units, grid / 2));
+    p->persist = true;
+    return WAVE1D_OK;
+}
+
+int launch_batch_step(wave1d_batch_t p, double* sig_hist) {
+    BatchStep a;
+    a.g = p->g;
+    a.g.sig_hist = sig_hist;
+    a.views = p->d_views;
+    a.B = p->B;
+    a.H = p->H;
+    a.ns = p->ns;
+    a.nr = p->nr;
+    a.perm_s = p->perm_s;
+    a.perm_r = p->perm_r;
+    a.inst_of = p->inst_of;
+    a.pulse = p->pulse;
+    a.c = p->c;
+    a.u = p->u;
+    a.ur = p->ur;
+    a.bar = p->bar;
+    void* args[] = {&a};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(p->pgrid);
+    cfg.blockDim = dim3(kBStepThreads);
+    cfg.dynamicSmemBytes = p->psmem;
+    cfg.stream = p->s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    BCK(cudaLaunchKernelExC(&cfg, batch_step_kernel(p->W), args));
+    return WAVE1D_OK;
+}
+
 // queue one step of every instance
 int enqueue_batch_step(wave1d_batch_t p, double* sig_hist) {
+    if (p->persist) return launch_batch_step(p, sig_hist);
     const Params& P = p->bt.g.P;
     DevPlan d = p->g;
     d.sig_hist = sig_hist;
@@ -423,6 +672,8 @@ int wave1d_batch_plan(int n_inst, const int64_t* offsets, const double* x, const
         cudaFuncSetAttribute(k_bhist_icols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)icols_phase_smem(P.L1)) !=
             cudaSuccess)
         return cleanup(bfail(WAVE1D_ECUDA, "cannot size the shared memory of the history passes"));
+    p->g.spin_limit = o.spin_limit > 0 ? (unsigned)o.spin_limit : (1u << 22);
+    if ((rc = setup_batch_step(p, o))) return cleanup(rc);
     if (cudaStreamSynchronize(p->s) != cudaSuccess) return cleanup(bfail(WAVE1D_ECUDA, "plan upload failed"));
     // the device holds the joined weights now: release the host copies
     std::vector<float>().swap(p->bt.g.litems.w);
@@ -480,6 +731,8 @@ int wave1d_batch_solve(wave1d_batch_t p, int64_t nsteps, double* u_rec, double* 
     if (st != 0) return bfail(st, "a density became non-finite during the march");
     return WAVE1D_OK;
 }
+
+int wave1d_batch_step_kernel(wave1d_batch_t p) { return p ? (p->persist ? 1 : 0) : WAVE1D_EINVAL; }
 
 int wave1d_batch_destroy(wave1d_batch_t p) {
     if (!p) return WAVE1D_OK;

@@ -32,6 +32,7 @@
 
 #include "internal.h"
 #include "nufft_host.h"
+#include "nufft_units.cuh"
 #include "device_common.cuh"
 #include "../../include/wave1d.h"
 
@@ -135,7 +136,6 @@ __device__ __forceinline__ void nu_taps(const NuPoly& P, const NuCheb<D>& ch, fl
 // does not depend on scheduling, and a dense cluster (hundreds of points per cell) spreads over
 // many ranges and lanes.
 // ---------------------------------------------------------------------------------------------
-constexpr int kUnitThreads = 256;
 
 // Mixed precision by Chebyshev moments.  With psi_t(y) = sum_d a[t][d] T_d(y),
 //   G[g] = sum_t sum_{q: i0_q = g - t} c_q psi_t(y_q) = sum_t sum_d a[t][d] M_d(g - t),
@@ -157,7 +157,6 @@ constexpr int kUnitThreads = 256;
 constexpr int kStage = 2048;        // staging capacity (points) of a range
 constexpr int kRangePoints = 2048;  // points a range is cut at, halo included (one cell may exceed it)
 constexpr int kRangeCells = 240;    // cells of a mixed range (w - 1 halo cells more fit one thread each)
-constexpr int kRangeCells64 = 128;  // cells of an FP64 range (its w tap sums per cell live in shared memory)
 constexpr int kRangePoints64 = 4096;  // FP64: its halo costs FP64 FMAs, so fewer, larger ranges
 constexpr int kEmptyCells = 8192;   // cells of a range no point reaches (zeros only)
 template <int W, int D>
@@ -254,68 +253,17 @@ __global__ void __launch_bounds__(kUnitThreads) k_nu_spread_mixed(const NuRange*
     }
 }
 
-// FP64 spreading on the same cell ranges: each cell's lanes accumulate the w tap sums
-// S_t(f) = sum_{q: i0_q = f} ker_q[t] c_q (one FMA per point and tap, the stored weights and the
-// densities read from global memory four points at a time), a fixed shuffle tree closes each
-// group, and grid real c0 + l = sum_t S_t(c0 + l - t).  Like the mixed pass, no block depends on
-// another.
+// FP64 spreading on the same cell ranges, one block per range (spread64_unit, nufft_units.cuh).
+// Like the mixed pass, no block depends on another.
 template <int W>
 __global__ void __launch_bounds__(kUnitThreads) k_nu_spread64(const NuRange* __restrict__ ranges,
                                                               const int32_t* __restrict__ runs,
                                                               const double* __restrict__ c,
                                                               const double* __restrict__ ker,
                                                               double* __restrict__ grid) {
-    __shared__ int rp[kRangeCells64 + 16 + 1];
+    __shared__ int rp[kSpread64Runs];
     __shared__ double seg[kRangeCells64 + 16][W];
-    const NuRange u = ranges[blockIdx.x];
-    const int nr = u.nc + W - 1, np = u.na + u.nb;
-    if (np == 0) {
-        for (int l = threadIdx.x; l < u.nc; l += kUnitThreads) grid[u.c0 + l] = 0.0;
-        return;
-    }
-    if ((int)threadIdx.x <= nr) rp[threadIdx.x] = __ldg(runs + u.roff + threadIdx.x);
-    __syncthreads();
-    const int G = 1 << u.lg, f = (int)threadIdx.x >> u.lg, gl = (int)threadIdx.x & (G - 1);
-    double acc[W];
-#pragma unroll
-    for (int t = 0; t < W; t++) acc[t] = 0.0;
-    if (f < nr) {
-        const int q1 = rp[f + 1];
-        constexpr int B = 4;
-        for (int q = rp[f] + gl; q < q1; q += B * G) {
-            double cb[B], kb[B][W];
-#pragma unroll
-            for (int i = 0; i < B; i++) {
-                const int qi = q + i * G < q1 ? q + i * G : q;
-                const int64_t j = qi < u.na ? u.a0 + qi : u.b0 + (qi - u.na);
-                cb[i] = q + i * G < q1 ? __ldcs(c + j) : 0.0;
-#pragma unroll
-                for (int t = 0; t < W; t++) kb[i][t] = __ldcs(ker + j * W + t);
-            }
-#pragma unroll
-            for (int i = 0; i < B; i++)
-#pragma unroll
-                for (int t = 0; t < W; t++) acc[t] = fma(kb[i][t], cb[i], acc[t]);
-        }
-    }
-    for (int o = G >> 1; o > 0; o >>= 1) {
-#pragma unroll
-        for (int t = 0; t < W; t++) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
-    }
-    if (gl == 0 && f < nr) {
-#pragma unroll
-        for (int t = 0; t < W; t++) seg[f][t] = acc[t];
-    }
-    __syncthreads();
-    if ((int)threadIdx.x < u.nc) {
-        const int l = threadIdx.x;
-        double a = 0.0;
-        if (rp[l + W] != rp[l]) {                     // else none of the w cells feeding it holds a point
-#pragma unroll
-            for (int t = 0; t < W; t++) a += seg[l + W - 1 - t][t];
-        }
-        grid[u.c0 + l] = a;
-    }
+    spread64_unit<W>(ranges[blockIdx.x], runs, c, ker, grid, seg, rp);
 }
 
 // type-1 post-processing: S_k from the half-length FFT Z (E, O split) with the deconvolution
@@ -352,33 +300,13 @@ __global__ void k_nu_pre2(const double* __restrict__ alpha, double2* __restrict_
     }
 }
 
-// FP64 interpolation: u_j = sum_t G[(i0_j + t) mod nf] ker[j][t] (i0_j: instance x nf + cell).  A block takes 256 consecutive
-// points; their weights (one contiguous run of 256 w doubles) are staged through shared memory
-// with coalesced streaming loads, and all w grid loads of a point are issued before any is used.
-constexpr int kInterpTile = 256;
+// FP64 interpolation, tiles of kInterpTile consecutive points (interp64_unit, nufft_units.cuh).
 __global__ void __launch_bounds__(kInterpTile) k_nu_interp64(const double* __restrict__ grid, double* __restrict__ u,
                                                              const int32_t* __restrict__ i0,
                                                              const double* __restrict__ ker, int64_t M, int w, int nf) {
     __shared__ double ks[kInterpTile * 16];
-    for (int64_t base = (int64_t)blockIdx.x * kInterpTile; base < M; base += (int64_t)gridDim.x * kInterpTile) {
-        const int np = (int)(M - base < kInterpTile ? M - base : kInterpTile);
-        __syncthreads();
-        const double* kr = ker + base * w;
-        for (int e = threadIdx.x; e < np * w; e += kInterpTile) ks[e] = __ldcs(kr + e);
-        __syncthreads();
-        if (threadIdx.x < np) {
-            const int64_t j = base + threadIdx.x;
-            const int a = __ldg(i0 + j), base = a & ~(nf - 1);   // instance x nf + cell
-            double g[16];
-#pragma unroll
-            for (int t = 0; t < 16; t++) g[t] = t < w ? __ldg(grid + (base | ((a + t) & (nf - 1)))) : 0.0;
-            double acc = 0.0;
-#pragma unroll
-            for (int t = 0; t < 16; t++)
-                if (t < w) acc = fma(g[t], ks[threadIdx.x * w + t], acc);
-            u[j] = acc;
-        }
-    }
+    const int64_t tiles = (M + kInterpTile - 1) / kInterpTile;
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) interp64_unit(t, grid, u, i0, ker, M, w, nf, ks);
 }
 
 // mixed interpolation (A6).  With psi_t(y) = sum_d a[t][d] T_d(y),
@@ -555,6 +483,21 @@ int nu_alloc(wave1d_nufft_t h, size_t count, T** out) {
 }
 
 }  // namespace
+
+namespace wave1d {
+int nufft_dev64(wave1d_nufft_t h, NuDev64& out) {
+    if (!h || h->precision != 0) return WAVE1D_EINVAL;
+    out.ranges = h->ranges;
+    out.runs = h->runs;
+    out.nunits = h->nunits;
+    out.ker = h->ker;
+    out.i0 = h->first;
+    out.M = h->M;
+    out.w = h->P.nufft_w;
+    out.nf = h->P.nf;
+    return WAVE1D_OK;
+}
+}  // namespace wave1d
 
 extern "C" {
 

@@ -27,6 +27,7 @@
 #include <cstdint>
 
 #include "internal.h"
+#include "grid_sync.cuh"
 #include "phases.cuh"
 #include "../../include/wave1d.h"
 
@@ -35,77 +36,6 @@ namespace wave1d {
 
 // counters in P.bar (all zero between steps)
 enum : int { kColDone = 0, kRowDone, kIcolDone, kTailDone, kForceDone, kGrid, kNumCounters };
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// thread 0 waits until *ctr >= target; false if the wait ran out (or another block's did).  The
-// block synchronises before and after.
-__device__ __forceinline__ bool wait_for(const DevPlan& P, const unsigned* ctr, unsigned target) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int good = 1;
-        unsigned polls = 0;
-        while (ld_acquire(ctr) < target) {
-            if (++polls > P.spin_limit) {
-                atomicCAS(P.status, 0, (int)WAVE1D_ETIMEOUT);
-                good = 0;
-                break;
-            }
-            if ((polls & 255u) == 0 && *(volatile int*)P.status == (int)WAVE1D_ETIMEOUT) {
-                good = 0;
-                break;
-            }
-            __nanosleep(100);
-        }
-        __threadfence();
-        ok = good;
-    }
-    __syncthreads();
-    return ok != 0;
-}
-
-// thread 0 waits until *a >= ta and *b >= tb (one poll reads both)
-__device__ __forceinline__ bool wait_for2(const DevPlan& P, const unsigned* a, unsigned ta, const unsigned* b,
-                                          unsigned tb) {
-    __shared__ int ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int good = 1;
-        unsigned polls = 0;
-        for (;;) {
-            const unsigned va = ld_acquire(a), vb = ld_acquire(b);
-            if (va >= ta && vb >= tb) break;
-            if (++polls > P.spin_limit) {
-                atomicCAS(P.status, 0, (int)WAVE1D_ETIMEOUT);
-                good = 0;
-                break;
-            }
-            if ((polls & 255u) == 0 && *(volatile int*)P.status == (int)WAVE1D_ETIMEOUT) {
-                good = 0;
-                break;
-            }
-            __nanosleep(100);
-        }
-        __threadfence();
-        ok = good;
-    }
-    __syncthreads();
-    return ok != 0;
-}
-
-// the block's writes of a finished unit become visible before the unit is counted
-__device__ __forceinline__ void finish(unsigned* ctr) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(ctr, 1u);
-    }
-}
 
 // The small working set of the later phases on the critical path (per-mode factors and FIR
 // tails, interpolation kernels, solve groups and block inverses: a few MB) is pulled into L2 after

@@ -57,3 +57,23 @@ def test_batched_march_is_bitwise_reproducible():
         finally:
             batch.close()
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_one_launch_step_equals_the_per_pass_launches():
+    """The batched step as one cooperative launch (opts.step_kernel = 1, the default) against the
+    same step as one launch per pass (step_kernel = 0): the same unit bodies in the same order, so
+    the densities and receiver fields agree bit for bit; also a larger instance (M = 3000, its
+    implicit blocks up to dozens of springs) among small ones."""
+    ws = _instances() + [W.make("big", M=3000, bc=W.PERIODIC, dt=0.01, Nt=300, tol=1e-10, p=8, seed=7,
+                                amp=(1.0,), center=(-2.0,), width=(0.1,), R=3)]
+    out = []
+    for sk in (1, 0):
+        batch = wave1d.Batch(ws, step_kernel=sk)
+        try:
+            assert batch.one_launch == bool(sk)
+            out.append(batch.solve(120))
+        finally:
+            batch.close()
+    (s1, u1), (s0, u0) = out
+    assert np.max(np.abs(s0)) > 1e-3
+    assert np.array_equal(s1, s0) and np.array_equal(u1, u0)
