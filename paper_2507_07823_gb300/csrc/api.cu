@@ -58,6 +58,12 @@ __global__ void k_mx_gather(DevPlan P, const int64_t* perm, double* c);
 __global__ void k_mx_rhs(DevPlan P, const int64_t* perm, const double* u);
 __global__ void k_mx_receivers(int64_t R, const int64_t* perm, const double* u, double* uHr);
 __global__ void k_rs_local(DevPlan P, RangeDev R);
+__global__ void k_rs_local_T(DevPlan P, RangeDev R, int64_t n, const double* cbar, double* sb);
+__global__ void k_rs_adj_init(DevPlan P, RangeDev R, double* slot_vals, double* rhs);
+__global__ void k_rs_adj_post(DevPlan P, RangeDev R, const double* sigma_next, const double* g_next, double* grad,
+                              double* gbar_next, double* cbar, double* uHbar);
+__global__ void k_rs_adj_receivers(DevPlan P, RangeDev R, int64_t n, const double* ubar, double* sb);
+size_t rs_local_T_smem(int nint, int nm);
 __global__ void k_rs_nearby_weights(DevPlan P, RangeDev R);
 __global__ void k_rs_solve_init(DevPlan P, RangeDev R);
 __global__ void k_rs_jacobi(DevPlan P, RangeDev R, int it);
@@ -1262,6 +1268,8 @@ struct Reverse {
     bool have_rcv = false;
     int npts = 0;
     size_t lsmem = 0;
+    double* rrhs = nullptr;   // plans without pair lists: the transposed solve's right-hand side
+    size_t tsmem = 0;
     static constexpr int kLocalWarps = 4;     // the transposed local sum: one warp per spring row
 
     int init(wave1d_plan_t pl) {
@@ -1294,6 +1302,13 @@ struct Reverse {
             (rc = wk.upload(rcol.mrange, &rmr)) || (rc = wk.upload(rcol.woff, &rwoff)) ||
             (rc = wk.upload(hp.rloc.w, &rw)))
             return rc;
+        if (p->range) {
+            if ((rc = wk.zeros(&rrhs, (size_t)M))) return rc;
+            tsmem = rs_local_T_smem(p->rd.nint, p->rd.nm);
+            if (tsmem > 227 * 1024) return fail(WAVE1D_EUNSUPPORTED, "window too long for the transposed local sum");
+            CK(cudaFuncSetAttribute(k_rs_local_T, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem));
+            return WAVE1D_OK;
+        }
         lsmem = adj_local_smem(P.m_max, kLocalWarps);
         if (lsmem > 227 * 1024) return fail(WAVE1D_EUNSUPPORTED, "window too long for the adjoint's local-sum accumulators");
         if (lsmem > 48 * 1024)
@@ -1315,13 +1330,29 @@ struct Reverse {
         int rc;
         for (int64_t n = n_hi - 1; n >= n_lo; n--) {
             const double* ub = R > 0 ? ubar + n * R : nullptr;
-            if (have_rcv) k_adj_receivers<<<gM, 256, 0, s>>>(M, ring, n, rptr, rrcv, rmr, rwoff, rw, ub, sb);
-            k_adj_take<<<gM, 256, 0, s>>>(M, sb + (int64_t)(((n + 1) % ring)) * M, tmp);
-            k_adj_solve<<<gM, 256, 0, s>>>(d, dblk, tmp, sig_rows + (n - row0) * M, g ? g + n * M : nullptr,
-                                           want_beta ? gsum : nullptr, grad_g ? grad_g + n * M : nullptr, cbar, uHbar);
-            if (n == 0) break;
-            if (d.l_nitems > 0)
-                k_adj_local<<<blocks_for(M * 32, 32 * kLocalWarps, INT32_MAX), 32 * kLocalWarps, lsmem, s>>>(d, n, cbar, sb);
+            if (p->range) {
+                // plan without pair lists: receivers, solve and local sum transposed on the
+                // range tables; the solve is the forward Jacobi sweeps on beta-scaled data
+                const RangeDev& rd = p->rd;
+                if (R > 0) k_rs_adj_receivers<<<gM, 256, 0, s>>>(d, rd, n, ub, sb);
+                k_rs_adj_init<<<gM, 256, 0, s>>>(d, rd, sb + (int64_t)((n + 1) % ring) * M, rrhs);
+                DevPlan dj = d;
+                dj.rhs = rrhs;
+                const unsigned sweeps = (unsigned)std::min<int64_t>(blocks_for(M * 32, 256, INT32_MAX), 16 * (int64_t)p->sms);
+                for (int it = 1; it <= kRsMaxIter; it++) k_rs_jacobi<<<sweeps, 256, 0, s>>>(dj, rd, it);
+                k_rs_adj_post<<<gM, 256, 0, s>>>(d, rd, sig_rows + (n - row0) * M, g ? g + n * M : nullptr,
+                                                 want_beta ? gsum : nullptr, grad_g ? grad_g + n * M : nullptr, cbar, uHbar);
+                if (n == 0) break;
+                k_rs_local_T<<<(unsigned)((M + kRsTTargets - 1) / kRsTTargets), kRsTTargets, tsmem, s>>>(d, rd, n, cbar, sb);
+            } else {
+                if (have_rcv) k_adj_receivers<<<gM, 256, 0, s>>>(M, ring, n, rptr, rrcv, rmr, rwoff, rw, ub, sb);
+                k_adj_take<<<gM, 256, 0, s>>>(M, sb + (int64_t)(((n + 1) % ring)) * M, tmp);
+                k_adj_solve<<<gM, 256, 0, s>>>(d, dblk, tmp, sig_rows + (n - row0) * M, g ? g + n * M : nullptr,
+                                               want_beta ? gsum : nullptr, grad_g ? grad_g + n * M : nullptr, cbar, uHbar);
+                if (n == 0) break;
+                if (d.l_nitems > 0)
+                    k_adj_local<<<blocks_for(M * 32, 32 * kLocalWarps, INT32_MAX), 32 * kLocalWarps, lsmem, s>>>(d, n, cbar, sb);
+            }
             k_adj_gather<<<gM, 256, 0, s>>>(M, dperm, uHbar, cnu);
             if ((rc = wave1d_nufft_type1(wk.nu, cnu, S1))) return fail(rc, wave1d_nufft_strerror());
             k_adj_modes_in<<<gK, 256, 0, s>>>(K, S1, xr, ub, R, ab);
@@ -1351,8 +1382,11 @@ struct Reverse {
 int adjoint_checks(wave1d_plan_t p, int64_t nsteps, const double* ubar, double* grad_beta, double* grad_g) {
     if (nsteps < 1 || (!grad_beta && !grad_g))
         return fail(WAVE1D_EINVAL, "need nsteps >= 1 and grad_beta or grad_g");
-    if (p->range) return fail(WAVE1D_EUNSUPPORTED, "the reverse march reads stored local weights (local_weights = 0)");
     const Params& P = p->hp.P;
+    if (p->range)
+        for (double b : p->hp.beta)
+            if (!(b > 0.0))
+                return fail(WAVE1D_EINVAL, "the transposed solve of a plan without pair lists needs every stiffness > 0");
     if (nsteps > P.Nt) return fail(WAVE1D_EINVAL, "nsteps beyond the Nt of the plan");
     if (P.R > 0 && !ubar) return fail(WAVE1D_EINVAL, "ubar is NULL");
     if (grad_beta)

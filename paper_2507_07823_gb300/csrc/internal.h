@@ -89,6 +89,7 @@ void build_range_tables(const Params& P, RangeTables& out);
 void local_weights_exact(const Params& P, const std::vector<double>& d, std::vector<double>& Q);
 // targets per block of the range-mode local sum (one per thread); cells of the distance lookup table
 constexpr int kRsTargets = 256;
+constexpr int kRsTTargets = 128;    // outputs per block of the transposed local sum (reverse march)
 constexpr int kRsCells = 2048;
 
 struct HostPlan {

@@ -490,4 +490,257 @@ __global__ void k_rs_finish(DevPlan P, RangeDev R) {
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Reverse march (wave1d_adjoint on a plan without pair lists): the transposed local sum,
+//   sigmabar_l^{n+1-m} += sum_j Q_m(d_jl) cbar_j,   m >= 1,
+// over the same pairs as k_rs_local (every j within delta of l, each once).  On interval iv,
+// Q_m(d) = sum_r a_{iv,m,r} z^r, so the pairs of output l that fall in iv enter only through the
+// moments F_r = sum_{j in iv} z_jl^r cbar_j, and the interval adds sum_r a_{iv,m,r} F_r to
+// output m.  One block of kRsTTargets outputs (thread t: output j0 + t) walks the inputs of its
+// window as k_rs_local walks its sources (the same grid, index side test, interval walk and
+// near/far rule); a thread accumulates the moments of its current interval (F_0, F_1 as
+// compensated pairs, F_2 .. F_7 single) and flushes them into its per-m FP64 outputs in shared
+// memory when the interval changes.  No atomics: every output has one writer, in a fixed order.
+// ---------------------------------------------------------------------------------------------
+size_t rs_local_T_smem(int nint, int nm) {
+    return (size_t)4 * nint * sizeof(float) + (size_t)kRsTTargets * nm * sizeof(double) +
+           (size_t)kRsChunk * sizeof(float2);
+}
+
+struct RsMoments {
+    float f0h, f0l, f1h, f1l, f2, f3, f4, f5, f6, f7;
+};
+
+// out[m] += sum_r a_{iv,m,r} F_r for the interval's m >= 1 (out: this thread's column, stride kRsTTargets)
+__device__ __forceinline__ void rs_flush(const RangeDev& R, int iv, const RsMoments& F, double* out) {
+    const int m0 = max(1, __ldg(R.mr + 2 * iv)), m1 = __ldg(R.mr + 2 * iv + 1);
+    const float4* c = (const float4*)R.coef + (size_t)iv * R.nm * 3;
+    for (int m = m0; m <= m1; m++) {
+        const float4 c01 = __ldg(c + 3 * m), c23 = __ldg(c + 3 * m + 1), c47 = __ldg(c + 3 * m + 2);
+        float h = 0.f, l = 0.f;
+        rs::acc_mac(h, l, c01.x, c01.y, F.f0h, F.f0l);
+        rs::acc_mac(h, l, c01.z, c01.w, F.f1h, F.f1l);
+        float r = __fmaf_rn(c23.y, F.f2, __fmaf_rn(c23.x, F.f2, 0.f));
+        r = __fmaf_rn(c23.w, F.f3, __fmaf_rn(c23.z, F.f3, r));
+        r = __fmaf_rn(c47.x, F.f4, r);
+        r = __fmaf_rn(c47.y, F.f5, r);
+        r = __fmaf_rn(c47.z, F.f6, r);
+        r = __fmaf_rn(c47.w, F.f7, r);
+        rs::acc_add(h, l, r, 0.f);
+        out[(size_t)m * kRsTTargets] += (double)h + (double)l;
+    }
+}
+
+// F += cbar z^r for one pair (z = zh + zl normalised, cbar = (ch, cl))
+__device__ __forceinline__ void rs_moments_add(RsMoments& F, float zh, float zl, float ch, float cl) {
+    rs::acc_add(F.f0h, F.f0l, ch, cl);
+    rs::acc_mac(F.f1h, F.f1l, zh, zl, ch, cl);
+    const float z2 = __fmul_rn(zh, zh);
+    float p = __fmul_rn(z2, ch);
+    F.f2 = __fadd_rn(F.f2, p);
+    p = __fmul_rn(p, zh);
+    F.f3 = __fadd_rn(F.f3, p);
+    p = __fmul_rn(p, zh);
+    F.f4 = __fadd_rn(F.f4, p);
+    p = __fmul_rn(p, zh);
+    F.f5 = __fadd_rn(F.f5, p);
+    p = __fmul_rn(p, zh);
+    F.f6 = __fadd_rn(F.f6, p);
+    p = __fmul_rn(p, zh);
+    F.f7 = __fadd_rn(F.f7, p);
+}
+
+// the pairs of one side for one output, inputs [k0, k1) of the chunk (cf. rs_pairs)
+template <int S>
+__device__ __forceinline__ void rs_pairs_T(const RangeDev& R, const float4* sMeta, const float2* sC, const float* ivt,
+                                           float cscale, int k0, int k1, int lbj, int nbl, int nbc, float bh, float bl,
+                                           rs::Track& tr, int& cur, RsMoments& F, double* out) {
+    for (int kk = k0; kk < k1; kk++) {
+        const float4 mt = sMeta[kk];
+        const int e = __float_as_int(mt.z), lohi = __float_as_int(mt.w);
+        if ((lohi & 0x7fff) > (lohi >> 16) || (S < 0 ? e >= lbj : e < lbj)) continue;
+        float zh, zl;
+        rs::z_of<S>(tr, mt.x, mt.y, zh, zl);
+        if (fabsf(zh) > rs::kZTol) rs::walk<S>(ivt, R.cell, cscale, R.nint, bh, bl, mt.x, mt.y, tr, zh, zl);
+        if (lohi & 0x8000)
+            rs::near_side<S>(ivt, R.iv_dt, (unsigned)(e - nbl) < (unsigned)nbc, bh, bl, mt.x, mt.y, tr, zh, zl);
+        if (!(fabsf(zh) <= rs::kZTol)) continue;
+        if (tr.iv != cur) {
+            if (cur >= 0) rs_flush(R, cur, F, out);
+            cur = tr.iv;
+            F = RsMoments{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        }
+        const float2 cb = sC[kk];
+        rs_moments_add(F, zh, zl, cb.x, cb.y);
+    }
+}
+
+__global__ void __launch_bounds__(kRsTTargets) k_rs_local_T(DevPlan P, RangeDev R, int64_t n,
+                                                           const double* __restrict__ cbar, double* sb) {
+    extern __shared__ __align__(16) float rs_sm[];
+    float* sIv = rs_sm;
+    double* sOut = (double*)(sIv + 4 * R.nint);                  // [m][thread]
+    float2* sC = (float2*)(sOut + (size_t)R.nm * kRsTTargets);   // the chunk's cbar (pairs)
+    __shared__ float4 sMeta[kRsTTargets];
+
+    const int64_t M = P.M;
+    const int t = threadIdx.x;
+    const int64_t j0 = (int64_t)blockIdx.x * kRsTTargets;
+    const int nT = (int)min((int64_t)kRsTTargets, M - j0);
+    const int b = (int)(j0 / kRsTargets);                        // the forward block holding these outputs
+    const double xa = P.x[j0], span = P.x[j0 + nT - 1] - xa;
+    const rs::Grid G = rs::grid_of(span, R.delta);
+    for (int iv = t; iv < R.nint; iv += blockDim.x) rs::interval_on_grid(__ldg(R.mid + iv), __ldg(R.ih + iv), G, sIv + 4 * iv);
+    double* out = sOut + t;
+    for (int m = 0; m < R.nm; m++) out[(size_t)m * kRsTTargets] = 0.0;
+    const bool valid = t < nT;
+    const int64_t j = j0 + (valid ? t : 0);
+    const double xj = P.x[j];
+    float hj, lj;
+    rs::grid_split(xj - xa, G, hj, lj);
+    int64_t lbj = j;
+    if (j > 0 && P.x[j - 1] == xj) {
+        int64_t lo = 0;
+        while (lo < lbj) {
+            const int64_t mid = (lo + lbj) >> 1;
+            if (P.x[mid] < xj) lo = mid + 1;
+            else lbj = mid;
+        }
+    }
+    const int nbl = __ldg(R.nb_lo + j), nbc = __ldg(R.nb_cnt + j);
+    // the forward block's window holds every input within delta of these outputs
+    const int wlo = __ldg(R.blk_win + 4 * b), inlo = __ldg(R.blk_win + 4 * b + 1);
+    const int inhi = __ldg(R.blk_win + 4 * b + 2), whi = __ldg(R.blk_win + 4 * b + 3);
+    const int nL = max(0, inhi - wlo), total = nL + max(0, whi - inlo);
+    const float cscale = R.cell_scale;
+    __syncthreads();
+    rs::Track trL, trR;
+    rs::track_to(sIv, 0, hj, lj, trL);
+    rs::track_to(sIv, 0, -hj, -lj, trR);
+    int cur = -1;
+    RsMoments F{0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int base = 0; base < total; base += kRsChunk) {
+        const int grp = base & (kRsTTargets - 1);                // the chunk's place in its group of 4
+        if (grp == 0) {
+            __syncthreads();
+            const int v = base + t;
+            int lohi = 1, e = 0;
+            float h = 0.f, l = 0.f;
+            if (v < total) {
+                const bool left = v < nL;
+                e = left ? wlo + v : inlo + (v - nL);
+                const double xr = rs_xext(P, e) - xa;
+                rs::grid_split(xr, G, h, l);
+                lohi = rs::source_range(xr, left, span, R.delta, P.dt, R.bp2, R.cell, cscale, R.nint);
+            }
+            sMeta[t] = make_float4(h, l, __int_as_float(e), __int_as_float(lohi));
+        }
+        __syncthreads();
+        if (t < kRsChunk) {
+            const int v = base + t;
+            float2 cb = make_float2(0.f, 0.f);
+            if (v < total) {
+                const double c = cbar[rs_spring(v < nL ? wlo + v : inlo + (v - nL), M)];
+                const float hi = (float)c;
+                cb = make_float2(hi, (float)(c - (double)hi));
+            }
+            sC[t] = cb;
+        }
+        __syncthreads();
+        if (valid) {
+            const int kend = min(kRsChunk, total - base), kL = min(kend, max(0, nL - base));
+            const float4* meta = sMeta + grp;
+            rs_pairs_T<-1>(R, meta, sC, sIv, cscale, 0, kL, (int)lbj, nbl, nbc, hj, lj, trL, cur, F, out);
+            rs_pairs_T<1>(R, meta, sC, sIv, cscale, kL, kend, (int)lbj, nbl, nbc, -hj, -lj, trR, cur, F, out);
+        }
+        __syncthreads();
+    }
+    if (!valid) return;
+    if (cur >= 0) rs_flush(R, cur, F, out);
+    for (int m = 1; m < R.nm; m++) {
+        const double v = out[(size_t)m * kRsTTargets];
+        if (v != 0.0) {
+            int64_t q = (n + 1 - m) % P.ring;
+            if (q < 0) q += P.ring;
+            sb[q * M + j] += v;
+        }
+    }
+}
+
+// Transposed implicit solve.  With S_jl = (beta_j / 2) Q_0(d_jl), (I + S)^T rb = b is
+// rb = y / beta with (I + S) y = beta b (beta > 0), so the forward Jacobi sweeps solve it on the
+// right-hand side beta b.  Set-up: that right-hand side (k_rs_jacobi reads it as P.rhs) and the
+// first iterate rhs / (1 + S_jj); b = sigmabar^{n+1}, taken out of its ring slot.
+__global__ void k_rs_adj_init(DevPlan P, RangeDev R, double* __restrict__ slot_vals, double* __restrict__ rhs) {
+    if (blockIdx.x == 0)
+        for (int i = threadIdx.x; i < 2 * (kRsMaxIter + 1); i += blockDim.x) R.stats[i] = 0ull;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < P.M; j += (int64_t)gridDim.x * blockDim.x) {
+        const double r = P.beta[j] * slot_vals[j];
+        slot_vals[j] = 0.0;
+        rhs[j] = r;
+        const double x0 = r / R.diag[j];
+        R.it64[0][j] = x0;
+        const rs::Pair p2 = rs::split(x0);
+        R.it2[0][2 * j] = p2.hi;
+        R.it2[0][2 * j + 1] = p2.lo;
+    }
+}
+
+// the converged sweep's y (as k_rs_store chooses it), then rb_j = y_j / beta_j and the step's
+// gradient terms and adjoints as the block-solve form gives them (k_adj_solve):
+//   grad_j += rb_j (sigma_j^{n+1} [+ g_j^{n+1}]) / beta_j,  gbar_j^{n+1} = -rb_j,  cbar_j = -beta_j rb_j / 2,
+//   u_Hbar_j = -beta_j rb_j  (sigma_next, gbar_next in caller order; grad, gbar_next may be null)
+__global__ void k_rs_adj_post(DevPlan P, RangeDev R, const double* __restrict__ sigma_next,
+                              const double* __restrict__ g_next, double* grad, double* __restrict__ gbar_next,
+                              double* cbar, double* uHbar) {
+    int fin = kRsMaxIter;
+    bool ok = false;
+    for (int it = 1; it <= kRsMaxIter; it++) {
+        const double dmax = rs_from_bits(__ldcg(R.stats + 2 * it)), smax = rs_from_bits(__ldcg(R.stats + 2 * it + 1));
+        if (dmax <= kRsTol * smax) {
+            fin = it;
+            ok = true;
+            break;
+        }
+    }
+    const double* y = R.it64[fin & 1];
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < P.M; j += (int64_t)gridDim.x * blockDim.x) {
+        const double bj = P.beta[j];
+        const double rb = __ldcg(y + j) / bj;
+        const int jc = P.perm[j];
+        if (grad) grad[j] += rb * (g_next ? sigma_next[jc] + g_next[jc] : sigma_next[jc]) / bj;
+        if (gbar_next) gbar_next[jc] = -rb;
+        cbar[j] = -0.5 * bj * rb;
+        uHbar[j] = -bj * rb;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && !ok) atomicCAS(P.status, 0, (int)WAVE1D_ENOTCONV);
+}
+
+// Transposed receiver read-out (eq. localSol2, every m including m = 0, FP64): for spring l and
+// each receiver r in order, the extended indices of l inside r's window (those of the forward
+// read-out), sigmabar_l^{n+1-m} += (1/2) Q_m(d) ubar_r.  One thread per spring, no atomics.
+__global__ void k_rs_adj_receivers(DevPlan P, RangeDev R, int64_t n, const double* __restrict__ ubar, double* sb) {
+    const int64_t M = P.M;
+    for (int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; l < M; l += (int64_t)gridDim.x * blockDim.x) {
+        for (int64_t r = 0; r < P.R; r++) {
+            const int lo = R.r_win[2 * r], hi = R.r_win[2 * r + 1];
+            for (int k = -1; k <= 1; k++) {
+                const int64_t e = l + k * M;
+                if (e < lo || e >= hi) continue;
+                const double d = fabs(rs_xext(P, e) - P.xr[r]);
+                if (!(d < R.delta)) continue;
+                const int iv = rs_locate64(R, d);
+                const double z = (d - __ldg(R.mid + iv)) * (double)__ldg(R.ih + iv);
+                const int m0 = __ldg(R.mr0 + 2 * iv), m1 = __ldg(R.mr0 + 2 * iv + 1);
+                for (int m = m0; m <= m1; m++) {
+                    const double q = rs_cheb(R.cheb + ((size_t)iv * R.nm + m) * 8, z);
+                    int64_t s = (n + 1 - m) % P.ring;
+                    if (s < 0) s += P.ring;
+                    sb[s * M + l] += 0.5 * q * ubar[r];
+                }
+            }
+        }
+    }
+}
+
 }  // namespace wave1d
