@@ -739,15 +739,61 @@ def _adjoint_plan(wave1d, w, beta=None):
                        max_local_bytes=64 << 30)
 
 
+def adjoint_full_M(torch, wave1d, workloads, args):
+    """The adjoint workload at its own M = 1e5 through the plan without pair lists (its one
+    implicit block of every spring needs the iterative solve), over the stable horizon
+    args.adjoint_full_steps (the scheme grows after about 2500 steps at this density): forward,
+    reverse from the stored densities, and the checkpointed form (every args.adjoint_interval
+    steps), which must give the same gradient bit for bit."""
+    nsteps = args.adjoint_full_steps
+    w = workloads.config4(Nt=nsteps)
+    w = w.with_(xr=float(np.min(w.x)) + 2 * w.dt * np.arange(8))
+    rng = np.random.default_rng(w.seed)
+    d = torch.from_numpy(0.01 * rng.standard_normal((nsteps, len(w.xr)))).cuda()
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    out = {"M": w.M, "steps": nsteps, "local_weights": "computed (plan without pair lists)"}
+    try:
+        plan = wave1d.Plan.from_workload(w, local_weights=1)
+        (sigma, u), ms_f = timed(lambda: plan.solve_device(nsteps))
+        g, ms_a = timed(lambda: plan.adjoint(sigma, u - d))
+        plan.close()
+        del sigma
+        iv = args.adjoint_interval
+        plan = wave1d.Plan.from_workload(w, local_weights=1)
+        (u2, ck), ms_cf = timed(lambda: plan.solve_checkpointed(nsteps, iv))
+        g2, ms_ca = timed(lambda: plan.adjoint_checkpointed(ck, nsteps, iv, u2 - d))
+        plan.close()
+        work = w.M * nsteps
+        out.update({"forward_ms_per_step": ms_f / nsteps, "adjoint_ms_per_step": ms_a / nsteps,
+                    "forward_value": work / (ms_f * 1e-3), "adjoint_value": work / (ms_a * 1e-3),
+                    "checkpointed": {"interval": iv, "checkpoint_bytes": ck.numel(),
+                                     "forward_ms_per_step": ms_cf / nsteps, "adjoint_ms_per_step": ms_ca / nsteps,
+                                     "gradient_equal_bitwise": bool(torch.equal(g, g2))},
+                    "grad_max": float(torch.max(torch.abs(g)))})
+    except Exception as e:                                  # noqa: BLE001
+        out["error"] = repr(e)[:300]
+    return out
+
+
 def run_adjoint_only(args):
     """The reverse-time march on the adjoint workload's recipe (free space, dt = 1e-3, tol = 1e-12,
     p = 8, beta ~ U[1, 10], 8 receivers): both strategies (stored densities, wave1d_adjoint; the
     march state checkpointed every `interval` steps and recomputed, wave1d_adjoint_checkpointed,
     which must give the same gradient bit for bit), and central differences of the loss
-    L = 1/2 sum (u - d)^2 (d a seeded target trace) on 32 random stiffnesses.  The workload's own
-    M = 1e5 is tried first; it puts all springs in one implicit block (18.5 springs per dt), which the stored-weight plan the
-    reverse march needs does not solve, so the line records that and runs the largest M of the
-    recipe given by --adjoint-M.  One JSON line; not part of the default benchmark line."""
+    L = 1/2 sum (u - d)^2 (d a seeded target trace) on 32 random stiffnesses, at --adjoint-M
+    springs with stored weights; and, as `full_workload`, the workload's own M = 1e5 through the
+    plan without pair lists over its stable horizon.  One JSON line; not part of the default
+    benchmark line."""
     import torch
 
     from paper_2507_07823_gb300 import build, wave1d, workloads
@@ -756,11 +802,7 @@ def run_adjoint_only(args):
     nsteps = args.adjoint_steps
     line = {"metric": "scatterer-steps/s of the reverse-time march (dL/dbeta)", "unit": "scatterer-steps/s",
             "dtype": "f64", "data": "synthetic"}
-    try:
-        _adjoint_plan(wave1d, workloads.config4(Nt=nsteps)).close()
-        line["full_workload"] = "planned"
-    except wave1d.Wave1DError as e:
-        line["full_workload"] = {"M": 100000, "unavailable": str(e)}
+    line["full_workload"] = adjoint_full_M(torch, wave1d, workloads, args)
     w = workloads.config4(M=args.adjoint_M, Nt=nsteps)
     # the 8 receivers at the medium's entry, 2 dt apart: at this density the transmitted field is
     # localized within a few hundred springs, so receivers spread over the medium (the recipe's
@@ -954,6 +996,8 @@ def main():
     ap.add_argument("--adjoint-M", type=int, default=10000)
     ap.add_argument("--adjoint-interval", type=int, default=100, help="checkpoint interval (steps)")
     ap.add_argument("--adjoint-fd", type=int, default=32, help="stiffnesses checked by central differences")
+    ap.add_argument("--adjoint-full-steps", type=int, default=1200,
+                    help="steps of the M = 1e5 march through the plan without pair lists")
     ap.add_argument("--local-only", action="store_true",
                     help="only the local sum of the plan without pair lists on a clustered case (not a benchmark line)")
     ap.add_argument("--local-M", type=int, default=250000)
