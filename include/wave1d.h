@@ -257,7 +257,10 @@ int wave1d_state_load(wave1d_plan_t plan, const void* buf, size_t bytes);
  *   grad_beta : device, M values, dL/dbeta_j in caller order (overwritten), or NULL.
  *   grad_g    : device, nsteps x M, row s = dL/dg^{s+1} in caller order (overwritten), or NULL.
  * At least one of grad_beta, grad_g.  grad_beta needs every stiffness > 0 (WAVE1D_EINVAL
- * otherwise).  The plan's tables are read and its march state is left alone.  Work arrays (a
+ * otherwise); so does a plan without pair lists (opts.local_weights = 1), whose reverse march
+ * transposes its range tables' local sum and its iterative implicit solve (the latter as the
+ * forward sweeps on beta-scaled data; WAVE1D_ENOTCONV if they do not converge).  The plan's
+ * tables are read and its march state is left alone.  Work arrays (a
  * ring of m_max + 1 density adjoints, the adjoint S ring and modes, an FP64 NUFFT plan of the
  * springs) are allocated for the call and freed before it returns.  No launch uses atomics: the
  * results are the same bit for bit from call to call.  Synchronises the plan's stream.
