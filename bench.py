@@ -880,6 +880,18 @@ def run_adjoint_only(args):
     print(json.dumps(line))
 
 
+def run_free_only(args):
+    """The free-space M = 1e4 workload alone (the `free_M1e4` key of the benchmark line: stored
+    weights, one-launch step kernel); the small case its kernel's profiles are taken on.  Not a
+    benchmark line."""
+    import torch
+
+    from paper_2507_07823_gb300 import build
+
+    build.build()
+    print(json.dumps({"free_M1e4": free_space_secondary(torch, torch.cuda.current_stream())}))
+
+
 def run_local_only(args):
     """The local sum of the plan without pair lists alone (k_rs_local) on the clustered recipe at
     --local-M springs in --local-clusters clusters (50,000 springs per cluster keeps the million-
@@ -998,6 +1010,8 @@ def main():
     ap.add_argument("--adjoint-fd", type=int, default=32, help="stiffnesses checked by central differences")
     ap.add_argument("--adjoint-full-steps", type=int, default=1200,
                     help="steps of the M = 1e5 march through the plan without pair lists")
+    ap.add_argument("--free-only", action="store_true",
+                    help="only the free-space M = 1e4 workload with stored weights (not a benchmark line)")
     ap.add_argument("--local-only", action="store_true",
                     help="only the local sum of the plan without pair lists on a clustered case (not a benchmark line)")
     ap.add_argument("--local-M", type=int, default=250000)
@@ -1012,6 +1026,8 @@ def main():
         run_spread_interp_only(args)
     elif args.local_only:
         run_local_only(args)
+    elif args.free_only:
+        run_free_only(args)
     elif args.adjoint_only:
         run_adjoint_only(args)
     elif args.mixed_only:
