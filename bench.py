@@ -42,8 +42,8 @@ L2_FLUSH_BYTES = 512 << 20
 # DRAM bytes (read + write) of one k_step launch at this workload, from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel sources it was taken
 # with: reported as roofline.traffic while their SHA-256 matches, else null
-STEP_KERNEL_SOURCES = ["step.cu", "phases.cuh", "device_common.cuh", "internal.h"]
-STEP_TRAFFIC = {"sources_sha256": "6b3e6ef8286ac0f3a0e111fd7bd1113295ef941cf0dc773cd82ab82aededf703", "bytes_per_launch": 316604416 + 4018432}
+STEP_KERNEL_SOURCES = ["step.cu", "grid_sync.cuh", "phases.cuh", "device_common.cuh", "internal.h"]
+STEP_TRAFFIC = {"sources_sha256": "fd4b65c8954f13382a1ec6a21aee738ffaefebd6ac8391607d8abde3052152a1", "bytes_per_launch": 316604416 + 4018432}
 L2_CLEAN_BYTES = 256 << 20
 # DRAM bytes of one k_rs_local launch from one ncu capture of the clustered layout at M = 2e5 (its
 # pairs below), for the kernel sources it was taken with (null once they change)
