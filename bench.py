@@ -538,8 +538,9 @@ def forms_beside_fp64(torch, w, steps, warmup=3):
       mixed_precision: the headline workload (a million clustered springs) with the history part's
         spreading and interpolation in FP32 (width-7 kernel, tol 1e-6), same plan otherwise; its
         error against the oracle is in error_vs_oracle.mixed.
-      adjoint, batched: reduced cases (the full adjoint and batched workloads are the
-        --adjoint-only and --batched-only legs)."""
+      adjoint: the adjoint recipe at M = 1e4 with stored weights, both strategies and central
+        differences on 8 stiffnesses (--adjoint-only adds M = 1e5 and 32 stiffnesses);
+      batched: the batched workload's 256 instances with M up to 1e4, one launch per step."""
     from paper_2507_07823_gb300 import wave1d, workloads
 
     out = {}
@@ -569,35 +570,70 @@ def forms_beside_fp64(torch, w, steps, warmup=3):
     except Exception as e:
         out["mixed_precision"] = {"error": repr(e)[:300]}
 
-    w1 = workloads.config1()
-    small = 200
+    # adjoint: the adjoint workload's recipe at M = 1e4 (stored weights), 2000 steps, receivers at
+    # the medium's entry and a seeded target trace; both strategies, and central differences of the
+    # GPU march on 8 stiffnesses (32 in --adjoint-only)
     try:
-        plan = wave1d.Plan.from_workload(w1.with_(Nt=small))
+        na = 2000
+        wa = workloads.config4(M=10000, Nt=na)
+        wa = wa.with_(xr=float(np.min(wa.x)) + 2 * wa.dt * np.arange(8))
+        rng = np.random.default_rng(wa.seed)
+        d = torch.from_numpy(0.01 * rng.standard_normal((na, len(wa.xr)))).cuda()
+        holder = {}
+        plan = wave1d.Plan.from_workload(wa)
         try:
-            holder = {}
-            ms_f = timed(lambda: holder.update(zip(("sigma", "u"), plan.solve_device(small))))
-            ubar = holder["u"] - 0.5 * holder["u"]
-            ms_a = timed(lambda: holder.update(g=plan.adjoint(holder["sigma"], ubar)))
-            out["adjoint"] = {"forward_value": w1.M * small / (ms_f * 1e-3), "adjoint_value": w1.M * small / (ms_a * 1e-3),
-                              "forward_ms_per_step": ms_f / small, "adjoint_ms_per_step": ms_a / small,
-                              "grad_finite": bool(torch.isfinite(holder["g"]).all()),
-                              "workload": f"reduced: {w1.name}, {small} steps (the adjoint workload is --adjoint-only)"}
+            ms_f = timed(lambda: holder.update(zip(("sigma", "u"), plan.solve_device(na))))
+            ms_a = timed(lambda: holder.update(g=plan.adjoint(holder["sigma"], holder["u"] - d)))
         finally:
             plan.close()
+        del holder["sigma"]
+        plan = wave1d.Plan.from_workload(wa)
+        try:
+            ms_cf = timed(lambda: holder.update(zip(("u2", "ck"), plan.solve_checkpointed(na, 100))))
+            ms_ca = timed(lambda: holder.update(g2=plan.adjoint_checkpointed(holder["ck"], na, 100, holder["u2"] - d)))
+        finally:
+            plan.close()
+        gh = holder["g"].cpu().numpy()
+        fd_err = 0.0
+        for j in np.random.default_rng(4).choice(wa.M, 8, replace=False):
+            h = 1e-4 * wa.beta[j]
+            Ls = []
+            for sgn in (1.0, -1.0):
+                bb = wa.beta.copy()
+                bb[j] += sgn * h
+                pl = wave1d.Plan.from_workload(wa.with_(beta=bb))
+                try:
+                    _, uu = pl.solve_device(na)
+                    Ls.append(0.5 * float(torch.sum((uu - d) ** 2)))
+                finally:
+                    pl.close()
+            fd_err = max(fd_err, abs((Ls[0] - Ls[1]) / (2 * h) - gh[j]))
+        out["adjoint"] = {"forward_value": wa.M * na / (ms_f * 1e-3), "adjoint_value": wa.M * na / (ms_a * 1e-3),
+                          "forward_ms_per_step": ms_f / na, "adjoint_ms_per_step": ms_a / na,
+                          "checkpointed": {"interval": 100, "forward_ms_per_step": ms_cf / na,
+                                           "adjoint_ms_per_step": ms_ca / na,
+                                           "gradient_equal_bitwise": bool(torch.equal(holder["g"], holder["g2"]))},
+                          "central_differences_8": {"max_abs_err_over_max_grad": fd_err / float(np.max(np.abs(gh)))},
+                          "workload": f"{wa.name} recipe at M = 1e4 (stored weights), {na} steps, 8 receivers at the "
+                                      "medium's entry, seeded target trace (M = 1e5 through the plan without pair "
+                                      "lists: --adjoint-only)"}
     except Exception as e:
         out["adjoint"] = {"error": repr(e)[:300]}
+    # batched: the batched workload's 256 instances with M up to 1e4, one persistent launch per step
     try:
-        ws = workloads.config3_instances(n_instances=64, m_range=(1e2, 2e3), Nt=20 + small + 1)
+        nb = 20
+        ws = workloads.config3_instances(m_range=(1e2, 1e4), Nt=5 + nb + 1)
         batch = wave1d.Batch(ws)
         try:
-            batch.solve(20, with_sigma=False)
+            batch.solve(5, with_sigma=False)
             st = {}
-            ms = timed(lambda: st.update(rc=wave1d.lib().wave1d_batch_solve(batch.h, small, None, None, 1)))
+            ms = timed(lambda: st.update(rc=wave1d.lib().wave1d_batch_solve(batch.h, nb, None, None, 1)))
             if st["rc"] != 0:
                 raise RuntimeError(wave1d.lib().wave1d_batch_strerror().decode())
-            out["batched"] = {"value": batch.M * small / (ms * 1e-3), "ms_per_step": ms / small, "M_total": batch.M,
-                              "workload": "reduced: 64 periodic instances, M log-uniform in [1e2, 2e3], dt = 1e-3 "
-                                          "(the batched workload is --batched-only)"}
+            out["batched"] = {"value": batch.M * nb / (ms * 1e-3), "ms_per_step": ms / nb, "M_total": batch.M,
+                              "one_launch": batch.one_launch,
+                              "workload": "256 periodic instances, M log-uniform in [1e2, 1e4], dt = 1e-3, tol 1e-12, "
+                                          "p = 8 (the workload's M up to 1e5 needs computed weights: not built)"}
         finally:
             batch.close()
     except Exception as e:
