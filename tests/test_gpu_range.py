@@ -3,7 +3,7 @@ the weights from their polynomials in the distance (compensated FP32 pairs), the
 Jacobi sweeps.  The march against the stored-weight plan of the same scheme and against the
 discrete scheme's oracle, in the periodic box, in free space and on a clustered layout whose blocks
 of 256 targets hold many sources (receivers placed where the field is live); the reverse march
-refuses such a plan.
+of such a plan refuses a zero stiffness.
 
 Bars: 1e-10 against the stored-weight plan (the range tables hold every weight to 1e-12 of
 max |Q|; single-float rounding of each source's curvature terms gives local sums within about 2e-11
@@ -67,14 +67,22 @@ def test_range_plan_reports_its_pairs_and_no_stored_weights():
         p1.close()
 
 
-def test_reverse_march_refuses_range_plans():
+def test_reverse_march_of_a_range_plan_refuses_a_zero_stiffness():
+    """The transposed Jacobi solve of a plan without pair lists works on beta-scaled data
+    ((I + S)^T r = b through (I + S) y = beta o b, r = y / beta), so its reverse march refuses a
+    layout with a zero stiffness even for dL/dg alone; the stored-weight plan of the same layout
+    takes it."""
     torch = pytest.importorskip("torch")
     w = W.config0(Nt=20)
-    plan = wave1d.Plan.from_workload(w, local_weights=1)
-    try:
-        sigma, u = plan.solve_device(20)
-        g = torch.empty(w.M, dtype=torch.float64, device="cuda")
-        st = wave1d.wave1d_adjoint(plan.h, 20, sigma, None, u.contiguous(), g, None)
-        assert st == wave1d.WAVE1D_EUNSUPPORTED
-    finally:
-        plan.close()
+    beta = w.beta.copy()
+    beta[5] = 0.0
+    w = w.with_(beta=beta)
+    for lw, want in ((1, wave1d.WAVE1D_EINVAL), (0, wave1d.WAVE1D_OK)):
+        plan = wave1d.Plan.from_workload(w, local_weights=lw)
+        try:
+            sigma, u = plan.solve_device(20)
+            gg = torch.empty((20, w.M), dtype=torch.float64, device="cuda")
+            st = wave1d.wave1d_adjoint(plan.h, 20, sigma, None, u.contiguous(), None, gg)
+            assert st == want
+        finally:
+            plan.close()
