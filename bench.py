@@ -989,7 +989,10 @@ def run_mixed_only(args):
 def run_batched_only(args):
     """The batched workload's instances (256 periodic instances, M log-uniform up to
     args.batch_mmax) marched together through wave1d_batch_solve for args.steps steps after
-    args.warmup: whole-batch scatterer-steps/s.  Not part of the default benchmark line."""
+    args.warmup: whole-batch scatterer-steps/s.  Forms: each instance's form chosen from its layout
+    (local_weights = 2: the small ones joined, their step one persistent launch or one launch per
+    pass; the large ones each a plan without pair lists, a branch of the step graph), and every
+    instance without pair lists (local_weights = 1).  Not part of the default benchmark line."""
     import torch
 
     from paper_2507_07823_gb300 import build, wave1d, workloads
@@ -997,10 +1000,13 @@ def run_batched_only(args):
     build.build()
     ws = workloads.config3_instances(m_range=(1e2, args.batch_mmax), Nt=args.warmup + args.steps + 1)
     res = {}
-    for name, sk in (("one_launch", 1), ("per_pass", 0)):
+    for name, kw in (("chosen_one_launch", dict(local_weights=2, step_kernel=1)),
+                     ("chosen_per_pass", dict(local_weights=2, step_kernel=0)),
+                     ("all_without_pair_lists", dict(local_weights=1))):
         t0 = time.perf_counter()
-        batch = wave1d.Batch(ws, step_kernel=sk)
+        batch = wave1d.Batch(ws, **kw)
         t_plan = time.perf_counter() - t0
+        forms = batch.forms
         batch.solve(args.warmup, with_sigma=False)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -1012,13 +1018,17 @@ def run_batched_only(args):
         if st != 0:
             raise RuntimeError(wave1d.lib().wave1d_batch_strerror().decode())
         ms = e0.elapsed_time(e1)
+        Ms = np.array([w.M for w in ws])
         res[name] = {"value": batch.M * args.steps / (ms * 1e-3), "ms_per_step": ms / args.steps,
-                     "one_launch": batch.one_launch, "plan_seconds": t_plan}
+                     "one_launch": batch.one_launch, "plan_seconds": t_plan,
+                     "instances_without_pair_lists": int(forms.sum()),
+                     "smallest_M_without_pair_lists": int(Ms[forms == 1].min()) if forms.any() else None,
+                     "largest_joined_M": int(Ms[forms == 0].max()) if (forms == 0).any() else None}
         M, R = batch.M, batch.R
         batch.close()
-    print(json.dumps({"metric": METRIC, "unit": UNIT, "value": res["one_launch"]["value"],
-                      "ms_per_step": res["one_launch"]["ms_per_step"], "steps": args.steps, "warmup": args.warmup,
-                      "dtype": "f64", "forms": res,
+    best = res["chosen_one_launch"]
+    print(json.dumps({"metric": METRIC, "unit": UNIT, "value": best["value"], "ms_per_step": best["ms_per_step"],
+                      "steps": args.steps, "warmup": args.warmup, "dtype": "f64 / f32x2 local sums", "forms": res,
                       "config": {"workload": f"{len(ws)} periodic instances, M log-uniform in [1e2, {args.batch_mmax:g}], "
                                              f"dt = 1e-3, tol 1e-12, p = 8", "M_total": M, "R_total": R}}))
 
@@ -1056,7 +1066,7 @@ def main():
                     help="only the FP64 and mixed-precision marches of the benchmark workload (not a benchmark line)")
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched march of the batched workload's instances (not a benchmark line)")
-    ap.add_argument("--batch-mmax", type=float, default=1e4)
+    ap.add_argument("--batch-mmax", type=float, default=1e5)
     args = ap.parse_args()
     if args.spread_interp_only:
         run_spread_interp_only(args)

@@ -89,7 +89,9 @@ typedef struct {
                            until the largest change is below 1e-14 of the largest density
                            (WAVE1D_ENOTCONV after 40).  For layouts whose weights or blocks do
                            not fit (a million clustered springs: 1.3e10 pairs); steps run as
-                           per-stage launches; wave1d_adjoint is not available                 */
+                           per-stage launches; wave1d_adjoint needs every stiffness > 0.
+                           Batched plans also take 2: each instance's form chosen from its layout
+                           (see wave1d_batch_plan)                                             */
     int spin_limit;     /* polls of a counter before a wait between the blocks of the one-launch
                            step kernel gives up and latches WAVE1D_ETIMEOUT; 0 = 2^22 (seconds)  */
     int hold_unit;      /* fault injection for tests, 0 = off: 1 makes the step kernel's column
@@ -392,8 +394,16 @@ int wave1d_nufft1_noalloc(const double* x, const double* c, int64_t M, int K, do
  *   pulse   : host, n_inst x 3: amplitude, centre, width of instance i's incident Gaussian.
  *   r_offsets, xr : host receivers, instance i's being xr[r_offsets[i] .. r_offsets[i+1]) (at
  *             least one each), or r_offsets = NULL for none.
- *   dt, Nt, tol : as wave1d_plan.  opts: NULL or as wave1d_plan with precision 0, nufft_w 0 and
- *                 local_weights 0 (others: WAVE1D_EINVAL).
+ *   dt, Nt, tol : as wave1d_plan.  opts: NULL or as wave1d_plan with precision 0 and nufft_w 0
+ *                 (others: WAVE1D_EINVAL), and local_weights:
+ *       0 (default): every instance in the joined tables above (stored weights);
+ *       1: every instance is a plan of its own without pair lists (opts.local_weights = 1 of
+ *          wave1d_plan), stepped as one branch of the step's graph, concurrently with the others;
+ *       2: per instance, from its positions: without pair lists when its largest block of springs
+ *          closer than dt has more than opts.max_block members, when more than 2^19 ordered pairs
+ *          of its springs are closer than delta = W dt, or when its stored weights would pass
+ *          what is left of opts.max_local_bytes; the joined tables otherwise.
+ *       The joined instances' step runs first (the one persistent launch), then the branches.
  * Every instance's derived sizes (K, W, fine grid) are the same, since they depend on dt, tol and
  * p only.  The springs' and receivers' global order is instance-major in the caller's order.
  * Returns WAVE1D_EINVAL / EDOMAIN / ENOMEM / ECUDA like wave1d_plan (message: wave1d_batch_strerror).
@@ -405,15 +415,20 @@ int wave1d_batch_plan(int n_inst, const int64_t* offsets, const double* x, const
 /*
  * Advance nsteps steps; u_rec[s * R + r] (R: all receivers) and, if sigma is not NULL,
  * sigma[s * M + j] (M: all springs) after step s + 1, device or host pointers as out_on_device.
- * Synchronises; WAVE1D_EDONE past Nt, WAVE1D_ENONFINITE if a density became non-finite.
+ * Synchronises; WAVE1D_EDONE past Nt, WAVE1D_ENONFINITE if a density became non-finite,
+ * WAVE1D_ENOTCONV if an instance without pair lists did not converge, WAVE1D_ETIMEOUT if a wait of
+ * the one-launch step ran out.
  */
 int wave1d_batch_solve(wave1d_batch_t plan, int64_t nsteps, double* u_rec, double* sigma,
                        int out_on_device);
 int wave1d_batch_destroy(wave1d_batch_t plan);
 const char* wave1d_batch_strerror(void);
-/* 1 if the plan's steps run as one persistent launch (see wave1d_batch_plan), 0 if as one launch
- * per pass, WAVE1D_EINVAL for a NULL plan. */
+/* 1 if the joined instances' steps run as one persistent launch (see wave1d_batch_plan), 0 if as
+ * one launch per pass or if no instance is joined, WAVE1D_EINVAL for a NULL plan. */
 int wave1d_batch_step_kernel(wave1d_batch_t plan);
+/* forms: host, n_inst values, 0 for an instance in the joined tables, 1 for one marched as its own
+ * plan without pair lists (opts.local_weights of wave1d_batch_plan).  WAVE1D_EINVAL for NULL. */
+int wave1d_batch_forms(wave1d_batch_t plan, int* forms);
 
 /* Free the plan and its device memory (synchronises).  NULL is accepted. */
 int wave1d_destroy(wave1d_plan_t plan);

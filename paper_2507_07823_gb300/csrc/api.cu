@@ -16,6 +16,7 @@
 
 #include "adjoint_host.h"
 #include "internal.h"
+#include "plan_hooks.h"
 #include "phases.cuh"
 #include "../../include/wave1d.h"
 
@@ -985,6 +986,43 @@ int wave1d_get_sigma(wave1d_plan_t p, double* out, int on_device) {
 // the plan's sizes.  Everything else a step uses is either fixed by the plan or rebuilt each step.
 // ---------------------------------------------------------------------------------------------
 }  // extern "C"
+
+namespace wave1d {
+
+int plan_hooks(wave1d_plan_t p, PlanHooks& out) {
+    if (!p) return fail(WAVE1D_EINVAL, "plan is NULL");
+    out.M = p->hp.P.M;
+    out.R = p->hp.P.R;
+    out.Nt = p->hp.P.Nt;
+    out.chunk = p->chunk;
+    out.rec_hist = p->dp.rec_hist;
+    out.status = p->dp.status;
+    return WAVE1D_OK;
+}
+
+int plan_branch_step(wave1d_plan_t p, cudaStream_t s, double* sig_hist) {
+    CK(cudaEventRecord(p->ev_fork, s));
+    CK(cudaStreamWaitEvent(p->s, p->ev_fork, 0));
+    p->started = true;
+    int rc = enqueue_step(p, p->n, nullptr, sig_hist);
+    if (rc) return rc;
+    CK(cudaEventRecord(p->ev_join, p->s));
+    CK(cudaStreamWaitEvent(s, p->ev_join, 0));
+    return WAVE1D_OK;
+}
+
+int plan_sigma_ring(wave1d_plan_t p, double** out) {
+    if (!p->d_sig_hist) {
+        int rc = dalloc(p, &p->d_sig_hist, (size_t)p->chunk * p->hp.P.M);
+        if (rc) return rc;
+    }
+    *out = p->d_sig_hist;
+    return WAVE1D_OK;
+}
+
+void plan_count_steps(wave1d_plan_t p, int64_t k) { p->n += k; }
+
+}  // namespace wave1d
 
 namespace {
 

@@ -21,6 +21,7 @@
 
 #include "batch_host.h"
 #include "internal.h"
+#include "plan_hooks.h"
 #include "grid_sync.cuh"
 #include "nufft_units.cuh"
 #include "phases.cuh"
@@ -283,6 +284,19 @@ struct wave1d_batch_s {
     size_t psmem = 0;
     unsigned* bar = nullptr;
     NuDev64 ns{}, nr{};
+    // all instances: springs and receivers (instance-major), steps planned, form of each instance
+    // (0: joined tables above, 1: its own plan without pair lists)
+    int n_inst = 0;
+    int64_t M_all = 0, R_all = 0, Nt = 0;
+    std::vector<int> form;
+    bool has_joined = false;
+    // the instances without pair lists: their plans, stepped as branches of the step graph
+    std::vector<wave1d_plan_t> sub;
+    std::vector<PlanHooks> sub_hooks;
+    std::vector<double*> sub_sig;
+    std::vector<int64_t> sub_moff, sub_roff;          // their first spring and receiver overall
+    // copies of the joined rings' columns to the output rows: (joined column, output column, width)
+    std::vector<int64_t> seg_m, seg_r;
 };
 
 namespace {
@@ -575,6 +589,83 @@ int enqueue_batch_step(wave1d_batch_t p, double* sig_hist) {
     return WAVE1D_OK;
 }
 
+// the joined instances on the device: tables, per-instance views, pulses, the batched NUFFT plans of
+// the springs and of the receivers, and the one-launch step
+int upload_joined_part(wave1d_batch_t p, const std::vector<int>& joined, const double* pulse, double tol,
+                       const wave1d_opts& o) {
+    const Params& P = p->bt.g.P;
+    int rc;
+    if ((rc = upload_joined(p)) || (rc = upload_views(p))) return rc;
+    std::vector<double> pl((size_t)3 * p->B);
+    for (int k = 0; k < p->B; k++) {
+        const int b = joined[k];
+        pl[3 * k] = pulse[3 * b];
+        pl[3 * k + 1] = pulse[3 * b + 1];
+        pl[3 * k + 2] = 1.0 / pulse[3 * b + 2];
+    }
+    if ((rc = bupload(p, pl, &p->pulse)) || (rc = bupload(p, p->bt.inst_of, &p->inst_of))) return rc;
+    if ((rc = balloc(p, &p->c, (size_t)P.M)) || (rc = balloc(p, &p->u, (size_t)P.M))) return rc;
+    // batched NUFFT plans of the springs and of the receivers: the instances' fine grids, kernel
+    // (width from tol, as each instance's plan) and deconvolution
+    rc = wave1d_nufft_plan_many(p->bt.g.x.data(), p->bt.moff.data(), p->B, P.K, tol, 0, (void*)p->s, &p->nu_s);
+    if (rc) return bfail(rc, std::string("batched NUFFT plan: ") + wave1d_nufft_strerror());
+    std::vector<int64_t> perm((size_t)P.M);
+    if ((rc = wave1d_nufft_perm(p->nu_s, perm.data()))) return bfail(rc, wave1d_nufft_strerror());
+    if ((rc = bupload(p, perm, &p->perm_s))) return rc;
+    if (P.R > 0) {
+        rc = wave1d_nufft_plan_many(p->bt.g.xr.data(), p->bt.roff.data(), p->B, P.K, tol, 0, (void*)p->s, &p->nu_r);
+        if (rc) return bfail(rc, std::string("batched NUFFT plan of the receivers: ") + wave1d_nufft_strerror());
+        std::vector<int64_t> permr((size_t)P.R);
+        if ((rc = wave1d_nufft_perm(p->nu_r, permr.data()))) return bfail(rc, wave1d_nufft_strerror());
+        if ((rc = bupload(p, permr, &p->perm_r)) || (rc = balloc(p, &p->ur, (size_t)P.R))) return rc;
+    }
+    if (cudaFuncSetAttribute(k_bhist_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_phase_smem(P.L2)) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_bfft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem_bytes(P.L1)) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_bhist_icols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)icols_phase_smem(P.L1)) !=
+            cudaSuccess)
+        return bfail(WAVE1D_ECUDA, "cannot size the shared memory of the history passes");
+    p->g.spin_limit = o.spin_limit > 0 ? (unsigned)o.spin_limit : (1u << 22);
+    return setup_batch_step(p, o);
+}
+
+// queue one step of every instance: the joined instances (one launch or one launch per pass), then
+// each instance without pair lists as a branch of its own, concurrent with the others
+int enqueue_all(wave1d_batch_t p, bool with_sigma) {
+    int rc;
+    if (p->has_joined && (rc = enqueue_batch_step(p, with_sigma ? p->sig_hist : nullptr))) return rc;
+    for (size_t i = 0; i < p->sub.size(); i++)
+        if ((rc = plan_branch_step(p->sub[i], p->s, with_sigma ? p->sub_sig[i] : nullptr)))
+            return bfail(rc, std::string("instance plan: ") + wave1d_strerror(rc));
+    return WAVE1D_OK;
+}
+
+// rows [row0, row0 + rows) of the rings (ring row slot0 ..) into rows first .. of the outputs
+int copy_rows(wave1d_batch_t p, double* u_rec, double* sigma, cudaMemcpyKind kind, int64_t slot0, int64_t first,
+              int64_t rows) {
+    const size_t d = sizeof(double);
+    if (p->has_joined) {
+        const Params& P = p->bt.g.P;
+        for (size_t i = 0; u_rec && i < p->seg_r.size(); i += 3)
+            BCK(cudaMemcpy2DAsync(u_rec + first * p->R_all + p->seg_r[i + 1], p->R_all * d,
+                                  p->g.rec_hist + slot0 * P.R + p->seg_r[i], P.R * d, p->seg_r[i + 2] * d, rows, kind, p->s));
+        for (size_t i = 0; sigma && i < p->seg_m.size(); i += 3)
+            BCK(cudaMemcpy2DAsync(sigma + first * p->M_all + p->seg_m[i + 1], p->M_all * d,
+                                  p->sig_hist + slot0 * P.M + p->seg_m[i], P.M * d, p->seg_m[i + 2] * d, rows, kind, p->s));
+    }
+    for (size_t k = 0; k < p->sub.size(); k++) {
+        const PlanHooks& h = p->sub_hooks[k];
+        if (u_rec && h.R > 0)
+            BCK(cudaMemcpy2DAsync(u_rec + first * p->R_all + p->sub_roff[k], p->R_all * d, h.rec_hist + slot0 * h.R,
+                                  h.R * d, h.R * d, rows, kind, p->s));
+        if (sigma)
+            BCK(cudaMemcpy2DAsync(sigma + first * p->M_all + p->sub_moff[k], p->M_all * d, p->sub_sig[k] + slot0 * h.M,
+                                  h.M * d, h.M * d, rows, kind, p->s));
+    }
+    return WAVE1D_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -601,8 +692,8 @@ int wave1d_batch_plan(int n_inst, const int64_t* offsets, const double* x, const
     if (o.p < 2 || o.p > 16 || (o.p % 2) != 0) return bfail(WAVE1D_EINVAL, "p must be even, 2..16");
     if (o.precision != 0 || o.nufft_w != 0)
         return bfail(WAVE1D_EINVAL, "the batched march runs in FP64 with the kernel width of its tolerance");
-    if (o.local_weights != 0)
-        return bfail(WAVE1D_EINVAL, "the batched march stores its local weights (local_weights = 0)");
+    if (o.local_weights < 0 || o.local_weights > 2)
+        return bfail(WAVE1D_EINVAL, "local_weights of a batched plan: 0 stored, 1 none, 2 chosen per instance");
     if (o.max_block <= 0) o.max_block = 4096;
     if (o.max_local_bytes <= 0) o.max_local_bytes = (int64_t)16 << 30;
 
@@ -612,26 +703,65 @@ int wave1d_batch_plan(int n_inst, const int64_t* offsets, const double* x, const
         wave1d_batch_destroy(p);
         return code;
     };
-    p->B = n_inst;
-    // the instances' own tables, then joined
-    std::vector<HostPlan> inst((size_t)n_inst);
+    p->n_inst = n_inst;
+    p->M_all = offsets[n_inst];
+    p->R_all = r_offsets ? r_offsets[n_inst] : 0;
+    p->Nt = Nt;
+    auto R_of = [&](int b) { return r_offsets ? r_offsets[b + 1] - r_offsets[b] : (int64_t)0; };
+    // the form of each instance: opts.local_weights, or (2) by its largest block and pair count
+    p->form.assign((size_t)n_inst, o.local_weights == 1 ? 1 : 0);
+    if (o.local_weights == 2) {
+        const double delta = window_steps(tol, o.gamma, o.W) * dt;
+        for (int b = 0; b < n_inst; b++) {
+            const InstanceShape sh = instance_shape(x + offsets[b], offsets[b + 1] - offsets[b], dt, delta);
+            if (sh.largest_block > o.max_block || sh.pairs > kBatchPairs) p->form[b] = 1;
+        }
+    }
+    // the joined instances' own tables (an instance over the remaining weight budget goes without
+    // pair lists under local_weights = 2), then joined
+    std::vector<HostPlan> inst;
+    std::vector<int> joined;
     std::string err;
     int64_t bytes = 0;
     for (int b = 0; b < n_inst; b++) {
+        if (p->form[b] != 0) continue;
         const int64_t M = offsets[b + 1] - offsets[b];
+        HostPlan h;
         int rc = build_host_plan(x + offsets[b], beta + offsets[b], M, WAVE1D_PERIODIC, dt, Nt, tol, o.p, o.gamma, o.W,
-                                 o.NL, o.Ng, 0, o.rbc_period, o.max_block, o.max_local_bytes - bytes, inst[b], err);
+                                 o.NL, o.Ng, 0, o.rbc_period, o.max_block, o.max_local_bytes - bytes, h, err);
+        if (rc == WAVE1D_ENOMEM && o.local_weights == 2) {
+            p->form[b] = 1;
+            continue;
+        }
         if (rc == WAVE1D_OK) {
             double none = 0.0;
-            const int64_t R = r_offsets ? r_offsets[b + 1] - r_offsets[b] : 0;
-            rc = build_receivers(inst[b], R ? xr + r_offsets[b] : &none, R, err);
+            const int64_t R = R_of(b);
+            rc = build_receivers(h, R ? xr + r_offsets[b] : &none, R, err);
         }
         if (rc) return cleanup(bfail(rc, "instance " + std::to_string(b) + ": " + err));
-        bytes += (int64_t)inst[b].litems.w.size() * 4;
+        bytes += (int64_t)h.litems.w.size() * 4;
+        inst.push_back(std::move(h));
+        joined.push_back(b);
     }
-    if (int rc = join_instances(inst, p->bt, err)) return cleanup(bfail(rc, err));
+    p->B = (int)joined.size();
+    p->has_joined = p->B > 0;
+    if (p->has_joined) {
+        if (int rc = join_instances(inst, p->bt, err)) return cleanup(bfail(rc, err));
+        // output columns of the joined rings, runs of consecutive instances merged
+        for (int k = 0; k < p->B; k++) {
+            const int b = joined[k];
+            const int64_t add[2][3] = {{p->bt.moff[k], offsets[b], offsets[b + 1] - offsets[b]},
+                                       {p->bt.roff[k], r_offsets ? r_offsets[b] : 0, R_of(b)}};
+            for (int t = 0; t < 2; t++) {
+                std::vector<int64_t>& seg = t ? p->seg_r : p->seg_m;
+                if (add[t][2] == 0) continue;
+                const size_t n = seg.size();
+                if (n && seg[n - 3] + seg[n - 1] == add[t][0] && seg[n - 2] + seg[n - 1] == add[t][1]) seg[n - 1] += add[t][2];
+                else seg.insert(seg.end(), add[t], add[t] + 3);
+            }
+        }
+    }
     inst.clear();
-    const Params& P = p->bt.g.P;
     p->user = (cudaStream_t)o.stream;
     if (cudaGetDevice(&p->device) != cudaSuccess) return cleanup(bfail(WAVE1D_ECUDA, "no CUDA device"));
     cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
@@ -642,63 +772,64 @@ int wave1d_batch_plan(int n_inst, const int64_t* offsets, const double* x, const
     if (cudaEventRecord(p->ev_in, p->user) != cudaSuccess || cudaStreamWaitEvent(p->s, p->ev_in, 0) != cudaSuccess)
         return cleanup(bfail(WAVE1D_ECUDA, "stream ordering failed"));
     int rc;
-    if ((rc = upload_joined(p)) || (rc = upload_views(p))) return cleanup(rc);
-    std::vector<double> pl((size_t)3 * n_inst);
+    if (p->has_joined) {
+        if ((rc = upload_joined_part(p, joined, pulse, tol, o))) return cleanup(rc);
+    }
+    // the instances without pair lists: one plan each
+    wave1d_opts so = o;
+    so.local_weights = 1;
     for (int b = 0; b < n_inst; b++) {
-        pl[3 * b] = pulse[3 * b];
-        pl[3 * b + 1] = pulse[3 * b + 1];
-        pl[3 * b + 2] = 1.0 / pulse[3 * b + 2];
+        if (p->form[b] != 1) continue;
+        wave1d_plan_t q = nullptr;
+        const std::string at = "instance " + std::to_string(b) + ": ";
+        rc = wave1d_plan(x + offsets[b], beta + offsets[b], offsets[b + 1] - offsets[b], WAVE1D_PERIODIC, dt, Nt, tol, &so,
+                         &q);
+        if (rc) return cleanup(bfail(rc, at + wave1d_strerror(rc)));
+        p->sub.push_back(q);
+        if ((rc = wave1d_set_incident_gaussians(q, 1, pulse + 3 * b, pulse + 3 * b + 1, pulse + 3 * b + 2)) ||
+            (R_of(b) > 0 && (rc = wave1d_set_receivers(q, xr + r_offsets[b], R_of(b)))))
+            return cleanup(bfail(rc, at + wave1d_strerror(rc)));
+        PlanHooks hk;
+        if ((rc = plan_hooks(q, hk))) return cleanup(bfail(rc, at + wave1d_strerror(rc)));
+        if (hk.chunk != p->chunk) return cleanup(bfail(WAVE1D_EINVAL, at + "ring length differs from the batch's"));
+        p->sub_hooks.push_back(hk);
+        p->sub_sig.push_back(nullptr);
+        p->sub_moff.push_back(offsets[b]);
+        p->sub_roff.push_back(r_offsets ? r_offsets[b] : 0);
     }
-    if ((rc = bupload(p, pl, &p->pulse)) || (rc = bupload(p, p->bt.inst_of, &p->inst_of))) return cleanup(rc);
-    if ((rc = balloc(p, &p->c, (size_t)P.M)) || (rc = balloc(p, &p->u, (size_t)P.M))) return cleanup(rc);
-    // batched NUFFT plans of the springs and of the receivers: the instances' fine grids, kernel
-    // (width from tol, as each instance's plan) and deconvolution
-    rc = wave1d_nufft_plan_many(p->bt.g.x.data(), p->bt.moff.data(), n_inst, P.K, tol, 0, (void*)p->s, &p->nu_s);
-    if (rc) return cleanup(bfail(rc, std::string("batched NUFFT plan: ") + wave1d_nufft_strerror()));
-    std::vector<int64_t> perm((size_t)P.M);
-    if ((rc = wave1d_nufft_perm(p->nu_s, perm.data()))) return cleanup(bfail(rc, wave1d_nufft_strerror()));
-    if ((rc = bupload(p, perm, &p->perm_s))) return cleanup(rc);
-    if (P.R > 0) {
-        rc = wave1d_nufft_plan_many(p->bt.g.xr.data(), p->bt.roff.data(), n_inst, P.K, tol, 0, (void*)p->s, &p->nu_r);
-        if (rc) return cleanup(bfail(rc, std::string("batched NUFFT plan of the receivers: ") + wave1d_nufft_strerror()));
-        std::vector<int64_t> permr((size_t)P.R);
-        if ((rc = wave1d_nufft_perm(p->nu_r, permr.data()))) return cleanup(bfail(rc, wave1d_nufft_strerror()));
-        if ((rc = bupload(p, permr, &p->perm_r)) || (rc = balloc(p, &p->ur, (size_t)P.R))) return cleanup(rc);
-    }
-    if (cudaFuncSetAttribute(k_bhist_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_phase_smem(P.L2)) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(k_bfft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fft_smem_bytes(P.L1)) !=
-            cudaSuccess ||
-        cudaFuncSetAttribute(k_bhist_icols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)icols_phase_smem(P.L1)) !=
-            cudaSuccess)
-        return cleanup(bfail(WAVE1D_ECUDA, "cannot size the shared memory of the history passes"));
-    p->g.spin_limit = o.spin_limit > 0 ? (unsigned)o.spin_limit : (1u << 22);
-    if ((rc = setup_batch_step(p, o))) return cleanup(rc);
     if (cudaStreamSynchronize(p->s) != cudaSuccess) return cleanup(bfail(WAVE1D_ECUDA, "plan upload failed"));
-    // the device holds the joined weights now: release the host copies
-    std::vector<float>().swap(p->bt.g.litems.w);
-    std::vector<float>().swap(p->bt.g.ritems.w);
-    std::vector<double>().swap(p->bt.g.inv);
+    if (p->has_joined) {
+        // the device holds the joined weights now: release the host copies
+        std::vector<float>().swap(p->bt.g.litems.w);
+        std::vector<float>().swap(p->bt.g.ritems.w);
+        std::vector<double>().swap(p->bt.g.inv);
+    }
     *out = p;
     return WAVE1D_OK;
 }
 
 int wave1d_batch_solve(wave1d_batch_t p, int64_t nsteps, double* u_rec, double* sigma, int out_on_device) {
     if (!p || nsteps < 0) return bfail(WAVE1D_EINVAL, "bad solve arguments");
-    const Params& P = p->bt.g.P;
-    if (p->n + nsteps > P.Nt) return bfail(WAVE1D_EDONE, "nsteps beyond the Nt of the plan");
+    if (p->n + nsteps > p->Nt) return bfail(WAVE1D_EDONE, "nsteps beyond the Nt of the plan");
     BCK(cudaSetDevice(p->device));
     BCK(cudaEventRecord(p->ev_in, p->user));
     BCK(cudaStreamWaitEvent(p->s, p->ev_in, 0));
-    if (sigma && !p->sig_hist) {
-        int rc = balloc(p, &p->sig_hist, (size_t)p->chunk * P.M);
-        if (rc) return rc;
+    if (sigma) {
+        if (p->has_joined && !p->sig_hist) {
+            int rc = balloc(p, &p->sig_hist, (size_t)p->chunk * p->bt.g.P.M);
+            if (rc) return rc;
+        }
+        for (size_t k = 0; k < p->sub.size(); k++)
+            if (!p->sub_sig[k]) {
+                int rc = plan_sigma_ring(p->sub[k], &p->sub_sig[k]);
+                if (rc) return bfail(rc, std::string("instance plan: ") + wave1d_strerror(rc));
+            }
     }
     cudaGraphExec_t& ge = p->graph[sigma ? 1 : 0];
     if (!ge) {
         cudaGraph_t graph;
         BCK(cudaStreamBeginCapture(p->s, cudaStreamCaptureModeThreadLocal));
-        int rc = enqueue_batch_step(p, sigma ? p->sig_hist : nullptr);
+        int rc = enqueue_all(p, sigma != nullptr);
         cudaError_t e = cudaStreamEndCapture(p->s, &graph);
         if (rc) return rc;
         if (e != cudaSuccess) return bfail(WAVE1D_ECUDA, std::string("graph capture: ") + cudaGetErrorString(e));
@@ -714,31 +845,43 @@ int wave1d_batch_solve(wave1d_batch_t p, int64_t nsteps, double* u_rec, double* 
         if (p->n % p->chunk == 0 || i == nsteps - 1) {
             // rows (n - pending) mod chunk .. of the chunk buffers: contiguous, they never wrap
             const int64_t slot0 = (p->n - pending) % p->chunk, first = i + 1 - pending;
-            if (u_rec && P.R > 0)
-                BCK(cudaMemcpyAsync(u_rec + first * P.R, p->g.rec_hist + slot0 * P.R, pending * P.R * sizeof(double),
-                                    kind, p->s));
-            if (sigma)
-                BCK(cudaMemcpyAsync(sigma + first * P.M, p->sig_hist + slot0 * P.M, pending * P.M * sizeof(double),
-                                    kind, p->s));
+            int rc = copy_rows(p, p->R_all > 0 ? u_rec : nullptr, sigma, kind, slot0, first, pending);
+            if (rc) return rc;
             pending = 0;
         }
     }
+    for (wave1d_plan_t q : p->sub) plan_count_steps(q, nsteps);
     BCK(cudaEventRecord(p->ev_out, p->s));
     BCK(cudaStreamWaitEvent(p->user, p->ev_out, 0));
-    int st = 0;
-    BCK(cudaMemcpyAsync(&st, p->g.status, sizeof(int), cudaMemcpyDeviceToHost, p->s));
+    // status words: the joined instances', then each plan's
+    std::vector<int> st(1 + p->sub.size(), 0);
+    if (p->has_joined) BCK(cudaMemcpyAsync(&st[0], p->g.status, sizeof(int), cudaMemcpyDeviceToHost, p->s));
+    for (size_t k = 0; k < p->sub.size(); k++)
+        BCK(cudaMemcpyAsync(&st[k + 1], p->sub_hooks[k].status, sizeof(int), cudaMemcpyDeviceToHost, p->s));
     BCK(cudaStreamSynchronize(p->s));
-    if (st != 0) return bfail(st, "a density became non-finite during the march");
+    for (int v : st) {
+        if (v == WAVE1D_ETIMEOUT) return bfail(v, "a bounded wait between the blocks of the batched step kernel ran out");
+        if (v == WAVE1D_ENOTCONV)
+            return bfail(v, "the Jacobi sweeps of an instance without pair lists did not converge");
+        if (v != 0) return bfail(v, "a density became non-finite during the march");
+    }
     return WAVE1D_OK;
 }
 
 int wave1d_batch_step_kernel(wave1d_batch_t p) { return p ? (p->persist ? 1 : 0) : WAVE1D_EINVAL; }
+
+int wave1d_batch_forms(wave1d_batch_t p, int* forms) {
+    if (!p || !forms) return bfail(WAVE1D_EINVAL, "plan or forms is NULL");
+    for (int b = 0; b < p->n_inst; b++) forms[b] = p->form[b];
+    return WAVE1D_OK;
+}
 
 int wave1d_batch_destroy(wave1d_batch_t p) {
     if (!p) return WAVE1D_OK;
     if (p->s) cudaStreamSynchronize(p->s);
     for (auto& g : p->graph)
         if (g) cudaGraphExecDestroy(g);
+    for (wave1d_plan_t q : p->sub) wave1d_destroy(q);
     if (p->nu_s) wave1d_nufft_destroy(p->nu_s);
     if (p->nu_r) wave1d_nufft_destroy(p->nu_r);
     for (void* a : p->allocs) cudaFree(a);

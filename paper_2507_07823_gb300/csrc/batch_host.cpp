@@ -2,6 +2,7 @@
 #include "batch_host.h"
 
 #include <algorithm>
+#include <cmath>
 
 #include "../../include/wave1d.h"
 
@@ -126,6 +127,45 @@ int join_instances(const std::vector<HostPlan>& inst, BatchTables& out, std::str
     }
     g.blk_inv_off.push_back((int64_t)g.inv.size());
     return WAVE1D_OK;
+}
+
+InstanceShape instance_shape(const double* x, int64_t M, double dt, double delta) {
+    InstanceShape out;
+    if (M < 1) return out;
+    const double two_pi = 2.0 * 3.14159265358979323846;
+    std::vector<double> v((size_t)M);
+    for (int64_t j = 0; j < M; j++) {
+        double a = std::fmod(x[j] + 0.5 * two_pi, two_pi);
+        if (a < 0) a += two_pi;
+        v[j] = a - 0.5 * two_pi;
+    }
+    std::sort(v.begin(), v.end());
+    // gap g_i between sorted neighbours i and i + 1, the last one across the seam
+    auto gap = [&](int64_t i) { return i + 1 < M ? v[i + 1] - v[i] : v[0] + two_pi - v[M - 1]; };
+    int64_t start = -1;
+    for (int64_t i = 0; i < M && start < 0; i++)
+        if (!(gap(i) < dt)) start = i;
+    if (start < 0 || M == 1) {
+        out.largest_block = M;
+    } else {
+        // walk the circle from the spring after a break; a run ends at each gap of dt or more
+        int64_t run = 1;
+        for (int64_t k = 1; k <= M; k++) {
+            const int64_t i = (start + k) % M;
+            out.largest_block = std::max(out.largest_block, run);
+            run = gap(i) < dt ? run + 1 : 1;
+        }
+    }
+    // sources l != j within delta of j: the sorted circle doubled, each unordered pair once
+    int64_t hi = 0, pairs = 0;
+    for (int64_t j = 0; j < M; j++) {
+        if (hi < j + 1) hi = j + 1;
+        auto pos = [&](int64_t e) { return e < M ? v[e] : v[e - M] + two_pi; };
+        while (hi < j + M && pos(hi) - v[j] < delta) hi++;
+        pairs += hi - (j + 1);
+    }
+    out.pairs = 2 * pairs;
+    return out;
 }
 
 }  // namespace wave1d

@@ -25,4 +25,16 @@ struct BatchTables {
 };
 int join_instances(const std::vector<HostPlan>& inst, BatchTables& out, std::string& err);
 
+// The two sizes that choose an instance's form in a batched plan with opts.local_weights = 2, from
+// its positions alone (periodic box, positions wrapped into [-pi, pi)):
+//   largest_block: members of the largest block of springs closer than dt (eq. linearSystem's
+//     nearby graph; in 1D the runs of sorted neighbours less than dt apart, across the seam too);
+//   pairs: ordered (target, source) pairs of distinct springs closer than delta (the local sum's).
+// An instance is planned without pair lists when largest_block > max_block or pairs > kBatchPairs.
+struct InstanceShape {
+    int64_t largest_block = 0, pairs = 0;
+};
+InstanceShape instance_shape(const double* x, int64_t M, double dt, double delta);
+constexpr int64_t kBatchPairs = (int64_t)1 << 19;
+
 }  // namespace wave1d

@@ -172,6 +172,8 @@ inline size_t fft_smem_bytes(int N) { return (size_t)(N + N / 2) * 16; }
 // threads of a block of the one-launch step kernel
 constexpr int kStepThreads = 256;
 
+// window width in steps: W given, else ceil(2 ln(1/tol) / (pi gamma)) (eqs. b, W)
+int window_steps(double tol, double gamma, int W);
 // Returns 0 or a negative wave1d_status; fills err with a message on failure.
 int build_host_plan(const double* x, const double* beta, int64_t M, int bc, double dt, int64_t Nt,
                     double tol, int p, double gamma, int W, int NL, int Ng, int nufft_w,

@@ -6,6 +6,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <functional>
+#include <mutex>
 #include <numeric>
 #include <thread>
 
@@ -489,6 +490,41 @@ int build_local_and_blocks(const Params& P, const Window& win, HostPlan& hp, int
 void range_windows(HostPlan& hp);
 }  // namespace
 
+// W = 2 b / (pi gamma) rounded up, b = ln(1/tol) (eqs. b, W), unless given
+int window_steps(double tol, double gamma, int W) {
+    return W > 0 ? W : (int)std::ceil(2.0 * std::log(1.0 / tol) / (kPi * gamma));
+}
+
+// The range tables depend on dt, delta, b, W, N_L, m_max and p only (and the interval cap), so plans
+// that share them (the instances of a batched plan) build them once: the last few are kept.
+static void range_tables_cached(const Params& P, RangeTables& rt) {
+    struct Entry {
+        double dt, delta, b, cap;
+        int W, NL, m_max, p;
+        RangeTables rt;
+    };
+    static std::mutex mu;
+    static std::vector<Entry> cache;
+    const char* env = std::getenv("WAVE1D_RANGE_WIDTH");
+    const double cap = env ? std::atof(env) : -1.0;
+    auto same = [&](const Entry& e) {
+        return e.dt == P.dt && e.delta == P.delta && e.b == P.b && e.cap == cap && e.W == P.W && e.NL == P.NL &&
+               e.m_max == P.m_max && e.p == P.p;
+    };
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        for (const Entry& e : cache)
+            if (same(e)) {
+                rt = e.rt;
+                return;
+            }
+    }
+    build_range_tables(P, rt);
+    std::lock_guard<std::mutex> lock(mu);
+    if (cache.size() >= 4) cache.erase(cache.begin());
+    cache.push_back(Entry{P.dt, P.delta, P.b, cap, P.W, P.NL, P.m_max, P.p, rt});
+}
+
 // ---------------------------------------------------------------------------------------------
 int build_host_plan(const double* x_in, const double* beta_in, int64_t M, int bc, double dt,
                     int64_t Nt, double tol, int p, double gamma, int W, int NL, int Ng, int nufft_w,
@@ -504,7 +540,7 @@ int build_host_plan(const double* x_in, const double* beta_in, int64_t M, int bc
     P.gamma = gamma;
     P.b = std::log(1.0 / tol);                                        // eq. b
     P.K = (int)std::floor(kPi / dt);                                  // eq. Kdt (floor)
-    P.W = W > 0 ? W : (int)std::ceil(2.0 * P.b / (kPi * gamma));      // W = 2b/(pi gamma)
+    P.W = window_steps(tol, gamma, W);
     P.delta = P.W * dt;                                               // eq. W
     P.m_max = P.W + (p + 1) / 2;                                      // Sec. 4.1
     P.NL = NL > 0 ? NL : P.W;                                         // Sec. 4.3
@@ -661,7 +697,7 @@ int build_host_plan(const double* x_in, const double* beta_in, int64_t M, int bc
     if (range) {
         // no pair lists: index windows, the weights as polynomials of the distance
         hp.range = true;
-        build_range_tables(P, hp.rt);
+        range_tables_cached(P, hp.rt);
         range_windows(hp);
     } else {
         int rc = build_local_and_blocks(P, win, hp, max_block, max_local_bytes, err);

@@ -47,7 +47,8 @@ EXPORTED = ["wave1d_opts_default", "wave1d_plan", "wave1d_set_incident_gaussians
             "wave1d_nufft_interp", "wave1d_nufft_type1", "wave1d_nufft_type2", "wave1d_nufft_destroy",
             "wave1d_nufft_strerror", "wave1d_adjoint", "wave1d_checkpoint_size", "wave1d_solve_checkpointed",
             "wave1d_adjoint_checkpointed", "wave1d_batch_plan", "wave1d_batch_solve",
-            "wave1d_batch_destroy", "wave1d_batch_strerror", "wave1d_batch_step_kernel", "wave1d_nufft_autotune"]
+            "wave1d_batch_destroy", "wave1d_batch_strerror", "wave1d_batch_step_kernel", "wave1d_batch_forms",
+            "wave1d_nufft_autotune"]
 
 WAVE1D_NSTAGE = 9
 STAGES = ["local", "spread", "fft_fwd", "modes", "rbc", "fft_inv", "interp", "solve", "receivers"]
@@ -134,6 +135,7 @@ def lib(path: str = LIB_PATH):
         L.wave1d_batch_solve.argtypes = [P, ctypes.c_int64, _D, _D, ctypes.c_int]
         L.wave1d_batch_destroy.argtypes = [P]
         L.wave1d_batch_step_kernel.argtypes = [P]
+        L.wave1d_batch_forms.argtypes = [P, ctypes.POINTER(ctypes.c_int)]
         L.wave1d_batch_strerror.argtypes = []
         L.wave1d_batch_strerror.restype = ctypes.c_char_p
         L.wave1d_nufft_strerror.argtypes = []
@@ -542,8 +544,18 @@ class Batch:
 
     @property
     def one_launch(self):
-        """True if the plan's steps run as one persistent launch."""
+        """True if the joined instances' steps run as one persistent launch."""
         return lib().wave1d_batch_step_kernel(self.h) == 1
+
+    @property
+    def forms(self):
+        """Per instance: 0 in the joined tables (stored weights), 1 marched as its own plan without
+        pair lists (`local_weights` = 1, or 2 with the choice made per instance)."""
+        f = np.zeros(len(self.offsets) - 1, dtype=np.int32)
+        st = lib().wave1d_batch_forms(self.h, f.ctypes.data_as(ctypes.POINTER(ctypes.c_int)))
+        if st != WAVE1D_OK:
+            raise Wave1DError(st, "wave1d_batch_forms: " + lib().wave1d_batch_strerror().decode())
+        return f
 
     def solve(self, nsteps, with_sigma=True):
         u = np.zeros((nsteps, max(self.R, 1)))

@@ -128,8 +128,10 @@ def test_batch_argument_validation_without_gpu(lib):
     o.precision = 1                                                     # the batched march is FP64
     assert plan([0, 1, 3], 2, opts=o) == wave1d.WAVE1D_EINVAL
     o = wave1d.wave1d_opts_default()
-    o.local_weights = 1                                                 # ... with stored local weights
+    o.local_weights = 3                                                 # forms 0, 1 or 2 only
     assert plan([0, 1, 3], 2, opts=o) == wave1d.WAVE1D_EINVAL
+    forms = (ctypes.c_int * 2)()
+    assert L.wave1d_batch_forms(None, forms) == wave1d.WAVE1D_EINVAL
     assert L.wave1d_batch_destroy(None) == 0
     assert isinstance(L.wave1d_batch_strerror(), bytes)
 

@@ -77,3 +77,68 @@ def test_one_launch_step_equals_the_per_pass_launches():
     (s1, u1), (s0, u0) = out
     assert np.max(np.abs(s0)) > 1e-3
     assert np.array_equal(s1, s0) and np.array_equal(u1, u0)
+
+
+def _dense(name, M, seed):
+    return W.make(name, M=M, bc=W.PERIODIC, dt=0.01, Nt=300, tol=1e-10, p=8, seed=seed, amp=(1.0,),
+                  center=(-2.0,), width=(0.1,), R=3)
+
+
+def _own_plan(w, n, lw):
+    plan = wave1d.Plan.from_workload(w, local_weights=lw)
+    try:
+        return plan.solve(n)
+    finally:
+        plan.close()
+
+
+def test_instances_chosen_without_pair_lists_equal_their_own_plans():
+    """local_weights = 2: an instance whose largest block of springs closer than dt passes
+    opts.max_block (two dense ones, M = 3000 and 2000, about five springs per dt) is marched as its
+    own plan without pair lists, a branch of the step graph beside the joined instances' one
+    launch; its densities and receiver fields equal that plan's own march bit for bit (the same
+    kernels in the same order), and the joined instances keep their one-instance agreement."""
+    ws = _instances()
+    ws = ws[:3] + [_dense("dense0", 3000, 7)] + ws[3:] + [_dense("dense1", 2000, 8)]
+    batch = wave1d.Batch(ws, local_weights=2, max_block=64)
+    try:
+        forms = batch.forms
+        assert list(forms) == [0, 0, 0, 1, 0, 0, 0, 1]
+        assert batch.one_launch
+        s, u = batch.solve(200)
+    finally:
+        batch.close()
+    assert np.max(np.abs(s[:, batch.offsets[3]:batch.offsets[4]])) > 1e-3
+    for i, w in enumerate(ws):
+        sb = s[:, batch.offsets[i]:batch.offsets[i + 1]]
+        ub = u[:, batch.r_offsets[i]:batch.r_offsets[i + 1]]
+        s1, u1 = _own_plan(w, 200, int(forms[i]))
+        if forms[i]:
+            assert np.array_equal(sb, s1) and np.array_equal(ub, u1), i
+        else:
+            assert _rel(sb, s1) < 1e-12 and _rel(ub, u1) < 1e-12, i
+
+
+def test_every_instance_without_pair_lists():
+    """local_weights = 1: every instance its own plan without pair lists, all of them branches of
+    one step graph; each equals its own march bit for bit, the smallest ones also the oracle at
+    1e-9, and the batch is reproducible from run to run."""
+    ws = _instances()[1:4] + [_dense("dense", 1500, 9)]
+    out = []
+    for _ in range(2):
+        batch = wave1d.Batch(ws, local_weights=1)
+        try:
+            assert list(batch.forms) == [1] * len(ws) and not batch.one_launch
+            out.append(batch.solve(150))
+            offs, roffs = batch.offsets, batch.r_offsets
+        finally:
+            batch.close()
+    (s, u), (s2, u2) = out
+    assert np.array_equal(s, s2) and np.array_equal(u, u2)
+    for i, w in enumerate(ws):
+        sb, ub = s[:, offs[i]:offs[i + 1]], u[:, roffs[i]:roffs[i + 1]]
+        s1, u1 = _own_plan(w, 150, 1)
+        assert np.array_equal(sb, s1) and np.array_equal(ub, u1), i
+        if w.M <= 200:
+            s_ref, u_ref = wfp.from_workload(w).run(150)
+            assert _rel(sb, s_ref[1:]) < 1e-9 and _rel(ub, u_ref[1:]) < 1e-9, i
