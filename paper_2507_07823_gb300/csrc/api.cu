@@ -1000,12 +1000,13 @@ int plan_hooks(wave1d_plan_t p, PlanHooks& out) {
     return WAVE1D_OK;
 }
 
-int plan_branch_step(wave1d_plan_t p, cudaStream_t s, double* sig_hist) {
-    CK(cudaEventRecord(p->ev_fork, s));
-    CK(cudaStreamWaitEvent(p->s, p->ev_fork, 0));
+int plan_branch_step(wave1d_plan_t p, cudaEvent_t fork, double* sig_hist) {
+    CK(cudaStreamWaitEvent(p->s, fork, 0));
     p->started = true;
-    int rc = enqueue_step(p, p->n, nullptr, sig_hist);
-    if (rc) return rc;
+    return enqueue_step(p, p->n, nullptr, sig_hist);
+}
+
+int plan_branch_join(wave1d_plan_t p, cudaStream_t s) {
     CK(cudaEventRecord(p->ev_join, p->s));
     CK(cudaStreamWaitEvent(s, p->ev_join, 0));
     return WAVE1D_OK;

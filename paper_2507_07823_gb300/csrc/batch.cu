@@ -267,7 +267,7 @@ struct wave1d_batch_s {
     DevPlan* d_views = nullptr;        // one view per instance for the history phases
     std::vector<void*> allocs;
     cudaStream_t user = nullptr, s = nullptr;
-    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_fork = nullptr;
     int device = 0, sms = 1, B = 0, chunk = 32;
     int64_t n = 0;
     wave1d_nufft_t nu_s = nullptr, nu_r = nullptr;
@@ -635,9 +635,13 @@ int upload_joined_part(wave1d_batch_t p, const std::vector<int>& joined, const d
 int enqueue_all(wave1d_batch_t p, bool with_sigma) {
     int rc;
     if (p->has_joined && (rc = enqueue_batch_step(p, with_sigma ? p->sig_hist : nullptr))) return rc;
+    if (p->sub.empty()) return WAVE1D_OK;
+    BCK(cudaEventRecord(p->ev_fork, p->s));
     for (size_t i = 0; i < p->sub.size(); i++)
-        if ((rc = plan_branch_step(p->sub[i], p->s, with_sigma ? p->sub_sig[i] : nullptr)))
+        if ((rc = plan_branch_step(p->sub[i], p->ev_fork, with_sigma ? p->sub_sig[i] : nullptr)))
             return bfail(rc, std::string("instance plan: ") + wave1d_strerror(rc));
+    for (wave1d_plan_t q : p->sub)
+        if ((rc = plan_branch_join(q, p->s))) return bfail(rc, std::string("instance plan: ") + wave1d_strerror(rc));
     return WAVE1D_OK;
 }
 
@@ -767,7 +771,8 @@ int wave1d_batch_plan(int n_inst, const int64_t* offsets, const double* x, const
     cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
     if (cudaStreamCreateWithFlags(&p->s, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming) != cudaSuccess)
         return cleanup(bfail(WAVE1D_ECUDA, "stream/event creation failed"));
     if (cudaEventRecord(p->ev_in, p->user) != cudaSuccess || cudaStreamWaitEvent(p->s, p->ev_in, 0) != cudaSuccess)
         return cleanup(bfail(WAVE1D_ECUDA, "stream ordering failed"));
@@ -887,6 +892,7 @@ int wave1d_batch_destroy(wave1d_batch_t p) {
     for (void* a : p->allocs) cudaFree(a);
     if (p->ev_in) cudaEventDestroy(p->ev_in);
     if (p->ev_out) cudaEventDestroy(p->ev_out);
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
     if (p->s) cudaStreamDestroy(p->s);
     delete p;
     return WAVE1D_OK;

@@ -19,10 +19,13 @@ struct PlanHooks {
 };
 int plan_hooks(wave1d_plan_t p, PlanHooks& out);
 
-// Queue plan p's next ordinary step on its private stream as a branch of work on stream s: p's
-// stream waits for what s has queued so far, and s for the step.  Valid inside a capture on s.
-// sig_hist: NULL, or the plan's density ring (plan_sigma_ring).
-int plan_branch_step(wave1d_plan_t p, cudaStream_t s, double* sig_hist);
+// Queue plan p's next ordinary step on its private stream as a branch: the stream waits on event
+// fork (recorded on the stream the branches leave), then the step.  plan_branch_join makes stream
+// s wait for that step.  Valid inside a capture on the forking stream; fork all branches before
+// joining any, so that they run concurrently.  sig_hist: NULL, or the plan's density ring
+// (plan_sigma_ring).
+int plan_branch_step(wave1d_plan_t p, cudaEvent_t fork, double* sig_hist);
+int plan_branch_join(wave1d_plan_t p, cudaStream_t s);
 
 // The plan's chunk x M density ring (caller order), allocated on first use.
 int plan_sigma_ring(wave1d_plan_t p, double** out);
