@@ -133,6 +133,51 @@ __device__ __forceinline__ void rs_pairs(const float* sE, const float4* sMeta, c
     }
 }
 
+// The pairs of one side for one target in a chunk where e-vectors would hardly be shared (the
+// chunk's interval range holds more than twice as many (source, interval) e-vectors as it has
+// pairs, as where springs lie farther apart than the intervals are wide): each pair folds its own
+// source's densities on its interval (the same e-vector, bit for bit, as the shared fold) and
+// evaluates it, with no interval windows.  Sources k0 .. k1 - 1 of the chunk.
+template <int S>
+__device__ __forceinline__ void rs_direct(const float4* sMeta, const float2* sSig, const float* ivt, const int* cell,
+                                          float cscale, int nint, int iv_dt, const float4* __restrict__ coef,
+                                          const int32_t* __restrict__ mr, int nm, int k0, int k1, int lbj, int nbl,
+                                          int nbc, float bh, float bl, rs::Track& tr, float& a0h, float& a0l,
+                                          float& a1h, float& a1l) {
+    for (int k = k0; k < k1; k++) {
+        const float4 mt = sMeta[k];
+        const int e = __float_as_int(mt.z), lohi = __float_as_int(mt.w);
+        const int lo = lohi & 0x7fff, hi = lohi >> 16;
+        if (lo > hi || (S < 0 ? e >= lbj : e < lbj)) continue;
+        float zh, zl;
+        rs::z_of<S>(tr, mt.x, mt.y, zh, zl);
+        if (fabsf(zh) > rs::kZTol) rs::walk<S>(ivt, cell, cscale, nint, bh, bl, mt.x, mt.y, tr, zh, zl);
+        if (lohi & 0x8000)
+            rs::near_side<S>(ivt, iv_dt, (unsigned)(e - nbl) < (unsigned)nbc, bh, bl, mt.x, mt.y, tr, zh, zl);
+        if (!(fabsf(zh) <= rs::kZTol && tr.iv >= lo && tr.iv <= hi)) continue;
+        rs::EVec ev;
+        rs::evec_zero(ev);
+        const int m0 = __ldg(mr + 2 * tr.iv), m1 = __ldg(mr + 2 * tr.iv + 1);
+        const float4* c = coef + (size_t)tr.iv * nm * 3;
+        const int kk = k & (kRsChunk - 1);
+#pragma unroll 1
+        for (int m = m0; m <= m1; m++) {
+            const float2 sg = sSig[m * kRsChunk + kk];
+            const float4 c01 = __ldg(c + 3 * m), c23 = __ldg(c + 3 * m + 1), c47 = __ldg(c + 3 * m + 2);
+            rs::acc_mac(ev.e0h, ev.e0l, c01.x, c01.y, sg.x, sg.y);
+            rs::acc_mac(ev.e1h, ev.e1l, c01.z, c01.w, sg.x, sg.y);
+            ev.e2 = rs::fma_(c23.y, sg.x, rs::fma_(c23.x, sg.x, ev.e2));
+            ev.e3 = rs::fma_(c23.w, sg.x, rs::fma_(c23.z, sg.x, ev.e3));
+            ev.e4 = rs::fma_(c47.x, sg.x, ev.e4);
+            ev.e5 = rs::fma_(c47.y, sg.x, ev.e5);
+            ev.e6 = rs::fma_(c47.z, sg.x, ev.e6);
+            ev.e7 = rs::fma_(c47.w, sg.x, ev.e7);
+        }
+        if (k & 1) rs::evec_eval_v(ev, zh, zl, a1h, a1l);
+        else rs::evec_eval_v(ev, zh, zl, a0h, a0l);
+    }
+}
+
 __global__ void __launch_bounds__(kRsTargets, 3) k_rs_local(DevPlan P, RangeDev R) {
     extern __shared__ __align__(16) float rs_sm[];
     float* sE = rs_sm;
@@ -142,6 +187,10 @@ __global__ void __launch_bounds__(kRsTargets, 3) k_rs_local(DevPlan P, RangeDev 
     // interval range), and the interval union of each chunk
     __shared__ float4 sMeta[kRsTargets];
     __shared__ int sU[2][kRsTargets / kRsChunk];
+    // targets' positions relative to the first (float, sorted), and per chunk an estimate of its
+    // pairs (sources' targets within delta) for the choice between shared and per-pair e-vectors
+    __shared__ float sT[kRsTargets];
+    __shared__ int sP[kRsTargets / kRsChunk];
 
     const int64_t M = P.M;
     const int64_t n = load_step(P);
@@ -169,6 +218,7 @@ __global__ void __launch_bounds__(kRsTargets, 3) k_rs_local(DevPlan P, RangeDev 
             else lbj = mid;
         }
     }
+    sT[t] = valid ? (float)(xj - xa) : 3.0e38f;
     const int nbl = __ldg(R.nb_lo + j), nbc = __ldg(R.nb_cnt + j);
     const int wlo = __ldg(R.blk_win + 4 * b), inlo = __ldg(R.blk_win + 4 * b + 1);
     const int inhi = __ldg(R.blk_win + 4 * b + 2), whi = __ldg(R.blk_win + 4 * b + 3);
@@ -188,7 +238,7 @@ __global__ void __launch_bounds__(kRsTargets, 3) k_rs_local(DevPlan P, RangeDev 
             // interval range; warp w reduces the union of chunk w
             if (base > 0) __syncthreads();             // the previous group's last chunk is done
             const int v = base + t;
-            int lohi = 1, e = 0;
+            int lohi = 1, e = 0, cnt = 0;
             float h = 0.f, l = 0.f;
             if (v < total) {
                 const bool left = v < nL;
@@ -196,6 +246,24 @@ __global__ void __launch_bounds__(kRsTargets, 3) k_rs_local(DevPlan P, RangeDev 
                 const double xr = rs_xext(P, e) - xa;
                 rs::grid_split(xr, G, h, l);
                 lohi = rs::source_range(xr, left, span, R.delta, P.dt, R.bp2, R.cell, cscale, R.nint);
+                if ((lohi & 0x7fff) <= (lohi >> 16)) {
+                    // targets within delta of the source (an estimate: float positions)
+                    const float xf = (float)xr, df = (float)R.delta;
+                    int a = 0, bnd = nT;
+                    while (a < bnd) {
+                        const int mid = (a + bnd) >> 1;
+                        if (sT[mid] > xf - df) bnd = mid;
+                        else a = mid + 1;
+                    }
+                    int c = a;
+                    bnd = nT;
+                    while (c < bnd) {
+                        const int mid = (c + bnd) >> 1;
+                        if (sT[mid] >= xf + df) bnd = mid;
+                        else c = mid + 1;
+                    }
+                    cnt = c - a;
+                }
             }
             sMeta[t] = make_float4(h, l, __int_as_float(e), __int_as_float(lohi));
             const int lo = lohi & 0x7fff, hi = lohi >> 16;
@@ -203,10 +271,12 @@ __global__ void __launch_bounds__(kRsTargets, 3) k_rs_local(DevPlan P, RangeDev 
             for (int o = 16; o > 0; o >>= 1) {
                 u0 = min(u0, __shfl_xor_sync(0xffffffffu, u0, o));
                 u1 = max(u1, __shfl_xor_sync(0xffffffffu, u1, o));
+                cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
             }
             if (lane == 0) {
                 sU[0][warp] = u0;
                 sU[1][warp] = u1;
+                sP[warp] = cnt;
             }
         }
         // the chunk's densities, sigma^{n+1-m} of source k at sSig[m][k] (pairs)
@@ -222,6 +292,19 @@ __global__ void __launch_bounds__(kRsTargets, 3) k_rs_local(DevPlan P, RangeDev 
         __syncthreads();
         const float4* meta = sMeta + grp;
         const int U0 = sU[0][grp / kRsChunk], U1 = sU[1][grp / kRsChunk];
+        if (U1 >= U0 && 2 * sP[grp / kRsChunk] < kRsChunk * (U1 - U0 + 1)) {
+            // few pairs per e-vector: each pair folds its own (no windows, no shared records)
+            if (valid) {
+                const int kend = min(kRsChunk, total - base), kL = min(kend, max(0, nL - base));
+                const float4* cf = (const float4*)R.coef;
+                rs_direct<-1>(meta, sSig, sIv, R.cell, cscale, R.nint, R.iv_dt, cf, R.mr, R.nm, 0, kL, (int)lbj, nbl, nbc,
+                              hj, lj, trL, a0h, a0l, a1h, a1l);
+                rs_direct<1>(meta, sSig, sIv, R.cell, cscale, R.nint, R.iv_dt, cf, R.mr, R.nm, kL, kend, (int)lbj, nbl,
+                             nbc, -hj, -lj, trR, a0h, a0l, a1h, a1l);
+            }
+            __syncthreads();
+            continue;
+        }
         const int lohi_lane = __float_as_int(meta[lane].w);
         const int lo_lane = lohi_lane & 0x7fff, hi_lane = lohi_lane >> 16;
         for (int W0 = U0; W0 <= U1; W0 += kRsIvCap) {

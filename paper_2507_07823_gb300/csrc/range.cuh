@@ -148,9 +148,8 @@ WAVE1D_RS_HD F4 load4(const float* p) {
 }
 
 // acc += e0 + z (e1 + z P(z)),  P(z) = e2 + z (e3 + z (e4 + z (e5 + z (e6 + z e7)))),
-// z = zh + zl normalised; e is a packed record
-WAVE1D_RS_HD void evec_eval(const float* e, float zh, float zl, float& ah, float& al) {
-    const F4 r0 = load4(e), r1 = load4(e + 4), r2 = load4(e + 8);   // (e0h e0l e1h e1l) (e2..e5) (e6 e7 - -)
+// z = zh + zl normalised; r0 = (e0h e0l e1h e1l), r1 = (e2 .. e5), r2 = (e6 e7 - -)
+WAVE1D_RS_HD void evec_eval4(const F4& r0, const F4& r1, const F4& r2, float zh, float zl, float& ah, float& al) {
     float P = fma_(r2.y, zh, r2.x);                 // e7 z + e6
     P = fma_(P, zh, r1.w);                          // + e5
     P = fma_(P, zh, r1.z);
@@ -169,6 +168,16 @@ WAVE1D_RS_HD void evec_eval(const float* e, float zh, float zl, float& ah, float
     float s, se;
     two_sum(r0.x, p, s, se);
     acc_add(ah, al, s, add(r0.y, add(pe, se)));
+}
+
+// the same from a packed record e (12 floats, 16-byte aligned)
+WAVE1D_RS_HD void evec_eval(const float* e, float zh, float zl, float& ah, float& al) {
+    evec_eval4(load4(e), load4(e + 4), load4(e + 8), zh, zl, ah, al);
+}
+
+// the same from an e-vector held in registers
+WAVE1D_RS_HD void evec_eval_v(const EVec& v, float zh, float zl, float& ah, float& al) {
+    evec_eval4(F4{v.e0h, v.e0l, v.e1h, v.e1l}, F4{v.e2, v.e3, v.e4, v.e5}, F4{v.e6, v.e7, 0.f, 0.f}, zh, zl, ah, al);
 }
 
 // ---------------------------------------------------------------------------------------------

@@ -6,9 +6,9 @@
 //
 // Mode "sum": the local sums c_j = sum_l sum_{m >= 1} Q_m(d_jl) h[m][l] of every spring, once with
 // the stored FP64 weights of an ordinary plan and once with the range-mode arithmetic of
-// range.cuh driven through the same chunks, interval windows, interval walk and order as the
-// k_rs_local kernel (the e-vector of each (source, interval) recomputed per pair, which gives the
-// same bits).  Prints "ok <max |difference| / max |row sum|> <pairs>".
+// range.cuh driven through the same chunks, interval windows (or, in chunks with few pairs per
+// e-vector, one pass per pair), interval walk and order as the k_rs_local kernel (the e-vector of
+// each (source, interval) recomputed per pair, which gives the same bits).  Prints "ok <max |difference| / max |row sum|> <pairs>".
 //
 // Input: mode M dt tol bc, then M positions (mode fit: only dt tol; M positions ignored).
 #include <algorithm>
@@ -81,6 +81,13 @@ void side_pairs(const HostPlan& hp, const std::vector<float>& ivt, const float* 
     }
 }
 
+// a chunk where the kernel folds one e-vector per pair: sources [k0, k1) once, no windows
+template <int S>
+void direct_pairs(const HostPlan& hp, const std::vector<float>& ivt, const float* meta, int k0, int k1, int64_t lbj,
+                  int nbl, int nbc, float bh, float bl, rs::Track& tr, float acc[4]) {
+    side_pairs<S>(hp, ivt, meta, k0, k1, 0, INT_MAX, lbj, nbl, nbc, bh, bl, tr, acc);
+}
+
 // the kernel's traversal for one block, every target of it
 void block_sums(const HostPlan& hp, int64_t b, std::vector<double>& out) {
     const RangeTables& rt = hp.rt;
@@ -100,6 +107,8 @@ void block_sums(const HostPlan& hp, int64_t b, std::vector<double>& out) {
         rs::Track trL{}, trR{};
     };
     std::vector<T> st(nT);
+    std::vector<float> sT(nT);
+    for (int t = 0; t < nT; t++) sT[t] = (float)(hp.x[j0 + t] - xa);
     for (int t = 0; t < nT; t++) {
         const int64_t j = j0 + t;
         rs::grid_split(hp.x[j] - xa, G, st[t].hj, st[t].lj);
@@ -112,7 +121,7 @@ void block_sums(const HostPlan& hp, int64_t b, std::vector<double>& out) {
     const int C = 32, CAP = 32;
     for (int base = 0; base < total; base += C) {
         float meta[4 * 32];
-        int U0 = INT_MAX, U1 = -1;
+        int U0 = INT_MAX, U1 = -1, pairs_est = 0;
         for (int k = 0; k < C; k++) {
             const int v = base + k;
             int lohi = 1, e = 0;
@@ -133,9 +142,23 @@ void block_sums(const HostPlan& hp, int64_t b, std::vector<double>& out) {
             if (lo <= hi) {
                 U0 = std::min(U0, lo);
                 U1 = std::max(U1, hi);
+                // the kernel's estimate of the source's targets within delta (float positions)
+                const float xf = (float)(xext(hp, e) - xa), df = (float)hp.P.delta;
+                const int a = (int)(std::upper_bound(sT.begin(), sT.end(), xf - df) - sT.begin());
+                const int c = (int)(std::lower_bound(sT.begin() + a, sT.end(), xf + df) - sT.begin());
+                pairs_est += c - a;
             }
         }
         const int kend = std::min(C, total - base), kL = std::min(kend, std::max(0, nL - base));
+        if (U1 >= U0 && 2 * pairs_est < C * (U1 - U0 + 1)) {
+            for (int t = 0; t < nT; t++) {
+                T& s = st[t];
+                const int64_t j = j0 + t;
+                direct_pairs<-1>(hp, ivt, meta, 0, kL, s.lbj, hp.nb_lo[j], hp.nb_cnt[j], s.hj, s.lj, s.trL, s.acc);
+                direct_pairs<1>(hp, ivt, meta, kL, kend, s.lbj, hp.nb_lo[j], hp.nb_cnt[j], -s.hj, -s.lj, s.trR, s.acc);
+            }
+            continue;
+        }
         for (int W0 = U0; W0 <= U1; W0 += CAP) {
             const int W1 = std::min(U1, W0 + CAP - 1);
             for (int t = 0; t < nT; t++) {
