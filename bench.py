@@ -619,21 +619,27 @@ def forms_beside_fp64(torch, w, steps, warmup=3):
                                       "lists: --adjoint-only)"}
     except Exception as e:
         out["adjoint"] = {"error": repr(e)[:300]}
-    # batched: the batched workload's 256 instances with M up to 1e4, one persistent launch per step
+    # batched: the batched workload's 256 instances (M up to 1e5), each instance's form chosen from
+    # its layout: the small ones joined (one persistent launch), the large ones plans without pair
+    # lists (concurrent branches of the step graph)
     try:
-        nb = 20
-        ws = workloads.config3_instances(m_range=(1e2, 1e4), Nt=5 + nb + 1)
-        batch = wave1d.Batch(ws)
+        nb = 10
+        ws = workloads.config3_instances(Nt=3 + nb + 1)
+        t0 = time.perf_counter()
+        batch = wave1d.Batch(ws, local_weights=2)
+        t_plan = time.perf_counter() - t0
         try:
-            batch.solve(5, with_sigma=False)
+            forms = batch.forms
+            batch.solve(3, with_sigma=False)
             st = {}
             ms = timed(lambda: st.update(rc=wave1d.lib().wave1d_batch_solve(batch.h, nb, None, None, 1)))
             if st["rc"] != 0:
                 raise RuntimeError(wave1d.lib().wave1d_batch_strerror().decode())
             out["batched"] = {"value": batch.M * nb / (ms * 1e-3), "ms_per_step": ms / nb, "M_total": batch.M,
-                              "one_launch": batch.one_launch,
-                              "workload": "256 periodic instances, M log-uniform in [1e2, 1e4], dt = 1e-3, tol 1e-12, "
-                                          "p = 8 (the workload's M up to 1e5 needs computed weights: not built)"}
+                              "one_launch_joined": batch.one_launch, "plan_seconds": t_plan,
+                              "instances_without_pair_lists": int(forms.sum()),
+                              "workload": "256 periodic instances, M log-uniform in [1e2, 1e5], dt = 1e-3, tol 1e-12, "
+                                          "p = 8, 10 steps after 3"}
         finally:
             batch.close()
     except Exception as e:

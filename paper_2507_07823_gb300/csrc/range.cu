@@ -178,6 +178,58 @@ __device__ __forceinline__ void rs_direct(const float4* sMeta, const float2* sSi
     }
 }
 
+// One side of one target in a block whose targets lie farther apart than two window widths (each
+// target meets few of the block's sources): the thread walks its own sources nearest first (left:
+// e = lb_j - 1, lb_j - 2, ..; right: e = lb_j, lb_j + 1, ..) until they lie beyond delta, with the
+// shared path's per-source data (position on the block grid, interval range over the block, the
+// walk and the near/far rule) and one e-vector per pair folded from the density ring itself; no
+// shared staging, no barriers.
+template <int S>
+__device__ __forceinline__ void rs_sparse_side(const DevPlan& P, const RangeDev& R, const float* ivt, float cscale,
+                                               rs::Grid G, double xa, double span, double xj, int64_t n, int wlo,
+                                               int whi, int lbj, int nbl, int nbc, float bh, float bl, rs::Track& tr,
+                                               float& a0h, float& a0l, float& a1h, float& a1l) {
+    const double reach = R.delta * (1.0 + 8.0 * rs::kRangeMargin);
+    const float4* coef = (const float4*)R.coef;
+    for (int q = 0;; q++) {
+        const int e = S > 0 ? lbj + q : lbj - 1 - q;
+        if (S > 0 ? e >= whi : e < wlo) break;
+        const double xe = rs_xext(P, e);
+        if (!((S > 0 ? xe - xj : xj - xe) < reach)) break;     // the farther ones lie farther still
+        const double xr = xe - xa;
+        const int lohi = rs::source_range(xr, S < 0, span, R.delta, P.dt, R.bp2, R.cell, cscale, R.nint);
+        const int lo = lohi & 0x7fff, hi = lohi >> 16;
+        if (lo > hi) continue;
+        float h, l;
+        rs::grid_split(xr, G, h, l);
+        float zh, zl;
+        rs::z_of<S>(tr, h, l, zh, zl);
+        if (fabsf(zh) > rs::kZTol) rs::walk<S>(ivt, R.cell, cscale, R.nint, bh, bl, h, l, tr, zh, zl);
+        if (lohi & 0x8000) rs::near_side<S>(ivt, R.iv_dt, (unsigned)(e - nbl) < (unsigned)nbc, bh, bl, h, l, tr, zh, zl);
+        if (!(fabsf(zh) <= rs::kZTol && tr.iv >= lo && tr.iv <= hi)) continue;
+        const int64_t sp = rs_spring(e, P.M);
+        rs::EVec ev;
+        rs::evec_zero(ev);
+        const int m0 = __ldg(R.mr + 2 * tr.iv), m1 = __ldg(R.mr + 2 * tr.iv + 1);
+        const float4* c = coef + (size_t)tr.iv * R.nm * 3;
+#pragma unroll 1
+        for (int m = m0; m <= m1; m++) {
+            const float2 sg = __ldg((const float2*)P.sig2 + (int64_t)ring_slot(n + 1 - m, P.ring) * P.M + sp);
+            const float4 c01 = __ldg(c + 3 * m), c23 = __ldg(c + 3 * m + 1), c47 = __ldg(c + 3 * m + 2);
+            rs::acc_mac(ev.e0h, ev.e0l, c01.x, c01.y, sg.x, sg.y);
+            rs::acc_mac(ev.e1h, ev.e1l, c01.z, c01.w, sg.x, sg.y);
+            ev.e2 = rs::fma_(c23.y, sg.x, rs::fma_(c23.x, sg.x, ev.e2));
+            ev.e3 = rs::fma_(c23.w, sg.x, rs::fma_(c23.z, sg.x, ev.e3));
+            ev.e4 = rs::fma_(c47.x, sg.x, ev.e4);
+            ev.e5 = rs::fma_(c47.y, sg.x, ev.e5);
+            ev.e6 = rs::fma_(c47.z, sg.x, ev.e6);
+            ev.e7 = rs::fma_(c47.w, sg.x, ev.e7);
+        }
+        if (q & 1) rs::evec_eval_v(ev, zh, zl, a1h, a1l);
+        else rs::evec_eval_v(ev, zh, zl, a0h, a0l);
+    }
+}
+
 __global__ void __launch_bounds__(kRsTargets, 3) k_rs_local(DevPlan P, RangeDev R) {
     extern __shared__ __align__(16) float rs_sm[];
     float* sE = rs_sm;
@@ -231,6 +283,17 @@ __global__ void __launch_bounds__(kRsTargets, 3) k_rs_local(DevPlan P, RangeDev 
     rs::track_to(sIv, 0, hj, lj, trL);
     rs::track_to(sIv, 0, -hj, -lj, trR);
 
+    if (span > 2.0 * R.delta) {
+        // targets farther apart than two window widths: no shared e-vectors to speak of
+        if (valid) {
+            rs_sparse_side<-1>(P, R, sIv, cscale, G, xa, span, xj, n, wlo, whi, (int)lbj, nbl, nbc, hj, lj, trL, a0h, a0l,
+                               a1h, a1l);
+            rs_sparse_side<1>(P, R, sIv, cscale, G, xa, span, xj, n, wlo, whi, (int)lbj, nbl, nbc, -hj, -lj, trR, a0h,
+                              a0l, a1h, a1l);
+            P.clocal[j] = ((double)a0h + (double)a0l) + ((double)a1h + (double)a1l);
+        }
+        return;
+    }
     for (int base = 0; base < total; base += kRsChunk) {
         const int grp = base & (kRsTargets - 1);       // the chunk's place in its group of 8
         if (grp == 0) {

@@ -7,7 +7,8 @@
 // Mode "sum": the local sums c_j = sum_l sum_{m >= 1} Q_m(d_jl) h[m][l] of every spring, once with
 // the stored FP64 weights of an ordinary plan and once with the range-mode arithmetic of
 // range.cuh driven through the same chunks, interval windows (or, in chunks with few pairs per
-// e-vector, one pass per pair), interval walk and order as the k_rs_local kernel (the e-vector of
+// e-vector, one pass per pair; in blocks whose targets lie farther apart than two window widths,
+// each target's own sources), interval walk and order as the k_rs_local kernel (the e-vector of
 // each (source, interval) recomputed per pair, which gives the same bits).  Prints "ok <max |difference| / max |row sum|> <pairs>".
 //
 // Input: mode M dt tol bc, then M positions (mode fit: only dt tol; M positions ignored).
@@ -88,6 +89,41 @@ void direct_pairs(const HostPlan& hp, const std::vector<float>& ivt, const float
     side_pairs<S>(hp, ivt, meta, k0, k1, 0, INT_MAX, lbj, nbl, nbc, bh, bl, tr, acc);
 }
 
+// a block whose targets lie farther apart than two window widths: each target walks its own
+// sources nearest first on one side until they lie beyond delta (the kernel's sparse-block path)
+template <int S>
+void sparse_side(const HostPlan& hp, const std::vector<float>& ivt, rs::Grid G, double xa, double span, int64_t j,
+                 int wlo, int whi, int64_t lbj, float bh, float bl, rs::Track& tr, float acc[4]) {
+    const RangeTables& rt = hp.rt;
+    const int64_t M = hp.P.M;
+    const double xj = hp.x[j], reach = hp.P.delta * (1.0 + 8.0 * rs::kRangeMargin);
+    const int nbl = hp.nb_lo[j], nbc = hp.nb_cnt[j];
+    for (int q = 0;; q++) {
+        const int64_t e = S > 0 ? lbj + q : lbj - 1 - q;
+        if (S > 0 ? e >= whi : e < wlo) break;
+        const double xe = xext(hp, e);
+        if (!((S > 0 ? xe - xj : xj - xe) < reach)) break;
+        const double xr = xe - xa;
+        const int lohi = rs::source_range(xr, S < 0, span, hp.P.delta, hp.P.dt, rt.bp2.data(), rt.cell.data(),
+                                          rt.cell_scale, rt.nint);
+        const int lo = lohi & 0x7fff, hi = lohi >> 16;
+        if (lo > hi) continue;
+        float h, l;
+        rs::grid_split(xr, G, h, l);
+        float zh, zl;
+        rs::z_of<S>(tr, h, l, zh, zl);
+        if (std::fabs(zh) > rs::kZTol)
+            rs::walk<S>(ivt.data(), rt.cell.data(), rt.cell_scale, rt.nint, bh, bl, h, l, tr, zh, zl);
+        if (lohi & 0x8000)
+            rs::near_side<S>(ivt.data(), rt.iv_dt, (unsigned)(e - nbl) < (unsigned)nbc, bh, bl, h, l, tr, zh, zl);
+        if (!(std::fabs(zh) <= rs::kZTol && tr.iv >= lo && tr.iv <= hi)) continue;
+        float rec[12];
+        evec_of(rt, tr.iv, e < 0 ? e + M : (e >= M ? e - M : e), rec);
+        float* a = acc + 2 * (q & 1);
+        rs::evec_eval(rec, zh, zl, a[0], a[1]);
+    }
+}
+
 // the kernel's traversal for one block, every target of it
 void block_sums(const HostPlan& hp, int64_t b, std::vector<double>& out) {
     const RangeTables& rt = hp.rt;
@@ -117,6 +153,15 @@ void block_sums(const HostPlan& hp, int64_t b, std::vector<double>& out) {
         st[t].lbj = lbj;
         rs::track_to(ivt.data(), 0, st[t].hj, st[t].lj, st[t].trL);
         rs::track_to(ivt.data(), 0, -st[t].hj, -st[t].lj, st[t].trR);
+    }
+    if (span > 2.0 * hp.P.delta) {
+        for (int t = 0; t < nT; t++) {
+            T& s = st[t];
+            sparse_side<-1>(hp, ivt, G, xa, span, j0 + t, wlo, whi, s.lbj, s.hj, s.lj, s.trL, s.acc);
+            sparse_side<1>(hp, ivt, G, xa, span, j0 + t, wlo, whi, s.lbj, -s.hj, -s.lj, s.trR, s.acc);
+            out[j0 + t] = ((double)s.acc[0] + (double)s.acc[1]) + ((double)s.acc[2] + (double)s.acc[3]);
+        }
+        return;
     }
     const int C = 32, CAP = 32;
     for (int base = 0; base < total; base += C) {
