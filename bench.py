@@ -540,7 +540,8 @@ def forms_beside_fp64(torch, w, steps, warmup=3):
         error against the oracle is in error_vs_oracle.mixed.
       adjoint: the adjoint recipe at M = 1e4 with stored weights, both strategies and central
         differences on 8 stiffnesses (--adjoint-only adds M = 1e5 and 32 stiffnesses);
-      batched: the batched workload's 256 instances with M up to 1e4, one launch per step."""
+      batched: the batched workload's 256 instances (M up to 1e5), each instance's form chosen from
+        its layout (joined in one launch per step, or its own plan without pair lists)."""
     from paper_2507_07823_gb300 import wave1d, workloads
 
     out = {}
