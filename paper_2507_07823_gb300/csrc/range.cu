@@ -133,6 +133,47 @@ __device__ __forceinline__ void rs_pairs(const float* sE, const float4* sMeta, c
     }
 }
 
+// The pairs of one side for one target in a chunk whose interval range takes several windows of
+// e-vectors: the sources in walk order (right: k ascending; left: k descending, so the distance
+// grows along both) from the thread's cursor cur, evaluated in the window that holds their
+// interval.  A source whose interval lies beyond the window stops the walk there (the tracked
+// interval kept, the cursor on it) until the next window; so each source is walked once per
+// thread and chunk, not once per window.  Sources beyond delta end the side.  k0 .. k1 - 1: the
+// side's sources in the chunk; par alternates the two accumulators.
+template <int S>
+__device__ __forceinline__ void rs_pairs_cursor(const float* sE, const float4* sMeta, const float* ivt, const int* cell,
+                                                float cscale, int nint, int iv_dt, int k0, int k1, int& cur, int W0,
+                                                int W1, int lbj, int nbl, int nbc, float bh, float bl, rs::Track& tr,
+                                                int& par, float& a0h, float& a0l, float& a1h, float& a1l) {
+    while (S > 0 ? cur < k1 : cur >= k0) {
+        const int k = cur;
+        const float4 mt = sMeta[k];
+        const int e = __float_as_int(mt.z), lohi = __float_as_int(mt.w);
+        const int lo = lohi & 0x7fff, hi = lohi >> 16;
+        if (lo > hi || (S < 0 ? e >= lbj : e < lbj)) {
+            cur += S;
+            continue;
+        }
+        if (lo > W1) break;                                   // its interval lies in a later window
+        float zh, zl;
+        rs::z_of<S>(tr, mt.x, mt.y, zh, zl);
+        if (fabsf(zh) > rs::kZTol) rs::walk<S>(ivt, cell, cscale, nint, bh, bl, mt.x, mt.y, tr, zh, zl);
+        if (lohi & 0x8000)
+            rs::near_side<S>(ivt, iv_dt, (unsigned)(e - nbl) < (unsigned)nbc, bh, bl, mt.x, mt.y, tr, zh, zl);
+        if (tr.iv > W1 && fabsf(zh) <= rs::kZTol) break;     // a later window
+        if (fabsf(zh) <= rs::kZTol && tr.iv >= lo && tr.iv <= hi && tr.iv >= W0) {
+            const float* rec = sE + (tr.iv - W0) * kRsRow + k * rs::kERecord;
+            if (par) rs::evec_eval(rec, zh, zl, a1h, a1l);
+            else rs::evec_eval(rec, zh, zl, a0h, a0l);
+            par ^= 1;
+        } else if (zh > rs::kZTol && tr.iv == nint - 1) {
+            cur = S > 0 ? k1 : k0 - 1;                         // beyond delta, and the rest farther
+            break;
+        }
+        cur += S;
+    }
+}
+
 // The pairs of one side for one target in a chunk where e-vectors would hardly be shared (the
 // chunk's interval range holds more than twice as many (source, interval) e-vectors as it has
 // pairs, as where springs lie farther apart than the intervals are wide): each pair folds its own
@@ -370,6 +411,9 @@ __global__ void __launch_bounds__(kRsTargets, 3) k_rs_local(DevPlan P, RangeDev 
         }
         const int lohi_lane = __float_as_int(meta[lane].w);
         const int lo_lane = lohi_lane & 0x7fff, hi_lane = lohi_lane >> 16;
+        const bool multi = U1 - U0 + 1 > kRsIvCap;
+        const int kend_c = min(kRsChunk, total - base), kL_c = min(kend_c, max(0, nL - base));
+        int curL = kL_c - 1, curR = kL_c, par = 0;
         for (int W0 = U0; W0 <= U1; W0 += kRsIvCap) {
             const int W1 = min(U1, W0 + kRsIvCap - 1);
             // e-vectors of the intervals [W0, W1]: warp per interval, lane per source
@@ -406,12 +450,16 @@ __global__ void __launch_bounds__(kRsTargets, 3) k_rs_local(DevPlan P, RangeDev 
                 rec[2] = make_float4(ev.e6, ev.e7, 0.f, 0.f);
             }
             __syncthreads();
-            if (valid) {
-                const int kend = min(kRsChunk, total - base), kL = min(kend, max(0, nL - base));
-                rs_pairs<-1>(sE, meta, sIv, R.cell, cscale, R.nint, R.iv_dt, 0, kL, W0, W1, (int)lbj, nbl, nbc, hj, lj, trL,
-                             a0h, a0l, a1h, a1l);
-                rs_pairs<1>(sE, meta, sIv, R.cell, cscale, R.nint, R.iv_dt, kL, kend, W0, W1, (int)lbj, nbl, nbc, -hj, -lj,
-                            trR, a0h, a0l, a1h, a1l);
+            if (valid && multi) {
+                rs_pairs_cursor<-1>(sE, meta, sIv, R.cell, cscale, R.nint, R.iv_dt, 0, kL_c, curL, W0, W1, (int)lbj, nbl,
+                                    nbc, hj, lj, trL, par, a0h, a0l, a1h, a1l);
+                rs_pairs_cursor<1>(sE, meta, sIv, R.cell, cscale, R.nint, R.iv_dt, kL_c, kend_c, curR, W0, W1, (int)lbj,
+                                   nbl, nbc, -hj, -lj, trR, par, a0h, a0l, a1h, a1l);
+            } else if (valid) {
+                rs_pairs<-1>(sE, meta, sIv, R.cell, cscale, R.nint, R.iv_dt, 0, kL_c, W0, W1, (int)lbj, nbl, nbc, hj, lj,
+                             trL, a0h, a0l, a1h, a1l);
+                rs_pairs<1>(sE, meta, sIv, R.cell, cscale, R.nint, R.iv_dt, kL_c, kend_c, W0, W1, (int)lbj, nbl, nbc, -hj,
+                            -lj, trR, a0h, a0l, a1h, a1l);
             }
             __syncthreads();
         }

@@ -82,6 +82,48 @@ void side_pairs(const HostPlan& hp, const std::vector<float>& ivt, const float* 
     }
 }
 
+// a chunk of several windows: the sources of one side in walk order from the cursor, each walked
+// once (the kernel's rs_pairs_cursor)
+template <int S>
+void cursor_pairs(const HostPlan& hp, const std::vector<float>& ivt, const float* meta, int k0, int k1, int& cur,
+                  int W0, int W1, int64_t lbj, int nbl, int nbc, float bh, float bl, rs::Track& tr, int& par,
+                  float acc[4]) {
+    const RangeTables& rt = hp.rt;
+    const int64_t M = hp.P.M;
+    while (S > 0 ? cur < k1 : cur >= k0) {
+        const int k = cur;
+        const float* mt = meta + 4 * k;
+        int e, lohi;
+        std::memcpy(&e, mt + 2, 4);
+        std::memcpy(&lohi, mt + 3, 4);
+        const int lo = lohi & 0x7fff, hi = lohi >> 16;
+        if (lo > hi || (S < 0 ? e >= lbj : e < lbj)) {
+            cur += S;
+            continue;
+        }
+        if (lo > W1) break;
+        float zh, zl;
+        rs::z_of<S>(tr, mt[0], mt[1], zh, zl);
+        if (std::fabs(zh) > rs::kZTol)
+            rs::walk<S>(ivt.data(), rt.cell.data(), rt.cell_scale, rt.nint, bh, bl, mt[0], mt[1], tr, zh, zl);
+        if (lohi & 0x8000)
+            rs::near_side<S>(ivt.data(), rt.iv_dt, (unsigned)(e - nbl) < (unsigned)nbc, bh, bl, mt[0], mt[1], tr, zh,
+                             zl);
+        if (tr.iv > W1 && std::fabs(zh) <= rs::kZTol) break;
+        if (std::fabs(zh) <= rs::kZTol && tr.iv >= lo && tr.iv <= hi && tr.iv >= W0) {
+            float rec[12];
+            evec_of(rt, tr.iv, e < 0 ? e + M : (e >= M ? e - M : e), rec);
+            float* a = acc + 2 * par;
+            rs::evec_eval(rec, zh, zl, a[0], a[1]);
+            par ^= 1;
+        } else if (zh > rs::kZTol && tr.iv == rt.nint - 1) {
+            cur = S > 0 ? k1 : k0 - 1;
+            break;
+        }
+        cur += S;
+    }
+}
+
 // a chunk where the kernel folds one e-vector per pair: sources [k0, k1) once, no windows
 template <int S>
 void direct_pairs(const HostPlan& hp, const std::vector<float>& ivt, const float* meta, int k0, int k1, int64_t lbj,
@@ -204,9 +246,19 @@ void block_sums(const HostPlan& hp, int64_t b, std::vector<double>& out) {
             }
             continue;
         }
+        const bool multi = U1 - U0 + 1 > CAP;
+        std::vector<int> curL(nT, kL - 1), curR(nT, kL), par(nT, 0);
         for (int W0 = U0; W0 <= U1; W0 += CAP) {
             const int W1 = std::min(U1, W0 + CAP - 1);
-            for (int t = 0; t < nT; t++) {
+            for (int t = 0; multi && t < nT; t++) {
+                T& s = st[t];
+                const int64_t j = j0 + t;
+                cursor_pairs<-1>(hp, ivt, meta, 0, kL, curL[t], W0, W1, s.lbj, hp.nb_lo[j], hp.nb_cnt[j], s.hj, s.lj, s.trL,
+                                 par[t], s.acc);
+                cursor_pairs<1>(hp, ivt, meta, kL, kend, curR[t], W0, W1, s.lbj, hp.nb_lo[j], hp.nb_cnt[j], -s.hj, -s.lj,
+                                s.trR, par[t], s.acc);
+            }
+            for (int t = 0; !multi && t < nT; t++) {
                 T& s = st[t];
                 const int64_t j = j0 + t;
                 side_pairs<-1>(hp, ivt, meta, 0, kL, W0, W1, s.lbj, hp.nb_lo[j], hp.nb_cnt[j], s.hj, s.lj, s.trL, s.acc);

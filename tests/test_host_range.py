@@ -2,8 +2,9 @@
 
 The harness tests/native/range_check.cpp compiles the plan builder (csrc/plan_host.cpp) and the
 pair arithmetic of csrc/range.cuh with -ffp-contract=off and runs the k_rs_local kernel's traversal
-(chunks of 32 sources, interval windows, the interval walk, the e-vectors, the compensated
-accumulator) on the CPU:
+(chunks of 32 sources, interval windows walked once per source, chunks with few pairs per e-vector
+folding one per pair, blocks spanning more than two window widths walking each target's own
+sources; the interval walk, the e-vectors, the compensated accumulator) on the CPU:
 
 * the distance polynomials of the range tables reproduce the plan's own weight rule Q_m(d)
   (Sec. 4.1: N_L-point Gauss-Legendre over [d, delta] of (1 - phi) times the p-point interpolant)
@@ -66,11 +67,19 @@ def _layout(name, rng):
         return 1, 1e-3, 1e-12, np.sort(np.concatenate([base, base[:50], base[50:80] + 1e-3]))
     if name == "single":
         return 1, 1e-3, 1e-12, np.array([0.0])
+    if name == "grouped":       # groups of 100 springs dt / 12 apart, 1.5 dt between groups: chunks
+        dt = 0.01               # whose interval ranges take many e-vector windows
+        period = 100 * dt / 12 + 1.5 * dt
+        return 1, dt, 1e-12, np.sort(np.concatenate([-1.0 + k * period + np.arange(100) * dt / 12
+                                                     + rng.uniform(0, dt / 60, 100) for k in range(20)]))
+    if name == "sparse":        # blocks of 256 springs spanning several window widths
+        return 0, 1e-3, 1e-12, np.sort(rng.uniform(-np.pi, np.pi, 3000))
     raise ValueError(name)
 
 
 @pytest.mark.parametrize("name,bar", [("uniform", 4e-11), ("cluster", 4e-12), ("seam", 4e-11),
-                                      ("coincident", 4e-11), ("single", 4e-11)])
+                                      ("coincident", 4e-11), ("single", 4e-11), ("grouped", 1e-11),
+                                      ("sparse", 4e-11)])
 def test_range_sums_match_stored_weights(checker, name, bar):
     bc, dt, tol, x = _layout(name, np.random.default_rng(9))
     text = f"sum {x.size} {dt!r} {tol!r} {bc}\n" + " ".join(repr(float(v)) for v in x) + "\n"
