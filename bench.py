@@ -43,12 +43,12 @@ L2_FLUSH_BYTES = 512 << 20
 # (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the kernel sources it was taken
 # with: reported as roofline.traffic while their SHA-256 matches, else null
 STEP_KERNEL_SOURCES = ["step.cu", "grid_sync.cuh", "phases.cuh", "device_common.cuh", "internal.h"]
-STEP_TRAFFIC = {"sources_sha256": "fd4b65c8954f13382a1ec6a21aee738ffaefebd6ac8391607d8abde3052152a1", "bytes_per_launch": 316604416 + 4018432}
+STEP_TRAFFIC = {"sources_sha256": "0453b92af3711282c1935bfbfe99074ca9290f375d132ba9ff09e97526413ac9", "bytes_per_launch": 316612437 + 4545109}
 L2_CLEAN_BYTES = 256 << 20
 # DRAM bytes of one k_rs_local launch from one ncu capture of the clustered layout at M = 2e5 (its
 # pairs below), for the kernel sources it was taken with (null once they change)
 RS_LOCAL_SOURCES = ["range.cu", "range.cuh", "phases.cuh", "device_common.cuh", "internal.h"]
-RS_LOCAL_TRAFFIC = {"sources_sha256": "1489e279f79dec7d841311135afe36ac62cf233bfa75ea742a8c7c618dd95239", "bytes_per_launch": 71748096.0, "pairs": 2935880666}
+RS_LOCAL_TRAFFIC = {"sources_sha256": "3b8b29ccbe01c9db3548bd9b08fc635e68d5ec064449b29392f4d5ef30967b2e", "bytes_per_launch": 71751168.0, "pairs": 2935880666}
 
 
 def _peaks():
@@ -938,12 +938,20 @@ def run_free_only(args):
 def run_local_only(args):
     """The local sum of the plan without pair lists alone (k_rs_local) on the clustered recipe at
     --local-M springs in --local-clusters clusters (50,000 springs per cluster keeps the million-
-    spring workload's cluster density): 2 steps, then 3 profiled steps.  The small case the
-    kernel's full profiles are taken on; not a benchmark line."""
+    spring workload's cluster density), or with --local-uniform on a uniform instance of the
+    batched workload's recipe: 2 steps, then 3 profiled steps.  The small cases the kernel's full
+    profiles are taken on; not a benchmark line."""
     from paper_2507_07823_gb300 import build, wave1d, workloads
 
     build.build()
-    w = workloads.config2(M=args.local_M, n_clusters=args.local_clusters, Nt=100)
+    if args.local_uniform:
+        # the batched workload's largest instance: uniform, dt = 1e-3, tol 1e-12, p = 8
+        w = workloads.make(f"uniform_M{args.local_M}", M=args.local_M, bc=workloads.PERIODIC, dt=1e-3, Nt=100,
+                           tol=1e-12, p=8, seed=7823 + 3, amp=(1.0,), center=(-2.0,), width=(0.1,), R=4)
+        label = f"uniform, M = {w.M}, dt = 1e-3, tol 1e-12, p = 8 (the batched workload's instance recipe)"
+    else:
+        w = workloads.config2(M=args.local_M, n_clusters=args.local_clusters, Nt=100)
+        label = f"clustered recipe, M = {w.M}, {args.local_clusters} clusters"
     plan = wave1d.Plan.from_workload(w, local_weights=1)
     plan.solve(2, with_sigma=False)
     wave1d.wave1d_profile(plan.h, 1)
@@ -952,7 +960,7 @@ def run_local_only(args):
     ms, steps = wave1d.wave1d_profile_read(plan.h)
     info = plan.info
     plan.close()
-    print(json.dumps({"workload": f"clustered recipe, M = {w.M}, {args.local_clusters} clusters", "M": w.M,
+    print(json.dumps({"workload": label, "M": w.M,
                       "local_pairs": info.local_pairs, "local_ms": float(ms[0] / steps),
                       "solve_ms": float(ms[wave1d.STAGES.index("solve")] / steps),
                       "pairs_per_s": info.local_pairs / (ms[0] / steps * 1e-3)}))
@@ -1069,6 +1077,8 @@ def main():
                     help="only the local sum of the plan without pair lists on a clustered case (not a benchmark line)")
     ap.add_argument("--local-M", type=int, default=250000)
     ap.add_argument("--local-clusters", type=int, default=4)
+    ap.add_argument("--local-uniform", action="store_true",
+                    help="--local-only on a uniform instance of the batched workload's recipe (--local-M springs)")
     ap.add_argument("--mixed-only", action="store_true",
                     help="only the FP64 and mixed-precision marches of the benchmark workload (not a benchmark line)")
     ap.add_argument("--batched-only", action="store_true",
