@@ -525,6 +525,100 @@ static void range_tables_cached(const Params& P, RangeTables& rt) {
     cache.push_back(Entry{P.dt, P.delta, P.b, cap, P.W, P.NL, P.m_max, P.p, rt});
 }
 
+// History tables (eqs. pkqkcomp, hkcompdisc, the mode rotation, the NUFFT deconvolution, the FFT
+// twiddles): functions of dt, K, W, N_g, the window and the fine grid alone, so plans that share
+// them (the instances of a batched plan) compute them once; the last few are kept.
+static void history_tables_build(const Params& P, const Window& win, HostPlan& hp) {
+    const double dt = P.dt;
+    std::vector<double> gx, gw;
+    gauss_legendre(P.Ng, gx, gw);
+    int K1 = P.K + 1;
+    std::vector<double> mu(P.Ng), wt(P.Ng), d1(P.W * P.Ng), d2(P.W * P.Ng);
+    for (int g = 0; g < P.Ng; g++) {
+        mu[g] = 0.5 * dt * (gx[g] + 1.0);
+        wt[g] = 0.5 * dt * gw[g];
+    }
+    for (int m = 0; m < P.W; m++)
+        for (int g = 0; g < P.Ng; g++) {
+            double tau = m * dt + mu[g];
+            d1[m * P.Ng + g] = win.dphi(tau);
+            d2[m * P.Ng + g] = win.ddphi(tau);
+        }
+    hp.pq.assign((size_t)P.W * K1 * 2, 0.0);
+    parallel_for(K1, [&](int64_t a, int64_t b) {
+        for (int64_t k = a; k < b; k++) {
+            double kd = (double)k;
+            for (int m = 0; m < P.W; m++) {
+                double sp = 0.0, sq = 0.0;
+                for (int g = 0; g < P.Ng; g++) {
+                    double tau = m * dt + mu[g];
+                    double psi = 2.0 * std::cos(kd * tau) * d1[m * P.Ng + g] +
+                                 sinc_k(kd, tau) * d2[m * P.Ng + g];       // eq. psidef
+                    sp += wt[g] * sinc_k(kd, dt - mu[g]) * psi;
+                    sq += wt[g] * std::cos(kd * (dt - mu[g])) * psi;
+                }
+                hp.pq[((size_t)m * K1 + k) * 2 + 0] = dt * sp;               // eq. hkcompdisc
+                hp.pq[((size_t)m * K1 + k) * 2 + 1] = dt * sq;
+            }
+        }
+    });
+    hp.rot.assign((size_t)K1 * 3, 0.0);
+    for (int k = 0; k < K1; k++) {
+        hp.rot[k * 3 + 0] = std::cos(k * dt);
+        hp.rot[k * 3 + 1] = sinc_k(k, dt);
+        hp.rot[k * 3 + 2] = k * std::sin(k * dt);
+    }
+    std::vector<double> modefac;
+    nufft_factors(P, hp.deconv1, hp.deconv2, modefac);
+    hp.twiddle.assign((size_t)P.L * 2, 0.0);
+    for (int j = 0; j < P.L; j++) {
+        double a = 2.0 * kPi * (double)j / (double)P.L;
+        hp.twiddle[2 * j] = std::cos(a);
+        hp.twiddle[2 * j + 1] = std::sin(a);
+    }
+    // per-mode factors of the real-FFT post/pre-processing folded with the deconvolution
+    hp.modefac = modefac;
+    hp.tw2K.assign((size_t)4 * P.K, 0.0);
+    for (int a = 0; a < 2 * P.K; a++) {
+        double ang = kPi * (double)a / (double)P.K;
+        hp.tw2K[2 * a] = std::cos(ang);
+        hp.tw2K[2 * a + 1] = std::sin(ang);
+    }
+}
+
+static void history_tables(const Params& P, const Window& win, HostPlan& hp) {
+    struct Entry {
+        double dt, b, delta, kb_beta;
+        int K, W, Ng, nf, L, nufft_w;
+        std::vector<double> pq, rot, deconv1, deconv2, twiddle, modefac, tw2K;
+    };
+    static std::mutex mu;
+    static std::vector<Entry> cache;
+    auto same = [&](const Entry& e) {
+        return e.dt == P.dt && e.b == P.b && e.delta == P.delta && e.kb_beta == P.kb_beta && e.K == P.K &&
+               e.W == P.W && e.Ng == P.Ng && e.nf == P.nf && e.L == P.L && e.nufft_w == P.nufft_w;
+    };
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        for (const Entry& e : cache)
+            if (same(e)) {
+                hp.pq = e.pq;
+                hp.rot = e.rot;
+                hp.deconv1 = e.deconv1;
+                hp.deconv2 = e.deconv2;
+                hp.twiddle = e.twiddle;
+                hp.modefac = e.modefac;
+                hp.tw2K = e.tw2K;
+                return;
+            }
+    }
+    history_tables_build(P, win, hp);
+    std::lock_guard<std::mutex> lock(mu);
+    if (cache.size() >= 4) cache.erase(cache.begin());
+    cache.push_back(Entry{P.dt, P.b, P.delta, P.kb_beta, P.K, P.W, P.Ng, P.nf, P.L, P.nufft_w, hp.pq, hp.rot,
+                          hp.deconv1, hp.deconv2, hp.twiddle, hp.modefac, hp.tw2K});
+}
+
 // ---------------------------------------------------------------------------------------------
 int build_host_plan(const double* x_in, const double* beta_in, int64_t M, int bc, double dt,
                     int64_t Nt, double tol, int p, double gamma, int W, int NL, int Ng, int nufft_w,
@@ -602,62 +696,7 @@ int build_host_plan(const double* x_in, const double* beta_in, int64_t M, int bc
     Window win(P.delta, P.b);
 
     // history kernels p_k, q_k (eq. pkqkcomp) with Ng-point Gauss-Legendre, dt folded in
-    {
-        std::vector<double> gx, gw;
-        gauss_legendre(P.Ng, gx, gw);
-        int K1 = P.K + 1;
-        std::vector<double> mu(P.Ng), wt(P.Ng), d1(P.W * P.Ng), d2(P.W * P.Ng);
-        for (int g = 0; g < P.Ng; g++) {
-            mu[g] = 0.5 * dt * (gx[g] + 1.0);
-            wt[g] = 0.5 * dt * gw[g];
-        }
-        for (int m = 0; m < P.W; m++)
-            for (int g = 0; g < P.Ng; g++) {
-                double tau = m * dt + mu[g];
-                d1[m * P.Ng + g] = win.dphi(tau);
-                d2[m * P.Ng + g] = win.ddphi(tau);
-            }
-        hp.pq.assign((size_t)P.W * K1 * 2, 0.0);
-        parallel_for(K1, [&](int64_t a, int64_t b) {
-            for (int64_t k = a; k < b; k++) {
-                double kd = (double)k;
-                for (int m = 0; m < P.W; m++) {
-                    double sp = 0.0, sq = 0.0;
-                    for (int g = 0; g < P.Ng; g++) {
-                        double tau = m * dt + mu[g];
-                        double psi = 2.0 * std::cos(kd * tau) * d1[m * P.Ng + g] +
-                                     sinc_k(kd, tau) * d2[m * P.Ng + g];       // eq. psidef
-                        sp += wt[g] * sinc_k(kd, dt - mu[g]) * psi;
-                        sq += wt[g] * std::cos(kd * (dt - mu[g])) * psi;
-                    }
-                    hp.pq[((size_t)m * K1 + k) * 2 + 0] = dt * sp;               // eq. hkcompdisc
-                    hp.pq[((size_t)m * K1 + k) * 2 + 1] = dt * sq;
-                }
-            }
-        });
-        hp.rot.assign((size_t)K1 * 3, 0.0);
-        for (int k = 0; k < K1; k++) {
-            hp.rot[k * 3 + 0] = std::cos(k * dt);
-            hp.rot[k * 3 + 1] = sinc_k(k, dt);
-            hp.rot[k * 3 + 2] = k * std::sin(k * dt);
-        }
-        std::vector<double> modefac;
-        nufft_factors(P, hp.deconv1, hp.deconv2, modefac);
-        hp.twiddle.assign((size_t)P.L * 2, 0.0);
-        for (int j = 0; j < P.L; j++) {
-            double a = 2.0 * kPi * (double)j / (double)P.L;
-            hp.twiddle[2 * j] = std::cos(a);
-            hp.twiddle[2 * j + 1] = std::sin(a);
-        }
-        // per-mode factors of the real-FFT post/pre-processing folded with the deconvolution
-        hp.modefac = modefac;
-        hp.tw2K.assign((size_t)4 * P.K, 0.0);
-        for (int a = 0; a < 2 * P.K; a++) {
-            double ang = kPi * (double)a / (double)P.K;
-            hp.tw2K[2 * a] = std::cos(ang);
-            hp.tw2K[2 * a + 1] = std::sin(ang);
-        }
-    }
+    history_tables(P, win, hp);
 
     // spreading weights and bins by first grid index
     spread_weights(P, hp.x, hp.sp_i0, hp.sp_ker);
