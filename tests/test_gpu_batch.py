@@ -142,3 +142,25 @@ def test_every_instance_without_pair_lists():
         if w.M <= 200:
             s_ref, u_ref = wfp.from_workload(w).run(150)
             assert _rel(sb, s_ref[1:]) < 1e-9 and _rel(ub, u_ref[1:]) < 1e-9, i
+
+
+def test_instances_over_the_weight_budget_go_without_pair_lists():
+    """local_weights = 2 with opts.max_local_bytes too small for the larger instances' stored
+    weights: an instance whose weights would pass what is left of the budget is planned without
+    pair lists instead of failing the plan, and still equals its own plan bit for bit."""
+    ws = _instances()
+    batch = wave1d.Batch(ws, local_weights=2, max_local_bytes=200_000)
+    try:
+        forms = batch.forms
+        assert forms[0] == 0 and forms.sum() >= 1, forms
+        s, u = batch.solve(200)
+    finally:
+        batch.close()
+    for i, w in enumerate(ws):
+        sb = s[:, batch.offsets[i]:batch.offsets[i + 1]]
+        ub = u[:, batch.r_offsets[i]:batch.r_offsets[i + 1]]
+        s1, u1 = _own_plan(w, 200, int(forms[i]))
+        if forms[i]:
+            assert np.array_equal(sb, s1) and np.array_equal(ub, u1), i
+        else:
+            assert _rel(sb, s1) < 1e-12 and _rel(ub, u1) < 1e-12, i
