@@ -1093,17 +1093,19 @@ int build_items(const LocalRows& rows, LocalItems& it) {
             for (int i = 0; i < nm; i++) off[i + 1] = off[i] + cnt[i];
             for (int64_t c = it.item_ptr[j]; c < it.item_ptr[j + 1]; c++) {
                 int r0 = (int)(32 * (c - it.item_ptr[j]));
-                for (int l = 0; l < 32; l++) {
-                    int r = r0 + l;
-                    if (r < ns) it.src[c * 32 + l] = rows.src[rows.src_off[j] + r];
-                    for (int t = 0; t < it.len[c]; t++) {
-                        int i = it.s0[c] + t;
-                        if (i < nm && r < ns && cnt[i] > r) {
-                            int64_t from = 2 * (rows.w_off[j] + off[i] + r);
-                            int64_t to = 2 * (it.wbase[c] + 64 * (int64_t)(t >> 1) + 2 * l + (t & 1));
-                            it.w[to] = rows.w[from];
-                            it.w[to + 1] = rows.w[from + 1];
-                        }
+                for (int l = 0; l < 32; l++)
+                    if (r0 + l < ns) it.src[c * 32 + l] = rows.src[rows.src_off[j] + r0 + l];
+                // slice by slice, lanes innermost: both the row's m-major weights and the item's
+                // element pairs are read and written contiguously
+                for (int t = 0; t < it.len[c]; t++) {
+                    int i = it.s0[c] + t;
+                    if (i >= nm) continue;
+                    const int lanes = std::min<int64_t>(32, std::min<int64_t>(ns, (int64_t)cnt[i]) - r0);
+                    for (int l = 0; l < lanes; l++) {
+                        int64_t from = 2 * (rows.w_off[j] + off[i] + r0 + l);
+                        int64_t to = 2 * (it.wbase[c] + 64 * (int64_t)(t >> 1) + 2 * l + (t & 1));
+                        it.w[to] = rows.w[from];
+                        it.w[to + 1] = rows.w[from + 1];
                     }
                 }
             }
