@@ -712,41 +712,12 @@ int wave1d_batch_plan(int n_inst, const int64_t* offsets, const double* x, const
     p->R_all = r_offsets ? r_offsets[n_inst] : 0;
     p->Nt = Nt;
     auto R_of = [&](int b) { return r_offsets ? r_offsets[b + 1] - r_offsets[b] : (int64_t)0; };
-    // the form of each instance: opts.local_weights, or (2) by its largest block and pair count
-    p->form.assign((size_t)n_inst, o.local_weights == 1 ? 1 : 0);
-    if (o.local_weights == 2) {
-        const double delta = window_steps(tol, o.gamma, o.W) * dt;
-        for (int b = 0; b < n_inst; b++) {
-            const InstanceShape sh = instance_shape(x + offsets[b], offsets[b + 1] - offsets[b], dt, delta);
-            if (sh.largest_block > o.max_block || sh.pairs > kBatchPairs) p->form[b] = 1;
-        }
-    }
-    // the joined instances' own tables (an instance over the remaining weight budget goes without
-    // pair lists under local_weights = 2), then joined
+    // the form of each instance and the joined ones' own tables (batch_host.cpp), then joined
     std::vector<HostPlan> inst;
     std::vector<int> joined;
     std::string err;
-    int64_t bytes = 0;
-    for (int b = 0; b < n_inst; b++) {
-        if (p->form[b] != 0) continue;
-        const int64_t M = offsets[b + 1] - offsets[b];
-        HostPlan h;
-        int rc = build_host_plan(x + offsets[b], beta + offsets[b], M, WAVE1D_PERIODIC, dt, Nt, tol, o.p, o.gamma, o.W,
-                                 o.NL, o.Ng, 0, o.rbc_period, o.max_block, o.max_local_bytes - bytes, h, err);
-        if (rc == WAVE1D_ENOMEM && o.local_weights == 2) {
-            p->form[b] = 1;
-            continue;
-        }
-        if (rc == WAVE1D_OK) {
-            double none = 0.0;
-            const int64_t R = R_of(b);
-            rc = build_receivers(h, R ? xr + r_offsets[b] : &none, R, err);
-        }
-        if (rc) return cleanup(bfail(rc, "instance " + std::to_string(b) + ": " + err));
-        bytes += (int64_t)h.litems.w.size() * 4;
-        inst.push_back(std::move(h));
-        joined.push_back(b);
-    }
+    if (int rc = batch_instances(n_inst, offsets, x, beta, r_offsets, xr, dt, Nt, tol, o, p->form, joined, inst, err))
+        return cleanup(bfail(rc, err));
     p->B = (int)joined.size();
     p->has_joined = p->B > 0;
     if (p->has_joined) {

@@ -168,4 +168,47 @@ InstanceShape instance_shape(const double* x, int64_t M, double dt, double delta
     return out;
 }
 
+int batch_instances(int n_inst, const int64_t* offsets, const double* x, const double* beta,
+                    const int64_t* r_offsets, const double* xr, double dt, int64_t Nt, double tol,
+                    const wave1d_opts& o, std::vector<int>& form, std::vector<int>& joined,
+                    std::vector<HostPlan>& inst, std::string& err) {
+    auto R_of = [&](int b) { return r_offsets ? r_offsets[b + 1] - r_offsets[b] : (int64_t)0; };
+    form.assign((size_t)n_inst, o.local_weights == 1 ? 1 : 0);
+    if (o.local_weights == 2) {
+        const double delta = window_steps(tol, o.gamma, o.W) * dt;
+        for (int b = 0; b < n_inst; b++) {
+            const InstanceShape sh = instance_shape(x + offsets[b], offsets[b + 1] - offsets[b], dt, delta);
+            if (sh.largest_block > o.max_block || sh.pairs > kBatchPairs) form[b] = 1;
+        }
+    }
+    joined.clear();
+    inst.clear();
+    int64_t bytes = 0;
+    for (int b = 0; b < n_inst; b++) {
+        if (form[b] != 0) continue;
+        const int64_t M = offsets[b + 1] - offsets[b];
+        HostPlan h;
+        std::string why;
+        int rc = build_host_plan(x + offsets[b], beta + offsets[b], M, WAVE1D_PERIODIC, dt, Nt, tol, o.p, o.gamma, o.W,
+                                 o.NL, o.Ng, 0, o.rbc_period, o.max_block, o.max_local_bytes - bytes, h, why);
+        if (rc == WAVE1D_ENOMEM && o.local_weights == 2) {
+            form[b] = 1;
+            continue;
+        }
+        if (rc == WAVE1D_OK) {
+            double none = 0.0;
+            const int64_t R = R_of(b);
+            rc = build_receivers(h, R ? xr + r_offsets[b] : &none, R, why);
+        }
+        if (rc) {
+            err = "instance " + std::to_string(b) + ": " + why;
+            return rc;
+        }
+        bytes += (int64_t)h.litems.w.size() * 4;
+        inst.push_back(std::move(h));
+        joined.push_back(b);
+    }
+    return WAVE1D_OK;
+}
+
 }  // namespace wave1d

@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "../../include/wave1d.h"
 
 namespace wave1d {
 
@@ -36,5 +37,18 @@ struct InstanceShape {
 };
 InstanceShape instance_shape(const double* x, int64_t M, double dt, double delta);
 constexpr int64_t kBatchPairs = (int64_t)1 << 19;
+
+// The instances of a batched plan (arguments as wave1d_batch_plan) split by form, and the joined
+// ones' own tables built in instance order against one weight budget: form[b] = 0 for a joined
+// instance, 1 for one planned without pair lists (opts.local_weights 0: all joined, 1: none,
+// 2: instance_shape's rule, and an instance whose stored weights would pass what is left of
+// opts.max_local_bytes also goes without pair lists).  joined: the joined instances' indices, inst
+// their tables (build_host_plan, build_receivers).  Returns 0, or the status of the first joined
+// instance that cannot be built (err names it).  opts must hold defaults for max_block and
+// max_local_bytes (> 0).
+int batch_instances(int n_inst, const int64_t* offsets, const double* x, const double* beta,
+                    const int64_t* r_offsets, const double* xr, double dt, int64_t Nt, double tol,
+                    const wave1d_opts& o, std::vector<int>& form, std::vector<int>& joined,
+                    std::vector<HostPlan>& inst, std::string& err);
 
 }  // namespace wave1d
