@@ -2,7 +2,9 @@
 #include "batch_host.h"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <thread>
 
 #include "../../include/wave1d.h"
 
@@ -183,29 +185,54 @@ int batch_instances(int n_inst, const int64_t* offsets, const double* x, const d
     }
     joined.clear();
     inst.clear();
+    // the candidates' tables are built side by side (each against the whole budget), then taken in
+    // instance order against what is left of it: the same split as building them one after another
+    std::vector<int> cand;
+    for (int b = 0; b < n_inst; b++)
+        if (form[b] == 0) cand.push_back(b);
+    const size_t nc = cand.size();
+    std::vector<HostPlan> built(nc);
+    std::vector<int> status(nc, WAVE1D_OK);
+    std::vector<std::string> why(nc);
+    std::atomic<size_t> next{0};
+    auto work = [&] {
+        for (size_t k = next++; k < nc; k = next++) {
+            const int b = cand[k];
+            int rc = build_host_plan(x + offsets[b], beta + offsets[b], offsets[b + 1] - offsets[b], WAVE1D_PERIODIC,
+                                     dt, Nt, tol, o.p, o.gamma, o.W, o.NL, o.Ng, 0, o.rbc_period, o.max_block,
+                                     o.max_local_bytes, built[k], why[k]);
+            if (rc == WAVE1D_OK) {
+                double none = 0.0;
+                const int64_t R = R_of(b);
+                rc = build_receivers(built[k], R ? xr + r_offsets[b] : &none, R, why[k]);
+            }
+            status[k] = rc;
+        }
+    };
+    const size_t nt = std::min<size_t>(nc, std::max(1u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> pool;
+    for (size_t t = 1; t < nt; t++) pool.emplace_back(work);
+    work();
+    for (auto& th : pool) th.join();
     int64_t bytes = 0;
-    for (int b = 0; b < n_inst; b++) {
-        if (form[b] != 0) continue;
-        const int64_t M = offsets[b + 1] - offsets[b];
-        HostPlan h;
-        std::string why;
-        int rc = build_host_plan(x + offsets[b], beta + offsets[b], M, WAVE1D_PERIODIC, dt, Nt, tol, o.p, o.gamma, o.W,
-                                 o.NL, o.Ng, 0, o.rbc_period, o.max_block, o.max_local_bytes - bytes, h, why);
+    for (size_t k = 0; k < nc; k++) {
+        const int b = cand[k];
+        int rc = status[k];
+        if (rc == WAVE1D_OK && (double)built[k].loc.woff.back() * 8.0 > (double)(o.max_local_bytes - bytes)) {
+            rc = WAVE1D_ENOMEM;
+            why[k] = "local weights need " + std::to_string(built[k].loc.woff.back() * 8) +
+                     " bytes, over the budget max_local_bytes";
+        }
         if (rc == WAVE1D_ENOMEM && o.local_weights == 2) {
             form[b] = 1;
             continue;
         }
-        if (rc == WAVE1D_OK) {
-            double none = 0.0;
-            const int64_t R = R_of(b);
-            rc = build_receivers(h, R ? xr + r_offsets[b] : &none, R, why);
-        }
         if (rc) {
-            err = "instance " + std::to_string(b) + ": " + why;
+            err = "instance " + std::to_string(b) + ": " + why[k];
             return rc;
         }
-        bytes += (int64_t)h.litems.w.size() * 4;
-        inst.push_back(std::move(h));
+        bytes += (int64_t)built[k].litems.w.size() * 4;
+        inst.push_back(std::move(built[k]));
         joined.push_back(b);
     }
     return WAVE1D_OK;
