@@ -11,6 +11,11 @@
 // per instance, each instance reading its own view of the plan (its modes, S ring, FIR tail, FFT
 // buffers and fine grid).  Every launch reads the step index from the device counter, so one step
 // is captured once in a CUDA graph and replayed.
+//
+// Instances too large or too dense for stored weights are not joined: each is a plan of its own
+// without pair lists (range.cu), and the step graph holds its ordinary step as one branch (its
+// private stream forked after the joined instances' step and joined before the graph's end,
+// plan_hooks.h), so those instances run concurrently with one another.
 #include <cuda_runtime.h>
 
 #include <algorithm>
