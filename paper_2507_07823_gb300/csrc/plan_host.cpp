@@ -260,7 +260,11 @@ int build_local(const Params& P, const Window& win, const std::vector<double>& x
     csr.src.assign(np, 0);
     csr.mrange.assign(np, 0);
     csr.woff.assign(np + 1, 0);
-    // first pass: ranges
+    // first pass: each pair's weights and their non-zero m range.  Where even m_max + 1 weights per
+    // pair fit the budget the weights are kept per row and copied into place afterwards; otherwise
+    // (the budget may refuse the layout) only the ranges are kept and a second pass recomputes them.
+    const bool keep = (double)np * (double)(P.m_max + 1) * 8.0 <= (double)max_bytes;
+    std::vector<std::vector<double>> rowbuf(keep ? T : 0);
     std::vector<int32_t> lo(np), cnt(np);
     std::atomic<int64_t> nearby{0};
     parallel_for(T, [&](int64_t a, int64_t b) {
@@ -279,6 +283,7 @@ int build_local(const Params& P, const Window& win, const std::vector<double>& x
                 if (first < 0) { first = m0; last = m0 - 1; }
                 lo[q] = first;
                 cnt[q] = last - first + 1;
+                if (keep) rowbuf[j].insert(rowbuf[j].end(), Q.begin() + first, Q.begin() + last + 1);
                 if (d < P.dt) nb++;
             }
         }
@@ -298,6 +303,12 @@ int build_local(const Params& P, const Window& win, const std::vector<double>& x
     parallel_for(T, [&](int64_t a, int64_t b) {
         std::vector<double> Q(P.m_max + 1);
         for (int64_t j = a; j < b; j++) {
+            if (keep) {
+                if (!rowbuf[j].empty())
+                    std::copy(rowbuf[j].begin(), rowbuf[j].end(), csr.w.begin() + csr.woff[csr.row_ptr[j]]);
+                std::vector<double>().swap(rowbuf[j]);
+                continue;
+            }
             for (size_t e = 0; e < pairs[j].size(); e++) {
                 int64_t q = csr.row_ptr[j] + (int64_t)e;
                 rule.weights(pairs[j][e].second, Q.data());
