@@ -185,55 +185,75 @@ int batch_instances(int n_inst, const int64_t* offsets, const double* x, const d
     }
     joined.clear();
     inst.clear();
-    // the candidates' tables are built side by side (each against the whole budget), then taken in
-    // instance order against what is left of it: the same split as building them one after another
+    // The candidates are built side by side in groups whose stored weights, bounded above by
+    // (pairs + M) (m_max + 1) doubles each, fit together in what is left of the budget (so none of
+    // them can fail it, and their host memory stays within it); a candidate that does not fit
+    // alone is built alone against the rest of the budget.  Each group is then taken in instance
+    // order with the budget's exact accounting: the same split as one build after another.
     std::vector<int> cand;
     for (int b = 0; b < n_inst; b++)
         if (form[b] == 0) cand.push_back(b);
     const size_t nc = cand.size();
-    std::vector<HostPlan> built(nc);
-    std::vector<int> status(nc, WAVE1D_OK);
-    std::vector<std::string> why(nc);
-    std::atomic<size_t> next{0};
-    auto work = [&] {
-        for (size_t k = next++; k < nc; k = next++) {
-            const int b = cand[k];
-            int rc = build_host_plan(x + offsets[b], beta + offsets[b], offsets[b + 1] - offsets[b], WAVE1D_PERIODIC,
-                                     dt, Nt, tol, o.p, o.gamma, o.W, o.NL, o.Ng, 0, o.rbc_period, o.max_block,
-                                     o.max_local_bytes, built[k], why[k]);
-            if (rc == WAVE1D_OK) {
-                double none = 0.0;
-                const int64_t R = R_of(b);
-                rc = build_receivers(built[k], R ? xr + r_offsets[b] : &none, R, why[k]);
-            }
-            status[k] = rc;
-        }
-    };
-    const size_t nt = std::min<size_t>(nc, std::max(1u, std::thread::hardware_concurrency()));
-    std::vector<std::thread> pool;
-    for (size_t t = 1; t < nt; t++) pool.emplace_back(work);
-    work();
-    for (auto& th : pool) th.join();
-    int64_t bytes = 0;
+    const double delta = window_steps(tol, o.gamma, o.W) * dt;
+    const int m_max = window_steps(tol, o.gamma, o.W) + (o.p + 1) / 2;
+    std::vector<double> est(nc);
     for (size_t k = 0; k < nc; k++) {
         const int b = cand[k];
-        int rc = status[k];
-        if (rc == WAVE1D_OK && (double)built[k].loc.woff.back() * 8.0 > (double)(o.max_local_bytes - bytes)) {
-            rc = WAVE1D_ENOMEM;
-            why[k] = "local weights need " + std::to_string(built[k].loc.woff.back() * 8) +
-                     " bytes, over the budget max_local_bytes";
+        const int64_t M = offsets[b + 1] - offsets[b];
+        const InstanceShape sh = instance_shape(x + offsets[b], M, dt, delta);
+        est[k] = ((double)sh.pairs * 1.01 + 2.0 * (double)M + 64.0) * (double)(m_max + 1) * 8.0;
+    }
+    const size_t hw = std::max(1u, std::thread::hardware_concurrency());
+    int64_t bytes = 0;
+    for (size_t k0 = 0; k0 < nc;) {
+        const int64_t left = o.max_local_bytes - bytes;
+        size_t k1 = k0 + 1;
+        for (double sum = est[k0]; sum <= (double)left && k1 < nc && sum + est[k1] <= (double)left; k1++)
+            sum += est[k1];
+        const size_t ng = k1 - k0;
+        std::vector<HostPlan> built(ng);
+        std::vector<int> status(ng, WAVE1D_OK);
+        std::vector<std::string> why(ng);
+        std::atomic<size_t> next{0};
+        auto work = [&] {
+            for (size_t g = next++; g < ng; g = next++) {
+                const int b = cand[k0 + g];
+                int rc = build_host_plan(x + offsets[b], beta + offsets[b], offsets[b + 1] - offsets[b],
+                                         WAVE1D_PERIODIC, dt, Nt, tol, o.p, o.gamma, o.W, o.NL, o.Ng, 0, o.rbc_period,
+                                         o.max_block, left, built[g], why[g]);
+                if (rc == WAVE1D_OK) {
+                    double none = 0.0;
+                    const int64_t R = R_of(b);
+                    rc = build_receivers(built[g], R ? xr + r_offsets[b] : &none, R, why[g]);
+                }
+                status[g] = rc;
+            }
+        };
+        std::vector<std::thread> pool;
+        for (size_t t = 1; t < std::min(ng, hw); t++) pool.emplace_back(work);
+        work();
+        for (auto& th : pool) th.join();
+        for (size_t g = 0; g < ng; g++) {
+            const int b = cand[k0 + g];
+            int rc = status[g];
+            if (rc == WAVE1D_OK && (double)built[g].loc.woff.back() * 8.0 > (double)(o.max_local_bytes - bytes)) {
+                rc = WAVE1D_ENOMEM;
+                why[g] = "local weights need " + std::to_string(built[g].loc.woff.back() * 8) +
+                         " bytes, over the budget max_local_bytes";
+            }
+            if (rc == WAVE1D_ENOMEM && o.local_weights == 2) {
+                form[b] = 1;
+                continue;
+            }
+            if (rc) {
+                err = "instance " + std::to_string(b) + ": " + why[g];
+                return rc;
+            }
+            bytes += (int64_t)built[g].litems.w.size() * 4;
+            inst.push_back(std::move(built[g]));
+            joined.push_back(b);
         }
-        if (rc == WAVE1D_ENOMEM && o.local_weights == 2) {
-            form[b] = 1;
-            continue;
-        }
-        if (rc) {
-            err = "instance " + std::to_string(b) + ": " + why[k];
-            return rc;
-        }
-        bytes += (int64_t)built[k].litems.w.size() * 4;
-        inst.push_back(std::move(built[k]));
-        joined.push_back(b);
+        k0 = k1;
     }
     return WAVE1D_OK;
 }
