@@ -11,6 +11,11 @@
 // each target's own sources), interval walk and order as the k_rs_local kernel (the e-vector of
 // each (source, interval) recomputed per pair, which gives the same bits).  Prints "ok <max |difference| / max |row sum|> <pairs>".
 //
+// Mode "tsum": the reverse march's transposed local sums out_j[m] = sum_e Q_m(d_je) cbar_e, m >= 1,
+// through the k_rs_local_T kernel's traversal (per output: the forward block's window in order,
+// the moments of the current interval flushed into out[m] when the interval changes) against the
+// stored FP64 weights.  Prints "ok <max |difference| / max |out|> <pairs>".
+//
 // Input: mode M dt tol bc, then M positions (mode fit: only dt tol; M positions ignored).
 #include <algorithm>
 #include <climits>
@@ -271,6 +276,118 @@ void block_sums(const HostPlan& hp, int64_t b, std::vector<double>& out) {
         out[j0 + t] = ((double)st[t].acc[0] + (double)st[t].acc[1]) + ((double)st[t].acc[2] + (double)st[t].acc[3]);
 }
 
+// ---- transposed local sum (the reverse march's k_rs_local_T): out_j[m] = sum_e Q_m(d_je) cbar_e ----
+static double cbar_of(int64_t l) { return std::sin(1.3 * (double)l) + 0.1; }
+
+struct Moments {
+    float f0h = 0.f, f0l = 0.f, f1h = 0.f, f1l = 0.f, f2 = 0.f, f3 = 0.f, f4 = 0.f, f5 = 0.f, f6 = 0.f, f7 = 0.f;
+};
+
+// out[m] += sum_r a_{iv,m,r} F_r, m >= 1 of the interval (the kernel's rs_flush)
+static void flush_T(const RangeTables& rt, int iv, const Moments& F, double* out) {
+    const int m0 = std::max(1, rt.mr[2 * iv]), m1 = rt.mr[2 * iv + 1];
+    for (int m = m0; m <= m1; m++) {
+        const float* c = &rt.coef[((size_t)iv * rt.nm + m) * 12];
+        float h = 0.f, l = 0.f;
+        rs::acc_mac(h, l, c[0], c[1], F.f0h, F.f0l);
+        rs::acc_mac(h, l, c[2], c[3], F.f1h, F.f1l);
+        float r = rs::fma_(c[5], F.f2, rs::fma_(c[4], F.f2, 0.f));
+        r = rs::fma_(c[7], F.f3, rs::fma_(c[6], F.f3, r));
+        r = rs::fma_(c[8], F.f4, r);
+        r = rs::fma_(c[9], F.f5, r);
+        r = rs::fma_(c[10], F.f6, r);
+        r = rs::fma_(c[11], F.f7, r);
+        rs::acc_add(h, l, r, 0.f);
+        out[m] += (double)h + (double)l;
+    }
+}
+
+// F += cbar z^r (the kernel's rs_moments_add)
+static void moments_add(Moments& F, float zh, float zl, float ch, float cl) {
+    rs::acc_add(F.f0h, F.f0l, ch, cl);
+    rs::acc_mac(F.f1h, F.f1l, zh, zl, ch, cl);
+    const float z2 = rs::mul(zh, zh);
+    float p = rs::mul(z2, ch);
+    F.f2 = rs::add(F.f2, p);
+    p = rs::mul(p, zh);
+    F.f3 = rs::add(F.f3, p);
+    p = rs::mul(p, zh);
+    F.f4 = rs::add(F.f4, p);
+    p = rs::mul(p, zh);
+    F.f5 = rs::add(F.f5, p);
+    p = rs::mul(p, zh);
+    F.f6 = rs::add(F.f6, p);
+    p = rs::mul(p, zh);
+    F.f7 = rs::add(F.f7, p);
+}
+
+// one output block of 128 springs, traversed as k_rs_local_T does: the forward block's window in
+// chunks of 32 inputs, each output walking its inputs side by side and flushing the moments of its
+// current interval when the interval changes
+static void block_sums_T(const HostPlan& hp, int64_t B, std::vector<double>& out) {
+    const RangeTables& rt = hp.rt;
+    const int64_t M = hp.P.M, j0 = B * kRsTTargets;
+    const int nT = (int)std::min<int64_t>(kRsTTargets, M - j0);
+    const int64_t b = j0 / kRsTargets;
+    const int wlo = hp.blk_win[4 * b], inlo = hp.blk_win[4 * b + 1], inhi = hp.blk_win[4 * b + 2],
+              whi = hp.blk_win[4 * b + 3];
+    const int nL = std::max(0, inhi - wlo), total = nL + std::max(0, whi - inlo);
+    const double xa = hp.x[j0], span = hp.x[j0 + nT - 1] - xa;
+    const rs::Grid G = rs::grid_of(span, hp.P.delta);
+    std::vector<float> ivt(4 * (size_t)rt.nint);
+    for (int iv = 0; iv < rt.nint; iv++) rs::interval_on_grid(rt.mid[iv], rt.ih[iv], G, &ivt[4 * (size_t)iv]);
+    for (int t = 0; t < nT; t++) {
+        const int64_t j = j0 + t;
+        float hj, lj;
+        rs::grid_split(hp.x[j] - xa, G, hj, lj);
+        int64_t lbj = j;
+        while (lbj > 0 && hp.x[lbj - 1] == hp.x[j]) lbj--;
+        rs::Track trL, trR;
+        rs::track_to(ivt.data(), 0, hj, lj, trL);
+        rs::track_to(ivt.data(), 0, -hj, -lj, trR);
+        int cur = -1;
+        Moments F;
+        double* o = &out[(size_t)j * rt.nm];
+        const int nbl = hp.nb_lo[j], nbc = hp.nb_cnt[j];
+        for (int v = 0; v < total; v++) {
+            const bool left = v < nL;
+            const int e = left ? wlo + v : inlo + (v - nL);
+            const double xr = xext(hp, e) - xa;
+            float h, l;
+            rs::grid_split(xr, G, h, l);
+            const int lohi = rs::source_range(xr, left, span, hp.P.delta, hp.P.dt, rt.bp2.data(), rt.cell.data(),
+                                              rt.cell_scale, rt.nint);
+            if ((lohi & 0x7fff) > (lohi >> 16) || (left ? e >= lbj : e < lbj)) continue;
+            float zh, zl;
+            rs::Track& tr = left ? trL : trR;
+            const float bh = left ? hj : -hj, bl = left ? lj : -lj;
+            if (left) {
+                rs::z_of<-1>(tr, h, l, zh, zl);
+                if (std::fabs(zh) > rs::kZTol)
+                    rs::walk<-1>(ivt.data(), rt.cell.data(), rt.cell_scale, rt.nint, bh, bl, h, l, tr, zh, zl);
+                if (lohi & 0x8000)
+                    rs::near_side<-1>(ivt.data(), rt.iv_dt, (unsigned)(e - nbl) < (unsigned)nbc, bh, bl, h, l, tr, zh, zl);
+            } else {
+                rs::z_of<1>(tr, h, l, zh, zl);
+                if (std::fabs(zh) > rs::kZTol)
+                    rs::walk<1>(ivt.data(), rt.cell.data(), rt.cell_scale, rt.nint, bh, bl, h, l, tr, zh, zl);
+                if (lohi & 0x8000)
+                    rs::near_side<1>(ivt.data(), rt.iv_dt, (unsigned)(e - nbl) < (unsigned)nbc, bh, bl, h, l, tr, zh, zl);
+            }
+            if (!(std::fabs(zh) <= rs::kZTol)) continue;
+            if (tr.iv != cur) {
+                if (cur >= 0) flush_T(rt, cur, F, o);
+                cur = tr.iv;
+                F = Moments();
+            }
+            const double c = cbar_of(e < 0 ? e + M : (e >= M ? e - M : e));
+            const float ch = (float)c;
+            moments_add(F, zh, zl, ch, (float)(c - (double)ch));
+        }
+        if (cur >= 0) flush_T(rt, cur, F, o);
+    }
+}
+
 }  // namespace
 
 int main() {
@@ -331,6 +448,26 @@ int main() {
                         err)) {
         std::printf("error %s\n", err.c_str());
         return 1;
+    }
+    if (std::strcmp(mode, "tsum") == 0) {
+        // the transposed sums per m against the stored FP64 weights: ref_j[m] = sum_e Q_m(d_je) cbar_e
+        const int nm = hr.rt.nm;
+        std::vector<double> tref((size_t)M * nm, 0.0), tgot((size_t)M * nm, 0.0);
+        const LocalCSR& C = hs.loc;
+        for (int64_t j = 0; j < M; j++)
+            for (int64_t e = C.row_ptr[j]; e < C.row_ptr[j + 1]; e++) {
+                const int lo = C.mrange[e] & 0xffff, cnt = C.mrange[e] >> 16;
+                for (int c = 0; c < cnt; c++) tref[(size_t)j * nm + lo + c] += C.w[C.woff[e] + c] * cbar_of(C.src[e]);
+            }
+        const int64_t nb = (M + kRsTTargets - 1) / kRsTTargets;
+        for (int64_t B = 0; B < nb; B++) block_sums_T(hr, B, tgot);
+        double worst = 0.0, scale = 0.0;
+        for (size_t i = 0; i < tref.size(); i++) {
+            worst = std::max(worst, std::fabs(tgot[i] - tref[i]));
+            scale = std::max(scale, std::fabs(tref[i]));
+        }
+        std::printf("ok %.3e %zu\n", worst / scale, C.src.size());
+        return 0;
     }
     std::vector<double> ref(M, 0.0), got(M, 0.0);
     const LocalCSR& Cs = hs.loc;

@@ -12,7 +12,9 @@ sources; the interval walk, the e-vectors, the compensated accumulator) on the C
   device evaluates;
 * the local sums of every spring equal those of the stored FP64 weights of an ordinary plan: within
   2e-12 of the largest row sum where rows hold thousands of pairs, 4e-11 where they hold a few (the
-  single-float rounding of each source's curvature terms, which averages out over many sources).
+  single-float rounding of each source's curvature terms, which averages out over many sources);
+* the reverse march's transposed sums per m (its own traversal, moments flushed per interval)
+  equal the stored weights' within 1e-9.
 """
 import os
 import shutil
@@ -85,6 +87,19 @@ def test_range_sums_match_stored_weights(checker, name, bar):
     text = f"sum {x.size} {dt!r} {tol!r} {bc}\n" + " ".join(repr(float(v)) for v in x) + "\n"
     err, pairs = _run(checker, text)
     assert float(err) < bar and int(pairs) >= x.size, (err, pairs)
+
+
+@pytest.mark.parametrize("name", ["uniform", "cluster", "seam", "coincident", "single", "grouped", "sparse"])
+def test_transposed_range_sums_match_stored_weights(checker, name):
+    """The reverse march's transposed local sums out_j[m] = sum_e Q_m(d_je) cbar_e (m >= 1) through
+    the k_rs_local_T kernel's traversal (each output walking the forward block's window, the
+    moments of its current interval flushed per m when the interval changes) against the stored
+    FP64 weights: within 1e-9 of the largest sum (the curvature moments are single floats, about
+    3e-10 here; a dropped or doubled pair would show at 1e-3)."""
+    bc, dt, tol, x = _layout(name, np.random.default_rng(9))
+    text = f"tsum {x.size} {dt!r} {tol!r} {bc}\n" + " ".join(repr(float(v)) for v in x) + "\n"
+    err, pairs = _run(checker, text)
+    assert float(err) < 1e-9 and int(pairs) >= 1, (err, pairs)
 
 
 def test_range_sums_at_clustered_million_spring_density(checker):
